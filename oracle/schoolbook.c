@@ -1,0 +1,94 @@
+/*
+ * Plain C schoolbook oracle for c = a*b in Z_q[x]/(x^n+1).
+ *
+ * TEST INFRASTRUCTURE ONLY: called by the test-suite, smoke() and the
+ * cpu_baseline leg of bench.py through ctypes.  It shares nothing with the
+ * CUDA library.
+ *
+ * It writes out the definition the paper gives (Sec. 2.1 (i) and the Sec. 2.2
+ * fold rule): the coefficient of x^j is the sum of a_i*b_k over i+k = j minus
+ * the sum of a_i*b_k over i+k = j+n, reduced once into [0, q).  Every product
+ * a_i*b_k < 2^128 is formed exactly in unsigned __int128 and added to a
+ * 192-bit accumulator (three 64-bit words), so nothing can overflow for any
+ * n <= 2^62 and q < 2^64.  No blocking, no lazy reduction, no reordering.
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+typedef unsigned __int128 u128;
+
+typedef struct {
+    uint64_t w0, w1, w2; /* value = w2*2^128 + w1*2^64 + w0 */
+} acc192;
+
+static void acc_add(acc192 *s, u128 p)
+{
+    uint64_t lo = (uint64_t)p;
+    uint64_t hi = (uint64_t)(p >> 64);
+    uint64_t t = s->w0 + lo;
+    uint64_t c = t < lo;
+    s->w0 = t;
+    uint64_t u = s->w1 + hi;
+    uint64_t c2 = u < hi;
+    uint64_t v = u + c;
+    c2 += v < u;
+    s->w1 = v;
+    s->w2 += c2;
+}
+
+/* value mod q by Horner's rule in base 2^64 */
+static uint64_t acc_mod(const acc192 *s, uint64_t q)
+{
+    u128 r = s->w2 % q;
+    r = ((r << 64) | s->w1) % q;
+    r = ((r << 64) | s->w0) % q;
+    return (uint64_t)r;
+}
+
+/* One product: a, b, c are n-entry arrays of canonical residues. */
+void oracle_negacyclic(const uint64_t *a, const uint64_t *b, uint64_t *c,
+                       uint64_t n, uint64_t q)
+{
+    for (uint64_t j = 0; j < n; ++j) {
+        acc192 pos = {0, 0, 0}, neg = {0, 0, 0};
+        /* i + k = j : k = j - i for i <= j */
+        for (uint64_t i = 0; i <= j; ++i)
+            acc_add(&pos, (u128)a[i] * b[j - i]);
+        /* i + k = j + n : k = j + n - i for i > j */
+        for (uint64_t i = j + 1; i < n; ++i)
+            acc_add(&neg, (u128)a[i] * b[j + n - i]);
+        uint64_t p = acc_mod(&pos, q), m = acc_mod(&neg, q);
+        c[j] = p >= m ? p - m : (uint64_t)(((u128)p + q) - m);
+    }
+}
+
+/*
+ * Batch over a [batch][k][n] layout (uint64 entries): products
+ * first .. first+count-1, every prime of each.
+ */
+void oracle_negacyclic_batch(const uint64_t *a, const uint64_t *b, uint64_t *c,
+                             uint64_t n, const uint64_t *q_list, uint64_t k,
+                             uint64_t first, uint64_t count)
+{
+    for (uint64_t p = first; p < first + count; ++p)
+        for (uint64_t j = 0; j < k; ++j) {
+            size_t off = (size_t)((p * k + j) * n);
+            oracle_negacyclic(a + off, b + off, c + off, n, q_list[j]);
+        }
+}
+
+/* Only the listed output coefficients of one product (sampled parity). */
+void oracle_negacyclic_coeffs(const uint64_t *a, const uint64_t *b, uint64_t n, uint64_t q,
+                              const uint64_t *js, uint64_t count, uint64_t *out)
+{
+    for (uint64_t t = 0; t < count; ++t) {
+        uint64_t j = js[t];
+        acc192 pos = {0, 0, 0}, neg = {0, 0, 0};
+        for (uint64_t i = 0; i <= j; ++i)
+            acc_add(&pos, (u128)a[i] * b[j - i]);
+        for (uint64_t i = j + 1; i < n; ++i)
+            acc_add(&neg, (u128)a[i] * b[j + n - i]);
+        uint64_t p = acc_mod(&pos, q), m = acc_mod(&neg, q);
+        out[t] = p >= m ? p - m : (uint64_t)(((u128)p + q) - m);
+    }
+}
