@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: exact negacyclic products/s on one GB300.
+
+Workload (one "step"): one batch of 4096 products in Z_q[x]/(x^n+1) with
+n = 1024, q = 12289, coefficients uniform in [0, q) stored as 32-bit words
+(seeded synthetic data), computed by the library's tuned path through the
+C-ABI (polymul_batch on device buffers).
+
+Printed: ONE JSON line with the device-timed throughput (``value``), the
+end-to-end throughput through the host-buffer entry point (``e2e``), the
+roofline of the dominant kernel, the CPU-oracle baseline and the SM clocks
+sampled during the timed region.
+
+``--impl reference`` times the CPU oracle (plain C schoolbook on the host
+cores) on the same metric and workload instead; under torchrun only rank 0
+runs it.
+
+Multi-GPU: one process per GPU (torchrun); every rank runs an independent
+replica of the workload (the products are independent, nothing is
+exchanged), ``value`` counts the products of all ranks over the slowest
+rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "negacyclic polymul products/s per (n,q), tensor vs NTT, bit-exact; % roofline"
+WORKLOAD = "ring_1024: n=1024, q=12289 (q = 1 mod 2n), batch 4096 pairs, coefficients uniform in [0,q) int32, seed 2"
+L2_BYTES = 129 * 1024 * 1024
+# Integer multiply-add lanes per SM per clock (IMAD issues on one FMA
+# datapath: 16 lanes per SM sub-partition, 4 sub-partitions).
+IMAD_LANES_PER_SM = 64
+# 32-bit multiplies per modular multiplication on the NTT path (Shoup:
+# one high product, one low product, one multiply-subtract).
+IMAD_PER_MULMOD = 3
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU oracle sample budget")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ traffic record
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("ntt.cuh", "arith.cuh", "ntt_info.cuh", "polymul_types.h"):
+        with open(os.path.join(ROOT, "paper_2307_06554_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ntt_ring1024_traffic.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel") == kernel_tag and kv.get("source_sha") == _kernel_source_hash():
+            return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_rate(w, seconds: float, max_products: int = None):
+    """The oracle as it stands (plain C schoolbook, one thread per host core)
+    on whole batches of the workload, repeated until ``seconds`` elapsed."""
+    from oracle import native
+    threads = _host_cores()
+    a, b = w.a, w.b
+    if max_products:
+        a, b = a[:max_products], b[:max_products]
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        native.polymul_batch(a, b, w.q_list, threads=threads)
+        done += a.shape[0]
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return done / el, threads, done, el
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_2307_06554_gb300 import workloads as wl
+    w = wl.ring_1024()
+    from oracle import native
+    threads = _host_cores()
+    per_step = 512  # products per step: a bounded sample of the 4096-product batch
+    for i in range(args.warmup):
+        s = (i * per_step) % w.batch
+        native.polymul_batch(w.a[s:s + per_step], w.b[s:s + per_step], w.q_list, threads=threads)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        s = (i * per_step) % w.batch
+        native.polymul_batch(w.a[s:s + per_step], w.b[s:s + per_step], w.q_list, threads=threads)
+    el = time.perf_counter() - t0
+    value = args.steps * per_step / el
+    sample = "%d products of the 4096-product batch per step (rotating), plain C schoolbook oracle" % per_step
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (192-bit accumulators)",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "path": "cpu oracle", "parallelism": "host threads"},
+        "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": "products/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "gpu_launches": 0,
+    }), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = wl.ring_1024()
+    n, batch, q_list = w.n, w.batch, w.q_list
+    plan = polymul.Plan(n, q_list)
+    info = plan.info
+    elem = info["elem_bytes"]
+    set_bytes = 3 * batch * len(q_list) * n * elem
+    nsets = max(2, math.ceil(3 * L2_BYTES / set_bytes))
+    a0 = torch.from_numpy(w.a.view(np.int32)).to(dev)
+    b0 = torch.from_numpy(w.b.view(np.int32)).to(dev)
+    sets = [(a0.clone(), b0.clone(), torch.empty_like(a0)) for _ in range(nsets)]
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+
+    def step(i):
+        a, b, c = sets[i % nsets]
+        polymul.polymul_batch(plan.handle, a, b, c, batch, sp)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+    stream.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    # per-launch durations of the dominant kernel (one launch per step)
+    per = []
+    for i in range(min(args.steps, 20)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(i)
+        e1.record(stream)
+        e1.synchronize()
+        per.append(e0.elapsed_time(e1))
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    ha = torch.from_numpy(w.a.view(np.int32)).pin_memory()
+    hb = torch.from_numpy(w.b.view(np.int32)).pin_memory()
+    hc = torch.empty_like(ha).pin_memory()
+    for _ in range(2):
+        polymul.polymul_batch_host(plan.handle, ha, hb, hc, batch, None)
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        polymul.polymul_batch_host(plan.handle, ha, hb, hc, batch, None)
+    e2e_s = time.perf_counter() - t0
+    clk = clocks.stop()
+
+    # bit-exactness on a seeded sample of the batch (oracle, CPU)
+    c_last = sets[(args.warmup + args.steps - 1) % nsets][2]
+    idx = [0, 1, 2047, 4095]
+    got = c_last[idx].cpu().numpy().view(np.uint32).astype(np.uint64)
+    from oracle import native
+    want = native.polymul_batch(w.a[idx], w.b[idx], q_list)
+    host_ok = bool(np.array_equal(hc.numpy().view(np.uint32)[idx].astype(np.uint64), want))
+    bit_exact = bool(np.array_equal(got, want)) and host_ok
+
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    if rank != 0:
+        return
+    products = batch * args.steps * ws
+    value = products / (elapsed_ms / 1e3)
+    e2e_value = batch * e2e_steps / e2e_s * ws
+
+    peaks, peak_src = _peaks()
+    launch_ms = statistics.mean(per)
+    units = batch * len(q_list)
+    mulmods = units * (3 * (n // 2) * int(math.log2(n)) + n + n // 2)
+    bytes_alg = 3 * units * n * elem
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = sms * IMAD_LANES_PER_SM * sm_mhz * 1e6 / IMAD_PER_MULMOD / 1e9  # Gmulmod/s
+    alu_ach = mulmods / (launch_ms / 1e3) / 1e9
+    hbm_ach = bytes_alg / (launch_ms / 1e3) / 1e9
+    hbm_peak = peaks["hbm_gbs"]
+    traffic = _recorded_traffic("k_ntt_batch<uint32_t,10,L4>")
+    roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Gmulmod/s",
+            "frac": alu_ach / alu_peak, "traffic": traffic,
+            "kernel": "k_ntt_batch<uint32_t,10,L4> (forward x2, pointwise, inverse; one launch per step)",
+            "peak_source": "derived: %d SMs x %d IMAD lanes x %.0f MHz / %d IMAD per mulmod" % (
+                sms, IMAD_LANES_PER_SM, sm_mhz, IMAD_PER_MULMOD),
+            "mulmods_per_launch": mulmods, "launch_ms": launch_ms,
+            "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
+                    "bytes_per_launch": bytes_alg, "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, cores, done, el = cpu_oracle_rate(w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "products/s", "cores": cores, "kind": "oracle",
+               "sample": "%d products (whole 4096-product batches, repeated) in %.1f s, plain C schoolbook" % (done, el)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded uniform residues)",
+        "config": {"workload": WORKLOAD, "path": {1: "ntt", 2: "tensor"}.get(info["path"], "?"),
+                   "n": n, "q": q_list, "batch": batch,
+                   "l2": "inputs rotated over %d buffer sets (%.0f MB > 3x L2)" % (nsets, nsets * set_bytes / 2**20),
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "e2e": {"value": e2e_value, "unit": "products/s", "h2d_bytes_per_step": 2 * batch * n * elem,
+                "d2h_bytes_per_step": batch * n * elem,
+                "api": "polymul_batch_host (pinned host buffers, copies + kernel inside the timed region)"},
+        "gpu_launches": args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "bit_exact_sample": bit_exact,
+    }
+    print(json.dumps(out), flush=True)
+    plan.close()
+
+
+def main():
+    args = _args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

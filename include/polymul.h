@@ -1,0 +1,137 @@
+/*
+ * libpolymul -- exact negacyclic polynomial multiplication on GB300 (sm_103a).
+ *
+ * The operation (paper: "TPU as Cryptographic Accelerator", arXiv 2307.06554):
+ * for operands a, b in the ring Z_q[x]/(x^n+1) (Sec. 2.1, ring and Eq.
+ * equ-poly-coef: coefficient vectors a_0..a_{n-1} in Z_q) compute
+ *
+ *     c_j = ( sum_{i+k=j} a_i b_k  -  sum_{i+k=j+n} a_i b_k ) mod q,
+ *
+ * i.e. the product in Z[x] reduced by x^n = -1 (Sec. 2.2 fold rule) and taken
+ * mod q, which is the row vector a times the negacyclic matrix of b of
+ * Eq. equ-genereal-mat.  Results are canonical residues in [0, q) and are
+ * bit-exact: no floating-point rounding can reach them.
+ *
+ * Algorithm 1 of the paper maps onto this interface as follows:
+ * GenConfig / ExtractModuli / ExtractDimensions  ->  polymul_create
+ * ConvertPoly / TPUMul / ConvertMatrix            ->  inside polymul_batch.
+ * Several moduli ("RNS primes", Sec. 2.4, where residues are kept until they
+ * are needed) are handled as independent rings of the same n.
+ *
+ * Conventions for every call below.
+ *  - Data layout: operand and result arrays are C-contiguous
+ *    [batch][k][n] (product, prime, coefficient) with coefficients
+ *    contiguous.  Entry (p, j, i) belongs to the ring with modulus q_list[j].
+ *    Inputs must be canonical (in [0, q_j)); behaviour for larger inputs is
+ *    unspecified unless POLYMUL_FLAG_VALIDATE is set.
+ *  - Element type: uint32_t when every modulus of the plan is < 2^32,
+ *    otherwise uint64_t (query with polymul_plan_info).
+ *  - Ownership: the caller owns a, b and c; the plan owns its tables and any
+ *    staging memory.  c must not overlap a or b.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Device-pointer calls are asynchronous with respect to
+ *    the host; results are visible once the stream has been synchronised.
+ *  - Errors: every int-returning call returns POLYMUL_OK (0) or one of the
+ *    codes below; polymul_last_error() gives a message for the calling
+ *    thread's most recent failure.  A failing call has no other effect.
+ *  - Threads: distinct plans may be used concurrently from different
+ *    threads; one plan must not be used by two threads at once.
+ */
+#ifndef POLYMUL_H
+#define POLYMUL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define POLYMUL_OK        0
+#define POLYMUL_EINVAL    1  /* bad argument: n, q, k, null pointer, size   */
+#define POLYMUL_ENOTSUP   2  /* valid request this build cannot serve        */
+#define POLYMUL_EDOMAIN   3  /* validate flag set and an input is >= q       */
+#define POLYMUL_ENOMEM    4  /* device or host allocation failed             */
+#define POLYMUL_ETIMEOUT  5  /* a bounded device wait gave up                */
+#define POLYMUL_ECUDA     6  /* CUDA runtime error (message has the detail)  */
+
+/* ---- computation paths ---- */
+#define POLYMUL_PATH_AUTO    0  /* pick the fastest exact path (tuned)        */
+#define POLYMUL_PATH_NTT     1  /* path (a): number-theoretic transform       */
+#define POLYMUL_PATH_TENSOR  2  /* path (b): Toeplitz matrix on tensor cores  */
+
+/* ---- flags ---- */
+#define POLYMUL_FLAG_VALIDATE 1u  /* check that inputs are < q (slower)       */
+
+typedef struct polymul_opts {
+    uint32_t path;      /* POLYMUL_PATH_*                                     */
+    uint32_t flags;     /* POLYMUL_FLAG_*                                     */
+    uint32_t reserved[6];
+} polymul_opts;
+
+typedef struct polymul_plan_info {
+    uint32_t n;
+    uint32_t k;
+    uint32_t elem_bytes;  /* 4 (uint32_t) or 8 (uint64_t)                     */
+    uint32_t path;        /* the path actually used (NTT or TENSOR)           */
+    uint32_t aux_primes;  /* NTT only: number of auxiliary primes (0 = direct)*/
+    uint32_t block;       /* threads per CTA of the main kernel               */
+    uint32_t grid;        /* CTAs of the main kernel (persistent grid)        */
+    uint32_t smem_bytes;  /* dynamic shared memory per CTA                    */
+} polymul_plan_info;
+
+typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
+
+/*
+ * polymul_create -- build a plan for products in Z_q[x]/(x^n+1) for each q
+ * of q_list (Algorithm 1, GenConfig: parameters are fixed here, once).
+ *   n       power of two, 16 <= n <= 65536.
+ *   q_list  k moduli, each 2 <= q < 2^62, pairwise distinct (host memory,
+ *           read during the call only).
+ *   opts    NULL for defaults (PATH_AUTO, no flags).
+ *   out     receives the plan; untouched on failure.
+ * Device tables (roots of unity, constants) are computed and uploaded on the
+ * current CUDA device; the plan must be used on that device.
+ * Errors: EINVAL (n, q, k, duplicates, null out), ENOTSUP (no path can serve
+ * the moduli at this n, or a forced path cannot), ENOMEM, ECUDA.
+ */
+int polymul_create(uint32_t n, const uint64_t *q_list, uint32_t k,
+                   const polymul_opts *opts, polymul_plan **out);
+
+/*
+ * polymul_batch -- c = a*b for `batch` products (each with all k moduli).
+ *   a, b, c  device pointers, [batch][k][n] of the plan's element type,
+ *            16-byte aligned.  batch == 0 is a no-op.
+ *   stream   cudaStream_t or NULL.
+ * Asynchronous.  Errors: EINVAL (null pointers with batch > 0, misaligned),
+ * EDOMAIN (validate flag and an input >= q; c is then unspecified), ECUDA.
+ */
+int polymul_batch(polymul_plan *plan, const void *a, const void *b, void *c,
+                  uint64_t batch, void *stream);
+
+/*
+ * polymul_batch_host -- as polymul_batch with HOST arrays a, b, c.  The
+ * library streams chunks through plan-owned device buffers, overlapping the
+ * host-to-device copy of one chunk with the kernel of another and with the
+ * device-to-host copy of a third (Sec. 4, "optimizing computation and I/O").
+ * Page-locked host memory gives full overlap; pageable memory works but
+ * copies synchronously.  Returns after c has been written (synchronous).
+ */
+int polymul_batch_host(polymul_plan *plan, const void *a, const void *b, void *c,
+                       uint64_t batch, void *stream);
+
+/* Fill *info with the plan's shape and launch configuration. */
+int polymul_plan_info_get(const polymul_plan *plan, polymul_plan_info *info);
+
+/* Release the plan and its device memory.  NULL is a no-op.  The caller must
+ * make sure no launch of the plan is still running. */
+void polymul_destroy(polymul_plan *plan);
+
+/* Message for the calling thread's most recent failing call ("" if none).
+ * The pointer stays valid until the next call from the same thread. */
+const char *polymul_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYMUL_H */

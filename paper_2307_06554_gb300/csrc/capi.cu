@@ -1,0 +1,320 @@
+// C-ABI entry points of libpolymul (declared in include/polymul.h).
+//
+// polymul_create plays the role of GenConfig/ExtractModuli/ExtractDimensions
+// of the paper's Algorithm 1: it fixes the path, computes every per-prime
+// constant and table once and uploads them; polymul_batch then only launches
+// kernels (ConvertPoly/TPUMul/ConvertMatrix happen inside them).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/polymul.h"
+#include "host_math.h"
+#include "kernels.h"
+#include "plan.h"
+#include "polymul_types.h"
+
+using namespace pm;
+
+// ---------------------------------------------------------------- errors
+namespace pm {
+static thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(POLYMUL_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { g_err.clear(); }
+}  // namespace pm
+
+#define PM_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return pm::cuda_fail(e_, #call); \
+  } while (0)
+
+extern "C" const char* polymul_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------- tables
+namespace {
+
+template <typename W>
+void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::vector<W>& twi, PrimeConst<W>& pc) {
+  using namespace pm::host;
+  const int bits = 8 * (int)sizeof(W);
+  const int logn = __builtin_ctz(n);
+  const uint64_t psi = primitive_2n_root(q, n);
+  const uint64_t psi_inv = powmod(psi, q - 2, q);
+  twf.resize(2 * (size_t)n);
+  twi.resize(2 * (size_t)n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t r = bitrev(i, logn);
+    const uint64_t w = powmod(psi, r, q), v = powmod(psi_inv, r, q);
+    twf[2 * i] = (W)w;
+    twf[2 * i + 1] = (W)shoup_companion(w, q, bits);
+    twi[2 * i] = (W)v;
+    twi[2 * i + 1] = (W)shoup_companion(v, q, bits);
+  }
+  const uint64_t r_mod_q = bits == 64 ? (uint64_t)(((u128)1 << 64) % q) : (uint64_t)((1ull << 32) % q);
+  const uint64_t ninv = powmod(n, q - 2, q);
+  const uint64_t scale = mulmod(ninv, r_mod_q, q);
+  const uint64_t scale_w = mulmod(powmod(psi_inv, bitrev(1, logn), q), scale, q);
+  pc.q = (W)q;
+  pc.q2 = (W)(2 * q);
+  pc.qinv = (W)inv_pow2_64(q);  // low bits are the inverse mod 2^32 too
+  pc.scale = (W)scale;
+  pc.scale_p = (W)shoup_companion(scale, q, bits);
+  pc.scale_w = (W)scale_w;
+  pc.scale_wp = (W)shoup_companion(scale_w, q, bits);
+  pc.pad = 0;
+}
+
+template <typename W>
+int upload_ntt_tables(polymul_plan* p) {
+  std::vector<W> all_f, all_i, f, i;
+  std::vector<PrimeConst<W>> pcs(p->k);
+  all_f.reserve(2 * (size_t)p->n * p->k);
+  all_i.reserve(2 * (size_t)p->n * p->k);
+  for (uint32_t j = 0; j < p->k; ++j) {
+    build_ntt_tables<W>(p->q[j], p->n, f, i, pcs[j]);
+    all_f.insert(all_f.end(), f.begin(), f.end());
+    all_i.insert(all_i.end(), i.begin(), i.end());
+  }
+  const size_t tb = all_f.size() * sizeof(W);
+  PM_CUDA(cudaMalloc(&p->d_twf, tb));
+  PM_CUDA(cudaMalloc(&p->d_twi, tb));
+  PM_CUDA(cudaMalloc(&p->d_pc, pcs.size() * sizeof(PrimeConst<W>)));
+  PM_CUDA(cudaMemcpy(p->d_twf, all_f.data(), tb, cudaMemcpyHostToDevice));
+  PM_CUDA(cudaMemcpy(p->d_twi, all_i.data(), tb, cudaMemcpyHostToDevice));
+  PM_CUDA(cudaMemcpy(p->d_pc, pcs.data(), pcs.size() * sizeof(PrimeConst<W>), cudaMemcpyHostToDevice));
+  return POLYMUL_OK;
+}
+
+bool lookup_ntt(uint32_t elem, int logn, bool l4, KernelInfo* ki) {
+  if (elem == 4) return lookup_ntt_u32_small(logn, l4, ki) || lookup_ntt_u32_large(logn, l4, ki);
+  return lookup_ntt_u64(logn, l4, ki);
+}
+
+int configure_launch(polymul_plan* p) {
+  PM_CUDA(cudaGetDevice(&p->device));
+  PM_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+  if (p->ki.smem > 48 * 1024)
+    PM_CUDA(cudaFuncSetAttribute(p->ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ki.smem));
+  int per_sm = 0;
+  PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->ki.fn, p->ki.block, p->ki.smem));
+  if (per_sm < 1) return fail(POLYMUL_ENOTSUP, "kernel does not fit on an SM (block %d, smem %d)", p->ki.block, p->ki.smem);
+  p->grid_cap = per_sm * p->num_sms;
+  return POLYMUL_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- create
+extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, const polymul_opts* opts,
+                              polymul_plan** out) {
+  clear_error();
+  if (!out) return fail(POLYMUL_EINVAL, "out is NULL");
+  if (n < 16 || n > 65536 || (n & (n - 1))) return fail(POLYMUL_EINVAL, "n=%u must be a power of two in [16, 65536]", n);
+  if (k == 0 || !q_list) return fail(POLYMUL_EINVAL, "need k >= 1 moduli");
+  for (uint32_t j = 0; j < k; ++j) {
+    if (q_list[j] < 2 || q_list[j] >= (1ull << 62))
+      return fail(POLYMUL_EINVAL, "q[%u]=%llu outside [2, 2^62)", j, (unsigned long long)q_list[j]);
+    for (uint32_t i = 0; i < j; ++i)
+      if (q_list[i] == q_list[j]) return fail(POLYMUL_EINVAL, "duplicate modulus %llu", (unsigned long long)q_list[j]);
+  }
+  const uint32_t path = opts ? opts->path : POLYMUL_PATH_AUTO;
+  if (path > POLYMUL_PATH_TENSOR) return fail(POLYMUL_EINVAL, "unknown path %u", path);
+
+  polymul_plan* p = new polymul_plan();
+  p->n = n;
+  p->logn = __builtin_ctz(n);
+  p->k = k;
+  p->q.assign(q_list, q_list + k);
+  p->flags = opts ? opts->flags : 0;
+  uint64_t qmax = *std::max_element(p->q.begin(), p->q.end());
+  p->elem = qmax < (1ull << 32) ? 4 : 8;
+
+  // direct NTT: every modulus prime with 2n | q-1 and within the word bounds
+  bool ntt_ok = true;
+  for (uint64_t q : p->q) {
+    if (!pm::host::is_prime(q) || (q - 1) % (2ull * n) != 0) ntt_ok = false;
+    if (p->elem == 4 && q >= (1ull << 31)) ntt_ok = false;
+  }
+  p->l4 = p->elem == 4 ? qmax < (1ull << 30) : true;
+  if (ntt_ok && !lookup_ntt(p->elem, (int)p->logn, p->l4, &p->ki)) ntt_ok = false;
+
+  int rc = POLYMUL_OK;
+  if (path == POLYMUL_PATH_TENSOR) {
+    rc = fail(POLYMUL_ENOTSUP, "tensor path not available for this plan");
+  } else if (!ntt_ok) {
+    rc = fail(POLYMUL_ENOTSUP, "no NTT route for these moduli at n=%u (need prime q = 1 mod 2n, q < 2^31 for 32-bit words)", n);
+  } else {
+    p->path = POLYMUL_PATH_NTT;
+    rc = p->elem == 4 ? upload_ntt_tables<uint32_t>(p) : upload_ntt_tables<uint64_t>(p);
+    if (rc == POLYMUL_OK) rc = configure_launch(p);
+  }
+  if (rc != POLYMUL_OK) {
+    std::string keep = g_err;
+    polymul_destroy(p);
+    g_err = keep;
+    return rc;
+  }
+  *out = p;
+  return POLYMUL_OK;
+}
+
+extern "C" void polymul_destroy(polymul_plan* p) {
+  if (!p) return;
+  cudaFree(p->d_twf);
+  cudaFree(p->d_twi);
+  cudaFree(p->d_pc);
+  cudaFree(p->d_flag);
+  for (int s = 0; s < 2; ++s) {
+    cudaFree(p->d_stage[s]);
+    if (p->streams[s]) cudaStreamDestroy(p->streams[s]);
+  }
+  if (p->ev_entry) cudaEventDestroy(p->ev_entry);
+  delete p;
+}
+
+extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* info) {
+  clear_error();
+  if (!p || !info) return fail(POLYMUL_EINVAL, "null argument");
+  memset(info, 0, sizeof *info);
+  info->n = p->n;
+  info->k = p->k;
+  info->elem_bytes = p->elem;
+  info->path = p->path;
+  info->aux_primes = 0;
+  info->block = (uint32_t)p->ki.block;
+  info->grid = (uint32_t)p->grid_cap;
+  info->smem_bytes = (uint32_t)p->ki.smem;
+  return POLYMUL_OK;
+}
+
+// ---------------------------------------------------------------- batch
+namespace pm {
+
+template <typename W>
+__global__ void k_validate(const W* __restrict__ a, const W* __restrict__ b, uint64_t units, uint32_t n,
+                           uint32_t k, const PrimeConst<W>* __restrict__ pc, int* flag) {
+  const uint64_t total = units * n;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const W q = pc[(i / n) % k].q;
+    if (a[i] >= q || b[i] >= q) *flag = 1;
+  }
+}
+
+int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st) {
+  const uint64_t units = batch * p->k;
+  if (p->flags & POLYMUL_FLAG_VALIDATE) {
+    if (!p->d_flag) PM_CUDA(cudaMalloc(&p->d_flag, sizeof(int)));
+    PM_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), st));
+    const int grid = p->num_sms * 4;
+    if (p->elem == 4)
+      k_validate<uint32_t><<<grid, 256, 0, st>>>((const uint32_t*)a, (const uint32_t*)b, units, p->n, p->k,
+                                                 (const PrimeConst<uint32_t>*)p->d_pc, p->d_flag);
+    else
+      k_validate<uint64_t><<<grid, 256, 0, st>>>((const uint64_t*)a, (const uint64_t*)b, units, p->n, p->k,
+                                                 (const PrimeConst<uint64_t>*)p->d_pc, p->d_flag);
+    PM_CUDA(cudaGetLastError());
+    int h = 0;
+    PM_CUDA(cudaMemcpyAsync(&h, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    if (h) return fail(POLYMUL_EDOMAIN, "an input coefficient is not below its modulus");
+  }
+  const uint64_t need = (units + p->ki.units_per_cta - 1) / p->ki.units_per_cta;
+  const int grid = (int)std::min<uint64_t>(need, (uint64_t)p->grid_cap);
+  if (p->elem == 4) {
+    NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
+                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k};
+    void* argv[] = {&args};
+    PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
+  } else {
+    NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
+                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k};
+    void* argv[] = {&args};
+    PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
+  }
+  return POLYMUL_OK;
+}
+
+}  // namespace pm
+
+static bool misaligned(const void* x) { return ((uintptr_t)x & 15u) != 0; }
+
+extern "C" int polymul_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, void* stream) {
+  clear_error();
+  if (!p) return fail(POLYMUL_EINVAL, "plan is NULL");
+  if (batch == 0) return POLYMUL_OK;
+  if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
+  if (misaligned(a) || misaligned(b) || misaligned(c)) return fail(POLYMUL_EINVAL, "operands must be 16-byte aligned");
+  if (batch > (1ull << 40)) return fail(POLYMUL_EINVAL, "batch too large");
+  return launch_batch(p, a, b, c, batch, (cudaStream_t)stream);
+}
+
+// Host buffers: chunks of products flow through two plan-owned device
+// staging slots on two streams, so that the copy-in of one chunk, the kernel
+// of another and the copy-out of a third overlap.
+extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch,
+                                  void* stream) {
+  clear_error();
+  if (!p) return fail(POLYMUL_EINVAL, "plan is NULL");
+  if (batch == 0) return POLYMUL_OK;
+  if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
+  const size_t prod_bytes = (size_t)p->k * p->n * p->elem;
+  const uint64_t chunk = std::max<uint64_t>(1, (8u << 20) / prod_bytes);
+  const size_t slot_bytes = 3 * chunk * prod_bytes;
+  for (int s = 0; s < 2; ++s) {
+    if (!p->streams[s]) PM_CUDA(cudaStreamCreateWithFlags(&p->streams[s], cudaStreamNonBlocking));
+    if (p->stage_bytes < slot_bytes) {
+      cudaFree(p->d_stage[s]);
+      p->d_stage[s] = nullptr;
+      if (cudaMalloc(&p->d_stage[s], slot_bytes) != cudaSuccess)
+        return fail(POLYMUL_ENOMEM, "staging allocation of %zu bytes failed", slot_bytes);
+    }
+  }
+  p->stage_bytes = std::max(p->stage_bytes, slot_bytes);
+  if (!p->ev_entry) PM_CUDA(cudaEventCreateWithFlags(&p->ev_entry, cudaEventDisableTiming));
+  PM_CUDA(cudaEventRecord(p->ev_entry, (cudaStream_t)stream));
+  for (int s = 0; s < 2; ++s) PM_CUDA(cudaStreamWaitEvent(p->streams[s], p->ev_entry, 0));
+  const char* ha = (const char*)a;
+  const char* hb = (const char*)b;
+  char* hc = (char*)c;
+  int rc = POLYMUL_OK;
+  for (uint64_t first = 0, it = 0; first < batch; first += chunk, ++it) {
+    const uint64_t cnt = std::min<uint64_t>(chunk, batch - first);
+    const int s = (int)(it & 1);
+    cudaStream_t st = p->streams[s];
+    char* da = (char*)p->d_stage[s];
+    char* db = da + chunk * prod_bytes;
+    char* dc = db + chunk * prod_bytes;
+    const size_t off = first * prod_bytes, bytes = cnt * prod_bytes;
+    PM_CUDA(cudaMemcpyAsync(da, ha + off, bytes, cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaMemcpyAsync(db, hb + off, bytes, cudaMemcpyHostToDevice, st));
+    rc = launch_batch(p, da, db, dc, cnt, st);
+    if (rc != POLYMUL_OK) break;
+    PM_CUDA(cudaMemcpyAsync(hc + off, dc, bytes, cudaMemcpyDeviceToHost, st));
+  }
+  for (int s = 0; s < 2; ++s) {
+    cudaError_t e = cudaStreamSynchronize(p->streams[s]);
+    if (e != cudaSuccess && rc == POLYMUL_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  return rc;
+}

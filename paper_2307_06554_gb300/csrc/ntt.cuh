@@ -1,0 +1,356 @@
+// Batched negacyclic NTT polynomial multiplication, one (product, prime)
+// unit per team of threads.
+//
+// What it computes: c = a*b in Z_q[x]/(x^n+1) for prime q = 1 mod 2n
+// (the "value representation" route of Sec. 2.1 (ii) of the paper, with the
+// NTT the paper names as the O(n log n) transform; it requires the root of
+// unity that Sec. 2.1 lists among NTT's restrictions).  The negacyclic twist
+// by psi (a primitive 2n-th root) is merged into the twiddles:
+//   forward  Cooley-Tukey, natural order in, bit-reversed out, table
+//            W[k] = psi^brv(k);
+//   pointwise Montgomery product (gives a^ b^ 2^-w);
+//   inverse  Gentleman-Sande, bit-reversed in, natural out, table
+//            V[k] = psi^-brv(k); the last stage also multiplies by
+//            n^-1 * 2^w, which undoes the Montgomery factor and the 1/n.
+//
+// Register/shared-memory layout.  A thread holds R = 2^RB coefficients of
+// each operand (RB = 5 for 32-bit words, 4 for 64-bit).  The log2(n) stage
+// bits are cut into phases at multiples of RB: phase P owns bits
+// [P*RB, min((P+1)*RB, log2 n)).  Inside a phase a thread's R values are
+// whole butterfly groups (indices differing only in the phase's bits), so
+// every stage of the phase runs in registers with no communication; between
+// phases the team exchanges through shared memory, word j stored at
+// j + (j >> RB) (one pad word per 2^RB), which makes every exchange pattern
+// used here free of bank conflicts.  For n = 1024 and 32-bit words this is
+// one exchange per transform with a team of one warp (32 lanes x 32 values).
+// The top phase's layout puts consecutive lanes on consecutive coefficients,
+// so global loads and stores are fully coalesced.
+#pragma once
+#include <cstdint>
+#include <type_traits>
+#include "arith.cuh"
+#include "polymul_types.h"
+
+namespace pm {
+
+// Compile-time loop: calls f(std::integral_constant<int, i>) for i = B, B+S,
+// ... while i != E.  Keeps every register-array index a constant.
+template <int B, int E, int S = 1, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (B != E) {
+    f(std::integral_constant<int, B>{});
+    sfor<B + S, E, S>(f);
+  }
+}
+
+template <typename W>
+struct alignas(2 * sizeof(W)) TwPair {
+  W w, wp;  // root power and its Shoup companion floor(w * 2^bits / q)
+};
+
+template <typename W>
+__device__ __forceinline__ TwPair<W> ldtw(const TwPair<W>* p) {
+  if constexpr (sizeof(W) == 4) {
+    uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    return TwPair<W>{v.x, v.y};
+  } else {
+    ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
+    return TwPair<W>{v.x, v.y};
+  }
+}
+
+template <typename W, int LOGN>
+struct Shape {
+  static constexpr int RB = sizeof(W) == 4 ? 5 : 4;
+  static constexpr int RLOG = LOGN < RB ? LOGN : RB;
+  static constexpr int R = 1 << RLOG;           // values per thread per operand
+  static constexpr int N = 1 << LOGN;
+  static constexpr int T = N / R;               // threads per unit (team size)
+  static constexpr int NPH = (LOGN + RB - 1) / RB;
+  static constexpr int SLICE = N + (N >> RB);   // padded words per operand in smem
+  // keep both operands' exchange buffers when they fit comfortably
+  static constexpr bool DUAL = 2 * SLICE * (int)sizeof(W) <= 100 * 1024;
+  static constexpr int SMEM_WORDS = DUAL ? 2 * SLICE : SLICE;
+};
+
+template <typename W, int LOGN, int P>
+struct PhaseBits {
+  using S = Shape<W, LOGN>;
+  static constexpr int LO = P * S::RB;
+  static constexpr int HI = (P + 1) * S::RB < LOGN ? (P + 1) * S::RB : LOGN;
+  static constexpr int B = HI - LO;
+  static constexpr int GS = 1 << B;   // butterfly group size
+  static constexpr int NG = S::R / GS;  // groups per thread
+};
+
+// coefficient index held in register slot e by team thread t during phase P
+template <typename W, int LOGN, int P>
+__device__ __forceinline__ uint32_t elem_index(int e, uint32_t t) {
+  using PB = PhaseBits<W, LOGN, P>;
+  using S = Shape<W, LOGN>;
+  const uint32_t u = (uint32_t)e & (PB::GS - 1);
+  const uint32_t g = t + (uint32_t)S::T * (uint32_t)(e >> PB::B);
+  return (g & ((1u << PB::LO) - 1)) | (u << PB::LO) | ((g >> PB::LO) << PB::HI);
+}
+
+template <int RB>
+__device__ __forceinline__ uint32_t spos(uint32_t j) { return j + (j >> RB); }
+
+// ---------------------------------------------------------------- butterflies
+template <typename W, bool L4>
+__device__ __forceinline__ void ct_bfly(W& x, W& y, const TwPair<W>& w, const PrimeConst<W>& pc) {
+  if constexpr (L4) {  // q < 2^(bits-2): values in [0, 4q)
+    W xr = csub(x, pc.q2);
+    W t = shoup(y, w.w, w.wp, pc.q);
+    x = xr + t;
+    y = xr - t + pc.q2;
+  } else {             // q < 2^(bits-1): values in [0, 2q)
+    W xr = csub(x, pc.q);
+    W t = csub(shoup(y, w.w, w.wp, pc.q), pc.q);
+    x = xr + t;
+    y = xr - t + pc.q;
+  }
+}
+
+template <typename W, bool L4>
+__device__ __forceinline__ void gs_bfly(W& x, W& y, W w, W wp, const PrimeConst<W>& pc) {
+  if constexpr (L4) {  // values in [0, 2q)
+    W s = x + y;
+    W d = x - y + pc.q2;
+    x = csub(s, pc.q2);
+    y = shoup(d, w, wp, pc.q);
+  } else {
+    W xr = csub(x, pc.q), yr = csub(y, pc.q);
+    W d = xr - yr + pc.q;
+    x = xr + yr;
+    y = shoup(d, w, wp, pc.q);
+  }
+}
+
+// last inverse stage: both outputs also multiplied by n^-1 * 2^bits
+template <typename W, bool L4>
+__device__ __forceinline__ void gs_last(W& x, W& y, const PrimeConst<W>& pc) {
+  W s, d;
+  if constexpr (L4) {
+    s = x + y;
+    d = x - y + pc.q2;
+  } else {
+    W xr = csub(x, pc.q), yr = csub(y, pc.q);
+    s = xr + yr;
+    d = xr - yr + pc.q;
+  }
+  x = shoup(s, pc.scale, pc.scale_p, pc.q);
+  y = shoup(d, pc.scale_w, pc.scale_wp, pc.q);
+}
+
+// ---------------------------------------------------------------- phases
+// forward Cooley-Tukey stages of phase P on two operands sharing twiddles
+template <typename W, int LOGN, bool L4, int P>
+__device__ __forceinline__ void fwd_phase2(W (&xa)[Shape<W, LOGN>::R], W (&xb)[Shape<W, LOGN>::R],
+                                           const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
+                                           uint32_t t) {
+  using PB = PhaseBits<W, LOGN, P>;
+  using S = Shape<W, LOGN>;
+  sfor<PB::HI - 1, PB::LO - 1, -1>([&](auto hc) {
+    constexpr int h = decltype(hc)::value;
+    constexpr int hb = h - PB::LO;
+    sfor<0, PB::NG>([&](auto glc) {
+      constexpr int gl = decltype(glc)::value;
+      const uint32_t g = t + (uint32_t)S::T * gl;
+      const uint32_t tb = (1u << (LOGN - 1 - h)) + ((g >> PB::LO) << (PB::HI - 1 - h));
+      sfor<0, (PB::GS >> (hb + 1))>([&](auto upc) {
+        constexpr int up = decltype(upc)::value;
+        const TwPair<W> w = ldtw(tw + tb + up);
+        sfor<0, (1 << hb)>([&](auto lwc) {
+          constexpr int lw = decltype(lwc)::value;
+          constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
+          constexpr int u1 = u0 + (1 << hb);
+          ct_bfly<W, L4>(xa[u0], xa[u1], w, pc);
+          ct_bfly<W, L4>(xb[u0], xb[u1], w, pc);
+        });
+      });
+    });
+  });
+}
+
+// inverse Gentleman-Sande stages of phase P
+template <typename W, int LOGN, bool L4, int P>
+__device__ __forceinline__ void inv_phase(W (&x)[Shape<W, LOGN>::R], const TwPair<W>* __restrict__ tw,
+                                          const PrimeConst<W>& pc, uint32_t t) {
+  using PB = PhaseBits<W, LOGN, P>;
+  using S = Shape<W, LOGN>;
+  sfor<PB::LO, PB::HI>([&](auto hc) {
+    constexpr int h = decltype(hc)::value;
+    constexpr int hb = h - PB::LO;
+    sfor<0, PB::NG>([&](auto glc) {
+      constexpr int gl = decltype(glc)::value;
+      const uint32_t g = t + (uint32_t)S::T * gl;
+      const uint32_t tb = (1u << (LOGN - 1 - h)) + ((g >> PB::LO) << (PB::HI - 1 - h));
+      sfor<0, (PB::GS >> (hb + 1))>([&](auto upc) {
+        constexpr int up = decltype(upc)::value;
+        if constexpr (h == LOGN - 1) {
+          sfor<0, (1 << hb)>([&](auto lwc) {
+            constexpr int lw = decltype(lwc)::value;
+            constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
+            gs_last<W, L4>(x[u0], x[u0 + (1 << hb)], pc);
+          });
+        } else {
+          const TwPair<W> w = ldtw(tw + tb + up);
+          sfor<0, (1 << hb)>([&](auto lwc) {
+            constexpr int lw = decltype(lwc)::value;
+            constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
+            gs_bfly<W, L4>(x[u0], x[u0 + (1 << hb)], w.w, w.wp, pc);
+          });
+        }
+      });
+    });
+  });
+}
+
+template <typename W, int LOGN, int P>
+__device__ __forceinline__ void store_layout(const W (&x)[Shape<W, LOGN>::R], W* s, uint32_t t) {
+  using S = Shape<W, LOGN>;
+  sfor<0, S::R>([&](auto ec) {
+    constexpr int e = decltype(ec)::value;
+    s[spos<S::RB>(elem_index<W, LOGN, P>(e, t))] = x[e];
+  });
+}
+
+template <typename W, int LOGN, int P>
+__device__ __forceinline__ void load_layout(W (&x)[Shape<W, LOGN>::R], const W* s, uint32_t t) {
+  using S = Shape<W, LOGN>;
+  sfor<0, S::R>([&](auto ec) {
+    constexpr int e = decltype(ec)::value;
+    x[e] = s[spos<S::RB>(elem_index<W, LOGN, P>(e, t))];
+  });
+}
+
+template <typename W, int LOGN, bool L4, int P, class Sync>
+__device__ __forceinline__ void fwd_from(W (&xa)[Shape<W, LOGN>::R], W (&xb)[Shape<W, LOGN>::R], W* sa,
+                                         W* sb, const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
+                                         uint32_t t, Sync sync) {
+  using S = Shape<W, LOGN>;
+  fwd_phase2<W, LOGN, L4, P>(xa, xb, tw, pc, t);
+  if constexpr (P > 0) {
+    if constexpr (S::DUAL) {
+      sync();
+      store_layout<W, LOGN, P>(xa, sa, t);
+      store_layout<W, LOGN, P>(xb, sb, t);
+      sync();
+      load_layout<W, LOGN, P - 1>(xa, sa, t);
+      load_layout<W, LOGN, P - 1>(xb, sb, t);
+    } else {
+      sync();
+      store_layout<W, LOGN, P>(xa, sa, t);
+      sync();
+      load_layout<W, LOGN, P - 1>(xa, sa, t);
+      sync();
+      store_layout<W, LOGN, P>(xb, sa, t);
+      sync();
+      load_layout<W, LOGN, P - 1>(xb, sa, t);
+    }
+    fwd_from<W, LOGN, L4, P - 1>(xa, xb, sa, sb, tw, pc, t, sync);
+  }
+}
+
+template <typename W, int LOGN, bool L4, int P, class Sync>
+__device__ __forceinline__ void inv_from(W (&x)[Shape<W, LOGN>::R], W* s, const TwPair<W>* __restrict__ tw,
+                                         const PrimeConst<W>& pc, uint32_t t, Sync sync) {
+  using S = Shape<W, LOGN>;
+  inv_phase<W, LOGN, L4, P>(x, tw, pc, t);
+  if constexpr (P + 1 < S::NPH) {
+    sync();
+    store_layout<W, LOGN, P>(x, s, t);
+    sync();
+    load_layout<W, LOGN, P + 1>(x, s, t);
+    inv_from<W, LOGN, L4, P + 1>(x, s, tw, pc, t, sync);
+  }
+}
+
+// One unit: c = a*b mod (x^n+1, q) for one prime.  Every thread of the team
+// calls it (inactive threads with act = false compute on zeros and store
+// nothing, so that team barriers stay uniform).
+template <typename W, int LOGN, bool L4, class Sync>
+__device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* __restrict__ b, W* __restrict__ c,
+                                             const TwPair<W>* __restrict__ twf,
+                                             const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
+                                             W* sa, W* sb, uint32_t t, bool act, Sync sync) {
+  using S = Shape<W, LOGN>;
+  constexpr int TOP = S::NPH - 1;
+  W xa[S::R], xb[S::R];
+  sfor<0, S::R>([&](auto ec) {
+    constexpr int e = decltype(ec)::value;
+    const uint32_t j = elem_index<W, LOGN, TOP>(e, t);
+    xa[e] = act ? a[j] : W(0);
+    xb[e] = act ? b[j] : W(0);
+  });
+  fwd_from<W, LOGN, L4, TOP>(xa, xb, sa, sb, twf, pc, t, sync);
+  // pointwise product in the bit-reversed domain (same layout for both)
+  sfor<0, S::R>([&](auto ec) {
+    constexpr int e = decltype(ec)::value;
+    if constexpr (L4) {
+      xa[e] = csub(montmul(xa[e], xb[e], pc.q, pc.qinv), pc.q2);
+    } else {
+      xa[e] = montmul(csub(xa[e], pc.q), csub(xb[e], pc.q), pc.q, pc.qinv);
+    }
+  });
+  inv_from<W, LOGN, L4, 0>(xa, sa, twi, pc, t, sync);
+  if (act) {
+    sfor<0, S::R>([&](auto ec) {
+      constexpr int e = decltype(ec)::value;
+      c[elem_index<W, LOGN, TOP>(e, t)] = csub(xa[e], pc.q);
+    });
+  }
+}
+
+struct WarpSync {
+  __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Homogeneous batch: `units` = batch * k units, unit u uses prime u % k and
+// the operand rows a + u*n, b + u*n, c + u*n.  Persistent: the grid is sized
+// to the resident capacity and strides over units.
+template <typename W, int LOGN, bool L4, int WARPS>
+__global__ void __launch_bounds__(Shape<W, LOGN>::T <= 32 ? 32 * WARPS : Shape<W, LOGN>::T)
+    k_ntt_batch(NttBatchArgs<W> args) {
+  using S = Shape<W, LOGN>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* smem = reinterpret_cast<W*>(smem_raw);
+  const TwPair<W>* twf = reinterpret_cast<const TwPair<W>*>(args.tw_fwd);
+  const TwPair<W>* twi = reinterpret_cast<const TwPair<W>*>(args.tw_inv);
+  const uint64_t units = args.units;
+  const uint32_t k = args.k;
+  if constexpr (S::T <= 32) {
+    constexpr int TPW = 32 / S::T;  // teams per warp
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t team = lane / S::T, t = lane % S::T;
+    W* sa = smem + (size_t)(warp * TPW + team) * S::SMEM_WORDS;
+    W* sb = S::DUAL ? sa + S::SLICE : sa;
+    const uint64_t gw = (uint64_t)blockIdx.x * WARPS + warp;
+    const uint64_t stride = (uint64_t)gridDim.x * WARPS * TPW;
+    for (uint64_t base = gw * TPW; base < units; base += stride) {
+      const uint64_t u = base + team;
+      const bool act = u < units;
+      const uint32_t j = act ? (uint32_t)(u % k) : 0u;
+      const size_t off = act ? (size_t)u * S::N : 0;
+      const PrimeConst<W> pc = args.pc[j];
+      polymul_unit<W, LOGN, L4>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
+                                twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{});
+    }
+  } else {
+    W* sa = smem;
+    W* sb = S::DUAL ? smem + S::SLICE : smem;
+    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+      const uint32_t j = (uint32_t)(u % k);
+      const size_t off = (size_t)u * S::N;
+      const PrimeConst<W> pc = args.pc[j];
+      polymul_unit<W, LOGN, L4>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
+                                twi + (size_t)j * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{});
+    }
+  }
+}
+
+}  // namespace pm

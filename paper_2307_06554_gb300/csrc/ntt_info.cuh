@@ -1,0 +1,27 @@
+// Launch description of one k_ntt_batch instantiation.
+#pragma once
+#include "kernels.h"
+#include "ntt.cuh"
+
+namespace pm {
+
+constexpr int kNttWarps = 4;  // warps per CTA when a team fits in a warp
+
+template <typename W, int LOGN, bool L4>
+KernelInfo ntt_info() {
+  using S = Shape<W, LOGN>;
+  KernelInfo ki;
+  ki.fn = (const void*)k_ntt_batch<W, LOGN, L4, kNttWarps>;
+  ki.team = S::T;
+  if (S::T <= 32) {
+    ki.block = 32 * kNttWarps;
+    ki.units_per_cta = kNttWarps * (32 / S::T);
+  } else {
+    ki.block = S::T;
+    ki.units_per_cta = 1;
+  }
+  ki.smem = ki.units_per_cta * S::SMEM_WORDS * (int)sizeof(W);
+  return ki;
+}
+
+}  // namespace pm

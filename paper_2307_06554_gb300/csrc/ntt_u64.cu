@@ -1,0 +1,19 @@
+// k_ntt_batch instantiations: 64-bit words (moduli < 2^62), n = 2^4 .. 2^13.
+#include "ntt_info.cuh"
+
+namespace pm {
+bool lookup_ntt_u64(int logn, bool l4, KernelInfo* ki) {
+  if (!l4) return false;  // 64-bit words always run with the [0, 4q) bounds
+  switch (logn) {
+#define PM_CASE(L)                                                                         \
+  case L:                                                                                  \
+    *ki = ntt_info<uint64_t, L, true>();                                                   \
+    return true;
+    PM_CASE(4) PM_CASE(5) PM_CASE(6) PM_CASE(7) PM_CASE(8) PM_CASE(9) PM_CASE(10)
+    PM_CASE(11) PM_CASE(12) PM_CASE(13)
+#undef PM_CASE
+    default:
+      return false;
+  }
+}
+}  // namespace pm

@@ -1,0 +1,36 @@
+// The opaque plan behind polymul_plan* (library-internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "kernels.h"
+
+struct polymul_plan {
+  uint32_t n = 0, logn = 0, k = 0;
+  uint32_t elem = 4;   // bytes per coefficient word (4 or 8)
+  uint32_t path = 0;   // POLYMUL_PATH_NTT or POLYMUL_PATH_TENSOR
+  uint32_t flags = 0;
+  std::vector<uint64_t> q;
+  bool l4 = false;     // every q < 2^(bits-2): Harvey [0, 4q) bounds
+  int device = 0, num_sms = 0;
+  // NTT tables: [k][n] (w, w') pairs, forward and inverse; [k] constants
+  void* d_twf = nullptr;
+  void* d_twi = nullptr;
+  void* d_pc = nullptr;
+  pm::KernelInfo ki;
+  int grid_cap = 0;    // resident CTAs of ki (persistent grid)
+  int* d_flag = nullptr;
+  // polymul_batch_host staging
+  void* d_stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaStream_t streams[2] = {nullptr, nullptr};
+  cudaEvent_t ev_entry = nullptr;
+};
+
+namespace pm {
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+}  // namespace pm

@@ -1,0 +1,32 @@
+// Structures shared by the host code and the kernels of libpolymul.
+#pragma once
+#include <cstdint>
+
+namespace pm {
+
+// Per-prime constants of one NTT plan (device resident, one per prime).
+template <typename W>
+struct alignas(16) PrimeConst {
+  W q;         // the prime
+  W q2;        // 2q
+  W qinv;      // q^-1 mod 2^bits (Montgomery)
+  W scale;     // n^-1 * 2^bits mod q   (undoes the Montgomery factor and 1/n)
+  W scale_p;   // Shoup companion of scale
+  W scale_w;   // psi^-brv(1) * scale mod q (last inverse stage twiddle)
+  W scale_wp;  // Shoup companion of scale_w
+  W pad;
+};
+
+template <typename W>
+struct NttBatchArgs {
+  const W* a;
+  const W* b;
+  W* c;
+  const void* tw_fwd;  // [k][n] TwPair<W>, psi^brv(i)
+  const void* tw_inv;  // [k][n] TwPair<W>, psi^-brv(i)
+  const PrimeConst<W>* pc;  // [k]
+  uint64_t units;      // batch * k
+  uint32_t k;
+};
+
+}  // namespace pm

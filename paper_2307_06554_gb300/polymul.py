@@ -1,0 +1,200 @@
+"""Thin ctypes binding of libpolymul (include/polymul.h).
+
+Argument marshalling only: every computation happens in the CUDA library.
+Functions keep the C names (``polymul_create``, ``polymul_batch``, ...);
+``Plan`` is a small convenience wrapper over them for torch tensors.
+Importing this module loads the library and raises if it has not been
+built (``python -c "import __graft_entry__ as g; g.build()"``); there is no
+fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+from . import build as _build
+
+POLYMUL_OK = 0
+POLYMUL_EINVAL = 1
+POLYMUL_ENOTSUP = 2
+POLYMUL_EDOMAIN = 3
+POLYMUL_ENOMEM = 4
+POLYMUL_ETIMEOUT = 5
+POLYMUL_ECUDA = 6
+
+PATH_AUTO = 0
+PATH_NTT = 1
+PATH_TENSOR = 2
+FLAG_VALIDATE = 1
+
+_ERRNAMES = {1: "EINVAL", 2: "ENOTSUP", 3: "EDOMAIN", 4: "ENOMEM", 5: "ETIMEOUT", 6: "ECUDA"}
+
+
+class PolymulError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("polymul error %s (%d): %s" % (_ERRNAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class polymul_opts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+
+
+class polymul_plan_info(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint32) for name in
+                ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes")]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libpolymul.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    lib.polymul_create.argtypes = [u32, ctypes.POINTER(u64), u32, ctypes.POINTER(polymul_opts), ctypes.POINTER(vp)]
+    lib.polymul_create.restype = i32
+    lib.polymul_batch.argtypes = [vp, vp, vp, vp, u64, vp]
+    lib.polymul_batch.restype = i32
+    lib.polymul_batch_host.argtypes = [vp, vp, vp, vp, u64, vp]
+    lib.polymul_batch_host.restype = i32
+    lib.polymul_plan_info_get.argtypes = [vp, ctypes.POINTER(polymul_plan_info)]
+    lib.polymul_plan_info_get.restype = i32
+    lib.polymul_destroy.argtypes = [vp]
+    lib.polymul_destroy.restype = None
+    lib.polymul_last_error.argtypes = []
+    lib.polymul_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def polymul_last_error() -> str:
+    return _lib.polymul_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != POLYMUL_OK:
+        raise PolymulError(rc, polymul_last_error())
+
+
+def _ptr(x) -> int:
+    """Device/host address of a torch tensor, numpy array or raw integer."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def polymul_create(n: int, q_list: Sequence[int], path: int = PATH_AUTO, flags: int = 0) -> int:
+    arr = (ctypes.c_uint64 * len(q_list))(*[int(q) for q in q_list])
+    opts = polymul_opts(path, flags)
+    out = ctypes.c_void_p()
+    _check(_lib.polymul_create(n, arr, len(q_list), ctypes.byref(opts), ctypes.byref(out)))
+    return out.value
+
+
+def polymul_batch(plan: int, a, b, c, batch: int, stream=None) -> None:
+    _check(_lib.polymul_batch(plan, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
+
+
+def polymul_batch_host(plan: int, a, b, c, batch: int, stream=None) -> None:
+    _check(_lib.polymul_batch_host(plan, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
+
+
+def polymul_plan_info_get(plan: int) -> dict:
+    info = polymul_plan_info()
+    _check(_lib.polymul_plan_info_get(plan, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in polymul_plan_info._fields_}
+
+
+def polymul_destroy(plan: int) -> None:
+    _lib.polymul_destroy(plan)
+
+
+class Plan:
+    """Owning wrapper: ``with Plan(n, qs) as p: p.batch(a, b, c)``."""
+
+    def __init__(self, n: int, q_list: Sequence[int], path: int = PATH_AUTO, flags: int = 0):
+        self.n = int(n)
+        self.q_list = [int(q) for q in q_list]
+        self.handle = polymul_create(self.n, self.q_list, path, flags)
+        self.info = polymul_plan_info_get(self.handle)
+
+    @property
+    def elem_bytes(self) -> int:
+        return self.info["elem_bytes"]
+
+    def batch(self, a, b, c, stream=None) -> None:
+        """a, b, c: device tensors of shape [batch][k][n] (uint32/int32 or
+        uint64/int64 per elem_bytes)."""
+        batch = self._check_shapes(a, b, c)
+        polymul_batch(self.handle, a, b, c, batch, stream if stream is not None else _current_stream(a))
+
+    def batch_host(self, a, b, c) -> None:
+        batch = self._check_shapes(a, b, c)
+        polymul_batch_host(self.handle, a, b, c, batch, None)
+
+    def _check_shapes(self, a, b, c) -> int:
+        shape = tuple(a.shape)
+        if tuple(b.shape) != shape or tuple(c.shape) != shape:
+            raise ValueError("a, b, c must have the same shape")
+        if len(shape) != 3 or shape[1] != len(self.q_list) or shape[2] != self.n:
+            raise ValueError("expected shape [batch][%d][%d], got %s" % (len(self.q_list), self.n, shape))
+        for x in (a, b, c):
+            size = x.element_size() if hasattr(x, "element_size") else x.itemsize
+            if size != self.elem_bytes:
+                raise ValueError("element size must be %d bytes" % self.elem_bytes)
+            contiguous = x.is_contiguous() if hasattr(x, "is_contiguous") else x.flags["C_CONTIGUOUS"]
+            if not contiguous:
+                raise ValueError("operands must be contiguous")
+        return shape[0]
+
+    def close(self):
+        if self.handle:
+            polymul_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _current_stream(x):
+    try:
+        import torch
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            return torch.cuda.current_stream(x.device).cuda_stream
+    except ImportError:  # pragma: no cover
+        pass
+    return 0

@@ -1,0 +1,157 @@
+"""Path (a), the batched negacyclic NTT, against the CPU oracle: bit-exact
+on seeded inputs at sizes spanning several teams/CTAs with ragged tails, at
+the full sizes of the standing workloads, and on the edge cases."""
+import numpy as np
+import pytest
+
+from oracle import native
+from oracle import schoolbook as sb
+from paper_2307_06554_gb300 import workloads as wl
+
+from helpers import assert_equal_residues, run_plan_batch, to_dev, from_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    from paper_2307_06554_gb300 import polymul
+    return polymul
+
+
+def _primes(seed, k, bits, n, exclude=()):
+    rng = np.random.default_rng(seed)
+    return wl.draw_primes(rng, k, bits, bits, max(n.bit_length(), 1), exclude)
+
+
+def _case(seed, batch, q_list, n, dtype=None):
+    rng = np.random.default_rng(seed)
+    return wl.uniform_coeffs(rng, batch, q_list, n, dtype), wl.uniform_coeffs(rng, batch, q_list, n, dtype)
+
+
+@pytest.mark.parametrize("logn", list(range(4, 15)))
+@pytest.mark.parametrize("bits", [30, 31])
+def test_u32_all_degrees(pm, logn, bits):
+    n = 1 << logn
+    k = 3 if n <= 4096 else 2
+    batch = {16: 37, 32: 37, 64: 29, 128: 21, 256: 19, 512: 13, 1024: 11}.get(n, 3)
+    q_list = _primes(100 + logn + bits, k, bits, 2 * n)
+    a, b = _case(logn * 7 + bits, batch, q_list, n, np.uint32)
+    with pm.Plan(n, q_list) as plan:
+        assert plan.info["path"] == pm.PATH_NTT and plan.elem_bytes == 4
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list), "n=%d bits=%d" % (n, bits))
+
+
+@pytest.mark.parametrize("logn", list(range(4, 14)))
+@pytest.mark.parametrize("bits", [59, 62])
+def test_u64_all_degrees(pm, logn, bits):
+    n = 1 << logn
+    k = 2
+    batch = {16: 37, 32: 33, 64: 19, 128: 17, 256: 9, 512: 7, 1024: 5}.get(n, 2)
+    q_list = _primes(200 + logn + bits, k, bits, 2 * n)
+    a, b = _case(logn * 11 + bits, batch, q_list, n, np.uint64)
+    with pm.Plan(n, q_list) as plan:
+        assert plan.info["path"] == pm.PATH_NTT and plan.elem_bytes == 8
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list), "n=%d bits=%d" % (n, bits))
+
+
+def test_ring_1024_full_size(pm):
+    """n=1024, q=12289, 4096 pairs: every output coefficient."""
+    w = wl.ring_1024()
+    with pm.Plan(w.n, w.q_list) as plan:
+        got = run_plan_batch(plan, w.a, w.b)
+    assert_equal_residues(got, native.polymul_batch(w.a, w.b, w.q_list), w.name)
+
+
+def test_rns_4096_full_size(pm):
+    """n=4096, 8 primes of 30 bits, 256 pairs, ternary b: every output."""
+    w = wl.rns_4096()
+    with pm.Plan(w.n, w.q_list) as plan:
+        got = run_plan_batch(plan, w.a, w.b)
+    assert_equal_residues(got, native.polymul_batch(w.a, w.b, w.q_list), w.name)
+
+
+@pytest.mark.parametrize("n,q", [(1024, 12289), (4096, 786433), (2048, 2013265921)])
+def test_edge_values(pm, n, q):
+    assert (q - 1) % (2 * n) == 0 and wl.is_prime(q)
+    zeros = np.zeros((1, 1, n), np.uint32)
+    top = np.full((1, 1, n), q - 1, np.uint32)
+    mono = np.zeros((1, 1, n), np.uint32)
+    mono[0, 0, n - 1] = 1
+    one = np.zeros((1, 1, n), np.uint32)
+    one[0, 0, 0] = 1
+    rng = np.random.default_rng(3)
+    r = rng.integers(0, q, size=(1, 1, n), dtype=np.uint64).astype(np.uint32)
+    a = np.concatenate([zeros, top, mono, one, r, top])
+    b = np.concatenate([r, top, mono, r, zeros, r])
+    with pm.Plan(n, [q]) as plan:
+        got = run_plan_batch(plan, a, b).astype(np.uint64)
+    want = native.polymul_batch(a, b, [q])
+    assert_equal_residues(got, want, "edges")
+    assert not got[0].any() and not got[4].any()
+    # x^(n-1) * x^(n-1) = -x^(n-2)
+    exp = np.zeros(n, np.uint64)
+    exp[n - 2] = q - 1
+    assert np.array_equal(got[2, 0], exp)
+    assert np.array_equal(got[3, 0], r[0, 0].astype(np.uint64))
+    # all (q-1) squared: coefficient j is 2j + 2 - n mod q
+    assert np.array_equal(got[1, 0], np.array([(2 * j + 2 - n) % q for j in range(n)], np.uint64))
+
+
+def test_batch_zero_and_one(pm):
+    import torch
+    n, q = 1024, 12289
+    a, b = _case(5, 1, [q], n, np.uint32)
+    with pm.Plan(n, [q]) as plan:
+        ta, tb = to_dev(a), to_dev(b)
+        tc = torch.full_like(ta, 7)
+        pm.polymul_batch(plan.handle, ta, tb, tc, 0)  # no-op
+        torch.cuda.synchronize()
+        assert (tc == 7).all()
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, [q]), "batch 1")
+
+
+def test_validate_flag_rejects_out_of_range(pm):
+    n, q = 256, 7681
+    a, b = _case(6, 4, [q], n, np.uint32)
+    a[2, 0, 17] = q  # not canonical
+    with pm.Plan(n, [q], flags=pm.FLAG_VALIDATE) as plan:
+        with pytest.raises(pm.PolymulError) as ei:
+            run_plan_batch(plan, a, b)
+        assert ei.value.code == pm.POLYMUL_EDOMAIN
+        a[2, 0, 17] = q - 1
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, [q]), "validated")
+
+
+def test_host_buffer_entry_matches_device_entry(pm):
+    w = wl.ring_1024(batch=3000, seed=12)
+    with pm.Plan(w.n, w.q_list) as plan:
+        dev = run_plan_batch(plan, w.a, w.b)
+        c = np.zeros_like(w.a)
+        plan.batch_host(w.a, w.b, c)
+    assert np.array_equal(c, dev)
+    # spot-check against the oracle
+    idx = [0, 1499, 2999]
+    want = native.polymul_batch(w.a[idx], w.b[idx], w.q_list)
+    assert_equal_residues(c[idx], want, "host entry")
+
+
+def test_other_stream_and_reuse(pm):
+    import torch
+    n = 2048
+    q_list = _primes(77, 2, 30, 2 * n)
+    a, b = _case(8, 9, q_list, n, np.uint32)
+    with pm.Plan(n, q_list) as plan:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            ta, tb = to_dev(a), to_dev(b)
+            tc = torch.empty_like(ta)
+            for _ in range(3):
+                plan.batch(ta, tb, tc, stream=s)
+        s.synchronize()
+        got = from_dev(tc, np.uint32)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list), "stream")
