@@ -105,9 +105,28 @@ int upload_ntt_tables(polymul_plan* p) {
   return POLYMUL_OK;
 }
 
-bool lookup_ntt(uint32_t elem, int logn, bool l4, KernelInfo* ki) {
-  if (elem == 4) return lookup_ntt_u32_small(logn, l4, ki) || lookup_ntt_u32_large(logn, l4, ki);
-  return lookup_ntt_u64(logn, l4, ki);
+bool lookup_ntt(uint32_t elem, int logn, int mode, KernelInfo* ki) {
+  if (elem == 4) {
+    if (mode == 0) return lookup_ntt_u32_m0(logn, ki);
+    if (mode == 1) return lookup_ntt_u32_m1(logn, ki);
+    return lookup_ntt_u32_m2(logn, ki);
+  }
+  if (mode == 1) return lookup_ntt_u64_m1(logn, ki);
+  if (mode == 2) return lookup_ntt_u64_m2(logn, ki);
+  return false;
+}
+
+// Reduction mode for the largest modulus (see the mode notes in ntt.cuh):
+// 2 = no conditional subtractions, 1 = Harvey [0, 4q), 0 = [0, 2q).
+int ntt_mode(uint64_t qmax, uint32_t logn, uint32_t elem) {
+  using pm::host::u128;
+  const int bits = 8 * (int)elem;
+  const u128 lim = (u128)1 << bits;
+  const u128 g = 1 + 2 * (u128)logn;
+  if (((u128)qmax << (logn + 1)) < lim && g * g * qmax < lim) return 2;
+  if ((u128)qmax * 4 < lim) return 1;
+  if ((u128)qmax * 2 < lim) return 0;
+  return -1;
 }
 
 int configure_launch(polymul_plan* p) {
@@ -155,8 +174,9 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     if (!pm::host::is_prime(q) || (q - 1) % (2ull * n) != 0) ntt_ok = false;
     if (p->elem == 4 && q >= (1ull << 31)) ntt_ok = false;
   }
-  p->l4 = p->elem == 4 ? qmax < (1ull << 30) : true;
-  if (ntt_ok && !lookup_ntt(p->elem, (int)p->logn, p->l4, &p->ki)) ntt_ok = false;
+  p->mode = ntt_mode(qmax, p->logn, p->elem);
+  if (p->mode < 0) ntt_ok = false;
+  if (ntt_ok && !lookup_ntt(p->elem, (int)p->logn, p->mode, &p->ki)) ntt_ok = false;
 
   int rc = POLYMUL_OK;
   if (path == POLYMUL_PATH_TENSOR) {
@@ -167,6 +187,12 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     p->path = POLYMUL_PATH_NTT;
     rc = p->elem == 4 ? upload_ntt_tables<uint32_t>(p) : upload_ntt_tables<uint64_t>(p);
     if (rc == POLYMUL_OK) rc = configure_launch(p);
+    if (rc == POLYMUL_OK) {
+      // work counters for the three launch slots (device entry, two host-entry streams)
+      if (cudaMalloc(&p->d_ctr, 6 * sizeof(unsigned long long)) != cudaSuccess ||
+          cudaMemset(p->d_ctr, 0, 6 * sizeof(unsigned long long)) != cudaSuccess)
+        rc = fail(POLYMUL_ENOMEM, "counter allocation failed");
+    }
   }
   if (rc != POLYMUL_OK) {
     std::string keep = g_err;
@@ -184,6 +210,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_twi);
   cudaFree(p->d_pc);
   cudaFree(p->d_flag);
+  cudaFree(p->d_ctr);
   for (int s = 0; s < 2; ++s) {
     cudaFree(p->d_stage[s]);
     if (p->streams[s]) cudaStreamDestroy(p->streams[s]);
@@ -221,8 +248,9 @@ __global__ void k_validate(const W* __restrict__ a, const W* __restrict__ b, uin
   }
 }
 
-int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st) {
+int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st, int slot) {
   const uint64_t units = batch * p->k;
+  unsigned long long* ctr = p->d_ctr + 2 * slot;
   if (p->flags & POLYMUL_FLAG_VALIDATE) {
     if (!p->d_flag) PM_CUDA(cudaMalloc(&p->d_flag, sizeof(int)));
     PM_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), st));
@@ -243,12 +271,12 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
   const int grid = (int)std::min<uint64_t>(need, (uint64_t)p->grid_cap);
   if (p->elem == 4) {
     NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
-                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k};
+                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
   } else {
     NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
-                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k};
+                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
   }
@@ -266,7 +294,7 @@ extern "C" int polymul_batch(polymul_plan* p, const void* a, const void* b, void
   if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
   if (misaligned(a) || misaligned(b) || misaligned(c)) return fail(POLYMUL_EINVAL, "operands must be 16-byte aligned");
   if (batch > (1ull << 40)) return fail(POLYMUL_EINVAL, "batch too large");
-  return launch_batch(p, a, b, c, batch, (cudaStream_t)stream);
+  return launch_batch(p, a, b, c, batch, (cudaStream_t)stream, 0);
 }
 
 // Host buffers: chunks of products flow through two plan-owned device
@@ -308,7 +336,7 @@ extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b,
     const size_t off = first * prod_bytes, bytes = cnt * prod_bytes;
     PM_CUDA(cudaMemcpyAsync(da, ha + off, bytes, cudaMemcpyHostToDevice, st));
     PM_CUDA(cudaMemcpyAsync(db, hb + off, bytes, cudaMemcpyHostToDevice, st));
-    rc = launch_batch(p, da, db, dc, cnt, st);
+    rc = launch_batch(p, da, db, dc, cnt, st, 1 + s);
     if (rc != POLYMUL_OK) break;
     PM_CUDA(cudaMemcpyAsync(hc + off, dc, bytes, cudaMemcpyDeviceToHost, st));
   }

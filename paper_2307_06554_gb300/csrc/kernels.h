@@ -13,9 +13,12 @@ struct KernelInfo {
   int units_per_cta = 0;     // units a CTA processes per iteration
 };
 
-// batched negacyclic NTT, k_ntt_batch<W, LOGN, L4>
-bool lookup_ntt_u32_small(int logn, bool l4, KernelInfo* ki);  // logn 4..10
-bool lookup_ntt_u32_large(int logn, bool l4, KernelInfo* ki);  // logn 11..14
-bool lookup_ntt_u64(int logn, bool l4, KernelInfo* ki);        // logn 4..13
+// batched negacyclic NTT, k_ntt_batch<W, LOGN, MODE> (MODE: 0 = kQ31,
+// 1 = kL4, 2 = kSmall; see ntt.cuh)
+bool lookup_ntt_u32_m0(int logn, KernelInfo* ki);  // logn 4..14
+bool lookup_ntt_u32_m1(int logn, KernelInfo* ki);
+bool lookup_ntt_u32_m2(int logn, KernelInfo* ki);
+bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
+bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
 
 }  // namespace pm

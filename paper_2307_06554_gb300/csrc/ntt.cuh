@@ -97,14 +97,29 @@ template <int RB>
 __device__ __forceinline__ uint32_t spos(uint32_t j) { return j + (j >> RB); }
 
 // ---------------------------------------------------------------- butterflies
-template <typename W, bool L4>
+// Reduction modes (chosen per plan from the largest modulus, see
+// ntt_mode()):
+//   kQ31   q < 2^(bits-1): every value kept in [0, 2q);
+//   kL4    q < 2^(bits-2): Harvey's bounds, [0, 4q) forward, [0, 2q) inverse;
+//   kSmall q < 2^(bits-1-log2 n) and (1+2 log2 n)^2 q < 2^bits: no
+//          conditional subtraction anywhere.  Forward values grow by at most
+//          2q per stage ((1+2s)q after s stages); inverse values at most
+//          double per stage (2^(s+1) q after s stages), the subtraction
+//          offset of stage s being that bound.
+enum { kQ31 = 0, kL4 = 1, kSmall = 2 };
+
+template <typename W, int MODE>
 __device__ __forceinline__ void ct_bfly(W& x, W& y, const TwPair<W>& w, const PrimeConst<W>& pc) {
-  if constexpr (L4) {  // q < 2^(bits-2): values in [0, 4q)
+  if constexpr (MODE == kSmall) {
+    W t = shoup(y, w.w, w.wp, pc.q);
+    y = x - t + pc.q2;
+    x = x + t;
+  } else if constexpr (MODE == kL4) {
     W xr = csub(x, pc.q2);
     W t = shoup(y, w.w, w.wp, pc.q);
     x = xr + t;
     y = xr - t + pc.q2;
-  } else {             // q < 2^(bits-1): values in [0, 2q)
+  } else {
     W xr = csub(x, pc.q);
     W t = csub(shoup(y, w.w, w.wp, pc.q), pc.q);
     x = xr + t;
@@ -112,9 +127,14 @@ __device__ __forceinline__ void ct_bfly(W& x, W& y, const TwPair<W>& w, const Pr
   }
 }
 
-template <typename W, bool L4>
+// inverse butterfly of stage h (h = number of inverse stages already done)
+template <typename W, int MODE, int H>
 __device__ __forceinline__ void gs_bfly(W& x, W& y, W w, W wp, const PrimeConst<W>& pc) {
-  if constexpr (L4) {  // values in [0, 2q)
+  if constexpr (MODE == kSmall) {
+    W d = x - y + (pc.q << (H + 1));
+    x = x + y;
+    y = shoup(d, w, wp, pc.q);
+  } else if constexpr (MODE == kL4) {
     W s = x + y;
     W d = x - y + pc.q2;
     x = csub(s, pc.q2);
@@ -128,10 +148,13 @@ __device__ __forceinline__ void gs_bfly(W& x, W& y, W w, W wp, const PrimeConst<
 }
 
 // last inverse stage: both outputs also multiplied by n^-1 * 2^bits
-template <typename W, bool L4>
+template <typename W, int MODE, int H>
 __device__ __forceinline__ void gs_last(W& x, W& y, const PrimeConst<W>& pc) {
   W s, d;
-  if constexpr (L4) {
+  if constexpr (MODE == kSmall) {
+    s = x + y;
+    d = x - y + (pc.q << (H + 1));
+  } else if constexpr (MODE == kL4) {
     s = x + y;
     d = x - y + pc.q2;
   } else {
@@ -143,9 +166,23 @@ __device__ __forceinline__ void gs_last(W& x, W& y, const PrimeConst<W>& pc) {
   y = shoup(d, pc.scale_w, pc.scale_wp, pc.q);
 }
 
+// Two consecutive twiddle pairs in one 16-byte load (32-bit words), else
+// one pair per load.  `p` is 16-byte aligned whenever a run has >= 2 pairs.
+template <typename W>
+__device__ __forceinline__ void ldtw2(const TwPair<W>* p, TwPair<W>& w0, TwPair<W>& w1) {
+  if constexpr (sizeof(W) == 4) {
+    uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    w0 = TwPair<W>{v.x, v.y};
+    w1 = TwPair<W>{v.z, v.w};
+  } else {
+    w0 = ldtw(p);
+    w1 = ldtw(p + 1);
+  }
+}
+
 // ---------------------------------------------------------------- phases
 // forward Cooley-Tukey stages of phase P on two operands sharing twiddles
-template <typename W, int LOGN, bool L4, int P>
+template <typename W, int LOGN, int MODE, int P>
 __device__ __forceinline__ void fwd_phase2(W (&xa)[Shape<W, LOGN>::R], W (&xb)[Shape<W, LOGN>::R],
                                            const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
                                            uint32_t t) {
@@ -154,27 +191,38 @@ __device__ __forceinline__ void fwd_phase2(W (&xa)[Shape<W, LOGN>::R], W (&xb)[S
   sfor<PB::HI - 1, PB::LO - 1, -1>([&](auto hc) {
     constexpr int h = decltype(hc)::value;
     constexpr int hb = h - PB::LO;
+    constexpr int NUP = PB::GS >> (hb + 1);  // distinct twiddles per group
     sfor<0, PB::NG>([&](auto glc) {
       constexpr int gl = decltype(glc)::value;
       const uint32_t g = t + (uint32_t)S::T * gl;
       const uint32_t tb = (1u << (LOGN - 1 - h)) + ((g >> PB::LO) << (PB::HI - 1 - h));
-      sfor<0, (PB::GS >> (hb + 1))>([&](auto upc) {
+      auto apply = [&](auto upc, const TwPair<W>& w) {
         constexpr int up = decltype(upc)::value;
-        const TwPair<W> w = ldtw(tw + tb + up);
         sfor<0, (1 << hb)>([&](auto lwc) {
           constexpr int lw = decltype(lwc)::value;
           constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
           constexpr int u1 = u0 + (1 << hb);
-          ct_bfly<W, L4>(xa[u0], xa[u1], w, pc);
-          ct_bfly<W, L4>(xb[u0], xb[u1], w, pc);
+          ct_bfly<W, MODE>(xa[u0], xa[u1], w, pc);
+          ct_bfly<W, MODE>(xb[u0], xb[u1], w, pc);
         });
-      });
+      };
+      if constexpr (NUP == 1) {
+        apply(std::integral_constant<int, 0>{}, ldtw(tw + tb));
+      } else {
+        sfor<0, NUP, 2>([&](auto upc) {
+          constexpr int up = decltype(upc)::value;
+          TwPair<W> w0, w1;
+          ldtw2(tw + tb + up, w0, w1);
+          apply(std::integral_constant<int, up>{}, w0);
+          apply(std::integral_constant<int, up + 1>{}, w1);
+        });
+      }
     });
   });
 }
 
 // inverse Gentleman-Sande stages of phase P
-template <typename W, int LOGN, bool L4, int P>
+template <typename W, int LOGN, int MODE, int P>
 __device__ __forceinline__ void inv_phase(W (&x)[Shape<W, LOGN>::R], const TwPair<W>* __restrict__ tw,
                                           const PrimeConst<W>& pc, uint32_t t) {
   using PB = PhaseBits<W, LOGN, P>;
@@ -182,27 +230,39 @@ __device__ __forceinline__ void inv_phase(W (&x)[Shape<W, LOGN>::R], const TwPai
   sfor<PB::LO, PB::HI>([&](auto hc) {
     constexpr int h = decltype(hc)::value;
     constexpr int hb = h - PB::LO;
+    constexpr int NUP = PB::GS >> (hb + 1);
     sfor<0, PB::NG>([&](auto glc) {
       constexpr int gl = decltype(glc)::value;
       const uint32_t g = t + (uint32_t)S::T * gl;
       const uint32_t tb = (1u << (LOGN - 1 - h)) + ((g >> PB::LO) << (PB::HI - 1 - h));
-      sfor<0, (PB::GS >> (hb + 1))>([&](auto upc) {
+      auto apply = [&](auto upc, const TwPair<W>& w) {
         constexpr int up = decltype(upc)::value;
-        if constexpr (h == LOGN - 1) {
+        sfor<0, (1 << hb)>([&](auto lwc) {
+          constexpr int lw = decltype(lwc)::value;
+          constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
+          gs_bfly<W, MODE, h>(x[u0], x[u0 + (1 << hb)], w.w, w.wp, pc);
+        });
+      };
+      if constexpr (h == LOGN - 1) {
+        sfor<0, NUP>([&](auto upc) {
+          constexpr int up = decltype(upc)::value;
           sfor<0, (1 << hb)>([&](auto lwc) {
             constexpr int lw = decltype(lwc)::value;
             constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
-            gs_last<W, L4>(x[u0], x[u0 + (1 << hb)], pc);
+            gs_last<W, MODE, h>(x[u0], x[u0 + (1 << hb)], pc);
           });
-        } else {
-          const TwPair<W> w = ldtw(tw + tb + up);
-          sfor<0, (1 << hb)>([&](auto lwc) {
-            constexpr int lw = decltype(lwc)::value;
-            constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
-            gs_bfly<W, L4>(x[u0], x[u0 + (1 << hb)], w.w, w.wp, pc);
-          });
-        }
-      });
+        });
+      } else if constexpr (NUP == 1) {
+        apply(std::integral_constant<int, 0>{}, ldtw(tw + tb));
+      } else {
+        sfor<0, NUP, 2>([&](auto upc) {
+          constexpr int up = decltype(upc)::value;
+          TwPair<W> w0, w1;
+          ldtw2(tw + tb + up, w0, w1);
+          apply(std::integral_constant<int, up>{}, w0);
+          apply(std::integral_constant<int, up + 1>{}, w1);
+        });
+      }
     });
   });
 }
@@ -225,12 +285,12 @@ __device__ __forceinline__ void load_layout(W (&x)[Shape<W, LOGN>::R], const W* 
   });
 }
 
-template <typename W, int LOGN, bool L4, int P, class Sync>
+template <typename W, int LOGN, int MODE, int P, class Sync>
 __device__ __forceinline__ void fwd_from(W (&xa)[Shape<W, LOGN>::R], W (&xb)[Shape<W, LOGN>::R], W* sa,
                                          W* sb, const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
                                          uint32_t t, Sync sync) {
   using S = Shape<W, LOGN>;
-  fwd_phase2<W, LOGN, L4, P>(xa, xb, tw, pc, t);
+  fwd_phase2<W, LOGN, MODE, P>(xa, xb, tw, pc, t);
   if constexpr (P > 0) {
     if constexpr (S::DUAL) {
       sync();
@@ -249,28 +309,28 @@ __device__ __forceinline__ void fwd_from(W (&xa)[Shape<W, LOGN>::R], W (&xb)[Sha
       sync();
       load_layout<W, LOGN, P - 1>(xb, sa, t);
     }
-    fwd_from<W, LOGN, L4, P - 1>(xa, xb, sa, sb, tw, pc, t, sync);
+    fwd_from<W, LOGN, MODE, P - 1>(xa, xb, sa, sb, tw, pc, t, sync);
   }
 }
 
-template <typename W, int LOGN, bool L4, int P, class Sync>
+template <typename W, int LOGN, int MODE, int P, class Sync>
 __device__ __forceinline__ void inv_from(W (&x)[Shape<W, LOGN>::R], W* s, const TwPair<W>* __restrict__ tw,
                                          const PrimeConst<W>& pc, uint32_t t, Sync sync) {
   using S = Shape<W, LOGN>;
-  inv_phase<W, LOGN, L4, P>(x, tw, pc, t);
+  inv_phase<W, LOGN, MODE, P>(x, tw, pc, t);
   if constexpr (P + 1 < S::NPH) {
     sync();
     store_layout<W, LOGN, P>(x, s, t);
     sync();
     load_layout<W, LOGN, P + 1>(x, s, t);
-    inv_from<W, LOGN, L4, P + 1>(x, s, tw, pc, t, sync);
+    inv_from<W, LOGN, MODE, P + 1>(x, s, tw, pc, t, sync);
   }
 }
 
 // One unit: c = a*b mod (x^n+1, q) for one prime.  Every thread of the team
 // calls it (inactive threads with act = false compute on zeros and store
 // nothing, so that team barriers stay uniform).
-template <typename W, int LOGN, bool L4, class Sync>
+template <typename W, int LOGN, int MODE, class Sync>
 __device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* __restrict__ b, W* __restrict__ c,
                                              const TwPair<W>* __restrict__ twf,
                                              const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
@@ -284,17 +344,19 @@ __device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* _
     xa[e] = act ? a[j] : W(0);
     xb[e] = act ? b[j] : W(0);
   });
-  fwd_from<W, LOGN, L4, TOP>(xa, xb, sa, sb, twf, pc, t, sync);
+  fwd_from<W, LOGN, MODE, TOP>(xa, xb, sa, sb, twf, pc, t, sync);
   // pointwise product in the bit-reversed domain (same layout for both)
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
-    if constexpr (L4) {
+    if constexpr (MODE == kSmall) {
+      xa[e] = montmul(xa[e], xb[e], pc.q, pc.qinv);
+    } else if constexpr (MODE == kL4) {
       xa[e] = csub(montmul(xa[e], xb[e], pc.q, pc.qinv), pc.q2);
     } else {
       xa[e] = montmul(csub(xa[e], pc.q), csub(xb[e], pc.q), pc.q, pc.qinv);
     }
   });
-  inv_from<W, LOGN, L4, 0>(xa, sa, twi, pc, t, sync);
+  inv_from<W, LOGN, MODE, 0>(xa, sa, twi, pc, t, sync);
   if (act) {
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;
@@ -311,9 +373,12 @@ struct BlockSync {
 };
 
 // Homogeneous batch: `units` = batch * k units, unit u uses prime u % k and
-// the operand rows a + u*n, b + u*n, c + u*n.  Persistent: the grid is sized
-// to the resident capacity and strides over units.
-template <typename W, int LOGN, bool L4, int WARPS>
+// the operand rows a + u*n, b + u*n, c + u*n.  Persistent grid (sized to the
+// resident capacity); teams take units from a device counter, so the work
+// balances across SMs whatever the unit count.  The counter pair
+// ctr = {next, finished} is zero between launches: the last team to finish
+// resets it.  Launches that share a counter must therefore not overlap.
+template <typename W, int LOGN, int MODE, int WARPS>
 __global__ void __launch_bounds__(Shape<W, LOGN>::T <= 32 ? 32 * WARPS : Shape<W, LOGN>::T)
     k_ntt_batch(NttBatchArgs<W> args) {
   using S = Shape<W, LOGN>;
@@ -323,32 +388,56 @@ __global__ void __launch_bounds__(Shape<W, LOGN>::T <= 32 ? 32 * WARPS : Shape<W
   const TwPair<W>* twi = reinterpret_cast<const TwPair<W>*>(args.tw_inv);
   const uint64_t units = args.units;
   const uint32_t k = args.k;
+  unsigned long long* ctr = args.ctr;
   if constexpr (S::T <= 32) {
     constexpr int TPW = 32 / S::T;  // teams per warp
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t team = lane / S::T, t = lane % S::T;
     W* sa = smem + (size_t)(warp * TPW + team) * S::SMEM_WORDS;
     W* sb = S::DUAL ? sa + S::SLICE : sa;
-    const uint64_t gw = (uint64_t)blockIdx.x * WARPS + warp;
-    const uint64_t stride = (uint64_t)gridDim.x * WARPS * TPW;
-    for (uint64_t base = gw * TPW; base < units; base += stride) {
+    for (;;) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(ctr, (unsigned long long)TPW);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= units) break;
       const uint64_t u = base + team;
       const bool act = u < units;
       const uint32_t j = act ? (uint32_t)(u % k) : 0u;
       const size_t off = act ? (size_t)u * S::N : 0;
       const PrimeConst<W> pc = args.pc[j];
-      polymul_unit<W, LOGN, L4>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
-                                twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{});
+      polymul_unit<W, LOGN, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
+                                  twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{});
+    }
+    if (lane == 0) {
+      __threadfence();
+      const unsigned long long teams = (unsigned long long)gridDim.x * WARPS;
+      if (atomicAdd(ctr + 1, 1ull) == teams - 1) {
+        atomicExch(ctr, 0ull);
+        atomicExch(ctr + 1, 0ull);
+      }
     }
   } else {
+    __shared__ unsigned long long s_base;
     W* sa = smem;
     W* sb = S::DUAL ? smem + S::SLICE : smem;
-    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    for (;;) {
+      if (threadIdx.x == 0) s_base = atomicAdd(ctr, 1ull);
+      __syncthreads();
+      const unsigned long long u = s_base;
+      __syncthreads();
+      if (u >= units) break;
       const uint32_t j = (uint32_t)(u % k);
       const size_t off = (size_t)u * S::N;
       const PrimeConst<W> pc = args.pc[j];
-      polymul_unit<W, LOGN, L4>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
-                                twi + (size_t)j * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{});
+      polymul_unit<W, LOGN, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
+                                  twi + (size_t)j * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{});
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(ctr + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+        atomicExch(ctr, 0ull);
+        atomicExch(ctr + 1, 0ull);
+      }
     }
   }
 }

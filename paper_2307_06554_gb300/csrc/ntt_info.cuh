@@ -7,11 +7,11 @@ namespace pm {
 
 constexpr int kNttWarps = 4;  // warps per CTA when a team fits in a warp
 
-template <typename W, int LOGN, bool L4>
+template <typename W, int LOGN, int MODE>
 KernelInfo ntt_info() {
   using S = Shape<W, LOGN>;
   KernelInfo ki;
-  ki.fn = (const void*)k_ntt_batch<W, LOGN, L4, kNttWarps>;
+  ki.fn = (const void*)k_ntt_batch<W, LOGN, MODE, kNttWarps>;
   ki.team = S::T;
   if (S::T <= 32) {
     ki.block = 32 * kNttWarps;

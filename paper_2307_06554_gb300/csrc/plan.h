@@ -13,7 +13,7 @@ struct polymul_plan {
   uint32_t path = 0;   // POLYMUL_PATH_NTT or POLYMUL_PATH_TENSOR
   uint32_t flags = 0;
   std::vector<uint64_t> q;
-  bool l4 = false;     // every q < 2^(bits-2): Harvey [0, 4q) bounds
+  int mode = -1;       // NTT reduction mode (0 = [0,2q), 1 = [0,4q), 2 = unreduced)
   int device = 0, num_sms = 0;
   // NTT tables: [k][n] (w, w') pairs, forward and inverse; [k] constants
   void* d_twf = nullptr;
@@ -22,6 +22,7 @@ struct polymul_plan {
   pm::KernelInfo ki;
   int grid_cap = 0;    // resident CTAs of ki (persistent grid)
   int* d_flag = nullptr;
+  unsigned long long* d_ctr = nullptr;  // 3 x {next, finished}: device entry, 2 host streams
   // polymul_batch_host staging
   void* d_stage[2] = {nullptr, nullptr};
   size_t stage_bytes = 0;

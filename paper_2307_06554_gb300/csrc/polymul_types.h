@@ -27,6 +27,7 @@ struct NttBatchArgs {
   const PrimeConst<W>* pc;  // [k]
   uint64_t units;      // batch * k
   uint32_t k;
+  unsigned long long* ctr;  // {next unit, finished teams}, zero between launches
 };
 
 }  // namespace pm

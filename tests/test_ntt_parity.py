@@ -57,6 +57,36 @@ def test_u64_all_degrees(pm, logn, bits):
     assert_equal_residues(got, native.polymul_batch(a, b, q_list), "n=%d bits=%d" % (n, bits))
 
 
+@pytest.mark.parametrize("logn", list(range(4, 15)))
+def test_u32_small_moduli_all_degrees(pm, logn):
+    """Small moduli (PQC sizes) run with no conditional subtractions; the
+    bound tracking must hold at every degree, including all-(q-1) inputs."""
+    n = 1 << logn
+    q_list = [65537] + ([40961] if logn <= 12 else []) + ([12289] if logn <= 11 else []) \
+        + ([8380417] if logn <= 8 else [])
+    batch = 23 if n <= 1024 else 3
+    a, b = _case(300 + logn, batch, q_list, n, np.uint32)
+    for j, q in enumerate(q_list):
+        a[-1, j, :] = q - 1
+        b[-1, j, :] = q - 1
+    with pm.Plan(n, q_list) as plan:
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list), "small q n=%d" % n)
+
+
+@pytest.mark.parametrize("logn", [4, 8, 10, 13])
+def test_u64_small_moduli(pm, logn):
+    n = 1 << logn
+    q_list = _primes(400 + logn, 2, 40, 2 * n)
+    a, b = _case(500 + logn, 5, q_list, n, np.uint64)
+    q_list = [int(q) for q in q_list]
+    a[-1] = np.array(q_list, np.uint64)[:, None] - 1
+    b[-1] = np.array(q_list, np.uint64)[:, None] - 1
+    with pm.Plan(n, q_list) as plan:
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list), "u64 small q n=%d" % n)
+
+
 def test_ring_1024_full_size(pm):
     """n=1024, q=12289, 4096 pairs: every output coefficient."""
     w = wl.ring_1024()
