@@ -59,6 +59,22 @@ __device__ __forceinline__ TwPair<W> ldtw(const TwPair<W>* p) {
   }
 }
 
+// Operand traffic is streamed (read once, written once): keep it out of L1 so
+// that the twiddle tables stay resident there.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ uint64_t ld_stream(const uint64_t* p) {
+  return (uint64_t)__ldcs(reinterpret_cast<const unsigned long long*>(p));
+}
+__device__ __forceinline__ void st_stream(uint32_t* p, uint32_t v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(uint64_t* p, uint64_t v) {
+  __stcs(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+// Bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename W, int LOGN>
 struct Shape {
   static constexpr int RB = sizeof(W) == 4 ? 5 : 4;
@@ -341,8 +357,8 @@ __device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* _
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
     const uint32_t j = elem_index<W, LOGN, TOP>(e, t);
-    xa[e] = act ? a[j] : W(0);
-    xb[e] = act ? b[j] : W(0);
+    xa[e] = act ? ld_stream(a + j) : W(0);
+    xb[e] = act ? ld_stream(b + j) : W(0);
   });
   fwd_from<W, LOGN, MODE, TOP>(xa, xb, sa, sb, twf, pc, t, sync);
   // pointwise product in the bit-reversed domain (same layout for both)
@@ -360,7 +376,7 @@ __device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* _
   if (act) {
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;
-      c[elem_index<W, LOGN, TOP>(e, t)] = csub(xa[e], pc.q);
+      st_stream(c + elem_index<W, LOGN, TOP>(e, t), csub(xa[e], pc.q));
     });
   }
 }
@@ -395,18 +411,29 @@ __global__ void __launch_bounds__(Shape<W, LOGN>::T <= 32 ? 32 * WARPS : Shape<W
     const uint32_t team = lane / S::T, t = lane % S::T;
     W* sa = smem + (size_t)(warp * TPW + team) * S::SMEM_WORDS;
     W* sb = S::DUAL ? sa + S::SLICE : sa;
-    for (;;) {
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(ctr, (unsigned long long)TPW);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (base >= units) break;
-      const uint64_t u = base + team;
+    // one ticket ahead: while a unit computes, its successor's rows are
+    // prefetched into L2
+    auto grab = [&]() {
+      unsigned long long v = 0;
+      if (lane == 0) v = atomicAdd(ctr, (unsigned long long)TPW);
+      return __shfl_sync(0xffffffffu, v, 0);
+    };
+    unsigned long long cur = grab();
+    while (cur < units) {
+      const unsigned long long nxt = grab();
+      if (lane == 0 && nxt < units) {
+        const uint32_t cnt = (uint32_t)(units - nxt < (unsigned long long)TPW ? units - nxt : TPW);
+        prefetch_l2(args.a + (size_t)nxt * S::N, cnt * S::N * (uint32_t)sizeof(W));
+        prefetch_l2(args.b + (size_t)nxt * S::N, cnt * S::N * (uint32_t)sizeof(W));
+      }
+      const uint64_t u = cur + team;
       const bool act = u < units;
       const uint32_t j = act ? (uint32_t)(u % k) : 0u;
       const size_t off = act ? (size_t)u * S::N : 0;
       const PrimeConst<W> pc = args.pc[j];
       polymul_unit<W, LOGN, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
                                   twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{});
+      cur = nxt;
     }
     if (lane == 0) {
       __threadfence();
@@ -420,17 +447,26 @@ __global__ void __launch_bounds__(Shape<W, LOGN>::T <= 32 ? 32 * WARPS : Shape<W
     __shared__ unsigned long long s_base;
     W* sa = smem;
     W* sb = S::DUAL ? smem + S::SLICE : smem;
-    for (;;) {
-      if (threadIdx.x == 0) s_base = atomicAdd(ctr, 1ull);
-      __syncthreads();
-      const unsigned long long u = s_base;
-      __syncthreads();
-      if (u >= units) break;
-      const uint32_t j = (uint32_t)(u % k);
-      const size_t off = (size_t)u * S::N;
+    if (threadIdx.x == 0) s_base = atomicAdd(ctr, 1ull);
+    __syncthreads();
+    unsigned long long cur = s_base;
+    while (cur < units) {
+      __syncthreads();  // everyone has read s_base
+      if (threadIdx.x == 0) {
+        const unsigned long long nxt = atomicAdd(ctr, 1ull);
+        s_base = nxt;
+        if (nxt < units) {
+          prefetch_l2(args.a + (size_t)nxt * S::N, S::N * (uint32_t)sizeof(W));
+          prefetch_l2(args.b + (size_t)nxt * S::N, S::N * (uint32_t)sizeof(W));
+        }
+      }
+      const uint32_t j = (uint32_t)(cur % k);
+      const size_t off = (size_t)cur * S::N;
       const PrimeConst<W> pc = args.pc[j];
       polymul_unit<W, LOGN, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
                                   twi + (size_t)j * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{});
+      __syncthreads();  // s_base written before the unit's barriers; read it now
+      cur = s_base;
     }
     if (threadIdx.x == 0) {
       __threadfence();
