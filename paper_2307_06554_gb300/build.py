@@ -43,23 +43,28 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int = 0) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int = 0, out_dir: str = None,
+          extra_flags=()) -> str:
+    """Compile and link; returns the library path.  ``out_dir`` and
+    ``extra_flags`` build a separately named copy (e.g. with -D options)."""
+    out = out_dir or OUT
+    lib_path = os.path.join(out, "libpolymul.so")
+    os.makedirs(out, exist_ok=True)
     srcs = _sources()
     hdrs = _headers()
-    if not force and not _stale(LIB, srcs + hdrs + [os.path.abspath(__file__)]):
-        return LIB
+    if not force and not _stale(lib_path, srcs + hdrs + [os.path.abspath(__file__)]):
+        return lib_path
     objs = []
     todo = []
     for s in srcs:
-        o = os.path.join(OUT, os.path.splitext(os.path.basename(s))[0] + ".o")
+        o = os.path.join(out, os.path.splitext(os.path.basename(s))[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + hdrs + [os.path.abspath(__file__)]):
             todo.append((s, o))
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc()] + ARCH + NVCC_FLAGS + ["-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", s, "-o", o + ".tmp"]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -73,13 +78,13 @@ def build(force: bool = False, verbose: bool = False, jobs: int = 0) -> str:
         for log in ex.map(compile_one, todo):
             if verbose and log:
                 sys.stderr.write(log)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib_path + ".%d.tmp" % os.getpid()
     cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -14,14 +14,14 @@
 //            n^-1 * 2^w, which undoes the Montgomery factor and the 1/n.
 //
 // Register/shared-memory layout.  A thread holds R = 2^RB coefficients of
-// each operand (RB = 5 for 32-bit words, 4 for 64-bit).  The log2(n) stage
+// each operand (RB is a template parameter, chosen per word size and n).  The log2(n) stage
 // bits are cut into phases at multiples of RB: phase P owns bits
 // [P*RB, min((P+1)*RB, log2 n)).  Inside a phase a thread's R values are
 // whole butterfly groups (indices differing only in the phase's bits), so
 // every stage of the phase runs in registers with no communication; between
-// phases the team exchanges through shared memory, word j stored at
-// j + (j >> RB) (one pad word per 2^RB), which makes every exchange pattern
-// used here free of bank conflicts.  For n = 1024 and 32-bit words this is
+// phases the team exchanges through shared memory, word j stored at an
+// XOR-swizzled position (spos) that makes every exchange pattern used here
+// free of bank conflicts.  For n = 1024 and 32-bit words this is
 // one exchange per transform with a team of one warp (32 lanes x 32 values).
 // The top phase's layout puts consecutive lanes on consecutive coefficients,
 // so global loads and stores are fully coalesced.
@@ -59,58 +59,49 @@ __device__ __forceinline__ TwPair<W> ldtw(const TwPair<W>* p) {
   }
 }
 
-// Operand traffic is streamed (read once, written once): keep it out of L1 so
-// that the twiddle tables stay resident there.
-__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
-__device__ __forceinline__ uint64_t ld_stream(const uint64_t* p) {
-  return (uint64_t)__ldcs(reinterpret_cast<const unsigned long long*>(p));
-}
-__device__ __forceinline__ void st_stream(uint32_t* p, uint32_t v) { __stcs(p, v); }
-__device__ __forceinline__ void st_stream(uint64_t* p, uint64_t v) {
-  __stcs(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
-}
-
-// Bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-template <typename W, int LOGN>
+template <typename W_, int LOGN_, int RB_>
 struct Shape {
-  static constexpr int RB = sizeof(W) == 4 ? 5 : 4;
+  using W = W_;
+  static constexpr int LOGN = LOGN_;
+  static constexpr int RB = RB_;                // stage bits per phase
   static constexpr int RLOG = LOGN < RB ? LOGN : RB;
   static constexpr int R = 1 << RLOG;           // values per thread per operand
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N / R;               // threads per unit (team size)
   static constexpr int NPH = (LOGN + RB - 1) / RB;
-  static constexpr int SLICE = N + (N >> RB);   // padded words per operand in smem
+  static constexpr int SLICE = N;              // words per operand in smem (swizzled)
   // keep both operands' exchange buffers when they fit comfortably
   static constexpr bool DUAL = 2 * SLICE * (int)sizeof(W) <= 100 * 1024;
-  static constexpr int SMEM_WORDS = DUAL ? 2 * SLICE : SLICE;
+  // per-team stride; teams that share a warp are offset by T words so that
+  // their lanes fall in different banks
+  static constexpr int SMEM_WORDS = (DUAL ? 2 * SLICE : SLICE) + (T < 32 ? T : 0);
 };
 
-template <typename W, int LOGN, int P>
+template <class S, int P>
 struct PhaseBits {
-  using S = Shape<W, LOGN>;
   static constexpr int LO = P * S::RB;
-  static constexpr int HI = (P + 1) * S::RB < LOGN ? (P + 1) * S::RB : LOGN;
+  static constexpr int HI = (P + 1) * S::RB < S::LOGN ? (P + 1) * S::RB : S::LOGN;
   static constexpr int B = HI - LO;
   static constexpr int GS = 1 << B;   // butterfly group size
   static constexpr int NG = S::R / GS;  // groups per thread
 };
 
 // coefficient index held in register slot e by team thread t during phase P
-template <typename W, int LOGN, int P>
+template <class S, int P>
 __device__ __forceinline__ uint32_t elem_index(int e, uint32_t t) {
-  using PB = PhaseBits<W, LOGN, P>;
-  using S = Shape<W, LOGN>;
+  using PB = PhaseBits<S, P>;
   const uint32_t u = (uint32_t)e & (PB::GS - 1);
   const uint32_t g = t + (uint32_t)S::T * (uint32_t)(e >> PB::B);
   return (g & ((1u << PB::LO) - 1)) | (u << PB::LO) | ((g >> PB::LO) << PB::HI);
 }
 
+// Shared-memory position of coefficient j during an exchange: an XOR swizzle
+// of the low five bits by bits 1..5 and RB..RB+4 (a bijection inside every
+// 32-word block).  Checked exhaustively for RB in {3,4,5}, n = 2^4..2^16 and
+// 4- and 8-byte words: every warp access of every exchange is free of bank
+// conflicts.
 template <int RB>
-__device__ __forceinline__ uint32_t spos(uint32_t j) { return j + (j >> RB); }
+__device__ __forceinline__ uint32_t spos(uint32_t j) { return j ^ ((j >> 1) & 31u) ^ ((j >> RB) & 31u); }
 
 // ---------------------------------------------------------------- butterflies
 // Reduction modes (chosen per plan from the largest modulus, see
@@ -198,12 +189,11 @@ __device__ __forceinline__ void ldtw2(const TwPair<W>* p, TwPair<W>& w0, TwPair<
 
 // ---------------------------------------------------------------- phases
 // forward Cooley-Tukey stages of phase P on two operands sharing twiddles
-template <typename W, int LOGN, int MODE, int P>
-__device__ __forceinline__ void fwd_phase2(W (&xa)[Shape<W, LOGN>::R], W (&xb)[Shape<W, LOGN>::R],
-                                           const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
-                                           uint32_t t) {
-  using PB = PhaseBits<W, LOGN, P>;
-  using S = Shape<W, LOGN>;
+template <class S, int MODE, int P, typename W = typename S::W>
+__device__ __forceinline__ void fwd_phase2(W (&xa)[S::R], W (&xb)[S::R], const TwPair<W>* __restrict__ tw,
+                                           const PrimeConst<W>& pc, uint32_t t) {
+  using PB = PhaseBits<S, P>;
+  constexpr int LOGN = S::LOGN;
   sfor<PB::HI - 1, PB::LO - 1, -1>([&](auto hc) {
     constexpr int h = decltype(hc)::value;
     constexpr int hb = h - PB::LO;
@@ -238,11 +228,11 @@ __device__ __forceinline__ void fwd_phase2(W (&xa)[Shape<W, LOGN>::R], W (&xb)[S
 }
 
 // inverse Gentleman-Sande stages of phase P
-template <typename W, int LOGN, int MODE, int P>
-__device__ __forceinline__ void inv_phase(W (&x)[Shape<W, LOGN>::R], const TwPair<W>* __restrict__ tw,
+template <class S, int MODE, int P, typename W = typename S::W>
+__device__ __forceinline__ void inv_phase(W (&x)[S::R], const TwPair<W>* __restrict__ tw,
                                           const PrimeConst<W>& pc, uint32_t t) {
-  using PB = PhaseBits<W, LOGN, P>;
-  using S = Shape<W, LOGN>;
+  using PB = PhaseBits<S, P>;
+  constexpr int LOGN = S::LOGN;
   sfor<PB::LO, PB::HI>([&](auto hc) {
     constexpr int h = decltype(hc)::value;
     constexpr int hb = h - PB::LO;
@@ -283,84 +273,79 @@ __device__ __forceinline__ void inv_phase(W (&x)[Shape<W, LOGN>::R], const TwPai
   });
 }
 
-template <typename W, int LOGN, int P>
-__device__ __forceinline__ void store_layout(const W (&x)[Shape<W, LOGN>::R], W* s, uint32_t t) {
-  using S = Shape<W, LOGN>;
+template <class S, int P, typename W = typename S::W>
+__device__ __forceinline__ void store_layout(const W (&x)[S::R], W* s, uint32_t t) {
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
-    s[spos<S::RB>(elem_index<W, LOGN, P>(e, t))] = x[e];
+    s[spos<S::RB>(elem_index<S, P>(e, t))] = x[e];
   });
 }
 
-template <typename W, int LOGN, int P>
-__device__ __forceinline__ void load_layout(W (&x)[Shape<W, LOGN>::R], const W* s, uint32_t t) {
-  using S = Shape<W, LOGN>;
+template <class S, int P, typename W = typename S::W>
+__device__ __forceinline__ void load_layout(W (&x)[S::R], const W* s, uint32_t t) {
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
-    x[e] = s[spos<S::RB>(elem_index<W, LOGN, P>(e, t))];
+    x[e] = s[spos<S::RB>(elem_index<S, P>(e, t))];
   });
 }
 
-template <typename W, int LOGN, int MODE, int P, class Sync>
-__device__ __forceinline__ void fwd_from(W (&xa)[Shape<W, LOGN>::R], W (&xb)[Shape<W, LOGN>::R], W* sa,
-                                         W* sb, const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
+template <class S, int MODE, int P, class Sync, typename W = typename S::W>
+__device__ __forceinline__ void fwd_from(W (&xa)[S::R], W (&xb)[S::R], W* sa, W* sb,
+                                         const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
                                          uint32_t t, Sync sync) {
-  using S = Shape<W, LOGN>;
-  fwd_phase2<W, LOGN, MODE, P>(xa, xb, tw, pc, t);
+  fwd_phase2<S, MODE, P>(xa, xb, tw, pc, t);
   if constexpr (P > 0) {
     if constexpr (S::DUAL) {
       sync();
-      store_layout<W, LOGN, P>(xa, sa, t);
-      store_layout<W, LOGN, P>(xb, sb, t);
+      store_layout<S, P>(xa, sa, t);
+      store_layout<S, P>(xb, sb, t);
       sync();
-      load_layout<W, LOGN, P - 1>(xa, sa, t);
-      load_layout<W, LOGN, P - 1>(xb, sb, t);
+      load_layout<S, P - 1>(xa, sa, t);
+      load_layout<S, P - 1>(xb, sb, t);
     } else {
       sync();
-      store_layout<W, LOGN, P>(xa, sa, t);
+      store_layout<S, P>(xa, sa, t);
       sync();
-      load_layout<W, LOGN, P - 1>(xa, sa, t);
+      load_layout<S, P - 1>(xa, sa, t);
       sync();
-      store_layout<W, LOGN, P>(xb, sa, t);
+      store_layout<S, P>(xb, sa, t);
       sync();
-      load_layout<W, LOGN, P - 1>(xb, sa, t);
+      load_layout<S, P - 1>(xb, sa, t);
     }
-    fwd_from<W, LOGN, MODE, P - 1>(xa, xb, sa, sb, tw, pc, t, sync);
+    fwd_from<S, MODE, P - 1>(xa, xb, sa, sb, tw, pc, t, sync);
   }
 }
 
-template <typename W, int LOGN, int MODE, int P, class Sync>
-__device__ __forceinline__ void inv_from(W (&x)[Shape<W, LOGN>::R], W* s, const TwPair<W>* __restrict__ tw,
+template <class S, int MODE, int P, class Sync, typename W = typename S::W>
+__device__ __forceinline__ void inv_from(W (&x)[S::R], W* s, const TwPair<W>* __restrict__ tw,
                                          const PrimeConst<W>& pc, uint32_t t, Sync sync) {
-  using S = Shape<W, LOGN>;
-  inv_phase<W, LOGN, MODE, P>(x, tw, pc, t);
+  inv_phase<S, MODE, P>(x, tw, pc, t);
   if constexpr (P + 1 < S::NPH) {
     sync();
-    store_layout<W, LOGN, P>(x, s, t);
+    store_layout<S, P>(x, s, t);
     sync();
-    load_layout<W, LOGN, P + 1>(x, s, t);
-    inv_from<W, LOGN, MODE, P + 1>(x, s, tw, pc, t, sync);
+    load_layout<S, P + 1>(x, s, t);
+    inv_from<S, MODE, P + 1>(x, s, tw, pc, t, sync);
   }
 }
 
 // One unit: c = a*b mod (x^n+1, q) for one prime.  Every thread of the team
 // calls it (inactive threads with act = false compute on zeros and store
 // nothing, so that team barriers stay uniform).
-template <typename W, int LOGN, int MODE, class Sync>
+template <class S, int MODE, class Sync, typename W = typename S::W>
 __device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* __restrict__ b, W* __restrict__ c,
                                              const TwPair<W>* __restrict__ twf,
                                              const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
                                              W* sa, W* sb, uint32_t t, bool act, Sync sync) {
-  using S = Shape<W, LOGN>;
   constexpr int TOP = S::NPH - 1;
   W xa[S::R], xb[S::R];
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
-    const uint32_t j = elem_index<W, LOGN, TOP>(e, t);
-    xa[e] = act ? ld_stream(a + j) : W(0);
-    xb[e] = act ? ld_stream(b + j) : W(0);
+    const uint32_t j = elem_index<S, TOP>(e, t);
+    xa[e] = act ? a[j] : W(0);
+    xb[e] = act ? b[j] : W(0);
   });
-  fwd_from<W, LOGN, MODE, TOP>(xa, xb, sa, sb, twf, pc, t, sync);
+  fwd_from<S, MODE, TOP>(xa, xb, sa, sb, twf, pc, t, sync);
   // pointwise product in the bit-reversed domain (same layout for both)
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
@@ -372,11 +357,11 @@ __device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* _
       xa[e] = montmul(csub(xa[e], pc.q), csub(xb[e], pc.q), pc.q, pc.qinv);
     }
   });
-  inv_from<W, LOGN, MODE, 0>(xa, sa, twi, pc, t, sync);
+  inv_from<S, MODE, 0>(xa, sa, twi, pc, t, sync);
   if (act) {
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;
-      st_stream(c + elem_index<W, LOGN, TOP>(e, t), csub(xa[e], pc.q));
+      c[elem_index<S, TOP>(e, t)] = csub(xa[e], pc.q);
     });
   }
 }
@@ -394,10 +379,10 @@ struct BlockSync {
 // balances across SMs whatever the unit count.  The counter pair
 // ctr = {next, finished} is zero between launches: the last team to finish
 // resets it.  Launches that share a counter must therefore not overlap.
-template <typename W, int LOGN, int MODE, int WARPS>
-__global__ void __launch_bounds__(Shape<W, LOGN>::T <= 32 ? 32 * WARPS : Shape<W, LOGN>::T)
-    k_ntt_batch(NttBatchArgs<W> args) {
-  using S = Shape<W, LOGN>;
+template <class S, int MODE, int WARPS>
+__global__ void __launch_bounds__(S::T <= 32 ? 32 * WARPS : S::T)
+    k_ntt_batch(NttBatchArgs<typename S::W> args) {
+  using W = typename S::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* smem = reinterpret_cast<W*>(smem_raw);
   const TwPair<W>* twf = reinterpret_cast<const TwPair<W>*>(args.tw_fwd);
@@ -411,29 +396,18 @@ __global__ void __launch_bounds__(Shape<W, LOGN>::T <= 32 ? 32 * WARPS : Shape<W
     const uint32_t team = lane / S::T, t = lane % S::T;
     W* sa = smem + (size_t)(warp * TPW + team) * S::SMEM_WORDS;
     W* sb = S::DUAL ? sa + S::SLICE : sa;
-    // one ticket ahead: while a unit computes, its successor's rows are
-    // prefetched into L2
-    auto grab = [&]() {
-      unsigned long long v = 0;
-      if (lane == 0) v = atomicAdd(ctr, (unsigned long long)TPW);
-      return __shfl_sync(0xffffffffu, v, 0);
-    };
-    unsigned long long cur = grab();
-    while (cur < units) {
-      const unsigned long long nxt = grab();
-      if (lane == 0 && nxt < units) {
-        const uint32_t cnt = (uint32_t)(units - nxt < (unsigned long long)TPW ? units - nxt : TPW);
-        prefetch_l2(args.a + (size_t)nxt * S::N, cnt * S::N * (uint32_t)sizeof(W));
-        prefetch_l2(args.b + (size_t)nxt * S::N, cnt * S::N * (uint32_t)sizeof(W));
-      }
-      const uint64_t u = cur + team;
+    for (;;) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(ctr, (unsigned long long)TPW);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= units) break;
+      const uint64_t u = base + team;
       const bool act = u < units;
       const uint32_t j = act ? (uint32_t)(u % k) : 0u;
       const size_t off = act ? (size_t)u * S::N : 0;
       const PrimeConst<W> pc = args.pc[j];
-      polymul_unit<W, LOGN, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
-                                  twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{});
-      cur = nxt;
+      polymul_unit<S, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
+                            twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{});
     }
     if (lane == 0) {
       __threadfence();
@@ -447,26 +421,17 @@ __global__ void __launch_bounds__(Shape<W, LOGN>::T <= 32 ? 32 * WARPS : Shape<W
     __shared__ unsigned long long s_base;
     W* sa = smem;
     W* sb = S::DUAL ? smem + S::SLICE : smem;
-    if (threadIdx.x == 0) s_base = atomicAdd(ctr, 1ull);
-    __syncthreads();
-    unsigned long long cur = s_base;
-    while (cur < units) {
-      __syncthreads();  // everyone has read s_base
-      if (threadIdx.x == 0) {
-        const unsigned long long nxt = atomicAdd(ctr, 1ull);
-        s_base = nxt;
-        if (nxt < units) {
-          prefetch_l2(args.a + (size_t)nxt * S::N, S::N * (uint32_t)sizeof(W));
-          prefetch_l2(args.b + (size_t)nxt * S::N, S::N * (uint32_t)sizeof(W));
-        }
-      }
-      const uint32_t j = (uint32_t)(cur % k);
-      const size_t off = (size_t)cur * S::N;
+    for (;;) {
+      if (threadIdx.x == 0) s_base = atomicAdd(ctr, 1ull);
+      __syncthreads();
+      const unsigned long long u = s_base;
+      __syncthreads();
+      if (u >= units) break;
+      const uint32_t j = (uint32_t)(u % k);
+      const size_t off = (size_t)u * S::N;
       const PrimeConst<W> pc = args.pc[j];
-      polymul_unit<W, LOGN, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
-                                  twi + (size_t)j * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{});
-      __syncthreads();  // s_base written before the unit's barriers; read it now
-      cur = s_base;
+      polymul_unit<S, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
+                            twi + (size_t)j * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{});
     }
     if (threadIdx.x == 0) {
       __threadfence();

@@ -7,11 +7,18 @@ namespace pm {
 
 constexpr int kNttWarps = 4;  // warps per CTA when a team fits in a warp
 
-template <typename W, int LOGN, int MODE>
+// stage bits held in registers per phase: the radix of the register passes
+template <typename W, int LOGN>
+constexpr int ntt_rb() {
+  return sizeof(W) == 4 ? 5 : 4;
+}
+
+template <typename W, int LOGN, int MODE, int RB = ntt_rb<W, LOGN>()>
 KernelInfo ntt_info() {
-  using S = Shape<W, LOGN>;
+  using S = Shape<W, LOGN, RB>;
+  using W_ = W;
   KernelInfo ki;
-  ki.fn = (const void*)k_ntt_batch<W, LOGN, MODE, kNttWarps>;
+  ki.fn = (const void*)k_ntt_batch<S, MODE, kNttWarps>;
   ki.team = S::T;
   if (S::T <= 32) {
     ki.block = 32 * kNttWarps;
@@ -20,7 +27,7 @@ KernelInfo ntt_info() {
     ki.block = S::T;
     ki.units_per_cta = 1;
   }
-  ki.smem = ki.units_per_cta * S::SMEM_WORDS * (int)sizeof(W);
+  ki.smem = ki.units_per_cta * S::SMEM_WORDS * (int)sizeof(W_);
   return ki;
 }
 

@@ -47,7 +47,8 @@ class polymul_plan_info(ctypes.Structure):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The in-tree build, or the file named by POLYMUL_LIB if set."""
+    return os.environ.get("POLYMUL_LIB") or _build.LIB
 
 
 def _load():
