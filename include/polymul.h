@@ -120,6 +120,16 @@ int polymul_batch(polymul_plan *plan, const void *a, const void *b, void *c,
 int polymul_batch_host(polymul_plan *plan, const void *a, const void *b, void *c,
                        uint64_t batch, void *stream);
 
+/*
+ * polymul_plan_status -- synchronise `stream`, then report whether a kernel
+ * of this plan abandoned a bounded device wait (an asynchronous copy that
+ * never completed) since the previous call.  Returns POLYMUL_ETIMEOUT in
+ * that case (the outputs of the affected launches are invalid) and resets
+ * the plan's device-side state so that it can be used again; POLYMUL_OK
+ * otherwise.  Kernels never spin without a bound.
+ */
+int polymul_plan_status(polymul_plan *plan, void *stream);
+
 /* Fill *info with the plan's shape and launch configuration. */
 int polymul_plan_info_get(const polymul_plan *plan, polymul_plan_info *info);
 

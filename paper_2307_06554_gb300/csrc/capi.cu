@@ -190,7 +190,8 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     if (rc == POLYMUL_OK) {
       // work counters for the three launch slots (device entry, two host-entry streams)
       if (cudaMalloc(&p->d_ctr, 6 * sizeof(unsigned long long)) != cudaSuccess ||
-          cudaMemset(p->d_ctr, 0, 6 * sizeof(unsigned long long)) != cudaSuccess)
+          cudaMemset(p->d_ctr, 0, 6 * sizeof(unsigned long long)) != cudaSuccess ||
+          cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess || cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess)
         rc = fail(POLYMUL_ENOMEM, "counter allocation failed");
     }
   }
@@ -211,6 +212,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_pc);
   cudaFree(p->d_flag);
   cudaFree(p->d_ctr);
+  cudaFree(p->d_err);
   for (int s = 0; s < 2; ++s) {
     cudaFree(p->d_stage[s]);
     if (p->streams[s]) cudaStreamDestroy(p->streams[s]);
@@ -271,12 +273,12 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
   const int grid = (int)std::min<uint64_t>(need, (uint64_t)p->grid_cap);
   if (p->elem == 4) {
     NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
-                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr};
+                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
   } else {
     NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
-                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr};
+                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
   }
@@ -295,6 +297,22 @@ extern "C" int polymul_batch(polymul_plan* p, const void* a, const void* b, void
   if (misaligned(a) || misaligned(b) || misaligned(c)) return fail(POLYMUL_EINVAL, "operands must be 16-byte aligned");
   if (batch > (1ull << 40)) return fail(POLYMUL_EINVAL, "batch too large");
   return launch_batch(p, a, b, c, batch, (cudaStream_t)stream, 0);
+}
+
+// Waits for `stream`, then reports whether any kernel of the plan gave up on
+// a bounded device wait since the last call; if so the plan's device state
+// (work counters, error word) is reset so that the plan can be used again.
+extern "C" int polymul_plan_status(polymul_plan* p, void* stream) {
+  clear_error();
+  if (!p) return fail(POLYMUL_EINVAL, "plan is NULL");
+  PM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (!p->d_err) return POLYMUL_OK;
+  int h = 0;
+  PM_CUDA(cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return POLYMUL_OK;
+  PM_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+  PM_CUDA(cudaMemset(p->d_ctr, 0, 6 * sizeof(unsigned long long)));
+  return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }
 
 // Host buffers: chunks of products flow through two plan-owned device

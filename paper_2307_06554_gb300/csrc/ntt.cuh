@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <type_traits>
 #include "arith.cuh"
+#include "async.cuh"
 #include "polymul_types.h"
 
 namespace pm {
@@ -69,12 +70,15 @@ struct Shape {
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N / R;               // threads per unit (team size)
   static constexpr int NPH = (LOGN + RB - 1) / RB;
-  static constexpr int SLICE = N;              // words per operand in smem (swizzled)
-  // keep both operands' exchange buffers when they fit comfortably
-  static constexpr bool DUAL = 2 * SLICE * (int)sizeof(W) <= 100 * 1024;
-  // per-team stride; teams that share a warp are offset by T words so that
-  // their lanes fall in different banks
-  static constexpr int SMEM_WORDS = (DUAL ? 2 * SLICE : SLICE) + (T < 32 ? T : 0);
+  static constexpr int SLICE = N;              // words per operand buffer
+  // two buffers per team (a and b): they receive the staged operands, then
+  // serve the exchanges.  Teams that share a warp are offset by T words
+  // (rounded up to 16 bytes, the bulk-copy alignment) so that their lanes
+  // fall in different banks.
+  static constexpr int ALIGN_WORDS = 16 / (int)sizeof(W);
+  static constexpr int TEAM_PAD = T < 32 ? (T + ALIGN_WORDS - 1) / ALIGN_WORDS * ALIGN_WORDS : 0;
+  static constexpr int SMEM_WORDS = 2 * SLICE + TEAM_PAD;
+  static_assert((SMEM_WORDS * sizeof(W)) % 16 == 0, "team buffers must stay 16-byte aligned");
 };
 
 template <class S, int P>
@@ -295,56 +299,56 @@ __device__ __forceinline__ void fwd_from(W (&xa)[S::R], W (&xb)[S::R], W* sa, W*
                                          uint32_t t, Sync sync) {
   fwd_phase2<S, MODE, P>(xa, xb, tw, pc, t);
   if constexpr (P > 0) {
-    if constexpr (S::DUAL) {
-      sync();
-      store_layout<S, P>(xa, sa, t);
-      store_layout<S, P>(xb, sb, t);
-      sync();
-      load_layout<S, P - 1>(xa, sa, t);
-      load_layout<S, P - 1>(xb, sb, t);
-    } else {
-      sync();
-      store_layout<S, P>(xa, sa, t);
-      sync();
-      load_layout<S, P - 1>(xa, sa, t);
-      sync();
-      store_layout<S, P>(xb, sa, t);
-      sync();
-      load_layout<S, P - 1>(xb, sa, t);
-    }
+    sync();
+    store_layout<S, P>(xa, sa, t);
+    store_layout<S, P>(xb, sb, t);
+    sync();
+    load_layout<S, P - 1>(xa, sa, t);
+    load_layout<S, P - 1>(xb, sb, t);
     fwd_from<S, MODE, P - 1>(xa, xb, sa, sb, tw, pc, t, sync);
   }
 }
 
-template <class S, int MODE, int P, class Sync, typename W = typename S::W>
+// `hook` runs once the team has finished reading the exchange buffers for
+// the last time in this unit (after the last exchange), so that the buffers
+// can receive the next unit's operands.
+template <class S, int MODE, int P, class Sync, class Hook, typename W = typename S::W>
 __device__ __forceinline__ void inv_from(W (&x)[S::R], W* s, const TwPair<W>* __restrict__ tw,
-                                         const PrimeConst<W>& pc, uint32_t t, Sync sync) {
+                                         const PrimeConst<W>& pc, uint32_t t, Sync sync, Hook&& hook) {
   inv_phase<S, MODE, P>(x, tw, pc, t);
   if constexpr (P + 1 < S::NPH) {
     sync();
     store_layout<S, P>(x, s, t);
     sync();
     load_layout<S, P + 1>(x, s, t);
-    inv_from<S, MODE, P + 1>(x, s, tw, pc, t, sync);
+    if constexpr (P + 2 == S::NPH) {
+      sync();
+      hook();
+    }
+    inv_from<S, MODE, P + 1>(x, s, tw, pc, t, sync, hook);
   }
 }
 
-// One unit: c = a*b mod (x^n+1, q) for one prime.  Every thread of the team
-// calls it (inactive threads with act = false compute on zeros and store
-// nothing, so that team barriers stay uniform).
-template <class S, int MODE, class Sync, typename W = typename S::W>
-__device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* __restrict__ b, W* __restrict__ c,
-                                             const TwPair<W>* __restrict__ twf,
+// One unit: c = a*b mod (x^n+1, q) for one prime, operands already staged
+// (unswizzled, contiguous) in sa and sb.  Every thread of the team calls it;
+// inactive threads (act = false) compute on stale data and store nothing, so
+// that team barriers stay uniform.  `hook` is called once sa/sb are free.
+template <class S, int MODE, class Sync, class Hook, typename W = typename S::W>
+__device__ __forceinline__ void polymul_unit(W* __restrict__ c, const TwPair<W>* __restrict__ twf,
                                              const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
-                                             W* sa, W* sb, uint32_t t, bool act, Sync sync) {
+                                             W* sa, W* sb, uint32_t t, bool act, Sync sync, Hook&& hook) {
   constexpr int TOP = S::NPH - 1;
   W xa[S::R], xb[S::R];
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
     const uint32_t j = elem_index<S, TOP>(e, t);
-    xa[e] = act ? a[j] : W(0);
-    xb[e] = act ? b[j] : W(0);
+    xa[e] = sa[j];
+    xb[e] = sb[j];
   });
+  if constexpr (S::NPH == 1) {
+    sync();
+    hook();
+  }
   fwd_from<S, MODE, TOP>(xa, xb, sa, sb, twf, pc, t, sync);
   // pointwise product in the bit-reversed domain (same layout for both)
   sfor<0, S::R>([&](auto ec) {
@@ -357,7 +361,7 @@ __device__ __forceinline__ void polymul_unit(const W* __restrict__ a, const W* _
       xa[e] = montmul(csub(xa[e], pc.q), csub(xb[e], pc.q), pc.q, pc.qinv);
     }
   });
-  inv_from<S, MODE, 0>(xa, sa, twi, pc, t, sync);
+  inv_from<S, MODE, 0>(xa, sa, twi, pc, t, sync, hook);
   if (act) {
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;
@@ -374,40 +378,89 @@ struct BlockSync {
 };
 
 // Homogeneous batch: `units` = batch * k units, unit u uses prime u % k and
-// the operand rows a + u*n, b + u*n, c + u*n.  Persistent grid (sized to the
-// resident capacity); teams take units from a device counter, so the work
-// balances across SMs whatever the unit count.  The counter pair
-// ctr = {next, finished} is zero between launches: the last team to finish
-// resets it.  Launches that share a counter must therefore not overlap.
-template <class S, int MODE, int WARPS>
-__global__ void __launch_bounds__(S::T <= 32 ? 32 * WARPS : S::T)
+// the operand rows a + u*n, b + u*n, c + u*n.
+//
+// Persistent grid (sized to the resident capacity).  Teams take units from a
+// device counter, so the work balances across SMs whatever the unit count.
+// Operands arrive by bulk asynchronous copy (one elected thread per warp or
+// CTA issues two row copies per unit into the team's two shared buffers,
+// completion tracked by an mbarrier); the next unit's copy is issued as soon
+// as the current unit has finished its last exchange, so DRAM latency hides
+// behind the last inverse phase.
+//
+// The counter pair ctr = {next, finished} is zero between launches: the last
+// team to finish resets it, so launches that share a counter must not
+// overlap.  A bounded wait that expires sets *err = 1 and the team leaves
+// (the counter is then left dirty; the host resets both).
+template <class S, int WARPS>
+constexpr int ntt_block() {
+  return S::T <= 32 ? 32 * WARPS : S::T;
+}
+
+// REGS: register budget per thread (sets the resident-CTA floor the
+// compiler must honour).
+template <class S, int MODE, int WARPS, int REGS>
+__global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, WARPS>() * REGS))
     k_ntt_batch(NttBatchArgs<typename S::W> args) {
   using W = typename S::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[WARPS];
   W* smem = reinterpret_cast<W*>(smem_raw);
   const TwPair<W>* twf = reinterpret_cast<const TwPair<W>*>(args.tw_fwd);
   const TwPair<W>* twi = reinterpret_cast<const TwPair<W>*>(args.tw_inv);
   const uint64_t units = args.units;
   const uint32_t k = args.k;
   unsigned long long* ctr = args.ctr;
+  constexpr uint32_t ROW = S::N * (uint32_t)sizeof(W);
   if constexpr (S::T <= 32) {
     constexpr int TPW = 32 / S::T;  // teams per warp
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t team = lane / S::T, t = lane % S::T;
-    W* sa = smem + (size_t)(warp * TPW + team) * S::SMEM_WORDS;
-    W* sb = S::DUAL ? sa + S::SLICE : sa;
-    for (;;) {
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(ctr, (unsigned long long)TPW);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (base >= units) break;
-      const uint64_t u = base + team;
+    W* wbase = smem + (size_t)warp * TPW * S::SMEM_WORDS;
+    W* sa = wbase + (size_t)team * S::SMEM_WORDS;
+    W* sb = sa + S::SLICE;
+    uint64_t* bar = &mbar[warp];
+    if (lane == 0) mbar_init(bar, 1);
+    fence_mbar_init();
+    __syncwarp();
+    auto grab = [&]() {
+      unsigned long long v = 0;
+      if (lane == 0) v = atomicAdd(ctr, (unsigned long long)TPW);
+      return __shfl_sync(0xffffffffu, v, 0);
+    };
+    auto issue = [&](unsigned long long base) {  // lane 0 only
+      const uint32_t cnt = (uint32_t)(units - base < (unsigned long long)TPW ? units - base : TPW);
+      fence_proxy_async();
+      mbar_arrive_expect_tx(bar, 2 * cnt * ROW);
+      for (uint32_t m = 0; m < cnt; ++m) {
+        W* da = wbase + (size_t)m * S::SMEM_WORDS;
+        bulk_g2s(da, args.a + (size_t)(base + m) * S::N, ROW, bar);
+        bulk_g2s(da + S::SLICE, args.b + (size_t)(base + m) * S::N, ROW, bar);
+      }
+    };
+    uint32_t parity = 0;
+    unsigned long long cur = grab();
+    if (lane == 0 && cur < units) issue(cur);
+    while (cur < units) {
+      const bool ok = mbar_wait(bar, parity);
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) atomicExch(args.err, 1);
+        mbar_wait(bar, parity);  // let the copy in flight land before leaving
+        return;
+      }
+      parity ^= 1u;
+      const uint64_t u = cur + team;
       const bool act = u < units;
       const uint32_t j = act ? (uint32_t)(u % k) : 0u;
-      const size_t off = act ? (size_t)u * S::N : 0;
       const PrimeConst<W> pc = args.pc[j];
-      polymul_unit<S, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
-                            twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{});
+      unsigned long long nxt = units;
+      auto hook = [&]() {
+        nxt = grab();
+        if (lane == 0 && nxt < units) issue(nxt);
+      };
+      polymul_unit<S, MODE>(args.c + (act ? (size_t)u * S::N : 0), twf + (size_t)j * S::N,
+                            twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{}, hook);
+      cur = nxt;
     }
     if (lane == 0) {
       __threadfence();
@@ -418,20 +471,45 @@ __global__ void __launch_bounds__(S::T <= 32 ? 32 * WARPS : S::T)
       }
     }
   } else {
-    __shared__ unsigned long long s_base;
+    __shared__ unsigned long long s_next;
     W* sa = smem;
-    W* sb = S::DUAL ? smem + S::SLICE : smem;
-    for (;;) {
-      if (threadIdx.x == 0) s_base = atomicAdd(ctr, 1ull);
-      __syncthreads();
-      const unsigned long long u = s_base;
-      __syncthreads();
-      if (u >= units) break;
-      const uint32_t j = (uint32_t)(u % k);
-      const size_t off = (size_t)u * S::N;
+    W* sb = smem + S::SLICE;
+    uint64_t* bar = &mbar[0];
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    fence_mbar_init();
+    auto issue = [&](unsigned long long u) {  // thread 0 only
+      fence_proxy_async();
+      mbar_arrive_expect_tx(bar, 2 * ROW);
+      bulk_g2s(sa, args.a + (size_t)u * S::N, ROW, bar);
+      bulk_g2s(sb, args.b + (size_t)u * S::N, ROW, bar);
+    };
+    if (threadIdx.x == 0) {
+      s_next = atomicAdd(ctr, 1ull);
+      if (s_next < units) issue(s_next);
+    }
+    __syncthreads();
+    unsigned long long cur = s_next;
+    uint32_t parity = 0;
+    while (cur < units) {
+      const bool ok = mbar_wait(bar, parity);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicExch(args.err, 1);
+        mbar_wait(bar, parity);
+        return;
+      }
+      parity ^= 1u;
+      const uint32_t j = (uint32_t)(cur % k);
       const PrimeConst<W> pc = args.pc[j];
-      polymul_unit<S, MODE>(args.a + off, args.b + off, args.c + off, twf + (size_t)j * S::N,
-                            twi + (size_t)j * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{});
+      auto hook = [&]() {  // called after a barrier: every thread is done with sa/sb
+        if (threadIdx.x == 0) {
+          s_next = atomicAdd(ctr, 1ull);
+          if (s_next < units) issue(s_next);
+        }
+      };
+      polymul_unit<S, MODE>(args.c + (size_t)cur * S::N, twf + (size_t)j * S::N, twi + (size_t)j * S::N, pc,
+                            sa, sb, threadIdx.x, true, BlockSync{}, hook);
+      __syncthreads();
+      cur = s_next;
     }
     if (threadIdx.x == 0) {
       __threadfence();

@@ -13,12 +13,18 @@ constexpr int ntt_rb() {
   return sizeof(W) == 4 ? 5 : 4;
 }
 
-template <typename W, int LOGN, int MODE, int RB = ntt_rb<W, LOGN>()>
+// register budget per thread
+template <typename W, int LOGN>
+constexpr int ntt_regs() {
+  return 128;
+}
+
+template <typename W, int LOGN, int MODE, int RB = ntt_rb<W, LOGN>(), int REGS = ntt_regs<W, LOGN>()>
 KernelInfo ntt_info() {
   using S = Shape<W, LOGN, RB>;
   using W_ = W;
   KernelInfo ki;
-  ki.fn = (const void*)k_ntt_batch<S, MODE, kNttWarps>;
+  ki.fn = (const void*)k_ntt_batch<S, MODE, kNttWarps, REGS>;
   ki.team = S::T;
   if (S::T <= 32) {
     ki.block = 32 * kNttWarps;

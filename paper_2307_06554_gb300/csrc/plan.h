@@ -23,6 +23,7 @@ struct polymul_plan {
   int grid_cap = 0;    // resident CTAs of ki (persistent grid)
   int* d_flag = nullptr;
   unsigned long long* d_ctr = nullptr;  // 3 x {next, finished}: device entry, 2 host streams
+  int* d_err = nullptr;                 // set by kernels whose bounded waits expired
   // polymul_batch_host staging
   void* d_stage[2] = {nullptr, nullptr};
   size_t stage_bytes = 0;

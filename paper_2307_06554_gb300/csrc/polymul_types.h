@@ -28,6 +28,7 @@ struct NttBatchArgs {
   uint64_t units;      // batch * k
   uint32_t k;
   unsigned long long* ctr;  // {next unit, finished teams}, zero between launches
+  int* err;                 // set to 1 when a bounded device wait expires
 };
 
 }  // namespace pm
