@@ -105,6 +105,37 @@ int upload_ntt_tables(polymul_plan* p) {
   return POLYMUL_OK;
 }
 
+// Tensor path shape: digit width w with n 2^(2w-2) <= 2^24 (exact fp32
+// partial sums), w <= 8 (exact bf16 digits); L balanced digits cover the
+// centred range |x| <= q/2.
+bool tensor_shape(uint32_t n, uint64_t qmax, int* wb, int* L) {
+  const int logn = __builtin_ctz(n);
+  int w = (24 - logn) / 2 + 1;
+  if (w > 8) w = 8;
+  if (w < 2) return false;
+  for (int l = 1; l <= 8; ++l) {
+    const pm::host::u128 cap = (((pm::host::u128)1 << (w * l)) - 1) / 2;
+    if (cap >= qmax / 2) {
+      *wb = w;
+      *L = l;
+      return true;
+    }
+  }
+  return false;
+}
+
+int upload_tensor_tables(polymul_plan* p) {
+  std::vector<TensorPrime> tp(p->k);
+  for (uint32_t j = 0; j < p->k; ++j) {
+    memset(&tp[j], 0, sizeof tp[j]);
+    tp[j].q = (uint32_t)p->q[j];
+    for (int e = 0; e < 15; ++e) tp[j].pw[e] = (int64_t)pm::host::powmod(2, (uint64_t)p->digit_bits * e, p->q[j]);
+  }
+  PM_CUDA(cudaMalloc(&p->d_pc, tp.size() * sizeof(TensorPrime)));
+  PM_CUDA(cudaMemcpy(p->d_pc, tp.data(), tp.size() * sizeof(TensorPrime), cudaMemcpyHostToDevice));
+  return POLYMUL_OK;
+}
+
 bool lookup_ntt(uint32_t elem, int logn, int mode, KernelInfo* ki) {
   if (elem == 4) {
     if (mode == 0) return lookup_ntt_u32_m0(logn, ki);
@@ -137,6 +168,7 @@ int configure_launch(polymul_plan* p) {
   int per_sm = 0;
   PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->ki.fn, p->ki.block, p->ki.smem));
   if (per_sm < 1) return fail(POLYMUL_ENOTSUP, "kernel does not fit on an SM (block %d, smem %d)", p->ki.block, p->ki.smem);
+  if (p->ki.tmem_cols > 0) per_sm = std::min(per_sm, 512 / p->ki.tmem_cols);  // never wait for tensor memory
   p->grid_cap = per_sm * p->num_sms;
   return POLYMUL_OK;
 }
@@ -178,22 +210,33 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
   if (p->mode < 0) ntt_ok = false;
   if (ntt_ok && !lookup_ntt(p->elem, (int)p->logn, p->mode, &p->ki)) ntt_ok = false;
 
+  // tensor path: 32-bit words, n in the instantiated set
+  bool tensor_ok = p->elem == 4 && tensor_shape(n, qmax, &p->digit_bits, &p->digits) &&
+                   lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki);
+
   int rc = POLYMUL_OK;
-  if (path == POLYMUL_PATH_TENSOR) {
-    rc = fail(POLYMUL_ENOTSUP, "tensor path not available for this plan");
+  if (path == POLYMUL_PATH_TENSOR || (path == POLYMUL_PATH_AUTO && !ntt_ok && tensor_ok)) {
+    if (!tensor_ok) {
+      rc = fail(POLYMUL_ENOTSUP, "tensor path not available for n=%u and these moduli", n);
+    } else {
+      p->path = POLYMUL_PATH_TENSOR;
+      p->ki = p->tki;
+      rc = upload_tensor_tables(p);
+      if (rc == POLYMUL_OK) rc = configure_launch(p);
+    }
   } else if (!ntt_ok) {
     rc = fail(POLYMUL_ENOTSUP, "no NTT route for these moduli at n=%u (need prime q = 1 mod 2n, q < 2^31 for 32-bit words)", n);
   } else {
     p->path = POLYMUL_PATH_NTT;
     rc = p->elem == 4 ? upload_ntt_tables<uint32_t>(p) : upload_ntt_tables<uint64_t>(p);
     if (rc == POLYMUL_OK) rc = configure_launch(p);
-    if (rc == POLYMUL_OK) {
-      // work counters for the three launch slots (device entry, two host-entry streams)
-      if (cudaMalloc(&p->d_ctr, 6 * sizeof(unsigned long long)) != cudaSuccess ||
-          cudaMemset(p->d_ctr, 0, 6 * sizeof(unsigned long long)) != cudaSuccess ||
-          cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess || cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess)
-        rc = fail(POLYMUL_ENOMEM, "counter allocation failed");
-    }
+  }
+  if (rc == POLYMUL_OK) {
+    // work counters for the three launch slots (device entry, two host-entry streams)
+    if (cudaMalloc(&p->d_ctr, 6 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(p->d_ctr, 0, 6 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess || cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess)
+      rc = fail(POLYMUL_ENOMEM, "counter allocation failed");
   }
   if (rc != POLYMUL_OK) {
     std::string keep = g_err;
@@ -213,6 +256,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_flag);
   cudaFree(p->d_ctr);
   cudaFree(p->d_err);
+  cudaFree(p->d_q);
   for (int s = 0; s < 2; ++s) {
     cudaFree(p->d_stage[s]);
     if (p->streams[s]) cudaStreamDestroy(p->streams[s]);
@@ -241,11 +285,11 @@ namespace pm {
 
 template <typename W>
 __global__ void k_validate(const W* __restrict__ a, const W* __restrict__ b, uint64_t units, uint32_t n,
-                           uint32_t k, const PrimeConst<W>* __restrict__ pc, int* flag) {
+                           uint32_t k, const uint64_t* __restrict__ qs, int* flag) {
   const uint64_t total = units * n;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const W q = pc[(i / n) % k].q;
+    const W q = (W)qs[(i / n) % k];
     if (a[i] >= q || b[i] >= q) *flag = 1;
   }
 }
@@ -255,14 +299,18 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
   unsigned long long* ctr = p->d_ctr + 2 * slot;
   if (p->flags & POLYMUL_FLAG_VALIDATE) {
     if (!p->d_flag) PM_CUDA(cudaMalloc(&p->d_flag, sizeof(int)));
+    if (!p->d_q) {
+      PM_CUDA(cudaMalloc(&p->d_q, p->k * sizeof(uint64_t)));
+      PM_CUDA(cudaMemcpy(p->d_q, p->q.data(), p->k * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    }
     PM_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), st));
     const int grid = p->num_sms * 4;
     if (p->elem == 4)
       k_validate<uint32_t><<<grid, 256, 0, st>>>((const uint32_t*)a, (const uint32_t*)b, units, p->n, p->k,
-                                                 (const PrimeConst<uint32_t>*)p->d_pc, p->d_flag);
+                                                 p->d_q, p->d_flag);
     else
       k_validate<uint64_t><<<grid, 256, 0, st>>>((const uint64_t*)a, (const uint64_t*)b, units, p->n, p->k,
-                                                 (const PrimeConst<uint64_t>*)p->d_pc, p->d_flag);
+                                                 p->d_q, p->d_flag);
     PM_CUDA(cudaGetLastError());
     int h = 0;
     PM_CUDA(cudaMemcpyAsync(&h, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -271,7 +319,12 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
   }
   const uint64_t need = (units + p->ki.units_per_cta - 1) / p->ki.units_per_cta;
   const int grid = (int)std::min<uint64_t>(need, (uint64_t)p->grid_cap);
-  if (p->elem == 4) {
+  if (p->path == POLYMUL_PATH_TENSOR) {
+    TensorBatchArgs args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, (const TensorPrime*)p->d_pc,
+                         units, p->k, ctr, p->d_err};
+    void* argv[] = {&args};
+    PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
+  } else if (p->elem == 4) {
     NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
                                 (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err};
     void* argv[] = {&args};

@@ -11,6 +11,7 @@ struct KernelInfo {
   int smem = 0;              // dynamic shared memory bytes per CTA
   int team = 0;              // threads per unit
   int units_per_cta = 0;     // units a CTA processes per iteration
+  int tmem_cols = 0;         // tensor-memory columns allocated per CTA (0: none)
 };
 
 // batched negacyclic NTT, k_ntt_batch<W, LOGN, MODE> (MODE: 0 = kQ31,
@@ -20,5 +21,8 @@ bool lookup_ntt_u32_m1(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
 bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
+
+// Toeplitz path on the tensor cores, k_toeplitz_batch<TShape<LOGN, WB, LA, LB>>
+bool lookup_toeplitz(int logn, int wb, int la, int lb, KernelInfo* ki);
 
 }  // namespace pm

@@ -14,12 +14,16 @@ struct polymul_plan {
   uint32_t flags = 0;
   std::vector<uint64_t> q;
   int mode = -1;       // NTT reduction mode (0 = [0,2q), 1 = [0,4q), 2 = unreduced)
+  int digit_bits = 0;  // tensor path: digit width w and digits per coefficient L
+  int digits = 0;
   int device = 0, num_sms = 0;
   // NTT tables: [k][n] (w, w') pairs, forward and inverse; [k] constants
   void* d_twf = nullptr;
   void* d_twi = nullptr;
   void* d_pc = nullptr;
-  pm::KernelInfo ki;
+  pm::KernelInfo ki;   // the main kernel of the chosen path
+  pm::KernelInfo tki;  // tensor-path kernel, when one exists for the shape
+  uint64_t* d_q = nullptr;  // moduli on the device (input validation)
   int grid_cap = 0;    // resident CTAs of ki (persistent grid)
   int* d_flag = nullptr;
   unsigned long long* d_ctr = nullptr;  // 3 x {next, finished}: device entry, 2 host streams

@@ -31,4 +31,22 @@ struct NttBatchArgs {
   int* err;                 // set to 1 when a bounded device wait expires
 };
 
+// Per-prime constants of the Toeplitz (tensor) path.
+struct alignas(16) TensorPrime {
+  uint32_t q;
+  uint32_t pad;
+  int64_t pw[15];  // pw[e] = 2^(w e) mod q: weight of digit pair (s, s') with s + s' = e
+};
+
+struct TensorBatchArgs {
+  const uint32_t* a;
+  const uint32_t* b;
+  uint32_t* c;
+  const TensorPrime* tp;  // [k]
+  uint64_t units;         // batch * k
+  uint32_t k;
+  unsigned long long* ctr;  // {next unit, finished CTAs}
+  int* err;
+};
+
 }  // namespace pm
