@@ -136,6 +136,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _tensor_digits(n: int, qmax: int):
+    """Digit width and count of the tensor path (mirrors the plan's rule:
+    n 2^(2w-2) <= 2^24, w <= 8, L digits cover |x| <= q/2)."""
+    logn = n.bit_length() - 1
+    w = min(8, (24 - logn) // 2 + 1)
+    L = next(l for l in range(1, 9) if ((1 << (w * l)) - 1) // 2 >= qmax // 2)
+    return w, L
+
+
 # ------------------------------------------------------------------ traffic record
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
@@ -270,6 +279,37 @@ def run_ours(args, ws, rank, local):
         e1.synchronize()
         per.append(e0.elapsed_time(e1))
 
+    # the same workload through the tensor (Toeplitz) path, side by side
+    tensor = None
+    try:
+        tplan = polymul.Plan(n, q_list, path=polymul.PATH_TENSOR)
+    except polymul.PolymulError:
+        tplan = None
+    if tplan is not None:
+        def tstep(i):
+            a, b, c = sets[i % nsets]
+            polymul.polymul_batch(tplan.handle, a, b, c, batch, sp)
+        with torch.cuda.stream(stream):
+            for i in range(args.warmup):
+                tstep(i)
+        torch.cuda.synchronize()
+        t0e = torch.cuda.Event(enable_timing=True)
+        t1e = torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        for i in range(args.steps):
+            tstep(i)
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        t_ms = t0e.elapsed_time(t1e) / args.steps
+        tc_last = sets[(args.steps - 1) % nsets][2]
+        t_got = tc_last[[0, 4095]].cpu().numpy().view(np.uint32).astype(np.uint64)
+        tinfo = tplan.info
+        tensor = {"ms_per_step": t_ms, "value": batch / (t_ms / 1e3), "unit": "products/s",
+                  "kernel": "k_toeplitz_batch (tcgen05 kind::f16, bf16 digits, fp32 TMEM accumulators)",
+                  "grid": tinfo["grid"], "block": tinfo["block"], "smem_bytes": tinfo["smem_bytes"],
+                  "_check": t_got}
+        tplan.close()
+
     # end to end through the host-buffer entry point (pinned host memory)
     ha = torch.from_numpy(w.a.view(np.int32)).pin_memory()
     hb = torch.from_numpy(w.b.view(np.int32)).pin_memory()
@@ -292,6 +332,9 @@ def run_ours(args, ws, rank, local):
     want = native.polymul_batch(w.a[idx], w.b[idx], q_list)
     host_ok = bool(np.array_equal(hc.numpy().view(np.uint32)[idx].astype(np.uint64), want))
     bit_exact = bool(np.array_equal(got, want)) and host_ok
+    if tensor is not None:
+        tw = native.polymul_batch(w.a[[0, 4095]], w.b[[0, 4095]], q_list)
+        tensor["bit_exact_sample"] = bool(np.array_equal(tensor.pop("_check"), tw))
 
     t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
     if ws > 1:
@@ -324,6 +367,17 @@ def run_ours(args, ws, rank, local):
             "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
                     "bytes_per_launch": bytes_alg, "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src}}
 
+    if tensor is not None:
+        digits = _tensor_digits(n, max(q_list))
+        flops = 2.0 * n * n * digits[1] * digits[1] * units  # every digit-pair product, as the method performs it
+        peak_tf = peaks.get("bf16_tflops", 1911.7)
+        ach_tf = flops / (tensor["ms_per_step"] / 1e3) / 1e12
+        tensor["digit_bits"], tensor["digits"] = digits
+        tensor["roofline"] = {"bound": "tensor", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                              "frac": ach_tf / peak_tf, "flops_per_launch": flops,
+                              "peak_source": "MEASURED_PEAKS.json bf16_tflops burst (%s)" % peak_src}
+        tensor["vs_ntt"] = tensor["value"] / value
+
     cpu = None
     if not args.no_cpu_baseline:
         rate, cores, done, el = cpu_oracle_rate(w, args.cpu_seconds)
@@ -346,6 +400,7 @@ def run_ours(args, ws, rank, local):
         "cpu_baseline": cpu,
         "clocks": clk,
         "bit_exact_sample": bit_exact,
+        "tensor_path": tensor,
     }
     print(json.dumps(out), flush=True)
     plan.close()
