@@ -78,6 +78,10 @@ typedef struct polymul_plan_info {
     uint32_t block;       /* threads per CTA of the main kernel               */
     uint32_t grid;        /* CTAs of the main kernel (persistent grid)        */
     uint32_t smem_bytes;  /* dynamic shared memory per CTA                    */
+    uint32_t ctas_per_sm; /* resident CTAs per SM of the main kernel          */
+    uint32_t digit_bits;  /* tensor path: digit width w (0 for NTT plans)     */
+    uint32_t digits;      /* tensor path: digits per coefficient L            */
+    uint32_t reserved[5];
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */

@@ -165,10 +165,26 @@ int configure_launch(polymul_plan* p) {
   PM_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
   if (p->ki.smem > 48 * 1024)
     PM_CUDA(cudaFuncSetAttribute(p->ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ki.smem));
+  PM_CUDA(cudaFuncSetAttribute(p->ki.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int per_sm = 0;
-  PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->ki.fn, p->ki.block, p->ki.smem));
+  if (p->ki.tmem_cols > 0) {
+    // The occupancy query reports one CTA per SM for kernels that allocate
+    // tensor memory; co-residency is in fact limited by shared memory,
+    // registers, threads and the 512 tensor-memory columns, so count those.
+    cudaFuncAttributes fa;
+    PM_CUDA(cudaFuncGetAttributes(&fa, p->ki.fn));
+    int smem_sm = 0, resv = 0;
+    PM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device));
+    PM_CUDA(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, p->device));
+    const int regs = (fa.numRegs + 7) / 8 * 8;
+    per_sm = smem_sm / (p->ki.smem + (int)fa.sharedSizeBytes + resv);
+    per_sm = std::min(per_sm, 65536 / std::max(1, regs * p->ki.block));
+    per_sm = std::min(per_sm, 2048 / p->ki.block);
+    per_sm = std::min(per_sm, 512 / p->ki.tmem_cols);  // never wait for tensor memory
+  } else {
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->ki.fn, p->ki.block, p->ki.smem));
+  }
   if (per_sm < 1) return fail(POLYMUL_ENOTSUP, "kernel does not fit on an SM (block %d, smem %d)", p->ki.block, p->ki.smem);
-  if (p->ki.tmem_cols > 0) per_sm = std::min(per_sm, 512 / p->ki.tmem_cols);  // never wait for tensor memory
   p->grid_cap = per_sm * p->num_sms;
   return POLYMUL_OK;
 }
@@ -277,6 +293,9 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->block = (uint32_t)p->ki.block;
   info->grid = (uint32_t)p->grid_cap;
   info->smem_bytes = (uint32_t)p->ki.smem;
+  info->ctas_per_sm = (uint32_t)(p->num_sms ? p->grid_cap / p->num_sms : 0);
+  info->digit_bits = p->path == POLYMUL_PATH_TENSOR ? (uint32_t)p->digit_bits : 0;
+  info->digits = p->path == POLYMUL_PATH_TENSOR ? (uint32_t)p->digits : 0;
   return POLYMUL_OK;
 }
 

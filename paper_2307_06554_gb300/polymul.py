@@ -43,7 +43,8 @@ class polymul_opts(ctypes.Structure):
 
 class polymul_plan_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
-                ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes")]
+                ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
+                 "digit_bits", "digits")] + [("reserved", ctypes.c_uint32 * 5)]
 
 
 def library_path() -> str:
@@ -134,7 +135,7 @@ def polymul_plan_status(plan: int, stream=None) -> None:
 def polymul_plan_info_get(plan: int) -> dict:
     info = polymul_plan_info()
     _check(_lib.polymul_plan_info_get(plan, ctypes.byref(info)))
-    return {name: getattr(info, name) for name, _ in polymul_plan_info._fields_}
+    return {name: getattr(info, name) for name, _ in polymul_plan_info._fields_ if name != "reserved"}
 
 
 def polymul_destroy(plan: int) -> None:
