@@ -84,14 +84,18 @@ void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::vector<W
   pc.pad = 0;
 }
 
+// Tables for the NTT primes: the plan's moduli, or (auxiliary-prime mode)
+// the single auxiliary prime.
 template <typename W>
 int upload_ntt_tables(polymul_plan* p) {
+  const std::vector<uint64_t> primes = p->aux_prime ? std::vector<uint64_t>{p->aux_prime} : p->q;
+  const uint32_t np = (uint32_t)primes.size();
   std::vector<W> all_f, all_i, f, i;
-  std::vector<PrimeConst<W>> pcs(p->k);
-  all_f.reserve(2 * (size_t)p->n * p->k);
-  all_i.reserve(2 * (size_t)p->n * p->k);
-  for (uint32_t j = 0; j < p->k; ++j) {
-    build_ntt_tables<W>(p->q[j], p->n, f, i, pcs[j]);
+  std::vector<PrimeConst<W>> pcs(np);
+  all_f.reserve(2 * (size_t)p->n * np);
+  all_i.reserve(2 * (size_t)p->n * np);
+  for (uint32_t j = 0; j < np; ++j) {
+    build_ntt_tables<W>(primes[j], p->n, f, i, pcs[j]);
     all_f.insert(all_f.end(), f.begin(), f.end());
     all_i.insert(all_i.end(), i.begin(), i.end());
   }
@@ -102,7 +106,27 @@ int upload_ntt_tables(polymul_plan* p) {
   PM_CUDA(cudaMemcpy(p->d_twf, all_f.data(), tb, cudaMemcpyHostToDevice));
   PM_CUDA(cudaMemcpy(p->d_twi, all_i.data(), tb, cudaMemcpyHostToDevice));
   PM_CUDA(cudaMemcpy(p->d_pc, pcs.data(), pcs.size() * sizeof(PrimeConst<W>), cudaMemcpyHostToDevice));
+  if (p->aux_prime) {
+    std::vector<W> qs(p->q.begin(), p->q.end());
+    PM_CUDA(cudaMalloc(&p->d_outer, qs.size() * sizeof(W)));
+    PM_CUDA(cudaMemcpy(p->d_outer, qs.data(), qs.size() * sizeof(W), cudaMemcpyHostToDevice));
+  }
   return POLYMUL_OK;
+}
+
+// Auxiliary NTT prime for moduli without a 2n-th root of unity: the largest
+// prime p < 2^31 with 2n | p - 1; usable when p > 2 n floor(qmax/2)^2 (the
+// centred integer product then fits in (-p/2, p/2)).  0 if none.
+uint64_t find_aux_prime(uint32_t n, uint64_t qmax) {
+  const pm::host::u128 half = qmax / 2;
+  const pm::host::u128 bound = 2 * (pm::host::u128)n * half * half;
+  const uint64_t step = 2ull * n;
+  for (uint64_t kk = ((1ull << 31) - 2) / step; kk > 0; --kk) {
+    const uint64_t cand = kk * step + 1;
+    if ((pm::host::u128)cand <= bound) return 0;
+    if (pm::host::is_prime(cand)) return cand;
+  }
+  return 0;
 }
 
 // Tensor path shape: digit width w with n 2^(2w-2) <= 2^24 (exact fp32
@@ -226,12 +250,31 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
   if (p->mode < 0) ntt_ok = false;
   if (ntt_ok && !lookup_ntt(p->elem, (int)p->logn, p->mode, &p->ki)) ntt_ok = false;
 
+  // auxiliary-prime NTT: one 31-bit prime carries the exact integer product
+  bool aux_ok = false;
+  if (!ntt_ok && p->elem == 4 && qmax < (1ull << 31)) {
+    const uint64_t ap = find_aux_prime(n, qmax);
+    KernelInfo aki;
+    if (ap && ap > (1ull << 30) && lookup_ntt_u32_aux((int)p->logn, &aki)) {
+      aux_ok = true;
+      p->aux_candidate = ap;
+      p->aki = aki;
+    }
+  }
+
   // tensor path: 32-bit words, n in the instantiated set
   bool tensor_ok = p->elem == 4 && tensor_shape(n, qmax, &p->digit_bits, &p->digits) &&
                    lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki);
 
   int rc = POLYMUL_OK;
-  if (path == POLYMUL_PATH_TENSOR || (path == POLYMUL_PATH_AUTO && !ntt_ok && tensor_ok)) {
+  if ((path == POLYMUL_PATH_NTT || path == POLYMUL_PATH_AUTO) && !ntt_ok && aux_ok) {
+    p->path = POLYMUL_PATH_NTT;
+    p->aux_prime = p->aux_candidate;
+    p->mode = 0;
+    p->ki = p->aki;
+    rc = upload_ntt_tables<uint32_t>(p);
+    if (rc == POLYMUL_OK) rc = configure_launch(p);
+  } else if (path == POLYMUL_PATH_TENSOR || (path == POLYMUL_PATH_AUTO && !ntt_ok && tensor_ok)) {
     if (!tensor_ok) {
       rc = fail(POLYMUL_ENOTSUP, "tensor path not available for n=%u and these moduli", n);
     } else {
@@ -273,6 +316,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_ctr);
   cudaFree(p->d_err);
   cudaFree(p->d_q);
+  cudaFree(p->d_outer);
   for (int s = 0; s < 2; ++s) {
     cudaFree(p->d_stage[s]);
     if (p->streams[s]) cudaStreamDestroy(p->streams[s]);
@@ -289,7 +333,7 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->k = p->k;
   info->elem_bytes = p->elem;
   info->path = p->path;
-  info->aux_primes = 0;
+  info->aux_primes = p->aux_prime ? 1u : 0u;
   info->block = (uint32_t)p->ki.block;
   info->grid = (uint32_t)p->grid_cap;
   info->smem_bytes = (uint32_t)p->ki.smem;
@@ -345,12 +389,14 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
   } else if (p->elem == 4) {
     NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
-                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err};
+                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err,
+                                (const uint32_t*)p->d_outer};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
   } else {
     NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
-                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err};
+                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err,
+                                (const uint64_t*)p->d_outer};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
   }

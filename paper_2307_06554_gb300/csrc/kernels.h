@@ -21,6 +21,7 @@ bool lookup_ntt_u32_m1(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
 bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
+bool lookup_ntt_u32_aux(int logn, KernelInfo* ki);  // auxiliary-prime mode, logn 4..14
 
 // Toeplitz path on the tensor cores, k_toeplitz_batch<TShape<LOGN, WB, LA, LB>>
 bool lookup_toeplitz(int logn, int wb, int la, int lb, KernelInfo* ki);

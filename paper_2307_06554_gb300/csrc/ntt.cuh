@@ -333,17 +333,28 @@ __device__ __forceinline__ void inv_from(W (&x)[S::R], W* s, const TwPair<W>* __
 // (unswizzled, contiguous) in sa and sb.  Every thread of the team calls it;
 // inactive threads (act = false) compute on stale data and store nothing, so
 // that team barriers stay uniform.  `hook` is called once sa/sb are free.
-template <class S, int MODE, class Sync, class Hook, typename W = typename S::W>
+// Auxiliary-prime mode (AUX = true): the ring modulus qo has no 2n-th root
+// of unity, so the product is formed over the integers instead.  Operands
+// are lifted to their centred representatives (|x| <= qo/2), which the NTT
+// prime p (> 2 n (qo/2)^2) holds as residues; the result mod p, centred,
+// is the exact integer negacyclic product, reduced mod qo on the way out.
+template <class S, int MODE, bool AUX, class Sync, class Hook, typename W = typename S::W>
 __device__ __forceinline__ void polymul_unit(W* __restrict__ c, const TwPair<W>* __restrict__ twf,
                                              const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
-                                             W* sa, W* sb, uint32_t t, bool act, Sync sync, Hook&& hook) {
+                                             W* sa, W* sb, uint32_t t, bool act, Sync sync, Hook&& hook,
+                                             W qo = 0) {
   constexpr int TOP = S::NPH - 1;
   W xa[S::R], xb[S::R];
+  const W lift = pc.q - qo, half = qo >> 1;
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
     const uint32_t j = elem_index<S, TOP>(e, t);
     xa[e] = sa[j];
     xb[e] = sb[j];
+    if constexpr (AUX) {
+      xa[e] = xa[e] > half ? xa[e] + lift : xa[e];
+      xb[e] = xb[e] > half ? xb[e] + lift : xb[e];
+    }
   });
   if constexpr (S::NPH == 1) {
     sync();
@@ -365,7 +376,17 @@ __device__ __forceinline__ void polymul_unit(W* __restrict__ c, const TwPair<W>*
   if (act) {
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;
-      c[elem_index<S, TOP>(e, t)] = csub(xa[e], pc.q);
+      W y = csub(xa[e], pc.q);
+      if constexpr (AUX) {
+        // centre mod p, then reduce mod qo
+        if (y > (pc.q >> 1)) {
+          const W r = (pc.q - y) % qo;
+          y = r ? qo - r : W(0);
+        } else {
+          y = y % qo;
+        }
+      }
+      c[elem_index<S, TOP>(e, t)] = y;
     });
   }
 }
@@ -399,7 +420,9 @@ constexpr int ntt_block() {
 
 // REGS: register budget per thread (sets the resident-CTA floor the
 // compiler must honour).
-template <class S, int MODE, int WARPS, int REGS>
+// AUX: auxiliary-prime mode (see polymul_unit); every unit then uses the
+// single NTT prime pc[0] and the ring modulus outer_q[u % k].
+template <class S, int MODE, int WARPS, int REGS, bool AUX = false>
 __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, WARPS>() * REGS))
     k_ntt_batch(NttBatchArgs<typename S::W> args) {
   using W = typename S::W;
@@ -452,14 +475,16 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       const uint64_t u = cur + team;
       const bool act = u < units;
       const uint32_t j = act ? (uint32_t)(u % k) : 0u;
-      const PrimeConst<W> pc = args.pc[j];
+      const PrimeConst<W> pc = args.pc[AUX ? 0 : j];
+      const W qo = AUX ? args.outer_q[j] : W(0);
       unsigned long long nxt = units;
       auto hook = [&]() {
         nxt = grab();
         if (lane == 0 && nxt < units) issue(nxt);
       };
-      polymul_unit<S, MODE>(args.c + (act ? (size_t)u * S::N : 0), twf + (size_t)j * S::N,
-                            twi + (size_t)j * S::N, pc, sa, sb, t, act, WarpSync{}, hook);
+      const uint32_t tj = AUX ? 0u : j;
+      polymul_unit<S, MODE, AUX>(args.c + (act ? (size_t)u * S::N : 0), twf + (size_t)tj * S::N,
+                                 twi + (size_t)tj * S::N, pc, sa, sb, t, act, WarpSync{}, hook, qo);
       cur = nxt;
     }
     if (lane == 0) {
@@ -499,15 +524,17 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       }
       parity ^= 1u;
       const uint32_t j = (uint32_t)(cur % k);
-      const PrimeConst<W> pc = args.pc[j];
+      const uint32_t tj = AUX ? 0u : j;
+      const PrimeConst<W> pc = args.pc[tj];
+      const W qo = AUX ? args.outer_q[j] : W(0);
       auto hook = [&]() {  // called after a barrier: every thread is done with sa/sb
         if (threadIdx.x == 0) {
           s_next = atomicAdd(ctr, 1ull);
           if (s_next < units) issue(s_next);
         }
       };
-      polymul_unit<S, MODE>(args.c + (size_t)cur * S::N, twf + (size_t)j * S::N, twi + (size_t)j * S::N, pc,
-                            sa, sb, threadIdx.x, true, BlockSync{}, hook);
+      polymul_unit<S, MODE, AUX>(args.c + (size_t)cur * S::N, twf + (size_t)tj * S::N,
+                                 twi + (size_t)tj * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{}, hook, qo);
       __syncthreads();
       cur = s_next;
     }

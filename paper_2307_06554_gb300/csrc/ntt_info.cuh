@@ -23,12 +23,13 @@ constexpr int ntt_regs() {
   return 128;
 }
 
-template <typename W, int LOGN, int MODE, int RB = ntt_rb<W, LOGN>(), int REGS = ntt_regs<W, LOGN>()>
+template <typename W, int LOGN, int MODE, bool AUX = false, int RB = ntt_rb<W, LOGN>(),
+          int REGS = ntt_regs<W, LOGN>()>
 KernelInfo ntt_info() {
   using S = Shape<W, LOGN, RB>;
   using W_ = W;
   KernelInfo ki;
-  ki.fn = (const void*)k_ntt_batch<S, MODE, kNttWarps, REGS>;
+  ki.fn = (const void*)k_ntt_batch<S, MODE, kNttWarps, REGS, AUX>;
   ki.team = S::T;
   if (S::T <= 32) {
     ki.block = 32 * kNttWarps;

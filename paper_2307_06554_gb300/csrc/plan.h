@@ -24,6 +24,10 @@ struct polymul_plan {
   pm::KernelInfo ki;   // the main kernel of the chosen path
   pm::KernelInfo tki;  // tensor-path kernel, when one exists for the shape
   uint64_t* d_q = nullptr;  // moduli on the device (input validation)
+  // auxiliary-prime NTT (moduli without a 2n-th root of unity)
+  uint64_t aux_prime = 0, aux_candidate = 0;
+  pm::KernelInfo aki;
+  void* d_outer = nullptr;  // the ring moduli as words [k]
   int grid_cap = 0;    // resident CTAs of ki (persistent grid)
   int* d_flag = nullptr;
   unsigned long long* d_ctr = nullptr;  // 3 x {next, finished}: device entry, 2 host streams

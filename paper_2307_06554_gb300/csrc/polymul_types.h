@@ -29,6 +29,7 @@ struct NttBatchArgs {
   uint32_t k;
   unsigned long long* ctr;  // {next unit, finished teams}, zero between launches
   int* err;                 // set to 1 when a bounded device wait expires
+  const W* outer_q;         // auxiliary-prime mode: the ring moduli [k]
 };
 
 // Per-prime constants of the Toeplitz (tensor) path.
