@@ -141,6 +141,63 @@ int polymul_plan_info_get(const polymul_plan *plan, polymul_plan_info *info);
  * make sure no launch of the plan is still running. */
 void polymul_destroy(polymul_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * Uneven batches (products of different degrees and prime counts) in one
+ * persistent launch.  Every modulus is a prime of a shared pool; each product
+ * has its own degree n and its own subset of the pool (its RNS primes,
+ * Sec. 2.4).  Operands and results live in flat caller-owned arrays of
+ * uint32_t: product p occupies rows [offset, offset + k*n) laid out [k][n].
+ * ---------------------------------------------------------------------- */
+typedef struct polymul_ragged polymul_ragged;             /* pool + tables   */
+typedef struct polymul_ragged_batch polymul_ragged_batch; /* a prepared list */
+
+typedef struct polymul_desc {
+    uint32_t n;            /* degree: power of two, 1024 <= n <= n_max        */
+    uint32_t k;            /* number of primes of this product (>= 1)         */
+    uint32_t prime_offset; /* its primes: prime_idx[prime_offset .. +k)       */
+    uint32_t reserved;
+    uint64_t offset;       /* element offset of its [k][n] rows (multiple of 4) */
+} polymul_desc;
+
+/*
+ * polymul_ragged_create -- tables for a pool of primes (each prime < 2^31,
+ * 2 n_max | q - 1, distinct) at the largest degree n_max (power of two in
+ * [1024, 16384]); a product of degree n <= n_max uses the length-n prefix.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int polymul_ragged_create(const uint64_t *pool, uint32_t pool_size, uint32_t n_max,
+                          polymul_ragged **out);
+
+/*
+ * polymul_ragged_prepare -- plan a list of `count` products: validates every
+ * descriptor (degree, prime indices < pool size, rows inside `total_elems`
+ * elements of the operand arrays), flattens them into (product, prime) units
+ * and packs the units into work items, largest degree first.  The plan is
+ * uploaded once and reused by every run.  Products must not overlap in c.
+ */
+int polymul_ragged_prepare(polymul_ragged *ctx, const polymul_desc *descs, uint32_t count,
+                           const uint32_t *prime_idx, uint64_t prime_idx_len,
+                           uint64_t total_elems, polymul_ragged_batch **out);
+
+/* One persistent launch over the whole prepared list (asynchronous). */
+int polymul_ragged_run(polymul_ragged_batch *batch, const void *a, const void *b, void *c,
+                       void *stream);
+
+/* The same launch as a CUDA graph: built on the first call, replayed after;
+ * new operand pointers update the recorded launch in place. */
+int polymul_ragged_run_graph(polymul_ragged_batch *batch, const void *a, const void *b, void *c,
+                             void *stream);
+
+/* As polymul_plan_status, for a prepared list. */
+int polymul_ragged_status(polymul_ragged_batch *batch, void *stream);
+
+/* Units, work items and CTAs of a prepared list (any pointer may be NULL). */
+int polymul_ragged_batch_info(const polymul_ragged_batch *batch, uint64_t *units, uint64_t *items,
+                              uint32_t *grid);
+
+void polymul_ragged_batch_destroy(polymul_ragged_batch *batch); /* NULL-safe */
+void polymul_ragged_destroy(polymul_ragged *ctx);               /* NULL-safe */
+
 /* Message for the calling thread's most recent failing call ("" if none).
  * The pointer stays valid until the next call from the same thread. */
 const char *polymul_last_error(void);

@@ -23,6 +23,10 @@ bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
 bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_aux(int logn, KernelInfo* ki);  // auxiliary-prime mode, logn 4..14
 
+// uneven batches in one persistent launch (32-bit words, n = 2^10..2^14)
+bool lookup_ntt_ragged(int mode, KernelInfo* ki);
+int ragged_teams(int logn);
+
 // Toeplitz path on the tensor cores, k_toeplitz_batch<TShape<LOGN, WB, LA, LB>>
 bool lookup_toeplitz(int logn, int wb, int la, int lb, KernelInfo* ki);
 

@@ -32,6 +32,36 @@ struct NttBatchArgs {
   const W* outer_q;         // auxiliary-prime mode: the ring moduli [k]
 };
 
+// Ragged (uneven) batches: one unit = one (product, prime) row of n words.
+struct alignas(16) RaggedUnit {
+  uint64_t offset;  // element offset of the row in a, b, c
+  uint32_t prime;   // index into the prime pool
+  uint32_t pad;
+};
+
+// One CTA work item: `count` consecutive units of degree 2^logn.
+struct alignas(16) RaggedItem {
+  uint32_t logn;
+  uint32_t first;
+  uint32_t count;
+  uint32_t pad;
+};
+
+struct RaggedArgs {
+  const uint32_t* a;
+  const uint32_t* b;
+  uint32_t* c;
+  const RaggedUnit* units;
+  const RaggedItem* items;
+  uint64_t n_items;
+  const void* tw_fwd;              // [pool][nmax] TwPair<uint32_t>
+  const void* tw_inv;
+  const PrimeConst<uint32_t>* pc;  // [pool][16]: constants for degree 2^logn at [p * 16 + logn]
+  uint32_t nmax;
+  unsigned long long* ctr;
+  int* err;
+};
+
 // Per-prime constants of the Toeplitz (tensor) path.
 struct alignas(16) TensorPrime {
   uint32_t q;

@@ -1,0 +1,305 @@
+// C-ABI entry points for uneven batches (polymul_ragged_*), see
+// include/polymul.h.  Host-side planning: tables per pool prime, units and
+// work items, one persistent launch, optional CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/polymul.h"
+#include "host_math.h"
+#include "kernels.h"
+#include "plan.h"
+#include "polymul_types.h"
+
+using namespace pm;
+
+#define PM_CUDA(call)                                       \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return pm::cuda_fail(e_, #call); \
+  } while (0)
+
+struct polymul_ragged {
+  uint32_t nmax = 0, lognmax = 0;
+  std::vector<uint64_t> pool;
+  int mode = 0;
+  void* d_twf = nullptr;
+  void* d_twi = nullptr;
+  void* d_pc = nullptr;
+  KernelInfo ki;
+  int grid_cap = 0, device = 0, num_sms = 0;
+};
+
+struct polymul_ragged_batch {
+  polymul_ragged* ctx = nullptr;
+  uint64_t n_units = 0, n_items = 0, total_elems = 0;
+  RaggedUnit* d_units = nullptr;
+  RaggedItem* d_items = nullptr;
+  unsigned long long* d_ctr = nullptr;
+  int* d_err = nullptr;
+  RaggedArgs args{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t node = nullptr;
+};
+
+namespace {
+
+// tables of one prime at nmax, plus the constants of every degree 2^logn
+// <= nmax derived from the same root (so that each degree's tables are
+// prefixes of these)
+void build_ragged_prime(uint64_t q, uint32_t nmax, std::vector<uint32_t>& twf, std::vector<uint32_t>& twi,
+                        PrimeConst<uint32_t>* pc16) {
+  using namespace pm::host;
+  const int lognmax = __builtin_ctz(nmax);
+  const uint64_t psi = primitive_2n_root(q, nmax);
+  const uint64_t psi_inv = powmod(psi, q - 2, q);
+  for (uint32_t i = 0; i < nmax; ++i) {
+    const uint32_t r = bitrev(i, lognmax);
+    const uint64_t w = powmod(psi, r, q), v = powmod(psi_inv, r, q);
+    twf.push_back((uint32_t)w);
+    twf.push_back((uint32_t)shoup_companion(w, q, 32));
+    twi.push_back((uint32_t)v);
+    twi.push_back((uint32_t)shoup_companion(v, q, 32));
+  }
+  const uint64_t v1 = powmod(psi_inv, bitrev(1, lognmax), q);  // = psi_n^-brv_n(1) for every n <= nmax
+  const uint64_t r_mod_q = (1ull << 32) % q;
+  for (int logn = 0; logn < 16; ++logn) {
+    PrimeConst<uint32_t>& c = pc16[logn];
+    memset(&c, 0, sizeof c);
+    if (logn > lognmax) continue;
+    const uint64_t ninv = powmod(1ull << logn, q - 2, q);
+    const uint64_t scale = mulmod(ninv, r_mod_q, q);
+    const uint64_t scale_w = mulmod(v1, scale, q);
+    c.q = (uint32_t)q;
+    c.q2 = (uint32_t)(2 * q);
+    c.qinv = (uint32_t)inv_pow2_64(q);
+    c.scale = (uint32_t)scale;
+    c.scale_p = (uint32_t)shoup_companion(scale, q, 32);
+    c.scale_w = (uint32_t)scale_w;
+    c.scale_wp = (uint32_t)shoup_companion(scale_w, q, 32);
+  }
+}
+
+}  // namespace
+
+extern "C" void polymul_ragged_destroy(polymul_ragged* r) {
+  if (!r) return;
+  cudaFree(r->d_twf);
+  cudaFree(r->d_twi);
+  cudaFree(r->d_pc);
+  delete r;
+}
+
+extern "C" int polymul_ragged_create(const uint64_t* pool, uint32_t pool_size, uint32_t n_max, polymul_ragged** out) {
+  clear_error();
+  if (!out || !pool || pool_size == 0) return fail(POLYMUL_EINVAL, "need a non-empty prime pool and an out pointer");
+  if (n_max < 1024 || n_max > 16384 || (n_max & (n_max - 1)))
+    return fail(POLYMUL_EINVAL, "n_max=%u must be a power of two in [1024, 16384]", n_max);
+  for (uint32_t j = 0; j < pool_size; ++j) {
+    const uint64_t q = pool[j];
+    if (q >= (1ull << 31) || !pm::host::is_prime(q) || (q - 1) % (2ull * n_max) != 0)
+      return fail(POLYMUL_EINVAL, "pool[%u]=%llu must be a prime < 2^31 with 2 n_max | q - 1", j,
+                  (unsigned long long)q);
+    for (uint32_t i = 0; i < j; ++i)
+      if (pool[i] == q) return fail(POLYMUL_EINVAL, "duplicate pool prime %llu", (unsigned long long)q);
+  }
+  polymul_ragged* r = new polymul_ragged();
+  r->nmax = n_max;
+  r->lognmax = __builtin_ctz(n_max);
+  r->pool.assign(pool, pool + pool_size);
+  const uint64_t qmax = *std::max_element(r->pool.begin(), r->pool.end());
+  r->mode = qmax < (1ull << 30) ? 1 : 0;  // Harvey bounds when every prime allows them
+  int rc = POLYMUL_OK;
+  std::vector<uint32_t> twf, twi;
+  std::vector<PrimeConst<uint32_t>> pcs((size_t)pool_size * 16);
+  for (uint32_t j = 0; j < pool_size; ++j) build_ragged_prime(r->pool[j], n_max, twf, twi, &pcs[(size_t)j * 16]);
+  auto up = [&](void** dst, const void* src, size_t bytes) -> int {
+    if (cudaMalloc(dst, bytes) != cudaSuccess) return fail(POLYMUL_ENOMEM, "table allocation failed");
+    PM_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return POLYMUL_OK;
+  };
+  if (rc == POLYMUL_OK) rc = up(&r->d_twf, twf.data(), twf.size() * 4);
+  if (rc == POLYMUL_OK) rc = up(&r->d_twi, twi.data(), twi.size() * 4);
+  if (rc == POLYMUL_OK) rc = up(&r->d_pc, pcs.data(), pcs.size() * sizeof(PrimeConst<uint32_t>));
+  if (rc == POLYMUL_OK && !lookup_ntt_ragged(r->mode, &r->ki)) rc = fail(POLYMUL_ENOTSUP, "no ragged kernel");
+  if (rc == POLYMUL_OK) {
+    int per_sm = 0;
+    cudaError_t e = cudaGetDevice(&r->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(r->ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->ki.smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, r->ki.fn, r->ki.block, r->ki.smem);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "ragged kernel configuration");
+    } else if (per_sm < 1) {
+      rc = fail(POLYMUL_ENOTSUP, "ragged kernel does not fit on an SM");
+    } else {
+      r->grid_cap = per_sm * r->num_sms;
+    }
+  }
+  if (rc != POLYMUL_OK) {
+    std::string keep = polymul_last_error();
+    polymul_ragged_destroy(r);
+    fail(rc, "%s", keep.c_str());
+    return rc;
+  }
+  *out = r;
+  return POLYMUL_OK;
+}
+
+extern "C" void polymul_ragged_batch_destroy(polymul_ragged_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_units);
+  cudaFree(b->d_items);
+  cudaFree(b->d_ctr);
+  cudaFree(b->d_err);
+  delete b;
+}
+
+extern "C" int polymul_ragged_prepare(polymul_ragged* r, const polymul_desc* descs, uint32_t count,
+                                      const uint32_t* prime_idx, uint64_t prime_idx_len, uint64_t total_elems,
+                                      polymul_ragged_batch** out) {
+  clear_error();
+  if (!r || !out || (count && (!descs || !prime_idx))) return fail(POLYMUL_EINVAL, "null argument");
+  // units grouped by degree class
+  std::vector<std::vector<RaggedUnit>> cls(16);
+  for (uint32_t p = 0; p < count; ++p) {
+    const polymul_desc& d = descs[p];
+    if (d.n < 1024 || d.n > r->nmax || (d.n & (d.n - 1)))
+      return fail(POLYMUL_EINVAL, "product %u: n=%u must be a power of two in [1024, %u]", p, d.n, r->nmax);
+    if (d.k == 0 || (uint64_t)d.prime_offset + d.k > prime_idx_len)
+      return fail(POLYMUL_EINVAL, "product %u: primes [%u, %u) outside the index array", p, d.prime_offset,
+                  d.prime_offset + d.k);
+    if (d.offset % 4 != 0 || d.offset + (uint64_t)d.k * d.n > total_elems)
+      return fail(POLYMUL_EINVAL, "product %u: rows must be 16-byte aligned and inside the buffers", p);
+    const int logn = __builtin_ctz(d.n);
+    for (uint32_t i = 0; i < d.k; ++i) {
+      const uint32_t pi = prime_idx[d.prime_offset + i];
+      if (pi >= r->pool.size()) return fail(POLYMUL_EINVAL, "product %u: prime index %u outside the pool", p, pi);
+      cls[logn].push_back(RaggedUnit{d.offset + (uint64_t)i * d.n, pi, 0});
+    }
+  }
+  std::vector<RaggedUnit> units;
+  std::vector<RaggedItem> items;
+  for (int logn = 15; logn >= 0; --logn) {  // largest degree first (longest items first)
+    if (cls[logn].empty()) continue;
+    const int g = ragged_teams(logn);
+    for (size_t i = 0; i < cls[logn].size(); i += g) {
+      const uint32_t cnt = (uint32_t)std::min<size_t>(g, cls[logn].size() - i);
+      items.push_back(RaggedItem{(uint32_t)logn, (uint32_t)(units.size() + i), cnt, 0});
+    }
+    units.insert(units.end(), cls[logn].begin(), cls[logn].end());
+  }
+  polymul_ragged_batch* b = new polymul_ragged_batch();
+  b->ctx = r;
+  b->n_units = units.size();
+  b->n_items = items.size();
+  b->total_elems = total_elems;
+  int rc = POLYMUL_OK;
+  auto up = [&](void** dst, const void* src, size_t bytes) -> int {
+    if (cudaMalloc(dst, bytes ? bytes : 16) != cudaSuccess) return fail(POLYMUL_ENOMEM, "batch allocation failed");
+    if (bytes) PM_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return POLYMUL_OK;
+  };
+  rc = up((void**)&b->d_units, units.data(), units.size() * sizeof(RaggedUnit));
+  if (rc == POLYMUL_OK) rc = up((void**)&b->d_items, items.data(), items.size() * sizeof(RaggedItem));
+  if (rc == POLYMUL_OK) {
+    const unsigned long long zero[2] = {0, 0};
+    const int z = 0;
+    rc = up((void**)&b->d_ctr, zero, sizeof zero);
+    if (rc == POLYMUL_OK) rc = up((void**)&b->d_err, &z, sizeof z);
+  }
+  if (rc != POLYMUL_OK) {
+    std::string keep = polymul_last_error();
+    polymul_ragged_batch_destroy(b);
+    fail(rc, "%s", keep.c_str());
+    return rc;
+  }
+  b->args = RaggedArgs{nullptr, nullptr, nullptr, b->d_units, b->d_items, b->n_items, r->d_twf, r->d_twi,
+                       (const PrimeConst<uint32_t>*)r->d_pc, r->nmax, b->d_ctr, b->d_err};
+  *out = b;
+  return POLYMUL_OK;
+}
+
+namespace {
+int ragged_check(polymul_ragged_batch* b, const void* a, const void* bb, void* c) {
+  if (!b) return fail(POLYMUL_EINVAL, "batch is NULL");
+  if (b->n_items && (!a || !bb || !c)) return fail(POLYMUL_EINVAL, "null operand pointer");
+  if (((uintptr_t)a | (uintptr_t)bb | (uintptr_t)c) & 15u) return fail(POLYMUL_EINVAL, "operands must be 16-byte aligned");
+  return POLYMUL_OK;
+}
+int ragged_grid(const polymul_ragged_batch* b) {
+  return (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap, std::max<uint64_t>(1, b->n_items));
+}
+}  // namespace
+
+extern "C" int polymul_ragged_run(polymul_ragged_batch* b, const void* a, const void* bb, void* c, void* stream) {
+  clear_error();
+  int rc = ragged_check(b, a, bb, c);
+  if (rc != POLYMUL_OK || b->n_items == 0) return rc;
+  b->args.a = (const uint32_t*)a;
+  b->args.b = (const uint32_t*)bb;
+  b->args.c = (uint32_t*)c;
+  void* argv[] = {&b->args};
+  PM_CUDA(cudaLaunchKernel(b->ctx->ki.fn, ragged_grid(b), b->ctx->ki.block, argv, b->ctx->ki.smem,
+                           (cudaStream_t)stream));
+  return POLYMUL_OK;
+}
+
+// The same single launch, recorded once as a one-node CUDA graph and
+// replayed; a change of operand pointers updates the node in place.
+extern "C" int polymul_ragged_run_graph(polymul_ragged_batch* b, const void* a, const void* bb, void* c,
+                                        void* stream) {
+  clear_error();
+  int rc = ragged_check(b, a, bb, c);
+  if (rc != POLYMUL_OK || b->n_items == 0) return rc;
+  b->args.a = (const uint32_t*)a;
+  b->args.b = (const uint32_t*)bb;
+  b->args.c = (uint32_t*)c;
+  void* argv[] = {&b->args};
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof kp);
+  kp.func = const_cast<void*>(b->ctx->ki.fn);
+  kp.gridDim = dim3(ragged_grid(b));
+  kp.blockDim = dim3(b->ctx->ki.block);
+  kp.sharedMemBytes = b->ctx->ki.smem;
+  kp.kernelParams = argv;
+  if (!b->exec) {
+    PM_CUDA(cudaGraphCreate(&b->graph, 0));
+    PM_CUDA(cudaGraphAddKernelNode(&b->node, b->graph, nullptr, 0, &kp));
+    PM_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  } else {
+    PM_CUDA(cudaGraphExecKernelNodeSetParams(b->exec, b->node, &kp));
+  }
+  PM_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return POLYMUL_OK;
+}
+
+extern "C" int polymul_ragged_status(polymul_ragged_batch* b, void* stream) {
+  clear_error();
+  if (!b) return fail(POLYMUL_EINVAL, "batch is NULL");
+  PM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int h = 0;
+  PM_CUDA(cudaMemcpy(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return POLYMUL_OK;
+  PM_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
+  PM_CUDA(cudaMemset(b->d_ctr, 0, 2 * sizeof(unsigned long long)));
+  return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
+}
+
+extern "C" int polymul_ragged_batch_info(const polymul_ragged_batch* b, uint64_t* units, uint64_t* items,
+                                         uint32_t* grid) {
+  clear_error();
+  if (!b) return fail(POLYMUL_EINVAL, "batch is NULL");
+  if (units) *units = b->n_units;
+  if (items) *items = b->n_items;
+  if (grid) *grid = (uint32_t)ragged_grid(b);
+  return POLYMUL_OK;
+}

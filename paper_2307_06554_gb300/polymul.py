@@ -47,6 +47,11 @@ class polymul_plan_info(ctypes.Structure):
                  "digit_bits", "digits")] + [("reserved", ctypes.c_uint32 * 5)]
 
 
+class polymul_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("k", ctypes.c_uint32), ("prime_offset", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("offset", ctypes.c_uint64)]
+
+
 def library_path() -> str:
     """The in-tree build, or the file named by POLYMUL_LIB if set."""
     return os.environ.get("POLYMUL_LIB") or _build.LIB
@@ -70,6 +75,22 @@ def _load():
     lib.polymul_plan_info_get.restype = i32
     lib.polymul_destroy.argtypes = [vp]
     lib.polymul_destroy.restype = None
+    lib.polymul_ragged_create.argtypes = [ctypes.POINTER(u64), u32, u32, ctypes.POINTER(vp)]
+    lib.polymul_ragged_create.restype = i32
+    lib.polymul_ragged_prepare.argtypes = [vp, ctypes.POINTER(polymul_desc), u32, ctypes.POINTER(u32), u64, u64,
+                                           ctypes.POINTER(vp)]
+    lib.polymul_ragged_prepare.restype = i32
+    for name in ("polymul_ragged_run", "polymul_ragged_run_graph"):
+        getattr(lib, name).argtypes = [vp, vp, vp, vp, vp]
+        getattr(lib, name).restype = i32
+    lib.polymul_ragged_status.argtypes = [vp, vp]
+    lib.polymul_ragged_status.restype = i32
+    lib.polymul_ragged_batch_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u32)]
+    lib.polymul_ragged_batch_info.restype = i32
+    lib.polymul_ragged_batch_destroy.argtypes = [vp]
+    lib.polymul_ragged_batch_destroy.restype = None
+    lib.polymul_ragged_destroy.argtypes = [vp]
+    lib.polymul_ragged_destroy.restype = None
     lib.polymul_last_error.argtypes = []
     lib.polymul_last_error.restype = ctypes.c_char_p
     return lib
@@ -206,3 +227,86 @@ def _current_stream(x):
     except ImportError:  # pragma: no cover
         pass
     return 0
+
+
+# ---------------------------------------------------------------- uneven batches
+def polymul_ragged_create(pool: Sequence[int], n_max: int) -> int:
+    arr = (ctypes.c_uint64 * len(pool))(*[int(q) for q in pool])
+    out = ctypes.c_void_p()
+    _check(_lib.polymul_ragged_create(arr, len(pool), n_max, ctypes.byref(out)))
+    return out.value
+
+
+def polymul_ragged_prepare(ctx: int, descs: Sequence[tuple], prime_idx: Sequence[int], total_elems: int) -> int:
+    """descs: (n, k, prime_offset, offset) per product."""
+    d = (polymul_desc * max(1, len(descs)))(*[polymul_desc(n, k, po, 0, off) for (n, k, po, off) in descs])
+    pi = (ctypes.c_uint32 * max(1, len(prime_idx)))(*[int(x) for x in prime_idx])
+    out = ctypes.c_void_p()
+    _check(_lib.polymul_ragged_prepare(ctx, d, len(descs), pi, len(prime_idx), total_elems, ctypes.byref(out)))
+    return out.value
+
+
+def polymul_ragged_run(batch: int, a, b, c, stream=None) -> None:
+    _check(_lib.polymul_ragged_run(batch, _ptr(a), _ptr(b), _ptr(c), _stream(stream)))
+
+
+def polymul_ragged_run_graph(batch: int, a, b, c, stream=None) -> None:
+    _check(_lib.polymul_ragged_run_graph(batch, _ptr(a), _ptr(b), _ptr(c), _stream(stream)))
+
+
+def polymul_ragged_status(batch: int, stream=None) -> None:
+    _check(_lib.polymul_ragged_status(batch, _stream(stream)))
+
+
+def polymul_ragged_batch_info(batch: int) -> dict:
+    u, i, g = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint32()
+    _check(_lib.polymul_ragged_batch_info(batch, ctypes.byref(u), ctypes.byref(i), ctypes.byref(g)))
+    return {"units": u.value, "items": i.value, "grid": g.value}
+
+
+def polymul_ragged_batch_destroy(batch: int) -> None:
+    _lib.polymul_ragged_batch_destroy(batch)
+
+
+def polymul_ragged_destroy(ctx: int) -> None:
+    _lib.polymul_ragged_destroy(ctx)
+
+
+class Ragged:
+    """Owning wrapper for a prime pool plus one prepared list of products.
+
+    ``layout(products)`` assigns offsets; ``run(a, b, c)`` launches once."""
+
+    def __init__(self, pool: Sequence[int], n_max: int, products: Sequence[tuple]):
+        """products: (n, [pool indices]) per product, packed back to back."""
+        self.ctx = polymul_ragged_create(pool, n_max)
+        descs, prime_idx, off = [], [], 0
+        for n, idx in products:
+            descs.append((n, len(idx), len(prime_idx), off))
+            prime_idx.extend(idx)
+            off += n * len(idx)
+        self.total = off
+        self.offsets = [d[3] for d in descs]
+        try:
+            self.batch = polymul_ragged_prepare(self.ctx, descs, prime_idx, off)
+        except Exception:
+            polymul_ragged_destroy(self.ctx)
+            raise
+        self.info = polymul_ragged_batch_info(self.batch)
+
+    def run(self, a, b, c, stream=None, graph=False):
+        (polymul_ragged_run_graph if graph else polymul_ragged_run)(self.batch, a, b, c, stream)
+
+    def close(self):
+        if getattr(self, "batch", None):
+            polymul_ragged_batch_destroy(self.batch)
+            self.batch = None
+        if getattr(self, "ctx", None):
+            polymul_ragged_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

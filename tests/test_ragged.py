@@ -1,0 +1,110 @@
+"""Uneven batches in one persistent launch (and as a CUDA graph) against the
+CPU oracle: every product of small mixed lists, a sample of the 2000-product
+workload (n from 1024 to 16384, 1..16 primes), graph replay identical to
+the direct launch, and argument validation."""
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+from oracle import native
+from paper_2307_06554_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    from paper_2307_06554_gb300 import polymul
+    return polymul
+
+
+def _pack(rag):
+    total = sum(p.n * len(p.prime_idx) for p in rag.products)
+    a = np.empty(total, np.uint32)
+    b = np.empty(total, np.uint32)
+    off = 0
+    for p in rag.products:
+        m = p.n * len(p.prime_idx)
+        a[off:off + m] = p.a.reshape(-1)
+        b[off:off + m] = p.b.reshape(-1)
+        off += m
+    return a, b
+
+
+def _run(pm, rag, nmax=16384, graph=False):
+    import torch
+    a, b = _pack(rag)
+    with pm.Ragged(rag.pool, nmax, [(p.n, p.prime_idx) for p in rag.products]) as r:
+        ta = torch.from_numpy(a.view(np.int32)).cuda()
+        tb = torch.from_numpy(b.view(np.int32)).cuda()
+        tc = torch.full_like(ta, -1)
+        r.run(ta, tb, tc, graph=graph)
+        pm.polymul_ragged_status(r.batch)
+        offsets = list(r.offsets)
+        c = tc.cpu().numpy().view(np.uint32)
+    return c, offsets
+
+
+def _check(rag, c, offsets, which):
+    def one(i):
+        p = rag.products[i]
+        qs = [rag.pool[j] for j in p.prime_idx]
+        want = native.polymul_batch(p.a[None], p.b[None], qs, threads=1)[0]
+        got = c[offsets[i]:offsets[i] + p.n * len(qs)].reshape(len(qs), p.n).astype(np.uint64)
+        return i if not np.array_equal(got, want) else None
+    with ThreadPoolExecutor(max_workers=native.default_threads()) as ex:
+        bad = [i for i in ex.map(one, which) if i is not None]
+    assert not bad, "mismatching products: %s" % bad[:10]
+
+
+def test_small_mixed_every_product(pm):
+    rag = wl.ragged_2000(count=40, seed=41, degrees=(1024, 2048, 4096), kmax=4, pool_size=8)
+    c, off = _run(pm, rag)
+    _check(rag, c, off, range(len(rag.products)))
+
+
+def test_largest_degrees(pm):
+    rag = wl.ragged_2000(count=4, seed=42, degrees=(8192, 16384), kmax=2, pool_size=4)
+    c, off = _run(pm, rag)
+    _check(rag, c, off, range(len(rag.products)))
+
+
+def test_smaller_nmax_prefix_tables(pm):
+    """A pool built for n_max = 4096 serves 1024..4096 through table prefixes."""
+    rag = wl.ragged_2000(count=24, seed=43, degrees=(1024, 2048, 4096), kmax=3, pool_size=6)
+    c, off = _run(pm, rag, nmax=4096)
+    _check(rag, c, off, range(len(rag.products)))
+
+
+def test_ragged_2000_sampled_and_graph(pm):
+    rag = wl.ragged_2000()
+    c1, off = _run(pm, rag)
+    c2, _ = _run(pm, rag, graph=True)
+    assert np.array_equal(c1, c2)
+    small = [i for i, p in enumerate(rag.products) if p.n == 1024]
+    rng = np.random.default_rng(7)
+    large = [int(i) for i in rng.choice([i for i, p in enumerate(rag.products) if p.n > 1024], 8, replace=False)]
+    _check(rag, c1, off, small + large)
+
+
+def test_prepare_rejects_bad_descriptors(pm):
+    pool = wl.ragged_2000(count=1, pool_size=4).pool
+    ctx = pm.polymul_ragged_create(pool, 4096)
+    try:
+        bad = [
+            ([(512, 1, 0, 0)], [0], 512),        # n below 1024
+            ([(8192, 1, 0, 0)], [0], 8192),      # n above n_max
+            ([(1024, 2, 0, 0)], [0], 2048),      # prime list too short
+            ([(1024, 1, 0, 0)], [9], 1024),      # prime index outside the pool
+            ([(1024, 1, 0, 2)], [0], 4096),      # misaligned offset
+            ([(1024, 2, 0, 0)], [0, 1], 1500),   # rows outside the buffers
+        ]
+        for descs, idx, total in bad:
+            with pytest.raises(pm.PolymulError) as ei:
+                pm.polymul_ragged_prepare(ctx, descs, idx, total)
+            assert ei.value.code == pm.POLYMUL_EINVAL
+    finally:
+        pm.polymul_ragged_destroy(ctx)
+    with pytest.raises(pm.PolymulError):
+        pm.polymul_ragged_create([12289], 1024)  # 12289 - 1 is not divisible by 2048
