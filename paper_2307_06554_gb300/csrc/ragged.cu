@@ -41,9 +41,11 @@ struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
 
+// `phases`: one parity bit per team barrier (an item completes one phase on
+// the barriers of the teams it uses, and only on those)
 template <class S, int MODE>
 __device__ __forceinline__ bool ragged_item(const RaggedArgs& args, const RaggedItem& item, uint32_t* smem,
-                                            uint64_t* mbar, uint32_t parity) {
+                                            uint64_t* mbar, uint32_t& phases) {
   static_assert(S::T <= kRaggedThreads && S::T >= 32, "team size");
   constexpr int TEAMS = kRaggedThreads / S::T;
   static_assert(TEAMS <= kRaggedMaxTeams, "too many teams");
@@ -63,7 +65,8 @@ __device__ __forceinline__ bool ragged_item(const RaggedArgs& args, const Ragged
   }
   // a bounded wait; the team agrees on its outcome (barrier reduction) so
   // that its barriers stay uniform
-  uint32_t fail = mbar_wait(&mbar[team], parity) ? 0u : 1u;
+  uint32_t fail = mbar_wait(&mbar[team], (phases >> team) & 1u) ? 0u : 1u;
+  phases ^= (1u << TEAMS) - 1u;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 q, %1, 0;\n\t"
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs arg
   if (threadIdx.x < kRaggedMaxTeams) mbar_init(&mbar[threadIdx.x], 1);
   fence_mbar_init();
   __syncthreads();
-  uint32_t parity = 0;
+  uint32_t phases = 0;
   bool failed = false;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -107,14 +110,13 @@ __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs arg
     if (item.count == 0) break;
     bool ok = true;
     switch (item.logn) {
-      case 10: ok = ragged_item<RaggedShape<10>, MODE>(args, item, smem, mbar, parity); break;
-      case 11: ok = ragged_item<RaggedShape<11>, MODE>(args, item, smem, mbar, parity); break;
-      case 12: ok = ragged_item<RaggedShape<12>, MODE>(args, item, smem, mbar, parity); break;
-      case 13: ok = ragged_item<RaggedShape<13>, MODE>(args, item, smem, mbar, parity); break;
-      case 14: ok = ragged_item<RaggedShape<14>, MODE>(args, item, smem, mbar, parity); break;
+      case 10: ok = ragged_item<RaggedShape<10>, MODE>(args, item, smem, mbar, phases); break;
+      case 11: ok = ragged_item<RaggedShape<11>, MODE>(args, item, smem, mbar, phases); break;
+      case 12: ok = ragged_item<RaggedShape<12>, MODE>(args, item, smem, mbar, phases); break;
+      case 13: ok = ragged_item<RaggedShape<13>, MODE>(args, item, smem, mbar, phases); break;
+      case 14: ok = ragged_item<RaggedShape<14>, MODE>(args, item, smem, mbar, phases); break;
       default: break;
     }
-    parity ^= 1u;
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -122,7 +124,9 @@ __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs arg
   }
   if (failed) {
     if (threadIdx.x == 0) atomicExch(args.err, 1);
-    if (threadIdx.x < kRaggedMaxTeams) mbar_wait(&mbar[threadIdx.x], parity ^ 1u);
+    // let copies in flight land: a barrier whose current phase is pending
+    // completes it (parity bit = the phase being waited for)
+    if (threadIdx.x < kRaggedMaxTeams) mbar_wait(&mbar[threadIdx.x], ((phases >> threadIdx.x) & 1u) ^ 1u);
     return;
   }
   if (threadIdx.x == 0) {

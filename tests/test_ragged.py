@@ -70,6 +70,15 @@ def test_largest_degrees(pm):
     _check(rag, c, off, range(len(rag.products)))
 
 
+def test_items_of_different_team_counts_on_one_cta(pm):
+    """More work items than CTAs, one-team items (n = 16384) scheduled before
+    eight-team items (n = 1024): CTAs move between team layouts, and every
+    team barrier must keep its own phase.  Checks the n = 1024 products."""
+    rag = wl.ragged_2000(count=400, seed=44, degrees=(1024, 16384), kmax=2, pool_size=4)
+    c, off = _run(pm, rag)
+    _check(rag, c, off, [i for i, p in enumerate(rag.products) if p.n == 1024])
+
+
 def test_smaller_nmax_prefix_tables(pm):
     """A pool built for n_max = 4096 serves 1024..4096 through table prefixes."""
     rag = wl.ragged_2000(count=24, seed=43, degrees=(1024, 2048, 4096), kmax=3, pool_size=6)
