@@ -116,4 +116,4 @@ def test_prepare_rejects_bad_descriptors(pm):
     finally:
         pm.polymul_ragged_destroy(ctx)
     with pytest.raises(pm.PolymulError):
-        pm.polymul_ragged_create([12289], 1024)  # 12289 - 1 is not divisible by 2048
+        pm.polymul_ragged_create([3329], 1024)  # 3329 - 1 is not divisible by 2048
