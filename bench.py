@@ -60,6 +60,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU oracle sample budget")
+    p.add_argument("--no-extras", action="store_true", help="skip the other standing workloads")
     return p.parse_args()
 
 
@@ -190,6 +191,100 @@ def cpu_oracle_rate(w, seconds: float, max_products: int = None):
         if el >= seconds:
             break
     return done / el, threads, done, el
+
+
+def _ntt_mulmods(n: int) -> int:
+    """Modular multiplications of one NTT unit: two forward transforms, one
+    inverse, the pointwise product and the last-stage scaling."""
+    return 3 * (n // 2) * int(math.log2(n)) + n + n // 2
+
+
+def _time_steps(step, stream, reps):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(reps):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def other_workloads(dev, stream, peaks, alu_peak_g):
+    """Throughput of the other standing workloads (not the headline line):
+    n=256 q=3329 (auxiliary-prime NTT, launch-latency bound), n=4096 with 8
+    RNS primes and ternary b, and the 2000-product uneven list (one
+    persistent launch replayed as a CUDA graph)."""
+    import torch
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+    from oracle import native
+    out = {}
+    sp = stream.cuda_stream
+    hbm = peaks["hbm_gbs"]
+
+    def homogeneous(name, w, sets_needed, reps):
+        plan = polymul.Plan(w.n, w.q_list)
+        k = len(w.q_list)
+        elem = plan.elem_bytes
+        view = np.int32 if elem == 4 else np.int64
+        a0 = torch.from_numpy(w.a.view(view)).to(dev)
+        b0 = torch.from_numpy(w.b.view(view)).to(dev)
+        sets = [(a0.clone(), b0.clone(), torch.empty_like(a0)) for _ in range(sets_needed)]
+
+        def step(i):
+            a, b, c = sets[i % len(sets)]
+            polymul.polymul_batch(plan.handle, a, b, c, w.batch, sp)
+        for i in range(3):
+            step(i)
+        ms = _time_steps(step, stream, reps)
+        idx = [0, w.batch - 1]
+        got = sets[(reps - 1) % len(sets)][2][idx].cpu().numpy().view(w.a.dtype).astype(np.uint64)
+        ok = bool(np.array_equal(got, native.polymul_batch(w.a[idx], w.b[idx], w.q_list)))
+        units = w.batch * k
+        mm = units * _ntt_mulmods(w.n)
+        byts = 3 * units * w.n * elem
+        out[name] = {"products_per_s": w.batch / (ms / 1e3), "us_per_step": ms * 1e3, "batch": w.batch,
+                     "n": w.n, "k": k, "path": "ntt" + (" (auxiliary prime)" if plan.info["aux_primes"] else ""),
+                     "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm,
+                     "bit_exact_sample": ok,
+                     "l2": "inputs rotated over %d buffer sets" % len(sets) if len(sets) > 1 else "L2-resident"}
+        plan.close()
+
+    homogeneous("ring_small", wl.ring_small(), 1, 200)
+    homogeneous("rns_4096", wl.rns_4096(), 6, 20)
+
+    rag = wl.ragged_2000()
+    total = sum(p.n * len(p.prime_idx) for p in rag.products)
+    ah = np.empty(total, np.uint32)
+    bh = np.empty(total, np.uint32)
+    off = 0
+    for p in rag.products:
+        m = p.n * len(p.prime_idx)
+        ah[off:off + m] = p.a.reshape(-1)
+        bh[off:off + m] = p.b.reshape(-1)
+        off += m
+    with polymul.Ragged(rag.pool, 16384, [(p.n, p.prime_idx) for p in rag.products]) as r:
+        ta = torch.from_numpy(ah.view(np.int32)).to(dev)
+        tb = torch.from_numpy(bh.view(np.int32)).to(dev)
+        tc = torch.empty_like(ta)
+        for _ in range(2):
+            r.run(ta, tb, tc, stream=sp, graph=True)
+        ms = _time_steps(lambda i: r.run(ta, tb, tc, stream=sp, graph=True), stream, 10)
+        polymul.polymul_ragged_status(r.batch, sp)
+        p0 = rag.products[0]
+        qs = [rag.pool[j] for j in p0.prime_idx]
+        got = tc[:p0.n * len(qs)].cpu().numpy().view(np.uint32).reshape(len(qs), p0.n).astype(np.uint64)
+        ok = bool(np.array_equal(got, native.polymul_batch(p0.a[None], p0.b[None], qs)[0]))
+        mm = sum(len(p.prime_idx) * _ntt_mulmods(p.n) for p in rag.products)
+        out["ragged_2000"] = {"products_per_s": len(rag.products) / (ms / 1e3), "us_per_launch": ms * 1e3,
+                              "units": r.info["units"], "work_items": r.info["items"], "grid": r.info["grid"],
+                              "path": "ntt, one persistent launch replayed as a CUDA graph",
+                              "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g,
+                              "hbm_frac": 3 * total * 4 / (ms / 1e3) / 1e9 / hbm,
+                              "bit_exact_sample": ok, "l2": "inputs 1.3 GB (> L2)"}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -349,7 +444,7 @@ def run_ours(args, ws, rank, local):
     peaks, peak_src = _peaks()
     launch_ms = statistics.mean(per)
     units = batch * len(q_list)
-    mulmods = units * (3 * (n // 2) * int(math.log2(n)) + n + n // 2)
+    mulmods = units * _ntt_mulmods(n)
     bytes_alg = 3 * units * n * elem
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -378,6 +473,10 @@ def run_ours(args, ws, rank, local):
                               "peak_source": "MEASURED_PEAKS.json bf16_tflops burst (%s)" % peak_src}
         tensor["vs_ntt"] = tensor["value"] / value
 
+    extras = None
+    if not args.no_extras:
+        extras = other_workloads(dev, stream, peaks, alu_peak)
+
     cpu = None
     if not args.no_cpu_baseline:
         rate, cores, done, el = cpu_oracle_rate(w, args.cpu_seconds)
@@ -401,6 +500,7 @@ def run_ours(args, ws, rank, local):
         "clocks": clk,
         "bit_exact_sample": bit_exact,
         "tensor_path": tensor,
+        "other_workloads": extras,
     }
     print(json.dumps(out), flush=True)
     plan.close()
