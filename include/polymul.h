@@ -134,6 +134,34 @@ int polymul_batch_host(polymul_plan *plan, const void *a, const void *b, void *c
  */
 int polymul_plan_status(polymul_plan *plan, void *stream);
 
+/*
+ * polymul_batch_static -- c = a*b in Z_q[x]/(x^n+1) for `batch` products of
+ * one prime modulus, WITHOUT any device allocation.  (Not an operation of
+ * the paper: it has no counterpart there.  It is polymul_batch's NTT kernel
+ * run from library-owned fixed memory.)
+ *
+ * For callers that cannot allocate device memory: code running while any
+ * thread of the process captures a CUDA graph in global capture mode (where
+ * cudaMalloc/cudaFree are not permitted), latency-critical code that cannot
+ * take the device-wide synchronisation of an allocation, and hosts whose
+ * memory manager owns all device memory.  polymul_create allocates tables,
+ * so these callers cannot hold a plan; this call needs none.
+ *   n      power of two, 16 <= n <= 4096 (the fixed memory's limit).
+ *   q      prime, q < 2^31, 2n | q - 1 (an NTT-friendly modulus).
+ *   a,b,c  device pointers, [batch][n] uint32_t, 16-byte aligned, canonical
+ *          inputs; the caller owns and provides them.
+ * The library keeps the twiddle tables, constants and the kernel's work
+ * counter in one fixed device array (64 KiB + 64 bytes) that every GPU using
+ * the library holds until the process exits.  Every call shares that array:
+ * calls whose kernels may overlap on the GPU race (issue them on one stream
+ * or order them with events); tables are refreshed only when (n, q) changes,
+ * and the work counter is cleared on every call.  The first call on a device
+ * looks up the array's device address; make it before any stream capture.
+ * Asynchronous like polymul_batch.  Errors: EINVAL, ENOTSUP, ECUDA.
+ */
+int polymul_batch_static(uint32_t n, uint64_t q, const void *a, const void *b, void *c,
+                         uint64_t batch, void *stream);
+
 /* Fill *info with the plan's shape and launch configuration. */
 int polymul_plan_info_get(const polymul_plan *plan, polymul_plan_info *info);
 

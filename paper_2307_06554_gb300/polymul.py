@@ -69,6 +69,8 @@ def _load():
     lib.polymul_batch.restype = i32
     lib.polymul_batch_host.argtypes = [vp, vp, vp, vp, u64, vp]
     lib.polymul_batch_host.restype = i32
+    lib.polymul_batch_static.argtypes = [u32, u64, vp, vp, vp, u64, vp]
+    lib.polymul_batch_static.restype = i32
     lib.polymul_plan_status.argtypes = [vp, vp]
     lib.polymul_plan_status.restype = i32
     lib.polymul_plan_info_get.argtypes = [vp, ctypes.POINTER(polymul_plan_info)]
@@ -147,6 +149,11 @@ def polymul_batch(plan: int, a, b, c, batch: int, stream=None) -> None:
 
 def polymul_batch_host(plan: int, a, b, c, batch: int, stream=None) -> None:
     _check(_lib.polymul_batch_host(plan, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
+
+
+def polymul_batch_static(n: int, q: int, a, b, c, batch: int, stream=None) -> None:
+    """Allocation-free entry point (one NTT-friendly prime, n <= 4096)."""
+    _check(_lib.polymul_batch_static(n, q, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
 
 
 def polymul_plan_status(plan: int, stream=None) -> None:
