@@ -131,6 +131,11 @@ int upload_tensor_tables(polymul_plan* p) {
 }
 
 bool lookup_ntt(uint32_t elem, int logn, int mode, KernelInfo* ki) {
+  if (logn >= 14) {
+    // beyond one CTA: one product per thread-block cluster; the unreduced
+    // mode falls back to Harvey's bounds where it is not instantiated
+    return lookup_ntt_cluster(elem, logn, mode, ki) || (mode == 2 && lookup_ntt_cluster(elem, logn, 1, ki));
+  }
   if (elem == 4) {
     if (mode == 0) return lookup_ntt_u32_m0(logn, ki);
     if (mode == 1) return lookup_ntt_u32_m1(logn, ki);
@@ -148,6 +153,26 @@ int configure_launch(polymul_plan* p) {
     PM_CUDA(cudaFuncSetAttribute(p->ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ki.smem));
   PM_CUDA(cudaFuncSetAttribute(p->ki.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int per_sm = 0;
+  if (p->ki.cluster > 0) {
+    // resident clusters: the persistent grid is that many clusters
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = p->ki.cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(p->ki.cluster * p->num_sms);
+    cfg.blockDim = dim3(p->ki.block);
+    cfg.dynamicSmemBytes = p->ki.smem;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    PM_CUDA(cudaOccupancyMaxActiveClusters(&clusters, p->ki.fn, &cfg));
+    if (clusters < 1) return fail(POLYMUL_ENOTSUP, "no %d-CTA cluster fits on the device", p->ki.cluster);
+    p->grid_cap = clusters * p->ki.cluster;
+    return POLYMUL_OK;
+  }
   if (p->ki.tmem_cols > 0) {
     // The occupancy query reports one CTA per SM for kernels that allocate
     // tensor memory; co-residency is in fact limited by shared memory,
@@ -338,7 +363,32 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     if (h) return fail(POLYMUL_EDOMAIN, "an input coefficient is not below its modulus");
   }
   const uint64_t need = (units + p->ki.units_per_cta - 1) / p->ki.units_per_cta;
-  const int grid = (int)std::min<uint64_t>(need, (uint64_t)p->grid_cap);
+  int grid = (int)std::min<uint64_t>(need, (uint64_t)p->grid_cap);
+  if (p->ki.cluster > 0) {
+    const uint64_t clusters = std::min<uint64_t>(units, (uint64_t)(p->grid_cap / p->ki.cluster));
+    grid = (int)(clusters * p->ki.cluster);
+  }
+  auto launch = [&](void** argv) -> int {
+    if (p->ki.cluster > 0) {
+      cudaLaunchConfig_t cfg;
+      memset(&cfg, 0, sizeof cfg);
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = p->ki.cluster;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(p->ki.block);
+      cfg.dynamicSmemBytes = p->ki.smem;
+      cfg.stream = st;
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      PM_CUDA(cudaLaunchKernelExC(&cfg, p->ki.fn, argv));
+    } else {
+      PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
+    }
+    return POLYMUL_OK;
+  };
   if (p->path == POLYMUL_PATH_TENSOR) {
     TensorBatchArgs args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, (const TensorPrime*)p->d_pc,
                          units, p->k, ctr, p->d_err};
@@ -349,13 +399,13 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
                                 (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err,
                                 (const uint32_t*)p->d_outer};
     void* argv[] = {&args};
-    PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
+    return launch(argv);
   } else {
     NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
                                 (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err,
                                 (const uint64_t*)p->d_outer};
     void* argv[] = {&args};
-    PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
+    return launch(argv);
   }
   return POLYMUL_OK;
 }

@@ -12,6 +12,7 @@ struct KernelInfo {
   int team = 0;              // threads per unit
   int units_per_cta = 0;     // units a CTA processes per iteration
   int tmem_cols = 0;         // tensor-memory columns allocated per CTA (0: none)
+  int cluster = 0;           // CTAs per thread-block cluster (0: no cluster launch)
 };
 
 // batched negacyclic NTT, k_ntt_batch<W, LOGN, MODE> (MODE: 0 = kQ31,
@@ -22,6 +23,9 @@ bool lookup_ntt_u32_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
 bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_aux(int logn, KernelInfo* ki);  // auxiliary-prime mode, logn 4..14
+
+// one product per thread-block cluster (n = 2^14 .. 2^16)
+bool lookup_ntt_cluster(uint32_t elem, int logn, int mode, KernelInfo* ki);
 
 // uneven batches in one persistent launch (32-bit words, n = 2^10..2^14)
 bool lookup_ntt_ragged(int mode, KernelInfo* ki);

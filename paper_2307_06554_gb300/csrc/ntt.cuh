@@ -293,8 +293,26 @@ __device__ __forceinline__ void load_layout(W (&x)[S::R], const W* s, uint32_t t
   });
 }
 
-template <class S, int MODE, int P, class Sync, typename W = typename S::W>
-__device__ __forceinline__ void fwd_from(W (&xa)[S::R], W (&xb)[S::R], W* sa, W* sb,
+// Exchange buffers may also be spread over the CTAs of a cluster: any type
+// with store(j, v) / load(j) and kCluster = true (see ntt_cluster.cu).
+template <class S, int P, class CB, typename W = typename S::W, bool = CB::kCluster>
+__device__ __forceinline__ void store_layout(const W (&x)[S::R], const CB& s, uint32_t t) {
+  sfor<0, S::R>([&](auto ec) {
+    constexpr int e = decltype(ec)::value;
+    s.store(elem_index<S, P>(e, t), x[e]);
+  });
+}
+
+template <class S, int P, class CB, typename W = typename S::W, bool = CB::kCluster>
+__device__ __forceinline__ void load_layout(W (&x)[S::R], const CB& s, uint32_t t) {
+  sfor<0, S::R>([&](auto ec) {
+    constexpr int e = decltype(ec)::value;
+    x[e] = s.load(elem_index<S, P>(e, t));
+  });
+}
+
+template <class S, int MODE, int P, class Sync, class B, typename W = typename S::W>
+__device__ __forceinline__ void fwd_from(W (&xa)[S::R], W (&xb)[S::R], B sa, B sb,
                                          const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
                                          uint32_t t, Sync sync) {
   fwd_phase2<S, MODE, P>(xa, xb, tw, pc, t);
@@ -312,8 +330,8 @@ __device__ __forceinline__ void fwd_from(W (&xa)[S::R], W (&xb)[S::R], W* sa, W*
 // `hook` runs once the team has finished reading the exchange buffers for
 // the last time in this unit (after the last exchange), so that the buffers
 // can receive the next unit's operands.
-template <class S, int MODE, int P, class Sync, class Hook, typename W = typename S::W>
-__device__ __forceinline__ void inv_from(W (&x)[S::R], W* s, const TwPair<W>* __restrict__ tw,
+template <class S, int MODE, int P, class Sync, class Hook, class B, typename W = typename S::W>
+__device__ __forceinline__ void inv_from(W (&x)[S::R], B s, const TwPair<W>* __restrict__ tw,
                                          const PrimeConst<W>& pc, uint32_t t, Sync sync, Hook&& hook) {
   inv_phase<S, MODE, P>(x, tw, pc, t);
   if constexpr (P + 1 < S::NPH) {
