@@ -73,7 +73,8 @@ def test_u64_cluster_degrees(pm, logn):
 def test_u32_cluster_degrees(pm, logn, bits):
     n = 1 << logn
     rng = np.random.default_rng(logn * 3 + bits)
-    q_list = wl.draw_primes(rng, 2, bits, bits, 17)
+    # 17 bits: 65537 = 2^16 + 1 (the unreduced small-modulus mode)
+    q_list = [65537] if bits == 17 else wl.draw_primes(rng, 2, bits, bits, 17)
     a = wl.uniform_coeffs(rng, 3, q_list, n, np.uint32)
     b = wl.uniform_coeffs(rng, 3, q_list, n, np.uint32)
     with pm.Plan(n, q_list) as plan:
