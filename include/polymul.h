@@ -226,6 +226,54 @@ int polymul_ragged_batch_info(const polymul_ragged_batch *batch, uint64_t *units
 void polymul_ragged_batch_destroy(polymul_ragged_batch *batch); /* NULL-safe */
 void polymul_ragged_destroy(polymul_ragged *ctx);               /* NULL-safe */
 
+/* ------------------------------------------------------------------------
+ * Serving: a continuously batching request loop.  Requests are products of
+ * any degree n <= n_max with their own subset of a prime pool (64-bit
+ * words, each prime < 2^62 with 2 n_max | q - 1), operands in HOST memory.
+ * A server thread admits queued requests in arrival order as soon as device
+ * memory (an arena of `device_bytes`) and an in-flight slot free up, runs
+ * each on one of `lanes` streams (copy in, kernel, copy out) so that work of
+ * different requests overlaps on the device, and retires finished ones.
+ * Twiddle tables of the whole pool stay resident (Sec. 4, "fine-tuning the
+ * design" (i)); copies overlap computation (Sec. 4 (ii)).
+ * ---------------------------------------------------------------------- */
+typedef struct polymul_server polymul_server;
+
+typedef struct polymul_request {
+    uint32_t n;                  /* degree, power of two, 16 <= n <= n_max */
+    uint32_t k;                  /* number of primes (>= 1)                */
+    const uint32_t *prime_idx;   /* k pool indices (read during submit)     */
+    const void *a;               /* host [k][n] uint64_t operands; must stay */
+    const void *b;               /*   valid until the request completes;    */
+    void *c;                     /*   page-locked memory overlaps copies     */
+} polymul_request;
+
+typedef struct polymul_server_stats {
+    uint64_t submitted, completed, failed, queued, in_flight;
+    uint64_t arena_bytes, arena_peak_bytes;
+    double p50_us, p99_us, mean_us, max_us; /* submit -> completion latency */
+} polymul_server_stats;
+
+/* Start a server on the current device.  Errors: EINVAL, ENOMEM, ENOTSUP. */
+int polymul_server_create(const uint64_t *pool, uint32_t pool_size, uint32_t n_max,
+                          uint64_t device_bytes, uint32_t lanes, polymul_server **out);
+/* Queue one request (asynchronous); *ticket identifies it. */
+int polymul_server_submit(polymul_server *srv, const polymul_request *req, uint64_t *ticket);
+/* *done = 1 once the result is in req->c (the ticket is then released). */
+int polymul_server_poll(polymul_server *srv, uint64_t ticket, int *done);
+/* Block until the request completes; ETIMEOUT after timeout_s seconds. */
+int polymul_server_wait(polymul_server *srv, uint64_t ticket, double timeout_s);
+/* Load generator: submit reqs[i] at arrival_s[i] seconds after the call,
+ * wait for all, and store each submit-to-completion latency (microseconds)
+ * in latency_us (may be NULL). */
+int polymul_server_replay(polymul_server *srv, const polymul_request *reqs, uint32_t count,
+                          const double *arrival_s, double *latency_us);
+/* Counters and latency percentiles of completed requests; reset != 0
+ * clears them afterwards. */
+int polymul_server_stats_get(polymul_server *srv, polymul_server_stats *out, int reset);
+/* Stop the loop (finishing work in flight) and free everything.  NULL-safe. */
+void polymul_server_destroy(polymul_server *srv);
+
 /* Message for the calling thread's most recent failing call ("" if none).
  * The pointer stays valid until the next call from the same thread. */
 const char *polymul_last_error(void);

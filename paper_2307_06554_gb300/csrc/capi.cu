@@ -397,13 +397,13 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
   } else if (p->elem == 4) {
     NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
                                 (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err,
-                                (const uint32_t*)p->d_outer};
+                                (const uint32_t*)p->d_outer, nullptr, p->n, 1, 0};
     void* argv[] = {&args};
     return launch(argv);
   } else {
     NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
                                 (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err,
-                                (const uint64_t*)p->d_outer};
+                                (const uint64_t*)p->d_outer, nullptr, p->n, 1, 0};
     void* argv[] = {&args};
     return launch(argv);
   }

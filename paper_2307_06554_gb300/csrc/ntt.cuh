@@ -493,16 +493,16 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       const uint64_t u = cur + team;
       const bool act = u < units;
       const uint32_t j = act ? (uint32_t)(u % k) : 0u;
-      const PrimeConst<W> pc = args.pc[AUX ? 0 : j];
+      const uint32_t pj = AUX ? 0u : (args.pmap ? args.pmap[j] : j);
+      const PrimeConst<W> pc = args.pc[(size_t)pj * args.pc_stride + args.pc_off];
       const W qo = AUX ? args.outer_q[j] : W(0);
       unsigned long long nxt = units;
       auto hook = [&]() {
         nxt = grab();
         if (lane == 0 && nxt < units) issue(nxt);
       };
-      const uint32_t tj = AUX ? 0u : j;
-      polymul_unit<S, MODE, AUX>(args.c + (act ? (size_t)u * S::N : 0), twf + (size_t)tj * S::N,
-                                 twi + (size_t)tj * S::N, pc, sa, sb, t, act, WarpSync{}, hook, qo);
+      polymul_unit<S, MODE, AUX>(args.c + (act ? (size_t)u * S::N : 0), twf + (size_t)pj * args.tw_stride,
+                                 twi + (size_t)pj * args.tw_stride, pc, sa, sb, t, act, WarpSync{}, hook, qo);
       cur = nxt;
     }
     if (lane == 0) {
@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       }
       parity ^= 1u;
       const uint32_t j = (uint32_t)(cur % k);
-      const uint32_t tj = AUX ? 0u : j;
-      const PrimeConst<W> pc = args.pc[tj];
+      const uint32_t pj = AUX ? 0u : (args.pmap ? args.pmap[j] : j);
+      const PrimeConst<W> pc = args.pc[(size_t)pj * args.pc_stride + args.pc_off];
       const W qo = AUX ? args.outer_q[j] : W(0);
       auto hook = [&]() {  // called after a barrier: every thread is done with sa/sb
         if (threadIdx.x == 0) {
@@ -551,8 +551,9 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
           if (s_next < units) issue(s_next);
         }
       };
-      polymul_unit<S, MODE, AUX>(args.c + (size_t)cur * S::N, twf + (size_t)tj * S::N,
-                                 twi + (size_t)tj * S::N, pc, sa, sb, threadIdx.x, true, BlockSync{}, hook, qo);
+      polymul_unit<S, MODE, AUX>(args.c + (size_t)cur * S::N, twf + (size_t)pj * args.tw_stride,
+                                 twi + (size_t)pj * args.tw_stride, pc, sa, sb, threadIdx.x, true, BlockSync{}, hook,
+                                 qo);
       __syncthreads();
       cur = s_next;
     }

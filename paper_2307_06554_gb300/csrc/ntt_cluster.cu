@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_ntt_cluster(NttBatchArgs
   const TwPair<W>* twi = reinterpret_cast<const TwPair<W>*>(args.tw_inv);
   for (uint64_t u = cluster_id(); u < args.units; u += cluster_count()) {
     const uint32_t j = (uint32_t)(u % args.k);
-    const PrimeConst<W> pc = args.pc[j];
+    const uint32_t pj = args.pmap ? args.pmap[j] : j;
+    const PrimeConst<W> pc = args.pc[(size_t)pj * args.pc_stride + args.pc_off];
     const W* a = args.a + (size_t)u * S::N;
     const W* b = args.b + (size_t)u * S::N;
     W xa[S::R], xb[S::R];
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_ntt_cluster(NttBatchArgs
       xa[e] = a[i];
       xb[e] = b[i];
     });
-    fwd_from<S, MODE, TOP>(xa, xb, sa, sb, twf + (size_t)j * S::N, pc, t, ClusterSync{});
+    fwd_from<S, MODE, TOP>(xa, xb, sa, sb, twf + (size_t)pj * args.tw_stride, pc, t, ClusterSync{});
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;
       if constexpr (MODE == kSmall) {
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_ntt_cluster(NttBatchArgs
         xa[e] = montmul(csub(xa[e], pc.q), csub(xb[e], pc.q), pc.q, pc.qinv);
       }
     });
-    inv_from<S, MODE, 0>(xa, sa, twi + (size_t)j * S::N, pc, t, ClusterSync{}, NoHookC{});
+    inv_from<S, MODE, 0>(xa, sa, twi + (size_t)pj * args.tw_stride, pc, t, ClusterSync{}, NoHookC{});
     W* c = args.c + (size_t)u * S::N;
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;

@@ -30,6 +30,15 @@ struct NttBatchArgs {
   unsigned long long* ctr;  // {next unit, finished teams}, zero between launches
   int* err;                 // set to 1 when a bounded device wait expires
   const W* outer_q;         // auxiliary-prime mode: the ring moduli [k]
+  // Table selection: unit prime j uses tables of prime pj = pmap ? pmap[j] : j,
+  // twiddles at tw_fwd/tw_inv + pj * tw_stride pairs and constants
+  // pc[pj * pc_stride + pc_off].  A plan passes (null, n, 1, 0); a server whose
+  // tables cover a prime pool at the largest degree passes the request's pool
+  // indices, that degree and the per-degree constant slot.
+  const uint32_t* pmap;
+  uint32_t tw_stride;
+  uint32_t pc_stride;
+  uint32_t pc_off;
 };
 
 // Ragged (uneven) batches: one unit = one (product, prime) row of n words.

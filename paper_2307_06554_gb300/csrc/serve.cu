@@ -1,0 +1,550 @@
+// Serving: a continuously batching request loop for mixed-size negacyclic
+// products (polymul_server_*, see include/polymul.h).
+//
+// State kept resident for the server's lifetime (the paper's advice to keep
+// prepared operands loaded rather than rebuild them per product, Sec. 4,
+// "fine-tuning the design" (i)): forward and inverse twiddle tables of every
+// pool prime at the largest degree (a product of degree n reads the length-n
+// prefix), and the per-degree constants.
+//
+// Requests carry host operands.  A server thread owns the device: it admits
+// queued requests in arrival order as soon as device memory (a first-fit
+// arena) and an in-flight slot are free, issues each one on one of several
+// stream lanes -- copy in, one kernel over the request's (prime) units, copy
+// out, completion event -- and retires requests whose event has fired,
+// releasing their memory to the next admissions.  Work of different requests
+// overlaps on the device (lanes are independent streams), and copies of one
+// request overlap kernels of others (Sec. 4, "optimizing computation and
+// I/O" (ii)).  Latency is taken from submission to the moment the server
+// observes completion.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/polymul.h"
+#include "host_math.h"
+#include "kernels.h"
+#include "plan.h"
+#include "polymul_types.h"
+
+using namespace pm;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
+
+constexpr int kServeMaxLog = 16;
+constexpr size_t kArenaAlign = 256;
+
+struct ServeReq {
+  uint64_t ticket = 0;
+  uint32_t n = 0, k = 0, logn = 0;
+  std::vector<uint32_t> primes;
+  const void* ha = nullptr;
+  const void* hb = nullptr;
+  void* hc = nullptr;
+  double t_submit = 0, t_done = 0;
+  int state = 0;  // 0 queued, 1 in flight, 2 done, 3 failed
+  size_t off = 0, bytes = 0;
+  int lane = 0;
+  cudaEvent_t ev = nullptr;
+};
+
+}  // namespace
+
+struct polymul_server {
+  uint32_t nmax = 0, lognmax = 0;
+  std::vector<uint64_t> pool;
+  void* d_twf = nullptr;
+  void* d_twi = nullptr;
+  void* d_pc = nullptr;  // PrimeConst<uint64_t>[pool][17]
+  KernelInfo ki[kServeMaxLog + 1];
+  int grid_cap[kServeMaxLog + 1] = {};
+  int device = 0, num_sms = 0;
+  int nlanes = 0;
+  std::vector<cudaStream_t> lanes;
+  unsigned long long* d_ctr = nullptr;  // 2 per lane
+  int* d_err = nullptr;
+  char* d_arena = nullptr;
+  size_t arena_bytes = 0, arena_used = 0, arena_peak = 0;
+  std::map<size_t, size_t> free_list;  // offset -> size
+  size_t max_inflight = 64;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<ServeReq*> queue;
+  std::vector<ServeReq*> inflight;
+  std::unordered_map<uint64_t, ServeReq*> reqs;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<double> latencies_us;
+  uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0;
+  int next_lane = 0;
+  std::atomic<bool> stop{false};
+  std::thread loop;
+  int cuda_error = 0;
+  std::string cuda_error_msg;
+};
+
+namespace {
+
+size_t arena_alloc(polymul_server* s, size_t bytes) {
+  bytes = (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+  for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
+    if (it->second >= bytes) {
+      const size_t off = it->first, rest = it->second - bytes;
+      s->free_list.erase(it);
+      if (rest) s->free_list[off + bytes] = rest;
+      s->arena_used += bytes;
+      s->arena_peak = std::max(s->arena_peak, s->arena_used);
+      return off;
+    }
+  }
+  return (size_t)-1;
+}
+
+void arena_free(polymul_server* s, size_t off, size_t bytes) {
+  bytes = (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+  s->arena_used -= bytes;
+  auto it = s->free_list.emplace(off, bytes).first;
+  auto next = std::next(it);
+  if (next != s->free_list.end() && it->first + it->second == next->first) {
+    it->second += next->second;
+    s->free_list.erase(next);
+  }
+  if (it != s->free_list.begin()) {
+    auto prev = std::prev(it);
+    if (prev->first + prev->second == it->first) {
+      prev->second += it->second;
+      s->free_list.erase(it);
+    }
+  }
+}
+
+size_t request_bytes(uint32_t n, uint32_t k) {
+  const size_t row = (size_t)k * n * 8;
+  const size_t map = ((size_t)k * 4 + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+  return 3 * ((row + kArenaAlign - 1) / kArenaAlign * kArenaAlign) + map;
+}
+
+// issue copy-in, kernel, copy-out and the completion event (lock held)
+cudaError_t issue(polymul_server* s, ServeReq* r) {
+  const size_t row = (size_t)r->k * r->n * 8;
+  const size_t rowa = (row + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+  char* base = s->d_arena + r->off;
+  uint64_t* da = reinterpret_cast<uint64_t*>(base);
+  uint64_t* db = reinterpret_cast<uint64_t*>(base + rowa);
+  uint64_t* dc = reinterpret_cast<uint64_t*>(base + 2 * rowa);
+  uint32_t* dmap = reinterpret_cast<uint32_t*>(base + 3 * rowa);
+  cudaStream_t st = s->lanes[r->lane];
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(dmap, r->primes.data(), r->k * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(da, r->ha, row, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(db, r->hb, row, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  const KernelInfo& ki = s->ki[r->logn];
+  NttBatchArgs<uint64_t> args{da,      db,       dc,      s->d_twf, s->d_twi, (const PrimeConst<uint64_t>*)s->d_pc,
+                              r->k,    r->k,     s->d_ctr + 2 * r->lane, s->d_err, nullptr, dmap,
+                              s->nmax, (uint32_t)(kServeMaxLog + 1), r->logn};
+  void* argv[] = {&args};
+  if (ki.cluster > 0) {
+    const int clusters = std::min<int>((int)r->k, s->grid_cap[r->logn] / ki.cluster);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = ki.cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(clusters * ki.cluster);
+    cfg.blockDim = dim3(ki.block);
+    cfg.dynamicSmemBytes = ki.smem;
+    cfg.stream = st;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelExC(&cfg, ki.fn, argv)) != cudaSuccess) return e;
+  } else {
+    const int grid = std::min<int>((int)((r->k + ki.units_per_cta - 1) / ki.units_per_cta), s->grid_cap[r->logn]);
+    if ((e = cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st)) != cudaSuccess) return e;
+  }
+  if ((e = cudaMemcpyAsync(r->hc, dc, row, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  return cudaEventRecord(r->ev, st);
+}
+
+void server_loop(polymul_server* s) {
+  cudaSetDevice(s->device);
+  while (!s->stop.load()) {
+    bool progress = false;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      // retire completed requests
+      for (size_t i = 0; i < s->inflight.size();) {
+        ServeReq* r = s->inflight[i];
+        const cudaError_t q = cudaEventQuery(r->ev);
+        if (q == cudaErrorNotReady) {
+          ++i;
+          continue;
+        }
+        r->t_done = now_s();
+        r->state = q == cudaSuccess ? 2 : 3;
+        if (q != cudaSuccess) {
+          s->cuda_error = 1;
+          s->cuda_error_msg = cudaGetErrorString(q);
+          ++s->failed;
+        } else {
+          s->latencies_us.push_back((r->t_done - r->t_submit) * 1e6);
+          ++s->completed;
+        }
+        arena_free(s, r->off, r->bytes);
+        s->event_pool.push_back(r->ev);
+        r->ev = nullptr;
+        s->inflight[i] = s->inflight.back();
+        s->inflight.pop_back();
+        progress = true;
+      }
+      // admit in arrival order while memory and slots allow
+      while (!s->queue.empty() && s->inflight.size() < s->max_inflight) {
+        ServeReq* r = s->queue.front();
+        const size_t off = arena_alloc(s, r->bytes);
+        if (off == (size_t)-1) break;
+        r->off = off;
+        r->lane = s->next_lane;
+        s->next_lane = (s->next_lane + 1) % s->nlanes;
+        if (s->event_pool.empty()) {
+          cudaEvent_t ev;
+          cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+          s->event_pool.push_back(ev);
+        }
+        r->ev = s->event_pool.back();
+        s->event_pool.pop_back();
+        const cudaError_t e = issue(s, r);
+        s->queue.pop_front();
+        if (e != cudaSuccess) {
+          s->cuda_error = 1;
+          s->cuda_error_msg = cudaGetErrorString(e);
+          r->state = 3;
+          r->t_done = now_s();
+          ++s->failed;
+          arena_free(s, r->off, r->bytes);
+          s->event_pool.push_back(r->ev);
+          r->ev = nullptr;
+        } else {
+          r->state = 1;
+          s->inflight.push_back(r);
+        }
+        progress = true;
+      }
+      if (progress) s->cv.notify_all();
+      if (!progress && s->inflight.empty() && s->queue.empty()) {
+        s->cv.wait_for(lock, std::chrono::milliseconds(1));
+        continue;
+      }
+    }
+    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(5));
+  }
+}
+
+void build_serve_prime(uint64_t q, uint32_t nmax, std::vector<uint64_t>& twf, std::vector<uint64_t>& twi,
+                       PrimeConst<uint64_t>* pc17) {
+  using namespace pm::host;
+  const int lognmax = __builtin_ctz(nmax);
+  const uint64_t psi = primitive_2n_root(q, nmax);
+  const uint64_t psi_inv = powmod(psi, q - 2, q);
+  for (uint32_t i = 0; i < nmax; ++i) {
+    const uint32_t r = bitrev(i, lognmax);
+    const uint64_t w = powmod(psi, r, q), v = powmod(psi_inv, r, q);
+    twf.push_back(w);
+    twf.push_back(shoup_companion(w, q, 64));
+    twi.push_back(v);
+    twi.push_back(shoup_companion(v, q, 64));
+  }
+  const uint64_t v1 = powmod(psi_inv, bitrev(1, lognmax), q);
+  const uint64_t r_mod_q = (uint64_t)(((u128)1 << 64) % q);
+  for (int logn = 0; logn <= kServeMaxLog; ++logn) {
+    PrimeConst<uint64_t>& c = pc17[logn];
+    memset(&c, 0, sizeof c);
+    if (logn > lognmax) continue;
+    const uint64_t scale = mulmod(powmod(1ull << logn, q - 2, q), r_mod_q, q);
+    const uint64_t scale_w = mulmod(v1, scale, q);
+    c.q = q;
+    c.q2 = 2 * q;
+    c.qinv = inv_pow2_64(q);
+    c.scale = scale;
+    c.scale_p = shoup_companion(scale, q, 64);
+    c.scale_w = scale_w;
+    c.scale_wp = shoup_companion(scale_w, q, 64);
+  }
+}
+
+}  // namespace
+
+#define PM_CUDA(call)                                       \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return pm::cuda_fail(e_, #call); \
+  } while (0)
+
+extern "C" void polymul_server_destroy(polymul_server* s) {
+  if (!s) return;
+  s->stop.store(true);
+  s->cv.notify_all();
+  if (s->loop.joinable()) s->loop.join();
+  for (cudaStream_t st : s->lanes) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (auto& kv : s->reqs) {
+    if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    delete kv.second;
+  }
+  for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
+  cudaFree(s->d_twf);
+  cudaFree(s->d_twi);
+  cudaFree(s->d_pc);
+  cudaFree(s->d_ctr);
+  cudaFree(s->d_err);
+  cudaFree(s->d_arena);
+  delete s;
+}
+
+extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, uint32_t n_max,
+                                     uint64_t device_bytes, uint32_t lanes, polymul_server** out) {
+  clear_error();
+  if (!out || !pool || pool_size == 0) return fail(POLYMUL_EINVAL, "need a prime pool and an out pointer");
+  if (n_max < 16 || n_max > 65536 || (n_max & (n_max - 1)))
+    return fail(POLYMUL_EINVAL, "n_max=%u must be a power of two in [16, 65536]", n_max);
+  if (lanes == 0 || lanes > 32) return fail(POLYMUL_EINVAL, "lanes must be in [1, 32]");
+  for (uint32_t j = 0; j < pool_size; ++j) {
+    const uint64_t q = pool[j];
+    if (q >= (1ull << 62) || !pm::host::is_prime(q) || (q - 1) % (2ull * n_max) != 0)
+      return fail(POLYMUL_EINVAL, "pool[%u]=%llu must be a prime < 2^62 with 2 n_max | q - 1", j,
+                  (unsigned long long)q);
+    for (uint32_t i = 0; i < j; ++i)
+      if (pool[i] == q) return fail(POLYMUL_EINVAL, "duplicate pool prime");
+  }
+  if (device_bytes < request_bytes(n_max, 1))
+    return fail(POLYMUL_EINVAL, "device_bytes too small for one product of degree n_max");
+  polymul_server* s = new polymul_server();
+  s->nmax = n_max;
+  s->lognmax = __builtin_ctz(n_max);
+  s->pool.assign(pool, pool + pool_size);
+  s->nlanes = (int)lanes;
+  int rc = POLYMUL_OK;
+  auto bail = [&](int code) {
+    std::string keep = polymul_last_error();
+    polymul_server_destroy(s);
+    fail(code, "%s", keep.c_str());
+    return code;
+  };
+  std::vector<uint64_t> twf, twi;
+  std::vector<PrimeConst<uint64_t>> pcs((size_t)pool_size * (kServeMaxLog + 1));
+  for (uint32_t j = 0; j < pool_size; ++j)
+    build_serve_prime(s->pool[j], n_max, twf, twi, &pcs[(size_t)j * (kServeMaxLog + 1)]);
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "device query"));
+  if (cudaMalloc(&s->d_twf, twf.size() * 8) != cudaSuccess || cudaMalloc(&s->d_twi, twi.size() * 8) != cudaSuccess ||
+      cudaMalloc(&s->d_pc, pcs.size() * sizeof(PrimeConst<uint64_t>)) != cudaSuccess ||
+      cudaMalloc(&s->d_ctr, 2 * lanes * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess || cudaMalloc(&s->d_arena, device_bytes) != cudaSuccess)
+    return bail(fail(POLYMUL_ENOMEM, "device allocation failed"));
+  if (cudaMemcpy(s->d_twf, twf.data(), twf.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->d_twi, twi.data(), twi.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->d_pc, pcs.data(), pcs.size() * sizeof(PrimeConst<uint64_t>), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemset(s->d_ctr, 0, 2 * lanes * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "table upload"));
+  s->arena_bytes = device_bytes;
+  s->free_list[0] = device_bytes;
+  // kernels per degree (64-bit words, Harvey bounds: every pool prime < 2^62)
+  for (int logn = 4; logn <= (int)s->lognmax; ++logn) {
+    KernelInfo ki;
+    const bool ok = logn >= 14 ? lookup_ntt_cluster(8, logn, 1, &ki) : lookup_ntt_u64_m1(logn, &ki);
+    if (!ok) return bail(fail(POLYMUL_ENOTSUP, "no kernel for n=2^%d", logn));
+    if (ki.smem > 48 * 1024 &&
+        cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "smem attribute"));
+    int cap = 0;
+    if (ki.cluster > 0) {
+      cudaLaunchConfig_t cfg;
+      memset(&cfg, 0, sizeof cfg);
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = ki.cluster;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.gridDim = dim3(ki.cluster * s->num_sms);
+      cfg.blockDim = dim3(ki.block);
+      cfg.dynamicSmemBytes = ki.smem;
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, ki.fn, &cfg) != cudaSuccess || clusters < 1)
+        return bail(fail(POLYMUL_ENOTSUP, "no cluster fits for n=2^%d", logn));
+      cap = clusters * ki.cluster;
+    } else {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, ki.block, ki.smem) != cudaSuccess ||
+          per_sm < 1)
+        return bail(fail(POLYMUL_ENOTSUP, "kernel for n=2^%d does not fit", logn));
+      cap = per_sm * s->num_sms;
+    }
+    s->ki[logn] = ki;
+    s->grid_cap[logn] = cap;
+  }
+  for (uint32_t l = 0; l < lanes; ++l) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "stream creation"));
+    s->lanes.push_back(st);
+  }
+  s->loop = std::thread(server_loop, s);
+  *out = s;
+  return rc;
+}
+
+extern "C" int polymul_server_submit(polymul_server* s, const polymul_request* q, uint64_t* ticket) {
+  clear_error();
+  if (!s || !q || !ticket) return fail(POLYMUL_EINVAL, "null argument");
+  if (q->n < 16 || q->n > s->nmax || (q->n & (q->n - 1)))
+    return fail(POLYMUL_EINVAL, "n=%u must be a power of two in [16, %u]", q->n, s->nmax);
+  if (q->k == 0 || q->k > s->pool.size() || !q->prime_idx) return fail(POLYMUL_EINVAL, "bad prime list");
+  if (!q->a || !q->b || !q->c) return fail(POLYMUL_EINVAL, "null operand pointer");
+  for (uint32_t i = 0; i < q->k; ++i)
+    if (q->prime_idx[i] >= s->pool.size()) return fail(POLYMUL_EINVAL, "prime index outside the pool");
+  const size_t bytes = request_bytes(q->n, q->k);
+  if (bytes > s->arena_bytes) return fail(POLYMUL_EINVAL, "request larger than the server's device memory");
+  ServeReq* r = new ServeReq();
+  r->n = q->n;
+  r->k = q->k;
+  r->logn = (uint32_t)__builtin_ctz(q->n);
+  r->primes.assign(q->prime_idx, q->prime_idx + q->k);
+  r->ha = q->a;
+  r->hb = q->b;
+  r->hc = q->c;
+  r->bytes = bytes;
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    r->ticket = s->next_ticket++;
+    s->reqs[r->ticket] = r;
+    s->queue.push_back(r);
+    ++s->submitted;
+  }
+  s->cv.notify_all();
+  *ticket = r->ticket;
+  return POLYMUL_OK;
+}
+
+// 1: done (and forgotten), 0: pending, <0 failure code
+static int take_if_done(polymul_server* s, uint64_t ticket) {
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return -POLYMUL_EINVAL;
+  ServeReq* r = it->second;
+  if (r->state < 2) return 0;
+  const int st = r->state;
+  delete r;
+  s->reqs.erase(it);
+  return st == 2 ? 1 : -POLYMUL_ECUDA;
+}
+
+extern "C" int polymul_server_poll(polymul_server* s, uint64_t ticket, int* done) {
+  clear_error();
+  if (!s || !done) return fail(POLYMUL_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  const int r = take_if_done(s, ticket);
+  if (r < 0) return fail(-r, r == -POLYMUL_EINVAL ? "unknown ticket" : "request failed: %s", s->cuda_error_msg.c_str());
+  *done = r;
+  return POLYMUL_OK;
+}
+
+extern "C" int polymul_server_wait(polymul_server* s, uint64_t ticket, double timeout_s) {
+  clear_error();
+  if (!s) return fail(POLYMUL_EINVAL, "server is NULL");
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (;;) {
+    const int r = take_if_done(s, ticket);
+    if (r < 0) return fail(-r, r == -POLYMUL_EINVAL ? "unknown ticket" : "request failed: %s", s->cuda_error_msg.c_str());
+    if (r == 1) return POLYMUL_OK;
+    if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout && Clock::now() >= deadline)
+      return fail(POLYMUL_ETIMEOUT, "request %llu not finished within %.3f s", (unsigned long long)ticket, timeout_s);
+  }
+}
+
+extern "C" int polymul_server_replay(polymul_server* s, const polymul_request* reqs, uint32_t count,
+                                     const double* arrival_s, double* latency_us) {
+  clear_error();
+  if (!s || (count && (!reqs || !arrival_s))) return fail(POLYMUL_EINVAL, "null argument");
+  std::vector<uint64_t> tickets(count);
+  const auto t0 = Clock::now();
+  for (uint32_t i = 0; i < count; ++i) {
+    const auto at = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(arrival_s[i]));
+    while (Clock::now() < at) {
+      const auto left = at - Clock::now();
+      if (left > std::chrono::microseconds(200)) std::this_thread::sleep_for(left - std::chrono::microseconds(100));
+    }
+    const int rc = polymul_server_submit(s, &reqs[i], &tickets[i]);
+    if (rc != POLYMUL_OK) return rc;
+  }
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (uint32_t i = 0; i < count; ++i) {
+    for (;;) {
+      auto it = s->reqs.find(tickets[i]);
+      if (it == s->reqs.end()) return fail(POLYMUL_EINVAL, "ticket vanished");
+      ServeReq* r = it->second;
+      if (r->state >= 2) {
+        if (latency_us) latency_us[i] = (r->t_done - r->t_submit) * 1e6;
+        const int st = r->state;
+        delete r;
+        s->reqs.erase(it);
+        if (st != 2) return fail(POLYMUL_ECUDA, "request failed: %s", s->cuda_error_msg.c_str());
+        break;
+      }
+      s->cv.wait_for(lock, std::chrono::milliseconds(50));
+    }
+  }
+  return POLYMUL_OK;
+}
+
+extern "C" int polymul_server_stats_get(polymul_server* s, polymul_server_stats* out, int reset) {
+  clear_error();
+  if (!s || !out) return fail(POLYMUL_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  memset(out, 0, sizeof *out);
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->queued = s->queue.size();
+  out->in_flight = s->inflight.size();
+  out->arena_bytes = s->arena_bytes;
+  out->arena_peak_bytes = s->arena_peak;
+  std::vector<double> l = s->latencies_us;
+  if (!l.empty()) {
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double p) { return l[std::min(l.size() - 1, (size_t)(p * (l.size() - 1) + 0.5))]; };
+    out->p50_us = pct(0.50);
+    out->p99_us = pct(0.99);
+    out->max_us = l.back();
+    double sum = 0;
+    for (double x : l) sum += x;
+    out->mean_us = sum / l.size();
+  }
+  if (reset) {
+    s->latencies_us.clear();
+    s->completed = s->submitted = s->failed = 0;
+    s->arena_peak = s->arena_used;
+  }
+  return POLYMUL_OK;
+}

@@ -170,7 +170,11 @@ extern "C" int polymul_batch_static(uint32_t n, uint64_t q, const void* a, const
                               1u,
                               reinterpret_cast<unsigned long long*>(s.ptr),
                               reinterpret_cast<int*>(s.ptr + 16),
-                              nullptr};
+                              nullptr,
+                              nullptr,
+                              n,
+                              1u,
+                              0u};
   void* argv[] = {&args};
   PM_CUDA(cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st));
   return POLYMUL_OK;

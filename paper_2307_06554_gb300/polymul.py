@@ -52,6 +52,17 @@ class polymul_desc(ctypes.Structure):
                 ("reserved", ctypes.c_uint32), ("offset", ctypes.c_uint64)]
 
 
+class polymul_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("k", ctypes.c_uint32), ("prime_idx", ctypes.POINTER(ctypes.c_uint32)),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("c", ctypes.c_void_p)]
+
+
+class polymul_server_stats(ctypes.Structure):
+    _fields_ = [(x, ctypes.c_uint64) for x in ("submitted", "completed", "failed", "queued", "in_flight",
+                                               "arena_bytes", "arena_peak_bytes")] + \
+               [(x, ctypes.c_double) for x in ("p50_us", "p99_us", "mean_us", "max_us")]
+
+
 def library_path() -> str:
     """The in-tree build, or the file named by POLYMUL_LIB if set."""
     return os.environ.get("POLYMUL_LIB") or _build.LIB
@@ -93,6 +104,21 @@ def _load():
     lib.polymul_ragged_batch_destroy.restype = None
     lib.polymul_ragged_destroy.argtypes = [vp]
     lib.polymul_ragged_destroy.restype = None
+    lib.polymul_server_create.argtypes = [ctypes.POINTER(u64), u32, u32, u64, u32, ctypes.POINTER(vp)]
+    lib.polymul_server_create.restype = i32
+    lib.polymul_server_submit.argtypes = [vp, ctypes.POINTER(polymul_request), ctypes.POINTER(u64)]
+    lib.polymul_server_submit.restype = i32
+    lib.polymul_server_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int)]
+    lib.polymul_server_poll.restype = i32
+    lib.polymul_server_wait.argtypes = [vp, u64, ctypes.c_double]
+    lib.polymul_server_wait.restype = i32
+    lib.polymul_server_replay.argtypes = [vp, ctypes.POINTER(polymul_request), u32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+    lib.polymul_server_replay.restype = i32
+    lib.polymul_server_stats_get.argtypes = [vp, ctypes.POINTER(polymul_server_stats), ctypes.c_int]
+    lib.polymul_server_stats_get.restype = i32
+    lib.polymul_server_destroy.argtypes = [vp]
+    lib.polymul_server_destroy.restype = None
     lib.polymul_last_error.argtypes = []
     lib.polymul_last_error.restype = ctypes.c_char_p
     return lib
@@ -311,6 +337,69 @@ class Ragged:
         if getattr(self, "ctx", None):
             polymul_ragged_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------------- serving
+class Server:
+    """Continuously batching request loop (see polymul_server_* in the
+    header).  Operands are host numpy uint64 arrays of shape [k][n]; keep
+    them alive until the request completes."""
+
+    def __init__(self, pool: Sequence[int], n_max: int, device_bytes: int = 1 << 30, lanes: int = 8):
+        arr = (ctypes.c_uint64 * len(pool))(*[int(q) for q in pool])
+        out = ctypes.c_void_p()
+        _check(_lib.polymul_server_create(arr, len(pool), n_max, device_bytes, lanes, ctypes.byref(out)))
+        self.handle = out.value
+        self._keep = {}
+
+    def _req(self, n, prime_idx, a, b, c):
+        idx = (ctypes.c_uint32 * len(prime_idx))(*[int(x) for x in prime_idx])
+        r = polymul_request(n, len(prime_idx), idx, _ptr(a), _ptr(b), _ptr(c))
+        return r, idx
+
+    def submit(self, n, prime_idx, a, b, c) -> int:
+        r, idx = self._req(n, prime_idx, a, b, c)
+        t = ctypes.c_uint64()
+        _check(_lib.polymul_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(_lib.polymul_server_poll(self.handle, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
+        _check(_lib.polymul_server_wait(self.handle, ticket, timeout_s))
+
+    def replay(self, requests, arrival_s):
+        """requests: (n, prime_idx, a, b, c) tuples; returns latencies (us)."""
+        m = len(requests)
+        arr = (polymul_request * max(1, m))()
+        keep = []
+        for i, (n, idx, a, b, c) in enumerate(requests):
+            r, ix = self._req(n, idx, a, b, c)
+            arr[i] = r
+            keep.append(ix)
+        times = (ctypes.c_double * max(1, m))(*[float(x) for x in arrival_s])
+        lat = (ctypes.c_double * max(1, m))()
+        _check(_lib.polymul_server_replay(self.handle, arr, m, times, lat))
+        return [lat[i] for i in range(m)]
+
+    def stats(self, reset: bool = False) -> dict:
+        st = polymul_server_stats()
+        _check(_lib.polymul_server_stats_get(self.handle, ctypes.byref(st), int(reset)))
+        return {name: getattr(st, name) for name, _ in polymul_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.polymul_server_destroy(self.handle)
+            self.handle = None
 
     def __enter__(self):
         return self
