@@ -23,12 +23,18 @@ def pool():
     return wl.serve_pool()
 
 
+def _pinned(x):
+    """A page-locked copy (host-device copies then overlap other work)."""
+    import torch
+    return torch.from_numpy(x).pin_memory().numpy()
+
+
 def _requests(pool, count, seed, kmax=6, degrees=wl.SERVE_DEGREES):
     reqs = wl.serve_requests(count=count, seed=seed, kmax=kmax, degrees=degrees)
     out = []
     for r in reqs:
         a, b = wl.request_operands(r, pool)
-        out.append((r.n, r.prime_idx, a, b))
+        out.append((r.n, r.prime_idx, _pinned(a), _pinned(b)))
     return out
 
 
@@ -65,7 +71,7 @@ def test_alone_equals_in_the_mix(pm, pool):
             c = np.zeros_like(a)
             srv.wait(srv.submit(n, idx, a, b, c))
             alone.append(c)
-        mix = [np.zeros_like(a) for _, _, a, _ in reqs]
+        mix = [_pinned(np.zeros_like(a)) for _, _, a, _ in reqs]
         tickets = [srv.submit(n, idx, a, b, c) for (n, idx, a, b), c in zip(reqs, mix)]
         for t in tickets:
             srv.wait(t)
@@ -100,7 +106,7 @@ def test_poisson_replay(pm, pool):
     reqs = _requests(pool, 120, seed=73, kmax=4, degrees=(4096, 8192, 16384))
     arrivals = [r.arrival_s for r in wl.serve_requests(count=120, seed=73, rate_per_s=2.0e4, kmax=4,
                                                        degrees=(4096, 8192, 16384))]
-    outs = [np.zeros_like(a) for _, _, a, _ in reqs]
+    outs = [_pinned(np.zeros_like(a)) for _, _, a, _ in reqs]
     with pm.Server(pool, 16384, device_bytes=1 << 28, lanes=8) as srv:
         lat = srv.replay([(n, idx, a, b, c) for (n, idx, a, b), c in zip(reqs, outs)], arrivals)
         st = srv.stats()
