@@ -62,11 +62,13 @@ extern "C" {
 
 /* ---- flags ---- */
 #define POLYMUL_FLAG_VALIDATE 1u  /* check that inputs are < q (slower)       */
+#define POLYMUL_FLAG_TUNE     2u  /* time the candidate kernels at creation    */
 
 typedef struct polymul_opts {
-    uint32_t path;      /* POLYMUL_PATH_*                                     */
-    uint32_t flags;     /* POLYMUL_FLAG_*                                     */
-    uint32_t reserved[6];
+    uint32_t path;        /* POLYMUL_PATH_*                                   */
+    uint32_t flags;       /* POLYMUL_FLAG_*                                   */
+    uint32_t tune_batch;  /* batch size to tune for (0: 1024)                 */
+    uint32_t reserved[5];
 } polymul_opts;
 
 typedef struct polymul_plan_info {
@@ -81,7 +83,10 @@ typedef struct polymul_plan_info {
     uint32_t ctas_per_sm; /* resident CTAs per SM of the main kernel          */
     uint32_t digit_bits;  /* tensor path: digit width w (0 for NTT plans)     */
     uint32_t digits;      /* tensor path: digits per coefficient L            */
-    uint32_t reserved[5];
+    uint32_t radix_bits;  /* NTT path: stage bits per register pass           */
+    uint32_t candidates;  /* kernels the autotuner chooses among              */
+    uint32_t tuned;       /* 1 once polymul_tune has chosen                   */
+    uint32_t reserved[2];
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
@@ -161,6 +166,24 @@ int polymul_plan_status(polymul_plan *plan, void *stream);
  */
 int polymul_batch_static(uint32_t n, uint64_t q, const void *a, const void *b, void *c,
                          uint64_t batch, void *stream);
+
+/*
+ * polymul_tune -- choose the plan's kernel by measurement (the paper leaves
+ * the matrix dimensions to "experimentation", Sec. 2.6): every candidate --
+ * the default NTT kernel, NTT kernels with other register radices, and the
+ * tensor path where it applies -- runs on a batch of `batch` products
+ * (rounded up to a power of two) and the fastest is kept.  Choices are
+ * cached per (GPU, word size, n, k, reduction mode, modulus size, batch
+ * bucket) for the process, and in the file named by the environment
+ * variable POLYMUL_TUNE_CACHE if set (read on first use, appended after each
+ * new measurement).  Allocates scratch buffers for the measurement only.
+ * Synchronous.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int polymul_tune(polymul_plan *plan, uint64_t batch, void *stream);
+
+/* Use candidate kernel `candidate` (0 .. info.candidates - 1; 0 is the
+ * default) instead of the tuned or default choice.  Errors: EINVAL. */
+int polymul_plan_select(polymul_plan *plan, uint32_t candidate);
 
 /* Fill *info with the plan's shape and launch configuration. */
 int polymul_plan_info_get(const polymul_plan *plan, polymul_plan_info *info);

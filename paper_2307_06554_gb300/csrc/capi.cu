@@ -125,8 +125,8 @@ int upload_tensor_tables(polymul_plan* p) {
     tp[j].q = (uint32_t)p->q[j];
     for (int e = 0; e < 15; ++e) tp[j].pw[e] = (int64_t)pm::host::powmod(2, (uint64_t)p->digit_bits * e, p->q[j]);
   }
-  PM_CUDA(cudaMalloc(&p->d_pc, tp.size() * sizeof(TensorPrime)));
-  PM_CUDA(cudaMemcpy(p->d_pc, tp.data(), tp.size() * sizeof(TensorPrime), cudaMemcpyHostToDevice));
+  PM_CUDA(cudaMalloc(&p->d_tpc, tp.size() * sizeof(TensorPrime)));
+  PM_CUDA(cudaMemcpy(p->d_tpc, tp.data(), tp.size() * sizeof(TensorPrime), cudaMemcpyHostToDevice));
   return POLYMUL_OK;
 }
 
@@ -249,29 +249,41 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
                    lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki);
 
   int rc = POLYMUL_OK;
+  auto add_candidate = [&](uint32_t cpath, const KernelInfo& ki) -> int {
+    p->ki = ki;
+    p->path = cpath;
+    int r = configure_launch(p);
+    if (r == POLYMUL_OK) p->cands.push_back(PlanCandidate{cpath, ki, p->grid_cap});
+    return r;
+  };
   if ((path == POLYMUL_PATH_NTT || path == POLYMUL_PATH_AUTO) && !ntt_ok && aux_ok) {
-    p->path = POLYMUL_PATH_NTT;
     p->aux_prime = p->aux_candidate;
     p->mode = 0;
-    p->ki = p->aki;
     rc = upload_ntt_tables<uint32_t>(p);
-    if (rc == POLYMUL_OK) rc = configure_launch(p);
+    if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_NTT, p->aki);
   } else if (path == POLYMUL_PATH_TENSOR || (path == POLYMUL_PATH_AUTO && !ntt_ok && tensor_ok)) {
     if (!tensor_ok) {
       rc = fail(POLYMUL_ENOTSUP, "tensor path not available for n=%u and these moduli", n);
     } else {
-      p->path = POLYMUL_PATH_TENSOR;
-      p->ki = p->tki;
       rc = upload_tensor_tables(p);
-      if (rc == POLYMUL_OK) rc = configure_launch(p);
+      if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
     }
   } else if (!ntt_ok) {
     rc = fail(POLYMUL_ENOTSUP, "no NTT route for these moduli at n=%u (need prime q = 1 mod 2n, q < 2^31 for 32-bit words)", n);
   } else {
-    p->path = POLYMUL_PATH_NTT;
+    // the default kernel first, then the candidates the autotuner may prefer
     rc = p->elem == 4 ? upload_ntt_tables<uint32_t>(p) : upload_ntt_tables<uint64_t>(p);
-    if (rc == POLYMUL_OK) rc = configure_launch(p);
+    KernelInfo v;
+    if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_NTT, p->ki);
+    if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb5((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
+    if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
+    if (rc == POLYMUL_OK && p->elem == 8 && lookup_ntt_u64_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
+    if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) {
+      rc = upload_tensor_tables(p);
+      if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
+    }
   }
+  if (rc == POLYMUL_OK) apply_candidate(p, 0);
   if (rc == POLYMUL_OK) {
     // work counters for the three launch slots (device entry, two host-entry streams)
     if (cudaMalloc(&p->d_ctr, 6 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -285,6 +297,16 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     g_err = keep;
     return rc;
   }
+  if (p->flags & POLYMUL_FLAG_TUNE) {
+    const uint64_t tb = opts && opts->reserved[0] ? opts->reserved[0] : 1024;
+    rc = polymul_tune(p, tb, nullptr);
+    if (rc != POLYMUL_OK) {
+      std::string keep = g_err;
+      polymul_destroy(p);
+      g_err = keep;
+      return rc;
+    }
+  }
   *out = p;
   return POLYMUL_OK;
 }
@@ -294,6 +316,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_twf);
   cudaFree(p->d_twi);
   cudaFree(p->d_pc);
+  cudaFree(p->d_tpc);
   cudaFree(p->d_flag);
   cudaFree(p->d_ctr);
   cudaFree(p->d_err);
@@ -322,6 +345,9 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->ctas_per_sm = (uint32_t)(p->num_sms ? p->grid_cap / p->num_sms : 0);
   info->digit_bits = p->path == POLYMUL_PATH_TENSOR ? (uint32_t)p->digit_bits : 0;
   info->digits = p->path == POLYMUL_PATH_TENSOR ? (uint32_t)p->digits : 0;
+  info->radix_bits = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.rb : 0;
+  info->candidates = (uint32_t)p->cands.size();
+  info->tuned = p->tuned ? 1u : 0u;
   return POLYMUL_OK;
 }
 
@@ -390,7 +416,7 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     return POLYMUL_OK;
   };
   if (p->path == POLYMUL_PATH_TENSOR) {
-    TensorBatchArgs args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, (const TensorPrime*)p->d_pc,
+    TensorBatchArgs args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, (const TensorPrime*)p->d_tpc,
                          units, p->k, ctr, p->d_err};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));

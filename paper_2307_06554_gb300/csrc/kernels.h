@@ -13,6 +13,7 @@ struct KernelInfo {
   int units_per_cta = 0;     // units a CTA processes per iteration
   int tmem_cols = 0;         // tensor-memory columns allocated per CTA (0: none)
   int cluster = 0;           // CTAs per thread-block cluster (0: no cluster launch)
+  int rb = 0;                // NTT: stage bits per register pass
 };
 
 // batched negacyclic NTT, k_ntt_batch<W, LOGN, MODE> (MODE: 0 = kQ31,
@@ -23,6 +24,10 @@ bool lookup_ntt_u32_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
 bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_aux(int logn, KernelInfo* ki);  // auxiliary-prime mode, logn 4..14
+// autotuner candidates: other register radices (RB = stage bits per pass)
+bool lookup_ntt_u32_rb5(int logn, int mode, KernelInfo* ki);  // logn 9..13, modes 1, 2
+bool lookup_ntt_u32_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, modes 1, 2
+bool lookup_ntt_u64_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, mode 1
 
 // one product per thread-block cluster (n = 2^14 .. 2^16)
 bool lookup_ntt_cluster(uint32_t elem, int logn, int mode, KernelInfo* ki);

@@ -123,6 +123,7 @@ static KernelInfo cluster_info() {
   ki.team = S::T;
   ki.units_per_cta = 1;
   ki.cluster = S::T / kClusterThreads;
+  ki.rb = 4;
   return ki;
 }
 

@@ -30,6 +30,7 @@ KernelInfo ntt_info() {
   using W_ = W;
   KernelInfo ki;
   ki.fn = (const void*)k_ntt_batch<S, MODE, kNttWarps, REGS, AUX>;
+  ki.rb = RB;
   ki.team = S::T;
   if (S::T <= 32) {
     ki.block = 32 * kNttWarps;

@@ -7,6 +7,13 @@
 
 #include "kernels.h"
 
+// One launchable way of computing a plan's products (the autotuner's choices).
+struct PlanCandidate {
+  uint32_t path;     // POLYMUL_PATH_NTT or POLYMUL_PATH_TENSOR
+  pm::KernelInfo ki;
+  int grid_cap;
+};
+
 struct polymul_plan {
   uint32_t n = 0, logn = 0, k = 0;
   uint32_t elem = 4;   // bytes per coefficient word (4 or 8)
@@ -23,6 +30,10 @@ struct polymul_plan {
   void* d_pc = nullptr;
   pm::KernelInfo ki;   // the main kernel of the chosen path
   pm::KernelInfo tki;  // tensor-path kernel, when one exists for the shape
+  std::vector<PlanCandidate> cands;  // [0] is the default
+  size_t chosen = 0;
+  bool tuned = false;
+  void* d_tpc = nullptr;  // tensor-path constants
   uint64_t* d_q = nullptr;  // moduli on the device (input validation)
   // auxiliary-prime NTT (moduli without a 2n-th root of unity)
   uint64_t aux_prime = 0, aux_candidate = 0;
@@ -39,7 +50,17 @@ struct polymul_plan {
   cudaEvent_t ev_entry = nullptr;
 };
 
+inline void apply_candidate(polymul_plan* p, size_t i) {
+  p->chosen = i;
+  p->path = p->cands[i].path;
+  p->ki = p->cands[i].ki;
+  p->grid_cap = p->cands[i].grid_cap;
+}
+
+extern "C" int polymul_tune(polymul_plan* plan, uint64_t batch, void* stream);
+
 namespace pm {
+int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st, int slot);
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 void clear_error();

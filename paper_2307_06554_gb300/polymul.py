@@ -27,6 +27,7 @@ PATH_AUTO = 0
 PATH_NTT = 1
 PATH_TENSOR = 2
 FLAG_VALIDATE = 1
+FLAG_TUNE = 2
 
 _ERRNAMES = {1: "EINVAL", 2: "ENOTSUP", 3: "EDOMAIN", 4: "ENOMEM", 5: "ETIMEOUT", 6: "ECUDA"}
 
@@ -38,13 +39,14 @@ class PolymulError(RuntimeError):
 
 
 class polymul_opts(ctypes.Structure):
-    _fields_ = [("path", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+    _fields_ = [("path", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("tune_batch", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
 
 
 class polymul_plan_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
-                 "digit_bits", "digits")] + [("reserved", ctypes.c_uint32 * 5)]
+                 "digit_bits", "digits", "radix_bits", "candidates", "tuned")] + [("reserved", ctypes.c_uint32 * 2)]
 
 
 class polymul_desc(ctypes.Structure):
@@ -82,6 +84,10 @@ def _load():
     lib.polymul_batch_host.restype = i32
     lib.polymul_batch_static.argtypes = [u32, u64, vp, vp, vp, u64, vp]
     lib.polymul_batch_static.restype = i32
+    lib.polymul_plan_select.argtypes = [vp, u32]
+    lib.polymul_plan_select.restype = i32
+    lib.polymul_tune.argtypes = [vp, u64, vp]
+    lib.polymul_tune.restype = i32
     lib.polymul_plan_status.argtypes = [vp, vp]
     lib.polymul_plan_status.restype = i32
     lib.polymul_plan_info_get.argtypes = [vp, ctypes.POINTER(polymul_plan_info)]
@@ -161,9 +167,10 @@ def _stream(stream) -> int:
     return stream.cuda_stream
 
 
-def polymul_create(n: int, q_list: Sequence[int], path: int = PATH_AUTO, flags: int = 0) -> int:
+def polymul_create(n: int, q_list: Sequence[int], path: int = PATH_AUTO, flags: int = 0,
+                   tune_batch: int = 0) -> int:
     arr = (ctypes.c_uint64 * len(q_list))(*[int(q) for q in q_list])
-    opts = polymul_opts(path, flags)
+    opts = polymul_opts(path, flags, tune_batch)
     out = ctypes.c_void_p()
     _check(_lib.polymul_create(n, arr, len(q_list), ctypes.byref(opts), ctypes.byref(out)))
     return out.value
@@ -180,6 +187,14 @@ def polymul_batch_host(plan: int, a, b, c, batch: int, stream=None) -> None:
 def polymul_batch_static(n: int, q: int, a, b, c, batch: int, stream=None) -> None:
     """Allocation-free entry point (one NTT-friendly prime, n <= 4096)."""
     _check(_lib.polymul_batch_static(n, q, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
+
+
+def polymul_plan_select(plan: int, candidate: int) -> None:
+    _check(_lib.polymul_plan_select(plan, candidate))
+
+
+def polymul_tune(plan: int, batch: int, stream=None) -> None:
+    _check(_lib.polymul_tune(plan, batch, _stream(stream)))
 
 
 def polymul_plan_status(plan: int, stream=None) -> None:
@@ -199,11 +214,22 @@ def polymul_destroy(plan: int) -> None:
 class Plan:
     """Owning wrapper: ``with Plan(n, qs) as p: p.batch(a, b, c)``."""
 
-    def __init__(self, n: int, q_list: Sequence[int], path: int = PATH_AUTO, flags: int = 0):
+    def __init__(self, n: int, q_list: Sequence[int], path: int = PATH_AUTO, flags: int = 0,
+                 tune_batch: int = 0):
         self.n = int(n)
         self.q_list = [int(q) for q in q_list]
-        self.handle = polymul_create(self.n, self.q_list, path, flags)
+        self.handle = polymul_create(self.n, self.q_list, path, flags, tune_batch)
         self.info = polymul_plan_info_get(self.handle)
+
+    def select(self, candidate: int) -> dict:
+        polymul_plan_select(self.handle, candidate)
+        self.info = polymul_plan_info_get(self.handle)
+        return self.info
+
+    def tune(self, batch: int, stream=None) -> dict:
+        polymul_tune(self.handle, batch, stream)
+        self.info = polymul_plan_info_get(self.handle)
+        return self.info
 
     @property
     def elem_bytes(self) -> int:
