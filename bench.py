@@ -225,7 +225,7 @@ def other_workloads(dev, stream, peaks, alu_peak_g):
     hbm = peaks["hbm_gbs"]
 
     def homogeneous(name, w, sets_needed, reps):
-        plan = polymul.Plan(w.n, w.q_list)
+        plan = polymul.Plan(w.n, w.q_list, flags=polymul.FLAG_TUNE, tune_batch=w.batch)
         k = len(w.q_list)
         elem = plan.elem_bytes
         view = np.int32 if elem == 4 else np.int64
@@ -245,8 +245,14 @@ def other_workloads(dev, stream, peaks, alu_peak_g):
         units = w.batch * k
         mm = units * _ntt_mulmods(w.n)
         byts = 3 * units * w.n * elem
+        path = {1: "ntt", 2: "tensor"}.get(plan.info["path"], "?")
+        if plan.info["aux_primes"]:
+            path += " (auxiliary prime)"
+        elif plan.info["path"] == 1:
+            path += " (radix %d register passes, autotuned over %d)" % (1 << plan.info["radix_bits"],
+                                                                     plan.info["candidates"])
         out[name] = {"products_per_s": w.batch / (ms / 1e3), "us_per_step": ms * 1e3, "batch": w.batch,
-                     "n": w.n, "k": k, "path": "ntt" + (" (auxiliary prime)" if plan.info["aux_primes"] else ""),
+                     "n": w.n, "k": k, "path": path,
                      "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm,
                      "bit_exact_sample": ok,
                      "l2": "inputs rotated over %d buffer sets" % len(sets) if len(sets) > 1 else "L2-resident"}
@@ -392,7 +398,8 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     w = wl.ring_1024()
     n, batch, q_list = w.n, w.batch, w.q_list
-    plan = polymul.Plan(n, q_list)
+    # the autotuned kernel for this shape (tuning runs before the timed region)
+    plan = polymul.Plan(n, q_list, flags=polymul.FLAG_TUNE, tune_batch=batch)
     info = plan.info
     elem = info["elem_bytes"]
     set_bytes = 3 * batch * len(q_list) * n * elem
@@ -553,6 +560,7 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded uniform residues)",
         "config": {"workload": WORKLOAD, "path": {1: "ntt", 2: "tensor"}.get(info["path"], "?"),
+                   "autotuned": {"candidates": info["candidates"], "radix_bits": info["radix_bits"]},
                    "n": n, "q": q_list, "batch": batch,
                    "l2": "inputs rotated over %d buffer sets (%.0f MB > 3x L2)" % (nsets, nsets * set_bytes / 2**20),
                    "parallelism": "replicas" if ws > 1 else "single"},
