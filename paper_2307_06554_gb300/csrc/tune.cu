@@ -100,17 +100,23 @@ extern "C" int polymul_tune(polymul_plan* p, uint64_t batch, void* stream) {
         return POLYMUL_OK;
       }
   }
-  // measure every candidate on zero operands (timing does not depend on data)
+  // measure every candidate on zero operands (timing does not depend on the
+  // data), rotating over enough buffer sets that the operands come from
+  // HBM, not L2, as they do in a stream of real batches
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = bucket * prod_bytes;
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, p->device);
+  int nsets = (int)std::min<uint64_t>(8, (3ull * (uint64_t)l2 + 3 * bytes - 1) / (3 * bytes));
+  while (nsets > 1 && (uint64_t)nsets * 3 * bytes > (1ull << 30)) --nsets;
+  if (nsets < 1) nsets = 1;
   void* buf = nullptr;
-  if (cudaMalloc(&buf, 3 * bytes) != cudaSuccess) return fail(POLYMUL_ENOMEM, "tuning buffers (%zu bytes)", 3 * bytes);
-  char* a = (char*)buf;
-  char* b = a + bytes;
-  char* c = b + bytes;
+  if (cudaMalloc(&buf, (size_t)nsets * 3 * bytes) != cudaSuccess)
+    return fail(POLYMUL_ENOMEM, "tuning buffers (%zu bytes)", (size_t)nsets * 3 * bytes);
+  auto set_ptr = [&](int i, int which) { return (char*)buf + ((size_t)(i % nsets) * 3 + which) * bytes; };
   int rc = POLYMUL_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaMemsetAsync(buf, 0, 3 * bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+  if (cudaMemsetAsync(buf, 0, (size_t)nsets * 3 * bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(POLYMUL_ECUDA, "tuning setup failed");
   const size_t saved_chosen = p->chosen;
@@ -121,9 +127,12 @@ extern "C" int polymul_tune(polymul_plan* p, uint64_t batch, void* stream) {
   for (size_t i = 0; rc == POLYMUL_OK && i < p->cands.size(); ++i) {
     apply_candidate(p, i);
     bool ok = true;
-    for (int w = 0; w < 2 && ok; ++w) ok = launch_batch(p, a, b, c, bucket, st, 0) == POLYMUL_OK;
+    constexpr int kTimed = 10;
+    for (int w = 0; w < 2 && ok; ++w)
+      ok = launch_batch(p, set_ptr(w, 0), set_ptr(w, 1), set_ptr(w, 2), bucket, st, 0) == POLYMUL_OK;
     if (ok) ok = cudaEventRecord(e0, st) == cudaSuccess;
-    for (int r = 0; r < 5 && ok; ++r) ok = launch_batch(p, a, b, c, bucket, st, 0) == POLYMUL_OK;
+    for (int r = 0; r < kTimed && ok; ++r)
+      ok = launch_batch(p, set_ptr(2 + r, 0), set_ptr(2 + r, 1), set_ptr(2 + r, 2), bucket, st, 0) == POLYMUL_OK;
     float ms = 0;
     if (ok) ok = cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
