@@ -122,30 +122,48 @@ extern "C" int polymul_tune(polymul_plan* p, uint64_t batch, void* stream) {
   const size_t saved_chosen = p->chosen;
   const uint32_t saved_flags = p->flags;
   p->flags &= ~POLYMUL_FLAG_VALIDATE;
-  size_t best = saved_chosen;
-  float best_ms = 1e30f;
-  for (size_t i = 0; rc == POLYMUL_OK && i < p->cands.size(); ++i) {
-    apply_candidate(p, i);
+  std::vector<float> best_ms(p->cands.size(), 1e30f);
+  int launch_no = 0;
+  auto run = [&](int times) {
     bool ok = true;
-    constexpr int kTimed = 10;
-    for (int w = 0; w < 2 && ok; ++w)
-      ok = launch_batch(p, set_ptr(w, 0), set_ptr(w, 1), set_ptr(w, 2), bucket, st, 0) == POLYMUL_OK;
-    if (ok) ok = cudaEventRecord(e0, st) == cudaSuccess;
-    for (int r = 0; r < kTimed && ok; ++r)
-      ok = launch_batch(p, set_ptr(2 + r, 0), set_ptr(2 + r, 1), set_ptr(2 + r, 2), bucket, st, 0) == POLYMUL_OK;
+    for (int r = 0; r < times && ok; ++r, ++launch_no)
+      ok = launch_batch(p, set_ptr(launch_no, 0), set_ptr(launch_no, 1), set_ptr(launch_no, 2), bucket, st, 0) ==
+           POLYMUL_OK;
+    return ok;
+  };
+  // warm-up: bring the clocks up before anything is timed (about 50 ms)
+  if (rc == POLYMUL_OK) {
+    apply_candidate(p, 0);
     float ms = 0;
-    if (ok) ok = cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-    if (!ok) {
-      rc = fail(POLYMUL_ECUDA, "candidate %s failed while tuning: %s", label_of(p->cands[i]).c_str(),
-                cudaGetErrorString(cudaGetLastError()));
-      break;
-    }
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = i;
+    for (int w = 0; w < 64 && rc == POLYMUL_OK && ms < 50.f; ++w) {
+      bool ok = cudaEventRecord(e0, st) == cudaSuccess && run(4) && cudaEventRecord(e1, st) == cudaSuccess &&
+                cudaEventSynchronize(e1) == cudaSuccess;
+      float m = 0;
+      if (ok) ok = cudaEventElapsedTime(&m, e0, e1) == cudaSuccess;
+      if (!ok) rc = fail(POLYMUL_ECUDA, "warm-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+      ms += m;
     }
   }
+  // three round-robin rounds; each candidate keeps its fastest round
+  for (int round = 0; round < 3 && rc == POLYMUL_OK; ++round) {
+    for (size_t i = 0; rc == POLYMUL_OK && i < p->cands.size(); ++i) {
+      apply_candidate(p, i);
+      constexpr int kTimed = 10;
+      bool ok = run(2) && cudaEventRecord(e0, st) == cudaSuccess && run(kTimed) &&
+                cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+      float ms = 0;
+      if (ok) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      if (!ok) {
+        rc = fail(POLYMUL_ECUDA, "candidate %s failed while tuning: %s", label_of(p->cands[i]).c_str(),
+                  cudaGetErrorString(cudaGetLastError()));
+        break;
+      }
+      best_ms[i] = std::min(best_ms[i], ms);
+    }
+  }
+  size_t best = saved_chosen;
+  for (size_t i = 0; i < p->cands.size(); ++i)
+    if (best_ms[i] < best_ms[best]) best = i;
   p->flags = saved_flags;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
