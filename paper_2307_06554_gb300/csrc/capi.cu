@@ -298,7 +298,7 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     return rc;
   }
   if (p->flags & POLYMUL_FLAG_TUNE) {
-    const uint64_t tb = opts && opts->reserved[0] ? opts->reserved[0] : 1024;
+    const uint64_t tb = opts && opts->tune_batch ? opts->tune_batch : 1024;
     rc = polymul_tune(p, tb, nullptr);
     if (rc != POLYMUL_OK) {
       std::string keep = g_err;
