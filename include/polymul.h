@@ -86,7 +86,8 @@ typedef struct polymul_plan_info {
     uint32_t radix_bits;  /* NTT path: stage bits per register pass           */
     uint32_t candidates;  /* kernels the autotuner chooses among              */
     uint32_t tuned;       /* 1 once polymul_tune has chosen                   */
-    uint32_t reserved[2];
+    uint32_t tuned_batch; /* batch bucket of that choice (0: not tuned)       */
+    uint32_t reserved[1];
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */

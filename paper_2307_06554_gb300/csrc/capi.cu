@@ -348,6 +348,7 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->radix_bits = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.rb : 0;
   info->candidates = (uint32_t)p->cands.size();
   info->tuned = p->tuned ? 1u : 0u;
+  info->tuned_batch = (uint32_t)p->tuned_batch;
   return POLYMUL_OK;
 }
 

@@ -33,6 +33,7 @@ struct polymul_plan {
   std::vector<PlanCandidate> cands;  // [0] is the default
   size_t chosen = 0;
   bool tuned = false;
+  uint64_t tuned_batch = 0;  // batch bucket of the tuned choice
   void* d_tpc = nullptr;  // tensor-path constants
   uint64_t* d_q = nullptr;  // moduli on the device (input validation)
   // auxiliary-prime NTT (moduli without a 2n-th root of unity)

@@ -76,6 +76,7 @@ extern "C" int polymul_tune(polymul_plan* p, uint64_t batch, void* stream) {
   if (batch == 0) return fail(POLYMUL_EINVAL, "batch must be positive");
   if (p->cands.size() <= 1) {
     p->tuned = true;
+    p->tuned_batch = batch;
     return POLYMUL_OK;
   }
   cudaDeviceProp prop;
@@ -97,6 +98,7 @@ extern "C" int polymul_tune(polymul_plan* p, uint64_t batch, void* stream) {
       if (label_of(p->cands[i]) == hit->second) {
         apply_candidate(p, i);
         p->tuned = true;
+        p->tuned_batch = bucket;
         return POLYMUL_OK;
       }
   }
@@ -171,6 +173,7 @@ extern "C" int polymul_tune(polymul_plan* p, uint64_t batch, void* stream) {
   apply_candidate(p, rc == POLYMUL_OK ? best : saved_chosen);
   if (rc != POLYMUL_OK) return rc;
   p->tuned = true;
+  p->tuned_batch = bucket;
   store_cache(key, label_of(p->cands[best]));
   return POLYMUL_OK;
 }

@@ -51,7 +51,7 @@ def test_every_candidate_is_exact(pm, n, bits, elem):
 def test_tune_chooses_and_stays_exact(pm):
     w = wl.ring_1024(batch=64, seed=31)
     with pm.Plan(w.n, w.q_list, flags=pm.FLAG_TUNE, tune_batch=4096) as plan:
-        assert plan.info["tuned"] == 1
+        assert plan.info["tuned"] == 1 and plan.info["tuned_batch"] == 4096
         got = run_plan_batch(plan, w.a, w.b)
     assert_equal_residues(got, native.polymul_batch(w.a, w.b, w.q_list), "tuned")
 
