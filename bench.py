@@ -71,6 +71,30 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate_over_ranks(durations, device=None):
+    """Per-rank durations -> their maximum over all ranks, element-wise.
+
+    The job is done when its slowest rank is; with one process (or no
+    initialised process group) the durations come back unchanged.  The
+    all-reduce runs on ``device`` (a CUDA device under NCCL, the CPU under
+    gloo)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x) for x in durations], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu().tolist()]
+
+
+def job_rate(units_per_rank: float, seconds: float, world_size: int) -> float:
+    """Whole-job throughput of independent replicas: every rank processes
+    ``units_per_rank`` units, the job takes the slowest rank's ``seconds``."""
+    if seconds <= 0:
+        raise ValueError("non-positive duration")
+    return units_per_rank * world_size / seconds
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -502,15 +526,11 @@ def run_ours(args, ws, rank, local):
         tw = native.polymul_batch(w.a[[0, 4095]], w.b[[0, 4095]], q_list)
         tensor["bit_exact_sample"] = bool(np.array_equal(tensor.pop("_check"), tw))
 
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    elapsed_ms, e2e_s = aggregate_over_ranks([elapsed_ms, e2e_s], device=dev)
     if rank != 0:
         return
-    products = batch * args.steps * ws
-    value = products / (elapsed_ms / 1e3)
-    e2e_value = batch * e2e_steps / e2e_s * ws
+    value = job_rate(batch * args.steps, elapsed_ms / 1e3, ws)
+    e2e_value = job_rate(batch * e2e_steps, e2e_s, ws)
 
     peaks, peak_src = _peaks()
     launch_ms = statistics.mean(per)
