@@ -197,7 +197,33 @@ def _recorded_traffic(kernel_tag: str):
     return None
 
 
-# ------------------------------------------------------------------ CPU oracle
+# ------------------------------------------------------------------ CPU oracle leg
+class Samples:
+    """GPU outputs of sampled products, kept for the CPU oracle leg to check
+    (the GPU legs never call the oracle themselves)."""
+
+    def __init__(self):
+        self.rows = []    # (name, a [m][k][n], b [m][k][n], q_list, got [m][k][n])
+        self.coeffs = []  # (name, a [n], b [n], q, coefficient indices, got)
+
+    def add(self, name, a, b, q_list, got):
+        self.rows.append((name, np.asarray(a), np.asarray(b), list(q_list), np.asarray(got, dtype=np.uint64)))
+
+    def add_coeffs(self, name, a, b, q, js, got):
+        self.coeffs.append((name, np.asarray(a), np.asarray(b), int(q), list(js), np.asarray(got, dtype=np.uint64)))
+
+    def check(self):
+        """name -> every sample of that name equals the oracle's result."""
+        from oracle import native
+        ok = {}
+        for name, a, b, q_list, got in self.rows:
+            want = native.polymul_batch(a, b, q_list)
+            ok[name] = ok.get(name, True) and bool(np.array_equal(got.reshape(want.shape), want))
+        for name, a, b, q, js, got in self.coeffs:
+            ok[name] = ok.get(name, True) and bool(np.array_equal(got, native.coeffs(a, b, q, js)))
+        return ok
+
+
 def cpu_oracle_rate(w, seconds: float, max_products: int = None):
     """The oracle as it stands (plain C schoolbook, one thread per host core)
     on whole batches of the workload, repeated until ``seconds`` elapsed."""
@@ -236,14 +262,13 @@ def _time_steps(step, stream, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def other_workloads(dev, stream, peaks, alu_peak_g):
+def other_workloads(dev, stream, peaks, alu_peak_g, samples):
     """Throughput of the other standing workloads (not the headline line):
     n=256 q=3329 (auxiliary-prime NTT, launch-latency bound), n=4096 with 8
     RNS primes and ternary b, and the 2000-product uneven list (one
     persistent launch replayed as a CUDA graph)."""
     import torch
     from paper_2307_06554_gb300 import polymul, workloads as wl
-    from oracle import native
     out = {}
     sp = stream.cuda_stream
     hbm = peaks["hbm_gbs"]
@@ -264,8 +289,8 @@ def other_workloads(dev, stream, peaks, alu_peak_g):
             step(i)
         ms = _time_steps(step, stream, reps)
         idx = [0, w.batch - 1]
-        got = sets[(reps - 1) % len(sets)][2][idx].cpu().numpy().view(w.a.dtype).astype(np.uint64)
-        ok = bool(np.array_equal(got, native.polymul_batch(w.a[idx], w.b[idx], w.q_list)))
+        got = sets[(reps - 1) % len(sets)][2][idx].cpu().numpy().view(w.a.dtype)
+        samples.add(name, w.a[idx], w.b[idx], w.q_list, got)
         units = w.batch * k
         mm = units * _ntt_mulmods(w.n)
         byts = 3 * units * w.n * elem
@@ -278,7 +303,7 @@ def other_workloads(dev, stream, peaks, alu_peak_g):
         out[name] = {"products_per_s": w.batch / (ms / 1e3), "us_per_step": ms * 1e3, "batch": w.batch,
                      "n": w.n, "k": k, "path": path,
                      "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm,
-                     "bit_exact_sample": ok,
+                     "bit_exact_sample": None,
                      "l2": "inputs rotated over %d buffer sets" % len(sets) if len(sets) > 1 else "L2-resident"}
         plan.close()
 
@@ -305,19 +330,76 @@ def other_workloads(dev, stream, peaks, alu_peak_g):
         polymul.polymul_ragged_status(r.batch, sp)
         p0 = rag.products[0]
         qs = [rag.pool[j] for j in p0.prime_idx]
-        got = tc[:p0.n * len(qs)].cpu().numpy().view(np.uint32).reshape(len(qs), p0.n).astype(np.uint64)
-        ok = bool(np.array_equal(got, native.polymul_batch(p0.a[None], p0.b[None], qs)[0]))
+        got = tc[:p0.n * len(qs)].cpu().numpy().view(np.uint32).reshape(1, len(qs), p0.n)
+        samples.add("ragged_2000", p0.a[None], p0.b[None], qs, got)
         mm = sum(len(p.prime_idx) * _ntt_mulmods(p.n) for p in rag.products)
         out["ragged_2000"] = {"products_per_s": len(rag.products) / (ms / 1e3), "us_per_launch": ms * 1e3,
                               "units": r.info["units"], "work_items": r.info["items"], "grid": r.info["grid"],
                               "path": "ntt, one persistent launch replayed as a CUDA graph",
                               "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g,
                               "hbm_frac": 3 * total * 4 / (ms / 1e3) / 1e9 / hbm,
-                              "bit_exact_sample": ok, "l2": "inputs 1.3 GB (> L2)"}
+                              "bit_exact_sample": None, "l2": "inputs 1.3 GB (> L2)"}
     return out
 
 
-def serving(dev, peaks, count=20000, lanes=8):
+def crossover(dev, stream, peaks, alu_peak_g, samples):
+    """Tensor (Toeplitz) path against the NTT path on the same inputs, for
+    every shape the tensor kernel covers: n in {1024, 2048} and 2..4 digits
+    per coefficient (prime sizes chosen to need that many digits).  Inputs:
+    seed 6, uniform residues, operands rotated over buffer sets larger than
+    L2.  Both paths must agree on every coefficient of the batch."""
+    import torch
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+    rng = np.random.default_rng(6)
+    shapes = [(1024, 12289), (1024, wl.draw_primes(rng, 1, 23, 23, 11)[0]),
+              (1024, wl.draw_primes(rng, 1, 30, 30, 11)[0]), (2048, 12289),
+              (2048, wl.draw_primes(rng, 1, 20, 20, 12)[0])]
+    sp = stream.cuda_stream
+    rows = []
+    for n, q in shapes:
+        batch = 4096 * 1024 // n
+        a = wl.uniform_coeffs(rng, batch, [q], n)
+        b = wl.uniform_coeffs(rng, batch, [q], n)
+        ta = torch.from_numpy(a.view(np.int32)).to(dev)
+        tb = torch.from_numpy(b.view(np.int32)).to(dev)
+        nsets = max(2, math.ceil(3 * L2_BYTES / (3 * batch * n * 4)))
+        sets = [(ta.clone(), tb.clone(), torch.empty_like(ta)) for _ in range(nsets)]
+        row = {"n": n, "q": q, "q_bits": q.bit_length(), "batch": batch}
+        outs = {}
+        for name, path, flags in (("ntt", polymul.PATH_NTT, polymul.FLAG_TUNE), ("tensor", polymul.PATH_TENSOR, 0)):
+            plan = polymul.Plan(n, [q], path=path, flags=flags, tune_batch=batch)
+
+            def step(i, h=plan.handle):
+                x, y, z = sets[i % nsets]
+                polymul.polymul_batch(h, x, y, z, batch, sp)
+            for i in range(3):
+                step(i)
+            ms = _time_steps(step, stream, 20)
+            info = plan.info
+            row[name + "_us"] = ms * 1e3
+            row[name + "_products_per_s"] = batch / (ms / 1e3)
+            if name == "tensor":
+                row["digit_bits"], row["digits"] = info["digit_bits"], info["digits"]
+                flops = 2.0 * n * n * info["digits"] ** 2 * batch
+                row["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
+            else:
+                row["ntt_alu_frac"] = batch * _ntt_mulmods(n) / (ms / 1e3) / 1e9 / alu_peak_g
+            c = torch.empty_like(ta)
+            polymul.polymul_batch(plan.handle, ta, tb, c, batch, sp)
+            stream.synchronize()
+            outs[name] = c
+            plan.close()
+        row["tensor_over_ntt"] = row["ntt_us"] / row["tensor_us"]
+        row["paths_agree"] = bool(torch.equal(outs["ntt"], outs["tensor"]))
+        samples.add("crossover", a[[0, batch - 1]], b[[0, batch - 1]], [q],
+                    outs["tensor"][[0, batch - 1]].cpu().numpy().view(np.uint32))
+        rows.append(row)
+        del sets, outs
+    return {"rows": rows, "bit_exact_sample": None,
+            "tensor_wins_at": [r["n"] for r in rows if r["tensor_over_ntt"] > 1.0]}
+
+
+def serving(dev, peaks, samples, count=20000, lanes=8):
     """The 20k-request serving workload: Poisson arrivals, n uniform over
     4096..65536, 1..32 primes of 59 bits per request (seed 5), operands in
     page-locked host memory.  Operand data: 16 sets of 32 x 65536 words
@@ -328,7 +410,6 @@ def serving(dev, peaks, count=20000, lanes=8):
     frees up).  Latency: a Poisson schedule at 80 % of that throughput."""
     import torch
     from paper_2307_06554_gb300 import polymul, workloads as wl
-    from oracle import native
     pool = wl.serve_pool()
     reqs = wl.serve_requests(count=count)
     nmax, kmax, nsets = 65536, 32, 16
@@ -355,8 +436,7 @@ def serving(dev, peaks, count=20000, lanes=8):
         t0 = time.perf_counter()
         lat = np.array(srv.replay(plist, arrivals))
         el2 = time.perf_counter() - t0
-        # bit-exactness of two requests computed alone, sampled coefficients
-        checks = []
+        # two requests computed alone: sampled coefficients for the oracle leg
         for i in (0, count - 1):
             r = reqs[i]
             a, b = sets[i % nsets]
@@ -367,8 +447,8 @@ def serving(dev, peaks, count=20000, lanes=8):
             bv = b.numpy().view(np.uint64)[:k * n].reshape(k, n)
             cv = c.numpy().view(np.uint64).reshape(k, n)
             js = [0, 1, n // 2, n - 1]
-            checks.append(all(np.array_equal(cv[j, js], native.coeffs(av[j], bv[j], pool[p], js))
-                              for j, p in enumerate(r.prime_idx)))
+            for j, p in enumerate(r.prime_idx):
+                samples.add_coeffs("serve_20k", av[j].copy(), bv[j].copy(), pool[p], js, cv[j, js])
     return {"requests": len(plist), "units": units, "lanes": lanes, "arena_bytes": 8 << 30,
             "bytes_moved": byts,
             "saturated": {"products_per_s": len(plist) / el, "units_per_s": units / el, "seconds": el,
@@ -377,7 +457,7 @@ def serving(dev, peaks, count=20000, lanes=8):
             "poisson_0.8": {"offered_per_s": rate, "achieved_per_s": len(plist) / el2,
                             "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
                             "mean_us": float(lat.mean())},
-            "bit_exact_sample": bool(all(checks)),
+            "bit_exact_sample": None,
             "data": "16 page-locked operand sets (values < 2^58, canonical for every pool prime)"}
 
 
@@ -450,15 +530,21 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
     ev0.record(stream)
     for i in range(args.steps):
         step(args.warmup + i)
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
-    # per-launch durations of the dominant kernel (one launch per step)
+    # the dominant kernel's average launch duration over the timed region
+    # (one launch per step, back to back on the launching stream)
+    launch_ms = elapsed_ms / args.steps
+    # and, for reference, launches timed one at a time (each bracketed by
+    # its own events and a synchronisation, so each starts cold)
     per = []
     for i in range(min(args.steps, 20)):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -492,7 +578,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         t_ms = t0e.elapsed_time(t1e) / args.steps
         tc_last = sets[(args.steps - 1) % nsets][2]
-        t_got = tc_last[[0, 4095]].cpu().numpy().view(np.uint32).astype(np.uint64)
+        t_got = tc_last[[0, 4095]].cpu().numpy().view(np.uint32)
         tinfo = tplan.info
         tensor = {"ms_per_step": t_ms, "value": batch / (t_ms / 1e3), "unit": "products/s",
                   "kernel": "k_toeplitz_batch (tcgen05 kind::f16, bf16 digits, fp32 TMEM accumulators)",
@@ -514,17 +600,14 @@ def run_ours(args, ws, rank, local):
     e2e_s = time.perf_counter() - t0
     clk = clocks.stop()
 
-    # bit-exactness on a seeded sample of the batch (oracle, CPU)
+    # sampled products of the timed batch, checked by the CPU oracle leg
+    samples = Samples()
     c_last = sets[(args.warmup + args.steps - 1) % nsets][2]
     idx = [0, 1, 2047, 4095]
-    got = c_last[idx].cpu().numpy().view(np.uint32).astype(np.uint64)
-    from oracle import native
-    want = native.polymul_batch(w.a[idx], w.b[idx], q_list)
-    host_ok = bool(np.array_equal(hc.numpy().view(np.uint32)[idx].astype(np.uint64), want))
-    bit_exact = bool(np.array_equal(got, want)) and host_ok
+    samples.add("ring_1024", w.a[idx], w.b[idx], q_list, c_last[idx].cpu().numpy().view(np.uint32))
+    samples.add("ring_1024", w.a[idx], w.b[idx], q_list, hc.numpy().view(np.uint32)[idx])
     if tensor is not None:
-        tw = native.polymul_batch(w.a[[0, 4095]], w.b[[0, 4095]], q_list)
-        tensor["bit_exact_sample"] = bool(np.array_equal(tensor.pop("_check"), tw))
+        samples.add("ring_1024_tensor", w.a[[0, 4095]], w.b[[0, 4095]], q_list, tensor.pop("_check"))
 
     elapsed_ms, e2e_s = aggregate_over_ranks([elapsed_ms, e2e_s], device=dev)
     if rank != 0:
@@ -533,7 +616,7 @@ def run_ours(args, ws, rank, local):
     e2e_value = job_rate(batch * e2e_steps, e2e_s, ws)
 
     peaks, peak_src = _peaks()
-    launch_ms = statistics.mean(per)
+    isolated_ms = statistics.mean(per)
     units = batch * len(q_list)
     mulmods = units * _ntt_mulmods(n)
     bytes_alg = 3 * units * n * elem
@@ -550,6 +633,8 @@ def run_ours(args, ws, rank, local):
             "peak_source": "derived: %d SMs x %d IMAD lanes x %.0f MHz / %d IMAD slots per Shoup mulmod" % (
                 sms, IMAD_LANES_PER_SM, sm_mhz, IMAD_SLOTS_PER_MULMOD),
             "mulmods_per_launch": mulmods, "launch_ms": launch_ms,
+            "launch_ms_source": "CUDA events over the timed region / launches (one per step)",
+            "isolated_launch_ms": isolated_ms,
             "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
                     "bytes_per_launch": bytes_alg, "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src}}
 
@@ -566,14 +651,25 @@ def run_ours(args, ws, rank, local):
 
     extras = None
     if not args.no_extras:
-        extras = other_workloads(dev, stream, peaks, alu_peak)
-        extras["serve_20k"] = serving(dev, peaks)
+        extras = other_workloads(dev, stream, peaks, alu_peak, samples)
+        extras["crossover"] = crossover(dev, stream, peaks, alu_peak, samples)
+        extras["serve_20k"] = serving(dev, peaks, samples)
 
-    cpu = None
+    # CPU oracle leg: its throughput (the CPU baseline) and its verdict on
+    # the sampled GPU outputs; skipped with --no-cpu-baseline (verdicts null)
+    cpu, verdict = None, {}
     if not args.no_cpu_baseline:
         rate, cores, done, el = cpu_oracle_rate(w, args.cpu_seconds)
         cpu = {"value": rate, "unit": "products/s", "cores": cores, "kind": "oracle",
                "sample": "%d products (whole 4096-product batches, repeated) in %.1f s, plain C schoolbook" % (done, el)}
+        verdict = samples.check()
+    bit_exact = verdict.get("ring_1024")
+    if tensor is not None:
+        tensor["bit_exact_sample"] = verdict.get("ring_1024_tensor")
+    if extras is not None:
+        for name, x in extras.items():
+            if isinstance(x, dict) and "bit_exact_sample" in x:
+                x["bit_exact_sample"] = verdict.get(name)
 
     out = {
         "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": ws, "steps": args.steps,
