@@ -87,7 +87,11 @@ typedef struct polymul_plan_info {
     uint32_t candidates;  /* kernels the autotuner chooses among              */
     uint32_t tuned;       /* 1 once polymul_tune has chosen                   */
     uint32_t tuned_batch; /* batch bucket of that choice (0: not tuned)       */
-    uint32_t reserved[1];
+    uint32_t launch_flags;/* bit 1: the main kernel takes a programmatic
+                             dependent launch (its CTAs start as the previous
+                             kernel on the stream drains and wait for it to
+                             complete before touching memory); set for the
+                             NTT batch kernels                              */
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */

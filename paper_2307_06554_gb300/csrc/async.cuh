@@ -65,4 +65,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// Programmatic dependent launch.  launch_dependents: the next kernel on the
+// stream (if launched with programmatic stream serialisation) may start its
+// CTAs as resources free up.  wait: block until the previous kernel on the
+// stream has completed and its memory operations are visible; a no-op for a
+// kernel launched without that attribute.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace pm

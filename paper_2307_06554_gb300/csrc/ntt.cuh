@@ -453,6 +453,9 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
   const uint32_t k = args.k;
   unsigned long long* ctr = args.ctr;
   constexpr uint32_t ROW = S::N * (uint32_t)sizeof(W);
+  // every CTA of this grid is resident from the start (persistent grid), so
+  // the next kernel may claim SM resources as soon as CTAs of this one exit
+  griddep_launch_dependents();
   if constexpr (S::T <= 32) {
     constexpr int TPW = 32 / S::T;  // teams per warp
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -480,6 +483,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       }
     };
     uint32_t parity = 0;
+    griddep_wait();  // the work counter, operands and results of the previous kernel
     unsigned long long cur = grab();
     if (lane == 0 && cur < units) issue(cur);
     while (cur < units) {
@@ -520,6 +524,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     uint64_t* bar = &mbar[0];
     if (threadIdx.x == 0) mbar_init(bar, 1);
     fence_mbar_init();
+    griddep_wait();  // the work counter, operands and results of the previous kernel
     auto issue = [&](unsigned long long u) {  // thread 0 only
       fence_proxy_async();
       mbar_arrive_expect_tx(bar, 2 * ROW);

@@ -12,7 +12,10 @@ struct PlanCandidate {
   uint32_t path;     // POLYMUL_PATH_NTT or POLYMUL_PATH_TENSOR
   pm::KernelInfo ki;
   int grid_cap;
+  uint32_t launch_flags = 0;  // kLaunchPdl for the NTT batch kernels
 };
+
+constexpr uint32_t kLaunchPdl = 2u;  // programmatic dependent launch
 
 struct polymul_plan {
   uint32_t n = 0, logn = 0, k = 0;
@@ -41,6 +44,7 @@ struct polymul_plan {
   pm::KernelInfo aki;
   void* d_outer = nullptr;  // the ring moduli as words [k]
   int grid_cap = 0;    // resident CTAs of ki (persistent grid)
+  uint32_t launch_flags = 0;
   int* d_flag = nullptr;
   unsigned long long* d_ctr = nullptr;  // 3 x {next, finished}: device entry, 2 host streams
   int* d_err = nullptr;                 // set by kernels whose bounded waits expired
@@ -56,6 +60,7 @@ inline void apply_candidate(polymul_plan* p, size_t i) {
   p->path = p->cands[i].path;
   p->ki = p->cands[i].ki;
   p->grid_cap = p->cands[i].grid_cap;
+  p->launch_flags = p->cands[i].launch_flags;
 }
 
 extern "C" int polymul_tune(polymul_plan* plan, uint64_t batch, void* stream);

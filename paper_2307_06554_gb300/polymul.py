@@ -46,8 +46,8 @@ class polymul_opts(ctypes.Structure):
 class polymul_plan_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
-                 "digit_bits", "digits", "radix_bits", "candidates", "tuned", "tuned_batch")] + \
-        [("reserved", ctypes.c_uint32 * 1)]
+                 "digit_bits", "digits", "radix_bits", "candidates", "tuned", "tuned_batch",
+                 "launch_flags")]
 
 
 class polymul_desc(ctypes.Structure):

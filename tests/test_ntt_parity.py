@@ -185,3 +185,33 @@ def test_other_stream_and_reuse(pm):
         s.synchronize()
         got = from_dev(tc, np.uint32)
     assert_equal_residues(got, native.polymul_batch(a, b, q_list), "stream")
+
+
+@pytest.mark.parametrize("n,batch", [(1024, 3000), (256, 64), (4096, 300)])
+def test_chained_batches_on_one_stream(pm, n, batch):
+    """Each launch reads the previous launch's results (the batch kernels take
+    a programmatic dependent launch: a dependent kernel may start while the
+    previous one drains, and must still see all of its results), with a
+    foreign kernel interleaved, all on one stream without synchronisation."""
+    import torch
+    q_list = [12289] if n <= 1024 else _primes(77, 1, 30, 2 * n)
+    a, b = _case(900 + n, batch, q_list, n, np.uint32)
+    stream = torch.cuda.Stream()
+    with pm.Plan(n, q_list) as plan, torch.cuda.stream(stream):
+        assert plan.info["launch_flags"] & 2
+        x, y = to_dev(a), to_dev(b)
+        outs = []
+        for i in range(4):
+            z = torch.empty_like(x)
+            plan.batch(x, y, z, stream=stream.cuda_stream)
+            if i == 1:
+                z = z.clone()  # a torch kernel between two dependent launches
+            outs.append(z)
+            x = z
+        stream.synchronize()
+        polymul_status = pm.polymul_plan_status(plan.handle, stream.cuda_stream)
+    assert polymul_status is None
+    want = a
+    for i in range(4):
+        want = native.polymul_batch(want.astype(np.uint32), b, q_list)
+        assert_equal_residues(from_dev(outs[i], np.uint32), want, "link %d" % i)

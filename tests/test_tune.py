@@ -70,3 +70,14 @@ def test_tune_cache_file_is_written_and_reused(pm, tmp_path):
     assert len(cache.read_text().strip().splitlines()) == 1  # the second process used the cache
     i1, i2 = json.loads(r1.stdout.strip()), json.loads(r2.stdout.strip())
     assert (i1["path"], i1["radix_bits"]) == (i2["path"], i2["radix_bits"])
+
+
+def test_launch_flags(pm):
+    """NTT batch kernels take a programmatic dependent launch; the tensor and
+    cluster kernels take plain launches."""
+    with pm.Plan(1024, [12289], path=pm.PATH_NTT) as plan:
+        assert plan.info["launch_flags"] == 2
+    with pm.Plan(1024, [12289], path=pm.PATH_TENSOR) as plan:
+        assert plan.info["launch_flags"] == 0
+    with pm.Plan(16384, wl.draw_primes(np.random.default_rng(3), 1, 30, 30, 15)) as plan:
+        assert plan.info["launch_flags"] == 0
