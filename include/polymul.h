@@ -92,6 +92,13 @@ typedef struct polymul_plan_info {
                              kernel on the stream drains and wait for it to
                              complete before touching memory); set for the
                              NTT batch kernels                              */
+    uint32_t ntt_mode;    /* NTT path: reduction mode of the main kernel:
+                             0 = values in [0, 2q), 1 = [0, 4q) (Harvey),
+                             2 = unreduced (small q), 3 = [0, 4q) with 16-bit
+                             Shoup quotients (q < 2^14)                     */
+    uint32_t regs;        /* NTT path: register budget per thread of the main
+                             kernel (fewer registers, more resident warps)  */
+    uint32_t reserved[2];
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */

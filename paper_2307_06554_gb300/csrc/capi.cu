@@ -282,6 +282,9 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb5((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && p->elem == 8 && lookup_ntt_u64_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
+    // primes below 2^14: Harvey bounds with 16-bit Shoup quotients (same tables)
+    if (rc == POLYMUL_OK && p->elem == 4 && qmax < (1u << 14) && lookup_ntt_u32_m3((int)p->logn, &v))
+      rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) {
       rc = upload_tensor_tables(p);
       if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
@@ -354,6 +357,8 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->tuned = p->tuned ? 1u : 0u;
   info->tuned_batch = (uint32_t)p->tuned_batch;
   info->launch_flags = p->launch_flags;
+  info->ntt_mode = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.mode : 0u;
+  info->regs = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.regs : 0u;
   return POLYMUL_OK;
 }
 

@@ -14,13 +14,16 @@ struct KernelInfo {
   int tmem_cols = 0;         // tensor-memory columns allocated per CTA (0: none)
   int cluster = 0;           // CTAs per thread-block cluster (0: no cluster launch)
   int rb = 0;                // NTT: stage bits per register pass
+  int mode = 0;              // NTT: reduction mode (0..3, see ntt.cuh)
+  int regs = 0;              // NTT: register budget per thread
 };
 
 // batched negacyclic NTT, k_ntt_batch<W, LOGN, MODE> (MODE: 0 = kQ31,
-// 1 = kL4, 2 = kSmall; see ntt.cuh)
+// 1 = kL4, 2 = kSmall, 3 = kS16; see ntt.cuh)
 bool lookup_ntt_u32_m0(int logn, KernelInfo* ki);  // logn 4..14
 bool lookup_ntt_u32_m1(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_m2(int logn, KernelInfo* ki);
+bool lookup_ntt_u32_m3(int logn, KernelInfo* ki);  // logn 4..12, q < 2^14
 bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
 bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_aux(int logn, KernelInfo* ki);  // auxiliary-prime mode, logn 4..14

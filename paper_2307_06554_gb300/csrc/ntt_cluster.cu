@@ -124,6 +124,8 @@ static KernelInfo cluster_info() {
   ki.units_per_cta = 1;
   ki.cluster = S::T / kClusterThreads;
   ki.rb = 4;
+  ki.mode = MODE;
+  ki.regs = 65536 / kClusterThreads;
   return ki;
 }
 

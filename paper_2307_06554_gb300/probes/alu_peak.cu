@@ -26,6 +26,7 @@ __global__ void k_probe(uint64_t* out, uint64_t w, uint64_t wp, uint64_t q, int 
         if (OP == 1) x[j] = __umulhi(x[j], wp32) ^ x[j];                             // IMAD.HI (+LOP)
         if (OP == 2) x[j] = x[j] * w32 - __umulhi(x[j], wp32) * q32;                 // 32-bit Shoup
         if (OP == 3) y[j] = y[j] * w - __umul64hi(y[j], wp) * q;                     // 64-bit Shoup
+        if (OP == 4) x[j] = x[j] * w32 - ((x[j] * wp32) >> 16) * q32;                // Shoup, 16-bit quotient
       }
   }
   uint64_t r = 0;
@@ -44,13 +45,14 @@ int main() {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const double ops = (double)threads * blocks * iters * UNROLL * CHAINS;
-  const char* names[] = {"imad32", "imad32_hi", "shoup32_mulmod", "shoup64_mulmod"};
+  const char* names[] = {"imad32", "imad32_hi", "shoup32_mulmod", "shoup64_mulmod", "shoup16q_mulmod"};
   // 12289 with w = 5000; 59-bit prime 288230376151760897 with w = 2^40 + 7
   const uint64_t W32 = 5000, WP32 = (uint64_t)((5000ull << 32) / 12289), Q32 = 12289;
   const uint64_t Q64 = 288230376151760897ull, W64 = (1ull << 40) + 7;
   const uint64_t WP64 = (uint64_t)(((unsigned __int128)W64 << 64) / Q64);
   printf("{\"sms\": %d, \"results\": [", sms);
-  for (int op = 0; op < 4; ++op) {
+  const uint64_t WP16 = (5000ull << 16) / 12289;  // x stays below 2q < 2^16 along each chain
+  for (int op = 0; op < 5; ++op) {
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0);
@@ -58,6 +60,7 @@ int main() {
       if (op == 1) k_probe<1><<<blocks, threads>>>(out, W32, WP32, Q32, iters);
       if (op == 2) k_probe<2><<<blocks, threads>>>(out, W32, WP32, Q32, iters);
       if (op == 3) k_probe<3><<<blocks, threads>>>(out, W64, WP64, Q64, iters / 4);
+      if (op == 4) k_probe<4><<<blocks, threads>>>(out, W32, WP16, Q32, iters);
       cudaEventRecord(e1);
       cudaEventSynchronize(e1);
       float ms = 0;

@@ -25,8 +25,8 @@ def pm():
     return polymul
 
 
-@pytest.mark.parametrize("n,bits,elem", [(512, 14, 4), (1024, 14, 4), (2048, 30, 4), (4096, 29, 4), (8192, 20, 4),
-                                         (1024, 59, 8), (4096, 59, 8)])
+@pytest.mark.parametrize("n,bits,elem", [(16, 14, 4), (256, 14, 4), (512, 14, 4), (1024, 14, 4), (2048, 14, 4),
+                                         (2048, 30, 4), (4096, 29, 4), (8192, 20, 4), (1024, 59, 8), (4096, 59, 8)])
 def test_every_candidate_is_exact(pm, n, bits, elem):
     rng = np.random.default_rng(n + bits)
     if bits == 14:
@@ -43,7 +43,7 @@ def test_every_candidate_is_exact(pm, n, bits, elem):
         labels = []
         for i in range(ncand):
             info = plan.select(i)
-            labels.append((info["path"], info["radix_bits"]))
+            labels.append((info["path"], info["radix_bits"], info["ntt_mode"], info["regs"]))
             assert_equal_residues(run_plan_batch(plan, a, b), want, "candidate %d %s" % (i, labels[-1]))
     assert len(set(labels)) == ncand
 
