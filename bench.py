@@ -49,7 +49,10 @@ IMAD_LANES_PER_SM = 64
 # low product (1), multiply-subtract (1).  Peak = 16 mulmod/clk/SM, which a
 # dependency-free microbenchmark of the same sequence reproduces (5.02e12/s
 # at 2070 MHz on 152 SMs).
-IMAD_SLOTS_PER_MULMOD = 4
+# The 16-bit-quotient variant (NTT mode 3, q < 2^14) replaces the high
+# product by a low product and a shift: 3 slots, 21.3 mulmod/clk/SM measured.
+IMAD_SLOTS_PER_MULMOD = {0: 4, 1: 4, 2: 4, 3: 3}
+MODE_NAMES = {0: "[0,2q)", 1: "[0,4q)", 2: "small-q", 3: "[0,4q) 16-bit quotients"}
 
 
 def _args():
@@ -249,6 +252,12 @@ def _ntt_mulmods(n: int) -> int:
     return 3 * (n // 2) * int(math.log2(n)) + n + n // 2
 
 
+def _mode_peak(alu_peak_g, info):
+    """ALU peak (Gmulmod/s) for the modular multiplication sequence of the
+    plan's NTT mode (alu_peak_g is the 4-slot Shoup peak)."""
+    return alu_peak_g * IMAD_SLOTS_PER_MULMOD[0] / IMAD_SLOTS_PER_MULMOD[info["ntt_mode"]]
+
+
 def _time_steps(step, stream, reps):
     import torch
     e0 = torch.cuda.Event(enable_timing=True)
@@ -302,7 +311,8 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
                                                                      plan.info["candidates"])
         out[name] = {"products_per_s": w.batch / (ms / 1e3), "us_per_step": ms * 1e3, "batch": w.batch,
                      "n": w.n, "k": k, "path": path,
-                     "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm,
+                     "alu_frac": mm / (ms / 1e3) / 1e9 / _mode_peak(alu_peak_g, plan.info),
+                     "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm,
                      "bit_exact_sample": None,
                      "l2": "inputs rotated over %d buffer sets" % len(sets) if len(sets) > 1 else "L2-resident"}
         plan.close()
@@ -383,7 +393,7 @@ def crossover(dev, stream, peaks, alu_peak_g, samples):
                 flops = 2.0 * n * n * info["digits"] ** 2 * batch
                 row["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
             else:
-                row["ntt_alu_frac"] = batch * _ntt_mulmods(n) / (ms / 1e3) / 1e9 / alu_peak_g
+                row["ntt_alu_frac"] = batch * _ntt_mulmods(n) / (ms / 1e3) / 1e9 / _mode_peak(alu_peak_g, info)
             c = torch.empty_like(ta)
             polymul.polymul_batch(plan.handle, ta, tb, c, batch, sp)
             stream.synchronize()
@@ -505,6 +515,7 @@ def run_ours(args, ws, rank, local):
     # the autotuned kernel for this shape (tuning runs before the timed region)
     plan = polymul.Plan(n, q_list, flags=polymul.FLAG_TUNE, tune_batch=batch)
     info = plan.info
+    assert info["path"] == polymul.PATH_NTT, "the roofline below describes the NTT kernel"
     elem = info["elem_bytes"]
     set_bytes = 3 * batch * len(q_list) * n * elem
     nsets = max(2, math.ceil(3 * L2_BYTES / set_bytes))
@@ -622,16 +633,19 @@ def run_ours(args, ws, rank, local):
     bytes_alg = 3 * units * n * elem
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = sms * IMAD_LANES_PER_SM * sm_mhz * 1e6 / IMAD_SLOTS_PER_MULMOD / 1e9  # Gmulmod/s
+    mode = info["ntt_mode"]
+    slots = IMAD_SLOTS_PER_MULMOD[mode]
+    alu_peak = sms * IMAD_LANES_PER_SM * sm_mhz * 1e6 / slots / 1e9  # Gmulmod/s
     alu_ach = mulmods / (launch_ms / 1e3) / 1e9
     hbm_ach = bytes_alg / (launch_ms / 1e3) / 1e9
     hbm_peak = peaks["hbm_gbs"]
-    traffic = _recorded_traffic("k_ntt_batch<u32,logn=10,small-q,RB=4>")
+    tag = "k_ntt_batch<u32,logn=10,%s,RB=%d>" % (MODE_NAMES[mode], info["radix_bits"])
+    traffic = _recorded_traffic(tag)
     roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Gmulmod/s",
             "frac": alu_ach / alu_peak, "traffic": traffic,
-            "kernel": "k_ntt_batch<u32,logn=10,small-q,RB=4> (forward x2, pointwise, inverse; one launch per step)",
+            "kernel": tag + " (forward x2, pointwise, inverse; one launch per step)",
             "peak_source": "derived: %d SMs x %d IMAD lanes x %.0f MHz / %d IMAD slots per Shoup mulmod" % (
-                sms, IMAD_LANES_PER_SM, sm_mhz, IMAD_SLOTS_PER_MULMOD),
+                sms, IMAD_LANES_PER_SM, sm_mhz, slots),
             "mulmods_per_launch": mulmods, "launch_ms": launch_ms,
             "launch_ms_source": "CUDA events over the timed region / launches (one per step)",
             "isolated_launch_ms": isolated_ms,
@@ -676,7 +690,8 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded uniform residues)",
         "config": {"workload": WORKLOAD, "path": {1: "ntt", 2: "tensor"}.get(info["path"], "?"),
-                   "autotuned": {"candidates": info["candidates"], "radix_bits": info["radix_bits"]},
+                   "autotuned": {"candidates": info["candidates"], "radix_bits": info["radix_bits"],
+                                 "ntt_mode": MODE_NAMES[info["ntt_mode"]], "launch_flags": info["launch_flags"]},
                    "n": n, "q": q_list, "batch": batch,
                    "l2": "inputs rotated over %d buffer sets (%.0f MB > 3x L2)" % (nsets, nsets * set_bytes / 2**20),
                    "parallelism": "replicas" if ws > 1 else "single"},
