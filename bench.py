@@ -252,6 +252,26 @@ def _ntt_mulmods(n: int) -> int:
     return 3 * (n // 2) * int(math.log2(n)) + n + n // 2
 
 
+# Shared-memory bytes a tcgen05 MMA of the tensor path reads per instruction:
+# the A slice (128 rows x 16 bf16) and the B slice (N rows x 16 bf16).  The
+# A operand is the aliased Hankel view of a's digits, re-read by every MMA,
+# so shared-memory bandwidth (128 B/clk/SM, nominal) bounds the path before
+# the tensor pipe does.
+SMEM_BYTES_PER_CLK_SM = 128
+
+
+def _tensor_smem_roofline(n, digits, units, seconds, sms, sm_mhz):
+    nb = (8 * digits + 15) // 16 * 16
+    mmas = digits * (n // 1024) * (n // 16)  # per unit: digits of a x row blocks x K steps
+    byts = units * mmas * (128 * 32 + nb * 32)
+    peak = sms * SMEM_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
+    ach = byts / seconds / 1e9
+    return {"bound": "smem", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "bytes_per_launch": byts,
+            "peak_source": "derived: %d SMs x %d B/clk x %.0f MHz (shared-memory operand reads of the MMAs)" % (
+                sms, SMEM_BYTES_PER_CLK_SM, sm_mhz)}
+
+
 def _mode_peak(alu_peak_g, info):
     """ALU peak (Gmulmod/s) for the modular multiplication sequence of the
     plan's NTT mode (alu_peak_g is the 4-slot Shoup peak)."""
@@ -392,6 +412,9 @@ def crossover(dev, stream, peaks, alu_peak_g, samples):
                 row["digit_bits"], row["digits"] = info["digit_bits"], info["digits"]
                 flops = 2.0 * n * n * info["digits"] ** 2 * batch
                 row["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
+                row["tensor_frac_smem"] = _tensor_smem_roofline(
+                    n, info["digits"], batch, ms / 1e3, torch.cuda.get_device_properties(dev).multi_processor_count,
+                    peaks.get("sm_max_mhz", 2070.0))["frac"]
             else:
                 row["ntt_alu_frac"] = batch * _ntt_mulmods(n) / (ms / 1e3) / 1e9 / _mode_peak(alu_peak_g, info)
             c = torch.empty_like(ta)
@@ -661,6 +684,7 @@ def run_ours(args, ws, rank, local):
         tensor["roofline"] = {"bound": "tensor", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
                               "frac": ach_tf / peak_tf, "flops_per_launch": flops,
                               "peak_source": "MEASURED_PEAKS.json bf16_tflops burst (%s)" % peak_src}
+        tensor["roofline_smem"] = _tensor_smem_roofline(n, digits[1], units, tensor["ms_per_step"] / 1e3, sms, sm_mhz)
         tensor["vs_ntt"] = tensor["value"] / value
 
     extras = None

@@ -122,8 +122,11 @@ int upload_tensor_tables(polymul_plan* p) {
   std::vector<TensorPrime> tp(p->k);
   for (uint32_t j = 0; j < p->k; ++j) {
     memset(&tp[j], 0, sizeof tp[j]);
-    tp[j].q = (uint32_t)p->q[j];
-    for (int e = 0; e < 15; ++e) tp[j].pw[e] = (int64_t)pm::host::powmod(2, (uint64_t)p->digit_bits * e, p->q[j]);
+    const uint64_t q = p->q[j];
+    tp[j].q = (uint32_t)q;
+    for (int e = 0; e < 15; ++e) tp[j].pw[e] = (uint32_t)pm::host::powmod(2, (uint64_t)p->digit_bits * e, q);
+    tp[j].mu = (uint64_t)(((pm::host::u128)1 << 64) / q);
+    tp[j].bias = ((1ull << 60) + q - 1) / q * q;
   }
   PM_CUDA(cudaMalloc(&p->d_tpc, tp.size() * sizeof(TensorPrime)));
   PM_CUDA(cudaMemcpy(p->d_tpc, tp.data(), tp.size() * sizeof(TensorPrime), cudaMemcpyHostToDevice));

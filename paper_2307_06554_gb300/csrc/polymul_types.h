@@ -74,8 +74,9 @@ struct RaggedArgs {
 // Per-prime constants of the Toeplitz (tensor) path.
 struct alignas(16) TensorPrime {
   uint32_t q;
-  uint32_t pad;
-  int64_t pw[15];  // pw[e] = 2^(w e) mod q: weight of digit pair (s, s') with s + s' = e
+  uint32_t pw[15];  // pw[e] = 2^(w e) mod q: weight of digit pair (s, s') with s + s' = e
+  uint64_t mu;      // floor(2^64 / q), Barrett reduction of the recombined sums
+  uint64_t bias;    // the multiple of q at or just above 2^60 (makes every recombined sum positive)
 };
 
 struct TensorBatchArgs {

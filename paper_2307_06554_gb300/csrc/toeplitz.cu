@@ -46,20 +46,37 @@ struct TShape {
   static constexpr int NCOLS = TCOLS <= 32 ? 32 : TCOLS <= 64 ? 64 : TCOLS <= 128 ? 128 : TCOLS <= 256 ? 256 : 512;
   static constexpr int THREADS = 128;
   static constexpr int CPT = N / THREADS;           // coefficients per thread
+  static constexpr int GPT = CPT / 8;               // 8-coefficient groups per thread
   static constexpr int XA_LEN = 2 * N;              // a~ over [-n, n)
-  static constexpr int XB_LEN = N + 16;             // b~ over [-8, n + 8)
   static constexpr int XA_OFF = 0;
-  static constexpr int XB_OFF = XA_OFF + LA * XA_LEN * 2;
-  static constexpr int BT_OFF = (XB_OFF + LB * XB_LEN * 2 + 127) / 128 * 128;
-  static constexpr int BT_BYTES = NB * N * 2;
+  // B: K-major core matrices; those adjacent along K are BT_PITCH bytes
+  // apart (16 bytes more than the N-groups need, so that the 16-byte
+  // stores of consecutive threads, one K-block each, fall in distinct banks)
+  static constexpr int BT_PITCH = NG * 128 + 16;
+  static constexpr int BT_OFF = (XA_OFF + LA * XA_LEN * 2 + 127) / 128 * 128;
+  static constexpr int BT_BYTES = (N / 8) * BT_PITCH;
   static constexpr int SMEM = BT_OFF + BT_BYTES;
   static_assert(TCOLS <= 512, "accumulators exceed tensor memory");
-  static_assert(N >= 1024 && CPT % 8 == 0, "n >= 1024");
+  static_assert(N >= 1024 && CPT % 8 == 0 && THREADS == 128, "n >= 1024, four warps");
   static_assert(N * (1 << (2 * WB - 2)) <= (1 << 24), "digit width breaks fp32 exactness");
 };
 
-__device__ __forceinline__ uint16_t bf16_bits(int v) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+// bf16 bit pattern of a small integer d (|d| <= 256, so exact in bf16):
+// adding d to the pattern of 1.5 * 2^23 puts d in the units of the
+// mantissa; subtracting 1.5 * 2^23 leaves d exactly as a float, whose top
+// 16 bits are then its bf16 pattern.  Two digits, packed low/high.
+__device__ __forceinline__ uint32_t bf16x2_of(int d0, int d1) {
+  const float f0 = __int_as_float(0x4B400000 + d0) - 12582912.0f;
+  const float f1 = __int_as_float(0x4B400000 + d1) - 12582912.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
+// x mod q for 0 <= x < 2^64 (Barrett, mu = floor(2^64 / q)): the estimate
+// is floor(x / q) or one less.
+__device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t q, uint64_t mu) {
+  const uint64_t qh = __umul64hi(x, mu);
+  const uint32_t r = (uint32_t)(x - qh * q);
+  return r >= q ? r - q : r;
 }
 
 template <class TS>
@@ -69,9 +86,10 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
   __shared__ uint32_t s_tmem;
   __shared__ unsigned long long s_next;
   uint16_t* Xa = reinterpret_cast<uint16_t*>(sm + TS::XA_OFF);
-  uint16_t* Xb = reinterpret_cast<uint16_t*>(sm + TS::XB_OFF);
   unsigned char* Bt = sm + TS::BT_OFF;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  // each warp's last 8 digits of b (per digit slot), for the next warp's first lane
+  __shared__ __align__(16) uint4 s_edge[4][TS::LB];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t units = args.units;
   const uint32_t k = args.k;
   constexpr uint32_t IDESC = idesc_bf16(128, TS::NB);
@@ -86,7 +104,7 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
   // padded rows of B (digit slots >= LB) stay zero for the whole launch
   for (int ch = tid; ch < (TS::N / 8) * TS::NG * 8; ch += TS::THREADS) {
     const int dp = ch / (TS::NG * 8), g = (ch / 8) % TS::NG, v = ch % 8;
-    if (g >= TS::LB) *reinterpret_cast<uint4*>(Bt + (dp * TS::NG + g) * 128 + 16 * v) = make_uint4(0, 0, 0, 0);
+    if (g >= TS::LB) *reinterpret_cast<uint4*>(Bt + dp * TS::BT_PITCH + g * 128 + 16 * v) = make_uint4(0, 0, 0, 0);
   }
   tc_fence_before();
   __syncthreads();
@@ -105,19 +123,21 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
     const uint32_t q = args.tp[j].q;
     const int32_t qh = (int32_t)(q >> 1);
 
-    // ---- ConvertPoly: digits of the centred coefficients ----
+    // ---- ConvertPoly: balanced digits of the centred coefficients, as bf16 ----
+    // thread t holds coefficients [t CPT, (t+1) CPT): groups g = t GPT + gi
     const uint32_t* a = args.a + (size_t)cur * TS::N;
     const uint32_t* b = args.b + (size_t)cur * TS::N;
+    uint4 bw[TS::GPT][TS::LB];  // b's digits of each own group, bf16 pairs
 #pragma unroll
-    for (int e0 = 0; e0 < TS::CPT; e0 += 8) {
-      const int i0 = tid * TS::CPT + e0;
+    for (int gi = 0; gi < TS::GPT; ++gi) {
+      const int i0 = tid * TS::CPT + 8 * gi;
       const uint4 va0 = *reinterpret_cast<const uint4*>(a + i0);
       const uint4 va1 = *reinterpret_cast<const uint4*>(a + i0 + 4);
       const uint4 vb0 = *reinterpret_cast<const uint4*>(b + i0);
       const uint4 vb1 = *reinterpret_cast<const uint4*>(b + i0 + 4);
       const uint32_t av[8] = {va0.x, va0.y, va0.z, va0.w, va1.x, va1.y, va1.z, va1.w};
       const uint32_t bv[8] = {vb0.x, vb0.y, vb0.z, vb0.w, vb1.x, vb1.y, vb1.z, vb1.w};
-      uint16_t pa[TS::LA][8], na[TS::LA][8], pb[TS::LB][8], nb[TS::LB][8];
+      int da[TS::LA][8], db[TS::LB][8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         int32_t x = (int32_t)av[e] > qh ? (int32_t)(av[e] - q) : (int32_t)av[e];
@@ -125,47 +145,74 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
         for (int s = 0; s < TS::LA; ++s) {
           const int32_t d = ((x + HALF) & MASK) - HALF;
           x = (x - d) >> TS::WB;
-          pa[s][e] = bf16_bits(d);
-          na[s][e] = bf16_bits(-d);
+          da[s][e] = d;
         }
         int32_t y = (int32_t)bv[e] > qh ? (int32_t)(bv[e] - q) : (int32_t)bv[e];
 #pragma unroll
         for (int s = 0; s < TS::LB; ++s) {
           const int32_t d = ((y + HALF) & MASK) - HALF;
           y = (y - d) >> TS::WB;
-          pb[s][e] = bf16_bits(d);
-          nb[s][e] = bf16_bits(-d);
+          db[s][e] = d;
         }
       }
 #pragma unroll
       for (int s = 0; s < TS::LA; ++s) {
         uint16_t* xs = Xa + s * TS::XA_LEN;
-        *reinterpret_cast<uint4*>(xs + TS::N + i0) = *reinterpret_cast<const uint4*>(pa[s]);
-        *reinterpret_cast<uint4*>(xs + i0) = *reinterpret_cast<const uint4*>(na[s]);
+        const uint4 p = make_uint4(bf16x2_of(da[s][0], da[s][1]), bf16x2_of(da[s][2], da[s][3]),
+                                   bf16x2_of(da[s][4], da[s][5]), bf16x2_of(da[s][6], da[s][7]));
+        *reinterpret_cast<uint4*>(xs + TS::N + i0) = p;
+        *reinterpret_cast<uint4*>(xs + i0) =
+            make_uint4(p.x ^ 0x80008000u, p.y ^ 0x80008000u, p.z ^ 0x80008000u, p.w ^ 0x80008000u);
       }
 #pragma unroll
-      for (int s = 0; s < TS::LB; ++s) {
-        uint16_t* xs = Xb + s * TS::XB_LEN;
-        // b~ at index i stored at i + 8: [8, n+8) holds b; [0, 8) holds -b[n-8..n-1];
-        // [n+8, n+16) holds -b[0..7]
+      for (int s = 0; s < TS::LB; ++s)
+        bw[gi][s] = make_uint4(bf16x2_of(db[s][0], db[s][1]), bf16x2_of(db[s][2], db[s][3]),
+                               bf16x2_of(db[s][4], db[s][5]), bf16x2_of(db[s][6], db[s][7]));
+    }
+    if (lane == 31) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int i = i0 + e;
-          xs[i + 8] = pb[s][e];
-          if (i >= TS::N - 8) xs[i - TS::N + 8] = nb[s][e];
-          if (i < 8) xs[TS::N + 8 + i] = nb[s][e];
-        }
-      }
+      for (int s = 0; s < TS::LB; ++s) s_edge[warp][s] = bw[TS::GPT - 1][s];
     }
     __syncthreads();
     // ---- B tile: row (s', v), column k = 8 d' + r holds b~_{8(D - d') + v - r} ----
-    for (int ch = tid; ch < (TS::N / 8) * TS::LB * 8; ch += TS::THREADS) {
-      const int dp = ch / (TS::LB * 8), s2 = (ch / 8) % TS::LB, v = ch % 8;
-      const uint16_t* xs = Xb + s2 * TS::XB_LEN + 8 * (TS::D - dp) + v + 8;
-      uint16_t row[8];
+    // For the K-block d' = D - g of group g, E[i] = b~_{8g - 8 + i} (i < 16)
+    // is the previous group followed by the own one (group -1 is minus the
+    // last group: the antiperiodic extension); row v is E[v + 8 - r],
+    // r = 0..7, a reversed window cut from E with byte permutes.
 #pragma unroll
-      for (int r = 0; r < 8; ++r) row[r] = xs[-r];
-      *reinterpret_cast<uint4*>(Bt + (dp * TS::NG + s2) * 128 + 16 * v) = *reinterpret_cast<const uint4*>(row);
+    for (int gi = 0; gi < TS::GPT; ++gi) {
+      const int g = tid * TS::GPT + gi, dp = TS::D - g;
+#pragma unroll
+      for (int s2 = 0; s2 < TS::LB; ++s2) {
+        uint4 pv;
+        if (gi > 0) {
+          pv = bw[gi - 1][s2];
+        } else {
+          const uint4 last = bw[TS::GPT - 1][s2];
+          pv.x = __shfl_up_sync(0xffffffffu, last.x, 1);
+          pv.y = __shfl_up_sync(0xffffffffu, last.y, 1);
+          pv.z = __shfl_up_sync(0xffffffffu, last.z, 1);
+          pv.w = __shfl_up_sync(0xffffffffu, last.w, 1);
+          if (lane == 0) {
+            pv = s_edge[(warp + 3) & 3][s2];
+            if (warp == 0) pv = make_uint4(pv.x ^ 0x80008000u, pv.y ^ 0x80008000u, pv.z ^ 0x80008000u, pv.w ^ 0x80008000u);
+          }
+        }
+        const uint4 ow = bw[gi][s2];
+        const uint32_t E[8] = {pv.x, pv.y, pv.z, pv.w, ow.x, ow.y, ow.z, ow.w};
+        unsigned char* dst = Bt + dp * TS::BT_PITCH + s2 * 128;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          uint32_t o[4];
+          const int c = v >> 1;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            // low half: E[v + 8 - 2 jj], high half: E[v + 7 - 2 jj]
+            o[jj] = (v & 1) ? __byte_perm(E[c + 4 - jj], 0u, 0x1032) : __byte_perm(E[c + 4 - jj], E[c + 3 - jj], 0x7610);
+          }
+          *reinterpret_cast<uint4*>(dst + 16 * v) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+      }
     }
     fence_proxy_async();
     tc_fence_before();
@@ -175,18 +222,18 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
     if (tid == 0) {
       tc_fence_after();
       const uint32_t xa0 = smem_u32(Xa), bt0 = smem_u32(Bt);
+      // descriptors advance by (byte step >> 4) in their address field
+      const uint64_t bd0 = smem_desc(bt0, TS::BT_PITCH, 128);
+      constexpr uint64_t BSTEP = (2 * TS::BT_PITCH) >> 4;
 #pragma unroll 1
       for (int blk = 0; blk < TS::RBLK; ++blk) {
 #pragma unroll 1
         for (int s = 0; s < TS::LA; ++s) {
           const uint32_t dcol = tmem + (uint32_t)((blk * TS::LA + s) * TS::NB);
-          const uint32_t abase = xa0 + (uint32_t)(s * TS::XA_LEN + 8 + 1024 * blk) * 2;
-#pragma unroll 4
-          for (int kk = 0; kk < TS::N / 16; ++kk) {
-            const uint64_t ad = smem_desc(abase + 32u * kk, 16, 128);
-            const uint64_t bd = smem_desc(bt0 + (uint32_t)(kk * 2 * TS::NG * 128), TS::NG * 128, 128);
-            tc_mma_f16(dcol, ad, bd, IDESC, kk > 0 ? 1u : 0u);
-          }
+          const uint64_t ad0 = smem_desc(xa0 + (uint32_t)(s * TS::XA_LEN + 8 + 1024 * blk) * 2, 16, 128);
+#pragma unroll 8
+          for (int kk = 0; kk < TS::N / 16; ++kk)
+            tc_mma_f16(dcol, ad0 + 2u * (uint64_t)kk, bd0 + BSTEP * (uint64_t)kk, IDESC, kk > 0 ? 1u : 0u);
         }
       }
       tc_commit(&mbar);
@@ -201,6 +248,7 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
     parity ^= 1u;
     tc_fence_after();
     uint32_t* c = args.c + (size_t)cur * TS::N;
+    const uint64_t mu = args.tp[j].mu, bias = args.tp[j].bias;
 #pragma unroll 1
     for (int blk = 0; blk < TS::RBLK; ++blk) {
       int64_t acc[8];
@@ -217,16 +265,13 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
           for (int cc = 0; cc < 16; ++cc) {
             const int col = 16 * c16 + cc, s2 = col / 8, v = col % 8;
             if (s2 < TS::LB)
-              acc[v] += (int64_t)__float2int_rn(__uint_as_float(r[cc])) * args.tp[j].pw[s + s2];
+              acc[v] += (int64_t)__float2int_rn(__uint_as_float(r[cc])) * (int64_t)(int32_t)args.tp[j].pw[s + s2];
           }
         }
       }
       uint32_t out[8];
 #pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        int64_t m = acc[v] % (int64_t)q;
-        out[v] = (uint32_t)(m < 0 ? m + (int64_t)q : m);
-      }
+      for (int v = 0; v < 8; ++v) out[v] = barrett64((uint64_t)(acc[v] + (int64_t)bias), q, mu);
       const int u = blk * 128 + tid;
       *reinterpret_cast<uint4*>(c + 8 * u) = make_uint4(out[0], out[1], out[2], out[3]);
       *reinterpret_cast<uint4*>(c + 8 * u + 4) = make_uint4(out[4], out[5], out[6], out[7]);
