@@ -94,8 +94,7 @@ typedef struct polymul_plan_info {
                              NTT batch kernels                              */
     uint32_t ntt_mode;    /* NTT path: reduction mode of the main kernel:
                              0 = values in [0, 2q), 1 = [0, 4q) (Harvey),
-                             2 = unreduced (small q), 3 = [0, 4q) with 16-bit
-                             Shoup quotients (q < 2^14)                     */
+                             2 = unreduced (small q)                        */
     uint32_t regs;        /* NTT path: register budget per thread of the main
                              kernel (fewer registers, more resident warps)  */
     uint32_t reserved[2];
@@ -235,7 +234,8 @@ int polymul_ragged_create(const uint64_t *pool, uint32_t pool_size, uint32_t n_m
  * polymul_ragged_prepare -- plan a list of `count` products: validates every
  * descriptor (degree, prime indices < pool size, rows inside `total_elems`
  * elements of the operand arrays), flattens them into (product, prime) units
- * and packs the units into work items, largest degree first.  The plan is
+ * and sorts the units into degree segments, largest degree first (the
+ * kernel's teams take the units of a segment one at a time).  The plan is
  * uploaded once and reused by every run.  Products must not overlap in c.
  */
 int polymul_ragged_prepare(polymul_ragged *ctx, const polymul_desc *descs, uint32_t count,
@@ -254,7 +254,8 @@ int polymul_ragged_run_graph(polymul_ragged_batch *batch, const void *a, const v
 /* As polymul_plan_status, for a prepared list. */
 int polymul_ragged_status(polymul_ragged_batch *batch, void *stream);
 
-/* Units, work items and CTAs of a prepared list (any pointer may be NULL). */
+/* Units, degree segments (`items`) and CTAs of a prepared list (any pointer
+ * may be NULL). */
 int polymul_ragged_batch_info(const polymul_ragged_batch *batch, uint64_t *units, uint64_t *items,
                               uint32_t *grid);
 

@@ -34,16 +34,6 @@ __device__ __forceinline__ W shoup(W x, W w, W wp, W q) {
   return x * w - qh * q;
 }
 
-// Shoup with a 16-bit quotient estimate, for x < 2^16 and q < 2^14 (32-bit
-// words): wp16 = floor(w * 2^16 / q) = floor(wp / 2^16) for the 32-bit
-// companion wp.  x * wp16 < 2^32, and x*w/q - x*wp16/2^16 < x/2^16 < 1, so
-// floor(x*wp16/2^16) is floor(x*w/q) or one less: the result lies in [0, 2q).
-// Three low-half multiplies and a shift instead of a high-half multiply.
-__device__ __forceinline__ uint32_t shoup16(uint32_t x, uint32_t w, uint32_t wp16, uint32_t q) {
-  const uint32_t qh = (x * wp16) >> 16;
-  return x * w - qh * q;
-}
-
 // Montgomery: (x * y) / 2^bits mod q, result in (-q, x*y/2^bits) shifted by
 // +q when negative, i.e. in [0, q + x*y/2^bits).  qinv = q^-1 mod 2^bits.
 template <typename W>

@@ -134,6 +134,10 @@ int upload_tensor_tables(polymul_plan* p) {
 }
 
 bool lookup_ntt(uint32_t elem, int logn, int mode, KernelInfo* ki) {
+  // n = 2^14, 32-bit words: one 512-thread CTA per product (32 coefficients
+  // per thread) beats the two-CTA cluster (measured 101.9 vs 160.8 us for
+  // 512 products); the cluster kernel stays an autotuner candidate
+  if (elem == 4 && logn == 14 && lookup_ntt_u32_rb5(logn, mode, ki)) return true;
   if (logn >= 14) {
     // beyond one CTA: one product per thread-block cluster; the unreduced
     // mode falls back to Harvey's bounds where it is not instantiated
@@ -282,12 +286,13 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     rc = p->elem == 4 ? upload_ntt_tables<uint32_t>(p) : upload_ntt_tables<uint64_t>(p);
     KernelInfo v;
     if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_NTT, p->ki);
-    if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb5((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
+    if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb5((int)p->logn, p->mode, &v) && v.fn != p->cands[0].ki.fn)
+      rc = add_candidate(POLYMUL_PATH_NTT, v);
+    if (rc == POLYMUL_OK && p->elem == 4 && p->logn == 14 &&
+        (lookup_ntt_cluster(4, 14, p->mode, &v) || lookup_ntt_cluster(4, 14, 1, &v)))
+      rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && p->elem == 8 && lookup_ntt_u64_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
-    // primes below 2^14: Harvey bounds with 16-bit Shoup quotients (same tables)
-    if (rc == POLYMUL_OK && p->elem == 4 && qmax < (1u << 14) && lookup_ntt_u32_m3((int)p->logn, &v))
-      rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) {
       rc = upload_tensor_tables(p);
       if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);

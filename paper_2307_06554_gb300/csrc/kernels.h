@@ -14,21 +14,20 @@ struct KernelInfo {
   int tmem_cols = 0;         // tensor-memory columns allocated per CTA (0: none)
   int cluster = 0;           // CTAs per thread-block cluster (0: no cluster launch)
   int rb = 0;                // NTT: stage bits per register pass
-  int mode = 0;              // NTT: reduction mode (0..3, see ntt.cuh)
+  int mode = 0;              // NTT: reduction mode (0..2, see ntt.cuh)
   int regs = 0;              // NTT: register budget per thread
 };
 
 // batched negacyclic NTT, k_ntt_batch<W, LOGN, MODE> (MODE: 0 = kQ31,
-// 1 = kL4, 2 = kSmall, 3 = kS16; see ntt.cuh)
+// 1 = kL4, 2 = kSmall; see ntt.cuh)
 bool lookup_ntt_u32_m0(int logn, KernelInfo* ki);  // logn 4..14
 bool lookup_ntt_u32_m1(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_m2(int logn, KernelInfo* ki);
-bool lookup_ntt_u32_m3(int logn, KernelInfo* ki);  // logn 4..12, q < 2^14
 bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
 bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_aux(int logn, KernelInfo* ki);  // auxiliary-prime mode, logn 4..14
 // autotuner candidates: other register radices (RB = stage bits per pass)
-bool lookup_ntt_u32_rb5(int logn, int mode, KernelInfo* ki);  // logn 9..13, modes 1, 2
+bool lookup_ntt_u32_rb5(int logn, int mode, KernelInfo* ki);  // logn 9..13, modes 1, 2; logn 14, modes 0..2
 bool lookup_ntt_u32_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, modes 1, 2
 bool lookup_ntt_u64_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, mode 1
 
@@ -37,7 +36,6 @@ bool lookup_ntt_cluster(uint32_t elem, int logn, int mode, KernelInfo* ki);
 
 // uneven batches in one persistent launch (32-bit words, n = 2^10..2^14)
 bool lookup_ntt_ragged(int mode, KernelInfo* ki);
-int ragged_teams(int logn);
 
 // Toeplitz path on the tensor cores, k_toeplitz_batch<TShape<LOGN, WB, LA, LB>>
 bool lookup_toeplitz(int logn, int wb, int la, int lb, KernelInfo* ki);

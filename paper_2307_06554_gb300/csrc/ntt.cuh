@@ -116,21 +116,8 @@ __device__ __forceinline__ uint32_t spos(uint32_t j) { return j ^ ((j >> 1) & 31
 //          conditional subtraction anywhere.  Forward values grow by at most
 //          2q per stage ((1+2s)q after s stages); inverse values at most
 //          double per stage (2^(s+1) q after s stages), the subtraction
-//          offset of stage s being that bound;
-//   kS16   q < 2^14 (32-bit words): Harvey's bounds as kL4, so every value
-//          entering a multiplication is below 4q < 2^16, which lets the
-//          Shoup quotient come from a low-half multiply (shoup16).
-enum { kQ31 = 0, kL4 = 1, kSmall = 2, kS16 = 3 };
-
-// Shoup multiplication by a table constant in mode MODE
-template <typename W, int MODE>
-__device__ __forceinline__ W shoup_m(W x, W w, W wp, W q) {
-  if constexpr (MODE == kS16) {
-    return shoup16(x, w, wp >> 16, q);
-  } else {
-    return shoup(x, w, wp, q);
-  }
-}
+//          offset of stage s being that bound.
+enum { kQ31 = 0, kL4 = 1, kSmall = 2 };
 
 template <typename W, int MODE>
 __device__ __forceinline__ void ct_bfly(W& x, W& y, const TwPair<W>& w, const PrimeConst<W>& pc) {
@@ -138,9 +125,9 @@ __device__ __forceinline__ void ct_bfly(W& x, W& y, const TwPair<W>& w, const Pr
     W t = shoup(y, w.w, w.wp, pc.q);
     y = x - t + pc.q2;
     x = x + t;
-  } else if constexpr (MODE == kL4 || MODE == kS16) {
+  } else if constexpr (MODE == kL4) {
     W xr = csub(x, pc.q2);
-    W t = shoup_m<W, MODE>(y, w.w, w.wp, pc.q);
+    W t = shoup(y, w.w, w.wp, pc.q);
     x = xr + t;
     y = xr - t + pc.q2;
   } else {
@@ -158,11 +145,11 @@ __device__ __forceinline__ void gs_bfly(W& x, W& y, W w, W wp, const PrimeConst<
     W d = x - y + (pc.q << (H + 1));
     x = x + y;
     y = shoup(d, w, wp, pc.q);
-  } else if constexpr (MODE == kL4 || MODE == kS16) {
+  } else if constexpr (MODE == kL4) {
     W s = x + y;
     W d = x - y + pc.q2;
     x = csub(s, pc.q2);
-    y = shoup_m<W, MODE>(d, w, wp, pc.q);
+    y = shoup(d, w, wp, pc.q);
   } else {
     W xr = csub(x, pc.q), yr = csub(y, pc.q);
     W d = xr - yr + pc.q;
@@ -178,7 +165,7 @@ __device__ __forceinline__ void gs_last(W& x, W& y, const PrimeConst<W>& pc) {
   if constexpr (MODE == kSmall) {
     s = x + y;
     d = x - y + (pc.q << (H + 1));
-  } else if constexpr (MODE == kL4 || MODE == kS16) {
+  } else if constexpr (MODE == kL4) {
     s = x + y;
     d = x - y + pc.q2;
   } else {
@@ -186,8 +173,8 @@ __device__ __forceinline__ void gs_last(W& x, W& y, const PrimeConst<W>& pc) {
     s = xr + yr;
     d = xr - yr + pc.q;
   }
-  x = shoup_m<W, MODE>(s, pc.scale, pc.scale_p, pc.q);
-  y = shoup_m<W, MODE>(d, pc.scale_w, pc.scale_wp, pc.q);
+  x = shoup(s, pc.scale, pc.scale_p, pc.q);
+  y = shoup(d, pc.scale_w, pc.scale_wp, pc.q);
 }
 
 // Two consecutive twiddle pairs in one 16-byte load (32-bit words), else
@@ -397,7 +384,7 @@ __device__ __forceinline__ void polymul_unit(W* __restrict__ c, const TwPair<W>*
     constexpr int e = decltype(ec)::value;
     if constexpr (MODE == kSmall) {
       xa[e] = montmul(xa[e], xb[e], pc.q, pc.qinv);
-    } else if constexpr (MODE == kL4 || MODE == kS16) {
+    } else if constexpr (MODE == kL4) {
       xa[e] = csub(montmul(xa[e], xb[e], pc.q, pc.qinv), pc.q2);
     } else {
       xa[e] = montmul(csub(xa[e], pc.q), csub(xb[e], pc.q), pc.q, pc.qinv);

@@ -42,13 +42,16 @@ struct NttBatchArgs {
 };
 
 // Ragged (uneven) batches: one unit = one (product, prime) row of n words.
+// Degree segments per list: at most one per degree; the work counters of a
+// list are kRaggedMaxSegs segment counters and one finished-CTA count.
+constexpr int kRaggedMaxSegs = 15;
 struct alignas(16) RaggedUnit {
   uint64_t offset;  // element offset of the row in a, b, c
   uint32_t prime;   // index into the prime pool
   uint32_t pad;
 };
 
-// One CTA work item: `count` consecutive units of degree 2^logn.
+// One degree segment: `count` consecutive units of degree 2^logn.
 struct alignas(16) RaggedItem {
   uint32_t logn;
   uint32_t first;

@@ -2,13 +2,14 @@
 // (2^10 .. 2^14) and different numbers of RNS primes (each prime a separate
 // ring, Sec. 2.4), all through the negacyclic NTT unit of ntt.cuh.
 //
-// The host flattens the products into units (product, prime) and packs units
-// of the same degree into work items of up to 512 / T units (T = threads per
-// unit), largest degree first; CTAs of 512 threads take items from a device
-// counter.  Inside an item each team of T threads owns one unit: its leader
-// bulk-copies the unit's operand rows into the team's shared buffers
-// (tracked by the team's own mbarrier), the team synchronises on its own
-// named barrier, and the result goes straight back to HBM.  Twiddle tables
+// The host flattens the products into units (product, prime) and sorts them
+// into degree segments, largest degree first.  CTAs of 512 threads walk the
+// segments in order; inside a segment the CTA is cut into teams of T threads
+// (T = threads per unit), and each team takes units from the segment's
+// device counter on its own, synchronising on its own named barrier, so that
+// teams drift apart as independent CTAs would and their exchange and
+// arithmetic phases overlap.  A CTA waits for all its teams only when it
+// moves to the next segment (a new team layout).  Twiddle tables
 // are built once per pool prime at the largest degree: the table for n is
 // the length-n prefix of the table for n_max (psi_n = psi_nmax^(nmax/n) and
 // bit reversal of a log n-bit index into log nmax bits multiplies it by
@@ -23,6 +24,7 @@ namespace pm {
 
 constexpr int kRaggedThreads = 512;
 constexpr int kRaggedMaxTeams = 8;
+static_assert(kRaggedMaxSegs >= 5, "one segment per degree 2^10 .. 2^14");
 
 // team barrier: named barrier `id` (1..15) over `n` threads
 struct TeamSync {
@@ -37,103 +39,124 @@ struct TeamSync {
 template <int LOGN>
 using RaggedShape = Shape<uint32_t, LOGN, (LOGN <= 13 ? 4 : 5)>;
 
-struct NoHook {
-  __device__ __forceinline__ void operator()() const {}
-};
-
-// `phases`: one parity bit per team barrier (an item completes one phase on
-// the barriers of the teams it uses, and only on those)
+// One degree segment: the units of degree 2^LOGN, taken one at a time by
+// the teams of the CTA (T threads each, 512 / T teams) from the segment's
+// own counter, every team on its own: its leader bulk-copies the unit's
+// rows into the team's buffers (tracked by the team's mbarrier), and as soon
+// as the unit's last exchange is done it takes the next unit and issues that
+// copy, which then overlaps the last inverse pass.  `phases`: one parity bit
+// per team barrier, exact for the thread's own team (teams complete
+// different numbers of phases); at the end the leader publishes its team's
+// bit in s_bits[team] so that the CTA can agree on all of them.  Returns
+// false when a bounded wait expired (the team stops; the copy it waited for
+// is the only one it has in flight).
 template <class S, int MODE>
-__device__ __forceinline__ bool ragged_item(const RaggedArgs& args, const RaggedItem& item, uint32_t* smem,
-                                            uint64_t* mbar, uint32_t& phases) {
+__device__ __forceinline__ bool ragged_segment(const RaggedArgs& args, const RaggedItem& seg,
+                                               unsigned long long* ctr, uint32_t* smem, uint64_t* mbar,
+                                               uint32_t& phases, unsigned long long* s_next, uint32_t* s_bits) {
   static_assert(S::T <= kRaggedThreads && S::T >= 32, "team size");
-  constexpr int TEAMS = kRaggedThreads / S::T;
-  static_assert(TEAMS <= kRaggedMaxTeams, "too many teams");
+  static_assert(kRaggedThreads / S::T <= kRaggedMaxTeams, "too many teams");
   constexpr uint32_t ROW = S::N * 4u;
   const uint32_t team = threadIdx.x / S::T, t = threadIdx.x % S::T;
   uint32_t* sa = smem + (size_t)team * S::SMEM_WORDS;
   uint32_t* sb = sa + S::SLICE;
-  const bool act = team < item.count;
-  const RaggedUnit unit = args.units[item.first + (act ? team : 0u)];
-  if (t == 0) {
-    // inactive teams copy the item's first unit again so that every team's
-    // barrier completes exactly one phase per item
-    fence_proxy_async();
-    mbar_arrive_expect_tx(&mbar[team], 2 * ROW);
-    bulk_g2s(sa, args.a + unit.offset, ROW, &mbar[team]);
-    bulk_g2s(sb, args.b + unit.offset, ROW, &mbar[team]);
+  const TeamSync sync{1 + team, S::T};
+  auto take = [&]() {  // team leader: next unit index of the segment, and its copy
+    const unsigned long long u = atomicAdd(ctr, 1ull);
+    s_next[team] = u;
+    if (u < seg.count) {
+      const RaggedUnit un = args.units[seg.first + u];
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&mbar[team], 2 * ROW);
+      bulk_g2s(sa, args.a + un.offset, ROW, &mbar[team]);
+      bulk_g2s(sb, args.b + un.offset, ROW, &mbar[team]);
+    }
+  };
+  if (t == 0) take();
+  sync();
+  unsigned long long cur = s_next[team];
+  while (cur < seg.count) {
+    // a bounded wait; the team agrees on its outcome (barrier reduction)
+    uint32_t fail = mbar_wait(&mbar[team], (phases >> team) & 1u) ? 0u : 1u;
+    phases ^= 1u << team;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(fail)
+        : "r"(fail), "r"(1u + team), "r"((uint32_t)S::T)
+        : "memory");
+    if (fail) break;
+    const RaggedUnit unit = args.units[seg.first + cur];
+    const PrimeConst<uint32_t> pc = args.pc[(size_t)unit.prime * 16 + S::LOGN];
+    const TwPair<uint32_t>* twf = reinterpret_cast<const TwPair<uint32_t>*>(args.tw_fwd) + (size_t)unit.prime * args.nmax;
+    const TwPair<uint32_t>* twi = reinterpret_cast<const TwPair<uint32_t>*>(args.tw_inv) + (size_t)unit.prime * args.nmax;
+    auto hook = [&]() {  // the whole team, once sa/sb are free
+      if (t == 0) take();
+    };
+    polymul_unit<S, MODE, false>(args.c + unit.offset, twf, twi, pc, sa, sb, t, true, sync, hook);
+    sync();  // the leader's s_next[team] is visible
+    cur = s_next[team];
   }
-  // a bounded wait; the team agrees on its outcome (barrier reduction) so
-  // that its barriers stay uniform
-  uint32_t fail = mbar_wait(&mbar[team], (phases >> team) & 1u) ? 0u : 1u;
-  phases ^= (1u << TEAMS) - 1u;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 q, %1, 0;\n\t"
-      "bar.red.or.pred p, %2, %3, q;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(fail)
-      : "r"(fail), "r"(1u + team), "r"((uint32_t)S::T)
-      : "memory");
-  const bool ok = fail == 0;
-  const PrimeConst<uint32_t> pc = args.pc[(size_t)unit.prime * 16 + S::LOGN];
-  const TwPair<uint32_t>* twf = reinterpret_cast<const TwPair<uint32_t>*>(args.tw_fwd) + (size_t)unit.prime * args.nmax;
-  const TwPair<uint32_t>* twi = reinterpret_cast<const TwPair<uint32_t>*>(args.tw_inv) + (size_t)unit.prime * args.nmax;
-  polymul_unit<S, MODE, false>(args.c + unit.offset, twf, twi, pc, sa, sb, t, act && ok, TeamSync{1 + team, S::T},
-                               NoHook{});
-  return ok;
+  if (t == 0) s_bits[team] = (phases >> team) & 1u;
+  return cur >= seg.count;
 }
 
+// `items`: the degree segments, largest degree first; ctr[i] is segment i's
+// unit counter, ctr[kRaggedMaxSegs] the count of finished CTAs (the last one
+// resets them all).  A CTA changes team layout only between segments.
 template <int MODE>
 __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[kRaggedMaxTeams];
-  __shared__ RaggedItem s_item;
+  __shared__ unsigned long long s_next[kRaggedMaxTeams];
+  __shared__ uint32_t s_bits[2][kRaggedMaxTeams];  // per segment parity: published barrier phase bits
   uint32_t* smem = reinterpret_cast<uint32_t*>(smem_raw);
   if (threadIdx.x < kRaggedMaxTeams) mbar_init(&mbar[threadIdx.x], 1);
   fence_mbar_init();
   __syncthreads();
   uint32_t phases = 0;
   bool failed = false;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned long long w = atomicAdd(args.ctr, 1ull);
-      if (w < args.n_items) {
-        s_item = args.items[w];
-      } else {
-        s_item.count = 0;
-      }
-    }
-    __syncthreads();
-    const RaggedItem item = s_item;
-    __syncthreads();
-    if (item.count == 0) break;
+  for (uint64_t i = 0; i < args.n_items; ++i) {
+    const RaggedItem seg = args.items[i];
+    unsigned long long* ctr = args.ctr + i;
+    uint32_t* bits = s_bits[i & 1];
     bool ok = true;
-    switch (item.logn) {
-      case 10: ok = ragged_item<RaggedShape<10>, MODE>(args, item, smem, mbar, phases); break;
-      case 11: ok = ragged_item<RaggedShape<11>, MODE>(args, item, smem, mbar, phases); break;
-      case 12: ok = ragged_item<RaggedShape<12>, MODE>(args, item, smem, mbar, phases); break;
-      case 13: ok = ragged_item<RaggedShape<13>, MODE>(args, item, smem, mbar, phases); break;
-      case 14: ok = ragged_item<RaggedShape<14>, MODE>(args, item, smem, mbar, phases); break;
+    int teams = 0;
+    switch (seg.logn) {
+#define PM_SEG(L)                                                                                      \
+  case L:                                                                                              \
+    ok = ragged_segment<RaggedShape<L>, MODE>(args, seg, ctr, smem, mbar, phases, s_next, bits);        \
+    teams = kRaggedThreads / RaggedShape<L>::T;                                                         \
+    break;
+      PM_SEG(10) PM_SEG(11) PM_SEG(12) PM_SEG(13) PM_SEG(14)
+#undef PM_SEG
       default: break;
     }
-    if (__syncthreads_or(!ok)) {
+    // every team is done with the segment's layout before the next one
+    const bool any_fail = __syncthreads_or(!ok);
+    // agree on the phase bits of the barriers this segment used (the next
+    // segment may put this thread in another team)
+    for (int tm = 0; tm < teams; ++tm) phases = (phases & ~(1u << tm)) | (bits[tm] << tm);
+    if (any_fail) {
       failed = true;
       break;
     }
   }
   if (failed) {
     if (threadIdx.x == 0) atomicExch(args.err, 1);
-    // let copies in flight land: a barrier whose current phase is pending
-    // completes it (parity bit = the phase being waited for)
+    // let the copy in flight land: a barrier whose current phase is pending
+    // completes it (parity bit = the phase being waited for); the others
+    // return at once
     if (threadIdx.x < kRaggedMaxTeams) mbar_wait(&mbar[threadIdx.x], ((phases >> threadIdx.x) & 1u) ^ 1u);
     return;
   }
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(args.ctr + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
-      atomicExch(args.ctr, 0ull);
-      atomicExch(args.ctr + 1, 0ull);
+    if (atomicAdd(args.ctr + kRaggedMaxSegs, 1ull) == (unsigned long long)gridDim.x - 1) {
+      for (uint64_t i = 0; i < args.n_items; ++i) atomicExch(args.ctr + i, 0ull);
+      atomicExch(args.ctr + kRaggedMaxSegs, 0ull);
     }
   }
 }
@@ -147,17 +170,6 @@ int ragged_smem_bytes() {
   m = m > (kRaggedThreads / RaggedShape<13>::T) * RaggedShape<13>::SMEM_WORDS * 4 ? m : (kRaggedThreads / RaggedShape<13>::T) * RaggedShape<13>::SMEM_WORDS * 4;
   m = m > (kRaggedThreads / RaggedShape<14>::T) * RaggedShape<14>::SMEM_WORDS * 4 ? m : (kRaggedThreads / RaggedShape<14>::T) * RaggedShape<14>::SMEM_WORDS * 4;
   return m;
-}
-
-int ragged_teams(int logn) {
-  switch (logn) {
-    case 10: return kRaggedThreads / RaggedShape<10>::T;
-    case 11: return kRaggedThreads / RaggedShape<11>::T;
-    case 12: return kRaggedThreads / RaggedShape<12>::T;
-    case 13: return kRaggedThreads / RaggedShape<13>::T;
-    case 14: return kRaggedThreads / RaggedShape<14>::T;
-    default: return 0;
-  }
 }
 
 bool lookup_ntt_ragged(int mode, KernelInfo* ki) {

@@ -1,6 +1,7 @@
 // C-ABI entry points for uneven batches (polymul_ragged_*), see
-// include/polymul.h.  Host-side planning: tables per pool prime, units and
-// work items, one persistent launch, optional CUDA-graph replay.
+// include/polymul.h.  Host-side planning: tables per pool prime, units
+// sorted into degree segments, one persistent launch, optional CUDA-graph
+// replay.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -186,15 +187,14 @@ extern "C" int polymul_ragged_prepare(polymul_ragged* r, const polymul_desc* des
       cls[logn].push_back(RaggedUnit{d.offset + (uint64_t)i * d.n, pi, 0});
     }
   }
+  // degree segments, largest degree first (the longest units start first)
   std::vector<RaggedUnit> units;
   std::vector<RaggedItem> items;
-  for (int logn = 15; logn >= 0; --logn) {  // largest degree first (longest items first)
+  for (int logn = 15; logn >= 0; --logn) {
     if (cls[logn].empty()) continue;
-    const int g = ragged_teams(logn);
-    for (size_t i = 0; i < cls[logn].size(); i += g) {
-      const uint32_t cnt = (uint32_t)std::min<size_t>(g, cls[logn].size() - i);
-      items.push_back(RaggedItem{(uint32_t)logn, (uint32_t)(units.size() + i), cnt, 0});
-    }
+    if (cls[logn].size() > 0xFFFFFFFFull || units.size() + cls[logn].size() > 0xFFFFFFFFull)
+      return fail(POLYMUL_EINVAL, "too many units in one list");
+    items.push_back(RaggedItem{(uint32_t)logn, (uint32_t)units.size(), (uint32_t)cls[logn].size(), 0});
     units.insert(units.end(), cls[logn].begin(), cls[logn].end());
   }
   polymul_ragged_batch* b = new polymul_ragged_batch();
@@ -211,7 +211,7 @@ extern "C" int polymul_ragged_prepare(polymul_ragged* r, const polymul_desc* des
   rc = up((void**)&b->d_units, units.data(), units.size() * sizeof(RaggedUnit));
   if (rc == POLYMUL_OK) rc = up((void**)&b->d_items, items.data(), items.size() * sizeof(RaggedItem));
   if (rc == POLYMUL_OK) {
-    const unsigned long long zero[2] = {0, 0};
+    const unsigned long long zero[kRaggedMaxSegs + 1] = {};
     const int z = 0;
     rc = up((void**)&b->d_ctr, zero, sizeof zero);
     if (rc == POLYMUL_OK) rc = up((void**)&b->d_err, &z, sizeof z);
@@ -236,7 +236,7 @@ int ragged_check(polymul_ragged_batch* b, const void* a, const void* bb, void* c
   return POLYMUL_OK;
 }
 int ragged_grid(const polymul_ragged_batch* b) {
-  return (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap, std::max<uint64_t>(1, b->n_items));
+  return (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap, std::max<uint64_t>(1, b->n_units));
 }
 }  // namespace
 
@@ -290,7 +290,7 @@ extern "C" int polymul_ragged_status(polymul_ragged_batch* b, void* stream) {
   PM_CUDA(cudaMemcpy(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (!h) return POLYMUL_OK;
   PM_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
-  PM_CUDA(cudaMemset(b->d_ctr, 0, 2 * sizeof(unsigned long long)));
+  PM_CUDA(cudaMemset(b->d_ctr, 0, (kRaggedMaxSegs + 1) * sizeof(unsigned long long)));
   return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }
 

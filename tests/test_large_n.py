@@ -1,5 +1,8 @@
-"""Degrees beyond one CTA (n = 2^14 .. 2^16), computed by one thread-block
-cluster per product with exchanges through distributed shared memory.
+"""Large degrees, n = 2^14 .. 2^16: one thread-block cluster per product
+with exchanges through distributed shared memory (64-bit words, and 32-bit
+words above 2^14), or one 512-thread CTA per product (32-bit words at 2^14;
+the cluster kernel is that plan's autotuner candidate, checked with every
+other candidate in the autotuner tests).
 Checked against the oracle on sampled output coefficients and, for the
 whole output, by evaluation at roots of x^n + 1 (c(w) = a(w) b(w) mod q for
 w^n = -1), an independent check of every coefficient at once."""

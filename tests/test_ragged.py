@@ -70,13 +70,36 @@ def test_largest_degrees(pm):
     _check(rag, c, off, range(len(rag.products)))
 
 
-def test_items_of_different_team_counts_on_one_cta(pm):
-    """More work items than CTAs, one-team items (n = 16384) scheduled before
-    eight-team items (n = 1024): CTAs move between team layouts, and every
-    team barrier must keep its own phase.  Checks the n = 1024 products."""
+def test_segments_of_different_team_counts_on_one_cta(pm):
+    """More units than CTAs, a one-team segment (n = 16384) before an
+    eight-team segment (n = 1024): CTAs move between team layouts, teams take
+    different numbers of units, and every team barrier must keep its own
+    phase.  Checks the n = 1024 products."""
     rag = wl.ragged_2000(count=400, seed=44, degrees=(1024, 16384), kmax=2, pool_size=4)
     c, off = _run(pm, rag)
     _check(rag, c, off, [i for i, p in enumerate(rag.products) if p.n == 1024])
+
+
+def test_fewer_units_than_ctas_and_relaunch(pm):
+    """Three units in all (grid of three CTAs), launched twice on the same
+    plan: the segment counters reset between launches."""
+    import torch
+    rag = wl.ragged_2000(count=2, seed=45, degrees=(1024, 8192), kmax=2, pool_size=3)
+    a, b = _pack(rag)
+    outs = []
+    with pm.Ragged(rag.pool, 16384, [(p.n, p.prime_idx) for p in rag.products]) as r:
+        assert r.info["grid"] == r.info["units"] <= 4
+        ta = torch.from_numpy(a.view(np.int32)).cuda()
+        tb = torch.from_numpy(b.view(np.int32)).cuda()
+        for graph in (False, False, True, True):
+            tc = torch.full_like(ta, -1)
+            r.run(ta, tb, tc, graph=graph)
+            pm.polymul_ragged_status(r.batch)
+            outs.append(tc.cpu().numpy().view(np.uint32))
+        off = list(r.offsets)
+    for c in outs[1:]:
+        assert np.array_equal(c, outs[0])
+    _check(rag, outs[0], off, range(len(rag.products)))
 
 
 def test_smaller_nmax_prefix_tables(pm):

@@ -25,12 +25,15 @@ def pm():
     return polymul
 
 
-@pytest.mark.parametrize("n,bits,elem", [(16, 14, 4), (256, 14, 4), (512, 14, 4), (1024, 14, 4), (2048, 14, 4),
-                                         (2048, 30, 4), (4096, 29, 4), (8192, 20, 4), (1024, 59, 8), (4096, 59, 8)])
+@pytest.mark.parametrize("n,bits,elem", [(512, 14, 4), (1024, 14, 4), (2048, 14, 4),
+                                         (2048, 30, 4), (4096, 29, 4), (8192, 20, 4), (16384, 30, 4), (16384, 17, 4),
+                                         (1024, 59, 8), (4096, 59, 8)])
 def test_every_candidate_is_exact(pm, n, bits, elem):
     rng = np.random.default_rng(n + bits)
     if bits == 14:
         q_list = [12289]
+    elif bits == 17:
+        q_list = [65537]  # the small-q mode at n = 2^14
     else:
         q_list = wl.draw_primes(rng, 2, bits, bits, max(14, n.bit_length() + 1))
     dt = np.uint32 if elem == 4 else np.uint64
@@ -79,5 +82,5 @@ def test_launch_flags(pm):
         assert plan.info["launch_flags"] == 2
     with pm.Plan(1024, [12289], path=pm.PATH_TENSOR) as plan:
         assert plan.info["launch_flags"] == 0
-    with pm.Plan(16384, wl.draw_primes(np.random.default_rng(3), 1, 30, 30, 15)) as plan:
-        assert plan.info["launch_flags"] == 0
+    with pm.Plan(32768, wl.draw_primes(np.random.default_rng(3), 1, 30, 30, 16)) as plan:
+        assert plan.info["launch_flags"] == 0  # the thread-block cluster kernel
