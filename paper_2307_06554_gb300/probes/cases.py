@@ -10,7 +10,8 @@ and checks the plan's device status.  Device memory stays below 1 GB.
 cases:
   ntt_ring1024     n = 1024, q = 12289, 4096 products (path a, default kernel)
   tensor_ring1024  the same batch through the Toeplitz tensor-core path
-  cluster_16384    n = 16384, one 30-bit prime, 1024 products (cluster path)
+  n16384           n = 16384, one 30-bit prime, 1024 products (one CTA per product)
+  cluster_32768    n = 32768, one 30-bit prime, 256 products (thread-block clusters)
   u64_4096         n = 4096, one 59-bit prime, 1024 products (64-bit words)
   ragged_300       the first 300 products of the uneven 2000-product list
                    (n 1024..16384, 1..16 primes), one persistent launch
@@ -75,7 +76,8 @@ def _ragged(count, launches):
 
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    p.add_argument("case", choices=["ntt_ring1024", "tensor_ring1024", "cluster_16384", "u64_4096", "ragged_300"])
+    p.add_argument("case", choices=["ntt_ring1024", "tensor_ring1024", "n16384", "cluster_32768", "u64_4096",
+                                    "ragged_300"])
     p.add_argument("--launches", type=int, default=4)
     args = p.parse_args(argv)
     rng = np.random.default_rng(8)
@@ -83,8 +85,10 @@ def main(argv=None):
         res = _homogeneous(1024, [12289], 4096, polymul.PATH_NTT, args.launches)
     elif args.case == "tensor_ring1024":
         res = _homogeneous(1024, [12289], 4096, polymul.PATH_TENSOR, args.launches)
-    elif args.case == "cluster_16384":
+    elif args.case == "n16384":
         res = _homogeneous(16384, wl.draw_primes(rng, 1, 30, 30, 15), 1024, polymul.PATH_NTT, args.launches)
+    elif args.case == "cluster_32768":
+        res = _homogeneous(32768, wl.draw_primes(rng, 1, 30, 30, 16), 256, polymul.PATH_NTT, args.launches)
     elif args.case == "u64_4096":
         res = _homogeneous(4096, wl.draw_primes(rng, 1, 59, 59, 13), 1024, polymul.PATH_NTT, args.launches)
     else:
