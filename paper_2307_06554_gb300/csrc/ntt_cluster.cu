@@ -64,7 +64,43 @@ struct NoHookC {
   __device__ __forceinline__ void operator()() const {}
 };
 
-template <class S, int MODE>
+// Double-buffered exchanges (32-bit words: four buffers fit in shared
+// memory).  Exchange e of a unit (forward exchanges first, e = 0, 1, ...)
+// uses buffer set e & 1, so a set is written again only two exchanges after
+// it was last read, with a whole exchange's barrier in between: no team
+// barrier is needed before the stores, only the one that publishes them.
+// Across units the same holds (the last exchange of a unit uses set 1, the
+// first of the next set 0).
+template <class S, int MODE, int P, class Buf, typename W = typename S::W>
+__device__ __forceinline__ void fwd_db(W (&xa)[S::R], W (&xb)[S::R], const Buf (&a)[2], const Buf (&b)[2],
+                                       const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc, uint32_t t) {
+  fwd_phase2<S, MODE, P>(xa, xb, tw, pc, t);
+  if constexpr (P > 0) {
+    constexpr int SET = (S::NPH - 1 - P) & 1;
+    store_layout<S, P>(xa, a[SET], t);
+    store_layout<S, P>(xb, b[SET], t);
+    ClusterSync{}();
+    load_layout<S, P - 1>(xa, a[SET], t);
+    load_layout<S, P - 1>(xb, b[SET], t);
+    fwd_db<S, MODE, P - 1>(xa, xb, a, b, tw, pc, t);
+  }
+}
+
+template <class S, int MODE, int P, class Buf, typename W = typename S::W>
+__device__ __forceinline__ void inv_db(W (&x)[S::R], const Buf (&a)[2], const TwPair<W>* __restrict__ tw,
+                                       const PrimeConst<W>& pc, uint32_t t) {
+  inv_phase<S, MODE, P>(x, tw, pc, t);
+  if constexpr (P + 1 < S::NPH) {
+    constexpr int SET = (S::NPH - 1 + P) & 1;
+    store_layout<S, P>(x, a[SET], t);
+    ClusterSync{}();
+    load_layout<S, P + 1>(x, a[SET], t);
+    inv_db<S, MODE, P + 1>(x, a, tw, pc, t);
+  }
+}
+
+// DB: double-buffered exchanges (four buffers of 8192 words per CTA)
+template <class S, int MODE, bool DB>
 __global__ void __launch_bounds__(kClusterThreads, 1) k_ntt_cluster(NttBatchArgs<typename S::W> args) {
   using W = typename S::W;
   using Buf = ClusterBuf<W, S::RB, kClusterLocalLog>;
@@ -72,8 +108,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_ntt_cluster(NttBatchArgs
                 "one CTA per 8192 coefficients");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* buf = reinterpret_cast<W*>(smem_raw);
+  constexpr uint32_t L = 1u << kClusterLocalLog;
   const Buf sa{buf};
-  const Buf sb{buf + (1u << kClusterLocalLog)};
+  const Buf sb{buf + L};
+  const Buf da[2] = {Buf{buf}, Buf{buf + 2 * L}};
+  const Buf db[2] = {Buf{buf + L}, Buf{buf + 3 * L}};
   const uint32_t t = cluster_rank() * kClusterThreads + threadIdx.x;
   constexpr int TOP = S::NPH - 1;
   const TwPair<W>* twf = reinterpret_cast<const TwPair<W>*>(args.tw_fwd);
@@ -91,7 +130,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_ntt_cluster(NttBatchArgs
       xa[e] = a[i];
       xb[e] = b[i];
     });
-    fwd_from<S, MODE, TOP>(xa, xb, sa, sb, twf + (size_t)pj * args.tw_stride, pc, t, ClusterSync{});
+    if constexpr (DB) {
+      fwd_db<S, MODE, TOP>(xa, xb, da, db, twf + (size_t)pj * args.tw_stride, pc, t);
+    } else {
+      fwd_from<S, MODE, TOP>(xa, xb, sa, sb, twf + (size_t)pj * args.tw_stride, pc, t, ClusterSync{});
+    }
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;
       if constexpr (MODE == kSmall) {
@@ -102,13 +145,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_ntt_cluster(NttBatchArgs
         xa[e] = montmul(csub(xa[e], pc.q), csub(xb[e], pc.q), pc.q, pc.qinv);
       }
     });
-    inv_from<S, MODE, 0>(xa, sa, twi + (size_t)pj * args.tw_stride, pc, t, ClusterSync{}, NoHookC{});
+    if constexpr (DB) {
+      inv_db<S, MODE, 0>(xa, da, twi + (size_t)pj * args.tw_stride, pc, t);
+    } else {
+      inv_from<S, MODE, 0>(xa, sa, twi + (size_t)pj * args.tw_stride, pc, t, ClusterSync{}, NoHookC{});
+    }
     W* c = args.c + (size_t)u * S::N;
     sfor<0, S::R>([&](auto ec) {
       constexpr int e = decltype(ec)::value;
       c[elem_index<S, TOP>(e, t)] = csub(xa[e], pc.q);
     });
-    ClusterSync{}();  // no CTA reuses its buffers while another still reads them
+    if constexpr (!DB) ClusterSync{}();  // no CTA reuses its buffers while another still reads them
   }
   ClusterSync{}();  // no CTA leaves while another may still address its shared memory
 }
@@ -116,10 +163,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_ntt_cluster(NttBatchArgs
 template <typename W, int LOGN, int MODE>
 static KernelInfo cluster_info() {
   using S = Shape<W, LOGN, 4>;
+  constexpr bool DB = sizeof(W) == 4;  // four 32 KB buffers; 64-bit words keep two
   KernelInfo ki;
-  ki.fn = (const void*)k_ntt_cluster<S, MODE>;
+  ki.fn = (const void*)k_ntt_cluster<S, MODE, DB>;
   ki.block = kClusterThreads;
-  ki.smem = 2 * (1 << kClusterLocalLog) * (int)sizeof(W);
+  ki.smem = (DB ? 4 : 2) * (1 << kClusterLocalLog) * (int)sizeof(W);
   ki.team = S::T;
   ki.units_per_cta = 1;
   ki.cluster = S::T / kClusterThreads;
