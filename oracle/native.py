@@ -42,12 +42,13 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             u64p = ctypes.POINTER(ctypes.c_uint64)
-            lib.oracle_negacyclic_batch.argtypes = [u64p, u64p, u64p, ctypes.c_uint64, u64p,
-                                                    ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
-            lib.oracle_negacyclic_batch.restype = None
-            lib.oracle_negacyclic_coeffs.argtypes = [u64p, u64p, ctypes.c_uint64, ctypes.c_uint64,
-                                                     u64p, ctypes.c_uint64, u64p]
-            lib.oracle_negacyclic_coeffs.restype = None
+            for fn in (lib.oracle_negacyclic_batch, lib.oracle_cyclic_batch):
+                fn.argtypes = [u64p, u64p, u64p, ctypes.c_uint64, u64p, ctypes.c_uint64, ctypes.c_uint64,
+                               ctypes.c_uint64]
+                fn.restype = None
+            for fn in (lib.oracle_negacyclic_coeffs, lib.oracle_cyclic_coeffs):
+                fn.argtypes = [u64p, u64p, ctypes.c_uint64, ctypes.c_uint64, u64p, ctypes.c_uint64, u64p]
+                fn.restype = None
             _lib = lib
     return _lib
 
@@ -61,8 +62,9 @@ def default_threads() -> int:
 
 
 def polymul_batch(a: np.ndarray, b: np.ndarray, q_list: Sequence[int],
-                  threads: Optional[int] = None) -> np.ndarray:
-    """Oracle over a [batch][k][n] batch; returns uint64 [batch][k][n]."""
+                  threads: Optional[int] = None, cyclic: bool = False) -> np.ndarray:
+    """Oracle over a [batch][k][n] batch; returns uint64 [batch][k][n].
+    ``cyclic``: the ring Z_q[x]/(x^n-1) instead of Z_q[x]/(x^n+1)."""
     if a.shape != b.shape or a.ndim != 3 or a.shape[1] != len(q_list):
         raise ValueError("shape mismatch")
     lib = _load()
@@ -78,8 +80,10 @@ def polymul_batch(a: np.ndarray, b: np.ndarray, q_list: Sequence[int],
     for first in range(0, batch, step):
         chunks.append((first, min(step, batch - first)))
 
+    fn = lib.oracle_cyclic_batch if cyclic else lib.oracle_negacyclic_batch
+
     def run(ch):
-        lib.oracle_negacyclic_batch(_ptr(a64), _ptr(b64), _ptr(c64), n, _ptr(qs), k, ch[0], ch[1])
+        fn(_ptr(a64), _ptr(b64), _ptr(c64), n, _ptr(qs), k, ch[0], ch[1])
 
     if len(chunks) == 1:
         run(chunks[0])
@@ -89,13 +93,14 @@ def polymul_batch(a: np.ndarray, b: np.ndarray, q_list: Sequence[int],
     return c64
 
 
-def polymul_one(a: np.ndarray, b: np.ndarray, q: int) -> np.ndarray:
+def polymul_one(a: np.ndarray, b: np.ndarray, q: int, cyclic: bool = False) -> np.ndarray:
     """One product of two length-n residue vectors."""
-    r = polymul_batch(np.asarray(a).reshape(1, 1, -1), np.asarray(b).reshape(1, 1, -1), [q], threads=1)
+    r = polymul_batch(np.asarray(a).reshape(1, 1, -1), np.asarray(b).reshape(1, 1, -1), [q], threads=1,
+                      cyclic=cyclic)
     return r[0, 0]
 
 
-def coeffs(a: np.ndarray, b: np.ndarray, q: int, js: Sequence[int]) -> np.ndarray:
+def coeffs(a: np.ndarray, b: np.ndarray, q: int, js: Sequence[int], cyclic: bool = False) -> np.ndarray:
     """Selected output coefficients c_j of one product (sampled checks at
     sizes where the whole product would take too long)."""
     lib = _load()
@@ -103,5 +108,6 @@ def coeffs(a: np.ndarray, b: np.ndarray, q: int, js: Sequence[int]) -> np.ndarra
     b64 = np.ascontiguousarray(b, dtype=np.uint64).reshape(-1)
     jj = np.ascontiguousarray(np.asarray(js, dtype=np.uint64))
     out = np.zeros(len(jj), dtype=np.uint64)
-    lib.oracle_negacyclic_coeffs(_ptr(a64), _ptr(b64), a64.size, int(q), _ptr(jj), len(jj), _ptr(out))
+    fn = lib.oracle_cyclic_coeffs if cyclic else lib.oracle_negacyclic_coeffs
+    fn(_ptr(a64), _ptr(b64), a64.size, int(q), _ptr(jj), len(jj), _ptr(out))
     return out

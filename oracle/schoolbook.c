@@ -1,5 +1,8 @@
 /*
- * Plain C schoolbook oracle for c = a*b in Z_q[x]/(x^n+1).
+ * Plain C schoolbook oracle for c = a*b in Z_q[x]/(x^n+1), and in the cyclic
+ * ring Z_q[x]/(x^n-1) (Sec. 2.1 names it as the other common ring): there
+ * x^n = 1, so the products with i + k = j + n are added instead of
+ * subtracted.
  *
  * TEST INFRASTRUCTURE ONLY: called by the test-suite, smoke() and the
  * cpu_baseline leg of bench.py through ctypes.  It shares nothing with the
@@ -45,50 +48,79 @@ static uint64_t acc_mod(const acc192 *s, uint64_t q)
     return (uint64_t)r;
 }
 
+/* Coefficient j of one product: the low sum (i + k = j) and the wrapped
+ * sum (i + k = j + n), combined with the wrap sign of the ring. */
+static uint64_t coeff(const uint64_t *a, const uint64_t *b, uint64_t n, uint64_t q,
+                      uint64_t j, int cyclic)
+{
+    acc192 low = {0, 0, 0}, wrap = {0, 0, 0};
+    /* i + k = j : k = j - i for i <= j */
+    for (uint64_t i = 0; i <= j; ++i)
+        acc_add(&low, (u128)a[i] * b[j - i]);
+    /* i + k = j + n : k = j + n - i for i > j */
+    for (uint64_t i = j + 1; i < n; ++i)
+        acc_add(&wrap, (u128)a[i] * b[j + n - i]);
+    uint64_t p = acc_mod(&low, q), m = acc_mod(&wrap, q);
+    if (cyclic)
+        return (uint64_t)(((u128)p + m) % q);
+    return p >= m ? p - m : (uint64_t)(((u128)p + q) - m);
+}
+
 /* One product: a, b, c are n-entry arrays of canonical residues. */
 void oracle_negacyclic(const uint64_t *a, const uint64_t *b, uint64_t *c,
                        uint64_t n, uint64_t q)
 {
-    for (uint64_t j = 0; j < n; ++j) {
-        acc192 pos = {0, 0, 0}, neg = {0, 0, 0};
-        /* i + k = j : k = j - i for i <= j */
-        for (uint64_t i = 0; i <= j; ++i)
-            acc_add(&pos, (u128)a[i] * b[j - i]);
-        /* i + k = j + n : k = j + n - i for i > j */
-        for (uint64_t i = j + 1; i < n; ++i)
-            acc_add(&neg, (u128)a[i] * b[j + n - i]);
-        uint64_t p = acc_mod(&pos, q), m = acc_mod(&neg, q);
-        c[j] = p >= m ? p - m : (uint64_t)(((u128)p + q) - m);
-    }
+    for (uint64_t j = 0; j < n; ++j)
+        c[j] = coeff(a, b, n, q, j, 0);
+}
+
+void oracle_cyclic(const uint64_t *a, const uint64_t *b, uint64_t *c,
+                   uint64_t n, uint64_t q)
+{
+    for (uint64_t j = 0; j < n; ++j)
+        c[j] = coeff(a, b, n, q, j, 1);
 }
 
 /*
  * Batch over a [batch][k][n] layout (uint64 entries): products
  * first .. first+count-1, every prime of each.
  */
-void oracle_negacyclic_batch(const uint64_t *a, const uint64_t *b, uint64_t *c,
-                             uint64_t n, const uint64_t *q_list, uint64_t k,
-                             uint64_t first, uint64_t count)
+static void batch(const uint64_t *a, const uint64_t *b, uint64_t *c, uint64_t n,
+                  const uint64_t *q_list, uint64_t k, uint64_t first, uint64_t count, int cyclic)
 {
     for (uint64_t p = first; p < first + count; ++p)
         for (uint64_t j = 0; j < k; ++j) {
             size_t off = (size_t)((p * k + j) * n);
-            oracle_negacyclic(a + off, b + off, c + off, n, q_list[j]);
+            for (uint64_t t = 0; t < n; ++t)
+                c[off + t] = coeff(a + off, b + off, n, q_list[j], t, cyclic);
         }
+}
+
+void oracle_negacyclic_batch(const uint64_t *a, const uint64_t *b, uint64_t *c,
+                             uint64_t n, const uint64_t *q_list, uint64_t k,
+                             uint64_t first, uint64_t count)
+{
+    batch(a, b, c, n, q_list, k, first, count, 0);
+}
+
+void oracle_cyclic_batch(const uint64_t *a, const uint64_t *b, uint64_t *c,
+                         uint64_t n, const uint64_t *q_list, uint64_t k,
+                         uint64_t first, uint64_t count)
+{
+    batch(a, b, c, n, q_list, k, first, count, 1);
 }
 
 /* Only the listed output coefficients of one product (sampled parity). */
 void oracle_negacyclic_coeffs(const uint64_t *a, const uint64_t *b, uint64_t n, uint64_t q,
                               const uint64_t *js, uint64_t count, uint64_t *out)
 {
-    for (uint64_t t = 0; t < count; ++t) {
-        uint64_t j = js[t];
-        acc192 pos = {0, 0, 0}, neg = {0, 0, 0};
-        for (uint64_t i = 0; i <= j; ++i)
-            acc_add(&pos, (u128)a[i] * b[j - i]);
-        for (uint64_t i = j + 1; i < n; ++i)
-            acc_add(&neg, (u128)a[i] * b[j + n - i]);
-        uint64_t p = acc_mod(&pos, q), m = acc_mod(&neg, q);
-        out[t] = p >= m ? p - m : (uint64_t)(((u128)p + q) - m);
-    }
+    for (uint64_t t = 0; t < count; ++t)
+        out[t] = coeff(a, b, n, q, js[t], 0);
+}
+
+void oracle_cyclic_coeffs(const uint64_t *a, const uint64_t *b, uint64_t n, uint64_t q,
+                          const uint64_t *js, uint64_t count, uint64_t *out)
+{
+    for (uint64_t t = 0; t < count; ++t)
+        out[t] = coeff(a, b, n, q, js[t], 1);
 }

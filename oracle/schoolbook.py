@@ -28,6 +28,13 @@ nothing can overflow; speed is not a goal.  Functions follow the paper
                                small coprime moduli whose product exceeds
                                l*q^2, per-modulus matrix products, CRT back,
                                then mod q.
+* ``fold_cyclic`` / ``cyclic_mul`` /
+  ``circulant_matrix``      -- the ring Z_q[x]/(x^n-1), which Sec. 2.1 names
+                               as the other common ring and to which Sec. 2.5
+                               says the matrix form carries over: x^n = 1, so
+                               c_d is added to c_{d-n}; the matrix is the
+                               circulant of b (rows shifted right by one, the
+                               wrapped entry kept).
 
 Readings of the paper taken here (each is pinned by a test):
 * orientation: c = a * T(b) with T[i][j] = b_{j-i} for j >= i and
@@ -240,15 +247,63 @@ def rns_polymul(a: Sequence[int], b: Sequence[int], q: int, moduli: Sequence[int
 
 
 # --------------------------------------------------------------------------
+# the cyclic ring Z_q[x]/(x^n - 1) (Sec. 2.1, Sec. 2.5)
+# --------------------------------------------------------------------------
+def fold_cyclic(full: Sequence, n: int) -> list:
+    """Reduce a Z[x] coefficient list modulo x^n - 1: the term c_d x^d with
+    d >= n is removed and c_d is added to the coefficient of x^(d-n)
+    (x^n = 1), from the top degree down."""
+    c = list(full)
+    for d in range(len(c) - 1, n - 1, -1):
+        c[d - n] = c[d - n] + c[d]
+        c[d] = 0
+    return c[:n] + [0] * max(0, n - len(c))
+
+
+def cyclic_convolution(a: Sequence, b: Sequence) -> list:
+    """a*b in Z[x]/(x^n-1) over the integers (no reduction mod q)."""
+    n = len(a)
+    if len(b) != n:
+        raise ValueError("operands must have the same length")
+    return fold_cyclic(full_product(a, b), n)
+
+
+def cyclic_mul(a: Sequence[int], b: Sequence[int], q: int) -> List[int]:
+    """c = a*b in Z_q[x]/(x^n-1), coefficients canonical in [0, q)."""
+    if q < 2:
+        raise ValueError("q must be >= 2")
+    return [int(x) % q for x in cyclic_convolution([int(v) for v in a], [int(v) for v in b])]
+
+
+def circulant_matrix(b: Sequence) -> list:
+    """The n x n matrix of multiplication by b in Z[x]/(x^n-1): row 0 is
+    (b_0 .. b_{n-1}); every further row is the row above shifted right by
+    one place, the entry that wraps around to column 0 kept as it is.
+    Entry [i][j] is b_{(j-i) mod n}."""
+    n = len(b)
+    rows = [list(b)]
+    for _ in range(1, n):
+        prev = rows[-1]
+        rows.append([prev[n - 1]] + prev[: n - 1])
+    return rows
+
+
+def circulant_form_mul(a: Sequence[int], b: Sequence[int], q: int) -> List[int]:
+    return [int(x) % q for x in vec_mat([int(v) for v in a], circulant_matrix([int(v) for v in b]))]
+
+
+# --------------------------------------------------------------------------
 # batched driver over numpy arrays ([batch][k][n], canonical residues)
 # --------------------------------------------------------------------------
-def polymul_batch(a: np.ndarray, b: np.ndarray, q_list: Sequence[int]) -> np.ndarray:
-    """Python-integer oracle over a [batch][k][n] batch.  Slow (n^2 Python
-    multiplications per product); meant for small cases."""
+def polymul_batch(a: np.ndarray, b: np.ndarray, q_list: Sequence[int], cyclic: bool = False) -> np.ndarray:
+    """Python-integer oracle over a [batch][k][n] batch (the cyclic ring
+    when ``cyclic``).  Slow (n^2 Python multiplications per product); meant
+    for small cases."""
     if a.shape != b.shape or a.ndim != 3 or a.shape[1] != len(q_list):
         raise ValueError("shape mismatch")
+    mul = cyclic_mul if cyclic else negacyclic_mul
     out = np.zeros(a.shape, dtype=np.uint64)
     for p in range(a.shape[0]):
         for j, q in enumerate(q_list):
-            out[p, j] = negacyclic_mul(a[p, j].tolist(), b[p, j].tolist(), int(q))
+            out[p, j] = mul(a[p, j].tolist(), b[p, j].tolist(), int(q))
     return out

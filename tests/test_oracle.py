@@ -11,8 +11,10 @@ mathematics, never from the oracle itself and never from the CUDA path.
 * Kronecker substitution with CPython big-int multiplication (a different
   exact algorithm) against the C oracle at mid sizes;
 * Sec. 2.5 divide identity, Sec. 4 Karatsuba identity, Sec. 2.4/2.6 RNS.
-A last test plants plausible mistakes in copies of the oracle and checks
-that some pin catches each one.
+A test plants plausible mistakes in copies of the oracle and checks that
+some pin catches each one.  The cyclic ring x^n - 1 (named in Sec. 2.1) has
+its own pins of the same kinds at the end, including numpy's FFT splitting
+the full product into both rings.
 """
 import os
 import random
@@ -380,3 +382,197 @@ def test_planted_mistakes_are_caught():
     for bad in (wrap_sign_dropped, transposed_matrix, off_by_one_fold, lazy_output,
                 dropped_term, shift_direction):
         assert _pins_fail(bad), bad.__name__
+
+
+# ---------------------------------------------------------------- the cyclic ring x^n - 1
+# Sec. 2.1 names Z_q[x]/(x^n-1) as the other common ring; Sec. 2.5 says the
+# matrix form carries over to other moduli.  Pins of the same kinds: the
+# monomial rule x^n = 1, brute force against numpy's long division by x^n - 1,
+# evaluation at all n-th roots of unity (complete when q = 1 mod n is prime),
+# numpy's FFT splitting the full product into both rings, and planted mistakes.
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 16, 33])
+def test_cyclic_monomial_rule(n):
+    for i in range(n):
+        for j in range(n):
+            ei = [0] * n
+            ej = [0] * n
+            ei[i] = 1
+            ej[j] = 1
+            want = [0] * n
+            want[(i + j) % n] = 1
+            assert sb.cyclic_convolution(ei, ej) == want, (n, i, j)
+            if n <= 16:
+                got = native.polymul_one(np.array(ei, np.uint64), np.array(ej, np.uint64), 97, cyclic=True)
+                assert got.tolist() == want
+
+
+def _numpy_remainder_cyclic(a, b, n, q):
+    """Z[x] product and remainder by x^n - 1 via numpy.polynomial."""
+    from numpy.polynomial import polynomial as P
+    prod = P.polymul(np.array(a, dtype=np.float64), np.array(b, dtype=np.float64))
+    div = np.zeros(n + 1)
+    div[0] = -1.0
+    div[n] = 1.0
+    _, rem = P.polydiv(prod, div)
+    rem = list(np.rint(rem).astype(np.int64)) + [0] * n
+    return [int(v) % q for v in rem[:n]]
+
+
+@pytest.mark.parametrize("n,q", [(1, 5), (2, 3), (3, 4), (4, 3), (2, 5)])
+def test_cyclic_brute_force_all_pairs_tiny(n, q):
+    import itertools
+    polys = list(itertools.product(range(q), repeat=n))
+    for a in polys:
+        for b in polys:
+            assert sb.cyclic_mul(list(a), list(b), q) == _numpy_remainder_cyclic(a, b, n, q)
+
+
+@pytest.mark.parametrize("n", [5, 8, 12, 16])
+def test_cyclic_brute_force_random_small(n):
+    rng = random.Random(100 + n)
+    for q in (2, 7, 97, 3329, 40961):
+        for _ in range(10):
+            a = _rand_poly(rng, n, q)
+            b = _rand_poly(rng, n, q)
+            want = _numpy_remainder_cyclic(a, b, n, q)
+            assert sb.cyclic_mul(a, b, q) == want
+            assert sb.circulant_form_mul(a, b, q) == want
+            got = native.polymul_one(np.array(a, np.uint64), np.array(b, np.uint64), q, cyclic=True)
+            assert got.tolist() == want
+
+
+def _primitive_n_root(q, n):
+    """Some w of multiplicative order exactly n mod prime q (q = 1 mod n)."""
+    assert (q - 1) % n == 0
+    for g in range(2, q):
+        w = pow(g, (q - 1) // n, q)
+        if all(pow(w, n // p, q) != 1 for p in (2, 3, 5, 7) if n % p == 0):
+            return w
+    raise AssertionError
+
+
+@pytest.mark.parametrize("n,q", [(16, 97), (64, 193), (256, 7681), (1024, 12289), (3, 7)])
+def test_cyclic_root_evaluation_complete(n, q):
+    rng = random.Random(7 * n + q)
+    a = _rand_poly(rng, n, q)
+    b = _rand_poly(rng, n, q)
+    c = native.polymul_one(np.array(a, np.uint64), np.array(b, np.uint64), q, cyclic=True).tolist()
+    if n <= 256:
+        assert c == sb.cyclic_mul(a, b, q)
+    w = _primitive_n_root(q, n)
+    roots = [pow(w, i, q) for i in range(n)]
+    assert len(set(roots)) == n  # n distinct roots of x^n - 1: the check is complete
+    step = 1 if n <= 256 else 5
+    for r in roots[::step]:
+        assert pow(r, n, q) == 1
+        assert _evaluate(c, r, q) == _evaluate(a, r, q) * _evaluate(b, r, q) % q
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 64])
+def test_fft_full_product_splits_into_both_rings(n):
+    """x^(2n) - 1 = (x^n - 1)(x^n + 1): the full product p = low + x^n high
+    (computed by numpy's FFT, exact for these small integers) reduces to
+    low + high in the cyclic ring and low - high in the negacyclic one."""
+    rng = random.Random(n)
+    a = [rng.randrange(50) for _ in range(n)]
+    b = [rng.randrange(50) for _ in range(n)]
+    fa = np.fft.rfft(np.array(a + [0] * n, dtype=np.float64))
+    fb = np.fft.rfft(np.array(b + [0] * n, dtype=np.float64))
+    full = [int(v) for v in np.rint(np.fft.irfft(fa * fb, 2 * n))]
+    low, high = full[:n], full[n:]
+    assert sb.cyclic_convolution(a, b) == [x + y for x, y in zip(low, high)]
+    assert sb.negacyclic_convolution(a, b) == [x - y for x, y in zip(low, high)]
+
+
+@pytest.mark.parametrize("n,q", [(1, 7), (8, 17), (16, 3329), (33, 1000), (64, (1 << 59) + 21)])
+def test_cyclic_identity_rotation_and_laws(n, q):
+    rng = random.Random(n * 3 + q % 97)
+    a = _rand_poly(rng, n, q)
+    b = _rand_poly(rng, n, q)
+    c = _rand_poly(rng, n, q)
+    one = [1] + [0] * (n - 1)
+    assert sb.cyclic_mul(a, one, q) == a
+    if n > 1:
+        x = [0, 1] + [0] * (n - 2)
+        assert sb.cyclic_mul(x, a, q) == [a[n - 1]] + a[: n - 1]  # rotation, nothing negated
+        r = a
+        for _ in range(n):
+            r = sb.cyclic_mul(x, r, q)
+        assert r == a  # x^n = 1
+    ab = sb.cyclic_mul(a, b, q)
+    assert ab == sb.cyclic_mul(b, a, q)
+    assert sb.cyclic_mul(ab, c, q) == sb.cyclic_mul(a, sb.cyclic_mul(b, c, q), q)
+    bc = [(u + v) % q for u, v in zip(b, c)]
+    assert sb.cyclic_mul(a, bc, q) == [(u + v) % q for u, v in zip(ab, sb.cyclic_mul(a, c, q))]
+    got = native.polymul_one(np.array(a, np.uint64), np.array(b, np.uint64), q, cyclic=True)
+    assert got.tolist() == ab
+    js = sorted(set([0, n - 1, n // 2]))
+    assert native.coeffs(np.array(a, np.uint64), np.array(b, np.uint64), q, js, cyclic=True).tolist() == \
+        [ab[j] for j in js]
+
+
+def test_circulant_matrix_rows():
+    b = [10, 20, 30, 40]
+    assert sb.circulant_matrix(b) == [[10, 20, 30, 40], [40, 10, 20, 30], [30, 40, 10, 20], [20, 30, 40, 10]]
+
+
+def _cyclic_pins_fail(mul):
+    rng = random.Random(2)
+    try:
+        for n in (3, 8):
+            for i in range(n):
+                for j in range(n):
+                    ei = [0] * n
+                    ej = [0] * n
+                    ei[i] = ej[j] = 1
+                    want = [0] * n
+                    want[(i + j) % n] = 1
+                    if mul(ei, ej, 97) != want:
+                        return True
+        n, q = 16, 97
+        a = _rand_poly(rng, n, q)
+        b = _rand_poly(rng, n, q)
+        c = mul(a, b, q)
+        if any(not (0 <= v < q) for v in c):
+            return True
+        w = _primitive_n_root(q, n)
+        for i in range(n):
+            r = pow(w, i, q)
+            if _evaluate(c, r, q) != _evaluate(a, r, q) * _evaluate(b, r, q) % q:
+                return True
+        if mul(a[:5], b[:5], q) != _numpy_remainder_cyclic(a[:5], b[:5], 5, q):
+            return True
+    except Exception:
+        return True
+    return False
+
+
+def test_cyclic_planted_mistakes_are_caught():
+    assert not _cyclic_pins_fail(sb.cyclic_mul)
+    assert not _cyclic_pins_fail(sb.circulant_form_mul)
+    assert not _cyclic_pins_fail(lambda a, b, q: native.polymul_one(np.array(a, np.uint64), np.array(b, np.uint64),
+                                                                    q, cyclic=True).tolist())
+
+    def negacyclic_instead(a, b, q):
+        return sb.negacyclic_mul(a, b, q)
+
+    def wrap_dropped(a, b, q):  # the product truncated to degree < n
+        return [v % q for v in sb.full_product(a, b)[: len(a)]]
+
+    def off_by_one_wrap(a, b, q):
+        full = sb.full_product(a, b)
+        n = len(a)
+        c = list(full[:n])
+        for d in range(n, len(full)):
+            c[(d - n + 1) % n] += full[d]
+        return [v % q for v in c]
+
+    def transposed_circulant(a, b, q):
+        t = [list(r) for r in zip(*sb.circulant_matrix(b))]
+        return [v % q for v in sb.vec_mat(a, t)]
+
+    def lazy_output(a, b, q):
+        return [v + q if v < q // 3 else v for v in sb.cyclic_mul(a, b, q)]
+
+    for bad in (negacyclic_instead, wrap_dropped, off_by_one_wrap, transposed_circulant, lazy_output):
+        assert _cyclic_pins_fail(bad), bad.__name__
