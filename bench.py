@@ -207,8 +207,9 @@ class Samples:
         self.rows = []    # (name, a [m][k][n], b [m][k][n], q_list, got [m][k][n])
         self.coeffs = []  # (name, a [n], b [n], q, coefficient indices, got)
 
-    def add(self, name, a, b, q_list, got):
-        self.rows.append((name, np.asarray(a), np.asarray(b), list(q_list), np.asarray(got, dtype=np.uint64)))
+    def add(self, name, a, b, q_list, got, cyclic=False):
+        self.rows.append((name, np.asarray(a), np.asarray(b), list(q_list), np.asarray(got, dtype=np.uint64),
+                          cyclic))
 
     def add_coeffs(self, name, a, b, q, js, got):
         self.coeffs.append((name, np.asarray(a), np.asarray(b), int(q), list(js), np.asarray(got, dtype=np.uint64)))
@@ -217,8 +218,8 @@ class Samples:
         """name -> every sample of that name equals the oracle's result."""
         from oracle import native
         ok = {}
-        for name, a, b, q_list, got in self.rows:
-            want = native.polymul_batch(a, b, q_list)
+        for name, a, b, q_list, got, cyclic in self.rows:
+            want = native.polymul_batch(a, b, q_list, cyclic=cyclic)
             ok[name] = ok.get(name, True) and bool(np.array_equal(got.reshape(want.shape), want))
         for name, a, b, q, js, got in self.coeffs:
             ok[name] = ok.get(name, True) and bool(np.array_equal(got, native.coeffs(a, b, q, js)))
@@ -286,16 +287,18 @@ def _time_steps(step, stream, reps):
 def other_workloads(dev, stream, peaks, alu_peak_g, samples):
     """Throughput of the other standing workloads (not the headline line):
     n=256 q=3329 (auxiliary-prime NTT, launch-latency bound), n=4096 with 8
-    RNS primes and ternary b, and the 2000-product uneven list (one
-    persistent launch replayed as a CUDA graph)."""
+    RNS primes and ternary b, the headline's batch in the cyclic ring
+    x^n - 1, and the 2000-product uneven list (one persistent launch
+    replayed as a CUDA graph)."""
     import torch
     from paper_2307_06554_gb300 import polymul, workloads as wl
     out = {}
     sp = stream.cuda_stream
     hbm = peaks["hbm_gbs"]
 
-    def homogeneous(name, w, sets_needed, reps):
-        plan = polymul.Plan(w.n, w.q_list, flags=polymul.FLAG_TUNE, tune_batch=w.batch)
+    def homogeneous(name, w, sets_needed, reps, cyclic=False):
+        flags = polymul.FLAG_TUNE | (polymul.FLAG_CYCLIC if cyclic else 0)
+        plan = polymul.Plan(w.n, w.q_list, flags=flags, tune_batch=w.batch)
         k = len(w.q_list)
         elem = plan.elem_bytes
         view = np.int32 if elem == 4 else np.int64
@@ -311,7 +314,7 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
         ms = _time_steps(step, stream, reps)
         idx = [0, w.batch - 1]
         got = sets[(reps - 1) % len(sets)][2][idx].cpu().numpy().view(w.a.dtype)
-        samples.add(name, w.a[idx], w.b[idx], w.q_list, got)
+        samples.add(name, w.a[idx], w.b[idx], w.q_list, got, cyclic=cyclic)
         units = w.batch * k
         mm = units * _ntt_mulmods(w.n)
         byts = 3 * units * w.n * elem
@@ -331,6 +334,8 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
 
     homogeneous("ring_small", wl.ring_small(), 1, 200)
     homogeneous("rns_4096", wl.rns_4096(), 6, 20)
+    # the cyclic ring x^n - 1 on the headline's shape and data
+    homogeneous("ring_1024_cyclic", wl.ring_1024(), 9, 50, cyclic=True)
 
     rag = wl.ragged_2000()
     total = sum(p.n * len(p.prime_idx) for p in rag.products)

@@ -10,7 +10,10 @@
  * i.e. the product in Z[x] reduced by x^n = -1 (Sec. 2.2 fold rule) and taken
  * mod q, which is the row vector a times the negacyclic matrix of b of
  * Eq. equ-genereal-mat.  Results are canonical residues in [0, q) and are
- * bit-exact: no floating-point rounding can reach them.
+ * bit-exact: no floating-point rounding can reach them.  With
+ * POLYMUL_FLAG_CYCLIC the ring is Z_q[x]/(x^n-1), the other ring Sec. 2.1
+ * names: x^n = 1, so the second sum is added, and the matrix is the
+ * circulant of b (Sec. 2.5 notes that the matrix form adapts to the modulus).
  *
  * Algorithm 1 of the paper maps onto this interface as follows:
  * GenConfig / ExtractModuli / ExtractDimensions  ->  polymul_create
@@ -63,6 +66,10 @@ extern "C" {
 /* ---- flags ---- */
 #define POLYMUL_FLAG_VALIDATE 1u  /* check that inputs are < q (slower)       */
 #define POLYMUL_FLAG_TUNE     2u  /* time the candidate kernels at creation    */
+#define POLYMUL_FLAG_CYCLIC   4u  /* the ring Z_q[x]/(x^n - 1) instead of
+                                     Z_q[x]/(x^n + 1) (Sec. 2.1 names it as the
+                                     other common ring): the NTT path then needs
+                                     q = 1 mod n; every path supports it      */
 
 typedef struct polymul_opts {
     uint32_t path;        /* POLYMUL_PATH_*                                   */
@@ -97,14 +104,16 @@ typedef struct polymul_plan_info {
                              2 = unreduced (small q)                        */
     uint32_t regs;        /* NTT path: register budget per thread of the main
                              kernel (fewer registers, more resident warps)  */
-    uint32_t reserved[2];
+    uint32_t cyclic;      /* 1: the ring Z_q[x]/(x^n-1); 0: Z_q[x]/(x^n+1) */
+    uint32_t reserved[1];
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
 
 /*
- * polymul_create -- build a plan for products in Z_q[x]/(x^n+1) for each q
- * of q_list (Algorithm 1, GenConfig: parameters are fixed here, once).
+ * polymul_create -- build a plan for products in Z_q[x]/(x^n+1) (or in
+ * Z_q[x]/(x^n-1) with POLYMUL_FLAG_CYCLIC) for each q of q_list
+ * (Algorithm 1, GenConfig: parameters are fixed here, once).
  *   n       power of two, 16 <= n <= 65536.
  *   q_list  k moduli, each 2 <= q < 2^62, pairwise distinct (host memory,
  *           read during the call only).

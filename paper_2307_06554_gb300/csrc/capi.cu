@@ -65,7 +65,7 @@ int upload_ntt_tables(polymul_plan* p) {
   all_f.reserve(2 * (size_t)p->n * np);
   all_i.reserve(2 * (size_t)p->n * np);
   for (uint32_t j = 0; j < np; ++j) {
-    build_ntt_tables<W>(primes[j], p->n, f, i, pcs[j]);
+    build_ntt_tables<W>(primes[j], p->n, f, i, pcs[j], p->cyclic);
     all_f.insert(all_f.end(), f.begin(), f.end());
     all_i.insert(all_i.end(), i.begin(), i.end());
   }
@@ -226,13 +226,16 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
   p->k = k;
   p->q.assign(q_list, q_list + k);
   p->flags = opts ? opts->flags : 0;
+  p->cyclic = (p->flags & POLYMUL_FLAG_CYCLIC) != 0;
   uint64_t qmax = *std::max_element(p->q.begin(), p->q.end());
   p->elem = qmax < (1ull << 32) ? 4 : 8;
 
-  // direct NTT: every modulus prime with 2n | q-1 and within the word bounds
+  // direct NTT: every modulus prime with 2n | q-1 (n | q-1 for the cyclic
+  // ring) and within the word bounds
+  const uint64_t root_order = p->cyclic ? n : 2ull * n;
   bool ntt_ok = true;
   for (uint64_t q : p->q) {
-    if (!pm::host::is_prime(q) || (q - 1) % (2ull * n) != 0) ntt_ok = false;
+    if (!pm::host::is_prime(q) || (q - 1) % root_order != 0) ntt_ok = false;
     if (p->elem == 4 && q >= (1ull << 31)) ntt_ok = false;
   }
   p->mode = ntt_mode(qmax, p->logn, p->elem);
@@ -280,7 +283,8 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
       if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
     }
   } else if (!ntt_ok) {
-    rc = fail(POLYMUL_ENOTSUP, "no NTT route for these moduli at n=%u (need prime q = 1 mod 2n, q < 2^31 for 32-bit words)", n);
+    rc = fail(POLYMUL_ENOTSUP, "no NTT route for these moduli at n=%u (need prime q = 1 mod %s, q < 2^31 for 32-bit words)",
+              n, p->cyclic ? "n" : "2n");
   } else {
     // the default kernel first, then the candidates the autotuner may prefer
     rc = p->elem == 4 ? upload_ntt_tables<uint32_t>(p) : upload_ntt_tables<uint64_t>(p);
@@ -367,6 +371,7 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->launch_flags = p->launch_flags;
   info->ntt_mode = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.mode : 0u;
   info->regs = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.regs : 0u;
+  info->cyclic = p->cyclic ? 1u : 0u;
   return POLYMUL_OK;
 }
 
@@ -449,7 +454,7 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
   };
   if (p->path == POLYMUL_PATH_TENSOR) {
     TensorBatchArgs args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, (const TensorPrime*)p->d_tpc,
-                         units, p->k, ctr, p->d_err};
+                         units, p->k, p->cyclic ? 0u : 0x80008000u, ctr, p->d_err};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
   } else if (p->elem == 4) {

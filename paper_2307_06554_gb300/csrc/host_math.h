@@ -62,6 +62,17 @@ inline uint64_t primitive_2n_root(uint64_t q, uint64_t n) {
   return 0;
 }
 
+// w of multiplicative order exactly n (mod prime q; n a power of two >= 2),
+// i.e. w^(n/2) = -1.  Requires n | q-1.  Deterministic: smallest base.
+inline uint64_t primitive_n_root(uint64_t q, uint64_t n) {
+  uint64_t e = (q - 1) / n;
+  for (uint64_t g = 2; g < q; ++g) {
+    uint64_t w = powmod(g, e, q);
+    if (powmod(w, n / 2, q) == q - 1) return w;
+  }
+  return 0;
+}
+
 inline uint32_t bitrev(uint32_t x, int bits) {
   uint32_t r = 0;
   for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);

@@ -1,5 +1,14 @@
 // Host-side NTT tables of one prime (plan creation): bit-reversed powers of
 // psi and psi^-1 with Shoup companions, and the per-prime constants.
+//
+// The kernels walk a fixed tree of butterflies; the ring is set by the
+// table.  Entry k (heap order, level l = floor(log2 k), j = k - 2^l) is the
+// root that splits node k's polynomial x^(2m) - z^2 into x^m - z and
+// x^m + z:
+//   x^n + 1 (negacyclic): psi^brv(k), psi of order 2n (q = 1 mod 2n);
+//   x^n - 1 (cyclic, Sec. 2.1's other ring): w^(brv(j)/2), w of order n
+//   (q = 1 mod n); the root node splits x^n - 1 by z = 1.
+// brv is the bit reversal over log2 n bits.
 #pragma once
 #include <cstdint>
 #include <vector>
@@ -10,17 +19,20 @@
 namespace pm {
 
 template <typename W>
-inline void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::vector<W>& twi, PrimeConst<W>& pc) {
+inline void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::vector<W>& twi, PrimeConst<W>& pc,
+                             bool cyclic = false) {
   using namespace pm::host;
   using pm::host::u128;
   const int bits = 8 * (int)sizeof(W);
   const int logn = __builtin_ctz(n);
-  const uint64_t psi = primitive_2n_root(q, n);
+  // negacyclic: root psi, exponent brv(k); cyclic: root w, exponent brv(j)/2
+  const uint64_t psi = cyclic ? primitive_n_root(q, n) : primitive_2n_root(q, n);
   const uint64_t psi_inv = powmod(psi, q - 2, q);
   twf.resize(2 * (size_t)n);
   twi.resize(2 * (size_t)n);
   for (uint32_t i = 0; i < n; ++i) {
-    const uint32_t r = bitrev(i, logn);
+    uint32_t r = bitrev(i, logn);
+    if (cyclic) r = i == 0 ? 0u : bitrev(i - (1u << (31 - __builtin_clz(i))), logn) / 2;
     const uint64_t w = powmod(psi, r, q), v = powmod(psi_inv, r, q);
     twf[2 * i] = (W)w;
     twf[2 * i + 1] = (W)shoup_companion(w, q, bits);
@@ -30,7 +42,9 @@ inline void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::v
   const uint64_t r_mod_q = bits == 64 ? (uint64_t)(((u128)1 << 64) % q) : (uint64_t)((1ull << 32) % q);
   const uint64_t ninv = powmod(n, q - 2, q);
   const uint64_t scale = mulmod(ninv, r_mod_q, q);
-  const uint64_t scale_w = mulmod(powmod(psi_inv, bitrev(1, logn), q), scale, q);
+  // the last inverse stage's twiddle (table entry 1) folded into its scale
+  const uint64_t v1 = cyclic ? 1 : powmod(psi_inv, bitrev(1, logn), q);
+  const uint64_t scale_w = mulmod(v1, scale, q);
   pc.q = (W)q;
   pc.q2 = (W)(2 * q);
   pc.qinv = (W)inv_pow2_64(q);  // low bits are the inverse mod 2^32 too

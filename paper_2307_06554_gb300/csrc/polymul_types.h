@@ -89,6 +89,7 @@ struct TensorBatchArgs {
   const TensorPrime* tp;  // [k]
   uint64_t units;         // batch * k
   uint32_t k;
+  uint32_t wrap;          // sign of the operand extensions, as a bf16x2 XOR mask: 0x80008000 for x^n + 1, 0 for x^n - 1
   unsigned long long* ctr;  // {next unit, finished CTAs}
   int* err;
 };

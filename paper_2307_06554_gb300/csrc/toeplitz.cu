@@ -18,7 +18,9 @@
 //   A[u][k] = a~_{8u + k - 8(n/8 - 1)}            (block-Hankel in a)
 //   B[v][k] = b~_{8(n/8 - 1 - d') + v - r}         (block-Toeplitz in b)
 // where a~, b~ are the antiperiodic extensions (x~_{i-n} = -x_i), so the n
-// terms of every sum are exactly the negacyclic convolution.  A's rows are
+// terms of every sum are exactly the negacyclic convolution; with periodic
+// extensions (x~_{i-n} = x_i) the same sums are the cyclic convolution of
+// Z_q[x]/(x^n-1), the other ring Sec. 2.1 names (args.wrap selects).  A's rows are
 // its digit array shifted by 8 elements = 16 bytes per row, which is the row
 // pitch of a tcgen05 core matrix: A is read straight from the 1-D digit
 // array through a descriptor with 16-byte K stride and 128-byte row-group
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t units = args.units;
   const uint32_t k = args.k;
+  const uint32_t wrap = args.wrap;  // sign flip of the wrapped-around copies (x^n + 1), none for x^n - 1
   constexpr uint32_t IDESC = idesc_bf16(128, TS::NB);
   constexpr int HALF = 1 << (TS::WB - 1), MASK = (1 << TS::WB) - 1;
 
@@ -161,8 +164,7 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
         const uint4 p = make_uint4(bf16x2_of(da[s][0], da[s][1]), bf16x2_of(da[s][2], da[s][3]),
                                    bf16x2_of(da[s][4], da[s][5]), bf16x2_of(da[s][6], da[s][7]));
         *reinterpret_cast<uint4*>(xs + TS::N + i0) = p;
-        *reinterpret_cast<uint4*>(xs + i0) =
-            make_uint4(p.x ^ 0x80008000u, p.y ^ 0x80008000u, p.z ^ 0x80008000u, p.w ^ 0x80008000u);
+        *reinterpret_cast<uint4*>(xs + i0) = make_uint4(p.x ^ wrap, p.y ^ wrap, p.z ^ wrap, p.w ^ wrap);
       }
 #pragma unroll
       for (int s = 0; s < TS::LB; ++s)
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
     // ---- B tile: row (s', v), column k = 8 d' + r holds b~_{8(D - d') + v - r} ----
     // For the K-block d' = D - g of group g, E[i] = b~_{8g - 8 + i} (i < 16)
     // is the previous group followed by the own one (group -1 is minus the
-    // last group: the antiperiodic extension); row v is E[v + 8 - r],
+    // last group, negated for x^n + 1: the extension); row v is E[v + 8 - r],
     // r = 0..7, a reversed window cut from E with byte permutes.
 #pragma unroll
     for (int gi = 0; gi < TS::GPT; ++gi) {
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
           pv.w = __shfl_up_sync(0xffffffffu, last.w, 1);
           if (lane == 0) {
             pv = s_edge[(warp + 3) & 3][s2];
-            if (warp == 0) pv = make_uint4(pv.x ^ 0x80008000u, pv.y ^ 0x80008000u, pv.z ^ 0x80008000u, pv.w ^ 0x80008000u);
+            if (warp == 0) pv = make_uint4(pv.x ^ wrap, pv.y ^ wrap, pv.z ^ wrap, pv.w ^ wrap);
           }
         }
         const uint4 ow = bw[gi][s2];

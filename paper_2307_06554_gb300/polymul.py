@@ -28,6 +28,7 @@ PATH_NTT = 1
 PATH_TENSOR = 2
 FLAG_VALIDATE = 1
 FLAG_TUNE = 2
+FLAG_CYCLIC = 4  # the ring Z_q[x]/(x^n-1) instead of Z_q[x]/(x^n+1)
 
 _ERRNAMES = {1: "EINVAL", 2: "ENOTSUP", 3: "EDOMAIN", 4: "ENOMEM", 5: "ETIMEOUT", 6: "ECUDA"}
 
@@ -47,7 +48,7 @@ class polymul_plan_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
                  "digit_bits", "digits", "radix_bits", "candidates", "tuned", "tuned_batch",
-                 "launch_flags", "ntt_mode", "regs")] + [("reserved", ctypes.c_uint32 * 2)]
+                 "launch_flags", "ntt_mode", "regs", "cyclic")] + [("reserved", ctypes.c_uint32 * 1)]
 
 
 class polymul_desc(ctypes.Structure):
