@@ -429,6 +429,62 @@ def crossover(dev, stream, peaks, alu_peak_g, samples):
             "tensor_wins_at": [r["n"] for r in rows if r["tensor_over_ntt"] > 1.0]}
 
 
+def shared_operand(dev, stream, peaks, samples):
+    """One operand a shared by the whole batch (the paper's many-vector
+    batching): c_i = a * b_i as the GEMM C = B * T(a) on the tensor cores
+    (polymul_batch_shared), against the NTT batch on the same products (a
+    repeated per product).  ring_1024's b operands and its first a, and the
+    same at n = 2048."""
+    import torch
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+    sp = stream.cuda_stream
+    rows = []
+    for n in (1024, 2048):
+        w = wl.ring_1024(n=n, batch=4096 * 1024 // n)
+        batch, q_list = w.batch, w.q_list
+        a = w.a[0]
+        ta = torch.from_numpy(a.view(np.int32)).to(dev)
+        tb = torch.from_numpy(w.b.view(np.int32)).to(dev)
+        nsets = max(2, math.ceil(3 * L2_BYTES / (2 * tb.numel() * 4)))
+        sets = [(tb.clone(), torch.empty_like(tb)) for _ in range(nsets)]
+        row = {"n": n, "batch": batch, "q": q_list}
+        with polymul.Plan(n, q_list, path=polymul.PATH_TENSOR) as plan:
+            def step(i, h=plan.handle):
+                x, y = sets[i % nsets]
+                polymul.polymul_batch_shared(h, ta, x, y, batch, sp)
+            for i in range(3):
+                step(i)
+            ms = _time_steps(step, stream, 20)
+            polymul.polymul_plan_status(plan.handle, sp)
+            c_t = torch.empty_like(tb)
+            polymul.polymul_batch_shared(plan.handle, ta, tb, c_t, batch, sp)
+        flops = 2.0 * batch * n * n * 4  # two digits of each operand: four digit-pair GEMMs
+        peak = peaks.get("bf16_tflops", 1911.7)
+        row.update({"tensor_shared_us": ms * 1e3, "products_per_s": batch / (ms / 1e3),
+                    "tflops": flops / (ms / 1e3) / 1e12, "bf16_frac": flops / (ms / 1e3) / 1e12 / peak})
+        ab = ta.repeat(batch, 1).view(batch, len(q_list), n)
+        with polymul.Plan(n, q_list) as plan:
+            def step2(i, h=plan.handle):
+                x, y = sets[i % nsets]
+                polymul.polymul_batch(h, ab, x, y, batch, sp)
+            for i in range(3):
+                step2(i)
+            ms2 = _time_steps(step2, stream, 20)
+            c_n = torch.empty_like(tb)
+            polymul.polymul_batch(plan.handle, ab, tb, c_n, batch, sp)
+        stream.synchronize()
+        row["ntt_us"] = ms2 * 1e3
+        row["tensor_over_ntt"] = ms2 / ms
+        row["paths_agree"] = bool(torch.equal(c_t, c_n))
+        idx = [0, batch - 1]
+        samples.add("shared_operand", np.stack([w.a[0]] * 2), w.b[idx], q_list, c_t[idx].cpu().numpy().view(np.uint32))
+        rows.append(row)
+        del sets
+    return {"rows": rows, "bit_exact_sample": None,
+            "kernels": "k_shared_bdigits + k_shared_tdigits (digit planes, tiled) + k_shared_gemm "
+                       "(tcgen05 kind::f16, M = N = 128, 4 digit-pair accumulators in tensor memory)"}
+
+
 def serving(dev, peaks, samples, count=20000, lanes=8):
     """The 20k-request serving workload: Poisson arrivals, n uniform over
     4096..65536, 1..32 primes of 59 bits per request (seed 5), operands in
@@ -693,6 +749,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_extras:
         extras = other_workloads(dev, stream, peaks, alu_peak, samples)
         extras["crossover"] = crossover(dev, stream, peaks, alu_peak, samples)
+        extras["shared_operand"] = shared_operand(dev, stream, peaks, samples)
         extras["serve_20k"] = serving(dev, peaks, samples)
 
     # CPU oracle leg: its throughput (the CPU baseline) and its verdict on

@@ -336,6 +336,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_twi);
   cudaFree(p->d_pc);
   cudaFree(p->d_tpc);
+  cudaFree(p->d_sh);
   cudaFree(p->d_flag);
   cudaFree(p->d_ctr);
   cudaFree(p->d_err);

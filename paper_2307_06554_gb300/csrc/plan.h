@@ -49,6 +49,9 @@ struct polymul_plan {
   int* d_flag = nullptr;
   unsigned long long* d_ctr = nullptr;  // 3 x {next, finished}: device entry, 2 host streams
   int* d_err = nullptr;                 // set by kernels whose bounded waits expired
+  // polymul_batch_shared scratch (digit planes of b and of T(a))
+  void* d_sh = nullptr;
+  size_t sh_bytes = 0;
   // polymul_batch_host staging
   void* d_stage[2] = {nullptr, nullptr};
   size_t stage_bytes = 0;

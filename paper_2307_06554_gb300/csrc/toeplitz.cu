@@ -240,6 +240,9 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
       }
       tc_commit(&mbar);
     }
+    // warp 0's other lanes wait for the issuing lane at the warp barrier, not
+    // in mbarrier polls that would suspend the warp it shares with them
+    if (warp == 0) __syncwarp();
 
     // ---- ConvertMatrix: recombine digit pairs, reduce mod q, store ----
     const bool ok = mbar_wait(&mbar, parity);

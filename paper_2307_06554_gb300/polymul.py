@@ -84,6 +84,8 @@ def _load():
     lib.polymul_batch.restype = i32
     lib.polymul_batch_host.argtypes = [vp, vp, vp, vp, u64, vp]
     lib.polymul_batch_host.restype = i32
+    lib.polymul_batch_shared.argtypes = [vp, vp, vp, vp, u64, vp]
+    lib.polymul_batch_shared.restype = i32
     lib.polymul_batch_static.argtypes = [u32, u64, vp, vp, vp, u64, vp]
     lib.polymul_batch_static.restype = i32
     lib.polymul_plan_select.argtypes = [vp, u32]
@@ -184,6 +186,11 @@ def polymul_batch(plan: int, a, b, c, batch: int, stream=None) -> None:
 
 def polymul_batch_host(plan: int, a, b, c, batch: int, stream=None) -> None:
     _check(_lib.polymul_batch_host(plan, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
+
+
+def polymul_batch_shared(plan: int, a, b, c, batch: int, stream=None) -> None:
+    """c_i = a * b_i for one shared operand a ([k][n]) and b, c [batch][k][n]."""
+    _check(_lib.polymul_batch_shared(plan, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
 
 
 def polymul_batch_static(n: int, q: int, a, b, c, batch: int, stream=None) -> None:
