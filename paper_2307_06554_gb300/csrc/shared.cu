@@ -119,47 +119,49 @@ __global__ void k_shared_bdigits(const uint32_t* __restrict__ b, unsigned char* 
 
 // T(a)'s digit planes as the GEMM's B operand (rows = output index jj, K =
 // input index k): entry (jj, k) is the extended a~_{jj-k} (a~_{i-n} = -a_i
-// for x^n + 1, +a_i for x^n - 1).  One CTA per (prime, 128-row block); a's
-// digits in shared memory; 8 consecutive threads write one core matrix.
+// for x^n + 1, +a_i for x^n - 1).  One thread per (prime, 16-byte chunk),
+// spread over the whole GPU; 8 consecutive threads write one core matrix.
+// a is small (n words per prime) and stays in L1/L2.
 template <int WB>
-__global__ void __launch_bounds__(256) k_shared_tdigits(const uint32_t* __restrict__ a, unsigned char* __restrict__ td,
-                                                        const TensorPrime* __restrict__ tp, uint32_t k, uint32_t n,
-                                                        uint32_t wrap) {
+__global__ void k_shared_tdigits(const uint32_t* __restrict__ a, unsigned char* __restrict__ td,
+                                 const TensorPrime* __restrict__ tp, uint32_t k, uint32_t n, uint32_t wrap) {
   constexpr int HALF = 1 << (WB - 1), MASK = (1 << WB) - 1;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  uint16_t* dig = reinterpret_cast<uint16_t*>(sm_raw);  // [L][n] bf16 digits of a (centred)
-  const uint32_t nblocks = n / kShRows;
-  const uint32_t j = blockIdx.x / nblocks, nb = blockIdx.x % nblocks;
-  const uint32_t q = tp[j].q;
-  const int32_t qh = (int32_t)(q >> 1);
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t v = a[(size_t)j * n + i];
-    int32_t x = (int32_t)v > qh ? (int32_t)(v - q) : (int32_t)v;
-#pragma unroll
-    for (int s = 0; s < kShL; ++s) {
-      const int32_t dd = ((x + HALF) & MASK) - HALF;
-      x = (x - dd) >> WB;
-      dig[s * n + i] = (uint16_t)(sh_bf16x2(dd, 0) & 0xFFFFu);
-    }
-  }
-  __syncthreads();
-  const uint32_t kgroups = n / 8;
-  for (uint32_t id = threadIdx.x; id < kShRows * kgroups; id += blockDim.x) {
-    // id = (g * 16 + rg) * 8 + r8
-    const uint32_t r8 = id & 7, rg = (id >> 3) & 15, g = id >> 7;
+  const uint32_t nblocks = n / kShRows, kgroups = n / 8;
+  const uint64_t total = (uint64_t)k * nblocks * kShRows * kgroups;
+  for (uint64_t id = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; id < total;
+       id += (uint64_t)gridDim.x * blockDim.x) {
+    // id = (((j * nblocks + nb) * kgroups + g) * 16 + rg) * 8 + r8
+    const uint32_t r8 = (uint32_t)(id & 7), rg = (uint32_t)((id >> 3) & 15);
+    uint64_t rest = id >> 7;
+    const uint32_t g = (uint32_t)(rest % kgroups);
+    rest /= kgroups;
+    const uint32_t nb = (uint32_t)(rest % nblocks);
+    const uint32_t j = (uint32_t)(rest / nblocks);
     const uint32_t r = rg * 8 + r8, jj = nb * kShRows + r;
+    const uint32_t q = tp[j].q;
+    const int32_t qh = (int32_t)(q >> 1);
+    const uint32_t* aj = a + (size_t)j * n;
+    uint32_t h[kShL][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int32_t idx = (int32_t)jj - (int32_t)(8 * g + e);
+      const uint32_t v = __ldg(aj + (idx >= 0 ? idx : idx + (int32_t)n));
+      int32_t x = (int32_t)v > qh ? (int32_t)(v - q) : (int32_t)v;
+      const uint32_t flip = idx >= 0 ? 0u : (wrap & 0xFFFFu);
+#pragma unroll
+      for (int s = 0; s < kShL; ++s) {
+        const int32_t dd = ((x + HALF) & MASK) - HALF;
+        x = (x - dd) >> WB;
+        h[s][e] = (sh_bf16x2(dd, 0) & 0xFFFFu) ^ flip;
+      }
+    }
     const uint32_t kb = g / 8, kg = g % 8;
 #pragma unroll
     for (int s = 0; s < kShL; ++s) {
-      uint32_t h[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int32_t idx = (int32_t)jj - (int32_t)(8 * g + e);
-        h[e] = idx >= 0 ? dig[s * n + idx] : (uint32_t)(dig[s * n + idx + n] ^ (wrap & 0xFFFFu));
-      }
       unsigned char* tile = td + ((((uint64_t)j * kShL + s) * nblocks + nb) * (n / kShK) + kb) * kShTileBytes;
       *reinterpret_cast<uint4*>(tile + sh_chunk(r, kg)) =
-          make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+          make_uint4(h[s][0] | (h[s][1] << 16), h[s][2] | (h[s][3] << 16), h[s][4] | (h[s][5] << 16),
+                     h[s][6] | (h[s][7] << 16));
     }
   }
 }
@@ -361,14 +363,15 @@ extern "C" int polymul_batch_shared(polymul_plan* p, const void* a, const void* 
   const int wb = p->digit_bits;
   // digit planes
   const uint64_t threads_b = (uint64_t)k * rblocks * kShRows * (n / 8);
+  const uint64_t threads_t = (uint64_t)k * nblocks * kShRows * (n / 8);
   const int grid_b = (int)std::min<uint64_t>((threads_b + 255) / 256, (uint64_t)p->num_sms * 16);
-  const int tsm = kShL * (int)n * 2;
+  const int grid_t = (int)std::min<uint64_t>((threads_t + 255) / 256, (uint64_t)p->num_sms * 16);
   if (wb == 8) {
     k_shared_bdigits<8><<<grid_b, 256, 0, st>>>((const uint32_t*)b, bd, tp, batch, k, n, rblocks);
-    k_shared_tdigits<8><<<k * nblocks, 256, tsm, st>>>((const uint32_t*)a, td, tp, k, n, wrap);
+    k_shared_tdigits<8><<<grid_t, 256, 0, st>>>((const uint32_t*)a, td, tp, k, n, wrap);
   } else if (wb == 7) {
     k_shared_bdigits<7><<<grid_b, 256, 0, st>>>((const uint32_t*)b, bd, tp, batch, k, n, rblocks);
-    k_shared_tdigits<7><<<k * nblocks, 256, tsm, st>>>((const uint32_t*)a, td, tp, k, n, wrap);
+    k_shared_tdigits<7><<<grid_t, 256, 0, st>>>((const uint32_t*)a, td, tp, k, n, wrap);
   } else {
     return fail(POLYMUL_ENOTSUP, "digit width %d", wb);
   }

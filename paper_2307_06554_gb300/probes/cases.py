@@ -15,6 +15,8 @@ cases:
   u64_4096         n = 4096, one 59-bit prime, 1024 products (64-bit words)
   ragged_300       the first 300 products of the uneven 2000-product list
                    (n 1024..16384, 1..16 primes), one persistent launch
+  shared_ring1024  one a times 4096 b's (n = 1024, q = 12289) as the
+                   tensor-core GEMM of polymul_batch_shared
 """
 from __future__ import annotations
 
@@ -74,10 +76,30 @@ def _ragged(count, launches):
     return {"products": count, "words": total, "launches": launches, **info}
 
 
+def _shared(n, q, batch, launches, seed=7):
+    import torch
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(seed)
+    a = wl.uniform_coeffs(rng, 1, [q], n)[0]
+    b = wl.uniform_coeffs(rng, batch, [q], n)
+    ta = torch.from_numpy(a.view(np.int32)).to(dev)
+    tb = torch.from_numpy(b.view(np.int32)).to(dev)
+    nsets = max(1, math.ceil(1.5 * L2_BYTES / (2 * tb.numel() * 4)))
+    sets = [(tb.clone(), torch.empty_like(tb)) for _ in range(nsets)]
+    stream = torch.cuda.Stream(dev)
+    with polymul.Plan(n, [q], path=polymul.PATH_TENSOR) as plan:
+        for i in range(launches):
+            x, y = sets[i % nsets]
+            polymul.polymul_batch_shared(plan.handle, ta, x, y, batch, stream.cuda_stream)
+        stream.synchronize()
+        polymul.polymul_plan_status(plan.handle, stream.cuda_stream)
+    return {"n": n, "batch": batch, "launches": launches, "sets": nsets}
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("case", choices=["ntt_ring1024", "tensor_ring1024", "n16384", "cluster_32768", "u64_4096",
-                                    "ragged_300"])
+                                    "ragged_300", "shared_ring1024"])
     p.add_argument("--launches", type=int, default=4)
     args = p.parse_args(argv)
     rng = np.random.default_rng(8)
@@ -91,6 +113,8 @@ def main(argv=None):
         res = _homogeneous(32768, wl.draw_primes(rng, 1, 30, 30, 16), 256, polymul.PATH_NTT, args.launches)
     elif args.case == "u64_4096":
         res = _homogeneous(4096, wl.draw_primes(rng, 1, 59, 59, 13), 1024, polymul.PATH_NTT, args.launches)
+    elif args.case == "shared_ring1024":
+        res = _shared(1024, 12289, 4096, args.launches)
     else:
         res = _ragged(300, args.launches)
     print(args.case, res)
