@@ -431,10 +431,11 @@ def crossover(dev, stream, peaks, alu_peak_g, samples):
 
 def shared_operand(dev, stream, peaks, samples):
     """One operand a shared by the whole batch (the paper's many-vector
-    batching): c_i = a * b_i as the GEMM C = B * T(a) on the tensor cores
-    (polymul_batch_shared), against the NTT batch on the same products (a
-    repeated per product).  ring_1024's b operands and its first a, and the
-    same at n = 2048."""
+    batching), polymul_batch_shared on both paths: the GEMM C = B * T(a) on
+    the tensor cores, and the NTT with a's transform computed once (two
+    transforms per product); beside them the ordinary NTT batch on the same
+    products (a repeated per product).  ring_1024's b operands and its first
+    a, and the same at n = 2048."""
     import torch
     from paper_2307_06554_gb300 import polymul, workloads as wl
     sp = stream.cuda_stream
@@ -462,6 +463,16 @@ def shared_operand(dev, stream, peaks, samples):
         peak = peaks.get("bf16_tflops", 1911.7)
         row.update({"tensor_shared_us": ms * 1e3, "products_per_s": batch / (ms / 1e3),
                     "tflops": flops / (ms / 1e3) / 1e12, "bf16_frac": flops / (ms / 1e3) / 1e12 / peak})
+        with polymul.Plan(n, q_list, path=polymul.PATH_NTT) as plan:
+            def step3(i, h=plan.handle):
+                x, y = sets[i % nsets]
+                polymul.polymul_batch_shared(h, ta, x, y, batch, sp)
+            for i in range(3):
+                step3(i)
+            ms3 = _time_steps(step3, stream, 20)
+            c_s = torch.empty_like(tb)
+            polymul.polymul_batch_shared(plan.handle, ta, tb, c_s, batch, sp)
+        row["ntt_shared_us"] = ms3 * 1e3
         ab = ta.repeat(batch, 1).view(batch, len(q_list), n)
         with polymul.Plan(n, q_list) as plan:
             def step2(i, h=plan.handle):
@@ -475,7 +486,8 @@ def shared_operand(dev, stream, peaks, samples):
         stream.synchronize()
         row["ntt_us"] = ms2 * 1e3
         row["tensor_over_ntt"] = ms2 / ms
-        row["paths_agree"] = bool(torch.equal(c_t, c_n))
+        row["tensor_over_ntt_shared"] = ms3 / ms
+        row["paths_agree"] = bool(torch.equal(c_t, c_n)) and bool(torch.equal(c_s, c_n))
         idx = [0, batch - 1]
         samples.add("shared_operand", np.stack([w.a[0]] * 2), w.b[idx], q_list, c_t[idx].cpu().numpy().view(np.uint32))
         rows.append(row)

@@ -141,18 +141,23 @@ int polymul_batch(polymul_plan *plan, const void *a, const void *b, void *c,
 /*
  * polymul_batch_shared -- c_i = a * b_i (i < batch) for one operand a shared
  * by every product: the paper's many-vector batching (Sec. 2.2: one matrix
- * times many vectors is one matrix product).  With c_i = b_i * T(a) the
- * batch is the GEMM C = B * T(a) (M = batch, N = K = n), computed on the
- * tensor cores with every digit pair in tensor memory.
+ * times many vectors is one matrix product).
  *   a        device pointer, [k][n] (one polynomial per modulus).
  *   b, c     device pointers, [batch][k][n].  All 16-byte aligned.
- * Needs a plan on the tensor path (POLYMUL_PATH_TENSOR) with 2 digits per
- * coefficient (n = 1024 with q < 2^15, n = 2048 with q < 2^14); the cyclic
- * flag is honoured.  The plan keeps scratch for the digit planes of b and of
- * T(a), grown (cudaMalloc) when a call needs more.  Asynchronous; a call must
- * not overlap another call on the same plan (they share the scratch).
- * Errors: EINVAL (pointers, alignment, batch > 2^32), ENOTSUP (plan not on
- * the tensor path or digits != 2), ENOMEM, ECUDA.
+ * The plan's path decides how:
+ *   tensor path: with c_i = b_i * T(a) the batch is the GEMM
+ *     C = B * T(a) (M = batch, N = K = n), every digit pair in tensor memory;
+ *     needs 2 digits per coefficient (n = 1024 with q < 2^15, n = 2048 with
+ *     q < 2^14);
+ *   NTT path: a's transform once per modulus, then one forward and one
+ *     inverse transform per product (instead of two forward and one
+ *     inverse); needs 32-bit words, 1024 <= n <= 8192, a direct NTT.
+ * The cyclic flag is honoured.  The plan keeps scratch (digit planes of b
+ * and T(a), or a's transforms), grown (cudaMalloc) when a call needs more.
+ * Asynchronous; a call must not overlap another call on the same plan (they
+ * share the scratch).
+ * Errors: EINVAL (pointers, alignment, batch > 2^32), ENOTSUP (a plan
+ * outside the cases above), ENOMEM, ECUDA.
  */
 int polymul_batch_shared(polymul_plan *plan, const void *a, const void *b, void *c,
                          uint64_t batch, void *stream);

@@ -31,6 +31,11 @@ bool lookup_ntt_u32_rb5(int logn, int mode, KernelInfo* ki);  // logn 9..13, mod
 bool lookup_ntt_u32_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, modes 1, 2
 bool lookup_ntt_u64_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, mode 1
 
+// shared-operand products on the NTT path: a's transform once per prime
+// (prep), then forward(b), pointwise, inverse per product (32-bit words,
+// logn 10..13, modes 0..2)
+bool lookup_ntt_shared(int logn, int mode, KernelInfo* prep, KernelInfo* main);
+
 // one product per thread-block cluster (n = 2^14 .. 2^16)
 bool lookup_ntt_cluster(uint32_t elem, int logn, int mode, KernelInfo* ki);
 

@@ -192,10 +192,11 @@ __device__ __forceinline__ void ldtw2(const TwPair<W>* p, TwPair<W>& w0, TwPair<
 }
 
 // ---------------------------------------------------------------- phases
-// forward Cooley-Tukey stages of phase P on two operands sharing twiddles
-template <class S, int MODE, int P, typename W = typename S::W>
-__device__ __forceinline__ void fwd_phase2(W (&xa)[S::R], W (&xb)[S::R], const TwPair<W>* __restrict__ tw,
-                                           const PrimeConst<W>& pc, uint32_t t) {
+// forward Cooley-Tukey stages of phase P on one operand, or on two operands
+// sharing twiddles (TWO)
+template <class S, int MODE, int P, bool TWO, typename W = typename S::W>
+__device__ __forceinline__ void fwd_phase(W (&xa)[S::R], W (&xb)[S::R], const TwPair<W>* __restrict__ tw,
+                                          const PrimeConst<W>& pc, uint32_t t) {
   using PB = PhaseBits<S, P>;
   constexpr int LOGN = S::LOGN;
   sfor<PB::HI - 1, PB::LO - 1, -1>([&](auto hc) {
@@ -213,7 +214,7 @@ __device__ __forceinline__ void fwd_phase2(W (&xa)[S::R], W (&xb)[S::R], const T
           constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
           constexpr int u1 = u0 + (1 << hb);
           ct_bfly<W, MODE>(xa[u0], xa[u1], w, pc);
-          ct_bfly<W, MODE>(xb[u0], xb[u1], w, pc);
+          if constexpr (TWO) ct_bfly<W, MODE>(xb[u0], xb[u1], w, pc);
         });
       };
       if constexpr (NUP == 1) {
@@ -229,6 +230,12 @@ __device__ __forceinline__ void fwd_phase2(W (&xa)[S::R], W (&xb)[S::R], const T
       }
     });
   });
+}
+
+template <class S, int MODE, int P, typename W = typename S::W>
+__device__ __forceinline__ void fwd_phase2(W (&xa)[S::R], W (&xb)[S::R], const TwPair<W>* __restrict__ tw,
+                                           const PrimeConst<W>& pc, uint32_t t) {
+  fwd_phase<S, MODE, P, true>(xa, xb, tw, pc, t);
 }
 
 // inverse Gentleman-Sande stages of phase P
@@ -324,6 +331,20 @@ __device__ __forceinline__ void fwd_from(W (&xa)[S::R], W (&xb)[S::R], B sa, B s
     load_layout<S, P - 1>(xa, sa, t);
     load_layout<S, P - 1>(xb, sb, t);
     fwd_from<S, MODE, P - 1>(xa, xb, sa, sb, tw, pc, t, sync);
+  }
+}
+
+// one operand through the forward transform (phases P .. 0)
+template <class S, int MODE, int P, class Sync, class B, typename W = typename S::W>
+__device__ __forceinline__ void fwd_from1(W (&x)[S::R], B s, const TwPair<W>* __restrict__ tw,
+                                          const PrimeConst<W>& pc, uint32_t t, Sync sync) {
+  fwd_phase<S, MODE, P, false>(x, x, tw, pc, t);
+  if constexpr (P > 0) {
+    sync();
+    store_layout<S, P>(x, s, t);
+    sync();
+    load_layout<S, P - 1>(x, s, t);
+    fwd_from1<S, MODE, P - 1>(x, s, tw, pc, t, sync);
   }
 }
 

@@ -74,6 +74,22 @@ struct RaggedArgs {
   int* err;
 };
 
+// Shared-operand products on the NTT path (k_ntt_prep / k_ntt_shared).
+template <typename W>
+struct NttSharedArgs {
+  const W* a;      // prep: [k][n] operand; product kernel: a^ in register layout [k][T][R]
+  const W* b;      // [batch][k][n]
+  W* c;            // prep: a^ out; product kernel: [batch][k][n]
+  const void* tw_fwd;
+  const void* tw_inv;
+  const PrimeConst<W>* pc;
+  uint64_t units;  // prep: k; product kernel: batch * k
+  uint32_t k;
+  uint32_t tw_stride;
+  unsigned long long* ctr;  // {next, finished}, zero between launches
+  int* err;
+};
+
 // Per-prime constants of the Toeplitz (tensor) path.
 struct alignas(16) TensorPrime {
   uint32_t q;

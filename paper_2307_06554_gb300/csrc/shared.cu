@@ -332,6 +332,45 @@ using namespace pm;
 
 static bool sh_misaligned(const void* x) { return ((uintptr_t)x & 15u) != 0; }
 
+// scratch of the plan: at least `bytes`, of which the first 16 bytes are a
+// zeroed work counter pair
+static int sh_scratch(polymul_plan* p, size_t bytes) {
+  if (p->sh_bytes >= bytes) return POLYMUL_OK;
+  if (p->d_sh) PM_CUDA(cudaFree(p->d_sh));
+  p->d_sh = nullptr;
+  p->sh_bytes = 0;
+  if (cudaMalloc(&p->d_sh, bytes) != cudaSuccess) return fail(POLYMUL_ENOMEM, "shared-operand scratch");
+  PM_CUDA(cudaMemset(p->d_sh, 0, 256));
+  p->sh_bytes = bytes;
+  return POLYMUL_OK;
+}
+
+// NTT path: a's transforms (k units) then the batch
+static int shared_ntt(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st) {
+  KernelInfo prep, kmain;
+  if (p->elem != 4 || p->aux_prime || p->ki.cluster || !lookup_ntt_shared((int)p->logn, p->mode, &prep, &kmain))
+    return fail(POLYMUL_ENOTSUP, "shared-operand NTT products need 32-bit words, n in [1024, 8192] and a direct NTT");
+  const size_t ahat_bytes = (size_t)p->k * p->n * 4;
+  int rc = sh_scratch(p, 256 + ahat_bytes);
+  if (rc != POLYMUL_OK) return rc;
+  unsigned long long* ctr = static_cast<unsigned long long*>(p->d_sh);
+  uint32_t* ahat = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(p->d_sh) + 256);
+  const PrimeConst<uint32_t>* pc = static_cast<const PrimeConst<uint32_t>*>(p->d_pc);
+  NttSharedArgs<uint32_t> pa{(const uint32_t*)a, nullptr, ahat, p->d_twf, p->d_twi, pc, p->k, p->k, p->n, nullptr, p->d_err};
+  void* argv_p[] = {&pa};
+  PM_CUDA(cudaLaunchKernel(prep.fn, p->k, prep.block, argv_p, prep.smem, st));
+  int per_sm = 0;
+  PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmain.fn, kmain.block, kmain.smem));
+  if (per_sm < 1) return fail(POLYMUL_ENOTSUP, "shared-operand NTT kernel does not fit on an SM");
+  const uint64_t units = batch * p->k;
+  const int grid = (int)std::min<uint64_t>(units, (uint64_t)per_sm * p->num_sms);
+  NttSharedArgs<uint32_t> ma{ahat, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi, pc, units, p->k, p->n, ctr,
+                             p->d_err};
+  void* argv_m[] = {&ma};
+  PM_CUDA(cudaLaunchKernel(kmain.fn, grid, kmain.block, argv_m, kmain.smem, st));
+  return POLYMUL_OK;
+}
+
 extern "C" int polymul_batch_shared(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch,
                                     void* stream) {
   clear_error();
@@ -340,23 +379,19 @@ extern "C" int polymul_batch_shared(polymul_plan* p, const void* a, const void* 
   if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
   if (sh_misaligned(a) || sh_misaligned(b) || sh_misaligned(c)) return fail(POLYMUL_EINVAL, "operands must be 16-byte aligned");
   if (batch > (1ull << 32)) return fail(POLYMUL_EINVAL, "batch too large");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p->path == POLYMUL_PATH_NTT) return shared_ntt(p, a, b, c, batch, st);
   if (p->path != POLYMUL_PATH_TENSOR || p->digits != kShL || !p->d_tpc)
     return fail(POLYMUL_ENOTSUP, "shared-operand products need a tensor-path plan with %d digits per coefficient", kShL);
   if (p->n % kShRows != 0) return fail(POLYMUL_ENOTSUP, "n=%u is not a multiple of %d", p->n, kShRows);
-  cudaStream_t st = (cudaStream_t)stream;
   const uint32_t n = p->n, k = p->k;
   const uint32_t rblocks = (uint32_t)((batch + kShRows - 1) / kShRows), nblocks = n / kShRows, kblocks = n / kShK;
   const size_t bd_bytes = (size_t)k * kShL * rblocks * kblocks * kShTileBytes;
   const size_t td_bytes = (size_t)k * kShL * nblocks * kblocks * kShTileBytes;
   // scratch: digit planes of b and of T(a), kept with the plan and grown on demand
-  if (p->sh_bytes < bd_bytes + td_bytes) {
-    if (p->d_sh) PM_CUDA(cudaFree(p->d_sh));
-    p->d_sh = nullptr;
-    p->sh_bytes = 0;
-    if (cudaMalloc(&p->d_sh, bd_bytes + td_bytes) != cudaSuccess) return fail(POLYMUL_ENOMEM, "shared-operand scratch");
-    p->sh_bytes = bd_bytes + td_bytes;
-  }
-  unsigned char* bd = static_cast<unsigned char*>(p->d_sh);
+  int rc = sh_scratch(p, 256 + bd_bytes + td_bytes);
+  if (rc != POLYMUL_OK) return rc;
+  unsigned char* bd = static_cast<unsigned char*>(p->d_sh) + 256;
   unsigned char* td = bd + bd_bytes;
   const TensorPrime* tp = static_cast<const TensorPrime*>(p->d_tpc);
   const uint32_t wrap = p->cyclic ? 0u : 0x8000u;

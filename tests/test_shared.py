@@ -1,7 +1,8 @@
 """Shared-operand products (polymul_batch_shared): c_i = a * b_i for one a,
-as the GEMM C = B * T(a) on the tensor cores, against the CPU oracle:
-ragged batch tails (not a multiple of the 128-row tile), several moduli,
-both rings, both digit widths, extreme operands, and the error cases."""
+as the GEMM C = B * T(a) on the tensor cores and on the NTT path (a's
+transform once), against the CPU oracle: ragged batch tails (not a multiple
+of the 128-row tile), several moduli, both rings, both digit widths, every
+NTT reduction mode, extreme operands, and the error cases."""
 import numpy as np
 import pytest
 
@@ -91,13 +92,31 @@ def test_shared_reuses_scratch_and_grows(pm):
             assert_equal_residues(_run(pm, plan, a, b), _want(a, b, [q]), "batch %d" % batch)
 
 
+@pytest.mark.parametrize("n,bits,k,cyclic", [(1024, 14, 1, False), (1024, 30, 2, False), (2048, 31, 1, False),
+                                              (4096, 29, 2, True), (8192, 20, 1, False), (1024, 14, 1, True)])
+def test_shared_ntt_path(pm, n, bits, k, cyclic):
+    """The NTT path: a's transforms once per prime, two transforms per product."""
+    rng = np.random.default_rng(n + bits + k)
+    q_list = [12289] if bits == 14 else wl.draw_primes(rng, k, bits, bits, n.bit_length())
+    a = wl.uniform_coeffs(rng, 1, q_list, n, np.uint32)[0]
+    b = wl.uniform_coeffs(rng, 37, q_list, n, np.uint32)
+    flags = pm.FLAG_CYCLIC if cyclic else 0
+    with pm.Plan(n, q_list, path=pm.PATH_NTT, flags=flags) as plan:
+        got = _run(pm, plan, a, b)
+        got2 = _run(pm, plan, a, b[:5])  # the counter resets between launches
+    want = _want(a, b, q_list, cyclic=cyclic)
+    assert_equal_residues(got, want, "ntt n=%d bits=%d" % (n, bits))
+    assert_equal_residues(got2, want[:5], "second launch")
+
+
 def test_shared_unsupported(pm):
     import torch
-    x = torch.zeros(1024, dtype=torch.int32, device="cuda")
-    with pm.Plan(1024, [12289], path=pm.PATH_NTT) as plan:
-        with pytest.raises(pm.PolymulError) as ei:
-            pm.polymul_batch_shared(plan.handle, x, x, x, 1)
-        assert ei.value.code == pm.POLYMUL_ENOTSUP
+    x = torch.zeros(1 << 16, dtype=torch.int32, device="cuda")
+    for n, q in ((512, 12289), (16384, 65537)):  # NTT path outside 1024 .. 8192
+        with pm.Plan(n, [q], path=pm.PATH_NTT) as plan:
+            with pytest.raises(pm.PolymulError) as ei:
+                pm.polymul_batch_shared(plan.handle, x, x, x, 1)
+            assert ei.value.code == pm.POLYMUL_ENOTSUP
     q = wl.draw_primes(np.random.default_rng(1), 1, 30, 30, 1)[0]  # four digits
     with pm.Plan(1024, [q], path=pm.PATH_TENSOR) as plan:
         with pytest.raises(pm.PolymulError) as ei:
