@@ -238,10 +238,11 @@ __device__ __forceinline__ void fwd_phase2(W (&xa)[S::R], W (&xb)[S::R], const T
   fwd_phase<S, MODE, P, true>(xa, xb, tw, pc, t);
 }
 
-// inverse Gentleman-Sande stages of phase P
-template <class S, int MODE, int P, typename W = typename S::W>
-__device__ __forceinline__ void inv_phase(W (&x)[S::R], const TwPair<W>* __restrict__ tw,
-                                          const PrimeConst<W>& pc, uint32_t t) {
+// inverse Gentleman-Sande stages of phase P on one operand, or on two
+// operands sharing twiddles (TWO)
+template <class S, int MODE, int P, bool TWO, typename W = typename S::W>
+__device__ __forceinline__ void inv_phase_n(W (&x)[S::R], W (&y)[S::R], const TwPair<W>* __restrict__ tw,
+                                            const PrimeConst<W>& pc, uint32_t t) {
   using PB = PhaseBits<S, P>;
   constexpr int LOGN = S::LOGN;
   sfor<PB::LO, PB::HI>([&](auto hc) {
@@ -258,6 +259,7 @@ __device__ __forceinline__ void inv_phase(W (&x)[S::R], const TwPair<W>* __restr
           constexpr int lw = decltype(lwc)::value;
           constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
           gs_bfly<W, MODE, h>(x[u0], x[u0 + (1 << hb)], w.w, w.wp, pc);
+          if constexpr (TWO) gs_bfly<W, MODE, h>(y[u0], y[u0 + (1 << hb)], w.w, w.wp, pc);
         });
       };
       if constexpr (h == LOGN - 1) {
@@ -267,6 +269,7 @@ __device__ __forceinline__ void inv_phase(W (&x)[S::R], const TwPair<W>* __restr
             constexpr int lw = decltype(lwc)::value;
             constexpr int u0 = gl * PB::GS + ((up << (hb + 1)) | lw);
             gs_last<W, MODE, h>(x[u0], x[u0 + (1 << hb)], pc);
+            if constexpr (TWO) gs_last<W, MODE, h>(y[u0], y[u0 + (1 << hb)], pc);
           });
         });
       } else if constexpr (NUP == 1) {
@@ -282,6 +285,12 @@ __device__ __forceinline__ void inv_phase(W (&x)[S::R], const TwPair<W>* __restr
       }
     });
   });
+}
+
+template <class S, int MODE, int P, typename W = typename S::W>
+__device__ __forceinline__ void inv_phase(W (&x)[S::R], const TwPair<W>* __restrict__ tw,
+                                          const PrimeConst<W>& pc, uint32_t t) {
+  inv_phase_n<S, MODE, P, false>(x, x, tw, pc, t);
 }
 
 template <class S, int P, typename W = typename S::W>
@@ -365,6 +374,27 @@ __device__ __forceinline__ void inv_from(W (&x)[S::R], B s, const TwPair<W>* __r
       hook();
     }
     inv_from<S, MODE, P + 1>(x, s, tw, pc, t, sync, hook);
+  }
+}
+
+// two operands of the same prime through the inverse transform together
+// (shared twiddle loads); `hook` as for inv_from, once both buffers are free
+template <class S, int MODE, int P, class Sync, class Hook, class B, typename W = typename S::W>
+__device__ __forceinline__ void inv_from2(W (&x)[S::R], W (&y)[S::R], B sx, B sy, const TwPair<W>* __restrict__ tw,
+                                          const PrimeConst<W>& pc, uint32_t t, Sync sync, Hook&& hook) {
+  inv_phase_n<S, MODE, P, true>(x, y, tw, pc, t);
+  if constexpr (P + 1 < S::NPH) {
+    sync();
+    store_layout<S, P>(x, sx, t);
+    store_layout<S, P>(y, sy, t);
+    sync();
+    load_layout<S, P + 1>(x, sx, t);
+    load_layout<S, P + 1>(y, sy, t);
+    if constexpr (P + 2 == S::NPH) {
+      sync();
+      hook();
+    }
+    inv_from2<S, MODE, P + 1>(x, y, sx, sy, tw, pc, t, sync, hook);
   }
 }
 

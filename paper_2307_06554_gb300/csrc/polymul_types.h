@@ -83,7 +83,8 @@ struct NttSharedArgs {
   const void* tw_fwd;
   const void* tw_inv;
   const PrimeConst<W>* pc;
-  uint64_t units;  // prep: k; product kernel: batch * k
+  uint64_t units;  // prep: k; product kernel: pairs of products, ceil(batch / 2) * k
+  uint64_t batch;  // product kernel: products per prime
   uint32_t k;
   uint32_t tw_stride;
   unsigned long long* ctr;  // {next, finished}, zero between launches

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "../../include/polymul.h"
 #include "kernels.h"
@@ -345,6 +346,25 @@ static int sh_scratch(polymul_plan* p, size_t bytes) {
   return POLYMUL_OK;
 }
 
+// a launch with programmatic stream serialisation: the kernel's CTAs may
+// start while the previous kernel on the stream drains (the kernels wait for
+// it with griddepcontrol before touching memory)
+static int pdl_launch(const void* fn, int grid, int block, int smem, void** argv, cudaStream_t st) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  PM_CUDA(cudaLaunchKernelExC(&cfg, fn, argv));
+  return POLYMUL_OK;
+}
+
 // NTT path: a's transforms (k units) then the batch
 static int shared_ntt(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st) {
   KernelInfo prep, kmain;
@@ -356,19 +376,22 @@ static int shared_ntt(polymul_plan* p, const void* a, const void* b, void* c, ui
   unsigned long long* ctr = static_cast<unsigned long long*>(p->d_sh);
   uint32_t* ahat = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(p->d_sh) + 256);
   const PrimeConst<uint32_t>* pc = static_cast<const PrimeConst<uint32_t>*>(p->d_pc);
-  NttSharedArgs<uint32_t> pa{(const uint32_t*)a, nullptr, ahat, p->d_twf, p->d_twi, pc, p->k, p->k, p->n, nullptr, p->d_err};
+  NttSharedArgs<uint32_t> pa{(const uint32_t*)a, nullptr, ahat, p->d_twf, p->d_twi, pc, p->k, 0, p->k, p->n, nullptr,
+                             p->d_err};
   void* argv_p[] = {&pa};
-  PM_CUDA(cudaLaunchKernel(prep.fn, p->k, prep.block, argv_p, prep.smem, st));
+  int rc2 = pdl_launch(prep.fn, (int)p->k, prep.block, prep.smem, argv_p, st);
+  if (rc2 != POLYMUL_OK) return rc2;
   int per_sm = 0;
+  if (kmain.smem > 48 * 1024)
+    PM_CUDA(cudaFuncSetAttribute(kmain.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kmain.smem));
   PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kmain.fn, kmain.block, kmain.smem));
   if (per_sm < 1) return fail(POLYMUL_ENOTSUP, "shared-operand NTT kernel does not fit on an SM");
-  const uint64_t units = batch * p->k;
-  const int grid = (int)std::min<uint64_t>(units, (uint64_t)per_sm * p->num_sms);
-  NttSharedArgs<uint32_t> ma{ahat, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi, pc, units, p->k, p->n, ctr,
-                             p->d_err};
+  const uint64_t pairs = (batch + 1) / 2 * p->k;
+  const int grid = (int)std::min<uint64_t>(pairs, (uint64_t)per_sm * p->num_sms);
+  NttSharedArgs<uint32_t> ma{ahat, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi, pc, pairs, batch, p->k, p->n,
+                             ctr, p->d_err};
   void* argv_m[] = {&ma};
-  PM_CUDA(cudaLaunchKernel(kmain.fn, grid, kmain.block, argv_m, kmain.smem, st));
-  return POLYMUL_OK;
+  return pdl_launch(kmain.fn, grid, kmain.block, kmain.smem, argv_m, st);
 }
 
 extern "C" int polymul_batch_shared(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch,
