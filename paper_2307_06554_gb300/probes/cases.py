@@ -17,6 +17,7 @@ cases:
                    (n 1024..16384, 1..16 primes), one persistent launch
   shared_ring1024  one a times 4096 b's (n = 1024, q = 12289) as the
                    tensor-core GEMM of polymul_batch_shared
+  shared_ntt1024   the same on the NTT path (a's transform once)
 """
 from __future__ import annotations
 
@@ -76,7 +77,7 @@ def _ragged(count, launches):
     return {"products": count, "words": total, "launches": launches, **info}
 
 
-def _shared(n, q, batch, launches, seed=7):
+def _shared(n, q, batch, launches, seed=7, path=polymul.PATH_TENSOR):
     import torch
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(seed)
@@ -87,7 +88,7 @@ def _shared(n, q, batch, launches, seed=7):
     nsets = max(1, math.ceil(1.5 * L2_BYTES / (2 * tb.numel() * 4)))
     sets = [(tb.clone(), torch.empty_like(tb)) for _ in range(nsets)]
     stream = torch.cuda.Stream(dev)
-    with polymul.Plan(n, [q], path=polymul.PATH_TENSOR) as plan:
+    with polymul.Plan(n, [q], path=path) as plan:
         for i in range(launches):
             x, y = sets[i % nsets]
             polymul.polymul_batch_shared(plan.handle, ta, x, y, batch, stream.cuda_stream)
@@ -99,7 +100,7 @@ def _shared(n, q, batch, launches, seed=7):
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("case", choices=["ntt_ring1024", "tensor_ring1024", "n16384", "cluster_32768", "u64_4096",
-                                    "ragged_300", "shared_ring1024"])
+                                    "ragged_300", "shared_ring1024", "shared_ntt1024"])
     p.add_argument("--launches", type=int, default=4)
     args = p.parse_args(argv)
     rng = np.random.default_rng(8)
@@ -115,6 +116,8 @@ def main(argv=None):
         res = _homogeneous(4096, wl.draw_primes(rng, 1, 59, 59, 13), 1024, polymul.PATH_NTT, args.launches)
     elif args.case == "shared_ring1024":
         res = _shared(1024, 12289, 4096, args.launches)
+    elif args.case == "shared_ntt1024":
+        res = _shared(1024, 12289, 4096, args.launches, path=polymul.PATH_NTT)
     else:
         res = _ragged(300, args.launches)
     print(args.case, res)
