@@ -333,6 +333,7 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
         plan.close()
 
     homogeneous("ring_small", wl.ring_small(), 1, 200)
+    out["ring_small"]["graph_1000"] = graph_replay(dev, wl.ring_small(), 1000)
     homogeneous("rns_4096", wl.rns_4096(), 6, 20)
     # the cyclic ring x^n - 1 on the headline's shape and data
     homogeneous("ring_1024_cyclic", wl.ring_1024(), 9, 50, cyclic=True)
@@ -367,6 +368,42 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
                               "hbm_frac": 3 * total * 4 / (ms / 1e3) / 1e9 / hbm,
                               "bit_exact_sample": None, "l2": "inputs 1.3 GB (> L2)"}
     return out
+
+
+def graph_replay(dev, w, launches):
+    """Launch-latency view of a small batch: `launches` calls of
+    polymul_batch captured once in a CUDA graph and replayed (the kernels keep
+    their programmatic dependent launches inside the graph)."""
+    import torch
+    from paper_2307_06554_gb300 import polymul
+    try:
+        plan = polymul.Plan(w.n, w.q_list)
+        ta = torch.from_numpy(w.a.view(np.int32)).to(dev)
+        tb = torch.from_numpy(w.b.view(np.int32)).to(dev)
+        tc = torch.empty_like(ta)
+        s = torch.cuda.Stream(dev)
+        with torch.cuda.stream(s):
+            polymul.polymul_batch(plan.handle, ta, tb, tc, w.batch, s.cuda_stream)  # first call outside capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            cs = torch.cuda.current_stream().cuda_stream
+            for _ in range(launches):
+                polymul.polymul_batch(plan.handle, ta, tb, tc, w.batch, cs)
+        g.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        polymul.polymul_plan_status(plan.handle)
+        us = e0.elapsed_time(e1) * 1e3 / launches
+        plan.close()
+        return {"launches": launches, "us_per_call": us, "products_per_s": w.batch / (us * 1e-6)}
+    except Exception as exc:  # report, do not fail the bench
+        return {"error": str(exc)[:200]}
 
 
 def crossover(dev, stream, peaks, alu_peak_g, samples):

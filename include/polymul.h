@@ -343,6 +343,17 @@ int polymul_server_stats_get(polymul_server *srv, polymul_server_stats *out, int
 /* Stop the loop (finishing work in flight) and free everything.  NULL-safe. */
 void polymul_server_destroy(polymul_server *srv);
 
+/*
+ * polymul_selftest_wait -- diagnostics (the paper has no counterpart).
+ * Runs one small kernel whose bounded mbarrier wait has nothing to wait for
+ * and therefore gives up after `polls` polls (1 .. 2^22), the path every
+ * kernel of the library takes when a copy or MMA never completes.  Returns
+ * POLYMUL_ETIMEOUT when the wait expired and was reported (the expected
+ * outcome; the CUDA context stays usable), EINVAL for polls outside the
+ * range, ECUDA otherwise.  Synchronises `stream`.
+ */
+int polymul_selftest_wait(uint32_t polls, void *stream);
+
 /* Message for the calling thread's most recent failing call ("" if none).
  * The pointer stays valid until the next call from the same thread. */
 const char *polymul_last_error(void);

@@ -17,6 +17,7 @@
 #include "host_math.h"
 #include "ntt_tables.h"
 #include "kernels.h"
+#include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
 
@@ -208,6 +209,7 @@ int configure_launch(polymul_plan* p) {
 extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, const polymul_opts* opts,
                               polymul_plan** out) {
   clear_error();
+  TraceRange trace_("polymul_create");
   if (!out) return fail(POLYMUL_EINVAL, "out is NULL");
   if (n < 16 || n > 65536 || (n & (n - 1))) return fail(POLYMUL_EINVAL, "n=%u must be a power of two in [16, 65536]", n);
   if (k == 0 || !q_list) return fail(POLYMUL_EINVAL, "need k >= 1 moduli");
@@ -480,6 +482,7 @@ static bool misaligned(const void* x) { return ((uintptr_t)x & 15u) != 0; }
 
 extern "C" int polymul_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, void* stream) {
   clear_error();
+  TraceRange trace_("polymul_batch");
   if (!p) return fail(POLYMUL_EINVAL, "plan is NULL");
   if (batch == 0) return POLYMUL_OK;
   if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
@@ -510,6 +513,7 @@ extern "C" int polymul_plan_status(polymul_plan* p, void* stream) {
 extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch,
                                   void* stream) {
   clear_error();
+  TraceRange trace_("polymul_batch_host");
   if (!p) return fail(POLYMUL_EINVAL, "plan is NULL");
   if (batch == 0) return POLYMUL_OK;
   if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");

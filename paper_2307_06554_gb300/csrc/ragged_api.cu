@@ -12,6 +12,7 @@
 #include "../../include/polymul.h"
 #include "host_math.h"
 #include "kernels.h"
+#include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
 
@@ -168,6 +169,7 @@ extern "C" int polymul_ragged_prepare(polymul_ragged* r, const polymul_desc* des
                                       const uint32_t* prime_idx, uint64_t prime_idx_len, uint64_t total_elems,
                                       polymul_ragged_batch** out) {
   clear_error();
+  TraceRange trace_("polymul_ragged_prepare");
   if (!r || !out || (count && (!descs || !prime_idx))) return fail(POLYMUL_EINVAL, "null argument");
   // units grouped by degree class
   std::vector<std::vector<RaggedUnit>> cls(16);
@@ -242,6 +244,7 @@ int ragged_grid(const polymul_ragged_batch* b) {
 
 extern "C" int polymul_ragged_run(polymul_ragged_batch* b, const void* a, const void* bb, void* c, void* stream) {
   clear_error();
+  TraceRange trace_("polymul_ragged_run");
   int rc = ragged_check(b, a, bb, c);
   if (rc != POLYMUL_OK || b->n_items == 0) return rc;
   b->args.a = (const uint32_t*)a;
@@ -258,6 +261,7 @@ extern "C" int polymul_ragged_run(polymul_ragged_batch* b, const void* a, const 
 extern "C" int polymul_ragged_run_graph(polymul_ragged_batch* b, const void* a, const void* bb, void* c,
                                         void* stream) {
   clear_error();
+  TraceRange trace_("polymul_ragged_run_graph");
   int rc = ragged_check(b, a, bb, c);
   if (rc != POLYMUL_OK || b->n_items == 0) return rc;
   b->args.a = (const uint32_t*)a;

@@ -35,6 +35,7 @@
 #include "../../include/polymul.h"
 #include "host_math.h"
 #include "kernels.h"
+#include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
 
@@ -416,6 +417,7 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
 
 extern "C" int polymul_server_submit(polymul_server* s, const polymul_request* q, uint64_t* ticket) {
   clear_error();
+  TraceRange trace_("polymul_server_submit");
   if (!s || !q || !ticket) return fail(POLYMUL_EINVAL, "null argument");
   if (q->n < 16 || q->n > s->nmax || (q->n & (q->n - 1)))
     return fail(POLYMUL_EINVAL, "n=%u must be a power of two in [16, %u]", q->n, s->nmax);
@@ -486,6 +488,7 @@ extern "C" int polymul_server_wait(polymul_server* s, uint64_t ticket, double ti
 extern "C" int polymul_server_replay(polymul_server* s, const polymul_request* reqs, uint32_t count,
                                      const double* arrival_s, double* latency_us) {
   clear_error();
+  TraceRange trace_("polymul_server_replay");
   if (!s || (count && (!reqs || !arrival_s))) return fail(POLYMUL_EINVAL, "null argument");
   std::vector<uint64_t> tickets(count);
   const auto t0 = Clock::now();

@@ -27,6 +27,7 @@
 
 #include "../../include/polymul.h"
 #include "kernels.h"
+#include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
 #include "tcgen05.cuh"
@@ -397,6 +398,7 @@ static int shared_ntt(polymul_plan* p, const void* a, const void* b, void* c, ui
 extern "C" int polymul_batch_shared(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch,
                                     void* stream) {
   clear_error();
+  TraceRange trace_("polymul_batch_shared");
   if (!p) return fail(POLYMUL_EINVAL, "plan is NULL");
   if (batch == 0) return POLYMUL_OK;
   if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");

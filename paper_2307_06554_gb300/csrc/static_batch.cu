@@ -33,6 +33,7 @@
 #include "kernels.h"
 #include "host_math.h"
 #include "ntt_tables.h"
+#include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
 
@@ -114,6 +115,7 @@ bool lookup_u32(int logn, int mode, KernelInfo* ki) {
 extern "C" int polymul_batch_static(uint32_t n, uint64_t q, const void* a, const void* b, void* c,
                                     uint64_t batch, void* stream) {
   clear_error();
+  TraceRange trace_("polymul_batch_static");
   if (n < 16 || n > kStaticMaxN || (n & (n - 1)))
     return fail(POLYMUL_EINVAL, "n=%u must be a power of two in [16, %u]", n, kStaticMaxN);
   if (q >= (1ull << 31) || !pm::host::is_prime(q) || (q - 1) % (2ull * n) != 0)

@@ -21,6 +21,7 @@
 
 #include "../../include/polymul.h"
 #include "kernels.h"
+#include "trace.h"
 #include "plan.h"
 
 using namespace pm;
@@ -72,6 +73,7 @@ uint64_t bucket_of(uint64_t batch) {
 
 extern "C" int polymul_tune(polymul_plan* p, uint64_t batch, void* stream) {
   clear_error();
+  TraceRange trace_("polymul_tune");
   if (!p) return fail(POLYMUL_EINVAL, "plan is NULL");
   if (batch == 0) return fail(POLYMUL_EINVAL, "batch must be positive");
   if (p->cands.size() <= 1) {

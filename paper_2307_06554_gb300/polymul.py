@@ -86,6 +86,8 @@ def _load():
     lib.polymul_batch_host.restype = i32
     lib.polymul_batch_shared.argtypes = [vp, vp, vp, vp, u64, vp]
     lib.polymul_batch_shared.restype = i32
+    lib.polymul_selftest_wait.argtypes = [ctypes.c_uint32, vp]
+    lib.polymul_selftest_wait.restype = i32
     lib.polymul_batch_static.argtypes = [u32, u64, vp, vp, vp, u64, vp]
     lib.polymul_batch_static.restype = i32
     lib.polymul_plan_select.argtypes = [vp, u32]
@@ -186,6 +188,12 @@ def polymul_batch(plan: int, a, b, c, batch: int, stream=None) -> None:
 
 def polymul_batch_host(plan: int, a, b, c, batch: int, stream=None) -> None:
     _check(_lib.polymul_batch_host(plan, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
+
+
+def polymul_selftest_wait(polls: int, stream=None) -> None:
+    """Device check that a bounded wait gives up: raises PolymulError with
+    POLYMUL_ETIMEOUT when it does (the expected outcome)."""
+    _check(_lib.polymul_selftest_wait(polls, _stream(stream)))
 
 
 def polymul_batch_shared(plan: int, a, b, c, batch: int, stream=None) -> None:
