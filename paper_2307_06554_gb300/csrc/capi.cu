@@ -277,6 +277,8 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     p->mode = 0;
     rc = upload_ntt_tables<uint32_t>(p);
     if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_NTT, p->aki);
+    KernelInfo v;
+    if (rc == POLYMUL_OK && lookup_ntt_u32_aux_rb2((int)p->logn, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
   } else if (path == POLYMUL_PATH_TENSOR || (path == POLYMUL_PATH_AUTO && !ntt_ok && tensor_ok)) {
     if (!tensor_ok) {
       rc = fail(POLYMUL_ENOTSUP, "tensor path not available for n=%u and these moduli", n);

@@ -26,6 +26,7 @@ bool lookup_ntt_u32_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u64_m1(int logn, KernelInfo* ki);  // logn 4..13
 bool lookup_ntt_u64_m2(int logn, KernelInfo* ki);
 bool lookup_ntt_u32_aux(int logn, KernelInfo* ki);  // auxiliary-prime mode, logn 4..14
+bool lookup_ntt_u32_aux_rb2(int logn, KernelInfo* ki);  // the same with radix-4 passes, logn 7..10
 // autotuner candidates: other register radices (RB = stage bits per pass)
 bool lookup_ntt_u32_rb5(int logn, int mode, KernelInfo* ki);  // logn 9..13, modes 1, 2; logn 14, modes 0..2
 bool lookup_ntt_u32_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, modes 1, 2

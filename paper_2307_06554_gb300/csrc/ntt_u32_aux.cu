@@ -16,4 +16,22 @@ bool lookup_ntt_u32_aux(int logn, KernelInfo* ki) {
       return false;
   }
 }
+
+// Radix-4 register passes (4 coefficients per operand per thread, four
+// times the threads per product): shorter dependency chains per thread, for
+// batches too small to fill the GPU, where one product's latency is the
+// whole call (autotuner candidates; the exchange swizzle is conflict-free
+// for these team sizes, n >= 2^7).
+bool lookup_ntt_u32_aux_rb2(int logn, KernelInfo* ki) {
+  switch (logn) {
+#define PM_CASE(L)                              \
+  case L:                                       \
+    *ki = ntt_info<uint32_t, L, 0, true, 2>();  \
+    return true;
+    PM_CASE(7) PM_CASE(8) PM_CASE(9) PM_CASE(10)
+#undef PM_CASE
+    default:
+      return false;
+  }
+}
 }  // namespace pm

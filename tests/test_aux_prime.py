@@ -56,3 +56,23 @@ def test_no_route_is_reported(pm):
     with pytest.raises(pm.PolymulError) as ei:
         pm.Plan(256, [8192])
     assert ei.value.code == pm.POLYMUL_ENOTSUP
+
+
+@pytest.mark.parametrize("n,q", [(128, 3331), (256, 3329), (512, 1000), (1024, 1000)])
+def test_aux_every_candidate(pm, n, q):
+    """Every kernel the autotuner may pick for an auxiliary-prime plan
+    (radix-16 and radix-4 register passes) is exact."""
+    rng = np.random.default_rng(n + q)
+    a = wl.uniform_coeffs(rng, 19, [q], n, np.uint32)
+    b = wl.uniform_coeffs(rng, 19, [q], n, np.uint32)
+    want = native.polymul_batch(a, b, [q])
+    with pm.Plan(n, [q]) as plan:
+        assert plan.info["aux_primes"] == 1
+        ncand = plan.info["candidates"]
+        assert ncand == 2
+        seen = set()
+        for i in range(ncand):
+            info = plan.select(i)
+            seen.add(info["radix_bits"])
+            assert_equal_residues(run_plan_batch(plan, a, b), want, "candidate %d" % i)
+        assert seen == {2, 4}
