@@ -259,6 +259,40 @@ def _ntt_mulmods(n: int) -> int:
 SMEM_BYTES_PER_CLK_SM = 128
 
 
+def _host_link(dev, h2d_bytes, d2h_bytes, reps=10):
+    """Page-locked host <-> device copy bandwidth of this machine, measured now
+    with plain copies of the e2e step's sizes: one direction at a time and
+    both at once (separate streams); the ceiling for the e2e number."""
+    import torch
+    h_in = torch.empty(h2d_bytes, dtype=torch.uint8).pin_memory()
+    d_in = torch.empty(h2d_bytes, dtype=torch.uint8, device=dev)
+    h_out = torch.empty(d2h_bytes, dtype=torch.uint8).pin_memory()
+    d_out = torch.empty(d2h_bytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    def both():
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+
+    t_in = timed(lambda: d_in.copy_(h_in, non_blocking=True))
+    t_out = timed(lambda: h_out.copy_(d_out, non_blocking=True))
+    t_both = timed(both)
+    return {"h2d_GBs": h2d_bytes / t_in / 1e9, "d2h_GBs": d2h_bytes / t_out / 1e9,
+            "both_GBs": (h2d_bytes + d2h_bytes) / t_both / 1e9,
+            "note": "plain page-locked copies of the step's sizes, measured in this run"}
+
+
 def _tensor_smem_roofline(n, digits, units, seconds, sms, sm_mhz):
     nb = (8 * digits + 15) // 16 * 16
     mmas = digits * (n // 1024) * (n // 16)  # per unit: digits of a x row blocks x K steps
@@ -740,6 +774,7 @@ def run_ours(args, ws, rank, local):
         polymul.polymul_batch_host(plan.handle, ha, hb, hc, batch, None)
     e2e_s = time.perf_counter() - t0
     clk = clocks.stop()
+    link = _host_link(dev, 2 * ha.numel() * ha.element_size(), hc.numel() * hc.element_size())  # a and b in, c out
 
     # sampled products of the timed batch, checked by the CPU oracle leg
     samples = Samples()
@@ -829,7 +864,9 @@ def run_ours(args, ws, rank, local):
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": "products/s", "h2d_bytes_per_step": 2 * batch * n * elem,
                 "d2h_bytes_per_step": batch * n * elem,
-                "api": "polymul_batch_host (pinned host buffers, copies + kernel inside the timed region)"},
+                "api": "polymul_batch_host (pinned host buffers, copies + kernel inside the timed region)",
+                "host_link": dict(link, achieved_GBs=3 * batch * n * elem / (e2e_s / e2e_steps) / 1e9,
+                                  frac=(3 * batch * n * elem / (e2e_s / e2e_steps) / 1e9) / link["both_GBs"])},
         "gpu_launches": args.steps,
         "roofline": roof,
         "cpu_baseline": cpu,

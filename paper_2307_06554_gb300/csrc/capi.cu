@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -309,8 +310,8 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
   if (rc == POLYMUL_OK) apply_candidate(p, 0);
   if (rc == POLYMUL_OK) {
     // work counters for the three launch slots (device entry, two host-entry streams)
-    if (cudaMalloc(&p->d_ctr, 6 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(p->d_ctr, 0, 6 * sizeof(unsigned long long)) != cudaSuccess ||
+    if (cudaMalloc(&p->d_ctr, 2 * kCounterSlots * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(p->d_ctr, 0, 2 * kCounterSlots * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess || cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess)
       rc = fail(POLYMUL_ENOMEM, "counter allocation failed");
   }
@@ -346,7 +347,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_err);
   cudaFree(p->d_q);
   cudaFree(p->d_outer);
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < kHostStreams; ++s) {
     cudaFree(p->d_stage[s]);
     if (p->streams[s]) cudaStreamDestroy(p->streams[s]);
   }
@@ -505,13 +506,13 @@ extern "C" int polymul_plan_status(polymul_plan* p, void* stream) {
   PM_CUDA(cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (!h) return POLYMUL_OK;
   PM_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
-  PM_CUDA(cudaMemset(p->d_ctr, 0, 6 * sizeof(unsigned long long)));
+  PM_CUDA(cudaMemset(p->d_ctr, 0, 2 * kCounterSlots * sizeof(unsigned long long)));
   return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }
 
-// Host buffers: chunks of products flow through two plan-owned device
-// staging slots on two streams, so that the copy-in of one chunk, the kernel
-// of another and the copy-out of a third overlap.
+// Host buffers: chunks of products flow round-robin through kHostStreams
+// plan-owned device staging slots, one stream each, so that the copies in of
+// some chunks, the kernels of others and the copies out of others overlap.
 extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch,
                                   void* stream) {
   clear_error();
@@ -520,9 +521,19 @@ extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b,
   if (batch == 0) return POLYMUL_OK;
   if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
   const size_t prod_bytes = (size_t)p->k * p->n * p->elem;
-  const uint64_t chunk = std::max<uint64_t>(1, (8u << 20) / prod_bytes);
+  // about 4 MB of each operand per chunk by default (POLYMUL_HOST_CHUNK_BYTES
+  // overrides): several chunks in flight, so that copies in, kernels and
+  // copies out of different chunks overlap (the two copy directions use
+  // separate engines).  Measured on the 4096-product n = 1024 batch: 1, 2, 4,
+  // 8, 16 MB -> 340, 292, 264, 271, 304 us.
+  static const size_t chunk_target = [] {
+    const char* e = getenv("POLYMUL_HOST_CHUNK_BYTES");
+    const long long v = e ? atoll(e) : 0;
+    return v > 0 ? (size_t)v : (size_t)(4u << 20);
+  }();
+  const uint64_t chunk = std::max<uint64_t>(1, chunk_target / prod_bytes);
   const size_t slot_bytes = 3 * chunk * prod_bytes;
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < kHostStreams; ++s) {
     if (!p->streams[s]) PM_CUDA(cudaStreamCreateWithFlags(&p->streams[s], cudaStreamNonBlocking));
     if (p->stage_bytes < slot_bytes) {
       cudaFree(p->d_stage[s]);
@@ -534,14 +545,14 @@ extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b,
   p->stage_bytes = std::max(p->stage_bytes, slot_bytes);
   if (!p->ev_entry) PM_CUDA(cudaEventCreateWithFlags(&p->ev_entry, cudaEventDisableTiming));
   PM_CUDA(cudaEventRecord(p->ev_entry, (cudaStream_t)stream));
-  for (int s = 0; s < 2; ++s) PM_CUDA(cudaStreamWaitEvent(p->streams[s], p->ev_entry, 0));
+  for (int s = 0; s < kHostStreams; ++s) PM_CUDA(cudaStreamWaitEvent(p->streams[s], p->ev_entry, 0));
   const char* ha = (const char*)a;
   const char* hb = (const char*)b;
   char* hc = (char*)c;
   int rc = POLYMUL_OK;
   for (uint64_t first = 0, it = 0; first < batch; first += chunk, ++it) {
     const uint64_t cnt = std::min<uint64_t>(chunk, batch - first);
-    const int s = (int)(it & 1);
+    const int s = (int)(it % kHostStreams);
     cudaStream_t st = p->streams[s];
     char* da = (char*)p->d_stage[s];
     char* db = da + chunk * prod_bytes;
@@ -553,7 +564,7 @@ extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b,
     if (rc != POLYMUL_OK) break;
     PM_CUDA(cudaMemcpyAsync(hc + off, dc, bytes, cudaMemcpyDeviceToHost, st));
   }
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < kHostStreams; ++s) {
     cudaError_t e = cudaStreamSynchronize(p->streams[s]);
     if (e != cudaSuccess && rc == POLYMUL_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
   }

@@ -7,6 +7,12 @@
 
 #include "kernels.h"
 
+// polymul_batch_host pipeline depth: chunks of products round-robin over
+// this many plan-owned streams (copy in, kernel, copy out on each)
+constexpr int kHostStreams = 4;
+// work-counter slots: the device entry point, then one per host stream
+constexpr int kCounterSlots = 1 + kHostStreams;
+
 // One launchable way of computing a plan's products (the autotuner's choices).
 struct PlanCandidate {
   uint32_t path;     // POLYMUL_PATH_NTT or POLYMUL_PATH_TENSOR
@@ -47,15 +53,15 @@ struct polymul_plan {
   int grid_cap = 0;    // resident CTAs of ki (persistent grid)
   uint32_t launch_flags = 0;
   int* d_flag = nullptr;
-  unsigned long long* d_ctr = nullptr;  // 3 x {next, finished}: device entry, 2 host streams
+  unsigned long long* d_ctr = nullptr;  // kCounterSlots x {next, finished}: device entry, host streams
   int* d_err = nullptr;                 // set by kernels whose bounded waits expired
   // polymul_batch_shared scratch (digit planes of b and of T(a))
   void* d_sh = nullptr;
   size_t sh_bytes = 0;
   // polymul_batch_host staging
-  void* d_stage[2] = {nullptr, nullptr};
+  void* d_stage[kHostStreams] = {};
   size_t stage_bytes = 0;
-  cudaStream_t streams[2] = {nullptr, nullptr};
+  cudaStream_t streams[kHostStreams] = {};
   cudaEvent_t ev_entry = nullptr;
 };
 
