@@ -9,8 +9,9 @@
 //
 // Requests carry host operands.  A server thread owns the device: it admits
 // queued requests in arrival order as soon as device memory (a first-fit
-// arena) and an in-flight slot are free, issues each one on one of several
-// stream lanes -- copy in, one kernel over the request's (prime) units, copy
+// arena) and an in-flight slot are free, issues each one on the stream lane
+// with the least work in flight -- copy in, one kernel over the request's
+// (prime) units, copy
 // out, completion event -- and retires requests whose event has fired,
 // releasing their memory to the next admissions.  Work of different requests
 // overlaps on the device (lanes are independent streams), and copies of one
@@ -91,7 +92,7 @@ struct polymul_server {
   std::vector<cudaEvent_t> event_pool;
   std::vector<double> latencies_us;
   uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0;
-  int next_lane = 0;
+  std::vector<uint64_t> lane_bytes;  // bytes of the requests in flight on each lane
   std::atomic<bool> stop{false};
   std::thread loop;
   int cuda_error = 0;
@@ -207,6 +208,7 @@ void server_loop(polymul_server* s) {
           ++s->completed;
         }
         arena_free(s, r->off, r->bytes);
+        s->lane_bytes[r->lane] -= r->bytes;
         s->event_pool.push_back(r->ev);
         r->ev = nullptr;
         s->inflight[i] = s->inflight.back();
@@ -219,8 +221,13 @@ void server_loop(polymul_server* s) {
         const size_t off = arena_alloc(s, r->bytes);
         if (off == (size_t)-1) break;
         r->off = off;
-        r->lane = s->next_lane;
-        s->next_lane = (s->next_lane + 1) % s->nlanes;
+        // the lane with the least work in flight: a small request does not
+        // queue behind a large one while another lane is idle
+        int lane = 0;
+        for (int l = 1; l < s->nlanes; ++l)
+          if (s->lane_bytes[l] < s->lane_bytes[lane]) lane = l;
+        r->lane = lane;
+        s->lane_bytes[lane] += r->bytes;
         if (s->event_pool.empty()) {
           cudaEvent_t ev;
           cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -237,6 +244,7 @@ void server_loop(polymul_server* s) {
           r->t_done = now_s();
           ++s->failed;
           arena_free(s, r->off, r->bytes);
+          s->lane_bytes[r->lane] -= r->bytes;
           s->event_pool.push_back(r->ev);
           r->ev = nullptr;
         } else {
@@ -340,6 +348,7 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
   s->lognmax = __builtin_ctz(n_max);
   s->pool.assign(pool, pool + pool_size);
   s->nlanes = (int)lanes;
+  s->lane_bytes.assign(lanes, 0);
   int rc = POLYMUL_OK;
   auto bail = [&](int code) {
     std::string keep = polymul_last_error();
