@@ -237,8 +237,8 @@ int polymul_plan_info_get(const polymul_plan *plan, polymul_plan_info *info);
 void polymul_destroy(polymul_plan *plan);
 
 /* ------------------------------------------------------------------------
- * Uneven batches (products of different degrees and prime counts) in one
- * persistent launch.  Every modulus is a prime of a shared pool; each product
+ * Uneven batches (products of different degrees and prime counts) in
+ * persistent launches.  Every modulus is a prime of a shared pool; each product
  * has its own degree n and its own subset of the pool (its RNS primes,
  * Sec. 2.4).  Operands and results live in flat caller-owned arrays of
  * uint32_t: product p occupies rows [offset, offset + k*n) laid out [k][n].
@@ -275,12 +275,18 @@ int polymul_ragged_prepare(polymul_ragged *ctx, const polymul_desc *descs, uint3
                            const uint32_t *prime_idx, uint64_t prime_idx_len,
                            uint64_t total_elems, polymul_ragged_batch **out);
 
-/* One persistent launch over the whole prepared list (asynchronous). */
+/* The whole prepared list (asynchronous, stream-ordered on `stream`): one
+ * persistent launch for the degrees 2^10 .. 2^13 and one for 2^14, the
+ * second forked onto a stream owned by the batch and joined back into
+ * `stream` before the call returns, so that work queued on `stream` after
+ * the call sees every result.  Also valid while `stream` is being captured
+ * into a CUDA graph.  Errors: EINVAL (NULL, misaligned), ECUDA. */
 int polymul_ragged_run(polymul_ragged_batch *batch, const void *a, const void *b, void *c,
                        void *stream);
 
-/* The same launch as a CUDA graph: built on the first call, replayed after;
- * new operand pointers update the recorded launch in place. */
+/* The same launches as a CUDA graph of independent kernel nodes: built on
+ * the first call, replayed after; new operand pointers update the recorded
+ * launches in place. */
 int polymul_ragged_run_graph(polymul_ragged_batch *batch, const void *a, const void *b, void *c,
                              void *stream);
 

@@ -40,8 +40,9 @@ bool lookup_ntt_shared(int logn, int mode, KernelInfo* prep, KernelInfo* main);
 // one product per thread-block cluster (n = 2^14 .. 2^16)
 bool lookup_ntt_cluster(uint32_t elem, int logn, int mode, KernelInfo* ki);
 
-// uneven batches in one persistent launch (32-bit words, n = 2^10..2^14)
-bool lookup_ntt_ragged(int mode, KernelInfo* ki);
+// uneven batches (32-bit words): one persistent kernel for the degrees
+// 2^10..2^13 and one for 2^14
+bool lookup_ntt_ragged(int mode, KernelInfo* small, KernelInfo* big);
 
 // Toeplitz path on the tensor cores, k_toeplitz_batch<TShape<LOGN, WB, LA, LB>>
 bool lookup_toeplitz(int logn, int wb, int la, int lb, KernelInfo* ki);

@@ -106,7 +106,10 @@ __device__ __forceinline__ bool ragged_segment(const RaggedArgs& args, const Rag
 // `items`: the degree segments, largest degree first; ctr[i] is segment i's
 // unit counter, ctr[kRaggedMaxSegs] the count of finished CTAs (the last one
 // resets them all).  A CTA changes team layout only between segments.
-template <int MODE>
+// One instantiation serves the degrees 2^LO .. 2^HI: the 2^14 body (32
+// coefficients per thread) has a kernel of its own, so that its register
+// pressure (and the spills it causes) does not reach the other degrees.
+template <int MODE, int LO, int HI>
 __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[kRaggedMaxTeams];
@@ -127,8 +130,10 @@ __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs arg
     switch (seg.logn) {
 #define PM_SEG(L)                                                                                      \
   case L:                                                                                              \
-    ok = ragged_segment<RaggedShape<L>, MODE>(args, seg, ctr, smem, mbar, phases, s_next, bits);        \
-    teams = kRaggedThreads / RaggedShape<L>::T;                                                         \
+    if constexpr (L >= LO && L <= HI) {                                                                 \
+      ok = ragged_segment<RaggedShape<L>, MODE>(args, seg, ctr, smem, mbar, phases, s_next, bits);      \
+      teams = kRaggedThreads / RaggedShape<L>::T;                                                       \
+    }                                                                                                   \
     break;
       PM_SEG(10) PM_SEG(11) PM_SEG(12) PM_SEG(13) PM_SEG(14)
 #undef PM_SEG
@@ -161,25 +166,39 @@ __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs arg
   }
 }
 
-// dynamic shared memory: the largest class's team buffers
-int ragged_smem_bytes() {
-  int m = 0;
-  m = m > (kRaggedThreads / RaggedShape<10>::T) * RaggedShape<10>::SMEM_WORDS * 4 ? m : (kRaggedThreads / RaggedShape<10>::T) * RaggedShape<10>::SMEM_WORDS * 4;
-  m = m > (kRaggedThreads / RaggedShape<11>::T) * RaggedShape<11>::SMEM_WORDS * 4 ? m : (kRaggedThreads / RaggedShape<11>::T) * RaggedShape<11>::SMEM_WORDS * 4;
-  m = m > (kRaggedThreads / RaggedShape<12>::T) * RaggedShape<12>::SMEM_WORDS * 4 ? m : (kRaggedThreads / RaggedShape<12>::T) * RaggedShape<12>::SMEM_WORDS * 4;
-  m = m > (kRaggedThreads / RaggedShape<13>::T) * RaggedShape<13>::SMEM_WORDS * 4 ? m : (kRaggedThreads / RaggedShape<13>::T) * RaggedShape<13>::SMEM_WORDS * 4;
-  m = m > (kRaggedThreads / RaggedShape<14>::T) * RaggedShape<14>::SMEM_WORDS * 4 ? m : (kRaggedThreads / RaggedShape<14>::T) * RaggedShape<14>::SMEM_WORDS * 4;
-  return m;
+// dynamic shared memory of one degree class's team buffers
+template <int L>
+constexpr int ragged_class_smem() {
+  return (kRaggedThreads / RaggedShape<L>::T) * RaggedShape<L>::SMEM_WORDS * 4;
 }
 
-bool lookup_ntt_ragged(int mode, KernelInfo* ki) {
-  if (mode != 0 && mode != 1) return false;
-  ki->fn = mode == 0 ? (const void*)k_ntt_ragged<0> : (const void*)k_ntt_ragged<1>;
+template <int MODE, int LO, int HI>
+static void ragged_info(KernelInfo* ki) {
+  ki->fn = (const void*)k_ntt_ragged<MODE, LO, HI>;
   ki->block = kRaggedThreads;
-  ki->smem = ragged_smem_bytes();
+  int m = 0;
+  if (LO <= 10 && 10 <= HI) m = m > ragged_class_smem<10>() ? m : ragged_class_smem<10>();
+  if (LO <= 11 && 11 <= HI) m = m > ragged_class_smem<11>() ? m : ragged_class_smem<11>();
+  if (LO <= 12 && 12 <= HI) m = m > ragged_class_smem<12>() ? m : ragged_class_smem<12>();
+  if (LO <= 13 && 13 <= HI) m = m > ragged_class_smem<13>() ? m : ragged_class_smem<13>();
+  if (LO <= 14 && 14 <= HI) m = m > ragged_class_smem<14>() ? m : ragged_class_smem<14>();
+  ki->smem = m;
   ki->team = 0;
   ki->units_per_cta = 1;
   ki->tmem_cols = 0;
+}
+
+// small: degrees 2^10 .. 2^13; big: 2^14
+bool lookup_ntt_ragged(int mode, KernelInfo* small, KernelInfo* big) {
+  if (mode == 0) {
+    ragged_info<0, 10, 13>(small);
+    ragged_info<0, 14, 14>(big);
+  } else if (mode == 1) {
+    ragged_info<1, 10, 13>(small);
+    ragged_info<1, 14, 14>(big);
+  } else {
+    return false;
+  }
   return true;
 }
 

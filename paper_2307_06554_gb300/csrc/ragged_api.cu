@@ -1,7 +1,7 @@
 // C-ABI entry points for uneven batches (polymul_ragged_*), see
 // include/polymul.h.  Host-side planning: tables per pool prime, units
-// sorted into degree segments, one persistent launch, optional CUDA-graph
-// replay.
+// sorted into degree segments, two concurrent persistent launches (2^14;
+// 2^10 .. 2^13), optional CUDA-graph replay.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,21 +31,28 @@ struct polymul_ragged {
   void* d_twf = nullptr;
   void* d_twi = nullptr;
   void* d_pc = nullptr;
-  KernelInfo ki;
-  int grid_cap = 0, device = 0, num_sms = 0;
+  KernelInfo ki[2];    // [0]: degrees 2^10 .. 2^13, [1]: 2^14
+  int grid_cap[2] = {0, 0};
+  int device = 0, num_sms = 0;
 };
 
+// A prepared list runs as up to two persistent launches (the 2^14 segment
+// and the smaller degrees), concurrent on two streams (or as two
+// independent nodes of one CUDA graph).
 struct polymul_ragged_batch {
   polymul_ragged* ctx = nullptr;
   uint64_t n_units = 0, n_items = 0, total_elems = 0;
+  uint64_t part_units[2] = {0, 0};  // units of each launch ([0] small degrees, [1] 2^14)
   RaggedUnit* d_units = nullptr;
   RaggedItem* d_items = nullptr;
-  unsigned long long* d_ctr = nullptr;
+  unsigned long long* d_ctr = nullptr;  // 2 x (kRaggedMaxSegs + 1): one counter set per launch
   int* d_err = nullptr;
-  RaggedArgs args{};
+  RaggedArgs args[2]{};
+  cudaStream_t side = nullptr;  // the second launch's stream (fork/join with the caller's)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t node = nullptr;
+  cudaGraphNode_t node[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -127,22 +134,20 @@ extern "C" int polymul_ragged_create(const uint64_t* pool, uint32_t pool_size, u
   if (rc == POLYMUL_OK) rc = up(&r->d_twf, twf.data(), twf.size() * 4);
   if (rc == POLYMUL_OK) rc = up(&r->d_twi, twi.data(), twi.size() * 4);
   if (rc == POLYMUL_OK) rc = up(&r->d_pc, pcs.data(), pcs.size() * sizeof(PrimeConst<uint32_t>));
-  if (rc == POLYMUL_OK && !lookup_ntt_ragged(r->mode, &r->ki)) rc = fail(POLYMUL_ENOTSUP, "no ragged kernel");
+  if (rc == POLYMUL_OK && !lookup_ntt_ragged(r->mode, &r->ki[0], &r->ki[1]))
+    rc = fail(POLYMUL_ENOTSUP, "no ragged kernel");
   if (rc == POLYMUL_OK) {
-    int per_sm = 0;
     cudaError_t e = cudaGetDevice(&r->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(r->ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->ki.smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, r->ki.fn, r->ki.block, r->ki.smem);
-    if (e != cudaSuccess) {
-      rc = cuda_fail(e, "ragged kernel configuration");
-    } else if (per_sm < 1) {
-      rc = fail(POLYMUL_ENOTSUP, "ragged kernel does not fit on an SM");
-    } else {
-      r->grid_cap = per_sm * r->num_sms;
+    for (int i = 0; i < 2 && e == cudaSuccess && rc == POLYMUL_OK; ++i) {
+      int per_sm = 0;
+      e = cudaFuncSetAttribute(r->ki[i].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->ki[i].smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, r->ki[i].fn, r->ki[i].block, r->ki[i].smem);
+      if (e == cudaSuccess && per_sm < 1) rc = fail(POLYMUL_ENOTSUP, "ragged kernel does not fit on an SM");
+      r->grid_cap[i] = per_sm * r->num_sms;
     }
+    if (e != cudaSuccess) rc = cuda_fail(e, "ragged kernel configuration");
   }
   if (rc != POLYMUL_OK) {
     std::string keep = polymul_last_error();
@@ -158,6 +163,9 @@ extern "C" void polymul_ragged_batch_destroy(polymul_ragged_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   cudaFree(b->d_units);
   cudaFree(b->d_items);
   cudaFree(b->d_ctr);
@@ -213,19 +221,30 @@ extern "C" int polymul_ragged_prepare(polymul_ragged* r, const polymul_desc* des
   rc = up((void**)&b->d_units, units.data(), units.size() * sizeof(RaggedUnit));
   if (rc == POLYMUL_OK) rc = up((void**)&b->d_items, items.data(), items.size() * sizeof(RaggedItem));
   if (rc == POLYMUL_OK) {
-    const unsigned long long zero[kRaggedMaxSegs + 1] = {};
+    const unsigned long long zero[2 * (kRaggedMaxSegs + 1)] = {};
     const int z = 0;
     rc = up((void**)&b->d_ctr, zero, sizeof zero);
     if (rc == POLYMUL_OK) rc = up((void**)&b->d_err, &z, sizeof z);
   }
+  if (rc == POLYMUL_OK && (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    rc = fail(POLYMUL_ECUDA, "stream or event creation failed");
   if (rc != POLYMUL_OK) {
     std::string keep = polymul_last_error();
     polymul_ragged_batch_destroy(b);
     fail(rc, "%s", keep.c_str());
     return rc;
   }
-  b->args = RaggedArgs{nullptr, nullptr, nullptr, b->d_units, b->d_items, b->n_items, r->d_twf, r->d_twi,
-                       (const PrimeConst<uint32_t>*)r->d_pc, r->nmax, b->d_ctr, b->d_err};
+  // the 2^14 segment (first, if present) goes to the second kernel
+  const uint64_t n_big = (!items.empty() && items[0].logn == 14) ? 1 : 0;
+  b->part_units[1] = n_big ? items[0].count : 0;
+  b->part_units[0] = b->n_units - b->part_units[1];
+  b->args[1] = RaggedArgs{nullptr, nullptr, nullptr, b->d_units, b->d_items, n_big, r->d_twf, r->d_twi,
+                          (const PrimeConst<uint32_t>*)r->d_pc, r->nmax, b->d_ctr, b->d_err};
+  b->args[0] = RaggedArgs{nullptr, nullptr, nullptr, b->d_units, b->d_items + n_big, b->n_items - n_big,
+                          r->d_twf, r->d_twi, (const PrimeConst<uint32_t>*)r->d_pc, r->nmax,
+                          b->d_ctr + (kRaggedMaxSegs + 1), b->d_err};
   *out = b;
   return POLYMUL_OK;
 }
@@ -237,50 +256,74 @@ int ragged_check(polymul_ragged_batch* b, const void* a, const void* bb, void* c
   if (((uintptr_t)a | (uintptr_t)bb | (uintptr_t)c) & 15u) return fail(POLYMUL_EINVAL, "operands must be 16-byte aligned");
   return POLYMUL_OK;
 }
-int ragged_grid(const polymul_ragged_batch* b) {
-  return (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap, std::max<uint64_t>(1, b->n_units));
+int ragged_grid(const polymul_ragged_batch* b, int part) {
+  return (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap[part], std::max<uint64_t>(1, b->part_units[part]));
+}
+void set_operands(polymul_ragged_batch* b, const void* a, const void* bb, void* c) {
+  for (int i = 0; i < 2; ++i) {
+    b->args[i].a = (const uint32_t*)a;
+    b->args[i].b = (const uint32_t*)bb;
+    b->args[i].c = (uint32_t*)c;
+  }
 }
 }  // namespace
 
+// Up to two persistent launches: the 2^14 segment on the caller's stream and
+// the smaller degrees on a side stream that forks from and joins back into
+// it, so that either launch's tail can fill with the other's CTAs.
 extern "C" int polymul_ragged_run(polymul_ragged_batch* b, const void* a, const void* bb, void* c, void* stream) {
   clear_error();
   TraceRange trace_("polymul_ragged_run");
   int rc = ragged_check(b, a, bb, c);
   if (rc != POLYMUL_OK || b->n_items == 0) return rc;
-  b->args.a = (const uint32_t*)a;
-  b->args.b = (const uint32_t*)bb;
-  b->args.c = (uint32_t*)c;
-  void* argv[] = {&b->args};
-  PM_CUDA(cudaLaunchKernel(b->ctx->ki.fn, ragged_grid(b), b->ctx->ki.block, argv, b->ctx->ki.smem,
-                           (cudaStream_t)stream));
+  set_operands(b, a, bb, c);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool both = b->part_units[0] && b->part_units[1];
+  if (both) {
+    PM_CUDA(cudaEventRecord(b->ev_fork, st));
+    PM_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+  }
+  for (int i = 1; i >= 0; --i) {
+    if (!b->part_units[i]) continue;
+    void* argv[] = {&b->args[i]};
+    cudaStream_t s = (both && i == 0) ? b->side : st;
+    PM_CUDA(cudaLaunchKernel(b->ctx->ki[i].fn, ragged_grid(b, i), b->ctx->ki[i].block, argv, b->ctx->ki[i].smem, s));
+  }
+  if (both) {
+    PM_CUDA(cudaEventRecord(b->ev_join, b->side));
+    PM_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
+  }
   return POLYMUL_OK;
 }
 
-// The same single launch, recorded once as a one-node CUDA graph and
-// replayed; a change of operand pointers updates the node in place.
+// The same launches, recorded once as a CUDA graph of one or two independent
+// kernel nodes and replayed; a change of operand pointers updates the nodes
+// in place.
 extern "C" int polymul_ragged_run_graph(polymul_ragged_batch* b, const void* a, const void* bb, void* c,
                                         void* stream) {
   clear_error();
   TraceRange trace_("polymul_ragged_run_graph");
   int rc = ragged_check(b, a, bb, c);
   if (rc != POLYMUL_OK || b->n_items == 0) return rc;
-  b->args.a = (const uint32_t*)a;
-  b->args.b = (const uint32_t*)bb;
-  b->args.c = (uint32_t*)c;
-  void* argv[] = {&b->args};
-  cudaKernelNodeParams kp;
-  memset(&kp, 0, sizeof kp);
-  kp.func = const_cast<void*>(b->ctx->ki.fn);
-  kp.gridDim = dim3(ragged_grid(b));
-  kp.blockDim = dim3(b->ctx->ki.block);
-  kp.sharedMemBytes = b->ctx->ki.smem;
-  kp.kernelParams = argv;
+  set_operands(b, a, bb, c);
+  cudaKernelNodeParams kp[2];
+  void* argv[2][1] = {{&b->args[0]}, {&b->args[1]}};
+  for (int i = 0; i < 2; ++i) {
+    memset(&kp[i], 0, sizeof kp[i]);
+    kp[i].func = const_cast<void*>(b->ctx->ki[i].fn);
+    kp[i].gridDim = dim3(ragged_grid(b, i));
+    kp[i].blockDim = dim3(b->ctx->ki[i].block);
+    kp[i].sharedMemBytes = b->ctx->ki[i].smem;
+    kp[i].kernelParams = argv[i];
+  }
   if (!b->exec) {
     PM_CUDA(cudaGraphCreate(&b->graph, 0));
-    PM_CUDA(cudaGraphAddKernelNode(&b->node, b->graph, nullptr, 0, &kp));
+    for (int i = 1; i >= 0; --i)
+      if (b->part_units[i]) PM_CUDA(cudaGraphAddKernelNode(&b->node[i], b->graph, nullptr, 0, &kp[i]));
     PM_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
   } else {
-    PM_CUDA(cudaGraphExecKernelNodeSetParams(b->exec, b->node, &kp));
+    for (int i = 0; i < 2; ++i)
+      if (b->node[i]) PM_CUDA(cudaGraphExecKernelNodeSetParams(b->exec, b->node[i], &kp[i]));
   }
   PM_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
   return POLYMUL_OK;
@@ -294,7 +337,7 @@ extern "C" int polymul_ragged_status(polymul_ragged_batch* b, void* stream) {
   PM_CUDA(cudaMemcpy(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (!h) return POLYMUL_OK;
   PM_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
-  PM_CUDA(cudaMemset(b->d_ctr, 0, (kRaggedMaxSegs + 1) * sizeof(unsigned long long)));
+  PM_CUDA(cudaMemset(b->d_ctr, 0, 2 * (kRaggedMaxSegs + 1) * sizeof(unsigned long long)));
   return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }
 
@@ -304,6 +347,6 @@ extern "C" int polymul_ragged_batch_info(const polymul_ragged_batch* b, uint64_t
   if (!b) return fail(POLYMUL_EINVAL, "batch is NULL");
   if (units) *units = b->n_units;
   if (items) *items = b->n_items;
-  if (grid) *grid = (uint32_t)ragged_grid(b);
+  if (grid) *grid = (uint32_t)std::max(b->part_units[0] ? ragged_grid(b, 0) : 0, b->part_units[1] ? ragged_grid(b, 1) : 0);
   return POLYMUL_OK;
 }
