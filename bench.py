@@ -295,7 +295,9 @@ def _host_link(dev, h2d_bytes, d2h_bytes, reps=10):
 
 def _tensor_smem_roofline(n, digits, units, seconds, sms, sm_mhz):
     nb = (8 * digits + 15) // 16 * 16
-    mmas = digits * (n // 1024) * (n // 16)  # per unit: digits of a x row blocks x K steps
+    # per (product, prime): digits of a x 128-row blocks (one below n = 1024,
+    # its rows past n/8 discarded) x K steps of 16
+    mmas = digits * max(1, n // 1024) * (n // 16)
     byts = units * mmas * (128 * 32 + nb * 32)
     peak = sms * SMEM_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
     ach = byts / seconds / 1e9
@@ -321,18 +323,20 @@ def _time_steps(step, stream, reps):
 def other_workloads(dev, stream, peaks, alu_peak_g, samples):
     """Throughput of the other standing workloads (not the headline line):
     n=256 q=3329 (auxiliary-prime NTT, launch-latency bound), n=4096 with 8
-    RNS primes and ternary b, the headline's batch in the cyclic ring
-    x^n - 1, and the 2000-product uneven list (one persistent launch
-    replayed as a CUDA graph)."""
+    RNS primes and ternary b, each also on the tensor path, the headline's
+    batch in the cyclic ring x^n - 1, and the 2000-product uneven list (two
+    concurrent persistent launches replayed as a CUDA graph)."""
     import torch
     from paper_2307_06554_gb300 import polymul, workloads as wl
     out = {}
     sp = stream.cuda_stream
     hbm = peaks["hbm_gbs"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    def homogeneous(name, w, sets_needed, reps, cyclic=False):
-        flags = polymul.FLAG_TUNE | (polymul.FLAG_CYCLIC if cyclic else 0)
-        plan = polymul.Plan(w.n, w.q_list, flags=flags, tune_batch=w.batch)
+    def homogeneous(name, w, sets_needed, reps, cyclic=False, path=None):
+        flags = (polymul.FLAG_TUNE if path is None else 0) | (polymul.FLAG_CYCLIC if cyclic else 0)
+        plan = polymul.Plan(w.n, w.q_list, path=polymul.PATH_AUTO if path is None else path, flags=flags,
+                            tune_batch=w.batch)
         k = len(w.q_list)
         elem = plan.elem_bytes
         view = np.int32 if elem == 4 else np.int64
@@ -358,17 +362,30 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
         elif plan.info["path"] == 1:
             path += " (radix %d register passes, autotuned over %d)" % (1 << plan.info["radix_bits"],
                                                                      plan.info["candidates"])
+        info = plan.info
+        if info["path"] == 2:
+            desc = "tensor (%d digits of %d bits, %s)" % (
+                info["digits"], info["digit_bits"],
+                "%d output groups per product" % info["tensor_groups"] if info["tensor_groups"] else "whole product per CTA")
         out[name] = {"products_per_s": w.batch / (ms / 1e3), "us_per_step": ms * 1e3, "batch": w.batch,
-                     "n": w.n, "k": k, "path": path,
-                     "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g,
+                     "n": w.n, "k": k, "path": desc if info["path"] == 2 else path,
                      "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm,
                      "bit_exact_sample": None,
                      "l2": "inputs rotated over %d buffer sets" % len(sets) if len(sets) > 1 else "L2-resident"}
+        if info["path"] == 2:
+            flops = 2.0 * w.n * w.n * info["digits"] ** 2 * units
+            out[name]["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
+            out[name]["tensor_frac_smem"] = _tensor_smem_roofline(
+                w.n, info["digits"], units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0))["frac"]
+        else:
+            out[name]["alu_frac"] = mm / (ms / 1e3) / 1e9 / alu_peak_g
         plan.close()
 
     homogeneous("ring_small", wl.ring_small(), 1, 200)
     out["ring_small"]["graph_1000"] = graph_replay(dev, wl.ring_small(), 1000)
+    homogeneous("ring_small_tensor", wl.ring_small(), 1, 200, path=polymul.PATH_TENSOR)
     homogeneous("rns_4096", wl.rns_4096(), 6, 20)
+    homogeneous("rns_4096_tensor", wl.rns_4096(), 6, 5, path=polymul.PATH_TENSOR)
     # the cyclic ring x^n - 1 on the headline's shape and data
     homogeneous("ring_1024_cyclic", wl.ring_1024(), 9, 50, cyclic=True)
 
@@ -397,7 +414,7 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
         mm = sum(len(p.prime_idx) * _ntt_mulmods(p.n) for p in rag.products)
         out["ragged_2000"] = {"products_per_s": len(rag.products) / (ms / 1e3), "us_per_launch": ms * 1e3,
                               "units": r.info["units"], "work_items": r.info["items"], "grid": r.info["grid"],
-                              "path": "ntt, one persistent launch replayed as a CUDA graph",
+                              "path": "ntt, two concurrent persistent launches (2^14; 2^10..2^13) replayed as a CUDA graph",
                               "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g,
                               "hbm_frac": 3 * total * 4 / (ms / 1e3) / 1e9 / hbm,
                               "bit_exact_sample": None, "l2": "inputs 1.3 GB (> L2)"}
@@ -441,21 +458,31 @@ def graph_replay(dev, w, launches):
 
 
 def crossover(dev, stream, peaks, alu_peak_g, samples):
-    """Tensor (Toeplitz) path against the NTT path on the same inputs, for
-    every shape the tensor kernel covers: n in {1024, 2048} and 2..4 digits
-    per coefficient (prime sizes chosen to need that many digits).  Inputs:
-    seed 6, uniform residues, operands rotated over buffer sets larger than
-    L2.  Both paths must agree on every coefficient of the batch."""
+    """Tensor (Toeplitz) path against the NTT path on the same inputs, over
+    n = 2^6 .. 2^14 at a fixed number of coefficients per batch (2^22), for
+    two modulus families: the smallest NTT-friendly prime from 12289 up (12289
+    itself to n = 2048; 40961, 65537 above: 2 or 3 digits) and a 30-bit prime
+    (4 or 5 digits).  Inputs: seed 6, uniform residues, operands rotated over
+    buffer sets larger than L2.  Both paths must agree on every coefficient
+    of the batch."""
     import torch
     from paper_2307_06554_gb300 import polymul, workloads as wl
     rng = np.random.default_rng(6)
-    shapes = [(1024, 12289), (1024, wl.draw_primes(rng, 1, 23, 23, 11)[0]),
-              (1024, wl.draw_primes(rng, 1, 30, 30, 11)[0]), (2048, 12289),
-              (2048, wl.draw_primes(rng, 1, 20, 20, 12)[0])]
+
+    def small_prime(n):
+        q = 12289
+        while (q - 1) % (2 * n) or not wl.is_prime(q):
+            q += 1
+        return q
+    shapes = []
+    for logn in range(6, 15):
+        n = 1 << logn
+        shapes.append((n, small_prime(n)))
+        shapes.append((n, wl.draw_primes(rng, 1, 30, 30, logn + 1)[0]))
     sp = stream.cuda_stream
     rows = []
     for n, q in shapes:
-        batch = 4096 * 1024 // n
+        batch = (1 << 22) // n
         a = wl.uniform_coeffs(rng, batch, [q], n)
         b = wl.uniform_coeffs(rng, batch, [q], n)
         ta = torch.from_numpy(a.view(np.int32)).to(dev)
@@ -472,12 +499,13 @@ def crossover(dev, stream, peaks, alu_peak_g, samples):
                 polymul.polymul_batch(h, x, y, z, batch, sp)
             for i in range(3):
                 step(i)
-            ms = _time_steps(step, stream, 20)
+            ms = _time_steps(step, stream, 20 if n * q.bit_length() < 4096 * 20 else 5)
             info = plan.info
             row[name + "_us"] = ms * 1e3
             row[name + "_products_per_s"] = batch / (ms / 1e3)
             if name == "tensor":
                 row["digit_bits"], row["digits"] = info["digit_bits"], info["digits"]
+                row["tensor_groups"] = info["tensor_groups"]
                 flops = 2.0 * n * n * info["digits"] ** 2 * batch
                 row["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
                 row["tensor_frac_smem"] = _tensor_smem_roofline(

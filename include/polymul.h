@@ -105,7 +105,10 @@ typedef struct polymul_plan_info {
     uint32_t regs;        /* NTT path: register budget per thread of the main
                              kernel (fewer registers, more resident warps)  */
     uint32_t cyclic;      /* 1: the ring Z_q[x]/(x^n-1); 0: Z_q[x]/(x^n+1) */
-    uint32_t reserved[1];
+    uint32_t tensor_groups;/* tensor path: 0 for the whole-product kernel
+                             (n = 1024, 2048); else the tiled kernel's units
+                             of work per (product, prime): output groups of
+                             up to 1024 coefficients each                   */
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */

@@ -21,6 +21,7 @@
 #include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
+#include "toeplitz_tiled.h"
 
 using namespace pm;
 
@@ -257,9 +258,21 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     }
   }
 
-  // tensor path: 32-bit words, n in the instantiated set
-  bool tensor_ok = p->elem == 4 && tensor_shape(n, qmax, &p->digit_bits, &p->digits) &&
-                   lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki);
+  // tensor path: moduli below 2^31, n = 2^6 .. 2^14.  The whole-product
+  // kernel where it is instantiated (n = 1024, 2048), the tiled kernel
+  // otherwise, and as a second candidate beside the whole-product one
+  bool tensor_ok = false, tiled_extra = false;
+  KernelInfo tki_tiled;
+  if (p->elem == 4 && qmax < (1ull << 31) && tensor_shape(n, qmax, &p->digit_bits, &p->digits)) {
+    const bool tiled = lookup_toeplitz_tiled((int)p->logn, p->digits, p->digits, &tki_tiled);
+    if (lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki)) {
+      tensor_ok = true;
+      tiled_extra = tiled;
+    } else if (tiled) {
+      p->tki = tki_tiled;
+      tensor_ok = true;
+    }
+  }
 
   int rc = POLYMUL_OK;
   // NTT batch kernels take a programmatic dependent launch (measured on
@@ -286,6 +299,7 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     } else {
       rc = upload_tensor_tables(p);
       if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
+      if (rc == POLYMUL_OK && tiled_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_tiled);
     }
   } else if (!ntt_ok) {
     rc = fail(POLYMUL_ENOTSUP, "no NTT route for these moduli at n=%u (need prime q = 1 mod %s, q < 2^31 for 32-bit words)",
@@ -305,6 +319,7 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) {
       rc = upload_tensor_tables(p);
       if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
+      if (rc == POLYMUL_OK && tiled_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_tiled);
     }
   }
   if (rc == POLYMUL_OK) apply_candidate(p, 0);
@@ -378,6 +393,11 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->ntt_mode = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.mode : 0u;
   info->regs = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.regs : 0u;
   info->cyclic = p->cyclic ? 1u : 0u;
+  info->tensor_groups = 0;
+  if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
+    TiledCfg tc;
+    if (toeplitz_tiled_config((int)p->logn, p->digits, p->digits, &tc)) info->tensor_groups = tc.ngrp;
+  }
   return POLYMUL_OK;
 }
 
@@ -458,7 +478,17 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     }
     return POLYMUL_OK;
   };
-  if (p->path == POLYMUL_PATH_TENSOR) {
+  if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
+    TiledCfg tc;
+    if (!toeplitz_tiled_config((int)p->logn, p->digits, p->digits, &tc)) return fail(POLYMUL_ENOTSUP, "tensor tiling");
+    const uint64_t tunits = units * tc.ngrp;
+    TensorTiledArgs args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, (const TensorPrime*)p->d_tpc,
+                         tunits, p->k, p->cyclic ? 0u : 0x80008000u, p->logn, (uint32_t)p->digit_bits,
+                         tc.bpg, tc.ngrp, tc.kc, tc.a_win, tc.bt_off, tc.tmem_cols, ctr, p->d_err};
+    void* argv[] = {&args};
+    const int tgrid = (int)std::min<uint64_t>(tunits, (uint64_t)p->grid_cap);
+    PM_CUDA(cudaLaunchKernel(p->ki.fn, tgrid, p->ki.block, argv, p->ki.smem, st));
+  } else if (p->path == POLYMUL_PATH_TENSOR) {
     TensorBatchArgs args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, (const TensorPrime*)p->d_tpc,
                          units, p->k, p->cyclic ? 0u : 0x80008000u, ctr, p->d_err};
     void* argv[] = {&args};

@@ -33,6 +33,7 @@
 #include "kernels.h"
 #include "polymul_types.h"
 #include "tcgen05.cuh"
+#include "toeplitz_common.cuh"
 
 namespace pm {
 
@@ -62,24 +63,6 @@ struct TShape {
   static_assert(N >= 1024 && CPT % 8 == 0 && THREADS == 128, "n >= 1024, four warps");
   static_assert(N * (1 << (2 * WB - 2)) <= (1 << 24), "digit width breaks fp32 exactness");
 };
-
-// bf16 bit pattern of a small integer d (|d| <= 256, so exact in bf16):
-// adding d to the pattern of 1.5 * 2^23 puts d in the units of the
-// mantissa; subtracting 1.5 * 2^23 leaves d exactly as a float, whose top
-// 16 bits are then its bf16 pattern.  Two digits, packed low/high.
-__device__ __forceinline__ uint32_t bf16x2_of(int d0, int d1) {
-  const float f0 = __int_as_float(0x4B400000 + d0) - 12582912.0f;
-  const float f1 = __int_as_float(0x4B400000 + d1) - 12582912.0f;
-  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-}
-
-// x mod q for 0 <= x < 2^64 (Barrett, mu = floor(2^64 / q)): the estimate
-// is floor(x / q) or one less.
-__device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t q, uint64_t mu) {
-  const uint64_t qh = __umul64hi(x, mu);
-  const uint32_t r = (uint32_t)(x - qh * q);
-  return r >= q ? r - q : r;
-}
 
 template <class TS>
 __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args) {
@@ -202,18 +185,7 @@ __global__ void __launch_bounds__(128, 1) k_toeplitz_batch(TensorBatchArgs args)
         }
         const uint4 ow = bw[gi][s2];
         const uint32_t E[8] = {pv.x, pv.y, pv.z, pv.w, ow.x, ow.y, ow.z, ow.w};
-        unsigned char* dst = Bt + dp * TS::BT_PITCH + s2 * 128;
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          uint32_t o[4];
-          const int c = v >> 1;
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            // low half: E[v + 8 - 2 jj], high half: E[v + 7 - 2 jj]
-            o[jj] = (v & 1) ? __byte_perm(E[c + 4 - jj], 0u, 0x1032) : __byte_perm(E[c + 4 - jj], E[c + 3 - jj], 0x7610);
-          }
-          *reinterpret_cast<uint4*>(dst + 16 * v) = make_uint4(o[0], o[1], o[2], o[3]);
-        }
+        b_block_rows(E, Bt + dp * TS::BT_PITCH + s2 * 128);
       }
     }
     fence_proxy_async();

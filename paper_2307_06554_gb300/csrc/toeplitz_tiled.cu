@@ -1,0 +1,324 @@
+// Path (b) at every degree 2^6 .. 2^14: the matrix form of toeplitz.cu with
+// the summation dimension in chunks and the outputs in groups.
+//
+// What it computes: c = a * T(b) in Z_q[x]/(x^n+1) (or x^n - 1), the row
+// vector of a times the negacyclic (cyclic) Toeplitz matrix of b (Sec. 2.2),
+// for many independent (a, b) pairs, with balanced w-bit digits of the
+// centred coefficients (Sec. 2.4) recombined mod q in the epilogue
+// (Algorithm 1, ConvertMatrix).  The algebra is that of toeplitz.cu
+// (Sec. 2.5 division into 8-coefficient blocks):
+//   c_j = sum_k A[u][k] B[v][k],  j = 8u + v,  k = 8d' + r,  D = n/8 - 1,
+//   A[u][k] = a~_{8u + k - 8D},   B[v][k] = b~_{8(D - d') + v - r},
+// a~, b~ the antiperiodic (periodic) extensions.
+//
+// Sec. 2.6 (high degrees): the product is cut into pieces that fit the
+// matrix unit.  A unit of work is one (product, prime, output group): BPG
+// blocks of 128 rows of A (1024 outputs each; for n < 1024 one block whose
+// rows past n/8 compute outputs that are discarded), accumulated in tensor
+// memory over the K chunks [KC c, KC (c + 1)).  For each chunk the CTA
+// builds in shared memory
+//   * the window of a~'s digits that the chunk's rows read: row u of block
+//     bl starts 8 (128 bl + u) elements into it, so A is read through a
+//     descriptor with a 16-byte row stride, never materialised, and
+//   * the chunk's KC/8 K-blocks of B in the canonical K-major layout,
+// one thread issues the MMA chains (one per digit of a and per block), and
+// the CTA waits for them before it rebuilds the buffers.  Two CTAs share an
+// SM (at most 256 tensor-memory columns and about 110 KB of shared memory
+// each), so that one builds while the other's MMAs run.
+//
+// Exactness: every digit has magnitude <= 2^(w-1) <= 128 (exact in bf16) and
+// n 2^(2w-2) <= 2^24 (the host chooses w so), so every fp32 partial sum over
+// the whole of K is an exact integer.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "polymul_types.h"
+#include "tcgen05.cuh"
+#include "toeplitz_common.cuh"
+#include "toeplitz_tiled.h"
+
+namespace pm {
+
+namespace {
+constexpr int kTiledThreads = 128;
+constexpr int kTiledSmemCap = 110 * 1024;  // two CTAs per SM
+constexpr int kTiledTmemCap = 256;         // tensor-memory columns per CTA
+}  // namespace
+
+template <int LA, int LB>
+struct TTShape {
+  static constexpr int NB = (8 * LB + 15) / 16 * 16;  // MMA N: 8 rows per digit of b, padded
+  static constexpr int NG = NB / 8;                   // 8-row groups of B
+  // core matrices adjacent along K are BT_PITCH bytes apart (16 bytes more
+  // than the N-groups need: consecutive threads' 16-byte stores, one K-block
+  // each, fall in distinct banks)
+  static constexpr int BT_PITCH = NG * 128 + 16;
+  static constexpr int CB = LA * NB;  // accumulator columns of one 128-row block
+};
+
+// balanced w-bit digits of the centred representative of v mod q (v < q < 2^31)
+template <int L>
+__device__ __forceinline__ void centred_digits(uint32_t v, uint32_t q, int wb, int (&d)[L]) {
+  const int32_t half = 1 << (wb - 1), mask = (1 << wb) - 1;
+  int32_t x = v > (q >> 1) ? (int32_t)(v - q) : (int32_t)v;
+#pragma unroll
+  for (int s = 0; s < L; ++s) {
+    const int32_t t = ((x + half) & mask) - half;
+    x = (x - t) >> wb;
+    d[s] = t;
+  }
+}
+
+// 8 consecutive coefficients (16-byte aligned) -> per digit, 8 bf16 packed
+// in a uint4
+template <int L>
+__device__ __forceinline__ void digits8(const uint32_t* src, uint32_t q, int wb, uint4 (&out)[L]) {
+  const uint4 v0 = *reinterpret_cast<const uint4*>(src);
+  const uint4 v1 = *reinterpret_cast<const uint4*>(src + 4);
+  const uint32_t xv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  int d[8][L];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) centred_digits<L>(xv[e], q, wb, d[e]);
+#pragma unroll
+  for (int s = 0; s < L; ++s)
+    out[s] = make_uint4(bf16x2_of(d[0][s], d[1][s]), bf16x2_of(d[2][s], d[3][s]), bf16x2_of(d[4][s], d[5][s]),
+                        bf16x2_of(d[6][s], d[7][s]));
+}
+
+template <int LA, int LB>
+__global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiledArgs args) {
+  using TS = TTShape<LA, LB>;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ unsigned long long s_next;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t n = 1u << args.logn, D = n / 8 - 1;
+  const uint32_t kc = args.kc, nch = n / kc, bpg = args.bpg, ngrp = args.ngrp, awin = args.a_win;
+  const int wb = (int)args.wb;
+  const uint32_t wrap = args.wrap;
+  const uint64_t units = args.units;
+  uint16_t* Xw = reinterpret_cast<uint16_t*>(sm);  // [LA][awin] digits of a~ over the chunk's window
+  unsigned char* Bt = sm + args.bt_off;             // [kc/8][BT_PITCH] the chunk of B
+  constexpr uint32_t IDESC = idesc_bf16(128, TS::NB);
+
+  if (warp == 0) {
+    tmem_alloc(&s_tmem, args.tmem_cols);
+    tmem_relinquish();
+  }
+  if (tid == 0) mbar_init(&mbar, 1);
+  fence_mbar_init();
+  // padded rows of B (digit slots >= LB) stay zero for the whole launch
+  if (TS::NG > LB) {
+    for (uint32_t ch = tid; ch < (kc / 8) * TS::NG * 8; ch += kTiledThreads) {
+      const uint32_t dp = ch / (TS::NG * 8), g = (ch / 8) % TS::NG, v = ch % 8;
+      if (g >= (uint32_t)LB) *reinterpret_cast<uint4*>(Bt + dp * TS::BT_PITCH + g * 128 + 16 * v) = make_uint4(0, 0, 0, 0);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (tid == 0) s_next = atomicAdd(args.ctr, 1ull);
+  __syncthreads();
+  unsigned long long cur = s_next;
+  uint32_t parity = 0;
+  bool failed = false;
+  while (cur < units) {
+    __syncthreads();  // every thread has read s_next
+    if (tid == 0) s_next = atomicAdd(args.ctr, 1ull);
+    const uint64_t row = cur / ngrp;
+    const uint32_t grp = (uint32_t)(cur % ngrp);
+    const uint32_t j = (uint32_t)(row % args.k);
+    const uint32_t q = args.tp[j].q;
+    const uint32_t* a = args.a + row * n;
+    const uint32_t* b = args.b + row * n;
+    const uint32_t b0 = grp * bpg;  // first 128-row block of the group
+
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+      // ---- ConvertPoly (a): digits of a~_{base + e}, e < awin ----
+      // base and every group of 8 are multiples of 8, so a group lies wholly
+      // in [0, n) (a itself), in [-n, 0) (the extension: a_{i+n}, sign per
+      // `wrap`) or outside both (zero: rows past n/8 when n < 1024)
+      const int32_t base = (int32_t)(1024 * b0) - (int32_t)n + 8 + (int32_t)(kc * ch);
+      for (uint32_t gi = tid; gi < awin / 8; gi += kTiledThreads) {
+        const int32_t i0 = base + 8 * (int32_t)gi;
+        uint4 p[LA];
+        uint32_t flip = 0;
+        if (i0 >= (int32_t)n || i0 < -(int32_t)n) {
+#pragma unroll
+          for (int s = 0; s < LA; ++s) p[s] = make_uint4(0, 0, 0, 0);
+        } else {
+          flip = i0 < 0 ? wrap : 0u;
+          digits8<LA>(a + (i0 < 0 ? i0 + (int32_t)n : i0), q, wb, p);
+        }
+#pragma unroll
+        for (int s = 0; s < LA; ++s)
+          *reinterpret_cast<uint4*>(Xw + (size_t)s * awin + 8 * gi) =
+              make_uint4(p[s].x ^ flip, p[s].y ^ flip, p[s].z ^ flip, p[s].w ^ flip);
+      }
+      // ---- ConvertPoly (b): the chunk's K-blocks d' = kc/8 ch + dl of B ----
+      // K-block d' belongs to b's group g = D - d'; its window is group g - 1
+      // followed by group g (group -1 is the last group, negated for x^n + 1)
+      for (uint32_t dl = tid; dl < kc / 8; dl += kTiledThreads) {
+        const uint32_t g = D - (kc / 8 * ch + dl);
+        const uint32_t gp = g == 0 ? n / 8 - 1 : g - 1;
+        const uint32_t pflip = g == 0 ? wrap : 0u;
+        uint4 pv[LB], ow[LB];
+        digits8<LB>(b + 8 * gp, q, wb, pv);
+        digits8<LB>(b + 8 * g, q, wb, ow);
+#pragma unroll
+        for (int s2 = 0; s2 < LB; ++s2) {
+          const uint32_t E[8] = {pv[s2].x ^ pflip, pv[s2].y ^ pflip, pv[s2].z ^ pflip, pv[s2].w ^ pflip,
+                                 ow[s2].x, ow[s2].y, ow[s2].z, ow[s2].w};
+          b_block_rows(E, Bt + dl * TS::BT_PITCH + s2 * 128);
+        }
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+
+      // ---- TPUMul: one thread issues the chains of this chunk ----
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t xa0 = smem_u32(Xw), bt0 = smem_u32(Bt);
+        const uint64_t bd0 = smem_desc(bt0, TS::BT_PITCH, 128);
+        constexpr uint64_t BSTEP = (2 * TS::BT_PITCH) >> 4;  // two K-blocks per MMA (K = 16)
+#pragma unroll 1
+        for (uint32_t bl = 0; bl < bpg; ++bl) {
+#pragma unroll 1
+          for (int s = 0; s < LA; ++s) {
+            const uint32_t dcol = tmem + (bl * LA + s) * TS::NB;
+            const uint64_t ad0 = smem_desc(xa0 + (uint32_t)(s * awin + 1024 * bl) * 2, 16, 128);
+#pragma unroll 4
+            for (uint32_t kk = 0; kk < kc / 16; ++kk)
+              tc_mma_f16(dcol, ad0 + 2u * (uint64_t)kk, bd0 + BSTEP * (uint64_t)kk, IDESC, (ch > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        tc_commit(&mbar);
+      }
+      // warp 0's other lanes wait for the issuing lane at the warp barrier
+      if (warp == 0) __syncwarp();
+      const bool ok = mbar_wait(&mbar, parity);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      parity ^= 1u;
+      tc_fence_after();
+    }
+    if (failed) break;
+
+    // ---- ConvertMatrix: recombine digit pairs, reduce mod q, store ----
+    uint32_t* c = args.c + row * n;
+    const uint64_t mu = args.tp[j].mu, bias = args.tp[j].bias;
+#pragma unroll 1
+    for (uint32_t bl = 0; bl < bpg; ++bl) {
+      int64_t acc[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[v] = 0;
+#pragma unroll
+      for (int s = 0; s < LA; ++s) {
+#pragma unroll
+        for (int c16 = 0; c16 < TS::NB / 16; ++c16) {
+          uint32_t r[16];
+          // warp-collective: every lane loads, only the stores below are predicated
+          tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (bl * LA + s) * TS::NB + 16 * c16, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const int col = 16 * c16 + cc, s2 = col / 8, v = col % 8;
+            if (s2 < LB)
+              acc[v] += (int64_t)__float2int_rn(__uint_as_float(r[cc])) * (int64_t)args.tp[j].pw[s + s2];
+          }
+        }
+      }
+      const uint32_t j0 = 8 * (128 * (b0 + bl) + (uint32_t)tid);
+      if (j0 < n) {
+        uint32_t out[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) out[v] = barrett64((uint64_t)(acc[v] + (int64_t)bias), q, mu);
+        *reinterpret_cast<uint4*>(c + j0) = make_uint4(out[0], out[1], out[2], out[3]);
+        *reinterpret_cast<uint4*>(c + j0 + 4) = make_uint4(out[4], out[5], out[6], out[7]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cur = s_next;
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(args.err, 1);
+    mbar_wait(&mbar, parity);  // let the MMAs in flight finish before freeing their memory
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, args.tmem_cols);
+  }
+  if (!failed && tid == 0) {
+    __threadfence();
+    if (atomicAdd(args.ctr + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+      atomicExch(args.ctr, 0ull);
+      atomicExch(args.ctr + 1, 0ull);
+    }
+  }
+}
+
+bool toeplitz_tiled_config(int logn, int la, int lb, TiledCfg* cfg) {
+  if (logn < 6 || logn > 14 || la < 1 || lb < 1 || la > 5 || lb > 5) return false;
+  const uint32_t n = 1u << logn;
+  const uint32_t nb = (8 * lb + 15) / 16 * 16, pitch = nb / 8 * 128 + 16, cb = (uint32_t)la * nb;
+  if (cb > (uint32_t)kTiledTmemCap) return false;
+  const uint32_t rblk = n >= 1024 ? n / 1024 : 1;
+  uint32_t bpg = 1;
+  while (bpg * 2 <= rblk && bpg * 2 * cb <= (uint32_t)kTiledTmemCap) bpg *= 2;
+  uint32_t kc = n < 1024 ? n : 1024;
+  for (;;) {
+    const uint32_t a_win = 1024 * bpg + kc;
+    const uint32_t bt_off = ((uint32_t)la * a_win * 2 + 127) / 128 * 128;
+    const uint32_t smem = bt_off + kc / 8 * pitch;
+    if (smem <= (uint32_t)kTiledSmemCap || kc <= 128) {
+      if (smem > (uint32_t)kTiledSmemCap) return false;
+      cfg->bpg = bpg;
+      cfg->ngrp = rblk / bpg;
+      cfg->kc = kc;
+      cfg->a_win = a_win;
+      cfg->bt_off = bt_off;
+      cfg->smem = (int)smem;
+      uint32_t cols = 32;
+      while (cols < bpg * cb) cols *= 2;
+      cfg->tmem_cols = cols;
+      return true;
+    }
+    kc /= 2;
+  }
+}
+
+template <int LA, int LB>
+static void tiled_info(const TiledCfg& cfg, KernelInfo* ki) {
+  ki->fn = (const void*)k_toeplitz_tiled<LA, LB>;
+  ki->block = kTiledThreads;
+  ki->smem = cfg.smem;
+  ki->team = kTiledThreads;
+  ki->units_per_cta = 1;
+  ki->tmem_cols = (int)cfg.tmem_cols;
+  ki->tiled = 1;
+}
+
+bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki) {
+  TiledCfg cfg;
+  if (la != lb || !toeplitz_tiled_config(logn, la, lb, &cfg)) return false;
+  switch (la) {
+    case 1: tiled_info<1, 1>(cfg, ki); return true;
+    case 2: tiled_info<2, 2>(cfg, ki); return true;
+    case 3: tiled_info<3, 3>(cfg, ki); return true;
+    case 4: tiled_info<4, 4>(cfg, ki); return true;
+    case 5: tiled_info<5, 5>(cfg, ki); return true;
+    default: return false;
+  }
+}
+
+}  // namespace pm

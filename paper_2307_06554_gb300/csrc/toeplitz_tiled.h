@@ -1,0 +1,44 @@
+// Path (b) at every degree 2^6 .. 2^14: launch arguments and the host-side
+// choice of output groups and K chunks (see toeplitz_tiled.cu).
+#pragma once
+#include <cstdint>
+
+#include "kernels.h"
+#include "polymul_types.h"
+
+namespace pm {
+
+// Tiling of one (product, prime) row: the n/8 rows of A (8 outputs each)
+// in blocks of 128, `bpg` blocks per unit of work (`ngrp` units per row),
+// the summation dimension in chunks of `kc`.  Shared memory per CTA: the
+// digit window of a~ (la x a_win bf16 values) at offset 0 and the chunk of
+// B at `bt_off`.
+struct TiledCfg {
+  uint32_t bpg = 0, ngrp = 0, kc = 0, a_win = 0, bt_off = 0, tmem_cols = 0;
+  int smem = 0;
+};
+
+struct TensorTiledArgs {
+  const uint32_t* a;
+  const uint32_t* b;
+  uint32_t* c;
+  const TensorPrime* tp;  // [k]
+  uint64_t units;         // batch * k * ngrp
+  uint32_t k;
+  uint32_t wrap;          // bf16x2 sign mask of the operand extensions: 0x80008000 (x^n + 1) or 0 (x^n - 1)
+  uint32_t logn, wb;      // degree, digit width
+  uint32_t bpg, ngrp, kc, a_win, bt_off, tmem_cols;
+  unsigned long long* ctr;  // {next unit, finished CTAs}
+  int* err;
+};
+
+// The tiling for degree 2^logn with la digits of a and lb of b (false if
+// the accumulators of one 128-row block do not fit in 256 tensor-memory
+// columns).
+bool toeplitz_tiled_config(int logn, int la, int lb, TiledCfg* cfg);
+
+// k_toeplitz_tiled<LA, LB> for LA = LB = 1 .. 5; ki->smem and
+// ki->tmem_cols from the tiling of degree 2^logn.
+bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki);
+
+}  // namespace pm

@@ -48,7 +48,7 @@ class polymul_plan_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
                  "digit_bits", "digits", "radix_bits", "candidates", "tuned", "tuned_batch",
-                 "launch_flags", "ntt_mode", "regs", "cyclic")] + [("reserved", ctypes.c_uint32 * 1)]
+                 "launch_flags", "ntt_mode", "regs", "cyclic", "tensor_groups")]
 
 
 class polymul_desc(ctypes.Structure):

@@ -51,10 +51,11 @@ def test_aux_moduli(pm, n, q_list):
 
 
 def test_no_route_is_reported(pm):
-    """q = 8192 at n = 256 needs more than one auxiliary prime and has no
-    tensor-path instantiation: creation fails with ENOTSUP, not a fallback."""
+    """q = 8192 (not prime) at n = 2^15 has neither an auxiliary-prime route
+    nor a tensor-path shape (degrees up to 2^14): creation fails with
+    ENOTSUP, not a fallback."""
     with pytest.raises(pm.PolymulError) as ei:
-        pm.Plan(256, [8192])
+        pm.Plan(32768, [8192])
     assert ei.value.code == pm.POLYMUL_ENOTSUP
 
 

@@ -1,0 +1,209 @@
+"""Path (b) at every degree 2^6 .. 2^14 (k_toeplitz_tiled: output groups
+and K chunks, Sec. 2.6) against the CPU oracle: whole products where the
+oracle is quick, sampled coefficients at the largest degrees, every digit
+count 1 .. 5, both rings, extreme operands whose partial sums reach the
+exactness bound, batches that are not a multiple of the grid, the small-ring
+and RNS workloads on the tensor path, and the tiled kernel as the second
+tensor candidate at n = 1024 and 2048."""
+import numpy as np
+import pytest
+
+from oracle import native
+from paper_2307_06554_gb300 import workloads as wl
+
+from helpers import assert_equal_residues, run_plan_batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    from paper_2307_06554_gb300 import polymul
+    return polymul
+
+
+def _tensor_plan(pm, n, q_list, cyclic=False):
+    plan = pm.Plan(n, q_list, path=pm.PATH_TENSOR, flags=pm.FLAG_CYCLIC if cyclic else 0)
+    info = plan.info
+    assert info["path"] == pm.PATH_TENSOR
+    return plan
+
+
+def _digit_width(n):
+    # the widest w with n 2^(2w-2) <= 2^24 and w <= 8
+    logn = n.bit_length() - 1
+    return min(8, (24 - logn) // 2 + 1)
+
+
+def _check_sampled(got, a, b, q_list, cyclic, rng, count=24):
+    n = a.shape[-1]
+    for p in range(a.shape[0]):
+        for jq, q in enumerate(q_list):
+            js = sorted(set([0, 1, 7, 8, n // 2, n - 9, n - 8, n - 1] +
+                            [int(x) for x in rng.integers(0, n, count)]))
+            want = native.coeffs(a[p, jq], b[p, jq], q, js, cyclic=cyclic)
+            assert np.array_equal(got[p, jq, js].astype(np.uint64), want), (p, jq)
+
+
+@pytest.mark.parametrize("n", [64, 128, 256, 512, 4096])
+@pytest.mark.parametrize("bits", [14, 22, 30])
+def test_tiled_against_oracle(pm, n, bits):
+    rng = np.random.default_rng(n * 100 + bits)
+    q_list = [12289] if bits == 14 else wl.draw_primes(rng, 2, bits, bits, 1)
+    batch = {64: 41, 128: 23, 256: 19, 512: 9, 4096: 3}[n]
+    a = wl.uniform_coeffs(rng, batch, q_list, n, np.uint32)
+    b = wl.uniform_coeffs(rng, batch, q_list, n, np.uint32)
+    with _tensor_plan(pm, n, q_list) as plan:
+        info = plan.info
+        assert info["tensor_groups"] >= 1 and info["digit_bits"] == _digit_width(n)
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list), "tiled n=%d bits=%d" % (n, bits))
+
+
+@pytest.mark.parametrize("n,bits", [(8192, 14), (8192, 30), (16384, 14), (16384, 29)])
+def test_tiled_large_degrees_sampled(pm, n, bits):
+    rng = np.random.default_rng(n + bits)
+    q_list = [12289] if bits == 14 else wl.draw_primes(rng, 1, bits, bits, 1)
+    a = wl.uniform_coeffs(rng, 2, q_list, n, np.uint32)
+    b = wl.uniform_coeffs(rng, 2, q_list, n, np.uint32)
+    with _tensor_plan(pm, n, q_list) as plan:
+        assert plan.info["tensor_groups"] > 1  # several output groups per product
+        got = run_plan_batch(plan, a, b)
+    _check_sampled(got, a, b, q_list, False, rng)
+
+
+@pytest.mark.parametrize("n,bits", [(64, 14), (256, 22), (4096, 30), (8192, 20)])
+def test_tiled_cyclic(pm, n, bits):
+    rng = np.random.default_rng(7 * n + bits)
+    q_list = [12289] if bits == 14 else wl.draw_primes(rng, 1, bits, bits, 1)
+    a = wl.uniform_coeffs(rng, 3, q_list, n, np.uint32)
+    b = wl.uniform_coeffs(rng, 3, q_list, n, np.uint32)
+    with _tensor_plan(pm, n, q_list, cyclic=True) as plan:
+        assert plan.info["cyclic"] == 1
+        got = run_plan_batch(plan, a, b)
+    if n <= 4096:
+        assert_equal_residues(got, native.polymul_batch(a, b, q_list, cyclic=True), "tiled cyclic n=%d" % n)
+    else:
+        _check_sampled(got, a, b, q_list, True, rng)
+
+
+@pytest.mark.parametrize("n,q,digits", [(256, 251, 1), (256, 3329, 2), (1024, 1000003, 3), (4096, 65537, 3),
+                                        (2048, 536870909, 5)])
+def test_tiled_digit_counts(pm, n, q, digits):
+    """Every instantiated digit count (1 .. 5)."""
+    rng = np.random.default_rng(q % 1000 + n)
+    a = wl.uniform_coeffs(rng, 5, [q], n, np.uint32)
+    b = wl.uniform_coeffs(rng, 5, [q], n, np.uint32)
+    with pm.Plan(n, [q], path=pm.PATH_TENSOR) as plan:
+        info = plan.info
+        assert info["digits"] == digits, info
+        # n = 1024, 2048 have a whole-product kernel too; use the tiled one
+        if info["tensor_groups"] == 0:
+            idx = [i for i in range(info["candidates"]) if plan.select(i)["tensor_groups"] > 0]
+            assert idx, "no tiled candidate"
+            plan.select(idx[0])
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, [q]), "digits=%d n=%d" % (digits, n))
+
+
+@pytest.mark.parametrize("n", [64, 256, 4096, 8192])
+def test_tiled_exactness_boundary(pm, n):
+    """The low digits of every coefficient at -2^(w-1): each of their
+    digit products is 2^(2w-2), so the output coefficient without wrap-around
+    sums n of them, n 2^(2w-2) = 2^24 at n = 4096 -- the edge of exact fp32
+    integers -- and the other sums mix signs.  Moduli at the top of what
+    five digits cover (31 bits up to 2^12, 30 bits above)."""
+    w = _digit_width(n)
+    q = 2147483629 if n <= 4096 else 1073741789  # primes just below 2^31 and 2^30
+    assert wl.is_prime(q)
+    digits = -(1 << (w - 1))
+    low = 3 if w == 8 else 4  # as many low digits at their minimum as stay inside (-q/2, q/2]
+    x = sum(digits << (w * s) for s in range(low))
+    v = q + x
+    assert 0 < v < q
+    a = np.full((2, 1, n), v, np.uint32)
+    b = np.full((2, 1, n), v, np.uint32)
+    a[1, 0] = q - 1
+    b[1, 0, ::3] = q // 2 + 1  # the most negative centred value
+    with pm.Plan(n, [q], path=pm.PATH_TENSOR) as plan:
+        got = run_plan_batch(plan, a, b)
+    js = sorted(set([0, 1, n // 2, n - 2, n - 1] + list(range(0, n, max(1, n // 64)))))
+    for p in range(2):
+        want = native.coeffs(a[p, 0], b[p, 0], q, js)
+        assert np.array_equal(got[p, 0, js].astype(np.uint64), want), p
+
+
+def test_tiled_ragged_units(pm):
+    """More units than resident CTAs, not a multiple of the grid, with
+    several output groups per product and several primes."""
+    n = 8192
+    rng = np.random.default_rng(81)
+    q_list = wl.draw_primes(rng, 3, 28, 30, 1)
+    a = wl.uniform_coeffs(rng, 131, q_list, n, np.uint32)
+    b = wl.uniform_coeffs(rng, 131, q_list, n, np.uint32)
+    with _tensor_plan(pm, n, q_list) as plan:
+        info = plan.info
+        assert 131 * 3 * info["tensor_groups"] > info["grid"]
+        got = run_plan_batch(plan, a, b)
+        got2 = run_plan_batch(plan, a[:5], b[:5])  # the counters reset between launches
+    rs = np.random.default_rng(82)
+    for p in [0, 1, 64, 129, 130]:
+        js = sorted(int(x) for x in rs.integers(0, n, 16))
+        for jq, q in enumerate(q_list):
+            want = native.coeffs(a[p, jq], b[p, jq], q, js)
+            assert np.array_equal(got[p, jq, js].astype(np.uint64), want), (p, jq)
+    assert np.array_equal(got2, got[:5])
+
+
+def test_ring_small_on_tensor_path(pm):
+    """The n = 256, q = 3329 workload (no 512-th root of unity mod 3329) on
+    the tensor path, whole batch against the oracle."""
+    w = wl.ring_small()
+    with _tensor_plan(pm, w.n, w.q_list) as plan:
+        got = run_plan_batch(plan, w.a, w.b)
+    assert_equal_residues(got, native.polymul_batch(w.a, w.b, w.q_list), "tensor " + w.name)
+
+
+def test_rns_4096_on_tensor_path(pm):
+    """The n = 4096 RNS workload (8 primes of 30 bits, ternary b) on the
+    tensor path: every product's every prime on sampled coefficients, and
+    whole products for a few."""
+    w = wl.rns_4096()
+    with _tensor_plan(pm, w.n, w.q_list) as plan:
+        assert plan.info["digits"] == 5
+        got = run_plan_batch(plan, w.a, w.b)
+    for p in (0, 255):
+        assert_equal_residues(got[p:p + 1], native.polymul_batch(w.a[p:p + 1], w.b[p:p + 1], w.q_list),
+                              "product %d" % p)
+    rng = np.random.default_rng(43)
+    for p in range(0, 256, 17):
+        js = sorted(int(x) for x in rng.integers(0, w.n, 6))
+        for jq, q in enumerate(w.q_list):
+            want = native.coeffs(w.a[p, jq], w.b[p, jq], q, js)
+            assert np.array_equal(got[p, jq, js].astype(np.uint64), want), (p, jq)
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_tiled_candidate_matches_whole_product_kernel(pm, n):
+    rng = np.random.default_rng(n)
+    q_list = [12289, 7681]
+    a = wl.uniform_coeffs(rng, 77, q_list, n, np.uint32)
+    b = wl.uniform_coeffs(rng, 77, q_list, n, np.uint32)
+    with pm.Plan(n, q_list, path=pm.PATH_TENSOR) as plan:
+        info = plan.info
+        assert info["candidates"] == 2 and info["tensor_groups"] == 0
+        whole = run_plan_batch(plan, a, b)
+        assert plan.select(1)["tensor_groups"] == 1
+        tiled = run_plan_batch(plan, a, b)
+    assert np.array_equal(whole, tiled)
+    assert_equal_residues(tiled, native.polymul_batch(a, b, q_list), "tiled n=%d" % n)
+
+
+def test_tensor_path_limits(pm):
+    """Outside the tensor path's shapes creation fails with ENOTSUP when the
+    path is forced: degree above 2^14, moduli of 2^31 and more, and digit
+    counts above five."""
+    for n, q in ((32768, 12289), (1024, 2147483659), (16384, 2147483629)):
+        with pytest.raises(pm.PolymulError) as ei:
+            pm.Plan(n, [q], path=pm.PATH_TENSOR)
+        assert ei.value.code == pm.POLYMUL_ENOTSUP, (n, q)

@@ -46,7 +46,7 @@ def test_every_candidate_is_exact(pm, n, bits, elem):
         labels = []
         for i in range(ncand):
             info = plan.select(i)
-            labels.append((info["path"], info["radix_bits"], info["ntt_mode"], info["regs"]))
+            labels.append((info["path"], info["radix_bits"], info["ntt_mode"], info["regs"], info["tensor_groups"]))
             assert_equal_residues(run_plan_batch(plan, a, b), want, "candidate %d %s" % (i, labels[-1]))
     assert len(set(labels)) == ncand
 
