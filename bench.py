@@ -293,11 +293,14 @@ def _host_link(dev, h2d_bytes, d2h_bytes, reps=10):
             "note": "plain page-locked copies of the step's sizes, measured in this run"}
 
 
-def _tensor_smem_roofline(n, digits, units, seconds, sms, sm_mhz):
+def _tensor_smem_roofline(n, digits, units, seconds, sms, sm_mhz, la=None):
+    """`digits` of the operand on the MMA's B (Toeplitz) side, `la` (default
+    the same) on its A (aliased) side."""
     nb = (8 * digits + 15) // 16 * 16
-    # per (product, prime): digits of a x 128-row blocks (one below n = 1024,
-    # its rows past n/8 discarded) x K steps of 16
-    mmas = digits * max(1, n // 1024) * (n // 16)
+    la = digits if la is None else la
+    # per (product, prime): A-side digits x 128-row blocks (one below
+    # n = 1024, its rows past n/8 discarded) x K steps of 16
+    mmas = la * max(1, n // 1024) * (n // 16)
     byts = units * mmas * (128 * 32 + nb * 32)
     peak = sms * SMEM_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
     ach = byts / seconds / 1e9
@@ -333,8 +336,8 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
     hbm = peaks["hbm_gbs"]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    def homogeneous(name, w, sets_needed, reps, cyclic=False, path=None):
-        flags = (polymul.FLAG_TUNE if path is None else 0) | (polymul.FLAG_CYCLIC if cyclic else 0)
+    def homogeneous(name, w, sets_needed, reps, cyclic=False, path=None, extra_flags=0):
+        flags = (polymul.FLAG_TUNE if path is None else 0) | (polymul.FLAG_CYCLIC if cyclic else 0) | extra_flags
         plan = polymul.Plan(w.n, w.q_list, path=polymul.PATH_AUTO if path is None else path, flags=flags,
                             tune_batch=w.batch)
         k = len(w.q_list)
@@ -364,8 +367,8 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
                                                                      plan.info["candidates"])
         info = plan.info
         if info["path"] == 2:
-            desc = "tensor (%d digits of %d bits, %s)" % (
-                info["digits"], info["digit_bits"],
+            desc = "tensor (%d digits of %d bits%s, %s)" % (
+                info["digits"], info["digit_bits"], "; b ternary, one digit" if extra_flags & polymul.FLAG_TERNARY_B else "",
                 "%d output groups per product" % info["tensor_groups"] if info["tensor_groups"] else "whole product per CTA")
         out[name] = {"products_per_s": w.batch / (ms / 1e3), "us_per_step": ms * 1e3, "batch": w.batch,
                      "n": w.n, "k": k, "path": desc if info["path"] == 2 else path,
@@ -373,10 +376,11 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
                      "bit_exact_sample": None,
                      "l2": "inputs rotated over %d buffer sets" % len(sets) if len(sets) > 1 else "L2-resident"}
         if info["path"] == 2:
-            flops = 2.0 * w.n * w.n * info["digits"] ** 2 * units
+            la, lb = (1, info["digits"]) if extra_flags & polymul.FLAG_TERNARY_B else (info["digits"], info["digits"])
+            flops = 2.0 * w.n * w.n * la * lb * units
             out[name]["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
             out[name]["tensor_frac_smem"] = _tensor_smem_roofline(
-                w.n, info["digits"], units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0))["frac"]
+                w.n, info["digits"], units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=la)["frac"]
         else:
             out[name]["alu_frac"] = mm / (ms / 1e3) / 1e9 / alu_peak_g
         plan.close()
@@ -386,6 +390,9 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
     homogeneous("ring_small_tensor", wl.ring_small(), 1, 200, path=polymul.PATH_TENSOR)
     homogeneous("rns_4096", wl.rns_4096(), 6, 20)
     homogeneous("rns_4096_tensor", wl.rns_4096(), 6, 5, path=polymul.PATH_TENSOR)
+    # its b is ternary: one digit of b, on the MMA's A side
+    homogeneous("rns_4096_tensor_ternary_b", wl.rns_4096(), 6, 10, path=polymul.PATH_TENSOR,
+                extra_flags=polymul.FLAG_TERNARY_B)
     # the cyclic ring x^n - 1 on the headline's shape and data
     homogeneous("ring_1024_cyclic", wl.ring_1024(), 9, 50, cyclic=True)
 

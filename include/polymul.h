@@ -70,6 +70,17 @@ extern "C" {
                                      Z_q[x]/(x^n + 1) (Sec. 2.1 names it as the
                                      other common ring): the NTT path then needs
                                      q = 1 mod n; every path supports it      */
+#define POLYMUL_FLAG_TERNARY_B 8u /* every coefficient of b is 0, 1 or q - 1
+                                     (a ternary polynomial lifted mod q, as the
+                                     secrets and errors of lattice schemes):
+                                     the tensor path splits b into a single
+                                     digit and computes c = b * T(a), one MMA
+                                     chain per block instead of L.  The NTT
+                                     path ignores it.  A tensor-path launch
+                                     that meets a b coefficient whose centred
+                                     value does not fit one digit leaves its
+                                     results invalid and makes
+                                     polymul_plan_status return EDOMAIN     */
 
 typedef struct polymul_opts {
     uint32_t path;        /* POLYMUL_PATH_*                                   */
@@ -181,8 +192,10 @@ int polymul_batch_host(polymul_plan *plan, const void *a, const void *b, void *c
  * of this plan abandoned a bounded device wait (an asynchronous copy that
  * never completed) since the previous call.  Returns POLYMUL_ETIMEOUT in
  * that case (the outputs of the affected launches are invalid) and resets
- * the plan's device-side state so that it can be used again; POLYMUL_OK
- * otherwise.  Kernels never spin without a bound.
+ * the plan's device-side state so that it can be used again; else
+ * POLYMUL_EDOMAIN if a tensor-path launch of a POLYMUL_FLAG_TERNARY_B plan
+ * met a b coefficient that does not fit one digit (its outputs are
+ * invalid); POLYMUL_OK otherwise.  Kernels never spin without a bound.
  */
 int polymul_plan_status(polymul_plan *plan, void *stream);
 

@@ -121,6 +121,10 @@ bool tensor_shape(uint32_t n, uint64_t qmax, int* wb, int* L) {
   return false;
 }
 
+// digits of the operand on the MMA's A side: one for a ternary b (which
+// takes that side), else L
+int tensor_la(const polymul_plan* p) { return p->ternary_b ? 1 : p->digits; }
+
 int upload_tensor_tables(polymul_plan* p) {
   std::vector<TensorPrime> tp(p->k);
   for (uint32_t j = 0; j < p->k; ++j) {
@@ -231,6 +235,7 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
   p->q.assign(q_list, q_list + k);
   p->flags = opts ? opts->flags : 0;
   p->cyclic = (p->flags & POLYMUL_FLAG_CYCLIC) != 0;
+  p->ternary_b = (p->flags & POLYMUL_FLAG_TERNARY_B) != 0;
   uint64_t qmax = *std::max_element(p->q.begin(), p->q.end());
   p->elem = qmax < (1ull << 32) ? 4 : 8;
 
@@ -264,8 +269,8 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
   bool tensor_ok = false, tiled_extra = false;
   KernelInfo tki_tiled;
   if (p->elem == 4 && qmax < (1ull << 31) && tensor_shape(n, qmax, &p->digit_bits, &p->digits)) {
-    const bool tiled = lookup_toeplitz_tiled((int)p->logn, p->digits, p->digits, &tki_tiled);
-    if (lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki)) {
+    const bool tiled = lookup_toeplitz_tiled((int)p->logn, tensor_la(p), p->digits, &tki_tiled);
+    if (!p->ternary_b && lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki)) {
       tensor_ok = true;
       tiled_extra = tiled;
     } else if (tiled) {
@@ -396,7 +401,7 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->tensor_groups = 0;
   if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
     TiledCfg tc;
-    if (toeplitz_tiled_config((int)p->logn, p->digits, p->digits, &tc)) info->tensor_groups = tc.ngrp;
+    if (toeplitz_tiled_config((int)p->logn, tensor_la(p), p->digits, &tc)) info->tensor_groups = tc.ngrp;
   }
   return POLYMUL_OK;
 }
@@ -480,9 +485,12 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
   };
   if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
     TiledCfg tc;
-    if (!toeplitz_tiled_config((int)p->logn, p->digits, p->digits, &tc)) return fail(POLYMUL_ENOTSUP, "tensor tiling");
+    if (!toeplitz_tiled_config((int)p->logn, tensor_la(p), p->digits, &tc)) return fail(POLYMUL_ENOTSUP, "tensor tiling");
     const uint64_t tunits = units * tc.ngrp;
-    TensorTiledArgs args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, (const TensorPrime*)p->d_tpc,
+    // ternary b: c = b * T(a) (the ring is commutative), b's single digit on the A side
+    const void* xa = p->ternary_b ? b : a;
+    const void* xb = p->ternary_b ? a : b;
+    TensorTiledArgs args{(const uint32_t*)xa, (const uint32_t*)xb, (uint32_t*)c, (const TensorPrime*)p->d_tpc,
                          tunits, p->k, p->cyclic ? 0u : 0x80008000u, p->logn, (uint32_t)p->digit_bits,
                          tc.bpg, tc.ngrp, tc.kc, tc.a_win, tc.bt_off, tc.tmem_cols, ctr, p->d_err};
     void* argv[] = {&args};
@@ -536,6 +544,7 @@ extern "C" int polymul_plan_status(polymul_plan* p, void* stream) {
   PM_CUDA(cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (!h) return POLYMUL_OK;
   PM_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+  if (!(h & 1)) return fail(POLYMUL_EDOMAIN, "b has a coefficient outside {0, 1, q - 1} (ternary-b plan); results invalid");
   PM_CUDA(cudaMemset(p->d_ctr, 0, 2 * kCounterSlots * sizeof(unsigned long long)));
   return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }

@@ -29,6 +29,7 @@ struct polymul_plan {
   uint32_t path = 0;   // POLYMUL_PATH_NTT or POLYMUL_PATH_TENSOR
   uint32_t flags = 0;
   bool cyclic = false;  // ring x^n - 1 (POLYMUL_FLAG_CYCLIC) instead of x^n + 1
+  bool ternary_b = false;  // POLYMUL_FLAG_TERNARY_B: b one digit, on the MMA's A side (operands swapped)
   std::vector<uint64_t> q;
   int mode = -1;       // NTT reduction mode (0 = [0,2q), 1 = [0,4q), 2 = unreduced)
   int digit_bits = 0;  // tensor path: digit width w and digits per coefficient L

@@ -57,9 +57,12 @@ struct TTShape {
   static constexpr int CB = LA * NB;  // accumulator columns of one 128-row block
 };
 
-// balanced w-bit digits of the centred representative of v mod q (v < q < 2^31)
+// balanced w-bit digits of the centred representative of v mod q (v < q <
+// 2^31); returns what the L digits leave over (0 whenever L digits cover
+// (-q/2, q/2], as the host chooses L; nonzero only for a single-digit
+// operand that does not fit one digit)
 template <int L>
-__device__ __forceinline__ void centred_digits(uint32_t v, uint32_t q, int wb, int (&d)[L]) {
+__device__ __forceinline__ int32_t centred_digits(uint32_t v, uint32_t q, int wb, int (&d)[L]) {
   const int32_t half = 1 << (wb - 1), mask = (1 << wb) - 1;
   int32_t x = v > (q >> 1) ? (int32_t)(v - q) : (int32_t)v;
 #pragma unroll
@@ -68,22 +71,25 @@ __device__ __forceinline__ void centred_digits(uint32_t v, uint32_t q, int wb, i
     x = (x - t) >> wb;
     d[s] = t;
   }
+  return x;
 }
 
 // 8 consecutive coefficients (16-byte aligned) -> per digit, 8 bf16 packed
-// in a uint4
+// in a uint4; false if a coefficient does not fit the L digits
 template <int L>
-__device__ __forceinline__ void digits8(const uint32_t* src, uint32_t q, int wb, uint4 (&out)[L]) {
+__device__ __forceinline__ bool digits8(const uint32_t* src, uint32_t q, int wb, uint4 (&out)[L]) {
   const uint4 v0 = *reinterpret_cast<const uint4*>(src);
   const uint4 v1 = *reinterpret_cast<const uint4*>(src + 4);
   const uint32_t xv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
   int d[8][L];
+  int32_t rest = 0;
 #pragma unroll
-  for (int e = 0; e < 8; ++e) centred_digits<L>(xv[e], q, wb, d[e]);
+  for (int e = 0; e < 8; ++e) rest |= centred_digits<L>(xv[e], q, wb, d[e]);
 #pragma unroll
   for (int s = 0; s < L; ++s)
     out[s] = make_uint4(bf16x2_of(d[0][s], d[1][s]), bf16x2_of(d[2][s], d[3][s]), bf16x2_of(d[4][s], d[5][s]),
                         bf16x2_of(d[6][s], d[7][s]));
+  return rest == 0;
 }
 
 template <int LA, int LB>
@@ -93,6 +99,7 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t s_tmem;
   __shared__ unsigned long long s_next;
+  __shared__ int s_domain;  // a single-digit A-side coefficient did not fit its digit
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t n = 1u << args.logn, D = n / 8 - 1;
   const uint32_t kc = args.kc, nch = n / kc, bpg = args.bpg, ngrp = args.ngrp, awin = args.a_win;
@@ -107,7 +114,10 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
     tmem_alloc(&s_tmem, args.tmem_cols);
     tmem_relinquish();
   }
-  if (tid == 0) mbar_init(&mbar, 1);
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    s_domain = 0;
+  }
   fence_mbar_init();
   // padded rows of B (digit slots >= LB) stay zero for the whole launch
   if (TS::NG > LB) {
@@ -152,7 +162,8 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
           for (int s = 0; s < LA; ++s) p[s] = make_uint4(0, 0, 0, 0);
         } else {
           flip = i0 < 0 ? wrap : 0u;
-          digits8<LA>(a + (i0 < 0 ? i0 + (int32_t)n : i0), q, wb, p);
+          const bool fits = digits8<LA>(a + (i0 < 0 ? i0 + (int32_t)n : i0), q, wb, p);
+          if (!fits) s_domain = 1;
         }
 #pragma unroll
         for (int s = 0; s < LA; ++s)
@@ -254,6 +265,7 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
   }
   tc_fence_before();
   __syncthreads();
+  if (tid == 0 && s_domain) atomicOr(args.err, 2);  // reported as POLYMUL_EDOMAIN
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, args.tmem_cols);
@@ -310,13 +322,23 @@ static void tiled_info(const TiledCfg& cfg, KernelInfo* ki) {
 
 bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki) {
   TiledCfg cfg;
-  if (la != lb || !toeplitz_tiled_config(logn, la, lb, &cfg)) return false;
-  switch (la) {
-    case 1: tiled_info<1, 1>(cfg, ki); return true;
-    case 2: tiled_info<2, 2>(cfg, ki); return true;
-    case 3: tiled_info<3, 3>(cfg, ki); return true;
-    case 4: tiled_info<4, 4>(cfg, ki); return true;
-    case 5: tiled_info<5, 5>(cfg, ki); return true;
+  if (!toeplitz_tiled_config(logn, la, lb, &cfg)) return false;
+  if (la == lb) {
+    switch (la) {
+      case 1: tiled_info<1, 1>(cfg, ki); return true;
+      case 2: tiled_info<2, 2>(cfg, ki); return true;
+      case 3: tiled_info<3, 3>(cfg, ki); return true;
+      case 4: tiled_info<4, 4>(cfg, ki); return true;
+      case 5: tiled_info<5, 5>(cfg, ki); return true;
+      default: return false;
+    }
+  }
+  if (la != 1) return false;
+  switch (lb) {  // a single-digit operand on the A side (ternary b)
+    case 2: tiled_info<1, 2>(cfg, ki); return true;
+    case 3: tiled_info<1, 3>(cfg, ki); return true;
+    case 4: tiled_info<1, 4>(cfg, ki); return true;
+    case 5: tiled_info<1, 5>(cfg, ki); return true;
     default: return false;
   }
 }

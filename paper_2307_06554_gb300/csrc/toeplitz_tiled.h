@@ -37,8 +37,9 @@ struct TensorTiledArgs {
 // columns).
 bool toeplitz_tiled_config(int logn, int la, int lb, TiledCfg* cfg);
 
-// k_toeplitz_tiled<LA, LB> for LA = LB = 1 .. 5; ki->smem and
-// ki->tmem_cols from the tiling of degree 2^logn.
+// k_toeplitz_tiled<LA, LB> for LA = LB = 1 .. 5 and for LA = 1, LB = 2 .. 5
+// (a single-digit operand on the A side); ki->smem and ki->tmem_cols from
+// the tiling of degree 2^logn.
 bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki);
 
 }  // namespace pm

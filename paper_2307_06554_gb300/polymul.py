@@ -29,6 +29,7 @@ PATH_TENSOR = 2
 FLAG_VALIDATE = 1
 FLAG_TUNE = 2
 FLAG_CYCLIC = 4  # the ring Z_q[x]/(x^n-1) instead of Z_q[x]/(x^n+1)
+FLAG_TERNARY_B = 8  # b in {0, 1, q-1}: the tensor path takes b as one digit (c = b * T(a))
 
 _ERRNAMES = {1: "EINVAL", 2: "ENOTSUP", 3: "EDOMAIN", 4: "ENOMEM", 5: "ETIMEOUT", 6: "ECUDA"}
 

@@ -207,3 +207,93 @@ def test_tensor_path_limits(pm):
         with pytest.raises(pm.PolymulError) as ei:
             pm.Plan(n, [q], path=pm.PATH_TENSOR)
         assert ei.value.code == pm.POLYMUL_ENOTSUP, (n, q)
+
+
+# ---- ternary b (POLYMUL_FLAG_TERNARY_B): b as one digit on the A side ----
+
+@pytest.mark.parametrize("n,bits,cyclic", [(64, 14, False), (1024, 30, False), (2048, 14, True), (4096, 29, False),
+                                           (512, 30, True)])
+def test_ternary_b_against_oracle(pm, n, bits, cyclic):
+    rng = np.random.default_rng(3 * n + bits)
+    q_list = [12289] if bits == 14 else wl.draw_primes(rng, 2, bits, bits, 1)
+    a = wl.uniform_coeffs(rng, 7, q_list, n, np.uint32)
+    b = wl.ternary_coeffs(rng, 7, q_list, n, np.uint32)
+    flags = pm.FLAG_TERNARY_B | (pm.FLAG_CYCLIC if cyclic else 0)
+    with pm.Plan(n, q_list, path=pm.PATH_TENSOR, flags=flags) as plan:
+        info = plan.info
+        assert info["tensor_groups"] >= 1  # the tiled kernel, also at n = 1024 and 2048
+        got = run_plan_batch(plan, a, b)
+        pm.polymul_plan_status(plan.handle)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list, cyclic=cyclic), "ternary n=%d" % n)
+
+
+def test_ternary_b_large_degree_sampled(pm):
+    n = 16384
+    rng = np.random.default_rng(161)
+    q_list = wl.draw_primes(rng, 1, 30, 30, 1)
+    a = wl.uniform_coeffs(rng, 3, q_list, n, np.uint32)
+    b = wl.ternary_coeffs(rng, 3, q_list, n, np.uint32)
+    with pm.Plan(n, q_list, path=pm.PATH_TENSOR, flags=pm.FLAG_TERNARY_B) as plan:
+        got = run_plan_batch(plan, a, b)
+        pm.polymul_plan_status(plan.handle)
+    _check_sampled(got, a, b, q_list, False, rng)
+
+
+def test_rns_4096_ternary_on_tensor_path(pm):
+    """The n = 4096 RNS workload's b is ternary: with the flag the tensor path
+    gives the same results as without it (five digits of b) and as the
+    oracle."""
+    w = wl.rns_4096(batch=24)
+    with _tensor_plan(pm, w.n, w.q_list) as plain:
+        want = run_plan_batch(plain, w.a, w.b)
+    with pm.Plan(w.n, w.q_list, path=pm.PATH_TENSOR, flags=pm.FLAG_TERNARY_B) as plan:
+        got = run_plan_batch(plan, w.a, w.b)
+        pm.polymul_plan_status(plan.handle)
+    assert np.array_equal(got, want)
+    assert_equal_residues(got[:2], native.polymul_batch(w.a[:2], w.b[:2], w.q_list), "ternary rns_4096")
+
+
+def test_ternary_b_one_digit_values(pm):
+    """Any b whose centred coefficients fit one digit is exact under the
+    flag, not only {-1, 0, 1}: here |b| < 2^(w-1) = 128 at n = 1024."""
+    n, q = 1024, 12289
+    rng = np.random.default_rng(5)
+    a = wl.uniform_coeffs(rng, 4, [q], n, np.uint32)
+    bs = rng.integers(-127, 128, size=(4, 1, n))
+    b = np.where(bs < 0, bs + q, bs).astype(np.uint32)
+    with pm.Plan(n, [q], path=pm.PATH_TENSOR, flags=pm.FLAG_TERNARY_B) as plan:
+        got = run_plan_batch(plan, a, b)
+        pm.polymul_plan_status(plan.handle)
+    assert_equal_residues(got, native.polymul_batch(a, b, [q]), "one-digit b")
+
+
+def test_ternary_b_domain_error_is_reported(pm):
+    """A b coefficient that does not fit one digit under the flag: the
+    launch's results are invalid and the status call returns EDOMAIN; the
+    plan then works again."""
+    n, q = 2048, 12289
+    rng = np.random.default_rng(6)
+    a = wl.uniform_coeffs(rng, 3, [q], n, np.uint32)
+    bad = wl.ternary_coeffs(rng, 3, [q], n, np.uint32)
+    bad[1, 0, 77] = 5000
+    good = wl.ternary_coeffs(rng, 3, [q], n, np.uint32)
+    with pm.Plan(n, [q], path=pm.PATH_TENSOR, flags=pm.FLAG_TERNARY_B) as plan:
+        run_plan_batch(plan, a, bad)
+        with pytest.raises(pm.PolymulError) as ei:
+            pm.polymul_plan_status(plan.handle)
+        assert ei.value.code == pm.POLYMUL_EDOMAIN
+        pm.polymul_plan_status(plan.handle)  # cleared
+        got = run_plan_batch(plan, a, good)
+        pm.polymul_plan_status(plan.handle)
+    assert_equal_residues(got, native.polymul_batch(a, good, [q]), "after the domain error")
+
+
+def test_ternary_flag_ignored_by_ntt_path(pm):
+    n, q = 1024, 12289
+    rng = np.random.default_rng(8)
+    a = wl.uniform_coeffs(rng, 5, [q], n, np.uint32)
+    b = wl.uniform_coeffs(rng, 5, [q], n, np.uint32)  # not ternary
+    with pm.Plan(n, [q], path=pm.PATH_NTT, flags=pm.FLAG_TERNARY_B) as plan:
+        got = run_plan_batch(plan, a, b)
+        pm.polymul_plan_status(plan.handle)
+    assert_equal_residues(got, native.polymul_batch(a, b, [q]), "ntt with the flag")
