@@ -366,7 +366,10 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
             path += " (radix %d register passes, autotuned over %d)" % (1 << plan.info["radix_bits"],
                                                                      plan.info["candidates"])
         info = plan.info
-        if info["path"] == 2:
+        if info["path"] == 2 and info["rns_moduli"]:
+            desc = "tensor, residue number system of %d small moduli (%d output groups per product)" % (
+                info["rns_moduli"], info["tensor_groups"])
+        elif info["path"] == 2:
             desc = "tensor (%d digits of %d bits%s, %s)" % (
                 info["digits"], info["digit_bits"], "; b ternary, one digit" if extra_flags & polymul.FLAG_TERNARY_B else "",
                 "%d output groups per product" % info["tensor_groups"] if info["tensor_groups"] else "whole product per CTA")
@@ -375,7 +378,13 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
                      "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm,
                      "bit_exact_sample": None,
                      "l2": "inputs rotated over %d buffer sets" % len(sets) if len(sets) > 1 else "L2-resident"}
-        if info["path"] == 2:
+        if info["path"] == 2 and info["rns_moduli"]:
+            # one chain per small modulus, N = 16 rows of which 8 carry residues
+            flops = 2.0 * w.n * w.n * info["rns_moduli"] * units
+            out[name]["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
+            out[name]["tensor_frac_smem"] = _tensor_smem_roofline(
+                w.n, 1, units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=info["rns_moduli"])["frac"]
+        elif info["path"] == 2:
             la, lb = (1, info["digits"]) if extra_flags & polymul.FLAG_TERNARY_B else (info["digits"], info["digits"])
             flops = 2.0 * w.n * w.n * la * lb * units
             out[name]["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
@@ -393,6 +402,15 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
     # its b is ternary: one digit of b, on the MMA's A side
     homogeneous("rns_4096_tensor_ternary_b", wl.rns_4096(), 6, 10, path=polymul.PATH_TENSOR,
                 extra_flags=polymul.FLAG_TERNARY_B)
+    # 59-bit moduli (the serving workload's prime size) at n = 4096: the NTT
+    # path on 64-bit words beside the tensor path's residue-number-system
+    # kernel (seed 12)
+    rng = np.random.default_rng(12)
+    q59 = wl.draw_primes(rng, 2, 59, 59, 13)
+    w59 = wl.Batch("u64_4096 n=4096 k=2 59-bit batch=128", 4096, q59, wl.uniform_coeffs(rng, 128, q59, 4096),
+                   wl.uniform_coeffs(rng, 128, q59, 4096))
+    homogeneous("u64_4096", w59, 6, 20)
+    homogeneous("u64_4096_tensor_rns", w59, 6, 5, path=polymul.PATH_TENSOR)
     # the cyclic ring x^n - 1 on the headline's shape and data
     homogeneous("ring_1024_cyclic", wl.ring_1024(), 9, 50, cyclic=True)
 

@@ -117,9 +117,11 @@ typedef struct polymul_plan_info {
                              kernel (fewer registers, more resident warps)  */
     uint32_t cyclic;      /* 1: the ring Z_q[x]/(x^n-1); 0: Z_q[x]/(x^n+1) */
     uint32_t tensor_groups;/* tensor path: 0 for the whole-product kernel
-                             (n = 1024, 2048); else the tiled kernel's units
-                             of work per (product, prime): output groups of
-                             up to 1024 coefficients each                   */
+                             (n = 1024, 2048); else the tiled or RNS
+                             kernel's units of work per (product, prime):
+                             output groups of up to 1024 coefficients each  */
+    uint32_t rns_moduli;  /* tensor path, RNS kernel: small moduli in the
+                             base (0 for the digit kernels)                 */
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
@@ -240,6 +242,20 @@ int polymul_batch_static(uint32_t n, uint64_t q, const void *a, const void *b, v
  * Synchronous.  Errors: EINVAL, ENOMEM, ECUDA.
  */
 int polymul_tune(polymul_plan *plan, uint64_t batch, void *stream);
+
+/*
+ * polymul_tensor_rns_base -- the residue number system of small moduli that
+ * the tensor path's RNS kernel uses for degree n and moduli up to qmax
+ * (Sec. 2.4 and the RNS-base selection of the key-parameter section): odd,
+ * pairwise coprime moduli below 2^8, the largest first, each small enough
+ * that n ((m-1)/2)^2 <= 2^24 (every fp32 partial sum of centred residues
+ * exact), until their product exceeds 16 n floor(qmax/2)^2.  Writes up to
+ * `cap` moduli to `moduli` (may be NULL when cap is 0) and their number to
+ * *count.  Host only (no device is touched).  Errors: EINVAL (n not a power
+ * of two in [64, 16384], qmax < 2, count NULL), ENOTSUP (no base of at most
+ * 32 moduli reaches the bound).
+ */
+int polymul_tensor_rns_base(uint32_t n, uint64_t qmax, uint32_t *moduli, uint32_t cap, uint32_t *count);
 
 /* Use candidate kernel `candidate` (0 .. info.candidates - 1; 0 is the
  * default) instead of the tuned or default choice.  Errors: EINVAL. */

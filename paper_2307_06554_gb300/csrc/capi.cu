@@ -21,6 +21,7 @@
 #include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
+#include "toeplitz_rns.h"
 #include "toeplitz_tiled.h"
 
 using namespace pm;
@@ -125,7 +126,22 @@ bool tensor_shape(uint32_t n, uint64_t qmax, int* wb, int* L) {
 // takes that side), else L
 int tensor_la(const polymul_plan* p) { return p->ternary_b ? 1 : p->digits; }
 
+// the small-moduli base of the RNS tensor kernel and its per-prime constants
+int upload_rns_tables(polymul_plan* p, const std::vector<uint32_t>& moduli) {
+  if (p->d_rns_base) return POLYMUL_OK;
+  RnsBase base;
+  std::vector<RnsPrime> per;
+  rns_tables(moduli, p->q, &base, &per);
+  p->rns_r = base.r;
+  PM_CUDA(cudaMalloc(&p->d_rns_base, sizeof base));
+  PM_CUDA(cudaMemcpy(p->d_rns_base, &base, sizeof base, cudaMemcpyHostToDevice));
+  PM_CUDA(cudaMalloc(&p->d_rns_primes, per.size() * sizeof(RnsPrime)));
+  PM_CUDA(cudaMemcpy(p->d_rns_primes, per.data(), per.size() * sizeof(RnsPrime), cudaMemcpyHostToDevice));
+  return POLYMUL_OK;
+}
+
 int upload_tensor_tables(polymul_plan* p) {
+  if (p->elem != 4 || p->d_tpc) return POLYMUL_OK;  // digit kernels only (32-bit words); once
   std::vector<TensorPrime> tp(p->k);
   for (uint32_t j = 0; j < p->k; ++j) {
     memset(&tp[j], 0, sizeof tp[j]);
@@ -268,6 +284,12 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
   // otherwise, and as a second candidate beside the whole-product one
   bool tensor_ok = false, tiled_extra = false;
   KernelInfo tki_tiled;
+  // the residue-number-system kernel (small moduli, Sec. 2.4): any q below
+  // 2^62 in 4- or 8-byte words, where a base of at most 32 moduli exists
+  std::vector<uint32_t> rns_moduli;
+  KernelInfo tki_rns;
+  const bool rns_ok = rns_choose_base(n, qmax, &rns_moduli) &&
+                      lookup_toeplitz_rns((int)p->logn, (uint32_t)rns_moduli.size(), p->elem, &tki_rns);
   if (p->elem == 4 && qmax < (1ull << 31) && tensor_shape(n, qmax, &p->digit_bits, &p->digits)) {
     const bool tiled = lookup_toeplitz_tiled((int)p->logn, tensor_la(p), p->digits, &tki_tiled);
     if (!p->ternary_b && lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki)) {
@@ -277,6 +299,15 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
       p->tki = tki_tiled;
       tensor_ok = true;
     }
+  }
+  // digits where the digit kernels serve, the RNS kernel as another
+  // candidate; the RNS kernel alone elsewhere (64-bit words, more digits)
+  bool rns_extra = false;
+  if (tensor_ok) {
+    rns_extra = rns_ok;
+  } else if (rns_ok) {
+    p->tki = tki_rns;
+    tensor_ok = true;
   }
 
   int rc = POLYMUL_OK;
@@ -303,8 +334,11 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
       rc = fail(POLYMUL_ENOTSUP, "tensor path not available for n=%u and these moduli", n);
     } else {
       rc = upload_tensor_tables(p);
+      if (rc == POLYMUL_OK && p->tki.rns) rc = upload_rns_tables(p, rns_moduli);
       if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
       if (rc == POLYMUL_OK && tiled_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_tiled);
+      if (rc == POLYMUL_OK && rns_extra) rc = upload_rns_tables(p, rns_moduli);
+      if (rc == POLYMUL_OK && rns_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_rns);
     }
   } else if (!ntt_ok) {
     rc = fail(POLYMUL_ENOTSUP, "no NTT route for these moduli at n=%u (need prime q = 1 mod %s, q < 2^31 for 32-bit words)",
@@ -323,8 +357,11 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     if (rc == POLYMUL_OK && p->elem == 8 && lookup_ntt_u64_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) {
       rc = upload_tensor_tables(p);
+      if (rc == POLYMUL_OK && p->tki.rns) rc = upload_rns_tables(p, rns_moduli);
       if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
       if (rc == POLYMUL_OK && tiled_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_tiled);
+      if (rc == POLYMUL_OK && rns_extra) rc = upload_rns_tables(p, rns_moduli);
+      if (rc == POLYMUL_OK && rns_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_rns);
     }
   }
   if (rc == POLYMUL_OK) apply_candidate(p, 0);
@@ -361,6 +398,9 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_twi);
   cudaFree(p->d_pc);
   cudaFree(p->d_tpc);
+  cudaFree(p->d_rns_base);
+  cudaFree(p->d_rns_primes);
+  for (int s = 0; s < kCounterSlots; ++s) cudaFree(p->d_rns_scr[s]);
   cudaFree(p->d_sh);
   cudaFree(p->d_flag);
   cudaFree(p->d_ctr);
@@ -399,10 +439,27 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->regs = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.regs : 0u;
   info->cyclic = p->cyclic ? 1u : 0u;
   info->tensor_groups = 0;
+  info->rns_moduli = p->path == POLYMUL_PATH_TENSOR && p->ki.rns ? p->rns_r : 0;
+  if (p->path == POLYMUL_PATH_TENSOR && p->ki.rns) {
+    RnsCfg rc;
+    if (rns_config((int)p->logn, p->rns_r, &rc)) info->tensor_groups = rc.ngrp;
+  }
   if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
     TiledCfg tc;
     if (toeplitz_tiled_config((int)p->logn, tensor_la(p), p->digits, &tc)) info->tensor_groups = tc.ngrp;
   }
+  return POLYMUL_OK;
+}
+
+extern "C" int polymul_tensor_rns_base(uint32_t n, uint64_t qmax, uint32_t* moduli, uint32_t cap, uint32_t* count) {
+  clear_error();
+  if (!count) return fail(POLYMUL_EINVAL, "count is NULL");
+  if (n < 64 || n > 16384 || (n & (n - 1))) return fail(POLYMUL_EINVAL, "n=%u must be a power of two in [64, 16384]", n);
+  if (qmax < 2) return fail(POLYMUL_EINVAL, "qmax must be at least 2");
+  std::vector<uint32_t> m;
+  if (!rns_choose_base(n, qmax, &m)) return fail(POLYMUL_ENOTSUP, "no base of at most %d moduli for n=%u", kRnsMax, n);
+  *count = (uint32_t)m.size();
+  for (uint32_t i = 0; i < cap && i < m.size(); ++i) moduli[i] = m[i];
   return POLYMUL_OK;
 }
 
@@ -483,7 +540,29 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     }
     return POLYMUL_OK;
   };
-  if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
+  if (p->path == POLYMUL_PATH_TENSOR && p->ki.rns) {
+    RnsCfg rc;
+    if (!rns_config((int)p->logn, p->rns_r, &rc)) return fail(POLYMUL_ENOTSUP, "tensor RNS tiling");
+    // residue planes of a and b (slot-private scratch), then the MMA kernel
+    const size_t plane = (size_t)units * p->rns_r * p->n;
+    if (p->rns_scr_bytes[slot] < 2 * plane) {
+      if (p->d_rns_scr[slot]) PM_CUDA(cudaFree(p->d_rns_scr[slot]));
+      p->d_rns_scr[slot] = nullptr;
+      p->rns_scr_bytes[slot] = 0;
+      if (cudaMalloc(&p->d_rns_scr[slot], 2 * plane) != cudaSuccess) return fail(POLYMUL_ENOMEM, "residue planes");
+      p->rns_scr_bytes[slot] = 2 * plane;
+    }
+    int8_t* planes = static_cast<int8_t*>(p->d_rns_scr[slot]);
+    PM_CUDA((cudaError_t)rns_prep_launch(p->elem, a, b, planes, units, p->n, p->k, (const RnsBase*)p->d_rns_base,
+                                         (const RnsPrime*)p->d_rns_primes, p->rns_r, p->num_sms, st));
+    const uint64_t tunits = units * rc.ngrp;
+    TensorRnsArgs args{planes, planes + plane, c, (const RnsBase*)p->d_rns_base, (const RnsPrime*)p->d_rns_primes, tunits, p->k,
+                       p->cyclic ? 0u : 0x80008000u, p->logn, rc.bpg, rc.ngrp, rc.kc, rc.a_win, rc.bt_off,
+                       rc.buf_bytes, rc.tmem_cols, ctr, p->d_err};
+    void* argv[] = {&args};
+    const int tgrid = (int)std::min<uint64_t>(tunits, (uint64_t)p->grid_cap);
+    PM_CUDA(cudaLaunchKernel(p->ki.fn, tgrid, p->ki.block, argv, p->ki.smem, st));
+  } else if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
     TiledCfg tc;
     if (!toeplitz_tiled_config((int)p->logn, tensor_la(p), p->digits, &tc)) return fail(POLYMUL_ENOTSUP, "tensor tiling");
     const uint64_t tunits = units * tc.ngrp;

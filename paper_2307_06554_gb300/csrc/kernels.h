@@ -17,6 +17,7 @@ struct KernelInfo {
   int mode = 0;              // NTT: reduction mode (0..2, see ntt.cuh)
   int regs = 0;              // NTT: register budget per thread
   int tiled = 0;             // tensor path: 1 for k_toeplitz_tiled (output groups, K chunks)
+  int rns = 0;               // tensor path: 1 for k_toeplitz_rns (residues of small moduli)
 };
 
 // batched negacyclic NTT, k_ntt_batch<W, LOGN, MODE> (MODE: 0 = kQ31,

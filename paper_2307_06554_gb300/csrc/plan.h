@@ -46,6 +46,15 @@ struct polymul_plan {
   bool tuned = false;
   uint64_t tuned_batch = 0;  // batch bucket of the tuned choice
   void* d_tpc = nullptr;  // tensor-path constants
+  // tensor path, residue number system of small moduli: the base and its
+  // per-prime constants (when the RNS kernel is a candidate)
+  uint32_t rns_r = 0;
+  void* d_rns_base = nullptr;
+  void* d_rns_primes = nullptr;
+  // residue planes of a and b, one buffer per launch slot (the host-buffer
+  // entry's streams run concurrently), grown on demand
+  void* d_rns_scr[kCounterSlots] = {};
+  size_t rns_scr_bytes[kCounterSlots] = {};
   uint64_t* d_q = nullptr;  // moduli on the device (input validation)
   // auxiliary-prime NTT (moduli without a 2n-th root of unity)
   uint64_t aux_prime = 0, aux_candidate = 0;

@@ -59,7 +59,7 @@ void store_cache(const std::string& key, const std::string& label) {
 }
 
 std::string label_of(const PlanCandidate& c) {
-  if (c.path == POLYMUL_PATH_TENSOR) return c.ki.tiled ? "tensor-tiled" : "tensor";
+  if (c.path == POLYMUL_PATH_TENSOR) return c.ki.rns ? "tensor-rns" : c.ki.tiled ? "tensor-tiled" : "tensor";
   return "ntt-rb" + std::to_string(c.ki.rb) + (c.ki.cluster ? "-cluster" : "");
 }
 

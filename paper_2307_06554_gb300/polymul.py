@@ -49,7 +49,7 @@ class polymul_plan_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
                  "digit_bits", "digits", "radix_bits", "candidates", "tuned", "tuned_batch",
-                 "launch_flags", "ntt_mode", "regs", "cyclic", "tensor_groups")]
+                 "launch_flags", "ntt_mode", "regs", "cyclic", "tensor_groups", "rns_moduli")]
 
 
 class polymul_desc(ctypes.Structure):
@@ -89,6 +89,8 @@ def _load():
     lib.polymul_batch_shared.restype = i32
     lib.polymul_selftest_wait.argtypes = [ctypes.c_uint32, vp]
     lib.polymul_selftest_wait.restype = i32
+    lib.polymul_tensor_rns_base.argtypes = [u32, u64, ctypes.POINTER(u32), u32, ctypes.POINTER(u32)]
+    lib.polymul_tensor_rns_base.restype = i32
     lib.polymul_batch_static.argtypes = [u32, u64, vp, vp, vp, u64, vp]
     lib.polymul_batch_static.restype = i32
     lib.polymul_plan_select.argtypes = [vp, u32]
@@ -195,6 +197,16 @@ def polymul_selftest_wait(polls: int, stream=None) -> None:
     """Device check that a bounded wait gives up: raises PolymulError with
     POLYMUL_ETIMEOUT when it does (the expected outcome)."""
     _check(_lib.polymul_selftest_wait(polls, _stream(stream)))
+
+
+def polymul_tensor_rns_base(n: int, qmax: int) -> list:
+    """The small moduli of the tensor path's residue-number-system kernel
+    for degree n and moduli up to qmax (host only)."""
+    count = ctypes.c_uint32(0)
+    _check(_lib.polymul_tensor_rns_base(n, qmax, None, 0, ctypes.byref(count)))
+    out = (ctypes.c_uint32 * max(1, count.value))()
+    _check(_lib.polymul_tensor_rns_base(n, qmax, out, count.value, ctypes.byref(count)))
+    return [int(x) for x in out[:count.value]]
 
 
 def polymul_batch_shared(plan: int, a, b, c, batch: int, stream=None) -> None:

@@ -12,6 +12,8 @@ cases:
   tensor_ring1024  the same batch through the Toeplitz tensor-core path
   tensor_rns4096   n = 4096, 8 primes of 30 bits, 64 products on the tiled
                    tensor kernel (5 digits, 4 output groups per product)
+  tensor_u64_4096  n = 4096, 2 primes of 59 bits, 64 products on the tensor
+                   path's residue-number-system kernel (21 small moduli)
   n16384           n = 16384, one 30-bit prime, 1024 products (one CTA per product)
   cluster_32768    n = 32768, one 30-bit prime, 256 products (thread-block clusters)
   u64_4096         n = 4096, one 59-bit prime, 1024 products (64-bit words)
@@ -101,8 +103,8 @@ def _shared(n, q, batch, launches, seed=7, path=polymul.PATH_TENSOR):
 
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    p.add_argument("case", choices=["ntt_ring1024", "tensor_ring1024", "tensor_rns4096", "n16384", "cluster_32768",
-                                    "u64_4096", "ragged_300", "shared_ring1024", "shared_ntt1024"])
+    p.add_argument("case", choices=["ntt_ring1024", "tensor_ring1024", "tensor_rns4096", "tensor_u64_4096", "n16384",
+                                    "cluster_32768", "u64_4096", "ragged_300", "shared_ring1024", "shared_ntt1024"])
     p.add_argument("--launches", type=int, default=4)
     args = p.parse_args(argv)
     rng = np.random.default_rng(8)
@@ -112,6 +114,8 @@ def main(argv=None):
         res = _homogeneous(1024, [12289], 4096, polymul.PATH_TENSOR, args.launches)
     elif args.case == "tensor_rns4096":
         res = _homogeneous(4096, wl.draw_primes(rng, 8, 30, 30, 13), 64, polymul.PATH_TENSOR, args.launches)
+    elif args.case == "tensor_u64_4096":
+        res = _homogeneous(4096, wl.draw_primes(rng, 2, 59, 59, 13), 64, polymul.PATH_TENSOR, args.launches)
     elif args.case == "n16384":
         res = _homogeneous(16384, wl.draw_primes(rng, 1, 30, 30, 15), 1024, polymul.PATH_NTT, args.launches)
     elif args.case == "cluster_32768":

@@ -144,8 +144,12 @@ def test_cyclic_and_negacyclic_plans_differ(pm):
 
 
 def test_cyclic_unsupported_moduli(pm):
-    """64-bit moduli without an n-th root of unity have no route."""
-    q = (1 << 61) - 1  # prime, q - 1 = 2 * odd: no root of order 1024
+    """64-bit moduli without an n-th root of unity have no NTT route; above
+    the tensor path's degrees (2^14) there is no route at all."""
+    q = (1 << 61) - 1  # prime, q - 1 = 2 * odd: no root of order 2^15
     with pytest.raises(pm.PolymulError) as ei:
-        pm.Plan(1024, [q], flags=pm.FLAG_CYCLIC)
+        pm.Plan(32768, [q], flags=pm.FLAG_CYCLIC)
+    assert ei.value.code == pm.POLYMUL_ENOTSUP
+    with pytest.raises(pm.PolymulError) as ei:
+        pm.Plan(1024, [q], path=pm.PATH_NTT, flags=pm.FLAG_CYCLIC)
     assert ei.value.code == pm.POLYMUL_ENOTSUP

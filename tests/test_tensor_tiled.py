@@ -191,9 +191,9 @@ def test_tiled_candidate_matches_whole_product_kernel(pm, n):
     b = wl.uniform_coeffs(rng, 77, q_list, n, np.uint32)
     with pm.Plan(n, q_list, path=pm.PATH_TENSOR) as plan:
         info = plan.info
-        assert info["candidates"] == 2 and info["tensor_groups"] == 0
+        assert info["candidates"] == 3 and info["tensor_groups"] == 0  # whole product, tiled, RNS
         whole = run_plan_batch(plan, a, b)
-        assert plan.select(1)["tensor_groups"] == 1
+        assert plan.select(1)["tensor_groups"] == 1 and plan.info["rns_moduli"] == 0
         tiled = run_plan_batch(plan, a, b)
     assert np.array_equal(whole, tiled)
     assert_equal_residues(tiled, native.polymul_batch(a, b, q_list), "tiled n=%d" % n)
@@ -201,12 +201,31 @@ def test_tiled_candidate_matches_whole_product_kernel(pm, n):
 
 def test_tensor_path_limits(pm):
     """Outside the tensor path's shapes creation fails with ENOTSUP when the
-    path is forced: degree above 2^14, moduli of 2^31 and more, and digit
-    counts above five."""
-    for n, q in ((32768, 12289), (1024, 2147483659), (16384, 2147483629)):
+    path is forced: degree above 2^14; a 31-bit modulus at 2^14 (six digits
+    of 6 bits, and no base of small moduli reaches its range); a 59-bit
+    modulus at 2^13 (64-bit words have only the RNS kernel, whose moduli
+    there stay below 92)."""
+    for n, q in ((32768, 12289), (16384, 2147483629), (8192, (1 << 59) - 55)):
         with pytest.raises(pm.PolymulError) as ei:
             pm.Plan(n, [q], path=pm.PATH_TENSOR)
         assert ei.value.code == pm.POLYMUL_ENOTSUP, (n, q)
+
+
+def test_rns_takes_32_bit_moduli_above_2_31(pm):
+    """A 32-bit modulus at or above 2^31 has no digit kernel (signed 32-bit
+    centring) and no NTT route (32-bit words hold moduli below 2^31); the
+    residue-number-system kernel serves it."""
+    q = 2147483659  # prime, between 2^31 and 2^32
+    assert wl.is_prime(q)
+    n = 1024
+    rng = np.random.default_rng(31)
+    a = wl.uniform_coeffs(rng, 4, [q], n, np.uint32)
+    b = wl.uniform_coeffs(rng, 4, [q], n, np.uint32)
+    with pm.Plan(n, [q]) as plan:
+        info = plan.info
+        assert info["path"] == pm.PATH_TENSOR and info["rns_moduli"] > 0 and plan.elem_bytes == 4
+        got = run_plan_batch(plan, a, b)
+    assert_equal_residues(got, native.polymul_batch(a, b, [q]), "q > 2^31 on the RNS kernel")
 
 
 # ---- ternary b (POLYMUL_FLAG_TERNARY_B): b as one digit on the A side ----

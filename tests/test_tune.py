@@ -46,7 +46,8 @@ def test_every_candidate_is_exact(pm, n, bits, elem):
         labels = []
         for i in range(ncand):
             info = plan.select(i)
-            labels.append((info["path"], info["radix_bits"], info["ntt_mode"], info["regs"], info["tensor_groups"]))
+            labels.append((info["path"], info["radix_bits"], info["ntt_mode"], info["regs"], info["tensor_groups"],
+                           info["rns_moduli"]))
             assert_equal_residues(run_plan_batch(plan, a, b), want, "candidate %d %s" % (i, labels[-1]))
     assert len(set(labels)) == ncand
 
