@@ -557,8 +557,8 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
                                          (const RnsPrime*)p->d_rns_primes, p->rns_r, p->num_sms, st));
     const uint64_t tunits = units * rc.ngrp;
     TensorRnsArgs args{planes, planes + plane, c, (const RnsBase*)p->d_rns_base, (const RnsPrime*)p->d_rns_primes, tunits, p->k,
-                       p->cyclic ? 0u : 0x80008000u, p->logn, rc.bpg, rc.ngrp, rc.kc, rc.a_win, rc.bt_off,
-                       rc.buf_bytes, rc.tmem_cols, ctr, p->d_err};
+                       p->cyclic ? 0u : 0x80008000u, p->logn, rc.shifts, rc.nb, rc.b_pitch, rc.ngrp, rc.kc, rc.a_win,
+                       rc.bt_off, rc.buf_bytes, rc.tmem_cols, ctr, p->d_err};
     void* argv[] = {&args};
     const int tgrid = (int)std::min<uint64_t>(tunits, (uint64_t)p->grid_cap);
     PM_CUDA(cudaLaunchKernel(p->ki.fn, tgrid, p->ki.block, argv, p->ki.smem, st));

@@ -53,9 +53,9 @@ namespace {
 constexpr int kRnsGroup = 128;                        // threads of one builder group (4 warps)
 constexpr int kRnsGroups = 2;                         // builder groups, taking alternate steps
 constexpr int kRnsBuilders = kRnsGroup * kRnsGroups;  // warps 0-7: operand builds; warps 0-3 the epilogue
-constexpr int kRnsThreads = kRnsBuilders + 32;        // + warp 8: MMA issue
+constexpr int kRnsIssuers = 2;                        // MMA-issuing warps (alternate moduli)
+constexpr int kRnsThreads = kRnsBuilders + 32 * kRnsIssuers;  // + warps 8, 9: MMA issue
 constexpr int kRnsStages = 2 * kRnsGroups;            // shared-memory stages in the ring
-constexpr int kRnsPitch = 2 * 128 + 16;  // K-block pitch of B: one group of residues + one of padding (+16: banks)
 constexpr int kRnsSmemCap = 200 * 1024;  // all stages
 }  // namespace
 
@@ -142,11 +142,14 @@ __device__ __forceinline__ void mbar_arrive_plain(uint64_t* bar) {
 // Two groups of four warps build the operands of alternate steps (one
 // modulus over one K chunk each) into a ring of kRnsStages shared-memory
 // stages, so that two steps' residue loads are in flight at once; warps 0-3
-// also run the epilogue; warp 8 issues the MMA chains.  full[s] (one
-// group's 128 arrivals) hands a built stage to the issuer, empty[s]
-// (tcgen05.commit) hands it back once its chains have read it.  Every wait
-// is bounded; after the first expired wait the CTA stops waiting, finishes
-// the unit (results invalid) and reports it.
+// also run the epilogue.  Warps 8 and 9 issue the MMA chains, one thread
+// each, for the moduli of even and of odd index (one thread issuing alone
+// measured about 100 cycles per small MMA); each accumulator is written by
+// one issuer only, so its chains stay in order.  full[s] (one group's 128
+// arrivals) hands a built stage to its issuer, empty[s] (tcgen05.commit)
+// hands it back once its chains have read it.  Every wait is bounded; after
+// the first expired wait the CTA stops waiting, finishes the unit (results
+// invalid) and reports it.
 template <typename W>
 __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs args) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -159,11 +162,12 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
   const bool builder = tid < kRnsBuilders;
   const uint32_t grp_id = (uint32_t)tid / kRnsGroup, gt = (uint32_t)tid % kRnsGroup;  // builder group, thread in it
   const uint32_t n = 1u << args.logn, D = n / 8 - 1;
-  const uint32_t kc = args.kc, nch = n / kc, bpg = args.bpg, ngrp = args.ngrp, awin = args.a_win;
+  const uint32_t kc = args.kc, nch = n / kc, S = args.shifts, ngrp = args.ngrp, awin = args.a_win;
+  const uint32_t NB = args.nb, pitch = args.b_pitch;
   const uint32_t wrap = args.wrap;
   const uint64_t units = args.units;
   W* C = static_cast<W*>(args.c);
-  constexpr uint32_t IDESC = idesc_bf16(128, 16);
+  const uint32_t IDESC = idesc_bf16(128, (int)NB);
 
   for (uint32_t i = tid; i < sizeof(RnsBase) / 4; i += kRnsThreads)
     reinterpret_cast<uint32_t*>(&s_base)[i] = reinterpret_cast<const uint32_t*>(args.base)[i];
@@ -179,11 +183,14 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
     s_fail = 0;
   }
   fence_mbar_init();
-  // the padding group of B (rows 8..15) stays zero for the whole launch
-  for (uint32_t ch = tid; ch < kRnsStages * (kc / 8) * 8; ch += kRnsThreads) {
-    const uint32_t st = ch / ((kc / 8) * 8), dp = (ch / 8) % (kc / 8), v = ch % 8;
-    *reinterpret_cast<uint4*>(sm + st * args.buf_bytes + args.bt_off + dp * kRnsPitch + 128 + 16 * v) =
-        make_uint4(0, 0, 0, 0);
+  // padding rows of B (8-row groups past the S shifted copies: only when
+  // S = 1) stay zero for the whole launch
+  if (NB / 8 > S) {
+    for (uint32_t ch = tid; ch < kRnsStages * (kc / 8) * 8; ch += kRnsThreads) {
+      const uint32_t st = ch / ((kc / 8) * 8), dp = (ch / 8) % (kc / 8), v = ch % 8;
+      *reinterpret_cast<uint4*>(sm + st * args.buf_bytes + args.bt_off + dp * pitch + 128 * S + 16 * v) =
+          make_uint4(0, 0, 0, 0);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
     const uint32_t grp = (uint32_t)(cur % ngrp);
     const uint32_t j = (uint32_t)(row % args.k);
     const RnsPrime* tp = args.tp + j;
-    const uint32_t b0 = grp * bpg;
+    const uint32_t b0 = grp * S;  // the unit's first 1024-output block
 
     if (builder) {
       for (uint32_t st = grp_id; st < nsteps; st += kRnsGroups) {
@@ -233,55 +240,65 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
           }
           *reinterpret_cast<uint4*>(Xw + 8 * gi) = p;
         }
-        // the chunk's K-blocks of B: K-block d' is b's group g = D - d' after
-        // group g - 1 (group -1: the last group, negated for x^n + 1)
+        // the chunk's K-blocks of B, one 8-row group per shift s: K-block d'
+        // of shift s is b~'s group G = D - d' + 128 s after group G - 1, with
+        // b~ the extension of b over [-n, 2n) (groups outside [0, n/8) are
+        // b's groups n/8 away, negated for x^n + 1); shift s gives the
+        // outputs 1024 s further on from the same A
+        const uint32_t ng = n / 8;
         for (uint32_t dl = gt; dl < kc / 8; dl += kRnsGroup) {
-          const uint32_t g = D - (kc / 8 * ch + dl);
-          const uint32_t gp = g == 0 ? n / 8 - 1 : g - 1;
-          const uint32_t pflip = g == 0 ? wrap : 0u;
-          const uint4 pv = bf16x8_of_i8(pb + 8 * gp);
-          const uint4 ow = bf16x8_of_i8(pb + 8 * g);
-          const uint32_t E[8] = {pv.x ^ pflip, pv.y ^ pflip, pv.z ^ pflip, pv.w ^ pflip, ow.x, ow.y, ow.z, ow.w};
-          b_block_rows(E, Bt + dl * kRnsPitch);
+          const int32_t g0 = (int32_t)(D - (kc / 8 * ch + dl));
+          for (uint32_t sh = 0; sh < S; ++sh) {
+            const int32_t G = g0 + 128 * (int32_t)sh, H = G - 1;
+            const uint32_t gg = (uint32_t)(G >= (int32_t)ng ? G - (int32_t)ng : G);
+            const uint32_t hh = (uint32_t)(H < 0 ? H + (int32_t)ng : H >= (int32_t)ng ? H - (int32_t)ng : H);
+            const uint32_t fg = G >= (int32_t)ng ? wrap : 0u;
+            const uint32_t fh = (H < 0 || H >= (int32_t)ng) ? wrap : 0u;
+            const uint4 pv = bf16x8_of_i8(pb + 8 * hh);
+            const uint4 ow = bf16x8_of_i8(pb + 8 * gg);
+            const uint32_t E[8] = {pv.x ^ fh, pv.y ^ fh, pv.z ^ fh, pv.w ^ fh, ow.x ^ fg, ow.y ^ fg, ow.z ^ fg, ow.w ^ fg};
+            b_block_rows(E, Bt + dl * pitch + 128 * sh);
+          }
         }
         fence_proxy_async();  // this thread's stores, visible to the tensor cores
         mbar_arrive_plain(&full[x]);
       }
     } else if (lane == 0) {
-      // ---- TPUMul: the chains of each step, as its stage fills ----
+      // ---- TPUMul: this issuer's steps (moduli of its parity), as their
+      // stages fill ----
+      const uint32_t e = (uint32_t)warp - kRnsBuilders / 32;
+      const uint64_t BSTEP = (2 * pitch) >> 4;
       for (uint32_t st = 0; st < nsteps; ++st) {
-        const uint32_t gs = step + st, x = gs % kRnsStages, ch = st / r, i = st % r;
+        const uint32_t i = st % r;
+        if ((i & 1u) != e) continue;
+        const uint32_t gs = step + st, x = gs % kRnsStages, ch = st / r;
         wait(&full[x], (gs / kRnsStages) & 1u);
         tc_fence_after();
-        const uint32_t xa0 = smem_u32(sm + x * args.buf_bytes), bt0 = xa0 + args.bt_off;
-        const uint64_t bd0 = smem_desc(bt0, kRnsPitch, 128);
-        constexpr uint64_t BSTEP = (2 * kRnsPitch) >> 4;
-#pragma unroll 1
-        for (uint32_t bl = 0; bl < bpg; ++bl) {
-          const uint32_t dcol = tmem + (bl * r + i) * 16;
-          const uint64_t ad0 = smem_desc(xa0 + 1024 * bl * 2, 16, 128);
+        const uint32_t xa0 = smem_u32(sm + x * args.buf_bytes);
+        const uint64_t ad0 = smem_desc(xa0, 16, 128), bd0 = smem_desc(xa0 + args.bt_off, pitch, 128);
+        const uint32_t dcol = tmem + i * NB;
 #pragma unroll 4
-          for (uint32_t kk = 0; kk < kc / 16; ++kk)
-            tc_mma_f16(dcol, ad0 + 2u * (uint64_t)kk, bd0 + BSTEP * (uint64_t)kk, IDESC, (ch > 0 || kk > 0) ? 1u : 0u);
-        }
+        for (uint32_t kk = 0; kk < kc / 16; ++kk)
+          tc_mma_f16(dcol, ad0 + 2u * (uint64_t)kk, bd0 + BSTEP * (uint64_t)kk, IDESC, (ch > 0 || kk > 0) ? 1u : 0u);
         tc_commit(&empty[x]);
       }
     }
-    if (warp == kRnsBuilders / 32) __syncwarp();
+    if (warp >= kRnsBuilders / 32) __syncwarp();
     step += nsteps;
 
     // ---- ConvertMatrix: the CRT per output, reduced mod q (warps 0-3) ----
     if (tid < kRnsGroup) {
-      // every chain of the unit has completed: the last kRnsStages commits,
-      // in issue order (commits complete in order, so each awaited phase is
-      // at most one ahead of its barrier and the parity test cannot alias)
+      // every chain of the unit has completed: the last kRnsStages steps'
+      // commits, one per stage (each stage's previous commit was awaited
+      // before the stage was refilled, so each awaited phase is at most one
+      // ahead of its barrier and the parity test cannot alias)
       for (uint32_t gs = step > (uint32_t)kRnsStages ? step - kRnsStages : 0; gs < step; ++gs)
         wait(&empty[gs % kRnsStages], (gs / kRnsStages) & 1u);
       tc_fence_after();
       const uint64_t q = tp->q;
       W* c = C + row * n;
 #pragma unroll 1
-      for (uint32_t bl = 0; bl < bpg; ++bl) {
+      for (uint32_t sh = 0; sh < S; ++sh) {
         uint64_t slo[8], shi[8];
         float f[8];
 #pragma unroll
@@ -294,15 +311,18 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
         for (uint32_t i = 0; i < r; ++i) {
           uint32_t acc[16];
           // warp-collective: every lane loads, only the stores below are predicated
-          tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (bl * r + i) * 16, acc);
+          // columns i N + 8 sh .. + 7: the 16-column load that holds them
+          tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + i * NB + 16 * (sh / 2), acc);
           tmem_wait_ld();
+          const uint32_t o8 = 8 * (sh & 1u);
           const uint32_t m = s_base.m[i], mu32 = s_base.mu32[i], t = s_base.t[i], off = s_base.off[i];
           const float im = s_base.inv_m[i];
           const uint64_t Mq = tp->Mq[i];
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
             // x mod m from the exact integer accumulator (|value| <= 2^24)
-            uint32_t u = (uint32_t)(__float2int_rn(__uint_as_float(acc[v])) + (int)off);
+            const uint32_t bits = o8 ? acc[8 + v] : acc[v];
+            uint32_t u = (uint32_t)(__float2int_rn(__uint_as_float(bits)) + (int)off);
             u -= __umulhi(u, mu32) * m;
             if (u >= m) u -= m;
             uint32_t y = u * t;  // < 2^16
@@ -314,7 +334,7 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
             f[v] = fmaf((float)y, im, f[v]);
           }
         }
-        const uint32_t j0 = 8 * (128 * (b0 + bl) + (uint32_t)tid);
+        const uint32_t j0 = 8 * (128 * (b0 + sh) + (uint32_t)tid);
         W out[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
@@ -438,24 +458,31 @@ bool rns_config(int logn, uint32_t r, RnsCfg* cfg) {
   if (logn < 6 || logn > 14 || r < 1 || r > (uint32_t)kRnsMax) return false;
   const uint32_t n = 1u << logn;
   const uint32_t rblk = n >= 1024 ? n / 1024 : 1;
-  uint32_t bpg = 1;
-  while (bpg * 2 <= rblk && bpg * 2 * r * 16 <= 512) bpg *= 2;
+  // shifted copies of b per chain: as many blocks as the accumulators of r
+  // chains of N = 8 S columns allow
+  uint32_t S = 1;
+  while (S * 2 <= rblk && r * 8 * (S * 2) <= 512) S *= 2;
+  const uint32_t nb = S * 8 < 16 ? 16 : S * 8;
+  const uint32_t pitch = nb / 8 * 128 + 16;
+  if (r * nb > 512) return false;
   uint32_t kc = n < 1024 ? n : 1024;
   for (;;) {
-    const uint32_t a_win = 1024 * bpg + kc;
+    const uint32_t a_win = 1024 + kc;  // one A slice (the unit's first block)
     const uint32_t bt_off = (a_win * 2 + 127) / 128 * 128;
-    const uint32_t buf = (bt_off + kc / 8 * kRnsPitch + 127) / 128 * 128;
+    const uint32_t buf = (bt_off + kc / 8 * pitch + 127) / 128 * 128;
     if (kRnsStages * buf <= (uint32_t)kRnsSmemCap || kc <= 128) {
       if (kRnsStages * buf > (uint32_t)kRnsSmemCap) return false;
-      cfg->bpg = bpg;
-      cfg->ngrp = rblk / bpg;
+      cfg->shifts = S;
+      cfg->nb = nb;
+      cfg->b_pitch = pitch;
+      cfg->ngrp = rblk / S;
       cfg->kc = kc;
       cfg->a_win = a_win;
       cfg->bt_off = bt_off;
       cfg->buf_bytes = buf;
       cfg->smem = (int)(kRnsStages * buf);
       uint32_t cols = 32;
-      while (cols < bpg * r * 16) cols *= 2;
+      while (cols < r * nb) cols *= 2;
       cfg->tmem_cols = cols;
       return true;
     }

@@ -39,13 +39,17 @@ struct TensorRnsArgs {
   uint64_t units;            // batch * k * ngrp
   uint32_t k;
   uint32_t wrap;             // bf16x2 sign mask of the operand extensions: 0x80008000 (x^n + 1) or 0 (x^n - 1)
-  uint32_t logn, bpg, ngrp, kc, a_win, bt_off, buf_bytes, tmem_cols;
+  uint32_t logn;
+  uint32_t shifts;           // S: 1024-output blocks per unit, one per shifted copy of b in the B operand
+  uint32_t nb;               // MMA N = max(16, 8 S)
+  uint32_t b_pitch;          // bytes between K-blocks of B
+  uint32_t ngrp, kc, a_win, bt_off, buf_bytes, tmem_cols;
   unsigned long long* ctr;   // {next unit, finished CTAs}
   int* err;
 };
 
 struct RnsCfg {
-  uint32_t bpg = 0, ngrp = 0, kc = 0, a_win = 0, bt_off = 0, buf_bytes = 0, tmem_cols = 0;
+  uint32_t shifts = 0, nb = 0, b_pitch = 0, ngrp = 0, kc = 0, a_win = 0, bt_off = 0, buf_bytes = 0, tmem_cols = 0;
   int smem = 0;
 };
 
@@ -64,7 +68,7 @@ bool rns_choose_base(uint32_t n, uint64_t qmax, std::vector<uint32_t>* moduli);
 void rns_tables(const std::vector<uint32_t>& moduli, const std::vector<uint64_t>& primes, RnsBase* base,
                 std::vector<RnsPrime>* per_prime);
 
-// Output groups, K chunk and the two shared-memory buffers for degree 2^logn
+// Shifts per unit, K chunk and the shared-memory stages for degree 2^logn
 // and r moduli.
 bool rns_config(int logn, uint32_t r, RnsCfg* cfg);
 
