@@ -164,10 +164,12 @@ class ClockSampler:
 
 def _tensor_digits(n: int, qmax: int):
     """Digit width and count of the tensor path (mirrors the plan's rule:
-    n 2^(2w-2) <= 2^24, w <= 8, L digits cover |x| <= q/2)."""
+    n 2^(2w-2) <= 2^24, w <= 8, L balanced digits in [-2^(w-1), 2^(w-1))
+    reach floor(q/2))."""
     logn = n.bit_length() - 1
     w = min(8, (24 - logn) // 2 + 1)
-    L = next(l for l in range(1, 9) if ((1 << (w * l)) - 1) // 2 >= qmax // 2)
+    L = next(l for l in range(1, 9)
+             if ((1 << (w - 1)) - 1) * ((1 << (w * l)) - 1) // ((1 << w) - 1) >= qmax // 2)
     return w, L
 
 
@@ -293,14 +295,35 @@ def _host_link(dev, h2d_bytes, d2h_bytes, reps=10):
             "note": "plain page-locked copies of the step's sizes, measured in this run"}
 
 
-def _tensor_smem_roofline(n, digits, units, seconds, sms, sm_mhz, la=None):
+def _tiled_shifts(n, digits):
+    """Shifted copies of b per A slice in the tiled tensor kernel (mirrors its
+    tiling: up to 4 for one or two digits, 2 for three or four, within the
+    256 tensor-memory columns of a CTA)."""
+    cap = 4 if digits <= 2 else 2 if digits <= 4 else 1
+    s = 1
+    while s * 2 <= max(1, n // 1024) and s * 2 <= cap and digits * ((8 * digits * s * 2 + 15) // 16 * 16) <= 256:
+        s *= 2
+    return s
+
+
+def _rns_shifts(n, r):
+    """Shifted copies of b per A slice in the RNS tensor kernel (mirrors its
+    tiling: r chains of N = 8 S columns within 512)."""
+    s = 1
+    while s * 2 <= max(1, n // 1024) and r * 8 * s * 2 <= 512:
+        s *= 2
+    return s
+
+
+def _tensor_smem_roofline(n, digits, units, seconds, sms, sm_mhz, la=None, shifts=1):
     """`digits` of the operand on the MMA's B (Toeplitz) side, `la` (default
-    the same) on its A (aliased) side."""
-    nb = (8 * digits + 15) // 16 * 16
+    the same) on its A (aliased) side; `shifts` copies of b share one A
+    slice (N = 8 digits shifts)."""
+    nb = (8 * digits * shifts + 15) // 16 * 16
     la = digits if la is None else la
-    # per (product, prime): A-side digits x 128-row blocks (one below
-    # n = 1024, its rows past n/8 discarded) x K steps of 16
-    mmas = la * max(1, n // 1024) * (n // 16)
+    # per (product, prime): A-side digits x A slices (128 rows each; one
+    # below n = 1024, its rows past n/8 discarded) x K steps of 16
+    mmas = la * max(1, n // 1024 // shifts) * (n // 16)
     byts = units * mmas * (128 * 32 + nb * 32)
     peak = sms * SMEM_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
     ach = byts / seconds / 1e9
@@ -383,13 +406,15 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
             flops = 2.0 * w.n * w.n * info["rns_moduli"] * units
             out[name]["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
             out[name]["tensor_frac_smem"] = _tensor_smem_roofline(
-                w.n, 1, units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=info["rns_moduli"])["frac"]
+                w.n, 1, units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=info["rns_moduli"],
+                shifts=_rns_shifts(w.n, info["rns_moduli"]))["frac"]
         elif info["path"] == 2:
             la, lb = (1, info["digits"]) if extra_flags & polymul.FLAG_TERNARY_B else (info["digits"], info["digits"])
             flops = 2.0 * w.n * w.n * la * lb * units
             out[name]["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
             out[name]["tensor_frac_smem"] = _tensor_smem_roofline(
-                w.n, info["digits"], units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=la)["frac"]
+                w.n, info["digits"], units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=la,
+                shifts=_tiled_shifts(w.n, info["digits"]) if (info["tensor_groups"] and la == lb) else 1)["frac"]
         else:
             out[name]["alu_frac"] = mm / (ms / 1e3) / 1e9 / alu_peak_g
         plan.close()
@@ -529,13 +554,21 @@ def crossover(dev, stream, peaks, alu_peak_g, samples):
             row[name + "_us"] = ms * 1e3
             row[name + "_products_per_s"] = batch / (ms / 1e3)
             if name == "tensor":
-                row["digit_bits"], row["digits"] = info["digit_bits"], info["digits"]
-                row["tensor_groups"] = info["tensor_groups"]
-                flops = 2.0 * n * n * info["digits"] ** 2 * batch
+                row["tensor_groups"], row["rns_moduli"] = info["tensor_groups"], info["rns_moduli"]
+                sms = torch.cuda.get_device_properties(dev).multi_processor_count
+                if info["rns_moduli"]:  # more digits than the digit kernels take: the RNS kernel
+                    row["digit_bits"], row["digits"] = 0, 0
+                    flops = 2.0 * n * n * info["rns_moduli"] * batch
+                    row["tensor_frac_smem"] = _tensor_smem_roofline(
+                        n, 1, batch, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=info["rns_moduli"],
+                        shifts=_rns_shifts(n, info["rns_moduli"]))["frac"]
+                else:
+                    row["digit_bits"], row["digits"] = info["digit_bits"], info["digits"]
+                    flops = 2.0 * n * n * info["digits"] ** 2 * batch
+                    row["tensor_frac_smem"] = _tensor_smem_roofline(
+                        n, info["digits"], batch, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0),
+                        shifts=_tiled_shifts(n, info["digits"]) if info["tensor_groups"] else 1)["frac"]
                 row["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
-                row["tensor_frac_smem"] = _tensor_smem_roofline(
-                    n, info["digits"], batch, ms / 1e3, torch.cuda.get_device_properties(dev).multi_processor_count,
-                    peaks.get("sm_max_mhz", 2070.0))["frac"]
             else:
                 row["ntt_alu_frac"] = batch * _ntt_mulmods(n) / (ms / 1e3) / 1e9 / alu_peak_g
             c = torch.empty_like(ta)

@@ -112,7 +112,11 @@ bool tensor_shape(uint32_t n, uint64_t qmax, int* wb, int* L) {
   if (w > 8) w = 8;
   if (w < 2) return false;
   for (int l = 1; l <= 8; ++l) {
-    const pm::host::u128 cap = (((pm::host::u128)1 << (w * l)) - 1) / 2;
+    // digits lie in [-2^(w-1), 2^(w-1) - 1], so l of them reach
+    // (2^(w-1) - 1) (2^(wl) - 1) / (2^w - 1) on the positive side; the
+    // centred residues reach floor(q/2) there (and less below zero)
+    const pm::host::u128 cap = ((((pm::host::u128)1 << (w - 1)) - 1) * (((pm::host::u128)1 << (w * l)) - 1)) /
+                               (((pm::host::u128)1 << w) - 1);
     if (cap >= qmax / 2) {
       *wb = w;
       *L = l;

@@ -46,16 +46,6 @@ constexpr int kTiledSmemCap = 110 * 1024;  // two CTAs per SM
 constexpr int kTiledTmemCap = 256;         // tensor-memory columns per CTA
 }  // namespace
 
-template <int LA, int LB>
-struct TTShape {
-  static constexpr int NB = (8 * LB + 15) / 16 * 16;  // MMA N: 8 rows per digit of b, padded
-  static constexpr int NG = NB / 8;                   // 8-row groups of B
-  // core matrices adjacent along K are BT_PITCH bytes apart (16 bytes more
-  // than the N-groups need: consecutive threads' 16-byte stores, one K-block
-  // each, fall in distinct banks)
-  static constexpr int BT_PITCH = NG * 128 + 16;
-  static constexpr int CB = LA * NB;  // accumulator columns of one 128-row block
-};
 
 // balanced w-bit digits of the centred representative of v mod q (v < q <
 // 2^31); returns what the L digits leave over (0 whenever L digits cover
@@ -92,9 +82,20 @@ __device__ __forceinline__ bool digits8(const uint32_t* src, uint32_t q, int wb,
   return rest == 0;
 }
 
-template <int LA, int LB>
+// MMA N and the B layout for LB digits of b and S shifted copies of it
+template <int LB, int S>
+struct TTShape {
+  static constexpr int NB = (8 * LB * S + 15) / 16 * 16;  // 8 rows per digit and shift, padded
+  static constexpr int NG = NB / 8;                       // 8-row groups of B
+  // core matrices adjacent along K are BT_PITCH bytes apart (16 bytes more
+  // than the N-groups need: consecutive threads' 16-byte stores, one K-block
+  // each, fall in distinct banks)
+  static constexpr int BT_PITCH = NG * 128 + 16;
+};
+
+template <int LA, int LB, int S>
 __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiledArgs args) {
-  using TS = TTShape<LA, LB>;
+  using TS = TTShape<LB, S>;
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t s_tmem;
@@ -119,11 +120,12 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
     s_domain = 0;
   }
   fence_mbar_init();
-  // padded rows of B (digit slots >= LB) stay zero for the whole launch
-  if (TS::NG > LB) {
+  // padded rows of B (8-row groups past the S x LB digit rows) stay zero
+  // for the whole launch
+  if (TS::NG > S * LB) {
     for (uint32_t ch = tid; ch < (kc / 8) * TS::NG * 8; ch += kTiledThreads) {
       const uint32_t dp = ch / (TS::NG * 8), g = (ch / 8) % TS::NG, v = ch % 8;
-      if (g >= (uint32_t)LB) *reinterpret_cast<uint4*>(Bt + dp * TS::BT_PITCH + g * 128 + 16 * v) = make_uint4(0, 0, 0, 0);
+      if (g >= (uint32_t)(S * LB)) *reinterpret_cast<uint4*>(Bt + dp * TS::BT_PITCH + g * 128 + 16 * v) = make_uint4(0, 0, 0, 0);
     }
   }
   tc_fence_before();
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
     const uint32_t q = args.tp[j].q;
     const uint32_t* a = args.a + row * n;
     const uint32_t* b = args.b + row * n;
-    const uint32_t b0 = grp * bpg;  // first 128-row block of the group
+    const uint32_t b0 = grp * bpg * S;  // the unit's first 1024-output block
 
     for (uint32_t ch = 0; ch < nch; ++ch) {
       // ---- ConvertPoly (a): digits of a~_{base + e}, e < awin ----
@@ -171,20 +173,30 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
               make_uint4(p[s].x ^ flip, p[s].y ^ flip, p[s].z ^ flip, p[s].w ^ flip);
       }
       // ---- ConvertPoly (b): the chunk's K-blocks d' = kc/8 ch + dl of B ----
-      // K-block d' belongs to b's group g = D - d'; its window is group g - 1
-      // followed by group g (group -1 is the last group, negated for x^n + 1)
+      // For shift sh, K-block d' is b~'s group G = D - d' + 128 sh after group
+      // G - 1, b~ extended over [-n, 2n) (groups outside [0, n/8) are b's
+      // groups n/8 away, negated for x^n + 1).  Shift sh gives, from the same
+      // A, the outputs 1024 sh further on (a~ b~ is periodic in the
+      // summation index); one 8-row group per digit of b.
+      const int32_t ng = (int32_t)(n / 8);
       for (uint32_t dl = tid; dl < kc / 8; dl += kTiledThreads) {
-        const uint32_t g = D - (kc / 8 * ch + dl);
-        const uint32_t gp = g == 0 ? n / 8 - 1 : g - 1;
-        const uint32_t pflip = g == 0 ? wrap : 0u;
-        uint4 pv[LB], ow[LB];
-        digits8<LB>(b + 8 * gp, q, wb, pv);
-        digits8<LB>(b + 8 * g, q, wb, ow);
+        const int32_t g0 = (int32_t)(D - (kc / 8 * ch + dl));
 #pragma unroll
-        for (int s2 = 0; s2 < LB; ++s2) {
-          const uint32_t E[8] = {pv[s2].x ^ pflip, pv[s2].y ^ pflip, pv[s2].z ^ pflip, pv[s2].w ^ pflip,
-                                 ow[s2].x, ow[s2].y, ow[s2].z, ow[s2].w};
-          b_block_rows(E, Bt + dl * TS::BT_PITCH + s2 * 128);
+        for (int sh = 0; sh < S; ++sh) {
+          const int32_t G = g0 + 128 * sh, H = G - 1;
+          const uint32_t gg = (uint32_t)(G >= ng ? G - ng : G);
+          const uint32_t hh = (uint32_t)(H < 0 ? H + ng : H >= ng ? H - ng : H);
+          const uint32_t fg = G >= ng ? wrap : 0u;
+          const uint32_t fh = (H < 0 || H >= ng) ? wrap : 0u;
+          uint4 pv[LB], ow[LB];
+          digits8<LB>(b + 8 * hh, q, wb, pv);
+          digits8<LB>(b + 8 * gg, q, wb, ow);
+#pragma unroll
+          for (int s2 = 0; s2 < LB; ++s2) {
+            const uint32_t E[8] = {pv[s2].x ^ fh, pv[s2].y ^ fh, pv[s2].z ^ fh, pv[s2].w ^ fh,
+                                   ow[s2].x ^ fg, ow[s2].y ^ fg, ow[s2].z ^ fg, ow[s2].w ^ fg};
+            b_block_rows(E, Bt + dl * TS::BT_PITCH + (sh * LB + s2) * 128);
+          }
         }
       }
       fence_proxy_async();
@@ -227,32 +239,37 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
     const uint64_t mu = args.tp[j].mu, bias = args.tp[j].bias;
 #pragma unroll 1
     for (uint32_t bl = 0; bl < bpg; ++bl) {
-      int64_t acc[8];
 #pragma unroll
-      for (int v = 0; v < 8; ++v) acc[v] = 0;
+      for (int sh = 0; sh < S; ++sh) {
+        int64_t acc[8];
 #pragma unroll
-      for (int s = 0; s < LA; ++s) {
+        for (int v = 0; v < 8; ++v) acc[v] = 0;
 #pragma unroll
-        for (int c16 = 0; c16 < TS::NB / 16; ++c16) {
-          uint32_t r[16];
-          // warp-collective: every lane loads, only the stores below are predicated
-          tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (bl * LA + s) * TS::NB + 16 * c16, r);
-          tmem_wait_ld();
+        for (int s = 0; s < LA; ++s) {
 #pragma unroll
-          for (int cc = 0; cc < 16; ++cc) {
-            const int col = 16 * c16 + cc, s2 = col / 8, v = col % 8;
-            if (s2 < LB)
-              acc[v] += (int64_t)__float2int_rn(__uint_as_float(r[cc])) * (int64_t)args.tp[j].pw[s + s2];
+          for (int c16 = 0; c16 < TS::NB / 16; ++c16) {
+            // only the 16-column loads that hold this shift's rows
+            if (16 * c16 + 16 <= 8 * sh * LB || 16 * c16 >= 8 * (sh + 1) * LB) continue;
+            uint32_t r[16];
+            // warp-collective: every lane loads, only the stores below are predicated
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (bl * LA + s) * TS::NB + 16 * c16, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) {
+              const int col = 16 * c16 + cc, g = col / 8, v = col % 8;
+              if (g >= sh * LB && g < (sh + 1) * LB)
+                acc[v] += (int64_t)__float2int_rn(__uint_as_float(r[cc])) * (int64_t)args.tp[j].pw[s + g - sh * LB];
+            }
           }
         }
-      }
-      const uint32_t j0 = 8 * (128 * (b0 + bl) + (uint32_t)tid);
-      if (j0 < n) {
-        uint32_t out[8];
+        const uint32_t j0 = 8 * (128 * (b0 + bl + sh) + (uint32_t)tid);
+        if (j0 < n) {
+          uint32_t out[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) out[v] = barrett64((uint64_t)(acc[v] + (int64_t)bias), q, mu);
-        *reinterpret_cast<uint4*>(c + j0) = make_uint4(out[0], out[1], out[2], out[3]);
-        *reinterpret_cast<uint4*>(c + j0 + 4) = make_uint4(out[4], out[5], out[6], out[7]);
+          for (int v = 0; v < 8; ++v) out[v] = barrett64((uint64_t)(acc[v] + (int64_t)bias), q, mu);
+          *reinterpret_cast<uint4*>(c + j0) = make_uint4(out[0], out[1], out[2], out[3]);
+          *reinterpret_cast<uint4*>(c + j0 + 4) = make_uint4(out[4], out[5], out[6], out[7]);
+        }
       }
     }
     tc_fence_before();
@@ -279,29 +296,44 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
   }
 }
 
+// the largest shift count instantiated for (la, lb): copies of b pay when
+// b's digits are no more than a's (the B operand grows with the shifts)
+static uint32_t max_shifts(int la, int lb) {
+  if (la != lb) return 1;
+  return la <= 2 ? 4 : la <= 4 ? 2 : 1;
+}
+
 bool toeplitz_tiled_config(int logn, int la, int lb, TiledCfg* cfg) {
   if (logn < 6 || logn > 14 || la < 1 || lb < 1 || la > 5 || lb > 5) return false;
   const uint32_t n = 1u << logn;
-  const uint32_t nb = (8 * lb + 15) / 16 * 16, pitch = nb / 8 * 128 + 16, cb = (uint32_t)la * nb;
-  if (cb > (uint32_t)kTiledTmemCap) return false;
+  auto nb_of = [&](uint32_t S) { return (8 * (uint32_t)lb * S + 15) / 16 * 16; };
+  if ((uint32_t)la * nb_of(1) > (uint32_t)kTiledTmemCap) return false;
   const uint32_t rblk = n >= 1024 ? n / 1024 : 1;
-  uint32_t bpg = 1;
-  while (bpg * 2 <= rblk && bpg * 2 * cb <= (uint32_t)kTiledTmemCap) bpg *= 2;
+  // shifted copies of b (one A slice), else consecutive A slices, as many as
+  // the CTA's tensor memory holds
+  uint32_t S = 1, bpg = 1;
+  while (S * 2 <= rblk && S * 2 <= max_shifts(la, lb) && (uint32_t)la * nb_of(S * 2) <= (uint32_t)kTiledTmemCap) S *= 2;
+  if (S == 1)
+    while (bpg * 2 <= rblk && bpg * 2 * (uint32_t)la * nb_of(1) <= (uint32_t)kTiledTmemCap) bpg *= 2;
+  const uint32_t nb = nb_of(S), pitch = nb / 8 * 128 + 16;
   uint32_t kc = n < 1024 ? n : 1024;
   for (;;) {
     const uint32_t a_win = 1024 * bpg + kc;
     const uint32_t bt_off = ((uint32_t)la * a_win * 2 + 127) / 128 * 128;
     const uint32_t smem = bt_off + kc / 8 * pitch;
-    if (smem <= (uint32_t)kTiledSmemCap || kc <= 128) {
+    if (smem <= (uint32_t)kTiledSmemCap || kc <= 64) {
       if (smem > (uint32_t)kTiledSmemCap) return false;
       cfg->bpg = bpg;
-      cfg->ngrp = rblk / bpg;
+      cfg->shifts = S;
+      cfg->nb = nb;
+      cfg->b_pitch = pitch;
+      cfg->ngrp = rblk / (bpg * S);
       cfg->kc = kc;
       cfg->a_win = a_win;
       cfg->bt_off = bt_off;
       cfg->smem = (int)smem;
       uint32_t cols = 32;
-      while (cols < bpg * cb) cols *= 2;
+      while (cols < bpg * (uint32_t)la * nb) cols *= 2;
       cfg->tmem_cols = cols;
       return true;
     }
@@ -309,9 +341,9 @@ bool toeplitz_tiled_config(int logn, int la, int lb, TiledCfg* cfg) {
   }
 }
 
-template <int LA, int LB>
+template <int LA, int LB, int S>
 static void tiled_info(const TiledCfg& cfg, KernelInfo* ki) {
-  ki->fn = (const void*)k_toeplitz_tiled<LA, LB>;
+  ki->fn = (const void*)k_toeplitz_tiled<LA, LB, S>;
   ki->block = kTiledThreads;
   ki->smem = cfg.smem;
   ki->team = kTiledThreads;
@@ -323,24 +355,20 @@ static void tiled_info(const TiledCfg& cfg, KernelInfo* ki) {
 bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki) {
   TiledCfg cfg;
   if (!toeplitz_tiled_config(logn, la, lb, &cfg)) return false;
-  if (la == lb) {
-    switch (la) {
-      case 1: tiled_info<1, 1>(cfg, ki); return true;
-      case 2: tiled_info<2, 2>(cfg, ki); return true;
-      case 3: tiled_info<3, 3>(cfg, ki); return true;
-      case 4: tiled_info<4, 4>(cfg, ki); return true;
-      case 5: tiled_info<5, 5>(cfg, ki); return true;
-      default: return false;
-    }
+  const int S = (int)cfg.shifts;
+#define PM_TT(A, B, SH)                    \
+  if (la == A && lb == B && S == SH) {     \
+    tiled_info<A, B, SH>(cfg, ki);         \
+    return true;                           \
   }
-  if (la != 1) return false;
-  switch (lb) {  // a single-digit operand on the A side (ternary b)
-    case 2: tiled_info<1, 2>(cfg, ki); return true;
-    case 3: tiled_info<1, 3>(cfg, ki); return true;
-    case 4: tiled_info<1, 4>(cfg, ki); return true;
-    case 5: tiled_info<1, 5>(cfg, ki); return true;
-    default: return false;
-  }
+  PM_TT(1, 1, 1) PM_TT(1, 1, 2) PM_TT(1, 1, 4)
+  PM_TT(2, 2, 1) PM_TT(2, 2, 2) PM_TT(2, 2, 4)
+  PM_TT(3, 3, 1) PM_TT(3, 3, 2)
+  PM_TT(4, 4, 1) PM_TT(4, 4, 2)
+  PM_TT(5, 5, 1)
+  PM_TT(1, 2, 1) PM_TT(1, 3, 1) PM_TT(1, 4, 1) PM_TT(1, 5, 1)  // a single-digit operand on the A side (ternary b)
+#undef PM_TT
+  return false;
 }
 
 }  // namespace pm

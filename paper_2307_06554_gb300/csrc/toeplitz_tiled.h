@@ -8,13 +8,16 @@
 
 namespace pm {
 
-// Tiling of one (product, prime) row: the n/8 rows of A (8 outputs each)
-// in blocks of 128, `bpg` blocks per unit of work (`ngrp` units per row),
-// the summation dimension in chunks of `kc`.  Shared memory per CTA: the
-// digit window of a~ (la x a_win bf16 values) at offset 0 and the chunk of
-// B at `bt_off`.
+// Tiling of one (product, prime) row: the outputs in blocks of 1024 (128
+// rows of A, 8 outputs each); a unit of work (`ngrp` per row) covers
+// `bpg` x `shifts` blocks: `bpg` consecutive A slices (one MMA chain per
+// slice and digit of a), or, with `shifts` > 1, one A slice against that
+// many copies of b shifted by 1024 coefficients in the B operand (N = nb
+// columns, K-blocks `b_pitch` bytes apart); the summation dimension in
+// chunks of `kc`.  Shared memory per CTA: the digit window of a~ (la x
+// a_win bf16 values) at offset 0 and the chunk of B at `bt_off`.
 struct TiledCfg {
-  uint32_t bpg = 0, ngrp = 0, kc = 0, a_win = 0, bt_off = 0, tmem_cols = 0;
+  uint32_t bpg = 0, shifts = 0, nb = 0, b_pitch = 0, ngrp = 0, kc = 0, a_win = 0, bt_off = 0, tmem_cols = 0;
   int smem = 0;
 };
 
@@ -37,9 +40,9 @@ struct TensorTiledArgs {
 // columns).
 bool toeplitz_tiled_config(int logn, int la, int lb, TiledCfg* cfg);
 
-// k_toeplitz_tiled<LA, LB> for LA = LB = 1 .. 5 and for LA = 1, LB = 2 .. 5
-// (a single-digit operand on the A side); ki->smem and ki->tmem_cols from
-// the tiling of degree 2^logn.
+// k_toeplitz_tiled<LA, LB, S> for LA = LB = 1 .. 5 and for LA = 1, LB = 2
+// .. 5 (a single-digit operand on the A side), S the shifts the tiling
+// chose; ki->smem and ki->tmem_cols from the tiling of degree 2^logn.
 bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki);
 
 }  // namespace pm

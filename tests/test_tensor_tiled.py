@@ -316,3 +316,33 @@ def test_ternary_flag_ignored_by_ntt_path(pm):
         got = run_plan_batch(plan, a, b)
         pm.polymul_plan_status(plan.handle)
     assert_equal_residues(got, native.polymul_batch(a, b, [q]), "ntt with the flag")
+
+
+@pytest.mark.parametrize("n,q,digits", [(1024, 65521, 3), (256, 65519, 3), (2048, 16381, 3), (4096, 16381, 3),
+                                        (8192, 1073479681, 0)])
+def test_digit_capacity_boundary(pm, n, q, digits):
+    """Moduli just below a digit-count boundary: L balanced w-bit digits in
+    [-2^(w-1), 2^(w-1)) reach (2^(w-1) - 1)(2^(wL) - 1)/(2^w - 1), a little
+    less than (2^(wL) - 1)/2, so floor(q/2) of these moduli needs one digit
+    more than the naive bound says (digits == 0: more than five digits,
+    served by the residue-number-system kernel).  Every coefficient at the
+    positive and negative extremes of the centred range."""
+    assert wl.is_prime(q)
+    rng = np.random.default_rng(q % 997)
+    a = wl.uniform_coeffs(rng, 3, [q], n, np.uint32)
+    b = wl.uniform_coeffs(rng, 3, [q], n, np.uint32)
+    a[0] = q // 2          # +floor(q/2)
+    b[0] = q // 2
+    a[1] = q // 2 + 1      # -floor(q/2) (q odd)
+    b[1, 0, ::2] = q // 2
+    with pm.Plan(n, [q], path=pm.PATH_TENSOR) as plan:
+        info = plan.info
+        if digits:
+            assert info["digits"] == digits and info["rns_moduli"] == 0, info
+        else:
+            assert info["rns_moduli"] > 0, info
+        got = run_plan_batch(plan, a, b)
+    if n <= 4096:
+        assert_equal_residues(got, native.polymul_batch(a, b, [q]), "boundary n=%d q=%d" % (n, q))
+    else:
+        _check_sampled(got, a, b, [q], False, rng)
