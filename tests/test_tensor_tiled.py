@@ -191,9 +191,13 @@ def test_tiled_candidate_matches_whole_product_kernel(pm, n):
     b = wl.uniform_coeffs(rng, 77, q_list, n, np.uint32)
     with pm.Plan(n, q_list, path=pm.PATH_TENSOR) as plan:
         info = plan.info
-        assert info["candidates"] == 3 and info["tensor_groups"] == 0  # whole product, tiled, RNS
+        assert info["candidates"] == 3  # whole product, tiled (first at 2048: shifted copies of b), RNS
+        kinds = [(plan.select(i)["tensor_groups"], plan.info["rns_moduli"]) for i in range(3)]
+        assert kinds[2][1] > 0 and sorted(kinds[:2]) == [(0, 0), (1, 0)]
+        assert kinds[0] == ((1, 0) if n == 2048 else (0, 0))
+        plan.select(kinds.index((0, 0)))
         whole = run_plan_batch(plan, a, b)
-        assert plan.select(1)["tensor_groups"] == 1 and plan.info["rns_moduli"] == 0
+        plan.select(kinds.index((1, 0)))
         tiled = run_plan_batch(plan, a, b)
     assert np.array_equal(whole, tiled)
     assert_equal_residues(tiled, native.polymul_batch(a, b, q_list), "tiled n=%d" % n)
