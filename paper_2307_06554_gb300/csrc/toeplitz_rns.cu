@@ -51,11 +51,11 @@ namespace pm {
 
 namespace {
 constexpr int kRnsGroup = 128;                        // threads of one builder group (4 warps)
-constexpr int kRnsGroups = 2;                         // builder groups, taking alternate steps
-constexpr int kRnsBuilders = kRnsGroup * kRnsGroups;  // warps 0-7: operand builds; warps 0-3 the epilogue
-constexpr int kRnsIssuers = 2;                        // MMA-issuing warps (alternate moduli)
-constexpr int kRnsThreads = kRnsBuilders + 32 * kRnsIssuers;  // + warps 8, 9: MMA issue
-constexpr int kRnsStages = 2 * kRnsGroups;            // shared-memory stages in the ring
+constexpr int kRnsPipes = 2;                          // pipelines: builder group g + issuing warp g
+constexpr int kRnsBuilders = kRnsGroup * kRnsPipes;   // warps 0-7: operand builds; warps 0-3 the epilogue
+constexpr int kRnsThreads = kRnsBuilders + 32 * kRnsPipes;  // + warps 8, 9: MMA issue
+constexpr int kRnsPipeStages = 2;                     // shared-memory stages of one pipeline
+constexpr int kRnsStages = kRnsPipes * kRnsPipeStages;
 constexpr int kRnsSmemCap = 200 * 1024;  // all stages
 }  // namespace
 
@@ -139,17 +139,21 @@ __device__ __forceinline__ void mbar_arrive_plain(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Two groups of four warps build the operands of alternate steps (one
-// modulus over one K chunk each) into a ring of kRnsStages shared-memory
-// stages, so that two steps' residue loads are in flight at once; warps 0-3
-// also run the epilogue.  Warps 8 and 9 issue the MMA chains, one thread
-// each, for the moduli of even and of odd index (one thread issuing alone
-// measured about 100 cycles per small MMA); each accumulator is written by
-// one issuer only, so its chains stay in order.  full[s] (one group's 128
-// arrivals) hands a built stage to its issuer, empty[s] (tcgen05.commit)
-// hands it back once its chains have read it.  Every wait is bounded; after
-// the first expired wait the CTA stops waiting, finishes the unit (results
-// invalid) and reports it.
+// Two independent pipelines, one for the moduli of even and one for those of
+// odd index: pipeline g is a group of four builder warps (warps 4g .. 4g+3)
+// that build its steps (one modulus over one K chunk each, in order) into
+// its own two shared-memory stages, and one issuing warp (8 + g) that issues
+// their MMA chains (one thread issuing alone measured about 100 cycles per
+// small MMA; two issue in parallel).  full[s] (the group's 128 arrivals)
+// hands a built stage to the issuer, empty[s] (tcgen05.commit) hands it back
+// once its chains have read it.  Each barrier has one producer sequence and
+// one consumer sequence, each waiting every phase in order, so an awaited
+// phase is never more than one ahead and the parity test cannot alias (a
+// shared ring whose stages two issuers took in turn could: an issuer could
+// wait on a stage whose previous use, another issuer's, was not built yet).
+// Warps 0-3 also run the epilogue.  Every wait is bounded; after the first
+// expired wait the CTA stops waiting, finishes the unit (results invalid)
+// and reports it.
 template <typename W>
 __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs args) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -197,7 +201,8 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   const uint32_t r = s_base.r;
-  const uint32_t nsteps = nch * r;
+  // steps of pipeline g per unit: every chunk times the moduli i = g mod 2
+  const uint32_t cnt[kRnsPipes] = {(r + 1) / 2, r / 2};
   volatile int* fail = &s_fail;
   // a bounded wait, skipped once any wait of the CTA has expired
   auto wait = [&](uint64_t* bar, uint32_t parity) {
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
   if (tid == 0) s_next = atomicAdd(args.ctr, 1ull);
   __syncthreads();
   unsigned long long cur = s_next;
-  uint32_t step = 0;  // steps issued by this CTA so far (the same count in every thread)
+  uint32_t done[kRnsPipes] = {0, 0};  // steps of each pipeline so far (the same counts in every thread)
   bool failed = false;
   while (cur < units) {
     __syncthreads();  // every thread has read s_next
@@ -220,9 +225,11 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
     const uint32_t b0 = grp * S;  // the unit's first 1024-output block
 
     if (builder) {
-      for (uint32_t st = grp_id; st < nsteps; st += kRnsGroups) {
-        const uint32_t gs = step + st, x = gs % kRnsStages, ch = st / r, i = st % r;
-        if (gs >= (uint32_t)kRnsStages) wait(&empty[x], ((gs / kRnsStages) - 1) & 1u);
+      const uint32_t g = grp_id;
+      for (uint32_t t = 0; t < nch * cnt[g]; ++t) {
+        const uint32_t lc = done[g] + t, x = g * kRnsPipeStages + lc % kRnsPipeStages;
+        const uint32_t ch = t / cnt[g], i = g + 2 * (t % cnt[g]);
+        if (lc >= (uint32_t)kRnsPipeStages) wait(&empty[x], ((lc / kRnsPipeStages) - 1) & 1u);
         unsigned char* buf = sm + x * args.buf_bytes;
         uint16_t* Xw = reinterpret_cast<uint16_t*>(buf);
         unsigned char* Bt = buf + args.bt_off;
@@ -264,15 +271,13 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
         mbar_arrive_plain(&full[x]);
       }
     } else if (lane == 0) {
-      // ---- TPUMul: this issuer's steps (moduli of its parity), as their
-      // stages fill ----
-      const uint32_t e = (uint32_t)warp - kRnsBuilders / 32;
+      // ---- TPUMul: pipeline g's chains, as its stages fill ----
+      const uint32_t g = (uint32_t)warp - kRnsBuilders / 32;
       const uint64_t BSTEP = (2 * pitch) >> 4;
-      for (uint32_t st = 0; st < nsteps; ++st) {
-        const uint32_t i = st % r;
-        if ((i & 1u) != e) continue;
-        const uint32_t gs = step + st, x = gs % kRnsStages, ch = st / r;
-        wait(&full[x], (gs / kRnsStages) & 1u);
+      for (uint32_t t = 0; t < nch * cnt[g]; ++t) {
+        const uint32_t lc = done[g] + t, x = g * kRnsPipeStages + lc % kRnsPipeStages;
+        const uint32_t ch = t / cnt[g], i = g + 2 * (t % cnt[g]);
+        wait(&full[x], (lc / kRnsPipeStages) & 1u);
         tc_fence_after();
         const uint32_t xa0 = smem_u32(sm + x * args.buf_bytes);
         const uint64_t ad0 = smem_desc(xa0, 16, 128), bd0 = smem_desc(xa0 + args.bt_off, pitch, 128);
@@ -284,16 +289,17 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
       }
     }
     if (warp >= kRnsBuilders / 32) __syncwarp();
-    step += nsteps;
+    for (int g = 0; g < kRnsPipes; ++g) done[g] += nch * cnt[g];
 
     // ---- ConvertMatrix: the CRT per output, reduced mod q (warps 0-3) ----
     if (tid < kRnsGroup) {
-      // every chain of the unit has completed: the last kRnsStages steps'
-      // commits, one per stage (each stage's previous commit was awaited
-      // before the stage was refilled, so each awaited phase is at most one
-      // ahead of its barrier and the parity test cannot alias)
-      for (uint32_t gs = step > (uint32_t)kRnsStages ? step - kRnsStages : 0; gs < step; ++gs)
-        wait(&empty[gs % kRnsStages], (gs / kRnsStages) & 1u);
+      // every chain of the unit has completed: each pipeline's last commits,
+      // in its order (each stage's previous commit was awaited by its
+      // builders before they refilled it, so no awaited phase is more than
+      // one ahead of its barrier)
+      for (int g = 0; g < kRnsPipes; ++g)
+        for (uint32_t lc = done[g] > (uint32_t)kRnsPipeStages ? done[g] - kRnsPipeStages : 0; lc < done[g]; ++lc)
+          wait(&empty[g * kRnsPipeStages + lc % kRnsPipeStages], (lc / kRnsPipeStages) & 1u);
       tc_fence_after();
       const uint64_t q = tp->q;
       W* c = C + row * n;
@@ -359,8 +365,9 @@ __global__ void __launch_bounds__(kRnsThreads, 1) k_toeplitz_rns(TensorRnsArgs a
   if (failed && tid == 0) {
     atomicExch(args.err, 1);
     // let the chains in flight finish before the memory they read is freed
-    for (uint32_t gs = step > (uint32_t)kRnsStages ? step - kRnsStages : 0; gs < step; ++gs)
-      mbar_wait(&empty[gs % kRnsStages], (gs / kRnsStages) & 1u);
+    for (int g = 0; g < kRnsPipes; ++g)
+      for (uint32_t lc = done[g] > (uint32_t)kRnsPipeStages ? done[g] - kRnsPipeStages : 0; lc < done[g]; ++lc)
+        mbar_wait(&empty[g * kRnsPipeStages + lc % kRnsPipeStages], (lc / kRnsPipeStages) & 1u);
   }
   tc_fence_before();
   __syncthreads();
