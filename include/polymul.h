@@ -137,6 +137,17 @@ typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
  *   out     receives the plan; untouched on failure.
  * Device tables (roots of unity, constants) are computed and uploaded on the
  * current CUDA device; the plan must be used on that device.
+ * Routes (PATH_AUTO takes the NTT where it exists; the tensor kernels are
+ * then autotuner candidates):
+ *   NTT      prime q = 1 mod 2n (mod n for the cyclic ring), q < 2^31 in
+ *            4-byte words or q < 2^62 in 8-byte words; else, for q < 2^31
+ *            and n <= 2^14, one 31-bit auxiliary prime when 2n floor(q/2)^2
+ *            fits it.
+ *   TENSOR   n = 2^6 .. 2^14: balanced bf16 digits for q < 2^31 with at
+ *            most five digits (whole-product kernel at n = 1024, 2048,
+ *            tiled kernel at every n); the residue number system of small
+ *            moduli for any q < 2^62 whose base needs at most 32 moduli
+ *            (polymul_tensor_rns_base).
  * Errors: EINVAL (n, q, k, duplicates, null out), ENOTSUP (no path can serve
  * the moduli at this n, or a forced path cannot), ENOMEM, ECUDA.
  */
@@ -148,8 +159,12 @@ int polymul_create(uint32_t n, const uint64_t *q_list, uint32_t k,
  *   a, b, c  device pointers, [batch][k][n] of the plan's element type,
  *            16-byte aligned.  batch == 0 is a no-op.
  *   stream   cudaStream_t or NULL.
- * Asynchronous.  Errors: EINVAL (null pointers with batch > 0, misaligned),
- * EDOMAIN (validate flag and an input >= q; c is then unspecified), ECUDA.
+ * Asynchronous.  The tensor path's residue-number-system kernel keeps
+ * residue planes in plan-owned scratch, allocated (or grown) on the first
+ * call with a larger batch: make one such call before capturing the stream
+ * into a CUDA graph.  Errors: EINVAL (null pointers with batch > 0,
+ * misaligned), EDOMAIN (validate flag and an input >= q; c is then
+ * unspecified), ENOMEM (scratch), ECUDA.
  */
 int polymul_batch(polymul_plan *plan, const void *a, const void *b, void *c,
                   uint64_t batch, void *stream);
