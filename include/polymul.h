@@ -259,6 +259,36 @@ int polymul_batch_static(uint32_t n, uint64_t q, const void *a, const void *b, v
 int polymul_tune(polymul_plan *plan, uint64_t batch, void *stream);
 
 /*
+ * polymul_tensor_shape -- the tensor path's default kernel for degree n and
+ * moduli up to qmax, as a POLYMUL_PATH_TENSOR plan with `flags` would take
+ * it (POLYMUL_FLAG_TERNARY_B matters; the cyclic flag does not change the
+ * shape), without creating a plan: host only, no device is touched.
+ * Errors: EINVAL (n not a power of two in [16, 65536], qmax outside
+ * [2, 2^62), info NULL), ENOTSUP (the tensor path has no kernel for it).
+ */
+typedef struct polymul_tensor_shape_info {
+    uint32_t kernel;      /* 1 whole-product digit kernel, 2 tiled digit
+                             kernel, 3 residue number system of small moduli */
+    uint32_t candidates;  /* tensor kernels the plan holds (the autotuner
+                             chooses among them)                            */
+    uint32_t digit_bits;  /* digit kernels: digit width w (0 for the RNS one) */
+    uint32_t digits_a;    /* digits of the operand on the MMA's A side (1 for
+                             a ternary b, which takes that side)            */
+    uint32_t digits_b;    /* digits of the operand on the B side            */
+    uint32_t shifts;      /* tiled and RNS kernels: shifted copies of b that
+                             share one A slice                              */
+    uint32_t slices;      /* A slices (1024 outputs each) per unit of work  */
+    uint32_t groups;      /* units of work per (product, prime); 0 for the
+                             whole-product kernel                           */
+    uint32_t rns_moduli;  /* RNS kernel: moduli in the base                 */
+    uint32_t smem_bytes;  /* dynamic shared memory per CTA                  */
+    uint32_t tmem_cols;   /* tensor-memory columns per CTA                  */
+    uint32_t reserved[5];
+} polymul_tensor_shape_info;
+
+int polymul_tensor_shape(uint32_t n, uint64_t qmax, uint32_t flags, polymul_tensor_shape_info *info);
+
+/*
  * polymul_tensor_rns_base -- the residue number system of small moduli that
  * the tensor path's RNS kernel uses for degree n and moduli up to qmax
  * (Sec. 2.4 and the RNS-base selection of the key-parameter section): odd,

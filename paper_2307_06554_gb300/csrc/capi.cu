@@ -130,6 +130,46 @@ bool tensor_shape(uint32_t n, uint64_t qmax, int* wb, int* L) {
 // takes that side), else L
 int tensor_la(const polymul_plan* p) { return p->ternary_b ? 1 : p->digits; }
 
+// The tensor path's kernels for degree n and moduli up to qmax, the default
+// first: the digit kernels for moduli below 2^31 (the whole-product kernel
+// at n = 1024, 2048 and the tiled one, the tiled first where it serves two
+// blocks from one A slice: measured 101 vs 165 us for two digits at
+// n = 2048, 174 vs 330 us for three), then the residue-number-system kernel
+// (any q < 2^62 with a base of at most 32 moduli).  Host only.
+struct TensorChoice {
+  int wb = 0, L = 0;                  // digit width and count of the digit kernels
+  std::vector<uint32_t> rns_moduli;   // the RNS base, when that kernel is a candidate
+  std::vector<KernelInfo> kernels;    // [0] the default
+};
+bool choose_tensor(uint32_t n, uint64_t qmax, uint32_t elem, bool ternary_b, TensorChoice* tc) {
+  const int logn = __builtin_ctz(n);
+  tc->kernels.clear();
+  tc->rns_moduli.clear();
+  tc->wb = tc->L = 0;
+  KernelInfo kwhole, ktiled, krns;
+  bool whole = false, tiled = false;
+  if (elem == 4 && qmax < (1ull << 31) && tensor_shape(n, qmax, &tc->wb, &tc->L)) {
+    tiled = lookup_toeplitz_tiled(logn, ternary_b ? 1 : tc->L, tc->L, &ktiled);
+    whole = !ternary_b && lookup_toeplitz(logn, tc->wb, tc->L, tc->L, &kwhole);
+  }
+  if (whole && tiled) {
+    TiledCfg cfg;
+    const bool shifted = toeplitz_tiled_config(logn, tc->L, tc->L, &cfg) && cfg.shifts > 1;
+    tc->kernels.push_back(shifted ? ktiled : kwhole);
+    tc->kernels.push_back(shifted ? kwhole : ktiled);
+  } else if (whole) {
+    tc->kernels.push_back(kwhole);
+  } else if (tiled) {
+    tc->kernels.push_back(ktiled);
+  }
+  std::vector<uint32_t> mods;
+  if (rns_choose_base(n, qmax, &mods) && lookup_toeplitz_rns(logn, (uint32_t)mods.size(), elem, &krns)) {
+    tc->kernels.push_back(krns);
+    tc->rns_moduli = mods;
+  }
+  return !tc->kernels.empty();
+}
+
 // the small-moduli base of the RNS tensor kernel and its per-prime constants
 int upload_rns_tables(polymul_plan* p, const std::vector<uint32_t>& moduli) {
   if (p->d_rns_base) return POLYMUL_OK;
@@ -286,39 +326,19 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
   // tensor path: moduli below 2^31, n = 2^6 .. 2^14.  The whole-product
   // kernel where it is instantiated (n = 1024, 2048), the tiled kernel
   // otherwise, and as a second candidate beside the whole-product one
-  bool tensor_ok = false, tiled_extra = false;
-  KernelInfo tki_tiled;
-  // the residue-number-system kernel (small moduli, Sec. 2.4): any q below
-  // 2^62 in 4- or 8-byte words, where a base of at most 32 moduli exists
-  std::vector<uint32_t> rns_moduli;
-  KernelInfo tki_rns;
-  const bool rns_ok = rns_choose_base(n, qmax, &rns_moduli) &&
-                      lookup_toeplitz_rns((int)p->logn, (uint32_t)rns_moduli.size(), p->elem, &tki_rns);
-  if (p->elem == 4 && qmax < (1ull << 31) && tensor_shape(n, qmax, &p->digit_bits, &p->digits)) {
-    const bool tiled = lookup_toeplitz_tiled((int)p->logn, tensor_la(p), p->digits, &tki_tiled);
-    if (!p->ternary_b && lookup_toeplitz((int)p->logn, p->digit_bits, p->digits, p->digits, &p->tki)) {
-      tensor_ok = true;
-      tiled_extra = tiled;
-      // where the tiled kernel serves two blocks from one A slice (n = 2048,
-      // shifted copies of b) it is the faster one (measured 101 vs 165 us
-      // for two digits, 174 vs 330 us for three): it goes first
-      TiledCfg tcfg;
-      if (tiled && toeplitz_tiled_config((int)p->logn, tensor_la(p), p->digits, &tcfg) && tcfg.shifts > 1)
-        std::swap(p->tki, tki_tiled);
-    } else if (tiled) {
-      p->tki = tki_tiled;
-      tensor_ok = true;
+  TensorChoice tch;
+  const bool tensor_ok = choose_tensor(n, qmax, p->elem, p->ternary_b, &tch);
+  p->digit_bits = tch.wb;
+  p->digits = tch.L;
+  if (tensor_ok) p->tki = tch.kernels[0];
+  auto add_tensor_candidates = [&](auto&& add) -> int {
+    int r = upload_tensor_tables(p);
+    for (const KernelInfo& k : tch.kernels) {
+      if (r == POLYMUL_OK && k.rns) r = upload_rns_tables(p, tch.rns_moduli);
+      if (r == POLYMUL_OK) r = add(POLYMUL_PATH_TENSOR, k);
     }
-  }
-  // digits where the digit kernels serve, the RNS kernel as another
-  // candidate; the RNS kernel alone elsewhere (64-bit words, more digits)
-  bool rns_extra = false;
-  if (tensor_ok) {
-    rns_extra = rns_ok;
-  } else if (rns_ok) {
-    p->tki = tki_rns;
-    tensor_ok = true;
-  }
+    return r;
+  };
 
   int rc = POLYMUL_OK;
   // NTT batch kernels take a programmatic dependent launch (measured on
@@ -343,12 +363,7 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     if (!tensor_ok) {
       rc = fail(POLYMUL_ENOTSUP, "tensor path not available for n=%u and these moduli", n);
     } else {
-      rc = upload_tensor_tables(p);
-      if (rc == POLYMUL_OK && p->tki.rns) rc = upload_rns_tables(p, rns_moduli);
-      if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
-      if (rc == POLYMUL_OK && tiled_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_tiled);
-      if (rc == POLYMUL_OK && rns_extra) rc = upload_rns_tables(p, rns_moduli);
-      if (rc == POLYMUL_OK && rns_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_rns);
+      rc = add_tensor_candidates(add_candidate);
     }
   } else if (!ntt_ok) {
     rc = fail(POLYMUL_ENOTSUP, "no NTT route for these moduli at n=%u (need prime q = 1 mod %s, q < 2^31 for 32-bit words)",
@@ -365,14 +380,7 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
       rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && p->elem == 8 && lookup_ntt_u64_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
-    if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) {
-      rc = upload_tensor_tables(p);
-      if (rc == POLYMUL_OK && p->tki.rns) rc = upload_rns_tables(p, rns_moduli);
-      if (rc == POLYMUL_OK) rc = add_candidate(POLYMUL_PATH_TENSOR, p->tki);
-      if (rc == POLYMUL_OK && tiled_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_tiled);
-      if (rc == POLYMUL_OK && rns_extra) rc = upload_rns_tables(p, rns_moduli);
-      if (rc == POLYMUL_OK && rns_extra) rc = add_candidate(POLYMUL_PATH_TENSOR, tki_rns);
-    }
+    if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) rc = add_tensor_candidates(add_candidate);
   }
   if (rc == POLYMUL_OK) apply_candidate(p, 0);
   if (rc == POLYMUL_OK) {
@@ -457,6 +465,52 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
     TiledCfg tc;
     if (toeplitz_tiled_config((int)p->logn, tensor_la(p), p->digits, &tc)) info->tensor_groups = tc.ngrp;
+  }
+  return POLYMUL_OK;
+}
+
+extern "C" int polymul_tensor_shape(uint32_t n, uint64_t qmax, uint32_t flags, polymul_tensor_shape_info* info) {
+  clear_error();
+  if (!info) return fail(POLYMUL_EINVAL, "info is NULL");
+  if (n < 16 || n > 65536 || (n & (n - 1))) return fail(POLYMUL_EINVAL, "n=%u must be a power of two in [16, 65536]", n);
+  if (qmax < 2 || qmax >= (1ull << 62)) return fail(POLYMUL_EINVAL, "qmax outside [2, 2^62)");
+  const bool ternary = (flags & POLYMUL_FLAG_TERNARY_B) != 0;
+  const uint32_t elem = qmax < (1ull << 32) ? 4 : 8;
+  TensorChoice tch;
+  if (!choose_tensor(n, qmax, elem, ternary, &tch))
+    return fail(POLYMUL_ENOTSUP, "tensor path not available for n=%u and moduli up to %llu", n, (unsigned long long)qmax);
+  memset(info, 0, sizeof *info);
+  const KernelInfo& k = tch.kernels[0];
+  const int logn = __builtin_ctz(n);
+  info->candidates = (uint32_t)tch.kernels.size();
+  info->smem_bytes = (uint32_t)k.smem;
+  info->tmem_cols = (uint32_t)k.tmem_cols;
+  if (k.rns) {
+    RnsCfg rc;
+    rns_config(logn, (uint32_t)tch.rns_moduli.size(), &rc);
+    info->kernel = 3;
+    info->rns_moduli = (uint32_t)tch.rns_moduli.size();
+    info->digits_a = info->digits_b = 1;
+    info->shifts = rc.shifts;
+    info->slices = 1;
+    info->groups = rc.ngrp;
+  } else {
+    info->digit_bits = (uint32_t)tch.wb;
+    info->digits_a = ternary ? 1u : (uint32_t)tch.L;
+    info->digits_b = (uint32_t)tch.L;
+    if (k.tiled) {
+      TiledCfg tc;
+      toeplitz_tiled_config(logn, (int)info->digits_a, tch.L, &tc);
+      info->kernel = 2;
+      info->shifts = tc.shifts;
+      info->slices = tc.bpg;
+      info->groups = tc.ngrp;
+    } else {
+      info->kernel = 1;
+      info->shifts = 1;
+      info->slices = n / 1024;
+      info->groups = 0;
+    }
   }
   return POLYMUL_OK;
 }

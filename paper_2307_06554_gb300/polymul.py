@@ -52,6 +52,12 @@ class polymul_plan_info(ctypes.Structure):
                  "launch_flags", "ntt_mode", "regs", "cyclic", "tensor_groups", "rns_moduli")]
 
 
+class polymul_tensor_shape_info(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint32) for name in
+                ("kernel", "candidates", "digit_bits", "digits_a", "digits_b", "shifts", "slices", "groups",
+                 "rns_moduli", "smem_bytes", "tmem_cols")] + [("reserved", ctypes.c_uint32 * 5)]
+
+
 class polymul_desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("k", ctypes.c_uint32), ("prime_offset", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("offset", ctypes.c_uint64)]
@@ -91,6 +97,8 @@ def _load():
     lib.polymul_selftest_wait.restype = i32
     lib.polymul_tensor_rns_base.argtypes = [u32, u64, ctypes.POINTER(u32), u32, ctypes.POINTER(u32)]
     lib.polymul_tensor_rns_base.restype = i32
+    lib.polymul_tensor_shape.argtypes = [u32, u64, u32, ctypes.POINTER(polymul_tensor_shape_info)]
+    lib.polymul_tensor_shape.restype = i32
     lib.polymul_batch_static.argtypes = [u32, u64, vp, vp, vp, u64, vp]
     lib.polymul_batch_static.restype = i32
     lib.polymul_plan_select.argtypes = [vp, u32]
@@ -197,6 +205,14 @@ def polymul_selftest_wait(polls: int, stream=None) -> None:
     """Device check that a bounded wait gives up: raises PolymulError with
     POLYMUL_ETIMEOUT when it does (the expected outcome)."""
     _check(_lib.polymul_selftest_wait(polls, _stream(stream)))
+
+
+def polymul_tensor_shape(n: int, qmax: int, flags: int = 0) -> dict:
+    """The tensor path's default kernel for degree n and moduli up to qmax
+    (host only; no plan is created)."""
+    info = polymul_tensor_shape_info()
+    _check(_lib.polymul_tensor_shape(n, qmax, flags, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in polymul_tensor_shape_info._fields_ if name != "reserved"}
 
 
 def polymul_tensor_rns_base(n: int, qmax: int) -> list:
