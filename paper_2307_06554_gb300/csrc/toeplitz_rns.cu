@@ -16,17 +16,18 @@
 // every m_i once per row, as int8 planes (|r| <= (m-1)/2 <= 127).
 //
 // Per modulus m: the residues (as bf16, exact) form the same block-Hankel A
-// and block-Toeplitz B as toeplitz.cu
-// (Sec. 2.5 division, 8-coefficient blocks; A aliased onto a's residue
-// window with a 16-byte row stride), one MMA chain per 128-row block with
-// N = 16 (8 rows of residues, 8 of zero padding); n ((m-1)/2)^2 <= 2^24
-// keeps every fp32 partial sum an exact integer.  Work is cut as in
-// toeplitz_tiled.cu: a unit is one (product, prime, output group), K runs in
-// chunks; the steps (chunk, modulus) go round a ring of three shared-memory
-// stages, filled by four builder warps and drained by an MMA-issuing warp
+// and block-Toeplitz B as toeplitz.cu (Sec. 2.5 division, 8-coefficient
+// blocks; A aliased onto a's residue window with a 16-byte row stride); B
+// holds S copies of b's residues shifted by 1024 coefficients, so one A
+// slice yields S blocks of 1024 outputs (N = max(16, 8 S)); one MMA chain
+// per modulus; n ((m-1)/2)^2 <= 2^24 keeps every fp32 partial sum an exact
+// integer.  A unit is one (product, prime, group of S blocks), K runs in
+// chunks, a step is one modulus over one chunk.  Two pipelines, for the
+// moduli of even and of odd index, each with its own group of four builder
+// warps, its own two shared-memory stages and its own MMA-issuing warp
 // (mbarrier hand-offs both ways), so the tensor cores run one step's chains
 // while the next steps' operands are built (one CTA per SM, up to 512
-// accumulator columns: 16 per modulus and block).
+// accumulator columns: N per modulus).
 //
 // Epilogue (ConvertMatrix, by the CRT): for each output, the accumulator of
 // modulus i gives x mod m_i; with y_i = (x mod m_i) (M/m_i)^-1 mod m_i,

@@ -12,19 +12,22 @@
 // a~, b~ the antiperiodic (periodic) extensions.
 //
 // Sec. 2.6 (high degrees): the product is cut into pieces that fit the
-// matrix unit.  A unit of work is one (product, prime, output group): BPG
-// blocks of 128 rows of A (1024 outputs each; for n < 1024 one block whose
-// rows past n/8 compute outputs that are discarded), accumulated in tensor
-// memory over the K chunks [KC c, KC (c + 1)).  For each chunk the CTA
-// builds in shared memory
-//   * the window of a~'s digits that the chunk's rows read: row u of block
+// matrix unit.  A unit of work is one (product, prime, output group) of
+// blocks of 1024 outputs (128 rows of A each; for n < 1024 one block whose
+// rows past n/8 compute outputs that are discarded): either BPG
+// consecutive A slices (one chain per slice and digit of a), or, when b has
+// no more digits than a, one A slice against S copies of b shifted by 1024
+// coefficients in the B operand (template parameter S; the same A yields S
+// blocks), accumulated in tensor memory over the K chunks
+// [KC c, KC (c + 1)).  For each chunk the CTA builds in shared memory
+//   * the window of a~'s digits that the chunk's rows read: row u of slice
 //     bl starts 8 (128 bl + u) elements into it, so A is read through a
 //     descriptor with a 16-byte row stride, never materialised, and
 //   * the chunk's KC/8 K-blocks of B in the canonical K-major layout,
-// one thread issues the MMA chains (one per digit of a and per block), and
-// the CTA waits for them before it rebuilds the buffers.  Two CTAs share an
-// SM (at most 256 tensor-memory columns and about 110 KB of shared memory
-// each), so that one builds while the other's MMAs run.
+// one thread issues the MMA chains, and the CTA waits for them before it
+// rebuilds the buffers.  Two CTAs share an SM (at most 256 tensor-memory
+// columns and about 110 KB of shared memory each), so that one builds while
+// the other's MMAs run.
 //
 // Exactness: every digit has magnitude <= 2^(w-1) <= 128 (exact in bf16) and
 // n 2^(2w-2) <= 2^24 (the host chooses w so), so every fp32 partial sum over
