@@ -3,8 +3,10 @@ and K chunks, Sec. 2.6) against the CPU oracle: whole products where the
 oracle is quick, sampled coefficients at the largest degrees, every digit
 count 1 .. 5, both rings, extreme operands whose partial sums reach the
 exactness bound, batches that are not a multiple of the grid, the small-ring
-and RNS workloads on the tensor path, and the tiled kernel as the second
-tensor candidate at n = 1024 and 2048."""
+and RNS workloads on the tensor path, the tiled kernel beside the
+whole-product one at n = 1024 and 2048 (first at 2048, where it serves two
+blocks from one A slice), ternary b, and moduli at the digit-count
+boundaries."""
 import numpy as np
 import pytest
 
