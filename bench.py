@@ -762,8 +762,10 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     w = wl.ring_1024()
     n, batch, q_list = w.n, w.batch, w.q_list
-    # the autotuned kernel for this shape (tuning runs before the timed region)
-    plan = polymul.Plan(n, q_list, flags=polymul.FLAG_TUNE, tune_batch=batch)
+    # the autotuned kernel for this shape (tuning runs before the timed
+    # region); consecutive batches use different buffers, so each may start
+    # while the previous one drains (POLYMUL_FLAG_OVERLAP)
+    plan = polymul.Plan(n, q_list, flags=polymul.FLAG_TUNE | polymul.FLAG_OVERLAP, tune_batch=batch)
     info = plan.info
     assert info["path"] == polymul.PATH_NTT, "the roofline below describes the NTT kernel"
     elem = info["elem_bytes"]
@@ -804,8 +806,26 @@ def run_ours(args, ws, rank, local):
     # the dominant kernel's average launch duration over the timed region
     # (one launch per step, back to back on the launching stream)
     launch_ms = elapsed_ms / args.steps
-    # and, for reference, launches timed one at a time (each bracketed by
-    # its own events and a synchronisation, so each starts cold)
+    # the same kernel without the overlap (each batch waits for the previous
+    # one to complete before it starts), back to back, for reference
+    seq_plan = polymul.Plan(n, q_list, flags=polymul.FLAG_TUNE, tune_batch=batch)
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            a, b, c = sets[i % nsets]
+            polymul.polymul_batch(seq_plan.handle, a, b, c, batch, sp)
+    stream.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for i in range(args.steps):
+        a, b, c = sets[i % nsets]
+        polymul.polymul_batch(seq_plan.handle, a, b, c, batch, sp)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    no_overlap_ms = s0.elapsed_time(s1) / args.steps
+    seq_plan.close()
+    # and launches timed one at a time (each bracketed by its own events and
+    # a synchronisation, so each starts cold)
     per = []
     for i in range(min(args.steps, 20)):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -898,7 +918,9 @@ def run_ours(args, ws, rank, local):
             "peak_source": "derived: %d SMs x %d IMAD lanes x %.0f MHz / %d IMAD slots per Shoup mulmod" % (
                 sms, IMAD_LANES_PER_SM, sm_mhz, slots),
             "mulmods_per_launch": mulmods, "launch_ms": launch_ms,
-            "launch_ms_source": "CUDA events over the timed region / launches (one per step)",
+            "launch_ms_source": "CUDA events over the timed region / launches (one per step); consecutive "
+                                "launches overlap (POLYMUL_FLAG_OVERLAP: a batch starts while the previous drains)",
+            "no_overlap_launch_ms": no_overlap_ms,
             "isolated_launch_ms": isolated_ms,
             "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
                     "bytes_per_launch": bytes_alg, "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src}}
@@ -944,7 +966,10 @@ def run_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded uniform residues)",
         "config": {"workload": WORKLOAD, "path": {1: "ntt", 2: "tensor"}.get(info["path"], "?"),
                    "autotuned": {"candidates": info["candidates"], "radix_bits": info["radix_bits"],
-                                 "ntt_mode": MODE_NAMES[info["ntt_mode"]], "launch_flags": info["launch_flags"]},
+                                 "ntt_mode": MODE_NAMES[info["ntt_mode"]], "launch_flags": info["launch_flags"],
+                                 "exchange_pad": info["exchange_pad"], "one_operand": info["one_operand"],
+                                 "regs": info["regs"]},
+                   "overlap": "POLYMUL_FLAG_OVERLAP (each batch starts while the previous one drains)",
                    "n": n, "q": q_list, "batch": batch,
                    "l2": "inputs rotated over %d buffer sets (%.0f MB > 3x L2)" % (nsets, nsets * set_bytes / 2**20),
                    "parallelism": "replicas" if ws > 1 else "single"},

@@ -81,6 +81,25 @@ extern "C" {
                                      value does not fit one digit leaves its
                                      results invalid and makes
                                      polymul_plan_status return EDOMAIN     */
+#define POLYMUL_FLAG_OVERLAP 16u  /* let a batch on the NTT path start before
+                                     the previous kernel on its stream has
+                                     finished, when that kernel is a batch
+                                     launch of this library (any plan) that
+                                     writes none of this batch's operands and
+                                     reads or writes none of its results: the
+                                     new batch loads and multiplies its first
+                                     products while the previous one drains,
+                                     so back-to-back batches do not each pay
+                                     a fill and a drain.  Results and stream
+                                     order are otherwise unchanged.  The
+                                     caller guarantees one thing the library
+                                     cannot see: no kernel of the caller's
+                                     own that lets its dependents start early
+                                     (programmatic dependent launch) is
+                                     enqueued right before a batch and
+                                     produces that batch's a or b.  Ignored
+                                     on the legacy and per-thread default
+                                     streams                                */
 
 typedef struct polymul_opts {
     uint32_t path;        /* POLYMUL_PATH_*                                   */
@@ -109,7 +128,8 @@ typedef struct polymul_plan_info {
                              dependent launch (its CTAs start as the previous
                              kernel on the stream drains and wait for it to
                              complete before touching memory); set for the
-                             NTT batch kernels                              */
+                             NTT batch kernels.  Bit 2: POLYMUL_FLAG_OVERLAP
+                             is in effect for it                            */
     uint32_t ntt_mode;    /* NTT path: reduction mode of the main kernel:
                              0 = values in [0, 2q), 1 = [0, 4q) (Harvey),
                              2 = unreduced (small q)                        */
@@ -122,6 +142,12 @@ typedef struct polymul_plan_info {
                              output groups of up to 1024 coefficients each  */
     uint32_t rns_moduli;  /* tensor path, RNS kernel: small moduli in the
                              base (0 for the digit kernels)                 */
+    uint32_t exchange_pad;/* NTT path: shared-memory exchange layout of the
+                             main kernel: 0 = XOR swizzle, s > 0 = one
+                             padding word after every 2^s words             */
+    uint32_t one_operand; /* NTT path: 1 when the main kernel holds one
+                             operand in registers at a time (a's transform
+                             parked in shared memory during b's)            */
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */

@@ -20,6 +20,7 @@
 #include "kernels.h"
 #include "trace.h"
 #include "plan.h"
+#include "stream_order.h"
 #include "polymul_types.h"
 #include "toeplitz_rns.h"
 #include "toeplitz_tiled.h"
@@ -379,7 +380,7 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
         (lookup_ntt_cluster(4, 14, p->mode, &v) || lookup_ntt_cluster(4, 14, 1, &v)))
       rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
-    if (rc == POLYMUL_OK && p->elem == 8 && lookup_ntt_u64_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
+    if (rc == POLYMUL_OK && p->logn < 14 && lookup_ntt_alt(p->elem, (int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) rc = add_tensor_candidates(add_candidate);
   }
   if (rc == POLYMUL_OK) apply_candidate(p, 0);
@@ -453,11 +454,14 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->tuned = p->tuned ? 1u : 0u;
   info->tuned_batch = (uint32_t)p->tuned_batch;
   info->launch_flags = p->launch_flags;
+  if ((p->launch_flags & kLaunchPdl) && (p->flags & POLYMUL_FLAG_OVERLAP)) info->launch_flags |= 4u;
   info->ntt_mode = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.mode : 0u;
   info->regs = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.regs : 0u;
   info->cyclic = p->cyclic ? 1u : 0u;
   info->tensor_groups = 0;
   info->rns_moduli = p->path == POLYMUL_PATH_TENSOR && p->ki.rns ? p->rns_r : 0;
+  info->exchange_pad = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.pad : 0u;
+  info->one_operand = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.seq : 0u;
   if (p->path == POLYMUL_PATH_TENSOR && p->ki.rns) {
     RnsCfg rc;
     if (rns_config((int)p->logn, p->rns_r, &rc)) info->tensor_groups = rc.ngrp;
@@ -644,18 +648,36 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
                          units, p->k, p->cyclic ? 0u : 0x80008000u, ctr, p->d_err};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernel(p->ki.fn, grid, p->ki.block, argv, p->ki.smem, st));
-  } else if (p->elem == 4) {
-    NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
-                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err,
-                                (const uint32_t*)p->d_outer, nullptr, p->n, 1, 0};
-    void* argv[] = {&args};
-    return launch(argv);
   } else {
-    NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
-                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err,
-                                (const uint64_t*)p->d_outer, nullptr, p->n, 1, 0};
-    void* argv[] = {&args};
-    return launch(argv);
+    // the batch kernel: record its footprint for the next launch on this
+    // stream, and let it run ahead of the previous one where that is safe
+    // (stream_order.h); the cluster kernel takes no dependent launch
+    const uintptr_t bytes = (uintptr_t)(units * p->n * p->elem);
+    LaunchFootprint fp;
+    fp.a_lo = (uintptr_t)a, fp.a_hi = (uintptr_t)a + bytes;
+    fp.b_lo = (uintptr_t)b, fp.b_hi = (uintptr_t)b + bytes;
+    fp.c_lo = (uintptr_t)c, fp.c_hi = (uintptr_t)c + bytes;
+    StreamOrderGuard order(p->device, st);
+    const bool pdl = p->ki.cluster == 0 && (p->launch_flags & kLaunchPdl);
+    const uint32_t early = pdl && (p->flags & POLYMUL_FLAG_OVERLAP) && order.may_run_ahead(fp) ? 1u : 0u;
+    int r;
+    if (p->elem == 4) {
+      NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
+                                  (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err,
+                                  (const uint32_t*)p->d_outer, nullptr, p->n, 1, 0, early};
+      void* argv[] = {&args};
+      r = launch(argv);
+    } else {
+      NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
+                                  (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err,
+                                  (const uint64_t*)p->d_outer, nullptr, p->n, 1, 0, early};
+      void* argv[] = {&args};
+      r = launch(argv);
+    }
+    // a failed launch enqueued nothing; a cluster launch lets its successor
+    // start only at completion, but recording it is harmless
+    if (r == POLYMUL_OK) order.record(&fp);
+    return r;
   }
   return POLYMUL_OK;
 }

@@ -16,6 +16,8 @@ struct KernelInfo {
   int rb = 0;                // NTT: stage bits per register pass
   int mode = 0;              // NTT: reduction mode (0..2, see ntt.cuh)
   int regs = 0;              // NTT: register budget per thread
+  int pad = 0;               // NTT: exchange layout (0 XOR swizzle, s > 0 one padding word per 2^s)
+  int seq = 0;               // NTT: 1 = one operand in registers at a time
   int tiled = 0;             // tensor path: 1 for k_toeplitz_tiled (output groups, K chunks)
   int rns = 0;               // tensor path: 1 for k_toeplitz_rns (residues of small moduli)
 };
@@ -32,7 +34,10 @@ bool lookup_ntt_u32_aux_rb2(int logn, KernelInfo* ki);  // the same with radix-4
 // autotuner candidates: other register radices (RB = stage bits per pass)
 bool lookup_ntt_u32_rb5(int logn, int mode, KernelInfo* ki);  // logn 9..13, modes 1, 2; logn 14, modes 0..2
 bool lookup_ntt_u32_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, modes 1, 2
-bool lookup_ntt_u64_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, mode 1
+// the alternative shape of the default kernel's measurements (the other
+// layout / operand scheme): 32-bit words, modes 1, 2, logn 5..13; 64-bit
+// words, mode 1, logn 6..12
+bool lookup_ntt_alt(uint32_t elem, int logn, int mode, KernelInfo* ki);
 
 // shared-operand products on the NTT path: a's transform once per prime
 // (prep), then forward(b), pointwise, inverse per product (32-bit words,

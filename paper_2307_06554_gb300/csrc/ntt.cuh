@@ -60,22 +60,31 @@ __device__ __forceinline__ TwPair<W> ldtw(const TwPair<W>* p) {
   }
 }
 
-template <typename W_, int LOGN_, int RB_>
+// PAD_ selects the exchange layout: 0 = the XOR swizzle spos (a bijection
+// of [0, n)), s > 0 = word j at j + (j >> s), one padding word after every
+// 2^s.  The padded position is additive over any split of j's bits, so a
+// thread's exchange addresses are one base register per layout plus
+// immediate offsets; the swizzle needs one register (or one XOR) per
+// coefficient.
+template <typename W_, int LOGN_, int RB_, int PAD_ = 0>
 struct Shape {
   using W = W_;
   static constexpr int LOGN = LOGN_;
   static constexpr int RB = RB_;                // stage bits per phase
+  static constexpr int PAD = PAD_;
   static constexpr int RLOG = LOGN < RB ? LOGN : RB;
   static constexpr int R = 1 << RLOG;           // values per thread per operand
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N / R;               // threads per unit (team size)
   static constexpr int NPH = (LOGN + RB - 1) / RB;
-  static constexpr int SLICE = N;              // words per operand buffer
+  static constexpr int ALIGN_WORDS = 16 / (int)sizeof(W);
+  // words per operand buffer
+  static constexpr int SLICE =
+      PAD == 0 ? N : (N + (N >> PAD) + ALIGN_WORDS - 1) / ALIGN_WORDS * ALIGN_WORDS;
   // two buffers per team (a and b): they receive the staged operands, then
   // serve the exchanges.  Teams that share a warp are offset by T words
   // (rounded up to 16 bytes, the bulk-copy alignment) so that their lanes
   // fall in different banks.
-  static constexpr int ALIGN_WORDS = 16 / (int)sizeof(W);
   static constexpr int TEAM_PAD = T < 32 ? (T + ALIGN_WORDS - 1) / ALIGN_WORDS * ALIGN_WORDS : 0;
   static constexpr int SMEM_WORDS = 2 * SLICE + TEAM_PAD;
   static_assert((SMEM_WORDS * sizeof(W)) % 16 == 0, "team buffers must stay 16-byte aligned");
@@ -106,6 +115,15 @@ __device__ __forceinline__ uint32_t elem_index(int e, uint32_t t) {
 // conflicts.
 template <int RB>
 __device__ __forceinline__ uint32_t spos(uint32_t j) { return j ^ ((j >> 1) & 31u) ^ ((j >> RB) & 31u); }
+
+// exchange position of coefficient j in a team buffer of shape S
+template <class S>
+__device__ __forceinline__ uint32_t xpos(uint32_t j) {
+  if constexpr (S::PAD > 0)
+    return j + (j >> S::PAD);
+  else
+    return spos<S::RB>(j);
+}
 
 // ---------------------------------------------------------------- butterflies
 // Reduction modes (chosen per plan from the largest modulus, see
@@ -293,20 +311,39 @@ __device__ __forceinline__ void inv_phase(W (&x)[S::R], const TwPair<W>* __restr
   inv_phase_n<S, MODE, P, false>(x, x, tw, pc, t);
 }
 
+// elem_index(e, t) is the bitwise OR of elem_index(e, 0) and elem_index(0, t)
+// (disjoint bits: t < T), so with the padded layout a position is a
+// per-thread base plus a compile-time offset.
 template <class S, int P, typename W = typename S::W>
 __device__ __forceinline__ void store_layout(const W (&x)[S::R], W* s, uint32_t t) {
-  sfor<0, S::R>([&](auto ec) {
-    constexpr int e = decltype(ec)::value;
-    s[spos<S::RB>(elem_index<S, P>(e, t))] = x[e];
-  });
+  if constexpr (S::PAD > 0) {
+    W* sb = s + xpos<S>(elem_index<S, P>(0, t));
+    sfor<0, S::R>([&](auto ec) {
+      constexpr int e = decltype(ec)::value;
+      sb[xpos<S>(elem_index<S, P>(e, 0))] = x[e];
+    });
+  } else {
+    sfor<0, S::R>([&](auto ec) {
+      constexpr int e = decltype(ec)::value;
+      s[xpos<S>(elem_index<S, P>(e, t))] = x[e];
+    });
+  }
 }
 
 template <class S, int P, typename W = typename S::W>
 __device__ __forceinline__ void load_layout(W (&x)[S::R], const W* s, uint32_t t) {
-  sfor<0, S::R>([&](auto ec) {
-    constexpr int e = decltype(ec)::value;
-    x[e] = s[spos<S::RB>(elem_index<S, P>(e, t))];
-  });
+  if constexpr (S::PAD > 0) {
+    const W* sb = s + xpos<S>(elem_index<S, P>(0, t));
+    sfor<0, S::R>([&](auto ec) {
+      constexpr int e = decltype(ec)::value;
+      x[e] = sb[xpos<S>(elem_index<S, P>(e, 0))];
+    });
+  } else {
+    sfor<0, S::R>([&](auto ec) {
+      constexpr int e = decltype(ec)::value;
+      x[e] = s[xpos<S>(elem_index<S, P>(e, t))];
+    });
+  }
 }
 
 // Exchange buffers may also be spread over the CTAs of a cluster: any type
@@ -327,16 +364,60 @@ __device__ __forceinline__ void load_layout(W (&x)[S::R], const CB& s, uint32_t 
   });
 }
 
+// ---------------------------------------------------------------- exchanges
+// Barriers of an exchange (stores in layout P, then loads in layout Q).
+//  * Before the stores: a thread stores exactly at the positions it loaded
+//    in layout P, so nothing is overwritten that another thread has still to
+//    read -- except in the first exchange of a transform, whose buffer held
+//    the staged operand at unswizzled positions.  Only that one needs the
+//    team barrier first.
+//  * Between stores and loads: when every warp holds the same coefficients
+//    in layouts P and Q (the team-thread bits that select the warp land on
+//    the same coefficient bits in both), each warp reads only what it wrote,
+//    and a warp barrier orders the exchange.  Otherwise the team barrier.
+// Exchange buffers spread over a cluster keep the cluster barrier at both
+// points.
+template <class B, class = void>
+struct is_cluster_buf : std::false_type {};
+template <class B>
+struct is_cluster_buf<B, std::void_t<decltype(B::kCluster)>> : std::bool_constant<B::kCluster> {};
+
+// coefficient-index bit that team-thread bit b occupies in layout P
+template <class S, int P>
+constexpr int tbit_pos(int b) {
+  return b < PhaseBits<S, P>::LO ? b : b - PhaseBits<S, P>::LO + PhaseBits<S, P>::HI;
+}
+
+template <class S, int P, int Q>
+constexpr bool warp_local() {
+  for (int b = 5; (1 << b) < S::T; ++b)
+    if (tbit_pos<S, P>(b) != tbit_pos<S, Q>(b)) return false;
+  return true;
+}
+
+template <bool FIRST, class B, class Sync>
+__device__ __forceinline__ void xsync_pre(Sync sync) {
+  if constexpr (FIRST || is_cluster_buf<B>::value) sync();
+}
+
+template <class S, int P, int Q, class B, class Sync>
+__device__ __forceinline__ void xsync_mid(Sync sync) {
+  if constexpr (!is_cluster_buf<B>::value && warp_local<S, P, Q>())
+    __syncwarp();
+  else
+    sync();
+}
+
 template <class S, int MODE, int P, class Sync, class B, typename W = typename S::W>
 __device__ __forceinline__ void fwd_from(W (&xa)[S::R], W (&xb)[S::R], B sa, B sb,
                                          const TwPair<W>* __restrict__ tw, const PrimeConst<W>& pc,
                                          uint32_t t, Sync sync) {
   fwd_phase2<S, MODE, P>(xa, xb, tw, pc, t);
   if constexpr (P > 0) {
-    sync();
+    xsync_pre<P == S::NPH - 1, B>(sync);
     store_layout<S, P>(xa, sa, t);
     store_layout<S, P>(xb, sb, t);
-    sync();
+    xsync_mid<S, P, P - 1, B>(sync);
     load_layout<S, P - 1>(xa, sa, t);
     load_layout<S, P - 1>(xb, sb, t);
     fwd_from<S, MODE, P - 1>(xa, xb, sa, sb, tw, pc, t, sync);
@@ -349,25 +430,27 @@ __device__ __forceinline__ void fwd_from1(W (&x)[S::R], B s, const TwPair<W>* __
                                           const PrimeConst<W>& pc, uint32_t t, Sync sync) {
   fwd_phase<S, MODE, P, false>(x, x, tw, pc, t);
   if constexpr (P > 0) {
-    sync();
+    xsync_pre<P == S::NPH - 1, B>(sync);
     store_layout<S, P>(x, s, t);
-    sync();
+    xsync_mid<S, P, P - 1, B>(sync);
     load_layout<S, P - 1>(x, s, t);
     fwd_from1<S, MODE, P - 1>(x, s, tw, pc, t, sync);
   }
 }
 
 // `hook` runs once the team has finished reading the exchange buffers for
-// the last time in this unit (after the last exchange), so that the buffers
-// can receive the next unit's operands.
+// the last time in this unit (after the last exchange, behind a team
+// barrier), so that the buffers can receive the next unit's operands.  The
+// buffer was last read in layout 0 by the forward transform (same positions
+// as the first stores here).
 template <class S, int MODE, int P, class Sync, class Hook, class B, typename W = typename S::W>
 __device__ __forceinline__ void inv_from(W (&x)[S::R], B s, const TwPair<W>* __restrict__ tw,
                                          const PrimeConst<W>& pc, uint32_t t, Sync sync, Hook&& hook) {
   inv_phase<S, MODE, P>(x, tw, pc, t);
   if constexpr (P + 1 < S::NPH) {
-    sync();
+    xsync_pre<false, B>(sync);
     store_layout<S, P>(x, s, t);
-    sync();
+    xsync_mid<S, P, P + 1, B>(sync);
     load_layout<S, P + 1>(x, s, t);
     if constexpr (P + 2 == S::NPH) {
       sync();
@@ -384,10 +467,10 @@ __device__ __forceinline__ void inv_from2(W (&x)[S::R], W (&y)[S::R], B sx, B sy
                                           const PrimeConst<W>& pc, uint32_t t, Sync sync, Hook&& hook) {
   inv_phase_n<S, MODE, P, true>(x, y, tw, pc, t);
   if constexpr (P + 1 < S::NPH) {
-    sync();
+    xsync_pre<false, B>(sync);
     store_layout<S, P>(x, sx, t);
     store_layout<S, P>(y, sy, t);
-    sync();
+    xsync_mid<S, P, P + 1, B>(sync);
     load_layout<S, P + 1>(x, sx, t);
     load_layout<S, P + 1>(y, sy, t);
     if constexpr (P + 2 == S::NPH) {
@@ -460,6 +543,82 @@ __device__ __forceinline__ void polymul_unit(W* __restrict__ c, const TwPair<W>*
   }
 }
 
+// The same unit with one operand in registers at a time: a's forward
+// transform, its result parked in a's staging buffer in a thread-private
+// order (word e*T + t, conflict-free), then b's forward transform, the
+// pointwise product against the parked values, and the inverse.  Half the
+// live coefficient registers of polymul_unit, so twice the units fit on an
+// SM at the same register budget; costs one store and one load per
+// coefficient of a and separate twiddle loads for the two forward
+// transforms.
+template <class S, int MODE, bool AUX, class Sync, class Hook, typename W = typename S::W>
+__device__ __forceinline__ void polymul_unit_seq(W* __restrict__ c, const TwPair<W>* __restrict__ twf,
+                                                 const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
+                                                 W* sa, W* sb, uint32_t t, bool act, Sync sync, Hook&& hook,
+                                                 W qo = 0) {
+  constexpr int TOP = S::NPH - 1;
+  W x[S::R];
+  const W lift = pc.q - qo, half = qo >> 1;
+  auto load_top = [&](const W* s) {
+    sfor<0, S::R>([&](auto ec) {
+      constexpr int e = decltype(ec)::value;
+      x[e] = s[elem_index<S, TOP>(e, t)];
+      if constexpr (AUX) x[e] = x[e] > half ? x[e] + lift : x[e];
+    });
+  };
+  load_top(sa);
+  fwd_from1<S, MODE, TOP>(x, sa, twf, pc, t, sync);
+  if constexpr (S::NPH > 1) sync();  // every exchange read of sa is done
+  sfor<0, S::R>([&](auto ec) {
+    constexpr int e = decltype(ec)::value;
+    sa[e * S::T + t] = x[e];
+  });
+  load_top(sb);
+  fwd_from1<S, MODE, TOP>(x, sb, twf, pc, t, sync);
+  sfor<0, S::R>([&](auto ec) {
+    constexpr int e = decltype(ec)::value;
+    const W y = sa[e * S::T + t];
+    if constexpr (MODE == kSmall) {
+      x[e] = montmul(y, x[e], pc.q, pc.qinv);
+    } else if constexpr (MODE == kL4) {
+      x[e] = csub(montmul(y, x[e], pc.q, pc.qinv), pc.q2);
+    } else {
+      x[e] = montmul(csub(y, pc.q), csub(x[e], pc.q), pc.q, pc.qinv);
+    }
+  });
+  if constexpr (S::NPH == 1) {
+    sync();
+    hook();
+  }
+  inv_from<S, MODE, 0>(x, sb, twi, pc, t, sync, hook);
+  if (act) {
+    sfor<0, S::R>([&](auto ec) {
+      constexpr int e = decltype(ec)::value;
+      W y = csub(x[e], pc.q);
+      if constexpr (AUX) {
+        if (y > (pc.q >> 1)) {
+          const W r = (pc.q - y) % qo;
+          y = r ? qo - r : W(0);
+        } else {
+          y = y % qo;
+        }
+      }
+      c[elem_index<S, TOP>(e, t)] = y;
+    });
+  }
+}
+
+template <class S, int MODE, bool AUX, bool SEQ, class Sync, class Hook, typename W = typename S::W>
+__device__ __forceinline__ void polymul_unit_any(W* __restrict__ c, const TwPair<W>* __restrict__ twf,
+                                                 const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
+                                                 W* sa, W* sb, uint32_t t, bool act, Sync sync, Hook&& hook,
+                                                 W qo = 0) {
+  if constexpr (SEQ)
+    polymul_unit_seq<S, MODE, AUX>(c, twf, twi, pc, sa, sb, t, act, sync, hook, qo);
+  else
+    polymul_unit<S, MODE, AUX>(c, twf, twi, pc, sa, sb, t, act, sync, hook, qo);
+}
+
 struct WarpSync {
   __device__ __forceinline__ void operator()() const { __syncwarp(); }
 };
@@ -491,7 +650,8 @@ constexpr int ntt_block() {
 // compiler must honour).
 // AUX: auxiliary-prime mode (see polymul_unit); every unit then uses the
 // single NTT prime pc[0] and the ring modulus outer_q[u % k].
-template <class S, int MODE, int WARPS, int REGS, bool AUX = false>
+// SEQ: one operand in registers at a time (polymul_unit_seq).
+template <class S, int MODE, int WARPS, int REGS, bool AUX = false, bool SEQ = false>
 __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, WARPS>() * REGS))
     k_ntt_batch(NttBatchArgs<typename S::W> args) {
   using W = typename S::W;
@@ -504,9 +664,25 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
   const uint32_t k = args.k;
   unsigned long long* ctr = args.ctr;
   constexpr uint32_t ROW = S::N * (uint32_t)sizeof(W);
-  // every CTA of this grid is resident from the start (persistent grid), so
-  // the next kernel may claim SM resources as soon as CTAs of this one exit
-  griddep_launch_dependents();
+  // Ordering against the previous kernel on the stream (programmatic
+  // dependent launch).  The wait blocks until that kernel has completed and
+  // its writes are visible; only then does this grid let the next kernel
+  // start (so that, when the next kernel starts, everything before this one
+  // is complete).  With args.early the host has checked that the previous
+  // kernel is one of this library's batch launches that writes no operand
+  // of this launch and touches none of its results: every team then loads
+  // and multiplies its first unit before the wait, and waits only before
+  // its first use of the work counter.
+  const bool early = args.early != 0;
+  bool waited = false;
+  auto order = [&]() {  // every thread of the CTA, at the same point
+    if (!waited) {
+      griddep_wait();
+      griddep_launch_dependents();
+      waited = true;
+    }
+  };
+  if (!early) order();
   if constexpr (S::T <= 32) {
     constexpr int TPW = 32 / S::T;  // teams per warp
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -518,9 +694,11 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     if (lane == 0) mbar_init(bar, 1);
     fence_mbar_init();
     __syncwarp();
-    auto grab = [&]() {
+    const unsigned long long first_round = (unsigned long long)gridDim.x * WARPS * TPW;
+    auto grab = [&]() {  // every lane of the warp
+      order();
       unsigned long long v = 0;
-      if (lane == 0) v = atomicAdd(ctr, (unsigned long long)TPW);
+      if (lane == 0) v = first_round + atomicAdd(ctr, (unsigned long long)TPW);
       return __shfl_sync(0xffffffffu, v, 0);
     };
     auto issue = [&](unsigned long long base) {  // lane 0 only
@@ -534,8 +712,9 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       }
     };
     uint32_t parity = 0;
-    griddep_wait();  // the work counter, operands and results of the previous kernel
-    unsigned long long cur = grab();
+    // first units by position (no atomic on the critical path at start-up),
+    // later ones from the counter, offset by the units handed out that way
+    unsigned long long cur = ((unsigned long long)blockIdx.x * WARPS + warp) * TPW;
     if (lane == 0 && cur < units) issue(cur);
     while (cur < units) {
       const bool ok = mbar_wait(bar, parity);
@@ -556,12 +735,16 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
         nxt = grab();
         if (lane == 0 && nxt < units) issue(nxt);
       };
-      polymul_unit<S, MODE, AUX>(args.c + (act ? (size_t)u * S::N : 0), twf + (size_t)pj * args.tw_stride,
-                                 twi + (size_t)pj * args.tw_stride, pc, sa, sb, t, act, WarpSync{}, hook, qo);
+      polymul_unit_any<S, MODE, AUX, SEQ>(args.c + (act ? (size_t)u * S::N : 0), twf + (size_t)pj * args.tw_stride,
+                                          twi + (size_t)pj * args.tw_stride, pc, sa, sb, t, act, WarpSync{}, hook,
+                                          qo);
       cur = nxt;
     }
+    order();
+    // no fence: the next launch that uses the counter is ordered after this
+    // kernel's completion, and every grab above returned before its team
+    // got here
     if (lane == 0) {
-      __threadfence();
       const unsigned long long teams = (unsigned long long)gridDim.x * WARPS;
       if (atomicAdd(ctr + 1, 1ull) == teams - 1) {
         atomicExch(ctr, 0ull);
@@ -575,15 +758,16 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     uint64_t* bar = &mbar[0];
     if (threadIdx.x == 0) mbar_init(bar, 1);
     fence_mbar_init();
-    griddep_wait();  // the work counter, operands and results of the previous kernel
     auto issue = [&](unsigned long long u) {  // thread 0 only
       fence_proxy_async();
       mbar_arrive_expect_tx(bar, 2 * ROW);
       bulk_g2s(sa, args.a + (size_t)u * S::N, ROW, bar);
       bulk_g2s(sb, args.b + (size_t)u * S::N, ROW, bar);
     };
+    // first unit by position, later ones from the counter (see above)
+    const unsigned long long first_round = gridDim.x;
     if (threadIdx.x == 0) {
-      s_next = atomicAdd(ctr, 1ull);
+      s_next = blockIdx.x;
       if (s_next < units) issue(s_next);
     }
     __syncthreads();
@@ -601,20 +785,21 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       const uint32_t pj = AUX ? 0u : (args.pmap ? args.pmap[j] : j);
       const PrimeConst<W> pc = args.pc[(size_t)pj * args.pc_stride + args.pc_off];
       const W qo = AUX ? args.outer_q[j] : W(0);
-      auto hook = [&]() {  // called after a barrier: every thread is done with sa/sb
+      auto hook = [&]() {  // every thread, after a barrier: all are done with sa/sb
+        order();
         if (threadIdx.x == 0) {
-          s_next = atomicAdd(ctr, 1ull);
+          s_next = first_round + atomicAdd(ctr, 1ull);
           if (s_next < units) issue(s_next);
         }
       };
-      polymul_unit<S, MODE, AUX>(args.c + (size_t)cur * S::N, twf + (size_t)pj * args.tw_stride,
-                                 twi + (size_t)pj * args.tw_stride, pc, sa, sb, threadIdx.x, true, BlockSync{}, hook,
-                                 qo);
+      polymul_unit_any<S, MODE, AUX, SEQ>(args.c + (size_t)cur * S::N, twf + (size_t)pj * args.tw_stride,
+                                          twi + (size_t)pj * args.tw_stride, pc, sa, sb, threadIdx.x, true,
+                                          BlockSync{}, hook, qo);
       __syncthreads();
       cur = s_next;
     }
+    order();
     if (threadIdx.x == 0) {
-      __threadfence();
       if (atomicAdd(ctr + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
         atomicExch(ctr, 0ull);
         atomicExch(ctr + 1, 0ull);

@@ -1,0 +1,7 @@
+// k_ntt_batch alternative shapes, 32-bit words, reduction mode 2: the shape
+// the default was measured against at each degree (autotuner candidates).
+#include "ntt_alt.cuh"
+
+namespace pm {
+bool lookup_ntt_alt_u32_m2(int logn, KernelInfo* ki) { return ntt_alt_u32<2>(logn, ki); }
+}  // namespace pm

@@ -51,8 +51,10 @@ __global__ void __launch_bounds__(S::T) k_ntt_prep(NttSharedArgs<typename S::W> 
   W* s = reinterpret_cast<W*>(smem_raw);
   constexpr int TOP = S::NPH - 1;
   const uint32_t j = blockIdx.x, t = threadIdx.x;
-  griddep_launch_dependents();  // the product kernel may come up meanwhile
   griddep_wait();               // a and the previous kernel's results
+  // only now may the next kernel start: when it does, everything before this
+  // one is complete
+  griddep_launch_dependents();
   if (j >= args.units) return;
   const W* a = args.a + (size_t)j * S::N;
   W x[S::R];
@@ -92,10 +94,10 @@ __global__ void __launch_bounds__(S::T, 65536 / (S::T * 128)) k_ntt_shared(NttSh
   constexpr uint32_t ROW = S::N * (uint32_t)sizeof(W);
   const uint32_t t = threadIdx.x;
   const uint64_t pairs = args.units, k = args.k, batch = args.batch;
-  griddep_launch_dependents();
   if (t == 0) mbar_init(&mbar, 1);
   fence_mbar_init();
   griddep_wait();  // the counter, operands and results of the previous kernel
+  griddep_launch_dependents();  // after the wait (see k_ntt_prep)
   auto rows = [&](unsigned long long v, uint64_t& r0, uint64_t& r1, bool& second) {
     const uint64_t j = v % k, p0 = 2 * (v / k);
     second = p0 + 1 < batch;

@@ -26,7 +26,7 @@ bool lookup_ntt_u32_aux_rb2(int logn, KernelInfo* ki) {
   switch (logn) {
 #define PM_CASE(L)                              \
   case L:                                       \
-    *ki = ntt_info<uint32_t, L, 0, true, 2>();  \
+    *ki = ntt_info_rb<uint32_t, L, 0, true, 2>();  \
     return true;
     PM_CASE(7) PM_CASE(8) PM_CASE(9) PM_CASE(10)
 #undef PM_CASE

@@ -9,7 +9,7 @@ namespace pm {
 bool lookup_ntt_u32_rb5(int logn, int mode, KernelInfo* ki) {
 #define PM_V(L, M)                                  \
   if (logn == L && mode == M) {                     \
-    *ki = ntt_info<uint32_t, L, M, false, 5>();     \
+    *ki = ntt_info_rb<uint32_t, L, M, false, 5>();     \
     return true;                                    \
   }
   PM_V(9, 1) PM_V(10, 1) PM_V(11, 1) PM_V(12, 1) PM_V(13, 1)

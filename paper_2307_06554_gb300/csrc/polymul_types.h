@@ -39,6 +39,10 @@ struct NttBatchArgs {
   uint32_t tw_stride;
   uint32_t pc_stride;
   uint32_t pc_off;
+  // 1: the previous kernel on the stream is a batch launch of this library
+  // that writes none of a, b and touches none of c (checked by the host), so
+  // each team may load and multiply its first unit before waiting for it
+  uint32_t early;
 };
 
 // Ragged (uneven) batches: one unit = one (product, prime) row of n words.

@@ -29,6 +29,7 @@
 #include "kernels.h"
 #include "trace.h"
 #include "plan.h"
+#include "stream_order.h"
 #include "polymul_types.h"
 #include "tcgen05.cuh"
 
@@ -380,6 +381,11 @@ static int shared_ntt(polymul_plan* p, const void* a, const void* b, void* c, ui
   NttSharedArgs<uint32_t> pa{(const uint32_t*)a, nullptr, ahat, p->d_twf, p->d_twi, pc, p->k, 0, p->k, p->n, nullptr,
                              p->d_err};
   void* argv_p[] = {&pa};
+  // both kernels let the next one on the stream start once they run; their
+  // footprint includes plan scratch, so record it as unknown: the next batch
+  // launch on the stream then waits for them in full (stream_order.h)
+  StreamOrderGuard order(p->device, st);
+  order.record(nullptr);
   int rc2 = pdl_launch(prep.fn, (int)p->k, prep.block, prep.smem, argv_p, st);
   if (rc2 != POLYMUL_OK) return rc2;
   int per_sm = 0;

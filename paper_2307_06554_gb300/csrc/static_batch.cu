@@ -36,6 +36,7 @@
 #include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
+#include "stream_order.h"
 
 using namespace pm;
 
@@ -178,6 +179,15 @@ extern "C" int polymul_batch_static(uint32_t n, uint64_t q, const void* a, const
                               1u,
                               0u};
   void* argv[] = {&args};
+  // the kernel lets the next one on the stream start once it is running:
+  // record what it reads and writes (stream_order.h)
+  const uintptr_t bytes = (uintptr_t)(batch * n * 4);
+  LaunchFootprint fp;
+  fp.a_lo = (uintptr_t)a, fp.a_hi = (uintptr_t)a + bytes;
+  fp.b_lo = (uintptr_t)b, fp.b_hi = (uintptr_t)b + bytes;
+  fp.c_lo = (uintptr_t)c, fp.c_hi = (uintptr_t)c + bytes;
+  StreamOrderGuard order(dev, st);
   PM_CUDA(cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st));
+  order.record(&fp);
   return POLYMUL_OK;
 }

@@ -30,6 +30,7 @@ FLAG_VALIDATE = 1
 FLAG_TUNE = 2
 FLAG_CYCLIC = 4  # the ring Z_q[x]/(x^n-1) instead of Z_q[x]/(x^n+1)
 FLAG_TERNARY_B = 8  # b in {0, 1, q-1}: the tensor path takes b as one digit (c = b * T(a))
+FLAG_OVERLAP = 16  # a batch may start while the previous batch launch on its stream drains
 
 _ERRNAMES = {1: "EINVAL", 2: "ENOTSUP", 3: "EDOMAIN", 4: "ENOMEM", 5: "ETIMEOUT", 6: "ECUDA"}
 
@@ -49,7 +50,8 @@ class polymul_plan_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
                  "digit_bits", "digits", "radix_bits", "candidates", "tuned", "tuned_batch",
-                 "launch_flags", "ntt_mode", "regs", "cyclic", "tensor_groups", "rns_moduli")]
+                 "launch_flags", "ntt_mode", "regs", "cyclic", "tensor_groups", "rns_moduli",
+                 "exchange_pad", "one_operand")]
 
 
 class polymul_tensor_shape_info(ctypes.Structure):
