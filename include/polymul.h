@@ -263,12 +263,25 @@ int polymul_plan_status(polymul_plan *plan, void *stream);
  * the library holds until the process exits.  Every call shares that array:
  * calls whose kernels may overlap on the GPU race (issue them on one stream
  * or order them with events); tables are refreshed only when (n, q) changes,
- * and the work counter is cleared on every call.  The first call on a device
- * looks up the array's device address; make it before any stream capture.
- * Asynchronous like polymul_batch.  Errors: EINVAL, ENOTSUP, ECUDA.
+ * and the work counter and error word are cleared on every call.  The first
+ * call on a device looks up the array's device address; make it before any
+ * stream capture.  Asynchronous like polymul_batch.  Errors: EINVAL,
+ * ENOTSUP, ECUDA; a bounded device wait that expired is reported by
+ * polymul_static_status.
  */
 int polymul_batch_static(uint32_t n, uint64_t q, const void *a, const void *b, void *c,
                          uint64_t batch, void *stream);
+
+/*
+ * polymul_static_status -- synchronise `stream`, then report whether the
+ * kernel of the most recent polymul_batch_static call on the current device
+ * abandoned a bounded device wait (POLYMUL_ETIMEOUT: its results are
+ * invalid; the word is cleared).  Call it after that call and before the
+ * next one (each call clears the word).  Allocates nothing, like the call
+ * it checks.  POLYMUL_OK when no call has run on the device yet.  Errors:
+ * ETIMEOUT, ENOTSUP (device ordinal >= 64), ECUDA.
+ */
+int polymul_static_status(void *stream);
 
 /*
  * polymul_tune -- choose the plan's kernel by measurement (the paper leaves
@@ -437,9 +450,13 @@ int polymul_server_create(const uint64_t *pool, uint32_t pool_size, uint32_t n_m
                           uint64_t device_bytes, uint32_t lanes, polymul_server **out);
 /* Queue one request (asynchronous); *ticket identifies it. */
 int polymul_server_submit(polymul_server *srv, const polymul_request *req, uint64_t *ticket);
-/* *done = 1 once the result is in req->c (the ticket is then released). */
+/* *done = 1 once the result is in req->c (the ticket is then released).  A
+ * request that failed releases its ticket and returns its error: ETIMEOUT
+ * when a bounded device wait of its kernel expired (c is invalid), ECUDA for
+ * a CUDA error. */
 int polymul_server_poll(polymul_server *srv, uint64_t ticket, int *done);
-/* Block until the request completes; ETIMEOUT after timeout_s seconds. */
+/* Block until the request completes; its failure as for polymul_server_poll,
+ * or ETIMEOUT after timeout_s seconds with the request still pending. */
 int polymul_server_wait(polymul_server *srv, uint64_t ticket, double timeout_s);
 /* Load generator: submit reqs[i] at arrival_s[i] seconds after the call,
  * wait for all, and store each submit-to-completion latency (microseconds)
@@ -462,6 +479,21 @@ void polymul_server_destroy(polymul_server *srv);
  * range, ECUDA otherwise.  Synchronises `stream`.
  */
 int polymul_selftest_wait(uint32_t polls, void *stream);
+
+/*
+ * polymul_selftest_inject_wait -- diagnostics (the paper has no counterpart).
+ * The next `launches` launches of the NTT batch kernel in this process (by
+ * any plan, server or polymul_batch_static; the thread-block-cluster kernel
+ * for n >= 2^14 does not count) expect 16 bytes more than their operand
+ * copies deliver, so every bounded wait they make expires after `polls`
+ * polls: the path of a copy that never completes, taken without any device
+ * fault.  Their results are invalid and they report it like a real expiry
+ * (polymul_plan_status and polymul_static_status return POLYMUL_ETIMEOUT; a
+ * server request completes as failed with POLYMUL_ETIMEOUT).  launches = 0
+ * cancels what is left.  Errors: EINVAL (polls outside [1, 2^22], launches
+ * > 2^20).
+ */
+int polymul_selftest_inject_wait(uint32_t launches, uint32_t polls);
 
 /* Message for the calling thread's most recent failing call ("" if none).
  * The pointer stays valid until the next call from the same thread. */

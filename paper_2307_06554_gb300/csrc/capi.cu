@@ -661,16 +661,18 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     const bool pdl = p->ki.cluster == 0 && (p->launch_flags & kLaunchPdl);
     const uint32_t early = pdl && (p->flags & POLYMUL_FLAG_OVERLAP) && order.may_run_ahead(fp) ? 1u : 0u;
     int r;
+    uint32_t tx_pad = 0, polls = 0;
+    if (p->ki.cluster == 0) take_injected_wait(&tx_pad, &polls);  // the cluster kernel has no copy waits
     if (p->elem == 4) {
       NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
                                   (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err,
-                                  (const uint32_t*)p->d_outer, nullptr, p->n, 1, 0, early};
+                                  (const uint32_t*)p->d_outer, nullptr, p->n, 1, 0, early, tx_pad, polls};
       void* argv[] = {&args};
       r = launch(argv);
     } else {
       NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
                                   (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err,
-                                  (const uint64_t*)p->d_outer, nullptr, p->n, 1, 0, early};
+                                  (const uint64_t*)p->d_outer, nullptr, p->n, 1, 0, early, tx_pad, polls};
       void* argv[] = {&args};
       r = launch(argv);
     }

@@ -640,7 +640,7 @@ struct BlockSync {
 // The counter pair ctr = {next, finished} is zero between launches: the last
 // team to finish resets it, so launches that share a counter must not
 // overlap.  A bounded wait that expires sets *err = 1 and the team leaves
-// (the counter is then left dirty; the host resets both).
+// its loop through the finish protocol (the counter stays consistent).
 template <class S, int WARPS>
 constexpr int ntt_block() {
   return S::T <= 32 ? 32 * WARPS : S::T;
@@ -674,6 +674,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
   // and multiplies its first unit before the wait, and waits only before
   // its first use of the work counter.
   const bool early = args.early != 0;
+  const uint32_t polls = args.wait_polls ? args.wait_polls : kWaitPolls;
   bool waited = false;
   auto order = [&]() {  // every thread of the CTA, at the same point
     if (!waited) {
@@ -704,7 +705,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     auto issue = [&](unsigned long long base) {  // lane 0 only
       const uint32_t cnt = (uint32_t)(units - base < (unsigned long long)TPW ? units - base : TPW);
       fence_proxy_async();
-      mbar_arrive_expect_tx(bar, 2 * cnt * ROW);
+      mbar_arrive_expect_tx(bar, 2 * cnt * ROW + args.tx_pad);
       for (uint32_t m = 0; m < cnt; ++m) {
         W* da = wbase + (size_t)m * S::SMEM_WORDS;
         bulk_g2s(da, args.a + (size_t)(base + m) * S::N, ROW, bar);
@@ -717,11 +718,13 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     unsigned long long cur = ((unsigned long long)blockIdx.x * WARPS + warp) * TPW;
     if (lane == 0 && cur < units) issue(cur);
     while (cur < units) {
-      const bool ok = mbar_wait(bar, parity);
+      const bool ok = mbar_wait(bar, parity, polls);
       if (__any_sync(0xffffffffu, !ok)) {
+        // record the failure, let the copy in flight land, and leave through
+        // the finish protocol so that the work counter is reset as usual
         if (lane == 0) atomicExch(args.err, 1);
-        mbar_wait(bar, parity);  // let the copy in flight land before leaving
-        return;
+        mbar_wait(bar, parity, polls);
+        break;
       }
       parity ^= 1u;
       const uint64_t u = cur + team;
@@ -760,7 +763,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     fence_mbar_init();
     auto issue = [&](unsigned long long u) {  // thread 0 only
       fence_proxy_async();
-      mbar_arrive_expect_tx(bar, 2 * ROW);
+      mbar_arrive_expect_tx(bar, 2 * ROW + args.tx_pad);
       bulk_g2s(sa, args.a + (size_t)u * S::N, ROW, bar);
       bulk_g2s(sb, args.b + (size_t)u * S::N, ROW, bar);
     };
@@ -774,11 +777,11 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     unsigned long long cur = s_next;
     uint32_t parity = 0;
     while (cur < units) {
-      const bool ok = mbar_wait(bar, parity);
-      if (__syncthreads_or(!ok)) {
+      const bool ok = mbar_wait(bar, parity, polls);
+      if (__syncthreads_or(!ok)) {  // as in the warp-team path
         if (threadIdx.x == 0) atomicExch(args.err, 1);
-        mbar_wait(bar, parity);
-        return;
+        mbar_wait(bar, parity, polls);
+        break;
       }
       parity ^= 1u;
       const uint32_t j = (uint32_t)(cur % k);

@@ -18,9 +18,9 @@
 
 namespace pm {
 
+// Writes 2n words to each of twf and twi (caller-owned) and the constants.
 template <typename W>
-inline void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::vector<W>& twi, PrimeConst<W>& pc,
-                             bool cyclic = false) {
+inline void build_ntt_tables_into(uint64_t q, uint32_t n, W* twf, W* twi, PrimeConst<W>& pc, bool cyclic = false) {
   using namespace pm::host;
   using pm::host::u128;
   const int bits = 8 * (int)sizeof(W);
@@ -28,8 +28,6 @@ inline void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::v
   // negacyclic: root psi, exponent brv(k); cyclic: root w, exponent brv(j)/2
   const uint64_t psi = cyclic ? primitive_n_root(q, n) : primitive_2n_root(q, n);
   const uint64_t psi_inv = powmod(psi, q - 2, q);
-  twf.resize(2 * (size_t)n);
-  twi.resize(2 * (size_t)n);
   for (uint32_t i = 0; i < n; ++i) {
     uint32_t r = bitrev(i, logn);
     if (cyclic) r = i == 0 ? 0u : bitrev(i - (1u << (31 - __builtin_clz(i))), logn) / 2;
@@ -53,6 +51,14 @@ inline void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::v
   pc.scale_w = (W)scale_w;
   pc.scale_wp = (W)shoup_companion(scale_w, q, bits);
   pc.pad = 0;
+}
+
+template <typename W>
+inline void build_ntt_tables(uint64_t q, uint32_t n, std::vector<W>& twf, std::vector<W>& twi, PrimeConst<W>& pc,
+                             bool cyclic = false) {
+  twf.resize(2 * (size_t)n);
+  twi.resize(2 * (size_t)n);
+  build_ntt_tables_into<W>(q, n, twf.data(), twi.data(), pc, cyclic);
 }
 
 // Reduction mode for the largest modulus (see the mode notes in ntt.cuh):

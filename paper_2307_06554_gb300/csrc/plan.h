@@ -90,4 +90,7 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 void clear_error();
+// diagnostics: true (and the kernel arguments that make its waits expire)
+// when this NTT batch launch is one that polymul_selftest_inject_wait asked for
+bool take_injected_wait(uint32_t* tx_pad, uint32_t* polls);
 }  // namespace pm

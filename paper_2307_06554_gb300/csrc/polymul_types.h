@@ -43,6 +43,12 @@ struct NttBatchArgs {
   // that writes none of a, b and touches none of c (checked by the host), so
   // each team may load and multiply its first unit before waiting for it
   uint32_t early;
+  // diagnostics (0 in normal use): extra bytes each unit's completion
+  // barrier expects beyond what its copies deliver, and the poll limit of
+  // its bounded waits (0: the default).  A nonzero tx_pad makes every wait
+  // expire after wait_polls polls, the path of a copy that never completes.
+  uint32_t tx_pad;
+  uint32_t wait_polls;
 };
 
 // Ragged (uneven) batches: one unit = one (product, prime) row of n words.

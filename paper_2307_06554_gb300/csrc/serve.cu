@@ -59,9 +59,10 @@ struct ServeReq {
   const void* hb = nullptr;
   void* hc = nullptr;
   double t_submit = 0, t_done = 0;
-  int state = 0;  // 0 queued, 1 in flight, 2 done, 3 failed
+  int state = 0;  // 0 queued, 1 in flight, 2 done, 3 failed (CUDA error), 4 failed (device wait expired)
   size_t off = 0, bytes = 0;
   int lane = 0;
+  int slot = -1;  // page-locked word that receives the lane's error word after the kernel
   cudaEvent_t ev = nullptr;
 };
 
@@ -79,7 +80,9 @@ struct polymul_server {
   int nlanes = 0;
   std::vector<cudaStream_t> lanes;
   unsigned long long* d_ctr = nullptr;  // 2 per lane
-  int* d_err = nullptr;
+  int* d_err = nullptr;                 // one error word per lane
+  int* h_err = nullptr;                 // page-locked, one per in-flight slot
+  std::vector<int> free_slots;
   char* d_arena = nullptr;
   size_t arena_bytes = 0, arena_used = 0, arena_peak = 0;
   std::map<size_t, size_t> free_list;  // offset -> size
@@ -155,9 +158,12 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
   if ((e = cudaMemcpyAsync(da, r->ha, row, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(db, r->hb, row, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   const KernelInfo& ki = s->ki[r->logn];
+  uint32_t tx_pad = 0, polls = 0;
+  if (ki.cluster == 0) take_injected_wait(&tx_pad, &polls);
+  int* lane_err = s->d_err + r->lane;
   NttBatchArgs<uint64_t> args{da,      db,       dc,      s->d_twf, s->d_twi, (const PrimeConst<uint64_t>*)s->d_pc,
-                              r->k,    r->k,     s->d_ctr + 2 * r->lane, s->d_err, nullptr, dmap,
-                              s->nmax, (uint32_t)(kServeMaxLog + 1), r->logn};
+                              r->k,    r->k,     s->d_ctr + 2 * r->lane, lane_err, nullptr, dmap,
+                              s->nmax, (uint32_t)(kServeMaxLog + 1), r->logn, 0u, tx_pad, polls};
   void* argv[] = {&args};
   if (ki.cluster > 0) {
     const int clusters = std::min<int>((int)r->k, s->grid_cap[r->logn] / ki.cluster);
@@ -180,6 +186,11 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
     if ((e = cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st)) != cudaSuccess) return e;
   }
   if ((e = cudaMemcpyAsync(r->hc, dc, row, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  // the lane's error word belongs to this request until the next one on the
+  // lane starts: bring it back with the result, then clear it
+  if ((e = cudaMemcpyAsync(s->h_err + r->slot, lane_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(lane_err, 0, sizeof(int), st)) != cudaSuccess) return e;
   return cudaEventRecord(r->ev, st);
 }
 
@@ -198,15 +209,23 @@ void server_loop(polymul_server* s) {
           continue;
         }
         r->t_done = now_s();
-        r->state = q == cudaSuccess ? 2 : 3;
         if (q != cudaSuccess) {
+          r->state = 3;
           s->cuda_error = 1;
           s->cuda_error_msg = cudaGetErrorString(q);
           ++s->failed;
+        } else if (s->h_err[r->slot] != 0) {
+          // a bounded device wait of the request's kernel expired: its
+          // result is invalid
+          r->state = 4;
+          ++s->failed;
         } else {
+          r->state = 2;
           s->latencies_us.push_back((r->t_done - r->t_submit) * 1e6);
           ++s->completed;
         }
+        s->free_slots.push_back(r->slot);
+        r->slot = -1;
         arena_free(s, r->off, r->bytes);
         s->lane_bytes[r->lane] -= r->bytes;
         s->event_pool.push_back(r->ev);
@@ -235,6 +254,9 @@ void server_loop(polymul_server* s) {
         }
         r->ev = s->event_pool.back();
         s->event_pool.pop_back();
+        r->slot = s->free_slots.back();  // fewer than max_inflight requests are in flight
+        s->free_slots.pop_back();
+        s->h_err[r->slot] = 0;
         const cudaError_t e = issue(s, r);
         s->queue.pop_front();
         if (e != cudaSuccess) {
@@ -243,6 +265,8 @@ void server_loop(polymul_server* s) {
           r->state = 3;
           r->t_done = now_s();
           ++s->failed;
+          s->free_slots.push_back(r->slot);
+          r->slot = -1;
           arena_free(s, r->off, r->bytes);
           s->lane_bytes[r->lane] -= r->bytes;
           s->event_pool.push_back(r->ev);
@@ -323,6 +347,7 @@ extern "C" void polymul_server_destroy(polymul_server* s) {
   cudaFree(s->d_ctr);
   cudaFree(s->d_err);
   cudaFree(s->d_arena);
+  if (s->h_err) cudaFreeHost(s->h_err);
   delete s;
 }
 
@@ -366,14 +391,17 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
   if (cudaMalloc(&s->d_twf, twf.size() * 8) != cudaSuccess || cudaMalloc(&s->d_twi, twi.size() * 8) != cudaSuccess ||
       cudaMalloc(&s->d_pc, pcs.size() * sizeof(PrimeConst<uint64_t>)) != cudaSuccess ||
       cudaMalloc(&s->d_ctr, 2 * lanes * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess || cudaMalloc(&s->d_arena, device_bytes) != cudaSuccess)
+      cudaMalloc(&s->d_err, lanes * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&s->d_arena, device_bytes) != cudaSuccess ||
+      cudaHostAlloc(&s->h_err, s->max_inflight * sizeof(int), cudaHostAllocDefault) != cudaSuccess)
     return bail(fail(POLYMUL_ENOMEM, "device allocation failed"));
+  for (int i = (int)s->max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
   if (cudaMemcpy(s->d_twf, twf.data(), twf.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_twi, twi.data(), twi.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_pc, pcs.data(), pcs.size() * sizeof(PrimeConst<uint64_t>), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
       cudaMemset(s->d_ctr, 0, 2 * lanes * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess)
+      cudaMemset(s->d_err, 0, lanes * sizeof(int)) != cudaSuccess)
     return bail(cuda_fail(cudaGetLastError(), "table upload"));
   s->arena_bytes = device_bytes;
   s->free_list[0] = device_bytes;
@@ -467,7 +495,15 @@ static int take_if_done(polymul_server* s, uint64_t ticket) {
   const int st = r->state;
   delete r;
   s->reqs.erase(it);
-  return st == 2 ? 1 : -POLYMUL_ECUDA;
+  return st == 2 ? 1 : st == 4 ? -POLYMUL_ETIMEOUT : -POLYMUL_ECUDA;
+}
+
+static int request_failure(polymul_server* s, int code, uint64_t ticket) {
+  if (code == POLYMUL_EINVAL) return fail(code, "unknown ticket %llu", (unsigned long long)ticket);
+  if (code == POLYMUL_ETIMEOUT)
+    return fail(code, "request %llu: a bounded device wait of its kernel expired; its result is invalid",
+                (unsigned long long)ticket);
+  return fail(code, "request %llu failed: %s", (unsigned long long)ticket, s->cuda_error_msg.c_str());
 }
 
 extern "C" int polymul_server_poll(polymul_server* s, uint64_t ticket, int* done) {
@@ -475,7 +511,7 @@ extern "C" int polymul_server_poll(polymul_server* s, uint64_t ticket, int* done
   if (!s || !done) return fail(POLYMUL_EINVAL, "null argument");
   std::lock_guard<std::mutex> lock(s->mu);
   const int r = take_if_done(s, ticket);
-  if (r < 0) return fail(-r, r == -POLYMUL_EINVAL ? "unknown ticket" : "request failed: %s", s->cuda_error_msg.c_str());
+  if (r < 0) return request_failure(s, -r, ticket);
   *done = r;
   return POLYMUL_OK;
 }
@@ -487,7 +523,7 @@ extern "C" int polymul_server_wait(polymul_server* s, uint64_t ticket, double ti
   std::unique_lock<std::mutex> lock(s->mu);
   for (;;) {
     const int r = take_if_done(s, ticket);
-    if (r < 0) return fail(-r, r == -POLYMUL_EINVAL ? "unknown ticket" : "request failed: %s", s->cuda_error_msg.c_str());
+    if (r < 0) return request_failure(s, -r, ticket);
     if (r == 1) return POLYMUL_OK;
     if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout && Clock::now() >= deadline)
       return fail(POLYMUL_ETIMEOUT, "request %llu not finished within %.3f s", (unsigned long long)ticket, timeout_s);
@@ -521,7 +557,7 @@ extern "C" int polymul_server_replay(polymul_server* s, const polymul_request* r
         const int st = r->state;
         delete r;
         s->reqs.erase(it);
-        if (st != 2) return fail(POLYMUL_ECUDA, "request failed: %s", s->cuda_error_msg.c_str());
+        if (st != 2) return request_failure(s, st == 4 ? POLYMUL_ETIMEOUT : POLYMUL_ECUDA, tickets[i]);
         break;
       }
       s->cv.wait_for(lock, std::chrono::milliseconds(50));

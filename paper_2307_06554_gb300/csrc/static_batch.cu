@@ -71,32 +71,9 @@ StaticDeviceState g_static_dev[64];
 uint32_t g_host_tw[2][2 * kStaticMaxN];
 PrimeConst<uint32_t> g_host_pc;
 
-// psi^brv(i), psi^-brv(i) with Shoup companions, and the constants of q, n
-void fill_tables(uint64_t q, uint32_t n) {
-  using namespace pm::host;
-  const int logn = __builtin_ctz(n);
-  const uint64_t psi = primitive_2n_root(q, n);
-  const uint64_t psi_inv = powmod(psi, q - 2, q);
-  for (uint32_t i = 0; i < n; ++i) {
-    const uint32_t r = bitrev(i, logn);
-    const uint64_t w = powmod(psi, r, q), v = powmod(psi_inv, r, q);
-    g_host_tw[0][2 * i] = (uint32_t)w;
-    g_host_tw[0][2 * i + 1] = (uint32_t)shoup_companion(w, q, 32);
-    g_host_tw[1][2 * i] = (uint32_t)v;
-    g_host_tw[1][2 * i + 1] = (uint32_t)shoup_companion(v, q, 32);
-  }
-  const uint64_t scale = mulmod(powmod(n, q - 2, q), (1ull << 32) % q, q);
-  const uint64_t scale_w = mulmod(powmod(psi_inv, bitrev(1, logn), q), scale, q);
-  PrimeConst<uint32_t>& pc = g_host_pc;
-  pc.q = (uint32_t)q;
-  pc.q2 = (uint32_t)(2 * q);
-  pc.qinv = (uint32_t)inv_pow2_64(q);
-  pc.scale = (uint32_t)scale;
-  pc.scale_p = (uint32_t)shoup_companion(scale, q, 32);
-  pc.scale_w = (uint32_t)scale_w;
-  pc.scale_wp = (uint32_t)shoup_companion(scale_w, q, 32);
-  pc.pad = 0;
-}
+// psi^brv(i), psi^-brv(i) with Shoup companions, and the constants of q, n:
+// the plan builder's tables, written into the static host staging arrays
+void fill_tables(uint64_t q, uint32_t n) { build_ntt_tables_into<uint32_t>(q, n, g_host_tw[0], g_host_tw[1], g_host_pc); }
 
 bool lookup_u32(int logn, int mode, KernelInfo* ki) {
   if (mode == 0) return lookup_ntt_u32_m0(logn, ki);
@@ -163,6 +140,8 @@ extern "C" int polymul_batch_static(uint32_t n, uint64_t q, const void* a, const
   if (per_sm < 1) return fail(POLYMUL_ENOTSUP, "kernel does not fit on an SM");
   const uint64_t need = (batch + ki.units_per_cta - 1) / ki.units_per_cta;
   const int grid = (int)std::min<uint64_t>(need, (uint64_t)per_sm * sms);
+  uint32_t tx_pad = 0, polls = 0;
+  take_injected_wait(&tx_pad, &polls);
   NttBatchArgs<uint32_t> args{(const uint32_t*)a,
                               (const uint32_t*)b,
                               (uint32_t*)c,
@@ -177,7 +156,10 @@ extern "C" int polymul_batch_static(uint32_t n, uint64_t q, const void* a, const
                               nullptr,
                               n,
                               1u,
-                              0u};
+                              0u,
+                              0u,
+                              tx_pad,
+                              polls};
   void* argv[] = {&args};
   // the kernel lets the next one on the stream start once it is running:
   // record what it reads and writes (stream_order.h)
@@ -190,4 +172,23 @@ extern "C" int polymul_batch_static(uint32_t n, uint64_t q, const void* a, const
   PM_CUDA(cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st));
   order.record(&fp);
   return POLYMUL_OK;
+}
+
+// The error word sits in the same fixed array and every call clears it, so
+// it describes the most recent call on the device; reading it allocates
+// nothing (a plain copy into a local word).
+extern "C" int polymul_static_status(void* stream) {
+  clear_error();
+  int dev = 0;
+  PM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(POLYMUL_ENOTSUP, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticDeviceState& s = g_static_dev[dev];
+  if (!s.ready) return POLYMUL_OK;  // no call on this device yet
+  PM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int h = 0;
+  PM_CUDA(cudaMemcpy(&h, s.ptr + 16, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return POLYMUL_OK;
+  PM_CUDA(cudaMemset(s.ptr + 16, 0, sizeof(int)));
+  return fail(POLYMUL_ETIMEOUT, "a bounded device wait of the last polymul_batch_static call expired; its results are invalid");
 }

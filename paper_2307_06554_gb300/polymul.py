@@ -103,6 +103,10 @@ def _load():
     lib.polymul_tensor_shape.restype = i32
     lib.polymul_batch_static.argtypes = [u32, u64, vp, vp, vp, u64, vp]
     lib.polymul_batch_static.restype = i32
+    lib.polymul_static_status.argtypes = [vp]
+    lib.polymul_static_status.restype = i32
+    lib.polymul_selftest_inject_wait.argtypes = [u32, u32]
+    lib.polymul_selftest_inject_wait.restype = i32
     lib.polymul_plan_select.argtypes = [vp, u32]
     lib.polymul_plan_select.restype = i32
     lib.polymul_tune.argtypes = [vp, u64, vp]
@@ -235,6 +239,18 @@ def polymul_batch_shared(plan: int, a, b, c, batch: int, stream=None) -> None:
 def polymul_batch_static(n: int, q: int, a, b, c, batch: int, stream=None) -> None:
     """Allocation-free entry point (one NTT-friendly prime, n <= 4096)."""
     _check(_lib.polymul_batch_static(n, q, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
+
+
+def polymul_static_status(stream=None) -> None:
+    """Raises PolymulError (POLYMUL_ETIMEOUT) when the last
+    polymul_batch_static call on the current device abandoned a device wait."""
+    _check(_lib.polymul_static_status(_stream(stream)))
+
+
+def polymul_selftest_inject_wait(launches: int, polls: int) -> None:
+    """Diagnostics: the next `launches` NTT batch-kernel launches take an
+    expired bounded wait after `polls` polls (no device fault)."""
+    _check(_lib.polymul_selftest_inject_wait(launches, polls))
 
 
 def polymul_plan_select(plan: int, candidate: int) -> None:
