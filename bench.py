@@ -50,6 +50,12 @@ IMAD_LANES_PER_SM = 64
 # dependency-free microbenchmark of the same sequence reproduces (5.02e12/s
 # at 2070 MHz on 152 SMs).
 IMAD_SLOTS_PER_MULMOD = 4
+# 64-bit Shoup modular multiplications per second on one GB300, measured by
+# `python bench.py --case alu_peak` (profiles/alu_peak.md): the ALU ceiling of
+# the kernels on 64-bit words (4.11x the cost of a 32-bit one), scaled by the
+# SM clock at which it was taken (2070 MHz)
+SHOUP64_PER_S = 1.2227e12
+SHOUP64_MHZ = 2070.0
 MODE_NAMES = {0: "[0,2q)", 1: "[0,4q)", 2: "small-q"}
 
 
@@ -62,6 +68,9 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU oracle sample budget")
     p.add_argument("--no-extras", action="store_true", help="skip the other standing workloads")
+    p.add_argument("--case", choices=sorted(CASES), help="run one small profiling case (or the ALU-peak "
+                   "microbenchmark) instead of the benchmark, and print what it ran")
+    p.add_argument("--launches", type=int, default=4, help="launches of a --case")
     return p.parse_args()
 
 
@@ -110,6 +119,243 @@ def _host_cores():
     except Exception:
         return os.cpu_count() or 1
 
+
+
+# ------------------------------------------------------------------ cases
+# Small, self-contained launches of each kernel family for profilers
+# (``python bench.py --case <name> [--launches K]``): the plan is built through
+# the public binding, operands are seeded uniform residues, K launches run on
+# one stream with operands rotated over buffer sets larger than L2 (so DRAM
+# counters mean something), and the plan's device status is checked.  Device
+# memory stays below 1 GB.
+def _case_homogeneous(n, q_list, batch, path, launches, seed=7, flags=0):
+    import torch
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(seed)
+    a = wl.uniform_coeffs(rng, batch, q_list, n)
+    b = wl.uniform_coeffs(rng, batch, q_list, n)
+    view = np.int32 if a.dtype == np.uint32 else np.int64
+    ta = torch.from_numpy(a.view(view)).to(dev)
+    tb = torch.from_numpy(b.view(view)).to(dev)
+    nsets = max(1, math.ceil(1.5 * L2_BYTES / (3 * ta.numel() * ta.element_size())))
+    sets = [(ta.clone(), tb.clone(), torch.empty_like(ta)) for _ in range(nsets)]
+    stream = torch.cuda.Stream(dev)
+    with polymul.Plan(n, q_list, path=path, flags=flags) as plan:
+        for i in range(launches):
+            x, y, z = sets[i % nsets]
+            polymul.polymul_batch(plan.handle, x, y, z, batch, stream.cuda_stream)
+        stream.synchronize()
+        polymul.polymul_plan_status(plan.handle, stream.cuda_stream)
+        info = plan.info
+    return {"n": n, "k": len(q_list), "batch": batch, "launches": launches, "grid": info["grid"],
+            "block": info["block"], "smem_bytes": info["smem_bytes"], "sets": nsets}
+
+
+def _case_ragged(count, launches):
+    import torch
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+    dev = torch.device("cuda", 0)
+    rag = wl.ragged_2000(count=count)
+    total = sum(p.n * len(p.prime_idx) for p in rag.products)
+    ah = np.concatenate([p.a.reshape(-1) for p in rag.products]).astype(np.uint32)
+    bh = np.concatenate([p.b.reshape(-1) for p in rag.products]).astype(np.uint32)
+    stream = torch.cuda.Stream(dev)
+    with polymul.Ragged(rag.pool, 16384, [(p.n, p.prime_idx) for p in rag.products]) as r:
+        ta = torch.from_numpy(ah.view(np.int32)).to(dev)
+        tb = torch.from_numpy(bh.view(np.int32)).to(dev)
+        tc = torch.empty_like(ta)
+        for _ in range(launches):
+            r.run(ta, tb, tc, stream=stream.cuda_stream)
+        stream.synchronize()
+        polymul.polymul_ragged_status(r.batch, stream.cuda_stream)
+        info = r.info
+    return {"products": count, "words": total, "launches": launches, **info}
+
+
+def _case_shared(n, q, batch, launches, path, seed=7):
+    import torch
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(seed)
+    a = wl.uniform_coeffs(rng, 1, [q], n)[0]
+    b = wl.uniform_coeffs(rng, batch, [q], n)
+    ta = torch.from_numpy(a.view(np.int32)).to(dev)
+    tb = torch.from_numpy(b.view(np.int32)).to(dev)
+    nsets = max(1, math.ceil(1.5 * L2_BYTES / (2 * tb.numel() * 4)))
+    sets = [(tb.clone(), torch.empty_like(tb)) for _ in range(nsets)]
+    stream = torch.cuda.Stream(dev)
+    with polymul.Plan(n, [q], path=path) as plan:
+        for i in range(launches):
+            x, y = sets[i % nsets]
+            polymul.polymul_batch_shared(plan.handle, ta, x, y, batch, stream.cuda_stream)
+        stream.synchronize()
+        polymul.polymul_plan_status(plan.handle, stream.cuda_stream)
+    return {"n": n, "batch": batch, "launches": launches, "sets": nsets}
+
+
+# Integer- and tensor-pipe ceilings the rooflines are reported against (the
+# measured peaks cover HBM and cuBLAS bf16 only).  Each thread runs 8
+# independent chains of one operation, no memory traffic inside the loop, the
+# grid filling every SM; the MMA operations run 8 independent accumulator
+# chains per warp.
+ALU_PROBE_SRC = r"""
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
+#define CHAINS 8
+#define UNROLL 16
+template <int OP>
+__global__ void k_probe(uint64_t* out, uint64_t w, uint64_t wp, uint64_t q, int iters) {
+  uint32_t x[CHAINS];
+  uint64_t y[CHAINS];
+  uint32_t acc[CHAINS][4];
+  for (int j = 0; j < CHAINS; ++j) {
+    x[j] = threadIdx.x * 131u + j;
+    y[j] = threadIdx.x * 131ull + j;
+    for (int r = 0; r < 4; ++r) acc[j][r] = j + r;
+  }
+  const uint32_t w32 = (uint32_t)w, wp32 = (uint32_t)wp, q32 = (uint32_t)q;
+  const uint32_t fa0 = threadIdx.x * 0x01010101u, fa1 = fa0 ^ 0x5a5a5a5au, fa2 = fa0 + 7u, fa3 = fa0 ^ 0x33u;
+  const uint32_t fb0 = threadIdx.x * 0x00ff00ffu, fb1 = fb0 ^ 0x12345678u;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u)
+#pragma unroll
+      for (int j = 0; j < CHAINS; ++j) {
+        if (OP == 0) x[j] = x[j] * w32 + wp32;                                       // IMAD
+        if (OP == 1) x[j] = __umulhi(x[j], wp32) ^ x[j];                             // IMAD.HI (+LOP)
+        if (OP == 2) x[j] = x[j] * w32 - __umulhi(x[j], wp32) * q32;                 // 32-bit Shoup
+        if (OP == 3) y[j] = y[j] * w - __umul64hi(y[j], wp) * q;                     // 64-bit Shoup
+        if (OP == 4) x[j] = x[j] * w32 - ((x[j] * wp32) >> 16) * q32;                // Shoup, 16-bit quotient
+        if (OP == 5)                                                                 // mma.sync u8 -> s32
+          asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.u8.u8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                       "{%0,%1,%2,%3};"
+                       : "+r"(acc[j][0]), "+r"(acc[j][1]), "+r"(acc[j][2]), "+r"(acc[j][3])
+                       : "r"(fa0), "r"(fa1), "r"(fa2), "r"(fa3), "r"(fb0), "r"(fb1));
+        if (OP == 6)                                                                 // mma.sync bf16 -> f32
+          asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                       "{%0,%1,%2,%3};"
+                       : "+r"(acc[j][0]), "+r"(acc[j][1]), "+r"(acc[j][2]), "+r"(acc[j][3])
+                       : "r"(fa0 & 0x3f803f80u), "r"(fa1 & 0x3f803f80u), "r"(fa2 & 0x3f803f80u),
+                         "r"(fa3 & 0x3f803f80u), "r"(fb0 & 0x3f803f80u), "r"(fb1 & 0x3f803f80u));
+      }
+  }
+  uint64_t r = 0;
+  for (int j = 0; j < CHAINS; ++j) r ^= x[j] ^ y[j] ^ acc[j][0] ^ acc[j][1] ^ acc[j][2] ^ acc[j][3];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+int main() {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256, blocks = sms * 8, iters = 2048;
+  uint64_t* out = nullptr;
+  if (cudaMalloc(&out, sizeof(uint64_t) * threads * blocks) != cudaSuccess) return 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const double per_thread = (double)iters * UNROLL * CHAINS;
+  const char* names[] = {"imad32", "imad32_hi", "shoup32_mulmod", "shoup64_mulmod", "shoup16q_mulmod",
+                         "mma_sync_u8_s32_ops", "mma_sync_bf16_f32_flops"};
+  const uint64_t W32 = 5000, WP32 = (uint64_t)((5000ull << 32) / 12289), Q32 = 12289;
+  const uint64_t Q64 = 288230376151760897ull, W64 = (1ull << 40) + 7;
+  const uint64_t WP64 = (uint64_t)(((unsigned __int128)W64 << 64) / Q64);
+  const uint64_t WP16 = (5000ull << 16) / 12289;  // x stays below 2q < 2^16 along each chain
+  printf("{\"sms\": %d, \"results\": [", sms);
+  for (int op = 0; op < 7; ++op) {
+    float best = 1e30f;
+    const int it = op == 3 ? iters / 4 : (op >= 5 ? iters / 8 : iters);
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0);
+      if (op == 0) k_probe<0><<<blocks, threads>>>(out, W32, WP32, Q32, it);
+      if (op == 1) k_probe<1><<<blocks, threads>>>(out, W32, WP32, Q32, it);
+      if (op == 2) k_probe<2><<<blocks, threads>>>(out, W32, WP32, Q32, it);
+      if (op == 3) k_probe<3><<<blocks, threads>>>(out, W64, WP64, Q64, it);
+      if (op == 4) k_probe<4><<<blocks, threads>>>(out, W32, WP16, Q32, it);
+      if (op == 5) k_probe<5><<<blocks, threads>>>(out, W32, WP32, Q32, it);
+      if (op == 6) k_probe<6><<<blocks, threads>>>(out, W32, WP32, Q32, it);
+      cudaEventRecord(e1);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) best = ms;
+    }
+    double n = (double)threads * blocks * per_thread * it / iters;
+    if (op == 5) n = n / 32 * (2.0 * 16 * 8 * 32);   // per warp-MMA: 16x8x32 MACs
+    if (op == 6) n = n / 32 * (2.0 * 16 * 8 * 16);
+    printf("%s{\"op\": \"%s\", \"per_s\": %.4e}", op ? ", " : "", names[op], n / (best * 1e-3));
+  }
+  printf("], \"error\": \"%s\"}\n", cudaGetErrorString(cudaGetLastError()));
+  cudaFree(out);
+  return 0;
+}
+"""
+
+
+def _case_alu_peak():
+    from paper_2307_06554_gb300 import build as _build
+    work = tempfile.mkdtemp()
+    src = os.path.join(work, "alu_peak.cu")
+    exe = os.path.join(work, "alu_peak")
+    with open(src, "w") as f:
+        f.write(ALU_PROBE_SRC)
+    subprocess.check_call([_build.nvcc()] + _build.ARCH + ["-O3", "-o", exe, src])
+    smi = subprocess.Popen(["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm", "--format=csv,noheader,nounits",
+                            "-lms", "50"], stdout=subprocess.PIPE, text=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    smi.terminate()
+    clocks = [l.split(",") for l in smi.communicate()[0].splitlines() if "," in l]
+    res = json.loads(out)
+    res["sm_mhz_max_seen"] = max(float(c[0]) for c in clocks) if clocks else None
+    mhz = res["sm_mhz_max_seen"] or 2070.0
+    for r in res["results"]:
+        r["per_sm_per_clk"] = r["per_s"] / res["sms"] / (mhz * 1e6)
+    return res
+
+
+def _case(name, launches):
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+    rng = np.random.default_rng(8)
+    if name == "alu_peak":
+        return _case_alu_peak()
+    if name == "ntt_ring1024":
+        return _case_homogeneous(1024, [12289], 4096, polymul.PATH_NTT, launches)
+    if name == "ntt_ring1024_overlap":
+        return _case_homogeneous(1024, [12289], 4096, polymul.PATH_NTT, launches, flags=polymul.FLAG_OVERLAP)
+    if name == "tensor_ring1024":
+        return _case_homogeneous(1024, [12289], 4096, polymul.PATH_TENSOR, launches)
+    if name == "tensor_rns4096":
+        return _case_homogeneous(4096, wl.draw_primes(rng, 8, 30, 30, 13), 64, polymul.PATH_TENSOR, launches)
+    if name == "tensor_u64_4096":
+        return _case_homogeneous(4096, wl.draw_primes(rng, 2, 59, 59, 13), 64, polymul.PATH_TENSOR, launches)
+    if name == "n16384":
+        return _case_homogeneous(16384, wl.draw_primes(rng, 1, 30, 30, 15), 1024, polymul.PATH_NTT, launches)
+    if name == "cluster_32768":
+        return _case_homogeneous(32768, wl.draw_primes(rng, 1, 30, 30, 16), 256, polymul.PATH_NTT, launches)
+    if name == "u64_4096":
+        return _case_homogeneous(4096, wl.draw_primes(rng, 1, 59, 59, 13), 1024, polymul.PATH_NTT, launches)
+    if name == "shared_ring1024":
+        return _case_shared(1024, 12289, 4096, launches, polymul.PATH_TENSOR)
+    if name == "shared_ntt1024":
+        return _case_shared(1024, 12289, 4096, launches, polymul.PATH_NTT)
+    return _case_ragged(300, launches)
+
+
+CASES = {
+    "alu_peak": "integer- and tensor-pipe microbenchmark (IMAD, Shoup 32/64-bit, mma.sync u8 and bf16)",
+    "ntt_ring1024": "n = 1024, q = 12289, 4096 products (path a, default kernel)",
+    "ntt_ring1024_overlap": "the same with POLYMUL_FLAG_OVERLAP",
+    "tensor_ring1024": "the same batch through the Toeplitz tensor-core path",
+    "tensor_rns4096": "n = 4096, 8 primes of 30 bits, 64 products on the tiled tensor kernel",
+    "tensor_u64_4096": "n = 4096, 2 primes of 59 bits, 64 products on the residue-number-system tensor kernel",
+    "n16384": "n = 16384, one 30-bit prime, 1024 products (one CTA per product)",
+    "cluster_32768": "n = 32768, one 30-bit prime, 256 products (thread-block clusters)",
+    "u64_4096": "n = 4096, one 59-bit prime, 1024 products (64-bit words)",
+    "ragged_300": "the first 300 products of the uneven 2000-product list, one persistent launch",
+    "shared_ring1024": "one a times 4096 b's (n = 1024, q = 12289), tensor-core GEMM",
+    "shared_ntt1024": "the same on the NTT path (a's transform once)",
+}
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
@@ -248,9 +494,22 @@ def cpu_oracle_rate(w, seconds: float, max_products: int = None):
 
 
 def _ntt_mulmods(n: int) -> int:
-    """Modular multiplications of one NTT unit: two forward transforms, one
-    inverse, the pointwise product and the last-stage scaling."""
-    return 3 * (n // 2) * int(math.log2(n)) + n + n // 2
+    """Algorithmic modular multiplications of one NTT unit, the scope table's
+    count: two forward transforms, one inverse, the pointwise product."""
+    return 3 * (n // 2) * int(math.log2(n)) + n
+
+
+def _ntt_mulmods_kernel(n: int) -> int:
+    """What the kernels execute: the above plus the last inverse stage's
+    scaling by n^-1 of the half of the outputs that carries no twiddle."""
+    return _ntt_mulmods(n) + n // 2
+
+
+def _alu_peak_g(elem: int, sms: int, sm_mhz: float) -> float:
+    """ALU ceiling in Gmulmod/s for the kernels on `elem`-byte words."""
+    if elem == 8:
+        return SHOUP64_PER_S * (sm_mhz / SHOUP64_MHZ) / 1e9
+    return sms * IMAD_LANES_PER_SM * sm_mhz * 1e6 / IMAD_SLOTS_PER_MULMOD / 1e9
 
 
 # Shared-memory bytes a tcgen05 MMA of the tensor path reads per instruction:
@@ -360,7 +619,9 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     def homogeneous(name, w, sets_needed, reps, cyclic=False, path=None, extra_flags=0):
-        flags = (polymul.FLAG_TUNE if path is None else 0) | (polymul.FLAG_CYCLIC if cyclic else 0) | extra_flags
+        # tuned plans: back-to-back batches on rotating buffers may overlap
+        flags = ((polymul.FLAG_TUNE | polymul.FLAG_OVERLAP) if path is None else 0) | \
+            (polymul.FLAG_CYCLIC if cyclic else 0) | extra_flags
         plan = polymul.Plan(w.n, w.q_list, path=polymul.PATH_AUTO if path is None else path, flags=flags,
                             tune_batch=w.batch)
         k = len(w.q_list)
@@ -416,7 +677,10 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
                 w.n, info["digits"], units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=la,
                 shifts=_tiled_shifts(w.n, info["digits"]) if (info["tensor_groups"] and la == lb) else 1)["frac"]
         else:
-            out[name]["alu_frac"] = mm / (ms / 1e3) / 1e9 / alu_peak_g
+            peak_g = _alu_peak_g(elem, sms, peaks.get("sm_max_mhz", 2070.0))
+            out[name]["alu_frac"] = mm / (ms / 1e3) / 1e9 / peak_g
+            out[name]["alu_peak"] = ("measured 64-bit Shoup rate (bench.py --case alu_peak), %.4g Gmulmod/s" % peak_g
+                                     if elem == 8 else "derived 32-bit Shoup rate, %.4g Gmulmod/s" % peak_g)
         plan.close()
 
     homogeneous("ring_small", wl.ring_small(), 1, 200)
@@ -901,6 +1165,7 @@ def run_ours(args, ws, rank, local):
     isolated_ms = statistics.mean(per)
     units = batch * len(q_list)
     mulmods = units * _ntt_mulmods(n)
+    mulmods_kernel = units * _ntt_mulmods_kernel(n)
     bytes_alg = 3 * units * n * elem
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -910,10 +1175,14 @@ def run_ours(args, ws, rank, local):
     alu_ach = mulmods / (launch_ms / 1e3) / 1e9
     hbm_ach = bytes_alg / (launch_ms / 1e3) / 1e9
     hbm_peak = peaks["hbm_gbs"]
-    tag = "k_ntt_batch<u32,logn=10,%s,RB=%d>" % (MODE_NAMES[mode], info["radix_bits"])
+    tag = "k_ntt_batch<u32,logn=10,%s,RB=%d,pad=%d,%s>" % (MODE_NAMES[mode], info["radix_bits"], info["exchange_pad"],
+                                                            "one-operand" if info["one_operand"] else "two-operand")
     traffic = _recorded_traffic(tag)
     roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Gmulmod/s",
             "frac": alu_ach / alu_peak, "traffic": traffic,
+            "work": "3 (n/2) log2 n + n modular multiplications per product (two forward transforms, inverse, "
+                    "pointwise); the kernel also scales half of the outputs by n^-1: with those, frac %.3f" % (
+                        mulmods_kernel / (launch_ms / 1e3) / 1e9 / alu_peak),
             "kernel": tag + " (forward x2, pointwise, inverse; one launch per step)",
             "peak_source": "derived: %d SMs x %d IMAD lanes x %.0f MHz / %d IMAD slots per Shoup mulmod" % (
                 sms, IMAD_LANES_PER_SM, sm_mhz, slots),
@@ -992,6 +1261,9 @@ def run_ours(args, ws, rank, local):
 
 def main():
     args = _args()
+    if args.case:
+        print(args.case, json.dumps(_case(args.case, args.launches)), flush=True)
+        return
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
