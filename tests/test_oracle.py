@@ -17,6 +17,7 @@ its own pins of the same kinds at the end, including numpy's FFT splitting
 the full product into both rings.
 """
 import os
+import math
 import random
 
 import numpy as np
@@ -293,6 +294,114 @@ def test_rns_route_and_base_rules():
     mods = [7, 9, 10]
     for x in range(0, 630, 13):
         assert sb.crt([x % m for m in mods], mods) == x
+
+
+def _coprime_sequences(maxv):
+    """Every pairwise-coprime set of integers in [2, maxv], as a descending
+    tuple (exhaustive enumeration)."""
+    out = []
+
+    def rec(top, cur):
+        out.append(tuple(cur))
+        for m in range(top, 1, -1):
+            if all(math.gcd(m, c) == 1 for c in cur):
+                rec(m - 1, cur + [m])
+    rec(maxv, [])
+    return out
+
+
+def _prod(xs):
+    p = 1
+    for x in xs:
+        p *= x
+    return p
+
+
+def _base_by_enumeration(sets, bound):
+    """The largest-first rule of Sec. 2.6 read off the enumeration: among the
+    minimal coprime sequences whose product exceeds the bound (every proper
+    prefix stays at or below it), the lexicographically greatest; None when
+    even the largest-first scan of all moduli cannot pass the bound."""
+    full = max(sets)  # the largest-first scan taken to the end
+    if _prod(full) <= bound:
+        return None
+    minimal = [t for t in sets if _prod(t) > bound and _prod(t[:-1]) <= bound]
+    best = max(minimal)
+    assert best == full[:len(best)]
+    return list(best)
+
+
+def _check_base_rule(select):
+    """True when `select(q, ell, max_bits)` agrees with the enumeration on
+    3- and 4-bit moduli for many bounds and on the closed-form boundary case
+    (a bound equal to the first modulus must take a second one)."""
+    for bits in (3, 4):
+        sets = _coprime_sequences((1 << bits) - 1)
+        for q in range(2, 60):
+            for ell in (1, 2, 3, 5, 7):
+                want = _base_by_enumeration(sets, ell * q * q)
+                try:
+                    got = select(q, ell, bits)
+                except ValueError:
+                    got = None
+                if got != want:
+                    return False
+    # 6-bit moduli: 63 = 7 * 3^2 is the first modulus; ell * q^2 = 63 is not
+    # yet exceeded by it, so the next largest coprime modulus, 62, follows
+    return select(3, 7, 6) == [63, 62]
+
+
+def test_rns_base_against_enumeration():
+    assert _check_base_rule(sb.select_rns_base)
+
+
+def test_rns_base_pin_catches_planted_mistakes():
+    def start_one_low(q, ell, max_bits=8):  # the scan starts at 2^b - 2
+        bound, chosen, prod, m = ell * q * q, [], 1, (1 << max_bits) - 2
+        while prod <= bound:
+            if m < 2:
+                raise ValueError
+            if all(math.gcd(m, c) == 1 for c in chosen):
+                chosen.append(m)
+                prod *= m
+            m -= 1
+        return chosen
+
+    def stops_at_equality(q, ell, max_bits=8):  # product >= bound accepted
+        bound, chosen, prod, m = ell * q * q, [], 1, (1 << max_bits) - 1
+        while prod < bound:
+            if m < 2:
+                raise ValueError
+            if all(math.gcd(m, c) == 1 for c in chosen):
+                chosen.append(m)
+                prod *= m
+            m -= 1
+        return chosen
+
+    def odd_only(q, ell, max_bits=8):  # skips valid even moduli
+        bound, chosen, prod, m = ell * q * q, [], 1, (1 << max_bits) - 1
+        while prod <= bound:
+            if m < 2:
+                raise ValueError
+            if m % 2 and all(math.gcd(m, c) == 1 for c in chosen):
+                chosen.append(m)
+                prod *= m
+            m -= 1
+        return chosen
+
+    def smallest_first(q, ell, max_bits=8):
+        bound, chosen, prod, m = ell * q * q, [], 1, 2
+        while prod <= bound:
+            if m >= (1 << max_bits):
+                raise ValueError
+            if all(math.gcd(m, c) == 1 for c in chosen):
+                chosen.append(m)
+                prod *= m
+            m += 1
+        return sorted(chosen, reverse=True)
+
+    for bad in (start_one_low, stops_at_equality, odd_only, smallest_first):
+        assert not _check_base_rule(bad), bad.__name__
 
 
 # ---------------------------------------------------------------- planted mistakes
