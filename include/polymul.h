@@ -409,6 +409,27 @@ int polymul_ragged_run_graph(polymul_ragged_batch *batch, const void *a, const v
 /* As polymul_plan_status, for a prepared list. */
 int polymul_ragged_status(polymul_ragged_batch *batch, void *stream);
 
+/*
+ * polymul_ragged_tune -- choose the kernel shapes of a prepared list by
+ * measurement on the caller's operands (the paper leaves such dimensions to
+ * experiment, Sec. 2.6).  Each of the list's two launches (degrees 2^10 ..
+ * 2^13; 2^14) exists in two shape sets -- 0: swizzled exchanges, both
+ * operands in registers; 1: padded exchanges, one operand in registers at
+ * 2^10, 2^11 and 2^14 (the default) -- and each launch keeps the faster set
+ * (best of three timed runs after a warm-up).  a, b, c as for
+ * polymul_ragged_run (c is overwritten with the products).  *choice
+ * (may be NULL) receives bit 0 = set of the smaller degrees, bit 1 = set of
+ * 2^14.  A recorded graph is rebuilt on its next replay.  Synchronous;
+ * returns as polymul_ragged_status afterwards.  Errors: EINVAL, ETIMEOUT,
+ * ECUDA.
+ */
+int polymul_ragged_tune(polymul_ragged_batch *batch, const void *a, const void *b, void *c,
+                        void *stream, uint32_t *choice);
+
+/* Use the shape sets `choice` (bits as for polymul_ragged_tune) instead of
+ * the default or tuned ones.  Errors: EINVAL. */
+int polymul_ragged_select(polymul_ragged_batch *batch, uint32_t choice);
+
 /* Units, degree segments (`items`) and CTAs of a prepared list (any pointer
  * may be NULL). */
 int polymul_ragged_batch_info(const polymul_ragged_batch *batch, uint64_t *units, uint64_t *items,
@@ -443,6 +464,16 @@ typedef struct polymul_server_stats {
     uint64_t submitted, completed, failed, queued, in_flight;
     uint64_t arena_bytes, arena_peak_bytes;
     double p50_us, p99_us, mean_us, max_us; /* submit -> completion latency */
+    double queue_p50_us, queue_p99_us;      /* submit -> admission (waiting
+                                               for memory, a slot or the
+                                               server thread)               */
+    double service_p50_us, service_p99_us;  /* admission -> observed
+                                               completion (copies in, kernel,
+                                               copy out)                    */
+    double issue_us_mean;                   /* host time the server thread
+                                               spends enqueuing one request */
+    double server_busy_s;                   /* server-thread time in passes
+                                               that admitted or retired work */
 } polymul_server_stats;
 
 /* Start a server on the current device.  Errors: EINVAL, ENOMEM, ENOTSUP. */

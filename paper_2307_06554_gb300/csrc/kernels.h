@@ -48,8 +48,10 @@ bool lookup_ntt_shared(int logn, int mode, KernelInfo* prep, KernelInfo* main);
 bool lookup_ntt_cluster(uint32_t elem, int logn, int mode, KernelInfo* ki);
 
 // uneven batches (32-bit words): one persistent kernel for the degrees
-// 2^10..2^13 and one for 2^14
-bool lookup_ntt_ragged(int mode, KernelInfo* small, KernelInfo* big);
+// 2^10..2^13 and one for 2^14, in two shape sets (0: swizzled exchanges,
+// both operands; 1: padded exchanges, one operand at 2^10, 2^11 and 2^14)
+constexpr int kRaggedSets = 2;
+bool lookup_ntt_ragged(int mode, int set, KernelInfo* small, KernelInfo* big);
 
 // Toeplitz path on the tensor cores, k_toeplitz_batch<TShape<LOGN, WB, LA, LB>>
 bool lookup_toeplitz(int logn, int wb, int la, int lb, KernelInfo* ki);

@@ -35,9 +35,20 @@ struct TeamSync {
 };
 
 // degree class -> register radix (16 coefficients per thread up to 2^13,
-// 32 for 2^14 so that a unit fits in 512 threads)
-template <int LOGN>
-using RaggedShape = Shape<uint32_t, LOGN, (LOGN <= 13 ? 4 : 5)>;
+// 32 for 2^14 so that a unit fits in 512 threads).  Two shape sets, chosen
+// per list by measurement (polymul_ragged_tune):
+//   set 0: the XOR-swizzled exchange layout, both operands in registers;
+//   set 1: the padded layout (one word after every 2^RB, a base register
+//          plus constant offsets per layout), one operand in registers at a
+//          time for 2^10, 2^11 (as the homogeneous kernels measured) and for
+//          2^14, whose 32 coefficients per operand and thread otherwise spill.
+constexpr int ragged_rb(int logn) { return logn <= 13 ? 4 : 5; }
+template <int LOGN, int SET>
+using RaggedShape = Shape<uint32_t, LOGN, ragged_rb(LOGN), SET == 1 ? ragged_rb(LOGN) : 0>;
+template <int LOGN, int SET>
+constexpr bool ragged_seq() {
+  return SET == 1 && (LOGN == 10 || LOGN == 11 || LOGN == 14);
+}
 
 // One degree segment: the units of degree 2^LOGN, taken one at a time by
 // the teams of the CTA (T threads each, 512 / T teams) from the segment's
@@ -50,7 +61,7 @@ using RaggedShape = Shape<uint32_t, LOGN, (LOGN <= 13 ? 4 : 5)>;
 // bit in s_bits[team] so that the CTA can agree on all of them.  Returns
 // false when a bounded wait expired (the team stops; the copy it waited for
 // is the only one it has in flight).
-template <class S, int MODE>
+template <class S, int MODE, bool SEQ>
 __device__ __forceinline__ bool ragged_segment(const RaggedArgs& args, const RaggedItem& seg,
                                                unsigned long long* ctr, uint32_t* smem, uint64_t* mbar,
                                                uint32_t& phases, unsigned long long* s_next, uint32_t* s_bits) {
@@ -95,7 +106,7 @@ __device__ __forceinline__ bool ragged_segment(const RaggedArgs& args, const Rag
     auto hook = [&]() {  // the whole team, once sa/sb are free
       if (t == 0) take();
     };
-    polymul_unit<S, MODE, false>(args.c + unit.offset, twf, twi, pc, sa, sb, t, true, sync, hook);
+    polymul_unit_any<S, MODE, false, SEQ>(args.c + unit.offset, twf, twi, pc, sa, sb, t, true, sync, hook);
     sync();  // the leader's s_next[team] is visible
     cur = s_next[team];
   }
@@ -109,7 +120,7 @@ __device__ __forceinline__ bool ragged_segment(const RaggedArgs& args, const Rag
 // One instantiation serves the degrees 2^LO .. 2^HI: the 2^14 body (32
 // coefficients per thread) has a kernel of its own, so that its register
 // pressure (and the spills it causes) does not reach the other degrees.
-template <int MODE, int LO, int HI>
+template <int MODE, int LO, int HI, int SET>
 __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[kRaggedMaxTeams];
@@ -131,8 +142,9 @@ __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs arg
 #define PM_SEG(L)                                                                                      \
   case L:                                                                                              \
     if constexpr (L >= LO && L <= HI) {                                                                 \
-      ok = ragged_segment<RaggedShape<L>, MODE>(args, seg, ctr, smem, mbar, phases, s_next, bits);      \
-      teams = kRaggedThreads / RaggedShape<L>::T;                                                       \
+      ok = ragged_segment<RaggedShape<L, SET>, MODE, ragged_seq<L, SET>()>(args, seg, ctr, smem, mbar,  \
+                                                                           phases, s_next, bits);       \
+      teams = kRaggedThreads / RaggedShape<L, SET>::T;                                                  \
     }                                                                                                   \
     break;
       PM_SEG(10) PM_SEG(11) PM_SEG(12) PM_SEG(13) PM_SEG(14)
@@ -167,39 +179,38 @@ __global__ void __launch_bounds__(kRaggedThreads, 1) k_ntt_ragged(RaggedArgs arg
 }
 
 // dynamic shared memory of one degree class's team buffers
-template <int L>
+template <int L, int SET>
 constexpr int ragged_class_smem() {
-  return (kRaggedThreads / RaggedShape<L>::T) * RaggedShape<L>::SMEM_WORDS * 4;
+  return (kRaggedThreads / RaggedShape<L, SET>::T) * RaggedShape<L, SET>::SMEM_WORDS * 4;
 }
 
-template <int MODE, int LO, int HI>
+template <int MODE, int LO, int HI, int SET>
 static void ragged_info(KernelInfo* ki) {
-  ki->fn = (const void*)k_ntt_ragged<MODE, LO, HI>;
+  ki->fn = (const void*)k_ntt_ragged<MODE, LO, HI, SET>;
   ki->block = kRaggedThreads;
   int m = 0;
-  if (LO <= 10 && 10 <= HI) m = m > ragged_class_smem<10>() ? m : ragged_class_smem<10>();
-  if (LO <= 11 && 11 <= HI) m = m > ragged_class_smem<11>() ? m : ragged_class_smem<11>();
-  if (LO <= 12 && 12 <= HI) m = m > ragged_class_smem<12>() ? m : ragged_class_smem<12>();
-  if (LO <= 13 && 13 <= HI) m = m > ragged_class_smem<13>() ? m : ragged_class_smem<13>();
-  if (LO <= 14 && 14 <= HI) m = m > ragged_class_smem<14>() ? m : ragged_class_smem<14>();
+  if (LO <= 10 && 10 <= HI) m = m > ragged_class_smem<10, SET>() ? m : ragged_class_smem<10, SET>();
+  if (LO <= 11 && 11 <= HI) m = m > ragged_class_smem<11, SET>() ? m : ragged_class_smem<11, SET>();
+  if (LO <= 12 && 12 <= HI) m = m > ragged_class_smem<12, SET>() ? m : ragged_class_smem<12, SET>();
+  if (LO <= 13 && 13 <= HI) m = m > ragged_class_smem<13, SET>() ? m : ragged_class_smem<13, SET>();
+  if (LO <= 14 && 14 <= HI) m = m > ragged_class_smem<14, SET>() ? m : ragged_class_smem<14, SET>();
   ki->smem = m;
   ki->team = 0;
   ki->units_per_cta = 1;
   ki->tmem_cols = 0;
 }
 
-// small: degrees 2^10 .. 2^13; big: 2^14
-bool lookup_ntt_ragged(int mode, KernelInfo* small, KernelInfo* big) {
-  if (mode == 0) {
-    ragged_info<0, 10, 13>(small);
-    ragged_info<0, 14, 14>(big);
-  } else if (mode == 1) {
-    ragged_info<1, 10, 13>(small);
-    ragged_info<1, 14, 14>(big);
-  } else {
-    return false;
+// small: degrees 2^10 .. 2^13; big: 2^14; `set` as for RaggedShape
+bool lookup_ntt_ragged(int mode, int set, KernelInfo* small, KernelInfo* big) {
+#define PM_R(M, S)                    \
+  if (mode == M && set == S) {        \
+    ragged_info<M, 10, 13, S>(small); \
+    ragged_info<M, 14, 14, S>(big);   \
+    return true;                      \
   }
-  return true;
+  PM_R(0, 0) PM_R(0, 1) PM_R(1, 0) PM_R(1, 1)
+#undef PM_R
+  return false;
 }
 
 }  // namespace pm

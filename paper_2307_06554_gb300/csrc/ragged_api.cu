@@ -31,8 +31,8 @@ struct polymul_ragged {
   void* d_twf = nullptr;
   void* d_twi = nullptr;
   void* d_pc = nullptr;
-  KernelInfo ki[2];    // [0]: degrees 2^10 .. 2^13, [1]: 2^14
-  int grid_cap[2] = {0, 0};
+  KernelInfo ki[kRaggedSets][2];    // [shape set][0: degrees 2^10 .. 2^13, 1: 2^14]
+  int grid_cap[kRaggedSets][2] = {};
   int device = 0, num_sms = 0;
 };
 
@@ -53,6 +53,9 @@ struct polymul_ragged_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t node[2] = {nullptr, nullptr};
+  // shape set of each launch: the padded one-operand set by default (fewer
+  // registers, no spills at 2^14); polymul_ragged_tune measures both
+  int set[2] = {1, 1};
 };
 
 namespace {
@@ -134,18 +137,19 @@ extern "C" int polymul_ragged_create(const uint64_t* pool, uint32_t pool_size, u
   if (rc == POLYMUL_OK) rc = up(&r->d_twf, twf.data(), twf.size() * 4);
   if (rc == POLYMUL_OK) rc = up(&r->d_twi, twi.data(), twi.size() * 4);
   if (rc == POLYMUL_OK) rc = up(&r->d_pc, pcs.data(), pcs.size() * sizeof(PrimeConst<uint32_t>));
-  if (rc == POLYMUL_OK && !lookup_ntt_ragged(r->mode, &r->ki[0], &r->ki[1]))
-    rc = fail(POLYMUL_ENOTSUP, "no ragged kernel");
+  for (int set = 0; set < kRaggedSets && rc == POLYMUL_OK; ++set)
+    if (!lookup_ntt_ragged(r->mode, set, &r->ki[set][0], &r->ki[set][1])) rc = fail(POLYMUL_ENOTSUP, "no ragged kernel");
   if (rc == POLYMUL_OK) {
     cudaError_t e = cudaGetDevice(&r->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
-    for (int i = 0; i < 2 && e == cudaSuccess && rc == POLYMUL_OK; ++i) {
+    for (int k = 0; k < 2 * kRaggedSets && e == cudaSuccess && rc == POLYMUL_OK; ++k) {
+      const int set = k / 2, i = k % 2;
+      const KernelInfo& ki = r->ki[set][i];
       int per_sm = 0;
-      e = cudaFuncSetAttribute(r->ki[i].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->ki[i].smem);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, r->ki[i].fn, r->ki[i].block, r->ki[i].smem);
+      e = cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, ki.block, ki.smem);
       if (e == cudaSuccess && per_sm < 1) rc = fail(POLYMUL_ENOTSUP, "ragged kernel does not fit on an SM");
-      r->grid_cap[i] = per_sm * r->num_sms;
+      r->grid_cap[set][i] = per_sm * r->num_sms;
     }
     if (e != cudaSuccess) rc = cuda_fail(e, "ragged kernel configuration");
   }
@@ -256,8 +260,19 @@ int ragged_check(polymul_ragged_batch* b, const void* a, const void* bb, void* c
   if (((uintptr_t)a | (uintptr_t)bb | (uintptr_t)c) & 15u) return fail(POLYMUL_EINVAL, "operands must be 16-byte aligned");
   return POLYMUL_OK;
 }
+const KernelInfo& ragged_kernel(const polymul_ragged_batch* b, int part) { return b->ctx->ki[b->set[part]][part]; }
+// the recorded graph holds the kernels of the previous shape sets
+void drop_graph(polymul_ragged_batch* b) {
+  if (!b->exec) return;
+  cudaGraphExecDestroy(b->exec);
+  cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->node[0] = b->node[1] = nullptr;
+}
 int ragged_grid(const polymul_ragged_batch* b, int part) {
-  return (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap[part], std::max<uint64_t>(1, b->part_units[part]));
+  return (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap[b->set[part]][part],
+                                 std::max<uint64_t>(1, b->part_units[part]));
 }
 void set_operands(polymul_ragged_batch* b, const void* a, const void* bb, void* c) {
   for (int i = 0; i < 2; ++i) {
@@ -287,7 +302,8 @@ extern "C" int polymul_ragged_run(polymul_ragged_batch* b, const void* a, const 
     if (!b->part_units[i]) continue;
     void* argv[] = {&b->args[i]};
     cudaStream_t s = (both && i == 0) ? b->side : st;
-    PM_CUDA(cudaLaunchKernel(b->ctx->ki[i].fn, ragged_grid(b, i), b->ctx->ki[i].block, argv, b->ctx->ki[i].smem, s));
+    const KernelInfo& ki = ragged_kernel(b, i);
+    PM_CUDA(cudaLaunchKernel(ki.fn, ragged_grid(b, i), ki.block, argv, ki.smem, s));
   }
   if (both) {
     PM_CUDA(cudaEventRecord(b->ev_join, b->side));
@@ -310,10 +326,11 @@ extern "C" int polymul_ragged_run_graph(polymul_ragged_batch* b, const void* a, 
   void* argv[2][1] = {{&b->args[0]}, {&b->args[1]}};
   for (int i = 0; i < 2; ++i) {
     memset(&kp[i], 0, sizeof kp[i]);
-    kp[i].func = const_cast<void*>(b->ctx->ki[i].fn);
+    const KernelInfo& ki = ragged_kernel(b, i);
+    kp[i].func = const_cast<void*>(ki.fn);
     kp[i].gridDim = dim3(ragged_grid(b, i));
-    kp[i].blockDim = dim3(b->ctx->ki[i].block);
-    kp[i].sharedMemBytes = b->ctx->ki[i].smem;
+    kp[i].blockDim = dim3(ki.block);
+    kp[i].sharedMemBytes = ki.smem;
     kp[i].kernelParams = argv[i];
   }
   if (!b->exec) {
@@ -348,5 +365,62 @@ extern "C" int polymul_ragged_batch_info(const polymul_ragged_batch* b, uint64_t
   if (units) *units = b->n_units;
   if (items) *items = b->n_items;
   if (grid) *grid = (uint32_t)std::max(b->part_units[0] ? ragged_grid(b, 0) : 0, b->part_units[1] ? ragged_grid(b, 1) : 0);
+  return POLYMUL_OK;
+}
+
+// The shape set of each of the list's launches, by measurement on the
+// caller's operands (Sec. 2.6 leaves the shapes to experiment): each launch
+// alone, with each set, three timed rounds after a warm-up, the minimum per
+// set.  The graph, if any, is rebuilt on its next replay.  Synchronous.
+extern "C" int polymul_ragged_tune(polymul_ragged_batch* b, const void* a, const void* bb, void* c, void* stream,
+                                   uint32_t* choice) {
+  clear_error();
+  TraceRange trace_("polymul_ragged_tune");
+  int rc = ragged_check(b, a, bb, c);
+  if (rc != POLYMUL_OK) return rc;
+  set_operands(b, a, bb, c);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PM_CUDA(cudaEventCreate(&e0));
+  PM_CUDA(cudaEventCreate(&e1));
+  for (int part = 0; part < 2 && rc == POLYMUL_OK; ++part) {
+    if (!b->part_units[part]) continue;
+    float best[kRaggedSets];
+    for (int set = 0; set < kRaggedSets; ++set) best[set] = 1e30f;
+    for (int round = 0; round < 4 && rc == POLYMUL_OK; ++round) {
+      for (int set = 0; set < kRaggedSets && rc == POLYMUL_OK; ++set) {
+        b->set[part] = set;
+        const KernelInfo& ki = ragged_kernel(b, part);
+        void* argv[] = {&b->args[part]};
+        cudaError_t e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = cudaLaunchKernel(ki.fn, ragged_grid(b, part), ki.block, argv, ki.smem, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ragged tuning launch");
+        if (round > 0 && ms < best[set]) best[set] = ms;  // round 0 warms up
+      }
+    }
+    int pick = 0;
+    for (int set = 1; set < kRaggedSets; ++set)
+      if (best[set] < best[pick]) pick = set;
+    b->set[part] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != POLYMUL_OK) return rc;
+  drop_graph(b);
+  if (choice) *choice = (uint32_t)b->set[0] | ((uint32_t)b->set[1] << 1);
+  return polymul_ragged_status(b, stream);
+}
+
+extern "C" int polymul_ragged_select(polymul_ragged_batch* b, uint32_t choice) {
+  clear_error();
+  if (!b) return fail(POLYMUL_EINVAL, "batch is NULL");
+  if (choice > 3) return fail(POLYMUL_EINVAL, "choice=%u must be in [0, 3]", choice);
+  b->set[0] = (int)(choice & 1u);
+  b->set[1] = (int)((choice >> 1) & 1u);
+  drop_graph(b);
   return POLYMUL_OK;
 }

@@ -58,8 +58,9 @@ struct ServeReq {
   const void* ha = nullptr;
   const void* hb = nullptr;
   void* hc = nullptr;
-  double t_submit = 0, t_done = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
   int state = 0;  // 0 queued, 1 in flight, 2 done, 3 failed (CUDA error), 4 failed (device wait expired)
+  int outcome = 0;  // the state it will take, decided by the server thread before it publishes it
   size_t off = 0, bytes = 0;
   int lane = 0;
   int slot = -1;  // page-locked word that receives the lane's error word after the kernel
@@ -82,19 +83,34 @@ struct polymul_server {
   unsigned long long* d_ctr = nullptr;  // 2 per lane
   int* d_err = nullptr;                 // one error word per lane
   int* h_err = nullptr;                 // page-locked, one per in-flight slot
+  // page-locked staging of each in-flight slot's prime-index map (pool size
+  // words per slot): a copy from pageable memory would first wait for the
+  // lane's stream to drain, stalling the server thread behind large requests
+  uint32_t* h_map = nullptr;
   std::vector<int> free_slots;
   char* d_arena = nullptr;
   size_t arena_bytes = 0, arena_used = 0, arena_peak = 0;
   std::map<size_t, size_t> free_list;  // offset -> size
   size_t max_inflight = 64;
+  // shared with submitting and waiting threads, under `mu`: the submission
+  // queue, the tickets, the published states and statistics
   std::mutex mu;
   std::condition_variable cv;
   std::deque<ServeReq*> queue;
-  std::vector<ServeReq*> inflight;
   std::unordered_map<uint64_t, ServeReq*> reqs;
-  std::vector<cudaEvent_t> event_pool;
-  std::vector<double> latencies_us;
+  std::vector<double> latencies_us, queue_us, service_us;
+  double issue_s = 0, loop_busy_s = 0;  // server-thread time issuing requests, and in passes that did work
+  uint64_t issued = 0;
   uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0;
+  size_t published_inflight = 0, published_pending = 0;
+  // owned by the server thread alone (no lock): requests taken from the
+  // queue and not yet admitted, the requests in flight on each lane in issue
+  // order (a lane is one stream, so they complete in that order), the
+  // arena, slots, events and lane loads
+  std::deque<ServeReq*> pending;
+  std::vector<std::deque<ServeReq*>> lane_fifo;
+  size_t inflight = 0;
+  std::vector<cudaEvent_t> event_pool;
   std::vector<uint64_t> lane_bytes;  // bytes of the requests in flight on each lane
   std::atomic<bool> stop{false};
   std::thread loop;
@@ -143,7 +159,7 @@ size_t request_bytes(uint32_t n, uint32_t k) {
   return 3 * ((row + kArenaAlign - 1) / kArenaAlign * kArenaAlign) + map;
 }
 
-// issue copy-in, kernel, copy-out and the completion event (lock held)
+// issue copy-in, kernel, copy-out and the completion event (server thread)
 cudaError_t issue(polymul_server* s, ServeReq* r) {
   const size_t row = (size_t)r->k * r->n * 8;
   const size_t rowa = (row + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
@@ -154,7 +170,9 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
   uint32_t* dmap = reinterpret_cast<uint32_t*>(base + 3 * rowa);
   cudaStream_t st = s->lanes[r->lane];
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(dmap, r->primes.data(), r->k * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  uint32_t* hmap = s->h_map + (size_t)r->slot * s->pool.size();
+  std::copy(r->primes.begin(), r->primes.end(), hmap);
+  if ((e = cudaMemcpyAsync(dmap, hmap, r->k * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(da, r->ha, row, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(db, r->hb, row, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   const KernelInfo& ki = s->ki[r->logn];
@@ -194,35 +212,43 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
   return cudaEventRecord(r->ev, st);
 }
 
+// The server thread.  Each pass: take the new submissions (under the lock),
+// retire what has completed, admit what fits (CUDA calls without the lock,
+// so that submitters never wait behind them), then publish the outcomes
+// (under the lock).  While work is in flight it polls with a yield; with
+// nothing in flight and nothing queued it sleeps on the condition variable
+// until a submission arrives.
 void server_loop(polymul_server* s) {
   cudaSetDevice(s->device);
+  std::vector<ServeReq*> done;
+  std::string err_msg;
   while (!s->stop.load()) {
     bool progress = false;
+    const double t_pass = now_s();
+    double issue_time = 0;
+    uint64_t issued = 0;
     {
-      std::unique_lock<std::mutex> lock(s->mu);
-      // retire completed requests
-      for (size_t i = 0; i < s->inflight.size();) {
-        ServeReq* r = s->inflight[i];
+      std::lock_guard<std::mutex> lock(s->mu);
+      while (!s->queue.empty()) {
+        s->pending.push_back(s->queue.front());
+        s->queue.pop_front();
+      }
+    }
+    // retire: only the oldest request of each lane can be the next to finish
+    for (int l = 0; l < s->nlanes; ++l) {
+      std::deque<ServeReq*>& f = s->lane_fifo[l];
+      while (!f.empty()) {
+        ServeReq* r = f.front();
         const cudaError_t q = cudaEventQuery(r->ev);
-        if (q == cudaErrorNotReady) {
-          ++i;
-          continue;
-        }
+        if (q == cudaErrorNotReady) break;
         r->t_done = now_s();
         if (q != cudaSuccess) {
-          r->state = 3;
-          s->cuda_error = 1;
-          s->cuda_error_msg = cudaGetErrorString(q);
-          ++s->failed;
-        } else if (s->h_err[r->slot] != 0) {
-          // a bounded device wait of the request's kernel expired: its
-          // result is invalid
-          r->state = 4;
-          ++s->failed;
+          r->outcome = 3;
+          err_msg = cudaGetErrorString(q);
         } else {
-          r->state = 2;
-          s->latencies_us.push_back((r->t_done - r->t_submit) * 1e6);
-          ++s->completed;
+          // a nonzero error word: a bounded device wait of the request's
+          // kernel expired and its result is invalid
+          r->outcome = s->h_err[r->slot] != 0 ? 4 : 2;
         }
         s->free_slots.push_back(r->slot);
         r->slot = -1;
@@ -230,60 +256,89 @@ void server_loop(polymul_server* s) {
         s->lane_bytes[r->lane] -= r->bytes;
         s->event_pool.push_back(r->ev);
         r->ev = nullptr;
-        s->inflight[i] = s->inflight.back();
-        s->inflight.pop_back();
-        progress = true;
-      }
-      // admit in arrival order while memory and slots allow
-      while (!s->queue.empty() && s->inflight.size() < s->max_inflight) {
-        ServeReq* r = s->queue.front();
-        const size_t off = arena_alloc(s, r->bytes);
-        if (off == (size_t)-1) break;
-        r->off = off;
-        // the lane with the least work in flight: a small request does not
-        // queue behind a large one while another lane is idle
-        int lane = 0;
-        for (int l = 1; l < s->nlanes; ++l)
-          if (s->lane_bytes[l] < s->lane_bytes[lane]) lane = l;
-        r->lane = lane;
-        s->lane_bytes[lane] += r->bytes;
-        if (s->event_pool.empty()) {
-          cudaEvent_t ev;
-          cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-          s->event_pool.push_back(ev);
-        }
-        r->ev = s->event_pool.back();
-        s->event_pool.pop_back();
-        r->slot = s->free_slots.back();  // fewer than max_inflight requests are in flight
-        s->free_slots.pop_back();
-        s->h_err[r->slot] = 0;
-        const cudaError_t e = issue(s, r);
-        s->queue.pop_front();
-        if (e != cudaSuccess) {
-          s->cuda_error = 1;
-          s->cuda_error_msg = cudaGetErrorString(e);
-          r->state = 3;
-          r->t_done = now_s();
-          ++s->failed;
-          s->free_slots.push_back(r->slot);
-          r->slot = -1;
-          arena_free(s, r->off, r->bytes);
-          s->lane_bytes[r->lane] -= r->bytes;
-          s->event_pool.push_back(r->ev);
-          r->ev = nullptr;
-        } else {
-          r->state = 1;
-          s->inflight.push_back(r);
-        }
-        progress = true;
-      }
-      if (progress) s->cv.notify_all();
-      if (!progress && s->inflight.empty() && s->queue.empty()) {
-        s->cv.wait_for(lock, std::chrono::milliseconds(1));
-        continue;
+        f.pop_front();
+        --s->inflight;
+        done.push_back(r);
       }
     }
-    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(5));
+    // admit in arrival order while memory and slots allow
+    while (!s->pending.empty() && s->inflight < s->max_inflight) {
+      ServeReq* r = s->pending.front();
+      const size_t off = arena_alloc(s, r->bytes);
+      if (off == (size_t)-1) break;
+      r->off = off;
+      // the lane with the least work in flight: a small request does not
+      // queue behind a large one while another lane is idle
+      int lane = 0;
+      for (int l = 1; l < s->nlanes; ++l)
+        if (s->lane_bytes[l] < s->lane_bytes[lane]) lane = l;
+      r->lane = lane;
+      s->lane_bytes[lane] += r->bytes;
+      if (s->event_pool.empty()) {
+        cudaEvent_t ev;
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        s->event_pool.push_back(ev);
+      }
+      r->ev = s->event_pool.back();
+      s->event_pool.pop_back();
+      r->slot = s->free_slots.back();  // fewer than max_inflight requests are in flight
+      s->free_slots.pop_back();
+      s->h_err[r->slot] = 0;
+      r->t_admit = now_s();
+      const cudaError_t e = issue(s, r);
+      issue_time += now_s() - r->t_admit;
+      ++issued;
+      s->pending.pop_front();
+      if (e != cudaSuccess) {
+        err_msg = cudaGetErrorString(e);
+        r->outcome = 3;
+        r->t_done = now_s();
+        s->free_slots.push_back(r->slot);
+        r->slot = -1;
+        arena_free(s, r->off, r->bytes);
+        s->lane_bytes[r->lane] -= r->bytes;
+        s->event_pool.push_back(r->ev);
+        r->ev = nullptr;
+        done.push_back(r);
+      } else {
+        s->lane_fifo[lane].push_back(r);
+        ++s->inflight;
+      }
+      progress = true;
+    }
+    if (!done.empty() || progress) {
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->issue_s += issue_time;
+      s->issued += issued;
+      s->loop_busy_s += now_s() - t_pass;
+      for (ServeReq* r : done) {
+        r->state = r->outcome;
+        if (r->outcome == 2) {
+          s->latencies_us.push_back((r->t_done - r->t_submit) * 1e6);
+          s->queue_us.push_back((r->t_admit - r->t_submit) * 1e6);
+          s->service_us.push_back((r->t_done - r->t_admit) * 1e6);
+          ++s->completed;
+        } else {
+          ++s->failed;
+          if (r->outcome == 3) {
+            s->cuda_error = 1;
+            s->cuda_error_msg = err_msg;
+          }
+        }
+      }
+      s->published_inflight = s->inflight;
+      s->published_pending = s->pending.size();
+      if (!done.empty()) s->cv.notify_all();
+      progress = progress || !done.empty();
+      done.clear();
+    }
+    if (progress) continue;
+    if (s->inflight == 0 && s->pending.empty()) {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->cv.wait_for(lock, std::chrono::milliseconds(1), [&] { return !s->queue.empty() || s->stop.load(); });
+    } else {
+      std::this_thread::yield();
+    }
   }
 }
 
@@ -348,6 +403,7 @@ extern "C" void polymul_server_destroy(polymul_server* s) {
   cudaFree(s->d_err);
   cudaFree(s->d_arena);
   if (s->h_err) cudaFreeHost(s->h_err);
+  if (s->h_map) cudaFreeHost(s->h_map);
   delete s;
 }
 
@@ -374,6 +430,8 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
   s->pool.assign(pool, pool + pool_size);
   s->nlanes = (int)lanes;
   s->lane_bytes.assign(lanes, 0);
+  s->lane_fifo.resize(lanes);
+  s->max_inflight = std::max<size_t>(64, 8 * (size_t)lanes);  // enough requests to keep every lane busy
   int rc = POLYMUL_OK;
   auto bail = [&](int code) {
     std::string keep = polymul_last_error();
@@ -393,7 +451,8 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
       cudaMalloc(&s->d_ctr, 2 * lanes * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&s->d_err, lanes * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&s->d_arena, device_bytes) != cudaSuccess ||
-      cudaHostAlloc(&s->h_err, s->max_inflight * sizeof(int), cudaHostAllocDefault) != cudaSuccess)
+      cudaHostAlloc(&s->h_err, s->max_inflight * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&s->h_map, s->max_inflight * pool_size * sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess)
     return bail(fail(POLYMUL_ENOMEM, "device allocation failed"));
   for (int i = (int)s->max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
   if (cudaMemcpy(s->d_twf, twf.data(), twf.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -574,23 +633,36 @@ extern "C" int polymul_server_stats_get(polymul_server* s, polymul_server_stats*
   out->submitted = s->submitted;
   out->completed = s->completed;
   out->failed = s->failed;
-  out->queued = s->queue.size();
-  out->in_flight = s->inflight.size();
+  out->queued = s->queue.size() + s->published_pending;
+  out->in_flight = s->published_inflight;
   out->arena_bytes = s->arena_bytes;
   out->arena_peak_bytes = s->arena_peak;
-  std::vector<double> l = s->latencies_us;
-  if (!l.empty()) {
+  auto pct = [](std::vector<double> l, double p) {
+    if (l.empty()) return 0.0;
     std::sort(l.begin(), l.end());
-    auto pct = [&](double p) { return l[std::min(l.size() - 1, (size_t)(p * (l.size() - 1) + 0.5))]; };
-    out->p50_us = pct(0.50);
-    out->p99_us = pct(0.99);
-    out->max_us = l.back();
+    return l[std::min(l.size() - 1, (size_t)(p * (l.size() - 1) + 0.5))];
+  };
+  const std::vector<double>& l = s->latencies_us;
+  if (!l.empty()) {
+    out->p50_us = pct(l, 0.50);
+    out->p99_us = pct(l, 0.99);
+    out->max_us = pct(l, 1.0);
     double sum = 0;
     for (double x : l) sum += x;
     out->mean_us = sum / l.size();
+    out->queue_p50_us = pct(s->queue_us, 0.50);
+    out->queue_p99_us = pct(s->queue_us, 0.99);
+    out->service_p50_us = pct(s->service_us, 0.50);
+    out->service_p99_us = pct(s->service_us, 0.99);
   }
+  out->issue_us_mean = s->issued ? s->issue_s / s->issued * 1e6 : 0.0;
+  out->server_busy_s = s->loop_busy_s;
   if (reset) {
     s->latencies_us.clear();
+    s->queue_us.clear();
+    s->service_us.clear();
+    s->issue_s = s->loop_busy_s = 0;
+    s->issued = 0;
     s->completed = s->submitted = s->failed = 0;
     s->arena_peak = s->arena_used;
   }

@@ -73,7 +73,9 @@ class polymul_request(ctypes.Structure):
 class polymul_server_stats(ctypes.Structure):
     _fields_ = [(x, ctypes.c_uint64) for x in ("submitted", "completed", "failed", "queued", "in_flight",
                                                "arena_bytes", "arena_peak_bytes")] + \
-               [(x, ctypes.c_double) for x in ("p50_us", "p99_us", "mean_us", "max_us")]
+               [(x, ctypes.c_double) for x in ("p50_us", "p99_us", "mean_us", "max_us", "queue_p50_us",
+                                               "queue_p99_us", "service_p50_us", "service_p99_us", "issue_us_mean",
+                                               "server_busy_s")]
 
 
 def library_path() -> str:
@@ -127,6 +129,10 @@ def _load():
         getattr(lib, name).restype = i32
     lib.polymul_ragged_status.argtypes = [vp, vp]
     lib.polymul_ragged_status.restype = i32
+    lib.polymul_ragged_tune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(u32)]
+    lib.polymul_ragged_tune.restype = i32
+    lib.polymul_ragged_select.argtypes = [vp, u32]
+    lib.polymul_ragged_select.restype = i32
     lib.polymul_ragged_batch_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u32)]
     lib.polymul_ragged_batch_info.restype = i32
     lib.polymul_ragged_batch_destroy.argtypes = [vp]
@@ -381,6 +387,14 @@ def polymul_ragged_status(batch: int, stream=None) -> None:
     _check(_lib.polymul_ragged_status(batch, _stream(stream)))
 
 
+def polymul_ragged_tune(batch: int, a, b, c, stream=None) -> int:
+    """Pick each launch's shape set by measurement; returns the choice bits
+    (bit 0: degrees 2^10..2^13, bit 1: 2^14)."""
+    ch = ctypes.c_uint32(0)
+    _check(_lib.polymul_ragged_tune(batch, _ptr(a), _ptr(b), _ptr(c), _stream(stream), ctypes.byref(ch)))
+    return ch.value
+
+
 def polymul_ragged_batch_info(batch: int) -> dict:
     u, i, g = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint32()
     _check(_lib.polymul_ragged_batch_info(batch, ctypes.byref(u), ctypes.byref(i), ctypes.byref(g)))
@@ -419,6 +433,12 @@ class Ragged:
 
     def run(self, a, b, c, stream=None, graph=False):
         (polymul_ragged_run_graph if graph else polymul_ragged_run)(self.batch, a, b, c, stream)
+
+    def tune(self, a, b, c, stream=None) -> int:
+        return polymul_ragged_tune(self.batch, a, b, c, stream)
+
+    def select(self, choice: int) -> None:
+        _check(_lib.polymul_ragged_select(self.batch, choice))
 
     def close(self):
         if getattr(self, "batch", None):

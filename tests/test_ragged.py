@@ -32,13 +32,18 @@ def _pack(rag):
     return a, b
 
 
-def _run(pm, rag, nmax=16384, graph=False):
+def _run(pm, rag, nmax=16384, graph=False, choice=None, tune=False):
     import torch
     a, b = _pack(rag)
     with pm.Ragged(rag.pool, nmax, [(p.n, p.prime_idx) for p in rag.products]) as r:
         ta = torch.from_numpy(a.view(np.int32)).cuda()
         tb = torch.from_numpy(b.view(np.int32)).cuda()
         tc = torch.full_like(ta, -1)
+        if choice is not None:
+            r.select(choice)
+        if tune:
+            assert 0 <= r.tune(ta, tb, tc) <= 3
+            tc.fill_(-1)
         r.run(ta, tb, tc, graph=graph)
         pm.polymul_ragged_status(r.batch)
         offsets = list(r.offsets)
@@ -140,3 +145,21 @@ def test_prepare_rejects_bad_descriptors(pm):
         pm.polymul_ragged_destroy(ctx)
     with pytest.raises(pm.PolymulError):
         pm.polymul_ragged_create([3329], 1024)  # 3329 - 1 is not divisible by 2048
+
+
+@pytest.mark.parametrize("choice", [0, 1, 2, 3])
+def test_every_shape_set_is_exact(pm, choice):
+    """Both shape sets of both launches (swizzled / padded exchanges, one or
+    both operands in registers), on a list that has every degree class."""
+    rag = wl.ragged_2000(count=25, seed=32)
+    assert {p.n for p in rag.products} == {1024, 2048, 4096, 8192, 16384}
+    c, offsets = _run(pm, rag, choice=choice)
+    _check(rag, c, offsets, range(len(rag.products)))
+
+
+def test_tuned_list_is_exact_direct_and_graph(pm):
+    rag = wl.ragged_2000(count=25, seed=35)
+    c, offsets = _run(pm, rag, tune=True)
+    _check(rag, c, offsets, range(len(rag.products)))
+    c, offsets = _run(pm, rag, tune=True, graph=True)
+    _check(rag, c, offsets, range(len(rag.products)))
