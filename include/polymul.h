@@ -476,7 +476,11 @@ typedef struct polymul_server_stats {
                                                that admitted or retired work */
 } polymul_server_stats;
 
-/* Start a server on the current device.  Errors: EINVAL, ENOMEM, ENOTSUP. */
+/* Start a server on the current device.  Each lane is three streams (copies
+ * in, kernels, copies out); with more than 8 streams in the process, set
+ * CUDA_DEVICE_MAX_CONNECTIONS (up to 32) before the CUDA context is created,
+ * or streams share hardware queues and lanes wait on each other.  Errors:
+ * EINVAL, ENOMEM, ENOTSUP. */
 int polymul_server_create(const uint64_t *pool, uint32_t pool_size, uint32_t n_max,
                           uint64_t device_bytes, uint32_t lanes, polymul_server **out);
 /* Queue one request (asynchronous); *ticket identifies it. */

@@ -207,8 +207,13 @@ bool lookup_ntt(uint32_t elem, int logn, int mode, KernelInfo* ki) {
   // 512 products); the cluster kernel stays an autotuner candidate
   if (elem == 4 && logn == 14 && lookup_ntt_u32_rb5(logn, mode, ki)) return true;
   if (logn >= 14) {
-    // beyond one CTA: one product per thread-block cluster; the unreduced
-    // mode falls back to Harvey's bounds where it is not instantiated
+    // beyond one CTA: one product per thread-block cluster, the form with
+    // CTA-local exchanges (measured on GB300 against the first form: 64-bit
+    // words with both operands in registers 1.38-1.49x faster at 2^14 ..
+    // 2^16; 32-bit words one operand at a time 1.2x at 2^15, 2^16); the
+    // unreduced mode takes the Harvey-bound kernels, whose bounds hold for
+    // its moduli too
+    if (lookup_ntt_cluster2(elem, logn, mode == 2 ? 1 : mode, elem == 4, ki)) return true;
     return lookup_ntt_cluster(elem, logn, mode, ki) || (mode == 2 && lookup_ntt_cluster(elem, logn, 1, ki));
   }
   if (elem == 4) {
@@ -379,6 +384,18 @@ extern "C" int polymul_create(uint32_t n, const uint64_t* q_list, uint32_t k, co
     if (rc == POLYMUL_OK && p->elem == 4 && p->logn == 14 &&
         (lookup_ntt_cluster(4, 14, p->mode, &v) || lookup_ntt_cluster(4, 14, 1, &v)))
       rc = add_candidate(POLYMUL_PATH_NTT, v);
+    // the cluster kernels not already the default: the second form's other
+    // operand scheme, and the first form
+    if (p->logn >= 14) {
+      const int cm = p->mode == 2 ? 1 : p->mode;
+      for (int seq = 0; seq < 2; ++seq)
+        if (rc == POLYMUL_OK && lookup_ntt_cluster2(p->elem, (int)p->logn, cm, seq != 0, &v) &&
+            v.fn != p->cands[0].ki.fn)
+          rc = add_candidate(POLYMUL_PATH_NTT, v);
+      if (rc == POLYMUL_OK && p->logn >= 15 &&
+          (lookup_ntt_cluster(p->elem, (int)p->logn, p->mode, &v) || lookup_ntt_cluster(p->elem, (int)p->logn, 1, &v)))
+        rc = add_candidate(POLYMUL_PATH_NTT, v);
+    }
     if (rc == POLYMUL_OK && p->elem == 4 && lookup_ntt_u32_rb3((int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && p->logn < 14 && lookup_ntt_alt(p->elem, (int)p->logn, p->mode, &v)) rc = add_candidate(POLYMUL_PATH_NTT, v);
     if (rc == POLYMUL_OK && path == POLYMUL_PATH_AUTO && tensor_ok) rc = add_tensor_candidates(add_candidate);

@@ -46,6 +46,9 @@ bool lookup_ntt_shared(int logn, int mode, KernelInfo* prep, KernelInfo* main);
 
 // one product per thread-block cluster (n = 2^14 .. 2^16)
 bool lookup_ntt_cluster(uint32_t elem, int logn, int mode, KernelInfo* ki);
+// its second form: CTA-local exchanges except the top phase's, padded
+// layout; one operand in registers at a time (seq) or both (mode 1 only)
+bool lookup_ntt_cluster2(uint32_t elem, int logn, int mode, bool seq, KernelInfo* ki);
 
 // uneven batches (32-bit words): one persistent kernel for the degrees
 // 2^10..2^13 and one for 2^14, in two shape sets (0: swizzled exchanges,

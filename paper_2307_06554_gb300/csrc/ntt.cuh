@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       if (__any_sync(0xffffffffu, !ok)) {
         // record the failure, let the copy in flight land, and leave through
         // the finish protocol so that the work counter is reset as usual
-        if (lane == 0) atomicExch(args.err, 1);
+        if (lane == 0) atomicExch_system(args.err, 1);
         mbar_wait(bar, parity, polls);
         break;
       }
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       const uint64_t u = cur + team;
       const bool act = u < units;
       const uint32_t j = act ? (uint32_t)(u % k) : 0u;
-      const uint32_t pj = AUX ? 0u : (args.pmap ? args.pmap[j] : j);
+      const uint32_t pj = AUX ? 0u : table_index(args, j);
       const PrimeConst<W> pc = args.pc[(size_t)pj * args.pc_stride + args.pc_off];
       const W qo = AUX ? args.outer_q[j] : W(0);
       unsigned long long nxt = units;
@@ -779,13 +779,13 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     while (cur < units) {
       const bool ok = mbar_wait(bar, parity, polls);
       if (__syncthreads_or(!ok)) {  // as in the warp-team path
-        if (threadIdx.x == 0) atomicExch(args.err, 1);
+        if (threadIdx.x == 0) atomicExch_system(args.err, 1);
         mbar_wait(bar, parity, polls);
         break;
       }
       parity ^= 1u;
       const uint32_t j = (uint32_t)(cur % k);
-      const uint32_t pj = AUX ? 0u : (args.pmap ? args.pmap[j] : j);
+      const uint32_t pj = AUX ? 0u : table_index(args, j);
       const PrimeConst<W> pc = args.pc[(size_t)pj * args.pc_stride + args.pc_off];
       const W qo = AUX ? args.outer_q[j] : W(0);
       auto hook = [&]() {  // every thread, after a barrier: all are done with sa/sb

@@ -49,7 +49,24 @@ struct NttBatchArgs {
   // expire after wait_polls polls, the path of a copy that never completes.
   uint32_t tx_pad;
   uint32_t wait_polls;
+  // unit prime j's table index as 8-bit fields (index j in byte j & 3 of word
+  // j >> 2) when pmap_inline is set: up to 32 primes of a pool of at most
+  // 256, carried by the launch itself instead of a device array
+  uint32_t pmap_inline;
+  uint32_t pmap_pack[8];
 };
+
+// table index of unit prime j (see NttBatchArgs::pmap, pmap_pack)
+template <typename W>
+__device__ __forceinline__ uint32_t table_index(const NttBatchArgs<W>& args, uint32_t j) {
+  if (args.pmap_inline) {
+    uint32_t w = args.pmap_pack[0];
+#pragma unroll
+    for (uint32_t i = 1; i < 8; ++i) w = (j >> 2) == i ? args.pmap_pack[i] : w;  // no dynamic parameter index
+    return (w >> (8 * (j & 3))) & 255u;
+  }
+  return args.pmap ? args.pmap[j] : j;
+}
 
 // Ragged (uneven) batches: one unit = one (product, prime) row of n words.
 // Degree segments per list: at most one per degree; the work counters of a

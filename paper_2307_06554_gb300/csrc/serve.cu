@@ -64,7 +64,9 @@ struct ServeReq {
   size_t off = 0, bytes = 0;
   int lane = 0;
   int slot = -1;  // page-locked word that receives the lane's error word after the kernel
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;     // the result is in host memory (end of the copy-out stage)
+  cudaEvent_t ev_in = nullptr;  // operands are on the device (end of the copy-in stage)
+  cudaEvent_t ev_k = nullptr;   // the kernel is done
 };
 
 }  // namespace
@@ -79,10 +81,18 @@ struct polymul_server {
   int grid_cap[kServeMaxLog + 1] = {};
   int device = 0, num_sms = 0;
   int nlanes = 0;
-  std::vector<cudaStream_t> lanes;
+  // each lane is a three-stage pipeline: copies in, kernels, copies out, on
+  // streams of their own joined by events, so that a request's copies in do
+  // not wait for the previous request's kernel and copy out on the lane
+  std::vector<cudaStream_t> lanes, lanes_in, lanes_out;
   unsigned long long* d_ctr = nullptr;  // 2 per lane
   int* d_err = nullptr;                 // one error word per lane
   int* h_err = nullptr;                 // page-locked, one per in-flight slot
+  // where the device supports native atomics on host memory, h_err is also
+  // mapped into the device's address space (d_err_mapped): each request's
+  // kernel reports into its slot's word directly, with no copy or reset on
+  // the lane; otherwise the lane's device word is copied back and cleared
+  int* d_err_mapped = nullptr;
   // page-locked staging of each in-flight slot's prime-index map (pool size
   // words per slot): a copy from pageable memory would first wait for the
   // lane's stream to drain, stalling the server thread behind large requests
@@ -168,20 +178,32 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
   uint64_t* db = reinterpret_cast<uint64_t*>(base + rowa);
   uint64_t* dc = reinterpret_cast<uint64_t*>(base + 2 * rowa);
   uint32_t* dmap = reinterpret_cast<uint32_t*>(base + 3 * rowa);
-  cudaStream_t st = s->lanes[r->lane];
+  cudaStream_t st = s->lanes[r->lane], st_in = s->lanes_in[r->lane], st_out = s->lanes_out[r->lane];
   cudaError_t e;
-  uint32_t* hmap = s->h_map + (size_t)r->slot * s->pool.size();
-  std::copy(r->primes.begin(), r->primes.end(), hmap);
-  if ((e = cudaMemcpyAsync(dmap, hmap, r->k * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(da, r->ha, row, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(db, r->hb, row, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  // the prime map rides in the launch's arguments when it fits (up to 32
+  // primes of a pool of at most 256), else it is copied to the arena
+  const bool inline_map = r->k <= 32 && s->pool.size() <= 256;
+  if (!inline_map) {
+    uint32_t* hmap = s->h_map + (size_t)r->slot * s->pool.size();
+    std::copy(r->primes.begin(), r->primes.end(), hmap);
+    if ((e = cudaMemcpyAsync(dmap, hmap, r->k * 4, cudaMemcpyHostToDevice, st_in)) != cudaSuccess) return e;
+  }
+  if ((e = cudaMemcpyAsync(da, r->ha, row, cudaMemcpyHostToDevice, st_in)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(db, r->hb, row, cudaMemcpyHostToDevice, st_in)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(r->ev_in, st_in)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st, r->ev_in, 0)) != cudaSuccess) return e;
   const KernelInfo& ki = s->ki[r->logn];
   uint32_t tx_pad = 0, polls = 0;
   if (ki.cluster == 0) take_injected_wait(&tx_pad, &polls);
   int* lane_err = s->d_err + r->lane;
+  int* err = s->d_err_mapped ? s->d_err_mapped + r->slot : lane_err;
   NttBatchArgs<uint64_t> args{da,      db,       dc,      s->d_twf, s->d_twi, (const PrimeConst<uint64_t>*)s->d_pc,
-                              r->k,    r->k,     s->d_ctr + 2 * r->lane, lane_err, nullptr, dmap,
+                              r->k,    r->k,     s->d_ctr + 2 * r->lane, err, nullptr, inline_map ? nullptr : dmap,
                               s->nmax, (uint32_t)(kServeMaxLog + 1), r->logn, 0u, tx_pad, polls};
+  if (inline_map) {
+    args.pmap_inline = 1;
+    for (uint32_t i = 0; i < r->k; ++i) args.pmap_pack[i >> 2] |= r->primes[i] << (8 * (i & 3));
+  }
   void* argv[] = {&args};
   if (ki.cluster > 0) {
     const int clusters = std::min<int>((int)r->k, s->grid_cap[r->logn] / ki.cluster);
@@ -203,13 +225,38 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
     const int grid = std::min<int>((int)((r->k + ki.units_per_cta - 1) / ki.units_per_cta), s->grid_cap[r->logn]);
     if ((e = cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st)) != cudaSuccess) return e;
   }
-  if ((e = cudaMemcpyAsync(r->hc, dc, row, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-  // the lane's error word belongs to this request until the next one on the
-  // lane starts: bring it back with the result, then clear it
-  if ((e = cudaMemcpyAsync(s->h_err + r->slot, lane_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-    return e;
-  if ((e = cudaMemsetAsync(lane_err, 0, sizeof(int), st)) != cudaSuccess) return e;
-  return cudaEventRecord(r->ev, st);
+  if (!s->d_err_mapped) {
+    // the lane's error word belongs to this request until the lane's next
+    // kernel: bring it back, then clear it, in the kernel stage
+    if ((e = cudaMemcpyAsync(s->h_err + r->slot, lane_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemsetAsync(lane_err, 0, sizeof(int), st)) != cudaSuccess) return e;
+  }
+  if ((e = cudaEventRecord(r->ev_k, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st_out, r->ev_k, 0)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(r->hc, dc, row, cudaMemcpyDeviceToHost, st_out)) != cudaSuccess) return e;
+  return cudaEventRecord(r->ev, st_out);
+}
+
+void take_events(polymul_server* s, ServeReq* r) {
+  cudaEvent_t* evs[3] = {&r->ev, &r->ev_in, &r->ev_k};
+  for (cudaEvent_t* ev : evs) {
+    if (s->event_pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      s->event_pool.push_back(e);
+    }
+    *ev = s->event_pool.back();
+    s->event_pool.pop_back();
+  }
+}
+
+void release_events(polymul_server* s, ServeReq* r) {
+  cudaEvent_t* evs[3] = {&r->ev, &r->ev_in, &r->ev_k};
+  for (cudaEvent_t* ev : evs) {
+    if (*ev) s->event_pool.push_back(*ev);
+    *ev = nullptr;
+  }
 }
 
 // The server thread.  Each pass: take the new submissions (under the lock),
@@ -254,8 +301,7 @@ void server_loop(polymul_server* s) {
         r->slot = -1;
         arena_free(s, r->off, r->bytes);
         s->lane_bytes[r->lane] -= r->bytes;
-        s->event_pool.push_back(r->ev);
-        r->ev = nullptr;
+        release_events(s, r);
         f.pop_front();
         --s->inflight;
         done.push_back(r);
@@ -274,16 +320,11 @@ void server_loop(polymul_server* s) {
         if (s->lane_bytes[l] < s->lane_bytes[lane]) lane = l;
       r->lane = lane;
       s->lane_bytes[lane] += r->bytes;
-      if (s->event_pool.empty()) {
-        cudaEvent_t ev;
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        s->event_pool.push_back(ev);
-      }
-      r->ev = s->event_pool.back();
-      s->event_pool.pop_back();
+      take_events(s, r);
       r->slot = s->free_slots.back();  // fewer than max_inflight requests are in flight
       s->free_slots.pop_back();
       s->h_err[r->slot] = 0;
+      std::atomic_thread_fence(std::memory_order_release);  // cleared before the launch that may report into it
       r->t_admit = now_s();
       const cudaError_t e = issue(s, r);
       issue_time += now_s() - r->t_admit;
@@ -297,8 +338,7 @@ void server_loop(polymul_server* s) {
         r->slot = -1;
         arena_free(s, r->off, r->bytes);
         s->lane_bytes[r->lane] -= r->bytes;
-        s->event_pool.push_back(r->ev);
-        r->ev = nullptr;
+        release_events(s, r);
         done.push_back(r);
       } else {
         s->lane_fifo[lane].push_back(r);
@@ -387,12 +427,14 @@ extern "C" void polymul_server_destroy(polymul_server* s) {
   s->stop.store(true);
   s->cv.notify_all();
   if (s->loop.joinable()) s->loop.join();
-  for (cudaStream_t st : s->lanes) {
-    cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
-  }
+  for (auto* v : {&s->lanes_in, &s->lanes, &s->lanes_out})
+    for (cudaStream_t st : *v) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
   for (auto& kv : s->reqs) {
-    if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    for (cudaEvent_t ev : {kv.second->ev, kv.second->ev_in, kv.second->ev_k})
+      if (ev) cudaEventDestroy(ev);
     delete kv.second;
   }
   for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
@@ -451,10 +493,19 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
       cudaMalloc(&s->d_ctr, 2 * lanes * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&s->d_err, lanes * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&s->d_arena, device_bytes) != cudaSuccess ||
-      cudaHostAlloc(&s->h_err, s->max_inflight * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&s->h_err, s->max_inflight * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostAlloc(&s->h_map, s->max_inflight * pool_size * sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess)
     return bail(fail(POLYMUL_ENOMEM, "device allocation failed"));
   for (int i = (int)s->max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
+  {
+    int native_atomics = 0, can_map = 0;
+    cudaDeviceGetAttribute(&native_atomics, cudaDevAttrHostNativeAtomicSupported, s->device);
+    cudaDeviceGetAttribute(&can_map, cudaDevAttrCanMapHostMemory, s->device);
+    void* dp = nullptr;
+    if (native_atomics && can_map && cudaHostGetDevicePointer(&dp, s->h_err, 0) == cudaSuccess)
+      s->d_err_mapped = static_cast<int*>(dp);
+    cudaGetLastError();  // a refused mapping only selects the copied error words
+  }
   if (cudaMemcpy(s->d_twf, twf.data(), twf.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_twi, twi.data(), twi.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->d_pc, pcs.data(), pcs.size() * sizeof(PrimeConst<uint64_t>), cudaMemcpyHostToDevice) !=
@@ -467,7 +518,7 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
   // kernels per degree (64-bit words, Harvey bounds: every pool prime < 2^62)
   for (int logn = 4; logn <= (int)s->lognmax; ++logn) {
     KernelInfo ki;
-    const bool ok = logn >= 14 ? lookup_ntt_cluster(8, logn, 1, &ki) : lookup_ntt_u64_m1(logn, &ki);
+    const bool ok = logn >= 14 ? lookup_ntt_cluster2(8, logn, 1, false, &ki) : lookup_ntt_u64_m1(logn, &ki);
     if (!ok) return bail(fail(POLYMUL_ENOTSUP, "no kernel for n=2^%d", logn));
     if (ki.smem > 48 * 1024 &&
         cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess)
@@ -500,12 +551,13 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
     s->ki[logn] = ki;
     s->grid_cap[logn] = cap;
   }
-  for (uint32_t l = 0; l < lanes; ++l) {
-    cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
-      return bail(cuda_fail(cudaGetLastError(), "stream creation"));
-    s->lanes.push_back(st);
-  }
+  for (auto* v : {&s->lanes_in, &s->lanes, &s->lanes_out})
+    for (uint32_t l = 0; l < lanes; ++l) {
+      cudaStream_t st;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "stream creation"));
+      v->push_back(st);
+    }
   s->loop = std::thread(server_loop, s);
   *out = s;
   return rc;

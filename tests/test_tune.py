@@ -1,6 +1,7 @@
 """Autotuner: every candidate kernel of a plan (NTT with 16, 32 or 8
-coefficients per thread per operand; the tensor path where it applies) is
-bit-exact; tuning picks one of them and records it; the on-disk cache is
+coefficients per thread per operand, swizzled or padded exchanges, one or
+both operands in registers, one CTA or a cluster per product; the tensor
+path where it applies) is bit-exact; tuning picks one of them and records it; the on-disk cache is
 written and reused by a fresh process."""
 import json
 import os
@@ -47,7 +48,7 @@ def test_every_candidate_is_exact(pm, n, bits, elem):
         for i in range(ncand):
             info = plan.select(i)
             labels.append((info["path"], info["radix_bits"], info["ntt_mode"], info["regs"], info["tensor_groups"],
-                           info["rns_moduli"]))
+                           info["rns_moduli"], info["exchange_pad"], info["one_operand"], info["block"]))
             assert_equal_residues(run_plan_batch(plan, a, b), want, "candidate %d %s" % (i, labels[-1]))
     assert len(set(labels)) == ncand
 
