@@ -559,15 +559,14 @@ def _host_link(dev, h2d_bytes, d2h_bytes, reps=10):
             "note": "plain page-locked copies of the step's sizes, measured in this run"}
 
 
-def _tiled_shifts(n, digits):
-    """Shifted copies of b per A slice in the tiled tensor kernel (mirrors its
-    tiling: up to 4 for one or two digits, 2 for three or four, within the
-    256 tensor-memory columns of a CTA)."""
-    cap = 4 if digits <= 2 else 2 if digits <= 4 else 1
-    s = 1
-    while s * 2 <= max(1, n // 1024) and s * 2 <= cap and digits * ((8 * digits * s * 2 + 15) // 16 * 16) <= 256:
-        s *= 2
-    return s
+def _tiled_shifts(n, info, same_digits=True):
+    """Shifted copies of b per A slice of a tiled tensor kernel, from the
+    plan's output groups: with as many digits on both sides each unit of
+    work is one A slice against S shifted copies of b, so the n/1024 output
+    blocks of a product split into n/1024/S groups."""
+    if not info["tensor_groups"] or not same_digits:
+        return 1
+    return max(1, max(1, n // 1024) // info["tensor_groups"])
 
 
 def _rns_shifts(n, r):
@@ -625,7 +624,8 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
 
     def homogeneous(name, w, sets_needed, reps, cyclic=False, path=None, extra_flags=0):
         # tuned plans: back-to-back batches on rotating buffers may overlap
-        flags = ((polymul.FLAG_TUNE | polymul.FLAG_OVERLAP) if path is None else 0) | \
+        # tensor plans are tuned over their own kernels (digit forms, RNS)
+        flags = ((polymul.FLAG_TUNE | polymul.FLAG_OVERLAP) if path is None else polymul.FLAG_TUNE) | \
             (polymul.FLAG_CYCLIC if cyclic else 0) | extra_flags
         plan = polymul.Plan(w.n, w.q_list, path=polymul.PATH_AUTO if path is None else path, flags=flags,
                             tune_batch=w.batch)
@@ -680,7 +680,7 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
             out[name]["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
             out[name]["tensor_frac_smem"] = _tensor_smem_roofline(
                 w.n, info["digits"], units, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0), la=la,
-                shifts=_tiled_shifts(w.n, info["digits"]) if (info["tensor_groups"] and la == lb) else 1)["frac"]
+                shifts=_tiled_shifts(w.n, info, la == lb))["frac"]
         else:
             peak_g = _alu_peak_g(elem, sms, peaks.get("sm_max_mhz", 2070.0))
             out[name]["alu_frac"] = mm / (ms / 1e3) / 1e9 / peak_g
@@ -840,7 +840,7 @@ def crossover(dev, stream, peaks, alu_peak_g, samples):
                     flops = 2.0 * n * n * info["digits"] ** 2 * batch
                     row["tensor_frac_smem"] = _tensor_smem_roofline(
                         n, info["digits"], batch, ms / 1e3, sms, peaks.get("sm_max_mhz", 2070.0),
-                        shifts=_tiled_shifts(n, info["digits"]) if info["tensor_groups"] else 1)["frac"]
+                        shifts=_tiled_shifts(n, info))["frac"]
                 row["tensor_frac_bf16"] = flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7)
             else:
                 row["ntt_alu_frac"] = batch * _ntt_mulmods(n) / (ms / 1e3) / 1e9 / alu_peak_g

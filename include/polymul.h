@@ -148,6 +148,9 @@ typedef struct polymul_plan_info {
     uint32_t one_operand; /* NTT path: 1 when the main kernel holds one
                              operand in registers at a time (a's transform
                              parked in shared memory during b's)            */
+    uint32_t tensor_kernel;/* tensor path: the main kernel, coded as
+                             polymul_tensor_shape_info.kernel (1 whole
+                             product, 2 tiled, 3 RNS, 4 tiled drained)      */
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
@@ -307,7 +310,9 @@ int polymul_tune(polymul_plan *plan, uint64_t batch, void *stream);
  */
 typedef struct polymul_tensor_shape_info {
     uint32_t kernel;      /* 1 whole-product digit kernel, 2 tiled digit
-                             kernel, 3 residue number system of small moduli */
+                             kernel, 3 residue number system of small moduli,
+                             4 tiled digit kernel that drains each K chunk
+                             (8-bit digits at every degree) */
     uint32_t candidates;  /* tensor kernels the plan holds (the autotuner
                              chooses among them)                            */
     uint32_t digit_bits;  /* digit kernels: digit width w (0 for the RNS one) */

@@ -131,6 +131,29 @@ bool tensor_shape(uint32_t n, uint64_t qmax, int* wb, int* L) {
 // takes that side), else L
 int tensor_la(const polymul_plan* p) { return p->ternary_b ? 1 : p->digits; }
 
+// Balanced 8-bit digits covering the centred residues of moduli up to qmax:
+// the drained tiled kernel's shape at any degree (its fp32 sums run over
+// chunks of at most 1024 K, 1024 2^14 = 2^24)
+int drain_digits(uint64_t qmax) {
+  for (int l = 1; l <= 4; ++l)
+    if ((uint64_t)127 * ((1ull << (8 * l)) - 1) / 255 >= qmax / 2) return l;
+  return 0;
+}
+
+// digit width and the two operands' digit counts of the tensor digit kernel
+// k in plan p (a drained kernel fixes its own)
+struct DigitShape {
+  int wb, la, lb;
+};
+DigitShape digit_shape(const polymul_plan* p, const KernelInfo& k) {
+  if (k.wb) return DigitShape{k.wb, p->ternary_b ? 1 : k.digits, k.digits};
+  return DigitShape{p->digit_bits, tensor_la(p), p->digits};
+}
+
+bool tiled_config_of(const KernelInfo& k, int logn, int la, int lb, TiledCfg* cfg) {
+  return k.drain ? toeplitz_tiled_config_drain(logn, la, lb, cfg) : toeplitz_tiled_config(logn, la, lb, cfg);
+}
+
 // The tensor path's kernels for degree n and moduli up to qmax, the default
 // first: the digit kernels for moduli below 2^31 (the whole-product kernel
 // at n = 1024, 2048 and the tiled one, the tiled first where it serves two
@@ -163,6 +186,19 @@ bool choose_tensor(uint32_t n, uint64_t qmax, uint32_t elem, bool ternary_b, Ten
   } else if (tiled) {
     tc->kernels.push_back(ktiled);
   }
+  // where exact fp32 sums over the whole of K force digits narrower than 8
+  // bits (n >= 2048), the drained tiled kernel keeps 8-bit digits; first
+  // where that saves digits (measured with 30-bit primes: 4 x 4 digits
+  // 1318 us vs 5 x 5 2079 us at n = 4096, 335 vs 539 us at n = 2048; ternary
+  // b, 1 x 4 vs 1 x 5: 439 vs 445 us at n = 4096, 109 vs 129 us at 2048)
+  KernelInfo kdrain;
+  const int l8 = elem == 4 && qmax < (1ull << 31) ? drain_digits(qmax) : 0;
+  if (l8 && tc->wb > 0 && tc->wb < 8 && lookup_toeplitz_tiled_drain(logn, ternary_b ? 1 : l8, l8, &kdrain)) {
+    if (l8 < tc->L || tc->kernels.empty())
+      tc->kernels.insert(tc->kernels.begin(), kdrain);
+    else
+      tc->kernels.push_back(kdrain);
+  }
   std::vector<uint32_t> mods;
   if (rns_choose_base(n, qmax, &mods) && lookup_toeplitz_rns(logn, (uint32_t)mods.size(), elem, &krns)) {
     tc->kernels.push_back(krns);
@@ -187,18 +223,23 @@ int upload_rns_tables(polymul_plan* p, const std::vector<uint32_t>& moduli) {
 
 int upload_tensor_tables(polymul_plan* p) {
   if (p->elem != 4 || p->d_tpc) return POLYMUL_OK;  // digit kernels only (32-bit words); once
-  std::vector<TensorPrime> tp(p->k);
-  for (uint32_t j = 0; j < p->k; ++j) {
-    memset(&tp[j], 0, sizeof tp[j]);
-    const uint64_t q = p->q[j];
-    tp[j].q = (uint32_t)q;
-    for (int e = 0; e < 15; ++e) tp[j].pw[e] = (uint32_t)pm::host::powmod(2, (uint64_t)p->digit_bits * e, q);
-    tp[j].mu = (uint64_t)(((pm::host::u128)1 << 64) / q);
-    tp[j].bias = ((1ull << 60) + q - 1) / q * q;
-  }
-  PM_CUDA(cudaMalloc(&p->d_tpc, tp.size() * sizeof(TensorPrime)));
-  PM_CUDA(cudaMemcpy(p->d_tpc, tp.data(), tp.size() * sizeof(TensorPrime), cudaMemcpyHostToDevice));
-  return POLYMUL_OK;
+  auto upload = [&](int wb, void** dst) -> int {
+    std::vector<TensorPrime> tp(p->k);
+    for (uint32_t j = 0; j < p->k; ++j) {
+      memset(&tp[j], 0, sizeof tp[j]);
+      const uint64_t q = p->q[j];
+      tp[j].q = (uint32_t)q;
+      for (int e = 0; e < 15; ++e) tp[j].pw[e] = (uint32_t)pm::host::powmod(2, (uint64_t)wb * e, q);
+      tp[j].mu = (uint64_t)(((pm::host::u128)1 << 64) / q);
+      tp[j].bias = ((1ull << 60) + q - 1) / q * q;
+    }
+    PM_CUDA(cudaMalloc(dst, tp.size() * sizeof(TensorPrime)));
+    PM_CUDA(cudaMemcpy(*dst, tp.data(), tp.size() * sizeof(TensorPrime), cudaMemcpyHostToDevice));
+    return POLYMUL_OK;
+  };
+  int r = upload(p->digit_bits, &p->d_tpc);
+  if (r == POLYMUL_OK && p->digit_bits > 0 && p->digit_bits < 8) r = upload(8, &p->d_tpc8);
+  return r;
 }
 
 bool lookup_ntt(uint32_t elem, int logn, int mode, KernelInfo* ki) {
@@ -434,6 +475,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_twi);
   cudaFree(p->d_pc);
   cudaFree(p->d_tpc);
+  cudaFree(p->d_tpc8);
   cudaFree(p->d_rns_base);
   cudaFree(p->d_rns_primes);
   for (int s = 0; s < kCounterSlots; ++s) cudaFree(p->d_rns_scr[s]);
@@ -464,8 +506,9 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->grid = (uint32_t)p->grid_cap;
   info->smem_bytes = (uint32_t)p->ki.smem;
   info->ctas_per_sm = (uint32_t)(p->num_sms ? p->grid_cap / p->num_sms : 0);
-  info->digit_bits = p->path == POLYMUL_PATH_TENSOR ? (uint32_t)p->digit_bits : 0;
-  info->digits = p->path == POLYMUL_PATH_TENSOR ? (uint32_t)p->digits : 0;
+  const DigitShape ds = digit_shape(p, p->ki);
+  info->digit_bits = p->path == POLYMUL_PATH_TENSOR ? (uint32_t)ds.wb : 0;
+  info->digits = p->path == POLYMUL_PATH_TENSOR ? (uint32_t)ds.lb : 0;
   info->radix_bits = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.rb : 0;
   info->candidates = (uint32_t)p->cands.size();
   info->tuned = p->tuned ? 1u : 0u;
@@ -479,13 +522,14 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->rns_moduli = p->path == POLYMUL_PATH_TENSOR && p->ki.rns ? p->rns_r : 0;
   info->exchange_pad = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.pad : 0u;
   info->one_operand = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.seq : 0u;
+  info->tensor_kernel = p->path != POLYMUL_PATH_TENSOR ? 0u : p->ki.rns ? 3u : p->ki.drain ? 4u : p->ki.tiled ? 2u : 1u;
   if (p->path == POLYMUL_PATH_TENSOR && p->ki.rns) {
     RnsCfg rc;
     if (rns_config((int)p->logn, p->rns_r, &rc)) info->tensor_groups = rc.ngrp;
   }
   if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
     TiledCfg tc;
-    if (toeplitz_tiled_config((int)p->logn, tensor_la(p), p->digits, &tc)) info->tensor_groups = tc.ngrp;
+    if (tiled_config_of(p->ki, (int)p->logn, ds.la, ds.lb, &tc)) info->tensor_groups = tc.ngrp;
   }
   return POLYMUL_OK;
 }
@@ -516,13 +560,14 @@ extern "C" int polymul_tensor_shape(uint32_t n, uint64_t qmax, uint32_t flags, p
     info->slices = 1;
     info->groups = rc.ngrp;
   } else {
-    info->digit_bits = (uint32_t)tch.wb;
-    info->digits_a = ternary ? 1u : (uint32_t)tch.L;
-    info->digits_b = (uint32_t)tch.L;
+    const int wb = k.wb ? k.wb : tch.wb, L = k.digits ? k.digits : tch.L;
+    info->digit_bits = (uint32_t)wb;
+    info->digits_a = ternary ? 1u : (uint32_t)L;
+    info->digits_b = (uint32_t)L;
     if (k.tiled) {
       TiledCfg tc;
-      toeplitz_tiled_config(logn, (int)info->digits_a, tch.L, &tc);
-      info->kernel = 2;
+      tiled_config_of(k, logn, (int)info->digits_a, L, &tc);
+      info->kernel = k.drain ? 4 : 2;
       info->shifts = tc.shifts;
       info->slices = tc.bpg;
       info->groups = tc.ngrp;
@@ -649,13 +694,15 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     PM_CUDA(cudaLaunchKernel(p->ki.fn, tgrid, p->ki.block, argv, p->ki.smem, st));
   } else if (p->path == POLYMUL_PATH_TENSOR && p->ki.tiled) {
     TiledCfg tc;
-    if (!toeplitz_tiled_config((int)p->logn, tensor_la(p), p->digits, &tc)) return fail(POLYMUL_ENOTSUP, "tensor tiling");
+    const DigitShape ds = digit_shape(p, p->ki);
+    if (!tiled_config_of(p->ki, (int)p->logn, ds.la, ds.lb, &tc)) return fail(POLYMUL_ENOTSUP, "tensor tiling");
     const uint64_t tunits = units * tc.ngrp;
     // ternary b: c = b * T(a) (the ring is commutative), b's single digit on the A side
     const void* xa = p->ternary_b ? b : a;
     const void* xb = p->ternary_b ? a : b;
-    TensorTiledArgs args{(const uint32_t*)xa, (const uint32_t*)xb, (uint32_t*)c, (const TensorPrime*)p->d_tpc,
-                         tunits, p->k, p->cyclic ? 0u : 0x80008000u, p->logn, (uint32_t)p->digit_bits,
+    const void* tpc = p->ki.drain && p->d_tpc8 ? p->d_tpc8 : p->d_tpc;
+    TensorTiledArgs args{(const uint32_t*)xa, (const uint32_t*)xb, (uint32_t*)c, (const TensorPrime*)tpc,
+                         tunits, p->k, p->cyclic ? 0u : 0x80008000u, p->logn, (uint32_t)ds.wb,
                          tc.bpg, tc.ngrp, tc.kc, tc.a_win, tc.bt_off, tc.tmem_cols, ctr, p->d_err};
     void* argv[] = {&args};
     const int tgrid = (int)std::min<uint64_t>(tunits, (uint64_t)p->grid_cap);

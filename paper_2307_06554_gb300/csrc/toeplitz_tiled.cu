@@ -96,7 +96,40 @@ struct TTShape {
   static constexpr int BT_PITCH = NG * 128 + 16;
 };
 
+// Adds shift sh's accumulators of this thread's tensor-memory lane (one row
+// of the output block, 8 outputs) to acc: sum over digit pairs (s, g) of the
+// exact fp32 partial sum times 2^(w (s + g)) mod q.
 template <int LA, int LB, int S>
+__device__ __forceinline__ void drain_shift(uint32_t lane_base, int sh, const uint32_t* pw, int64_t (&acc)[8]) {
+  using TS = TTShape<LB, S>;
+#pragma unroll
+  for (int s = 0; s < LA; ++s) {
+#pragma unroll
+    for (int c16 = 0; c16 < TS::NB / 16; ++c16) {
+      if (16 * c16 + 16 <= 8 * sh * LB || 16 * c16 >= 8 * (sh + 1) * LB) continue;
+      uint32_t r[16];
+      // warp-collective: every lane loads
+      tmem_ld16(lane_base + s * TS::NB + 16 * c16, r);
+      tmem_wait_ld();
+#pragma unroll
+      for (int cc = 0; cc < 16; ++cc) {
+        const int col = 16 * c16 + cc, g = col / 8, v = col % 8;
+        if (g >= sh * LB && g < (sh + 1) * LB)
+          acc[v] += (int64_t)__float2int_rn(__uint_as_float(r[cc])) * (int64_t)pw[s + g - sh * LB];
+      }
+    }
+  }
+}
+
+// DRAIN: each K chunk's accumulators are drained into 64-bit integer sums in
+// registers after the chunk (and restart at zero), so only a chunk's partial
+// sums must stay exact in fp32: kc * 2^(2w-2) <= 2^24, which 8-bit digits
+// meet at kc = 1024 whatever n.  The running sums are reduced mod q after
+// every chunk: a chunk adds at most LA LB 2^24 q < 2^59 in magnitude (at
+// most 4 x 4 digit pairs), below the 2^60 bias.  BD: the A slices per unit
+// of work of a drained kernel (its registers hold BD x S rows of sums; the
+// host passes bpg == BD), 1 otherwise.
+template <int LA, int LB, int S, bool DRAIN, int BD>
 __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiledArgs args) {
   using TS = TTShape<LB, S>;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -141,6 +174,9 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
   unsigned long long cur = s_next;
   uint32_t parity = 0;
   bool failed = false;
+  // DRAIN: this thread's row, per A slice and shift and output, recombined
+  // over the chunks drained so far
+  int64_t dacc[BD * S][8];
   while (cur < units) {
     __syncthreads();  // every thread has read s_next
     if (tid == 0) s_next = atomicAdd(args.ctr, 1ull);
@@ -151,6 +187,12 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
     const uint32_t* a = args.a + row * n;
     const uint32_t* b = args.b + row * n;
     const uint32_t b0 = grp * bpg * S;  // the unit's first 1024-output block
+    if constexpr (DRAIN) {
+#pragma unroll
+      for (int g = 0; g < BD * S; ++g)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) dacc[g][v] = 0;
+    }
 
     for (uint32_t ch = 0; ch < nch; ++ch) {
       // ---- ConvertPoly (a): digits of a~_{base + e}, e < awin ----
@@ -220,7 +262,8 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
             const uint64_t ad0 = smem_desc(xa0 + (uint32_t)(s * awin + 1024 * bl) * 2, 16, 128);
 #pragma unroll 4
             for (uint32_t kk = 0; kk < kc / 16; ++kk)
-              tc_mma_f16(dcol, ad0 + 2u * (uint64_t)kk, bd0 + BSTEP * (uint64_t)kk, IDESC, (ch > 0 || kk > 0) ? 1u : 0u);
+              tc_mma_f16(dcol, ad0 + 2u * (uint64_t)kk, bd0 + BSTEP * (uint64_t)kk, IDESC,
+                         ((!DRAIN && ch > 0) || kk > 0) ? 1u : 0u);
           }
         }
         tc_commit(&mbar);
@@ -234,14 +277,46 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
       }
       parity ^= 1u;
       tc_fence_after();
+      if constexpr (DRAIN) {
+        // the chunk's exact fp32 sums into the rows' integer recombination;
+        // the next chunk's first MMA overwrites the accumulators only after
+        // the barrier that precedes its issue
+#pragma unroll
+        for (int bl = 0; bl < BD; ++bl) {
+#pragma unroll
+          for (int sh = 0; sh < S; ++sh) {
+            int64_t (&acc)[8] = dacc[bl * S + sh];
+            drain_shift<LA, LB, S>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(bl * LA * TS::NB), sh,
+                                   args.tp[j].pw, acc);
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+              acc[v] = barrett64((uint64_t)(acc[v] + (int64_t)args.tp[j].bias), q, args.tp[j].mu);
+          }
+        }
+      }
     }
     if (failed) break;
 
     // ---- ConvertMatrix: recombine digit pairs, reduce mod q, store ----
     uint32_t* c = args.c + row * n;
     const uint64_t mu = args.tp[j].mu, bias = args.tp[j].bias;
+    if constexpr (DRAIN) {
+#pragma unroll
+      for (int g = 0; g < BD * S; ++g) {
+        // accumulator group g = (slice bl, shift sh) holds block b0 + bl + sh
+        // (one of the two is 0)
+        const uint32_t j0 = 8 * (128 * (b0 + (uint32_t)(g / S) + (uint32_t)(g % S)) + (uint32_t)tid);
+        if (j0 < n) {
+          uint32_t out[8];
+#pragma unroll
+          for (int v = 0; v < 8; ++v) out[v] = (uint32_t)dacc[g][v];  // reduced after the last chunk
+          *reinterpret_cast<uint4*>(c + j0) = make_uint4(out[0], out[1], out[2], out[3]);
+          *reinterpret_cast<uint4*>(c + j0 + 4) = make_uint4(out[4], out[5], out[6], out[7]);
+        }
+      }
+    }
 #pragma unroll 1
-    for (uint32_t bl = 0; bl < bpg; ++bl) {
+    for (uint32_t bl = 0; bl < (DRAIN ? 0u : bpg); ++bl) {
 #pragma unroll
       for (int sh = 0; sh < S; ++sh) {
         int64_t acc[8];
@@ -344,9 +419,10 @@ bool toeplitz_tiled_config(int logn, int la, int lb, TiledCfg* cfg) {
   }
 }
 
-template <int LA, int LB, int S>
+template <int LA, int LB, int S, bool DRAIN = false, int BD = 1>
 static void tiled_info(const TiledCfg& cfg, KernelInfo* ki) {
-  ki->fn = (const void*)k_toeplitz_tiled<LA, LB, S>;
+  ki->fn = (const void*)k_toeplitz_tiled<LA, LB, S, DRAIN, BD>;
+  ki->drain = DRAIN ? 1 : 0;
   ki->block = kTiledThreads;
   ki->smem = cfg.smem;
   ki->team = kTiledThreads;
@@ -371,6 +447,74 @@ bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki) {
   PM_TT(5, 5, 1)
   PM_TT(1, 2, 1) PM_TT(1, 3, 1) PM_TT(1, 4, 1) PM_TT(1, 5, 1)  // a single-digit operand on the A side (ternary b)
 #undef PM_TT
+  return false;
+}
+
+}  // namespace pm
+
+namespace pm {
+
+// Drained tiling: 8-bit digits (exact per chunk of at most 1024 K); with as
+// many digits on both sides one A slice per unit of work against as many
+// shifted copies of b as tensor memory holds, with a single-digit A side up
+// to 4 A slices against one B (the undrained kernel's choice there too).
+
+bool toeplitz_tiled_config_drain(int logn, int la, int lb, TiledCfg* cfg) {
+  if (logn < 6 || logn > 14 || la < 1 || lb < 1 || la > 4 || lb > 4) return false;
+  const uint32_t n = 1u << logn;
+  auto nb_of = [&](uint32_t S) { return (8 * (uint32_t)lb * S + 15) / 16 * 16; };
+  if ((uint32_t)la * nb_of(1) > (uint32_t)kTiledTmemCap) return false;
+  const uint32_t rblk = n >= 1024 ? n / 1024 : 1;
+  uint32_t S = 1, bpg = 1;
+  if (la == lb) {
+    while (S * 2 <= rblk && S * 2 <= max_shifts(la, lb) && (uint32_t)la * nb_of(S * 2) <= (uint32_t)kTiledTmemCap)
+      S *= 2;
+  } else {
+    while (bpg * 2 <= rblk && bpg * 2 <= 4 && bpg * 2 * (uint32_t)la * nb_of(1) <= (uint32_t)kTiledTmemCap) bpg *= 2;
+  }
+  const uint32_t nb = nb_of(S), pitch = nb / 8 * 128 + 16;
+  for (uint32_t kc = n < 1024 ? n : 1024; kc >= 64; kc /= 2) {
+    const uint32_t a_win = 1024 * bpg + kc;
+    const uint32_t bt_off = ((uint32_t)la * a_win * 2 + 127) / 128 * 128;
+    const uint32_t smem = bt_off + kc / 8 * pitch;
+    if (smem > (uint32_t)kTiledSmemCap) continue;
+    cfg->bpg = bpg;
+    cfg->shifts = S;
+    cfg->nb = nb;
+    cfg->b_pitch = pitch;
+    cfg->ngrp = rblk / (bpg * S);
+    cfg->kc = kc;
+    cfg->a_win = a_win;
+    cfg->bt_off = bt_off;
+    cfg->smem = (int)smem;
+    uint32_t cols = 32;
+    while (cols < bpg * (uint32_t)la * nb) cols *= 2;
+    cfg->tmem_cols = cols;
+    return true;
+  }
+  return false;
+}
+
+bool lookup_toeplitz_tiled_drain(int logn, int la, int lb, KernelInfo* ki) {
+  TiledCfg cfg;
+  if (!toeplitz_tiled_config_drain(logn, la, lb, &cfg)) return false;
+  const int S = (int)cfg.shifts, bd = (int)cfg.bpg;
+#define PM_TD(A, B, SH, BPG)                       \
+  if (la == A && lb == B && S == SH && bd == BPG) { \
+    tiled_info<A, B, SH, true, BPG>(cfg, ki);      \
+    ki->wb = 8;                                    \
+    ki->digits = B;                                \
+    return true;                                   \
+  }
+  PM_TD(1, 1, 1, 1) PM_TD(1, 1, 2, 1) PM_TD(1, 1, 4, 1)
+  PM_TD(2, 2, 1, 1) PM_TD(2, 2, 2, 1) PM_TD(2, 2, 4, 1)
+  PM_TD(3, 3, 1, 1) PM_TD(3, 3, 2, 1)
+  PM_TD(4, 4, 1, 1) PM_TD(4, 4, 2, 1)
+  // a single-digit operand on the A side (ternary b)
+  PM_TD(1, 2, 1, 1) PM_TD(1, 2, 1, 2) PM_TD(1, 2, 1, 4)
+  PM_TD(1, 3, 1, 1) PM_TD(1, 3, 1, 2) PM_TD(1, 3, 1, 4)
+  PM_TD(1, 4, 1, 1) PM_TD(1, 4, 1, 2) PM_TD(1, 4, 1, 4)
+#undef PM_TD
   return false;
 }
 

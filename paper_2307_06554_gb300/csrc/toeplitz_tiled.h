@@ -45,4 +45,12 @@ bool toeplitz_tiled_config(int logn, int la, int lb, TiledCfg* cfg);
 // chose; ki->smem and ki->tmem_cols from the tiling of degree 2^logn.
 bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki);
 
+// The drained variant: each K chunk's fp32 accumulators are drained into
+// 64-bit integer sums, so 8-bit digits are exact at every degree (chunks of
+// at most 1024); at most 4 digits (every q < 2^31), one A slice per unit of
+// work, shifted copies of b as tensor memory allows.  ki->wb = 8,
+// ki->digits = lb.
+bool toeplitz_tiled_config_drain(int logn, int la, int lb, TiledCfg* cfg);
+bool lookup_toeplitz_tiled_drain(int logn, int la, int lb, KernelInfo* ki);
+
 }  // namespace pm

@@ -33,6 +33,23 @@ def _digits(n, q):
     return w, next(L for L in range(1, 9) if _reach(w, L) >= q // 2)
 
 
+def _drain_digits(q):
+    """8-bit digits of the drained kernel (exact per K chunk of 1024 at any
+    degree), at most four; None past that."""
+    return next((L for L in range(1, 5) if _reach(8, L) >= q // 2), None)
+
+
+def _default_digits(n, q):
+    """The default digit kernel's (width, digits): the drained one where
+    the undrained width is below 8 and it needs fewer digits, or where the
+    undrained one has none (more than five digits)."""
+    w, L = _digits(n, q)
+    l8 = _drain_digits(q)
+    if w < 8 and l8 is not None and (l8 < L or L > 5):
+        return 8, l8
+    return w, L
+
+
 def test_reach_is_the_balanced_digit_range():
     """Brute force on small widths: the largest value L balanced w-bit digits
     represent is the closed form used above."""
@@ -49,15 +66,20 @@ def test_reach_is_the_balanced_digit_range():
                                         (2048, 16253, 2), (4096, 16383, 3), (1024, 12289, 2), (256, 3329, 2),
                                         (4096, 1073479681, 5)])
 def test_digit_boundaries(pm, n, q, digits):
+    assert digits == _digits(n, q)[1]
     info = pm.polymul_tensor_shape(n, q)
-    assert info["digit_bits"] == _width(n)
-    assert info["digits_a"] == info["digits_b"] == digits == _digits(n, q)[1]
+    assert (info["digit_bits"], info["digits_b"]) == _default_digits(n, q)
+    assert info["digits_a"] == info["digits_b"]
+    assert info["kernel"] == (4 if info["digit_bits"] != _width(n) else 1 if n == 1024 else 2)
 
 
-def test_more_than_five_digits_go_to_the_rns_kernel(pm):
+def test_more_than_five_digits_go_to_the_drained_kernel(pm):
     info = pm.polymul_tensor_shape(8192, 1073479681)  # needs six digits of 6 bits
     assert _digits(8192, 1073479681)[1] == 6
-    assert info["kernel"] == 3 and info["rns_moduli"] == len(pm.polymul_tensor_rns_base(8192, 1073479681))
+    assert (info["kernel"], info["digit_bits"], info["digits_b"], info["candidates"]) == (4, 8, 4, 2)
+    # a 32-bit word modulus above 2^31: the RNS kernel alone
+    info = pm.polymul_tensor_shape(8192, 2147483659)
+    assert info["kernel"] == 3 and info["rns_moduli"] == len(pm.polymul_tensor_rns_base(8192, 2147483659))
 
 
 def test_sweep_fits_the_hardware(pm):
@@ -77,10 +99,13 @@ def test_sweep_fits_the_hardware(pm):
                 seen.add(info["kernel"])
                 assert info["smem_bytes"] <= 227 * 1024 and info["tmem_cols"] <= 512
                 assert info["tmem_cols"] >= 32 and info["tmem_cols"] & (info["tmem_cols"] - 1) == 0
-                if info["kernel"] in (1, 2):
+                if info["kernel"] in (1, 2, 4):
                     w = info["digit_bits"]
-                    assert n * (1 << (2 * w - 2)) <= 1 << 24 and (1 << (w - 1)) <= 128
-                    assert (info["digits_b"], w) == (_digits(n, q)[1], _width(n))
+                    # exact fp32 sums over the whole of K, or over chunks of
+                    # at most 1024 for the drained kernel
+                    assert min(n, 1024 if info["kernel"] == 4 else n) * (1 << (2 * w - 2)) <= 1 << 24
+                    assert (1 << (w - 1)) <= 128
+                    assert (w, info["digits_b"]) == _default_digits(n, q)
                     assert q < 1 << 31
                 else:
                     ms = pm.polymul_tensor_rns_base(n, q)
@@ -89,7 +114,7 @@ def test_sweep_fits_the_hardware(pm):
                     assert info["rns_moduli"] * max(16, 8 * info["shifts"]) <= 512
                 blocks = max(1, n // 1024)
                 assert info["groups"] == 0 or info["groups"] * info["shifts"] * info["slices"] == blocks
-    assert seen == {1, 2, 3}
+    assert seen == {1, 2, 3, 4}
 
 
 def test_kernel_choice(pm):
@@ -97,10 +122,14 @@ def test_kernel_choice(pm):
     i = pm.polymul_tensor_shape(2048, 12289)
     assert (i["kernel"], i["shifts"], i["groups"]) == (2, 2, 1)          # shifted copies of b at 2048
     i = pm.polymul_tensor_shape(4096, (1 << 30) - 35, pm.FLAG_TERNARY_B)
-    assert (i["digits_a"], i["digits_b"], i["shifts"], i["slices"]) == (1, 5, 1, 4)
+    assert (i["kernel"], i["digits_a"], i["digits_b"], i["shifts"], i["slices"]) == (4, 1, 4, 1, 4)
+    i = pm.polymul_tensor_shape(4096, (1 << 30) - 35)
+    assert (i["kernel"], i["digits_a"], i["digits_b"], i["shifts"], i["groups"]) == (4, 4, 4, 2, 2)
+    i = pm.polymul_tensor_shape(16384, (1 << 31) - 1)   # six 6-bit digits undrained: drained only
+    assert (i["kernel"], i["digits_b"], i["candidates"]) == (4, 4, 1)
     i = pm.polymul_tensor_shape(4096, (1 << 59) - 55)
     assert (i["kernel"], i["rns_moduli"], i["shifts"], i["groups"]) == (3, 21, 2, 2)
-    for n, q in ((8192, (1 << 59) - 55), (32768, 12289), (16, 12289)):
+    for n, q in ((8192, (1 << 59) - 55), (32768, 12289), (16, 12289), (32768, (1 << 30) - 35)):
         with pytest.raises(pm.PolymulError) as ei:
             pm.polymul_tensor_shape(n, q)
         assert ei.value.code == pm.POLYMUL_ENOTSUP, (n, q)
@@ -123,6 +152,8 @@ def test_bench_mirrors_agree(pm):
             if info["kernel"] == 3:
                 assert bench._rns_shifts(n, info["rns_moduli"]) == info["shifts"], (n, q)
             else:
-                assert bench._tensor_digits(n, q) == (info["digit_bits"], info["digits_b"]), (n, q)
-                if info["kernel"] == 2:
-                    assert bench._tiled_shifts(n, info["digits_b"]) == info["shifts"], (n, q)
+                if info["kernel"] in (1, 2):
+                    assert bench._tensor_digits(n, q) == (info["digit_bits"], info["digits_b"]), (n, q)
+                if info["kernel"] in (2, 4):
+                    got = bench._tiled_shifts(n, {"tensor_groups": info["groups"]})
+                    assert got == info["shifts"], (n, q)

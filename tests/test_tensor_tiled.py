@@ -6,7 +6,9 @@ exactness bound, batches that are not a multiple of the grid, the small-ring
 and RNS workloads on the tensor path, the tiled kernel beside the
 whole-product one at n = 1024 and 2048 (first at 2048, where it serves two
 blocks from one A slice), ternary b, and moduli at the digit-count
-boundaries."""
+boundaries.  The drained form (8-bit digits at every degree, exact per K
+chunk of at most 1024) likewise, with its own exactness boundary, and where
+the undrained form has no digit count (a 31-bit modulus at 2^14)."""
 import numpy as np
 import pytest
 
@@ -37,6 +39,18 @@ def _digit_width(n):
     return min(8, (24 - logn) // 2 + 1)
 
 
+def _select(plan, code):
+    """Select the plan's candidate whose tensor kernel has the given code (1
+    whole product, 2 tiled, 3 RNS, 4 tiled drained); returns its info."""
+    codes = []
+    for i in range(plan.info["candidates"]):
+        info = plan.select(i)
+        codes.append(info["tensor_kernel"])
+        if info["tensor_kernel"] == code:
+            return info
+    raise AssertionError("no candidate with tensor kernel %d (have %s)" % (code, codes))
+
+
 def _check_sampled(got, a, b, q_list, cyclic, rng, count=24):
     n = a.shape[-1]
     for p in range(a.shape[0]):
@@ -56,7 +70,7 @@ def test_tiled_against_oracle(pm, n, bits):
     a = wl.uniform_coeffs(rng, batch, q_list, n, np.uint32)
     b = wl.uniform_coeffs(rng, batch, q_list, n, np.uint32)
     with _tensor_plan(pm, n, q_list) as plan:
-        info = plan.info
+        info = _select(plan, 2)
         assert info["tensor_groups"] >= 1 and info["digit_bits"] == _digit_width(n)
         got = run_plan_batch(plan, a, b)
     assert_equal_residues(got, native.polymul_batch(a, b, q_list), "tiled n=%d bits=%d" % (n, bits))
@@ -97,26 +111,26 @@ def test_tiled_digit_counts(pm, n, q, digits):
     a = wl.uniform_coeffs(rng, 5, [q], n, np.uint32)
     b = wl.uniform_coeffs(rng, 5, [q], n, np.uint32)
     with pm.Plan(n, [q], path=pm.PATH_TENSOR) as plan:
-        info = plan.info
+        # n = 1024, 2048 have a whole-product kernel too, n >= 2048 the
+        # drained one; use the tiled one
+        info = _select(plan, 2)
         assert info["digits"] == digits, info
-        # n = 1024, 2048 have a whole-product kernel too; use the tiled one
-        if info["tensor_groups"] == 0:
-            idx = [i for i in range(info["candidates"]) if plan.select(i)["tensor_groups"] > 0]
-            assert idx, "no tiled candidate"
-            plan.select(idx[0])
         got = run_plan_batch(plan, a, b)
     assert_equal_residues(got, native.polymul_batch(a, b, [q]), "digits=%d n=%d" % (digits, n))
 
 
-@pytest.mark.parametrize("n", [64, 256, 4096, 8192])
-def test_tiled_exactness_boundary(pm, n):
+@pytest.mark.parametrize("n,kernel", [(64, 2), (256, 2), (4096, 2), (8192, 2), (4096, 4), (16384, 4)])
+def test_tiled_exactness_boundary(pm, n, kernel):
     """The low digits of every coefficient at -2^(w-1): each of their
     digit products is 2^(2w-2), so the output coefficient without wrap-around
     sums n of them, n 2^(2w-2) = 2^24 at n = 4096 -- the edge of exact fp32
     integers -- and the other sums mix signs.  Moduli at the top of what
-    five digits cover (31 bits up to 2^12, 30 bits above)."""
-    w = _digit_width(n)
-    q = 2147483629 if n <= 4096 else 1073741789  # primes just below 2^31 and 2^30
+    five digits cover (31 bits up to 2^12; at 2^13 the largest prime whose
+    half five 6-bit digits reach, 1056698273).  The drained
+    kernel (8-bit digits) reaches 1024 x 2^14 = 2^24 within each K chunk;
+    four digits cover 31-bit moduli at every degree."""
+    w = 8 if kernel == 4 else _digit_width(n)
+    q = 2147483629 if n <= 4096 or kernel == 4 else 1056698273
     assert wl.is_prime(q)
     digits = -(1 << (w - 1))
     low = 3 if w == 8 else 4  # as many low digits at their minimum as stay inside (-q/2, q/2]
@@ -128,6 +142,7 @@ def test_tiled_exactness_boundary(pm, n):
     a[1, 0] = q - 1
     b[1, 0, ::3] = q // 2 + 1  # the most negative centred value
     with pm.Plan(n, [q], path=pm.PATH_TENSOR) as plan:
+        assert _select(plan, kernel)["digit_bits"] == w
         got = run_plan_batch(plan, a, b)
     js = sorted(set([0, 1, n // 2, n - 2, n - 1] + list(range(0, n, max(1, n // 64)))))
     for p in range(2):
@@ -172,7 +187,8 @@ def test_rns_4096_on_tensor_path(pm):
     whole products for a few."""
     w = wl.rns_4096()
     with _tensor_plan(pm, w.n, w.q_list) as plan:
-        assert plan.info["digits"] == 5
+        # four 8-bit digits (drained K chunks) rather than five of 7 bits
+        assert (plan.info["tensor_kernel"], plan.info["digits"], plan.info["digit_bits"]) == (4, 4, 8)
         got = run_plan_batch(plan, w.a, w.b)
     for p in (0, 255):
         assert_equal_residues(got[p:p + 1], native.polymul_batch(w.a[p:p + 1], w.b[p:p + 1], w.q_list),
@@ -187,31 +203,33 @@ def test_rns_4096_on_tensor_path(pm):
 
 @pytest.mark.parametrize("n", [1024, 2048])
 def test_tiled_candidate_matches_whole_product_kernel(pm, n):
+    """At n = 1024 the whole-product kernel first, then the tiled and RNS
+    ones; at 2048 the tiled one first (two blocks from one A slice), and the
+    drained one too (7-bit digits there, as many 8-bit ones): every digit
+    kernel gives the same coefficients, and the oracle's."""
     rng = np.random.default_rng(n)
     q_list = [12289, 7681]
     a = wl.uniform_coeffs(rng, 77, q_list, n, np.uint32)
     b = wl.uniform_coeffs(rng, 77, q_list, n, np.uint32)
     with pm.Plan(n, q_list, path=pm.PATH_TENSOR) as plan:
         info = plan.info
-        assert info["candidates"] == 3  # whole product, tiled (first at 2048: shifted copies of b), RNS
-        kinds = [(plan.select(i)["tensor_groups"], plan.info["rns_moduli"]) for i in range(3)]
-        assert kinds[2][1] > 0 and sorted(kinds[:2]) == [(0, 0), (1, 0)]
-        assert kinds[0] == ((1, 0) if n == 2048 else (0, 0))
-        plan.select(kinds.index((0, 0)))
-        whole = run_plan_batch(plan, a, b)
-        plan.select(kinds.index((1, 0)))
-        tiled = run_plan_batch(plan, a, b)
-    assert np.array_equal(whole, tiled)
-    assert_equal_residues(tiled, native.polymul_batch(a, b, q_list), "tiled n=%d" % n)
+        codes = [plan.select(i)["tensor_kernel"] for i in range(info["candidates"])]
+        assert codes == ([2, 1, 4, 3] if n == 2048 else [1, 2, 3]), codes
+        outs = {}
+        for code in codes:
+            if code != 3:
+                _select(plan, code)
+                outs[code] = run_plan_batch(plan, a, b)
+    for code in outs:
+        assert np.array_equal(outs[code], outs[2]), code
+    assert_equal_residues(outs[2], native.polymul_batch(a, b, q_list), "tiled n=%d" % n)
 
 
 def test_tensor_path_limits(pm):
     """Outside the tensor path's shapes creation fails with ENOTSUP when the
-    path is forced: degree above 2^14; a 31-bit modulus at 2^14 (six digits
-    of 6 bits, and no base of small moduli reaches its range); a 59-bit
-    modulus at 2^13 (64-bit words have only the RNS kernel, whose moduli
-    there stay below 92)."""
-    for n, q in ((32768, 12289), (16384, 2147483629), (8192, (1 << 59) - 55)):
+    path is forced: degree above 2^14; a 59-bit modulus at 2^13 (64-bit
+    words have only the RNS kernel, whose moduli there stay below 92)."""
+    for n, q in ((32768, 12289), (8192, (1 << 59) - 55)):
         with pytest.raises(pm.PolymulError) as ei:
             pm.Plan(n, [q], path=pm.PATH_TENSOR)
         assert ei.value.code == pm.POLYMUL_ENOTSUP, (n, q)
@@ -330,9 +348,11 @@ def test_digit_capacity_boundary(pm, n, q, digits):
     """Moduli just below a digit-count boundary: L balanced w-bit digits in
     [-2^(w-1), 2^(w-1)) reach (2^(w-1) - 1)(2^(wL) - 1)/(2^w - 1), a little
     less than (2^(wL) - 1)/2, so floor(q/2) of these moduli needs one digit
-    more than the naive bound says (digits == 0: more than five digits,
-    served by the residue-number-system kernel).  Every coefficient at the
-    positive and negative extremes of the centred range."""
+    more than the naive bound says (digits == 0: more than five digits of
+    the undrained kernels; the drained kernel's four 8-bit digits serve it,
+    and the residue-number-system kernel too).  Every coefficient at the
+    positive and negative extremes of the centred range, on each digit
+    kernel the plan holds."""
     assert wl.is_prime(q)
     rng = np.random.default_rng(q % 997)
     a = wl.uniform_coeffs(rng, 3, [q], n, np.uint32)
@@ -342,13 +362,70 @@ def test_digit_capacity_boundary(pm, n, q, digits):
     a[1] = q // 2 + 1      # -floor(q/2) (q odd)
     b[1, 0, ::2] = q // 2
     with pm.Plan(n, [q], path=pm.PATH_TENSOR) as plan:
-        info = plan.info
+        codes = [plan.select(i)["tensor_kernel"] for i in range(plan.info["candidates"])]
         if digits:
-            assert info["digits"] == digits and info["rns_moduli"] == 0, info
+            assert _select(plan, next(c for c in codes if c in (1, 2)))["digits"] == digits
         else:
-            assert info["rns_moduli"] > 0, info
+            assert codes == [4, 3], codes
+        gots = []
+        for code in codes:
+            if code != 3 or not digits:
+                _select(plan, code)
+                gots.append((code, run_plan_batch(plan, a, b)))
+    for code, got in gots:
+        if n <= 4096:
+            assert_equal_residues(got, native.polymul_batch(a, b, [q]), "boundary n=%d q=%d kernel %d" % (n, q, code))
+        else:
+            _check_sampled(got, a, b, [q], False, rng)
+
+
+# ---- the drained tiled kernel: 8-bit digits at every degree ----
+
+@pytest.mark.parametrize("n,bits,cyclic", [(2048, 22, False), (2048, 31, True), (4096, 30, False), (4096, 31, False),
+                                           (4096, 26, True)])
+def test_drained_against_oracle(pm, n, bits, cyclic):
+    rng = np.random.default_rng(11 * n + bits)
+    q_list = wl.draw_primes(rng, 2, bits, bits, 1)
+    a = wl.uniform_coeffs(rng, 5, q_list, n, np.uint32)
+    b = wl.uniform_coeffs(rng, 5, q_list, n, np.uint32)
+    with _tensor_plan(pm, n, q_list, cyclic=cyclic) as plan:
+        info = _select(plan, 4)
+        assert info["digit_bits"] == 8 and info["digits"] <= 4
         got = run_plan_batch(plan, a, b)
-    if n <= 4096:
-        assert_equal_residues(got, native.polymul_batch(a, b, [q]), "boundary n=%d q=%d" % (n, q))
-    else:
-        _check_sampled(got, a, b, [q], False, rng)
+        pm.polymul_plan_status(plan.handle)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list, cyclic=cyclic), "drained n=%d bits=%d" % (n, bits))
+
+
+@pytest.mark.parametrize("n,bits,ternary", [(8192, 30, False), (16384, 31, False), (16384, 31, True),
+                                            (8192, 20, True)])
+def test_drained_large_degrees_sampled(pm, n, bits, ternary):
+    """Up to 16 K chunks drained per unit of work; a 31-bit modulus at 2^14
+    has no undrained digit kernel (six 6-bit digits)."""
+    rng = np.random.default_rng(n + 3 * bits + ternary)
+    q_list = wl.draw_primes(rng, 2, bits, bits, 1)
+    a = wl.uniform_coeffs(rng, 3, q_list, n, np.uint32)
+    b = (wl.ternary_coeffs if ternary else wl.uniform_coeffs)(rng, 3, q_list, n, np.uint32)
+    with pm.Plan(n, q_list, path=pm.PATH_TENSOR, flags=pm.FLAG_TERNARY_B if ternary else 0) as plan:
+        info = _select(plan, 4)
+        assert info["tensor_groups"] >= 1
+        got = run_plan_batch(plan, a, b)
+        pm.polymul_plan_status(plan.handle)
+    _check_sampled(got, a, b, q_list, False, rng)
+
+
+def test_drained_matches_undrained_on_many_units(pm):
+    """Both digit kernels on a batch with more units of work than resident
+    CTAs: the same coefficients, bit for bit, and the oracle's on a sample."""
+    n = 4096
+    rng = np.random.default_rng(4099)
+    q_list = wl.draw_primes(rng, 3, 29, 30, 13)
+    a = wl.uniform_coeffs(rng, 97, q_list, n, np.uint32)
+    b = wl.uniform_coeffs(rng, 97, q_list, n, np.uint32)
+    with _tensor_plan(pm, n, q_list) as plan:
+        assert plan.info["tensor_kernel"] == 4  # first: four 8-bit digits instead of five 7-bit ones
+        assert 97 * 3 * plan.info["tensor_groups"] > plan.info["grid"]
+        drained = run_plan_batch(plan, a, b)
+        _select(plan, 2)
+        undrained = run_plan_batch(plan, a, b)
+    assert np.array_equal(drained, undrained)
+    _check_sampled(drained[:4], a[:4], b[:4], q_list, False, rng, count=8)

@@ -48,7 +48,8 @@ def test_every_candidate_is_exact(pm, n, bits, elem):
         for i in range(ncand):
             info = plan.select(i)
             labels.append((info["path"], info["radix_bits"], info["ntt_mode"], info["regs"], info["tensor_groups"],
-                           info["rns_moduli"], info["exchange_pad"], info["one_operand"], info["block"]))
+                           info["rns_moduli"], info["exchange_pad"], info["one_operand"], info["block"],
+                           info["tensor_kernel"], info["digits"]))
             assert_equal_residues(run_plan_batch(plan, a, b), want, "candidate %d %s" % (i, labels[-1]))
     assert len(set(labels)) == ncand
 
