@@ -415,24 +415,33 @@ int polymul_ragged_run_graph(polymul_ragged_batch *batch, const void *a, const v
 int polymul_ragged_status(polymul_ragged_batch *batch, void *stream);
 
 /*
- * polymul_ragged_tune -- choose the kernel shapes of a prepared list by
- * measurement on the caller's operands (the paper leaves such dimensions to
- * experiment, Sec. 2.6).  Each of the list's two launches (degrees 2^10 ..
- * 2^13; 2^14) exists in two shape sets -- 0: swizzled exchanges, both
- * operands in registers; 1: padded exchanges, one operand in registers at
- * 2^10, 2^11 and 2^14 (the default) -- and each launch keeps the faster set
- * (best of three timed runs after a warm-up).  a, b, c as for
- * polymul_ragged_run (c is overwritten with the products).  *choice
- * (may be NULL) receives bit 0 = set of the smaller degrees, bit 1 = set of
- * 2^14.  A recorded graph is rebuilt on its next replay.  Synchronous;
- * returns as polymul_ragged_status afterwards.  Errors: EINVAL, ETIMEOUT,
- * ECUDA.
+ * polymul_ragged_tune -- choose the kernel shapes and paths of a prepared
+ * list by measurement on the caller's operands (the paper leaves such
+ * dimensions to experiment, Sec. 2.6).  Each of the list's two NTT launches
+ * (degrees 2^10 .. 2^13; 2^14) exists in two shape sets -- 0: swizzled
+ * exchanges, both operands in registers; 1: padded exchanges, one operand
+ * in registers at 2^10, 2^11 and 2^14 (the default) -- and each launch
+ * keeps the faster set; then each degree class runs on the path that is
+ * faster for its rows: its NTT segment alone, or the tensor path (Sec. 2.2
+ * matrix form: the tiled digit kernel with 8-bit digits drained per K
+ * chunk, one launch per class, behind the NTT launches).  Best of three
+ * timed runs after a warm-up each.  a, b, c as for polymul_ragged_run (c is
+ * overwritten with the products).  *choice (may be NULL) receives bit 0 =
+ * set of the smaller degrees, bit 1 = set of 2^14, bit 2 + (log2 n - 10) =
+ * degree class n on the tensor path.  A recorded graph is rebuilt on its
+ * next replay.  Synchronous; returns as polymul_ragged_status afterwards.
+ * Errors: EINVAL, ETIMEOUT, ECUDA.
  */
 int polymul_ragged_tune(polymul_ragged_batch *batch, const void *a, const void *b, void *c,
                         void *stream, uint32_t *choice);
 
-/* Use the shape sets `choice` (bits as for polymul_ragged_tune) instead of
- * the default or tuned ones.  Errors: EINVAL. */
+/* Use the shape sets and paths `choice` (bits as for polymul_ragged_tune;
+ * tensor bits of classes the list does not hold are ignored) instead of the
+ * default (every class on the NTT path, set 1) or tuned ones.  Waits for
+ * the device to finish its work first (the NTT launches' segment list is
+ * rewritten).  Errors: EINVAL (choice >= 128, or a class with units and no
+ * tensor kernel for the pool: each pool prime needs at most four 8-bit
+ * digits, i.e. q < 2^31), ECUDA. */
 int polymul_ragged_select(polymul_ragged_batch *batch, uint32_t choice);
 
 /* Units, degree segments (`items`) and CTAs of a prepared list (any pointer

@@ -267,6 +267,28 @@ bool lookup_ntt(uint32_t elem, int logn, int mode, KernelInfo* ki) {
   return false;
 }
 
+}  // namespace
+
+// The occupancy query reports one CTA per SM for kernels that allocate
+// tensor memory; co-residency is in fact limited by shared memory,
+// registers, threads and the 512 tensor-memory columns, so count those.
+int pm::tmem_kernel_per_sm(const KernelInfo& ki, int device, int* per_sm) {
+  cudaFuncAttributes fa;
+  PM_CUDA(cudaFuncGetAttributes(&fa, ki.fn));
+  int smem_sm = 0, resv = 0;
+  PM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  PM_CUDA(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, device));
+  const int regs = (fa.numRegs + 7) / 8 * 8;
+  int n = smem_sm / (ki.smem + (int)fa.sharedSizeBytes + resv);
+  n = std::min(n, 65536 / std::max(1, regs * ki.block));
+  n = std::min(n, 2048 / ki.block);
+  n = std::min(n, 512 / ki.tmem_cols);  // never wait for tensor memory
+  *per_sm = n;
+  return POLYMUL_OK;
+}
+
+namespace {
+
 int configure_launch(polymul_plan* p) {
   PM_CUDA(cudaGetDevice(&p->device));
   PM_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -295,19 +317,8 @@ int configure_launch(polymul_plan* p) {
     return POLYMUL_OK;
   }
   if (p->ki.tmem_cols > 0) {
-    // The occupancy query reports one CTA per SM for kernels that allocate
-    // tensor memory; co-residency is in fact limited by shared memory,
-    // registers, threads and the 512 tensor-memory columns, so count those.
-    cudaFuncAttributes fa;
-    PM_CUDA(cudaFuncGetAttributes(&fa, p->ki.fn));
-    int smem_sm = 0, resv = 0;
-    PM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device));
-    PM_CUDA(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, p->device));
-    const int regs = (fa.numRegs + 7) / 8 * 8;
-    per_sm = smem_sm / (p->ki.smem + (int)fa.sharedSizeBytes + resv);
-    per_sm = std::min(per_sm, 65536 / std::max(1, regs * p->ki.block));
-    per_sm = std::min(per_sm, 2048 / p->ki.block);
-    per_sm = std::min(per_sm, 512 / p->ki.tmem_cols);  // never wait for tensor memory
+    const int r = tmem_kernel_per_sm(p->ki, p->device, &per_sm);
+    if (r != POLYMUL_OK) return r;
   } else {
     PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->ki.fn, p->ki.block, p->ki.smem));
   }

@@ -56,9 +56,16 @@ bool lookup_ntt_cluster2(uint32_t elem, int logn, int mode, bool seq, KernelInfo
 // 2^10..2^13 and one for 2^14, in two shape sets (0: swizzled exchanges,
 // both operands; 1: padded exchanges, one operand at 2^10, 2^11 and 2^14)
 constexpr int kRaggedSets = 2;
+constexpr int kRaggedClasses = 5;  // degree classes 2^10 .. 2^14 of an uneven list
 bool lookup_ntt_ragged(int mode, int set, KernelInfo* small, KernelInfo* big);
 
 // Toeplitz path on the tensor cores, k_toeplitz_batch<TShape<LOGN, WB, LA, LB>>
 bool lookup_toeplitz(int logn, int wb, int la, int lb, KernelInfo* ki);
+
+// Resident CTAs per SM of a kernel that allocates tensor memory (shared
+// memory, registers, threads and the 512 columns; the occupancy query does
+// not count them).  The kernel's dynamic shared-memory attribute must be set.
+// Returns a POLYMUL_* code.
+int tmem_kernel_per_sm(const KernelInfo& ki, int device, int* per_sm);
 
 }  // namespace pm

@@ -1,7 +1,9 @@
 // C-ABI entry points for uneven batches (polymul_ragged_*), see
 // include/polymul.h.  Host-side planning: tables per pool prime, units
 // sorted into degree segments, two concurrent persistent launches (2^14;
-// 2^10 .. 2^13), optional CUDA-graph replay.
+// 2^10 .. 2^13), optional CUDA-graph replay; a degree class may instead run
+// on the tensor path (Sec. 2.2 matrix form, the drained tiled kernel over
+// that class's rows), chosen per class by measurement.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,6 +17,7 @@
 #include "trace.h"
 #include "plan.h"
 #include "polymul_types.h"
+#include "toeplitz_tiled.h"
 
 using namespace pm;
 
@@ -34,6 +37,15 @@ struct polymul_ragged {
   KernelInfo ki[kRaggedSets][2];    // [shape set][0: degrees 2^10 .. 2^13, 1: 2^14]
   int grid_cap[kRaggedSets][2] = {};
   int device = 0, num_sms = 0;
+  // the tensor route of degree class 2^(10 + i): the drained tiled kernel
+  // with `tdigits` 8-bit digits per operand (enough for every pool prime),
+  // its tiling and resident grid, and the pool's constants for it
+  bool tensor_ok[kRaggedClasses] = {};
+  KernelInfo tki[kRaggedClasses];
+  TiledCfg tcfg[kRaggedClasses];
+  int tgrid_cap[kRaggedClasses] = {};
+  int tdigits = 0;
+  void* d_tpc = nullptr;  // [pool] TensorPrime (8-bit digit weights)
 };
 
 // A prepared list runs as up to two persistent launches (the 2^14 segment
@@ -56,6 +68,15 @@ struct polymul_ragged_batch {
   // shape set of each launch: the padded one-operand set by default (fewer
   // registers, no spills at 2^14); polymul_ragged_tune measures both
   int set[2] = {1, 1};
+  // degree segments of the whole list (host copy; d_items holds those the
+  // NTT launches take), and the classes on the tensor path (bit logn - 10)
+  std::vector<RaggedItem> items_h;
+  uint32_t present = 0;      // classes with units (bit logn - 10)
+  uint32_t tensor_mask = 0;  // a subset of `present`
+  unsigned long long* d_tctr = nullptr;  // 2 counters per tensor class launch
+  TensorTiledArgs targs[kRaggedClasses]{};
+  cudaGraphNode_t tnode[kRaggedClasses] = {};
+  RaggedItem* d_item1 = nullptr;  // one segment, for timing a class alone
 };
 
 namespace {
@@ -96,6 +117,52 @@ void build_ragged_prime(uint64_t q, uint32_t nmax, std::vector<uint32_t>& twf, s
   }
 }
 
+// 8-bit balanced digits covering the centred residues of every prime up to
+// qmax (at most 4: q < 2^31); 0 if more are needed
+int ragged_tensor_digits(uint64_t qmax) {
+  for (int l = 1; l <= 4; ++l)
+    if ((uint64_t)127 * ((1ull << (8 * l)) - 1) / 255 >= qmax / 2) return l;
+  return 0;
+}
+
+// The tensor route of every degree class up to n_max: kernels, their
+// resident grids, and the pool's digit-weight constants.  A class whose
+// kernel does not fit keeps the NTT route only.
+int ragged_tensor_setup(polymul_ragged* r) {
+  const uint64_t qmax = *std::max_element(r->pool.begin(), r->pool.end());
+  r->tdigits = ragged_tensor_digits(qmax);
+  if (!r->tdigits) return POLYMUL_OK;
+  for (int i = 0; i < kRaggedClasses; ++i) {
+    const int logn = 10 + i;
+    if (logn > (int)r->lognmax) break;
+    KernelInfo ki;
+    if (!lookup_toeplitz_tiled_drain(logn, r->tdigits, r->tdigits, &ki) ||
+        !toeplitz_tiled_config_drain(logn, r->tdigits, r->tdigits, &r->tcfg[i]))
+      continue;
+    PM_CUDA(cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem));
+    int per_sm = 0;
+    const int rc = tmem_kernel_per_sm(ki, r->device, &per_sm);
+    if (rc != POLYMUL_OK) return rc;
+    if (per_sm < 1) continue;
+    r->tki[i] = ki;
+    r->tgrid_cap[i] = per_sm * r->num_sms;
+    r->tensor_ok[i] = true;
+  }
+  std::vector<TensorPrime> tp(r->pool.size());
+  for (size_t j = 0; j < r->pool.size(); ++j) {
+    const uint64_t q = r->pool[j];
+    memset(&tp[j], 0, sizeof tp[j]);
+    tp[j].q = (uint32_t)q;
+    for (int e = 0; e < 15; ++e) tp[j].pw[e] = (uint32_t)pm::host::powmod(2, 8ull * e, q);
+    tp[j].mu = (uint64_t)(((pm::host::u128)1 << 64) / q);
+    tp[j].bias = ((1ull << 60) + q - 1) / q * q;
+  }
+  if (cudaMalloc(&r->d_tpc, tp.size() * sizeof(TensorPrime)) != cudaSuccess)
+    return fail(POLYMUL_ENOMEM, "tensor constants");
+  PM_CUDA(cudaMemcpy(r->d_tpc, tp.data(), tp.size() * sizeof(TensorPrime), cudaMemcpyHostToDevice));
+  return POLYMUL_OK;
+}
+
 }  // namespace
 
 extern "C" void polymul_ragged_destroy(polymul_ragged* r) {
@@ -103,6 +170,7 @@ extern "C" void polymul_ragged_destroy(polymul_ragged* r) {
   cudaFree(r->d_twf);
   cudaFree(r->d_twi);
   cudaFree(r->d_pc);
+  cudaFree(r->d_tpc);
   delete r;
 }
 
@@ -153,6 +221,7 @@ extern "C" int polymul_ragged_create(const uint64_t* pool, uint32_t pool_size, u
     }
     if (e != cudaSuccess) rc = cuda_fail(e, "ragged kernel configuration");
   }
+  if (rc == POLYMUL_OK) rc = ragged_tensor_setup(r);
   if (rc != POLYMUL_OK) {
     std::string keep = polymul_last_error();
     polymul_ragged_destroy(r);
@@ -174,8 +243,48 @@ extern "C" void polymul_ragged_batch_destroy(polymul_ragged_batch* b) {
   cudaFree(b->d_items);
   cudaFree(b->d_ctr);
   cudaFree(b->d_err);
+  cudaFree(b->d_tctr);
+  cudaFree(b->d_item1);
   delete b;
 }
+
+namespace {
+
+// The launches of the list under its path choice: the NTT segments (d_items,
+// rewritten here; the 2^14 one, if present and on the NTT path, goes to the
+// second kernel) and one tiled tensor launch per class on the tensor path.
+// The caller makes sure that no launch of the list is in flight.
+void apply_paths(polymul_ragged_batch* b) {
+  polymul_ragged* r = b->ctx;
+  std::vector<RaggedItem> ntt;
+  uint64_t ntt_units = 0;
+  for (const RaggedItem& it : b->items_h) {
+    const int cls = (int)it.logn - 10;
+    if (r->tensor_ok[cls]) {
+      const TiledCfg& tc = r->tcfg[cls];
+      const TensorTiledArgs keep = b->targs[cls];  // operands, if set
+      b->targs[cls] = TensorTiledArgs{keep.a, keep.b, keep.c, (const TensorPrime*)r->d_tpc,
+                                      (uint64_t)it.count * tc.ngrp, 1, 0x80008000u, it.logn, 8u, tc.bpg, tc.ngrp,
+                                      tc.kc, tc.a_win, tc.bt_off, tc.tmem_cols, b->d_tctr + 2 * cls, b->d_err,
+                                      b->d_units + it.first};
+    }
+    if (!((b->tensor_mask >> cls) & 1u)) {
+      ntt.push_back(it);
+      ntt_units += it.count;
+    }
+  }
+  if (!ntt.empty()) cudaMemcpy(b->d_items, ntt.data(), ntt.size() * sizeof(RaggedItem), cudaMemcpyHostToDevice);
+  const uint64_t n_big = (!ntt.empty() && ntt[0].logn == 14) ? 1 : 0;
+  b->part_units[1] = n_big ? ntt[0].count : 0;
+  b->part_units[0] = ntt_units - b->part_units[1];
+  b->args[1] = RaggedArgs{nullptr, nullptr, nullptr, b->d_units, b->d_items, n_big, r->d_twf, r->d_twi,
+                          (const PrimeConst<uint32_t>*)r->d_pc, r->nmax, b->d_ctr, b->d_err};
+  b->args[0] = RaggedArgs{nullptr, nullptr, nullptr, b->d_units, b->d_items + n_big, ntt.size() - n_big,
+                          r->d_twf, r->d_twi, (const PrimeConst<uint32_t>*)r->d_pc, r->nmax,
+                          b->d_ctr + (kRaggedMaxSegs + 1), b->d_err};
+}
+
+}  // namespace
 
 extern "C" int polymul_ragged_prepare(polymul_ragged* r, const polymul_desc* descs, uint32_t count,
                                       const uint32_t* prime_idx, uint64_t prime_idx_len, uint64_t total_elems,
@@ -229,6 +338,8 @@ extern "C" int polymul_ragged_prepare(polymul_ragged* r, const polymul_desc* des
     const int z = 0;
     rc = up((void**)&b->d_ctr, zero, sizeof zero);
     if (rc == POLYMUL_OK) rc = up((void**)&b->d_err, &z, sizeof z);
+    if (rc == POLYMUL_OK) rc = up((void**)&b->d_tctr, zero, 2 * kRaggedClasses * sizeof(unsigned long long));
+    if (rc == POLYMUL_OK) rc = up((void**)&b->d_item1, nullptr, 0);
   }
   if (rc == POLYMUL_OK && (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
                            cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -240,15 +351,9 @@ extern "C" int polymul_ragged_prepare(polymul_ragged* r, const polymul_desc* des
     fail(rc, "%s", keep.c_str());
     return rc;
   }
-  // the 2^14 segment (first, if present) goes to the second kernel
-  const uint64_t n_big = (!items.empty() && items[0].logn == 14) ? 1 : 0;
-  b->part_units[1] = n_big ? items[0].count : 0;
-  b->part_units[0] = b->n_units - b->part_units[1];
-  b->args[1] = RaggedArgs{nullptr, nullptr, nullptr, b->d_units, b->d_items, n_big, r->d_twf, r->d_twi,
-                          (const PrimeConst<uint32_t>*)r->d_pc, r->nmax, b->d_ctr, b->d_err};
-  b->args[0] = RaggedArgs{nullptr, nullptr, nullptr, b->d_units, b->d_items + n_big, b->n_items - n_big,
-                          r->d_twf, r->d_twi, (const PrimeConst<uint32_t>*)r->d_pc, r->nmax,
-                          b->d_ctr + (kRaggedMaxSegs + 1), b->d_err};
+  b->items_h = items;
+  for (const RaggedItem& it : items) b->present |= 1u << (it.logn - 10);
+  apply_paths(b);
   *out = b;
   return POLYMUL_OK;
 }
@@ -269,6 +374,7 @@ void drop_graph(polymul_ragged_batch* b) {
   b->exec = nullptr;
   b->graph = nullptr;
   b->node[0] = b->node[1] = nullptr;
+  for (int i = 0; i < kRaggedClasses; ++i) b->tnode[i] = nullptr;
 }
 int ragged_grid(const polymul_ragged_batch* b, int part) {
   return (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap[b->set[part]][part],
@@ -280,6 +386,20 @@ void set_operands(polymul_ragged_batch* b, const void* a, const void* bb, void* 
     b->args[i].b = (const uint32_t*)bb;
     b->args[i].c = (uint32_t*)c;
   }
+  for (int i = 0; i < kRaggedClasses; ++i) {
+    b->targs[i].a = (const uint32_t*)a;
+    b->targs[i].b = (const uint32_t*)bb;
+    b->targs[i].c = (uint32_t*)c;
+  }
+}
+int tensor_grid(const polymul_ragged_batch* b, int cls) {
+  return (int)std::min<uint64_t>((uint64_t)b->ctx->tgrid_cap[cls], std::max<uint64_t>(1, b->targs[cls].units));
+}
+bool tensor_class(const polymul_ragged_batch* b, int cls) { return (b->tensor_mask >> cls) & 1u; }
+cudaError_t launch_tensor(polymul_ragged_batch* b, int cls, cudaStream_t s) {
+  const KernelInfo& ki = b->ctx->tki[cls];
+  void* argv[] = {&b->targs[cls]};
+  return cudaLaunchKernel(ki.fn, tensor_grid(b, cls), ki.block, argv, ki.smem, s);
 }
 }  // namespace
 
@@ -309,6 +429,9 @@ extern "C" int polymul_ragged_run(polymul_ragged_batch* b, const void* a, const 
     PM_CUDA(cudaEventRecord(b->ev_join, b->side));
     PM_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
   }
+  // classes on the tensor path: one tiled launch each, behind the NTT ones
+  for (int cls = kRaggedClasses - 1; cls >= 0; --cls)
+    if (tensor_class(b, cls)) PM_CUDA(launch_tensor(b, cls, st));
   return POLYMUL_OK;
 }
 
@@ -333,14 +456,32 @@ extern "C" int polymul_ragged_run_graph(polymul_ragged_batch* b, const void* a, 
     kp[i].sharedMemBytes = ki.smem;
     kp[i].kernelParams = argv[i];
   }
+  // the tensor classes' launches: independent nodes as well
+  cudaKernelNodeParams tp[kRaggedClasses];
+  void* targv[kRaggedClasses][1];
+  for (int i = 0; i < kRaggedClasses; ++i) {
+    memset(&tp[i], 0, sizeof tp[i]);
+    if (!tensor_class(b, i)) continue;
+    const KernelInfo& ki = b->ctx->tki[i];
+    targv[i][0] = &b->targs[i];
+    tp[i].func = const_cast<void*>(ki.fn);
+    tp[i].gridDim = dim3(tensor_grid(b, i));
+    tp[i].blockDim = dim3(ki.block);
+    tp[i].sharedMemBytes = ki.smem;
+    tp[i].kernelParams = targv[i];
+  }
   if (!b->exec) {
     PM_CUDA(cudaGraphCreate(&b->graph, 0));
     for (int i = 1; i >= 0; --i)
       if (b->part_units[i]) PM_CUDA(cudaGraphAddKernelNode(&b->node[i], b->graph, nullptr, 0, &kp[i]));
+    for (int i = kRaggedClasses - 1; i >= 0; --i)
+      if (tensor_class(b, i)) PM_CUDA(cudaGraphAddKernelNode(&b->tnode[i], b->graph, nullptr, 0, &tp[i]));
     PM_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
   } else {
     for (int i = 0; i < 2; ++i)
       if (b->node[i]) PM_CUDA(cudaGraphExecKernelNodeSetParams(b->exec, b->node[i], &kp[i]));
+    for (int i = 0; i < kRaggedClasses; ++i)
+      if (b->tnode[i]) PM_CUDA(cudaGraphExecKernelNodeSetParams(b->exec, b->tnode[i], &tp[i]));
   }
   PM_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
   return POLYMUL_OK;
@@ -355,6 +496,7 @@ extern "C" int polymul_ragged_status(polymul_ragged_batch* b, void* stream) {
   if (!h) return POLYMUL_OK;
   PM_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
   PM_CUDA(cudaMemset(b->d_ctr, 0, 2 * (kRaggedMaxSegs + 1) * sizeof(unsigned long long)));
+  PM_CUDA(cudaMemset(b->d_tctr, 0, 2 * kRaggedClasses * sizeof(unsigned long long)));
   return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }
 
@@ -378,6 +520,9 @@ extern "C" int polymul_ragged_tune(polymul_ragged_batch* b, const void* a, const
   TraceRange trace_("polymul_ragged_tune");
   int rc = ragged_check(b, a, bb, c);
   if (rc != POLYMUL_OK) return rc;
+  PM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  b->tensor_mask = 0;  // shape sets first, on every class's NTT segment
+  apply_paths(b);
   set_operands(b, a, bb, c);
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -407,20 +552,68 @@ extern "C" int polymul_ragged_tune(polymul_ragged_batch* b, const void* a, const
       if (best[set] < best[pick]) pick = set;
     b->set[part] = pick;
   }
+  // then the path of each degree class: its NTT segment alone (a one-segment
+  // launch of its kernel, shape set as chosen) against its tensor launch
+  auto time_launch = [&](auto&& launch_one) -> float {
+    float best = 1e30f;
+    for (int round = 0; round < 4 && rc == POLYMUL_OK; ++round) {
+      cudaError_t e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = launch_one();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) rc = cuda_fail(e, "ragged tuning launch");
+      if (round > 0 && ms < best) best = ms;
+    }
+    return best;
+  };
+  uint32_t mask = 0;
+  for (const RaggedItem& it : b->items_h) {
+    const int cls = (int)it.logn - 10;
+    if (rc != POLYMUL_OK || !b->ctx->tensor_ok[cls]) continue;
+    const int part = it.logn == 14 ? 1 : 0;
+    if (cudaMemcpy(b->d_item1, &it, sizeof it, cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = fail(POLYMUL_ECUDA, "ragged tuning segment");
+      break;
+    }
+    RaggedArgs one = b->args[part];
+    one.items = b->d_item1;
+    one.n_items = 1;
+    const KernelInfo& ki = ragged_kernel(b, part);
+    const int grid = (int)std::min<uint64_t>((uint64_t)b->ctx->grid_cap[b->set[part]][part],
+                                             std::max<uint32_t>(1u, it.count));
+    const float t_ntt = time_launch([&]() {
+      void* argv[] = {&one};
+      return cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st);
+    });
+    const float t_tc = time_launch([&]() { return launch_tensor(b, cls, st); });
+    if (t_tc < t_ntt) mask |= 1u << cls;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != POLYMUL_OK) return rc;
+  b->tensor_mask = mask;
+  apply_paths(b);
   drop_graph(b);
-  if (choice) *choice = (uint32_t)b->set[0] | ((uint32_t)b->set[1] << 1);
+  if (choice) *choice = (uint32_t)b->set[0] | ((uint32_t)b->set[1] << 1) | (mask << 2);
   return polymul_ragged_status(b, stream);
 }
 
 extern "C" int polymul_ragged_select(polymul_ragged_batch* b, uint32_t choice) {
   clear_error();
   if (!b) return fail(POLYMUL_EINVAL, "batch is NULL");
-  if (choice > 3) return fail(POLYMUL_EINVAL, "choice=%u must be in [0, 3]", choice);
+  if (choice >= (4u << kRaggedClasses)) return fail(POLYMUL_EINVAL, "choice=%u must be below %u", choice, 4u << kRaggedClasses);
+  const uint32_t mask = (choice >> 2) & b->present;
+  for (int cls = 0; cls < kRaggedClasses; ++cls)
+    if (((mask >> cls) & 1u) && !b->ctx->tensor_ok[cls])
+      return fail(POLYMUL_EINVAL, "degree 2^%d has no tensor kernel for this pool", 10 + cls);
+  // the NTT launches' segment list is rewritten: let every launch finish
+  PM_CUDA(cudaDeviceSynchronize());
   b->set[0] = (int)(choice & 1u);
   b->set[1] = (int)((choice >> 1) & 1u);
+  b->tensor_mask = mask;
+  apply_paths(b);
   drop_graph(b);
   return POLYMUL_OK;
 }

@@ -182,10 +182,19 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
     if (tid == 0) s_next = atomicAdd(args.ctr, 1ull);
     const uint64_t row = cur / ngrp;
     const uint32_t grp = (uint32_t)(cur % ngrp);
-    const uint32_t j = (uint32_t)(row % args.k);
+    uint64_t off;
+    uint32_t j;
+    if (args.rows) {
+      const RaggedUnit u = args.rows[row];
+      off = u.offset;
+      j = u.prime;
+    } else {
+      off = row * n;
+      j = (uint32_t)(row % args.k);
+    }
     const uint32_t q = args.tp[j].q;
-    const uint32_t* a = args.a + row * n;
-    const uint32_t* b = args.b + row * n;
+    const uint32_t* a = args.a + off;
+    const uint32_t* b = args.b + off;
     const uint32_t b0 = grp * bpg * S;  // the unit's first 1024-output block
     if constexpr (DRAIN) {
 #pragma unroll
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
     if (failed) break;
 
     // ---- ConvertMatrix: recombine digit pairs, reduce mod q, store ----
-    uint32_t* c = args.c + row * n;
+    uint32_t* c = args.c + off;
     const uint64_t mu = args.tp[j].mu, bias = args.tp[j].bias;
     if constexpr (DRAIN) {
 #pragma unroll

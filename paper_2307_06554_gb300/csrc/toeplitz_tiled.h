@@ -33,6 +33,10 @@ struct TensorTiledArgs {
   uint32_t bpg, ngrp, kc, a_win, bt_off, tmem_cols;
   unsigned long long* ctr;  // {next unit, finished CTAs}
   int* err;
+  // NULL: row r (product r / k, prime r % k) at element offset r n of a, b,
+  // c with tp[r % k]; else row r at rows[r].offset with tp[rows[r].prime]
+  // (the rows of one degree class of an uneven list)
+  const RaggedUnit* rows;
 };
 
 // The tiling for degree 2^logn with la digits of a and lb of b (false if
@@ -47,9 +51,9 @@ bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki);
 
 // The drained variant: each K chunk's fp32 accumulators are drained into
 // 64-bit integer sums, so 8-bit digits are exact at every degree (chunks of
-// at most 1024); at most 4 digits (every q < 2^31), one A slice per unit of
-// work, shifted copies of b as tensor memory allows.  ki->wb = 8,
-// ki->digits = lb.
+// at most 1024); at most 4 digits (every q < 2^31); with la == lb one A
+// slice per unit of work against shifted copies of b as tensor memory
+// allows, with la == 1 up to 4 A slices.  ki->wb = 8, ki->digits = lb.
 bool toeplitz_tiled_config_drain(int logn, int la, int lb, TiledCfg* cfg);
 bool lookup_toeplitz_tiled_drain(int logn, int la, int lb, KernelInfo* ki);
 

@@ -387,9 +387,20 @@ def polymul_ragged_status(batch: int, stream=None) -> None:
     _check(_lib.polymul_ragged_status(batch, _stream(stream)))
 
 
+# polymul_ragged_select / _tune choice bits: bit 0 the shape set of degrees
+# 2^10..2^13, bit 1 that of 2^14, bit 2 + (log2 n - 10) degree class n on
+# the tensor path
+RAGGED_TENSOR_SHIFT = 2
+
+
+def ragged_tensor_bits(*logns) -> int:
+    """Choice bits putting the degree classes 2^logn on the tensor path."""
+    return sum(1 << (RAGGED_TENSOR_SHIFT + l - 10) for l in logns)
+
+
 def polymul_ragged_tune(batch: int, a, b, c, stream=None) -> int:
-    """Pick each launch's shape set by measurement; returns the choice bits
-    (bit 0: degrees 2^10..2^13, bit 1: 2^14)."""
+    """Pick each launch's shape set, then each degree class's path, by
+    measurement; returns the choice bits (see RAGGED_TENSOR_SHIFT)."""
     ch = ctypes.c_uint32(0)
     _check(_lib.polymul_ragged_tune(batch, _ptr(a), _ptr(b), _ptr(c), _stream(stream), ctypes.byref(ch)))
     return ch.value

@@ -1,7 +1,9 @@
 """Uneven batches in one persistent launch (and as a CUDA graph) against the
 CPU oracle: every product of small mixed lists, a sample of the 2000-product
 workload (n from 1024 to 16384, 1..16 primes), graph replay identical to
-the direct launch, and argument validation."""
+the direct launch, argument validation, and degree classes moved to the
+tensor path (the drained tiled digit kernel over the class's rows) alone,
+mixed with NTT classes, and as the tuner chooses."""
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
@@ -42,7 +44,7 @@ def _run(pm, rag, nmax=16384, graph=False, choice=None, tune=False):
         if choice is not None:
             r.select(choice)
         if tune:
-            assert 0 <= r.tune(ta, tb, tc) <= 3
+            assert 0 <= r.tune(ta, tb, tc) < 128
             tc.fill_(-1)
         r.run(ta, tb, tc, graph=graph)
         pm.polymul_ragged_status(r.batch)
@@ -163,3 +165,64 @@ def test_tuned_list_is_exact_direct_and_graph(pm):
     _check(rag, c, offsets, range(len(rag.products)))
     c, offsets = _run(pm, rag, tune=True, graph=True)
     _check(rag, c, offsets, range(len(rag.products)))
+
+
+ALL_CLASSES = (10, 11, 12, 13, 14)
+
+
+@pytest.mark.parametrize("logns,sets", [(ALL_CLASSES, 3), ((10, 12, 14), 1), ((11, 13), 2), ((14,), 0)])
+def test_tensor_classes_are_exact(pm, logns, sets):
+    """Degree classes on the tensor path, the rest on the NTT launches (with
+    either shape set), direct and as a graph: every product against the
+    oracle."""
+    rag = wl.ragged_2000(count=25, seed=32)
+    choice = sets | pm.ragged_tensor_bits(*logns)
+    c, offsets = _run(pm, rag, choice=choice)
+    _check(rag, c, offsets, range(len(rag.products)))
+    c2, _ = _run(pm, rag, choice=choice, graph=True)
+    assert np.array_equal(c, c2)
+
+
+def test_tensor_classes_relaunch_and_switch(pm):
+    """The same list launched repeatedly while its classes move between the
+    paths (the tensor launches' counters reset, the NTT segment list is
+    rewritten, a recorded graph is rebuilt): identical results each time."""
+    import torch
+    rag = wl.ragged_2000(count=30, seed=36, kmax=4)
+    a, b = _pack(rag)
+    outs = []
+    with pm.Ragged(rag.pool, 16384, [(p.n, p.prime_idx) for p in rag.products]) as r:
+        ta = torch.from_numpy(a.view(np.int32)).cuda()
+        tb = torch.from_numpy(b.view(np.int32)).cuda()
+        for choice, graph in ((1, True), (1 | pm.ragged_tensor_bits(*ALL_CLASSES), True),
+                              (1 | pm.ragged_tensor_bits(*ALL_CLASSES), False), (3 | pm.ragged_tensor_bits(12), True),
+                              (1, False)):
+            r.select(choice)
+            for _ in range(2):
+                tc = torch.full_like(ta, -1)
+                r.run(ta, tb, tc, graph=graph)
+                pm.polymul_ragged_status(r.batch)
+                outs.append(tc.cpu().numpy().view(np.uint32))
+        off = list(r.offsets)
+    for c in outs[1:]:
+        assert np.array_equal(c, outs[0])
+    _check(rag, outs[0], off, range(len(rag.products)))
+
+
+def test_select_rejects_bad_choice(pm):
+    import torch
+    rag = wl.ragged_2000(count=3, seed=37, degrees=(1024,), kmax=2, pool_size=4)
+    with pm.Ragged(rag.pool, 4096, [(p.n, p.prime_idx) for p in rag.products]) as r:
+        with pytest.raises(pm.PolymulError) as ei:
+            r.select(128)
+        assert ei.value.code == pm.POLYMUL_EINVAL
+        r.select(pm.ragged_tensor_bits(13, 14))  # classes the list does not hold: ignored
+        a, b = _pack(rag)
+        ta = torch.from_numpy(a.view(np.int32)).cuda()
+        tb = torch.from_numpy(b.view(np.int32)).cuda()
+        tc = torch.full_like(ta, -1)
+        r.run(ta, tb, tc)
+        pm.polymul_ragged_status(r.batch)
+        c = tc.cpu().numpy().view(np.uint32)
+        off = list(r.offsets)
+    _check(rag, c, off, range(len(rag.products)))
