@@ -76,6 +76,8 @@ def _args():
     p.add_argument("--case", choices=sorted(CASES), help="run one small profiling case (or the ALU-peak "
                    "microbenchmark) instead of the benchmark, and print what it ran")
     p.add_argument("--launches", type=int, default=4, help="launches of a --case")
+    p.add_argument("--karatsuba-model", action="store_true",
+                   help="print the tile cost model of one degree-level Karatsuba step on the tensor path (no GPU)")
     return p.parse_args()
 
 
@@ -578,6 +580,83 @@ def _rns_shifts(n, r):
     return s
 
 
+# ------------------------------------------------------------------ Karatsuba cost model
+# Tile cost of the tensor path's matrix form (Sec. 2.2, 2.5), for deciding
+# whether one degree-level Karatsuba step (Sec. 4: h0 = a0 b0, h2 = a1 b1,
+# h1 = (a0 + a1)(b0 + b1) - h0 - h2, three half-size linear products) pays.
+# An MMA covers 128 rows of A (8 outputs each: a block of 1024 outputs) by
+# K = 16 by N = 8 x digits of b x shifts (padded to 16); it reads a 4 KB A
+# tile and an N x 16 bf16 B tile from shared memory.  The direct negacyclic
+# kernels run every (block group, K step) tile; a linear product of size m
+# (2m outputs, K = m) can skip the tiles of its Toeplitz matrix that are all
+# zero, at that granularity.  Optimistic for Karatsuba: the operand sums
+# and the recombination of h0, h1, h2 are counted as free.
+
+def _digit_reach(w, L):
+    return ((1 << (w - 1)) - 1) * ((1 << (w * L)) - 1) // ((1 << w) - 1)
+
+
+def _digits_for(w, bound):
+    """Balanced w-bit digits that reach every |x| <= bound."""
+    return next(L for L in range(1, 16) if _digit_reach(w, L) >= bound)
+
+
+def _mma_n(lb, shifts):
+    return (8 * lb * shifts + 15) // 16 * 16
+
+
+def _mma_smem_bytes(nn):
+    return 128 * 16 * 2 + nn * 16 * 2
+
+
+def _linear_tile_needed(m, blocks, k0):
+    """Whether the tile of output blocks `blocks` (1024 outputs each) and
+    K step [k0, k0 + 16) of a linear product of size m holds a nonzero entry
+    (c_j sums a_{j-k} b_k, 0 <= j - k < m, 0 <= k < m)."""
+    return any(1024 * o + 1023 - k0 >= 0 and 1024 * o - (k0 + 15) <= m - 1 for o in blocks)
+
+
+def _linear_tiles(m, shifts):
+    nblk = max(1, 2 * m // 1024)
+    return sum(_linear_tile_needed(m, range(g, min(nblk, g + shifts)), 16 * c)
+               for g in range(0, nblk, shifts) for c in range(m // 16))
+
+
+def _tile_cost(mmas, nn):
+    return {"mmas": mmas, "mma_n": nn, "smem_bytes": mmas * _mma_smem_bytes(nn), "mac_slots": mmas * 128 * 16 * nn}
+
+
+def karatsuba_model(n, q, la, lb, shifts, ternary_b=False):
+    """Per (product, prime): the direct kernel's tiles against one
+    Karatsuba step's, with 8-bit digits (the drained kernel's; exact per K
+    chunk at any length).  h1's operands are sums of two centred residues
+    (|x| <= 2 floor(q/2)): one digit more where that crosses a digit
+    boundary; a ternary b's sums stay within one digit."""
+    direct = _tile_cost(la * (max(1, n // 1024) // shifts) * (n // 16), _mma_n(lb, shifts))
+    m = n // 2
+    la1 = la if ternary_b else max(la, _digits_for(8, 2 * (q // 2)))
+    lb1 = max(lb, _digits_for(8, 2 * (q // 2)))
+    out = {"n": n, "q_bits": q.bit_length(), "digits": [la, lb], "h1_digits": [la1, lb1], "direct": direct}
+    for s in sorted({1, shifts}):
+        t = _linear_tiles(m, s)
+        h02 = _tile_cost(2 * la * t, _mma_n(lb, s))
+        h1 = _tile_cost(la1 * t, _mma_n(lb1, s))
+        kara = {k: h02[k] + h1[k] for k in ("mmas", "smem_bytes", "mac_slots")}
+        kara["tiles_per_linear_product"] = t
+        kara["smem_ratio"] = kara["smem_bytes"] / direct["smem_bytes"]
+        kara["mac_slot_ratio"] = kara["mac_slots"] / direct["mac_slots"]
+        out["karatsuba_shifts_%d" % s] = kara
+    return out
+
+
+KARATSUBA_SHAPES = [
+    ("ring_1024 (n = 1024, q = 12289)", 1024, 12289, 2, 2, 1, False),
+    ("rns_4096 (n = 4096, 30-bit primes)", 4096, (1 << 30) - 35, 4, 4, 2, False),
+    ("rns_4096, ternary b", 4096, (1 << 30) - 35, 1, 4, 1, True),
+    ("n = 16384, 30-bit prime", 16384, (1 << 30) - 35, 4, 4, 2, False),
+]
+
+
 def _tensor_smem_roofline(n, digits, units, seconds, sms, sm_mhz, la=None, shifts=1):
     """`digits` of the operand on the MMA's B (Toeplitz) side, `la` (default
     the same) on its A (aliased) side; `shifts` copies of b share one A
@@ -741,6 +820,24 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
                               "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g,
                               "hbm_frac": 3 * total * 4 / (ms / 1e3) / 1e9 / hbm,
                               "bit_exact_sample": None, "l2": "inputs 1.3 GB (> L2)"}
+        # the tensor route of the same list: each degree class as one launch
+        # of the drained tiled digit kernel (four 8-bit digits per operand),
+        # beside the tuner's per-class path choice
+        ntt_out = tc.clone()
+        out["ragged_2000"]["class_paths"] = {
+            "2^%d" % l: ("tensor" if (choice >> (polymul.RAGGED_TENSOR_SHIFT + l - 10)) & 1 else "ntt")
+            for l in range(10, 15)}
+        r.select((choice & 3) | polymul.ragged_tensor_bits(10, 11, 12, 13, 14))
+        r.run(ta, tb, tc, stream=sp, graph=True)
+        tms = _time_steps(lambda i: r.run(ta, tb, tc, stream=sp, graph=True), stream, 2)
+        polymul.polymul_ragged_status(r.batch, sp)
+        flops = sum(2.0 * p.n * p.n * 16 * len(p.prime_idx) for p in rag.products)
+        out["ragged_2000"]["tensor_route"] = {
+            "us_per_launch": tms * 1e3, "products_per_s": len(rag.products) / (tms / 1e3),
+            "kernel": "k_toeplitz_tiled drained, 4 x 4 digits of 8 bits, one launch per degree class (graph)",
+            "tensor_frac_bf16": flops / (tms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1911.7),
+            "bit_exact_vs_ntt": bool(torch.equal(tc, ntt_out))}
+        r.select(choice)
     return out
 
 
@@ -1286,6 +1383,10 @@ def run_ours(args, ws, rank, local):
 
 def main():
     args = _args()
+    if args.karatsuba_model:
+        for name, n, q, la, lb, s, tern in KARATSUBA_SHAPES:
+            print(json.dumps({"shape": name, **karatsuba_model(n, q, la, lb, s, tern)}), flush=True)
+        return
     if args.case:
         print(args.case, json.dumps(_case(args.case, args.launches)), flush=True)
         return
