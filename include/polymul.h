@@ -150,7 +150,12 @@ typedef struct polymul_plan_info {
                              parked in shared memory during b's)            */
     uint32_t tensor_kernel;/* tensor path: the main kernel, coded as
                              polymul_tensor_shape_info.kernel (1 whole
-                             product, 2 tiled, 3 RNS, 4 tiled drained)      */
+                             product, 2 tiled, 3 RNS, 4 tiled drained, 5
+                             tiled drained warp-specialised)                 */
+    uint32_t kernel_regs;  /* registers per thread the main kernel was
+                             compiled to (from the CUDA runtime)            */
+    uint32_t kernel_max_block;/* the largest CTA the main kernel can launch
+                             with (from the CUDA runtime)                   */
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
@@ -312,7 +317,8 @@ typedef struct polymul_tensor_shape_info {
     uint32_t kernel;      /* 1 whole-product digit kernel, 2 tiled digit
                              kernel, 3 residue number system of small moduli,
                              4 tiled digit kernel that drains each K chunk
-                             (8-bit digits at every degree) */
+                             (8-bit digits at every degree), 5 the same as
+                             a warp-specialised pipeline (one CTA per SM) */
     uint32_t candidates;  /* tensor kernels the plan holds (the autotuner
                              chooses among them)                            */
     uint32_t digit_bits;  /* digit kernels: digit width w (0 for the RNS one) */

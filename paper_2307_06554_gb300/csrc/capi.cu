@@ -151,7 +151,13 @@ DigitShape digit_shape(const polymul_plan* p, const KernelInfo& k) {
 }
 
 bool tiled_config_of(const KernelInfo& k, int logn, int la, int lb, TiledCfg* cfg) {
+  if (k.ws) return toeplitz_ws_config(logn, la, lb, cfg);
   return k.drain ? toeplitz_tiled_config_drain(logn, la, lb, cfg) : toeplitz_tiled_config(logn, la, lb, cfg);
+}
+
+// tensor kernel code reported by polymul_plan_info and polymul_tensor_shape
+uint32_t tensor_kernel_code(const KernelInfo& k) {
+  return k.rns ? 3u : k.ws ? 5u : k.drain ? 4u : k.tiled ? 2u : 1u;
 }
 
 // The tensor path's kernels for degree n and moduli up to qmax, the default
@@ -192,13 +198,17 @@ bool choose_tensor(uint32_t n, uint64_t qmax, uint32_t elem, bool ternary_b, Ten
   // 1318 us vs 5 x 5 2079 us at n = 4096, 335 vs 539 us at n = 2048; ternary
   // b, 1 x 4 vs 1 x 5: 439 vs 445 us at n = 4096, 109 vs 129 us at 2048)
   KernelInfo kdrain;
-  const int l8 = elem == 4 && qmax < (1ull << 31) ? drain_digits(qmax) : 0;
+  const int l8 = elem == 4 && qmax < (1ull << 31) ? drain_digits(qmax) : 0;  // 0: no drained kernel
   if (l8 && tc->wb > 0 && tc->wb < 8 && lookup_toeplitz_tiled_drain(logn, ternary_b ? 1 : l8, l8, &kdrain)) {
     if (l8 < tc->L || tc->kernels.empty())
       tc->kernels.insert(tc->kernels.begin(), kdrain);
     else
       tc->kernels.push_back(kdrain);
   }
+  // the drained kernel as a warp-specialised pipeline (one CTA per SM: the
+  // operand builds and the drains overlap the MMAs), at every degree
+  KernelInfo kws;
+  if (l8 && lookup_toeplitz_ws(logn, ternary_b ? 1 : l8, l8, &kws)) tc->kernels.push_back(kws);
   std::vector<uint32_t> mods;
   if (rns_choose_base(n, qmax, &mods) && lookup_toeplitz_rns(logn, (uint32_t)mods.size(), elem, &krns)) {
     tc->kernels.push_back(krns);
@@ -533,7 +543,12 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->rns_moduli = p->path == POLYMUL_PATH_TENSOR && p->ki.rns ? p->rns_r : 0;
   info->exchange_pad = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.pad : 0u;
   info->one_operand = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.seq : 0u;
-  info->tensor_kernel = p->path != POLYMUL_PATH_TENSOR ? 0u : p->ki.rns ? 3u : p->ki.drain ? 4u : p->ki.tiled ? 2u : 1u;
+  info->tensor_kernel = p->path != POLYMUL_PATH_TENSOR ? 0u : tensor_kernel_code(p->ki);
+  cudaFuncAttributes fa;
+  if (p->ki.fn && cudaFuncGetAttributes(&fa, p->ki.fn) == cudaSuccess) {
+    info->kernel_regs = (uint32_t)fa.numRegs;
+    info->kernel_max_block = (uint32_t)fa.maxThreadsPerBlock;
+  }
   if (p->path == POLYMUL_PATH_TENSOR && p->ki.rns) {
     RnsCfg rc;
     if (rns_config((int)p->logn, p->rns_r, &rc)) info->tensor_groups = rc.ngrp;
@@ -578,7 +593,7 @@ extern "C" int polymul_tensor_shape(uint32_t n, uint64_t qmax, uint32_t flags, p
     if (k.tiled) {
       TiledCfg tc;
       tiled_config_of(k, logn, (int)info->digits_a, L, &tc);
-      info->kernel = k.drain ? 4 : 2;
+      info->kernel = tensor_kernel_code(k);
       info->shifts = tc.shifts;
       info->slices = tc.bpg;
       info->groups = tc.ngrp;
@@ -714,7 +729,8 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     const void* tpc = p->ki.drain && p->d_tpc8 ? p->d_tpc8 : p->d_tpc;
     TensorTiledArgs args{(const uint32_t*)xa, (const uint32_t*)xb, (uint32_t*)c, (const TensorPrime*)tpc,
                          tunits, p->k, p->cyclic ? 0u : 0x80008000u, p->logn, (uint32_t)ds.wb,
-                         tc.bpg, tc.ngrp, tc.kc, tc.a_win, tc.bt_off, tc.tmem_cols, ctr, p->d_err};
+                         tc.bpg, tc.ngrp, tc.kc, tc.a_win, tc.bt_off, tc.tmem_cols, ctr, p->d_err, nullptr,
+                         tc.stage_bytes};
     void* argv[] = {&args};
     const int tgrid = (int)std::min<uint64_t>(tunits, (uint64_t)p->grid_cap);
     PM_CUDA(cudaLaunchKernel(p->ki.fn, tgrid, p->ki.block, argv, p->ki.smem, st));

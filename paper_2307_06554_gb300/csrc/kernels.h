@@ -20,6 +20,7 @@ struct KernelInfo {
   int seq = 0;               // NTT: 1 = one operand in registers at a time
   int tiled = 0;             // tensor path: 1 for k_toeplitz_tiled (output groups, K chunks)
   int drain = 0;             // tensor path: tiled kernel draining each K chunk (8-bit digits at any n)
+  int ws = 0;                // tensor path: the drained kernel's warp-specialised pipeline (k_toeplitz_ws)
   int wb = 0, digits = 0;    // tensor path: the digit width and count a kernel fixes itself (0: the plan's)
   int rns = 0;               // tensor path: 1 for k_toeplitz_rns (residues of small moduli)
 };

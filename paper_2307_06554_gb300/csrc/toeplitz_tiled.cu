@@ -40,6 +40,7 @@
 #include "tcgen05.cuh"
 #include "toeplitz_common.cuh"
 #include "toeplitz_tiled.h"
+#include "toeplitz_tiled.cuh"
 
 namespace pm {
 
@@ -49,77 +50,6 @@ constexpr int kTiledSmemCap = 110 * 1024;  // two CTAs per SM
 constexpr int kTiledTmemCap = 256;         // tensor-memory columns per CTA
 }  // namespace
 
-
-// balanced w-bit digits of the centred representative of v mod q (v < q <
-// 2^31); returns what the L digits leave over (0 whenever L digits cover
-// (-q/2, q/2], as the host chooses L; nonzero only for a single-digit
-// operand that does not fit one digit)
-template <int L>
-__device__ __forceinline__ int32_t centred_digits(uint32_t v, uint32_t q, int wb, int (&d)[L]) {
-  const int32_t half = 1 << (wb - 1), mask = (1 << wb) - 1;
-  int32_t x = v > (q >> 1) ? (int32_t)(v - q) : (int32_t)v;
-#pragma unroll
-  for (int s = 0; s < L; ++s) {
-    const int32_t t = ((x + half) & mask) - half;
-    x = (x - t) >> wb;
-    d[s] = t;
-  }
-  return x;
-}
-
-// 8 consecutive coefficients (16-byte aligned) -> per digit, 8 bf16 packed
-// in a uint4; false if a coefficient does not fit the L digits
-template <int L>
-__device__ __forceinline__ bool digits8(const uint32_t* src, uint32_t q, int wb, uint4 (&out)[L]) {
-  const uint4 v0 = *reinterpret_cast<const uint4*>(src);
-  const uint4 v1 = *reinterpret_cast<const uint4*>(src + 4);
-  const uint32_t xv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-  int d[8][L];
-  int32_t rest = 0;
-#pragma unroll
-  for (int e = 0; e < 8; ++e) rest |= centred_digits<L>(xv[e], q, wb, d[e]);
-#pragma unroll
-  for (int s = 0; s < L; ++s)
-    out[s] = make_uint4(bf16x2_of(d[0][s], d[1][s]), bf16x2_of(d[2][s], d[3][s]), bf16x2_of(d[4][s], d[5][s]),
-                        bf16x2_of(d[6][s], d[7][s]));
-  return rest == 0;
-}
-
-// MMA N and the B layout for LB digits of b and S shifted copies of it
-template <int LB, int S>
-struct TTShape {
-  static constexpr int NB = (8 * LB * S + 15) / 16 * 16;  // 8 rows per digit and shift, padded
-  static constexpr int NG = NB / 8;                       // 8-row groups of B
-  // core matrices adjacent along K are BT_PITCH bytes apart (16 bytes more
-  // than the N-groups need: consecutive threads' 16-byte stores, one K-block
-  // each, fall in distinct banks)
-  static constexpr int BT_PITCH = NG * 128 + 16;
-};
-
-// Adds shift sh's accumulators of this thread's tensor-memory lane (one row
-// of the output block, 8 outputs) to acc: sum over digit pairs (s, g) of the
-// exact fp32 partial sum times 2^(w (s + g)) mod q.
-template <int LA, int LB, int S>
-__device__ __forceinline__ void drain_shift(uint32_t lane_base, int sh, const uint32_t* pw, int64_t (&acc)[8]) {
-  using TS = TTShape<LB, S>;
-#pragma unroll
-  for (int s = 0; s < LA; ++s) {
-#pragma unroll
-    for (int c16 = 0; c16 < TS::NB / 16; ++c16) {
-      if (16 * c16 + 16 <= 8 * sh * LB || 16 * c16 >= 8 * (sh + 1) * LB) continue;
-      uint32_t r[16];
-      // warp-collective: every lane loads
-      tmem_ld16(lane_base + s * TS::NB + 16 * c16, r);
-      tmem_wait_ld();
-#pragma unroll
-      for (int cc = 0; cc < 16; ++cc) {
-        const int col = 16 * c16 + cc, g = col / 8, v = col % 8;
-        if (g >= sh * LB && g < (sh + 1) * LB)
-          acc[v] += (int64_t)__float2int_rn(__uint_as_float(r[cc])) * (int64_t)pw[s + g - sh * LB];
-      }
-    }
-  }
-}
 
 // DRAIN: each K chunk's accumulators are drained into 64-bit integer sums in
 // registers after the chunk (and restart at zero), so only a chunk's partial
@@ -263,6 +193,8 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
         const uint32_t xa0 = smem_u32(Xw), bt0 = smem_u32(Bt);
         const uint64_t bd0 = smem_desc(bt0, TS::BT_PITCH, 128);
         constexpr uint64_t BSTEP = (2 * TS::BT_PITCH) >> 4;  // two K-blocks per MMA (K = 16)
+        // one chain at a time (measured faster here than K steps outermost,
+        // with two CTAs of an SM interleaving their chains)
 #pragma unroll 1
         for (uint32_t bl = 0; bl < bpg; ++bl) {
 #pragma unroll 1

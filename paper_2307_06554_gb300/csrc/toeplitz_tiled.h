@@ -19,6 +19,7 @@ namespace pm {
 struct TiledCfg {
   uint32_t bpg = 0, shifts = 0, nb = 0, b_pitch = 0, ngrp = 0, kc = 0, a_win = 0, bt_off = 0, tmem_cols = 0;
   int smem = 0;
+  uint32_t stage_bytes = 0;  // warp-specialised kernel: bytes per shared-memory stage (two stages)
 };
 
 struct TensorTiledArgs {
@@ -37,6 +38,7 @@ struct TensorTiledArgs {
   // c with tp[r % k]; else row r at rows[r].offset with tp[rows[r].prime]
   // (the rows of one degree class of an uneven list)
   const RaggedUnit* rows;
+  uint32_t stage_bytes;  // warp-specialised kernel: shared-memory stage size (0 otherwise)
 };
 
 // The tiling for degree 2^logn with la digits of a and lb of b (false if
@@ -56,5 +58,13 @@ bool lookup_toeplitz_tiled(int logn, int la, int lb, KernelInfo* ki);
 // allows, with la == 1 up to 4 A slices.  ki->wb = 8, ki->digits = lb.
 bool toeplitz_tiled_config_drain(int logn, int la, int lb, TiledCfg* cfg);
 bool lookup_toeplitz_tiled_drain(int logn, int la, int lb, KernelInfo* ki);
+
+// The drained kernel as a warp-specialised pipeline (k_toeplitz_ws, one CTA
+// per SM): two shared-memory stages and two tensor-memory buffers, so that
+// builder warps fill one stage and drainer warps empty one buffer while the
+// MMAs of the other run.  Same digits, shifts and slices as the drained
+// kernel; K chunks as large as two stages allow.  ki->ws = 1, ki->drain = 1.
+bool toeplitz_ws_config(int logn, int la, int lb, TiledCfg* cfg);
+bool lookup_toeplitz_ws(int logn, int la, int lb, KernelInfo* ki);
 
 }  // namespace pm

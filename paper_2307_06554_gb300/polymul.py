@@ -51,7 +51,7 @@ class polymul_plan_info(ctypes.Structure):
                 ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
                  "digit_bits", "digits", "radix_bits", "candidates", "tuned", "tuned_batch",
                  "launch_flags", "ntt_mode", "regs", "cyclic", "tensor_groups", "rns_moduli",
-                 "exchange_pad", "one_operand", "tensor_kernel")]
+                 "exchange_pad", "one_operand", "tensor_kernel", "kernel_regs", "kernel_max_block")]
 
 
 class polymul_tensor_shape_info(ctypes.Structure):

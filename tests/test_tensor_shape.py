@@ -76,7 +76,7 @@ def test_digit_boundaries(pm, n, q, digits):
 def test_more_than_five_digits_go_to_the_drained_kernel(pm):
     info = pm.polymul_tensor_shape(8192, 1073479681)  # needs six digits of 6 bits
     assert _digits(8192, 1073479681)[1] == 6
-    assert (info["kernel"], info["digit_bits"], info["digits_b"], info["candidates"]) == (4, 8, 4, 2)
+    assert (info["kernel"], info["digit_bits"], info["digits_b"], info["candidates"]) == (4, 8, 4, 3)
     # a 32-bit word modulus above 2^31: the RNS kernel alone
     info = pm.polymul_tensor_shape(8192, 2147483659)
     assert info["kernel"] == 3 and info["rns_moduli"] == len(pm.polymul_tensor_rns_base(8192, 2147483659))
@@ -126,7 +126,7 @@ def test_kernel_choice(pm):
     i = pm.polymul_tensor_shape(4096, (1 << 30) - 35)
     assert (i["kernel"], i["digits_a"], i["digits_b"], i["shifts"], i["groups"]) == (4, 4, 4, 2, 2)
     i = pm.polymul_tensor_shape(16384, (1 << 31) - 1)   # six 6-bit digits undrained: drained only
-    assert (i["kernel"], i["digits_b"], i["candidates"]) == (4, 4, 1)
+    assert (i["kernel"], i["digits_b"], i["candidates"]) == (4, 4, 2)
     i = pm.polymul_tensor_shape(4096, (1 << 59) - 55)
     assert (i["kernel"], i["rns_moduli"], i["shifts"], i["groups"]) == (3, 21, 2, 2)
     for n, q in ((8192, (1 << 59) - 55), (32768, 12289), (16, 12289), (32768, (1 << 30) - 35)):

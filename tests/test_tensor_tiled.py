@@ -214,7 +214,7 @@ def test_tiled_candidate_matches_whole_product_kernel(pm, n):
     with pm.Plan(n, q_list, path=pm.PATH_TENSOR) as plan:
         info = plan.info
         codes = [plan.select(i)["tensor_kernel"] for i in range(info["candidates"])]
-        assert codes == ([2, 1, 4, 3] if n == 2048 else [1, 2, 3]), codes
+        assert codes == ([2, 1, 4, 5, 3] if n == 2048 else [1, 2, 5, 3]), codes
         outs = {}
         for code in codes:
             if code != 3:
@@ -366,7 +366,7 @@ def test_digit_capacity_boundary(pm, n, q, digits):
         if digits:
             assert _select(plan, next(c for c in codes if c in (1, 2)))["digits"] == digits
         else:
-            assert codes == [4, 3], codes
+            assert codes == [4, 5, 3], codes
         gots = []
         for code in codes:
             if code != 3 or not digits:
@@ -429,3 +429,80 @@ def test_drained_matches_undrained_on_many_units(pm):
         undrained = run_plan_batch(plan, a, b)
     assert np.array_equal(drained, undrained)
     _check_sampled(drained[:4], a[:4], b[:4], q_list, False, rng, count=8)
+
+
+# ---- the drained kernel as a warp-specialised pipeline (one CTA per SM) ----
+
+@pytest.mark.parametrize("n,bits,ternary,cyclic", [(256, 13, False, False), (1024, 14, False, True), (2048, 30, False, False),
+                                                   (4096, 30, False, False), (4096, 30, True, False),
+                                                   (4096, 31, False, True), (2048, 22, True, True)])
+def test_pipelined_against_oracle(pm, n, bits, ternary, cyclic):
+    rng = np.random.default_rng(13 * n + bits + ternary)
+    q_list = [12289] if bits == 14 else wl.draw_primes(rng, 2, bits, bits, 1)
+    batch = 300 if n <= 1024 else 7  # more units than CTAs: several per CTA, walked statically
+    a = wl.uniform_coeffs(rng, batch, q_list, n, np.uint32)
+    b = (wl.ternary_coeffs if ternary else wl.uniform_coeffs)(rng, batch, q_list, n, np.uint32)
+    flags = (pm.FLAG_TERNARY_B if ternary else 0) | (pm.FLAG_CYCLIC if cyclic else 0)
+    with pm.Plan(n, q_list, path=pm.PATH_TENSOR, flags=flags) as plan:
+        info = _select(plan, 5)
+        assert info["digit_bits"] == 8 and info["block"] == 512
+        got = run_plan_batch(plan, a, b)
+        pm.polymul_plan_status(plan.handle)
+    if n <= 1024:
+        assert_equal_residues(got, native.polymul_batch(a, b, q_list, cyclic=cyclic), "pipelined n=%d" % n)
+    else:
+        assert_equal_residues(got[:3], native.polymul_batch(a[:3], b[:3], q_list, cyclic=cyclic), "pipelined n=%d" % n)
+
+
+@pytest.mark.parametrize("n,bits,ternary", [(8192, 30, False), (16384, 31, True), (16384, 30, False)])
+def test_pipelined_large_degrees_sampled(pm, n, bits, ternary):
+    rng = np.random.default_rng(n + 7 * bits + ternary)
+    q_list = wl.draw_primes(rng, 2, bits, bits, 1)
+    a = wl.uniform_coeffs(rng, 3, q_list, n, np.uint32)
+    b = (wl.ternary_coeffs if ternary else wl.uniform_coeffs)(rng, 3, q_list, n, np.uint32)
+    with pm.Plan(n, q_list, path=pm.PATH_TENSOR, flags=pm.FLAG_TERNARY_B if ternary else 0) as plan:
+        _select(plan, 5)
+        got = run_plan_batch(plan, a, b)
+        pm.polymul_plan_status(plan.handle)
+    _check_sampled(got, a, b, q_list, False, rng)
+
+
+def test_pipelined_matches_drained_and_relaunches(pm):
+    """Fewer units than SMs, then many: the pipeline's static walk, its
+    mbarrier phases across launches and the hand-off between its drainer
+    sets give the drained kernel's coefficients bit for bit."""
+    n = 4096
+    rng = np.random.default_rng(4097)
+    q_list = wl.draw_primes(rng, 3, 29, 30, 13)
+    for batch in (5, 97):
+        a = wl.uniform_coeffs(rng, batch, q_list, n, np.uint32)
+        b = wl.uniform_coeffs(rng, batch, q_list, n, np.uint32)
+        with _tensor_plan(pm, n, q_list) as plan:
+            _select(plan, 4)
+            want = run_plan_batch(plan, a, b)
+            _select(plan, 5)
+            got = run_plan_batch(plan, a, b)
+            again = run_plan_batch(plan, a, b)
+            pm.polymul_plan_status(plan.handle)
+        assert np.array_equal(got, want) and np.array_equal(again, want), batch
+    _check_sampled(want[:2], a[:2], b[:2], q_list, False, rng, count=8)
+
+
+def test_pipelined_domain_error_is_reported(pm):
+    """A b coefficient outside one digit under the ternary flag, on the
+    pipelined kernel: EDOMAIN, then exact again."""
+    n, q = 4096, 1073479681
+    rng = np.random.default_rng(61)
+    a = wl.uniform_coeffs(rng, 3, [q], n, np.uint32)
+    bad = wl.ternary_coeffs(rng, 3, [q], n, np.uint32)
+    bad[2, 0, 4000] = 1000
+    good = wl.ternary_coeffs(rng, 3, [q], n, np.uint32)
+    with pm.Plan(n, [q], path=pm.PATH_TENSOR, flags=pm.FLAG_TERNARY_B) as plan:
+        _select(plan, 5)
+        run_plan_batch(plan, a, bad)
+        with pytest.raises(pm.PolymulError) as ei:
+            pm.polymul_plan_status(plan.handle)
+        assert ei.value.code == pm.POLYMUL_EDOMAIN
+        got = run_plan_batch(plan, a, good)
+        pm.polymul_plan_status(plan.handle)
+    assert_equal_residues(got[:1], native.polymul_batch(a[:1], good[:1], [q]), "after the domain error")
