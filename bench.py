@@ -135,7 +135,7 @@ def _host_cores():
 # one stream with operands rotated over buffer sets larger than L2 (so DRAM
 # counters mean something), and the plan's device status is checked.  Device
 # memory stays below 1 GB.
-def _case_homogeneous(n, q_list, batch, path, launches, seed=7, flags=0):
+def _case_homogeneous(n, q_list, batch, path, launches, seed=7, flags=0, tensor_kernel=0):
     import torch
     from paper_2307_06554_gb300 import polymul, workloads as wl
     dev = torch.device("cuda", 0)
@@ -149,6 +149,9 @@ def _case_homogeneous(n, q_list, batch, path, launches, seed=7, flags=0):
     sets = [(ta.clone(), tb.clone(), torch.empty_like(ta)) for _ in range(nsets)]
     stream = torch.cuda.Stream(dev)
     with polymul.Plan(n, q_list, path=path, flags=flags) as plan:
+        if tensor_kernel:  # a given tensor kernel (polymul_tensor_shape_info.kernel code) instead of the default
+            codes = [plan.select(i)["tensor_kernel"] for i in range(plan.info["candidates"])]
+            plan.select(codes.index(tensor_kernel))
         for i in range(launches):
             x, y, z = sets[i % nsets]
             polymul.polymul_batch(plan.handle, x, y, z, batch, stream.cuda_stream)
@@ -334,6 +337,9 @@ def _case(name, launches):
         return _case_homogeneous(1024, [12289], 4096, polymul.PATH_TENSOR, launches)
     if name == "tensor_rns4096":
         return _case_homogeneous(4096, wl.draw_primes(rng, 8, 30, 30, 13), 64, polymul.PATH_TENSOR, launches)
+    if name == "tensor_rns4096_pipelined":
+        return _case_homogeneous(4096, wl.draw_primes(rng, 8, 30, 30, 13), 64, polymul.PATH_TENSOR, launches,
+                                 tensor_kernel=5)
     if name == "tensor_u64_4096":
         return _case_homogeneous(4096, wl.draw_primes(rng, 2, 59, 59, 13), 64, polymul.PATH_TENSOR, launches)
     if name == "n16384":
@@ -355,6 +361,7 @@ CASES = {
     "ntt_ring1024_overlap": "the same with POLYMUL_FLAG_OVERLAP",
     "tensor_ring1024": "the same batch through the Toeplitz tensor-core path",
     "tensor_rns4096": "n = 4096, 8 primes of 30 bits, 64 products on the tiled tensor kernel",
+    "tensor_rns4096_pipelined": "the same on the warp-specialised pipeline form of the drained kernel",
     "tensor_u64_4096": "n = 4096, 2 primes of 59 bits, 64 products on the residue-number-system tensor kernel",
     "n16384": "n = 16384, one 30-bit prime, 1024 products (one CTA per product)",
     "cluster_32768": "n = 32768, one 30-bit prime, 256 products (thread-block clusters)",
