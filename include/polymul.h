@@ -505,6 +505,16 @@ int polymul_server_create(const uint64_t *pool, uint32_t pool_size, uint32_t n_m
                           uint64_t device_bytes, uint32_t lanes, polymul_server **out);
 /* Queue one request (asynchronous); *ticket identifies it. */
 int polymul_server_submit(polymul_server *srv, const polymul_request *req, uint64_t *ticket);
+/* The path of requests submitted after the call: POLYMUL_PATH_NTT (the
+ * default) or POLYMUL_PATH_TENSOR -- the matrix form (Sec. 2.2) as the
+ * 64-bit-word digit kernel: 5 .. 8 balanced 8-bit digits of each centred
+ * residue per operand (as many as the pool's largest prime needs, at least
+ * five), the exact fp32 sums of each K chunk of at most 1024 drained into
+ * 64-bit modular sums, for degrees 2^10 .. n_max (smaller degrees stay on
+ * the NTT path).  The first switch to the tensor path sets up its kernels
+ * and the pool's constants (synchronous).  Errors: EINVAL (path), ENOTSUP
+ * (n_max below 1024), ENOMEM, ECUDA. */
+int polymul_server_set_path(polymul_server *srv, uint32_t path);
 /* *done = 1 once the result is in req->c (the ticket is then released).  A
  * request that failed releases its ticket and returns its error: ETIMEOUT
  * when a bounded device wait of its kernel expired (c is invalid), ECUDA for

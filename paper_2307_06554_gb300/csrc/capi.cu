@@ -24,6 +24,7 @@
 #include "polymul_types.h"
 #include "toeplitz_rns.h"
 #include "toeplitz_tiled.h"
+#include "toeplitz_u64.h"
 
 using namespace pm;
 
@@ -151,13 +152,14 @@ DigitShape digit_shape(const polymul_plan* p, const KernelInfo& k) {
 }
 
 bool tiled_config_of(const KernelInfo& k, int logn, int la, int lb, TiledCfg* cfg) {
+  if (k.u64) return toeplitz_u64_config(logn, lb, cfg);
   if (k.ws) return toeplitz_ws_config(logn, la, lb, cfg);
   return k.drain ? toeplitz_tiled_config_drain(logn, la, lb, cfg) : toeplitz_tiled_config(logn, la, lb, cfg);
 }
 
 // tensor kernel code reported by polymul_plan_info and polymul_tensor_shape
 uint32_t tensor_kernel_code(const KernelInfo& k) {
-  return k.rns ? 3u : k.ws ? 5u : k.drain ? 4u : k.tiled ? 2u : 1u;
+  return k.rns ? 3u : k.u64 ? 6u : k.ws ? 5u : k.drain ? 4u : k.tiled ? 2u : 1u;
 }
 
 // The tensor path's kernels for degree n and moduli up to qmax, the default
@@ -214,6 +216,19 @@ bool choose_tensor(uint32_t n, uint64_t qmax, uint32_t elem, bool ternary_b, Ten
     tc->kernels.push_back(krns);
     tc->rns_moduli = mods;
   }
+  // 64-bit words: 5 .. 8 drained 8-bit digits per operand at n = 2^10 ..
+  // 2^16; first up to n = 2048 and where the RNS kernel has no base (above
+  // n = 4096 for 59-bit moduli), after it otherwise (measured with two
+  // 59-bit primes: 41 vs 94 us for 64 products at n = 1024, 405 vs 357 us
+  // at 4096)
+  KernelInfo ku64;
+  const int l64 = elem == 8 && !ternary_b ? std::max(5, u64_digits(qmax)) : 0;
+  if (l64 && l64 <= 8 && lookup_toeplitz_u64(logn, l64, &ku64)) {
+    if (logn <= 11 || tc->kernels.empty())
+      tc->kernels.insert(tc->kernels.begin(), ku64);
+    else
+      tc->kernels.push_back(ku64);
+  }
   return !tc->kernels.empty();
 }
 
@@ -231,7 +246,27 @@ int upload_rns_tables(polymul_plan* p, const std::vector<uint32_t>& moduli) {
   return POLYMUL_OK;
 }
 
+// per-prime constants of the 64-bit-word digit kernel
+int upload_tensor_tables64(polymul_plan* p) {
+  if (p->elem != 8 || p->d_tp64) return POLYMUL_OK;
+  std::vector<TensorPrime64> tp(p->k);
+  for (uint32_t j = 0; j < p->k; ++j) {
+    memset(&tp[j], 0, sizeof tp[j]);
+    const uint64_t q = p->q[j];
+    tp[j].q = q;
+    tp[j].bias = ((1ull << 28) + q - 1) / q * q;
+    for (int e = 0; e < 15; ++e) {
+      tp[j].pw[e] = pm::host::powmod(2, 8ull * e, q);
+      tp[j].pwp[e] = (uint64_t)(((pm::host::u128)tp[j].pw[e] << 64) / q);
+    }
+  }
+  PM_CUDA(cudaMalloc(&p->d_tp64, tp.size() * sizeof(TensorPrime64)));
+  PM_CUDA(cudaMemcpy(p->d_tp64, tp.data(), tp.size() * sizeof(TensorPrime64), cudaMemcpyHostToDevice));
+  return POLYMUL_OK;
+}
+
 int upload_tensor_tables(polymul_plan* p) {
+  if (p->elem == 8) return upload_tensor_tables64(p);
   if (p->elem != 4 || p->d_tpc) return POLYMUL_OK;  // digit kernels only (32-bit words); once
   auto upload = [&](int wb, void** dst) -> int {
     std::vector<TensorPrime> tp(p->k);
@@ -497,6 +532,7 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_pc);
   cudaFree(p->d_tpc);
   cudaFree(p->d_tpc8);
+  cudaFree(p->d_tp64);
   cudaFree(p->d_rns_base);
   cudaFree(p->d_rns_primes);
   for (int s = 0; s < kCounterSlots; ++s) cudaFree(p->d_rns_scr[s]);
@@ -715,6 +751,16 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     TensorRnsArgs args{planes, planes + plane, c, (const RnsBase*)p->d_rns_base, (const RnsPrime*)p->d_rns_primes, tunits, p->k,
                        p->cyclic ? 0u : 0x80008000u, p->logn, rc.shifts, rc.nb, rc.b_pitch, rc.ngrp, rc.kc, rc.a_win,
                        rc.bt_off, rc.buf_bytes, rc.tmem_cols, ctr, p->d_err};
+    void* argv[] = {&args};
+    const int tgrid = (int)std::min<uint64_t>(tunits, (uint64_t)p->grid_cap);
+    PM_CUDA(cudaLaunchKernel(p->ki.fn, tgrid, p->ki.block, argv, p->ki.smem, st));
+  } else if (p->path == POLYMUL_PATH_TENSOR && p->ki.u64) {
+    TiledCfg tc;
+    if (!toeplitz_u64_config((int)p->logn, p->ki.digits, &tc)) return fail(POLYMUL_ENOTSUP, "tensor tiling (64-bit)");
+    const uint64_t tunits = units * tc.ngrp;
+    TensorU64Args args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, (const TensorPrime64*)p->d_tp64, nullptr,
+                       tunits, p->k, p->cyclic ? 0u : 0x80008000u, p->logn, tc.ngrp, tc.kc, tc.a_win, tc.bt_off,
+                       tc.tmem_cols, ctr, p->d_err};
     void* argv[] = {&args};
     const int tgrid = (int)std::min<uint64_t>(tunits, (uint64_t)p->grid_cap);
     PM_CUDA(cudaLaunchKernel(p->ki.fn, tgrid, p->ki.block, argv, p->ki.smem, st));

@@ -21,6 +21,7 @@ struct KernelInfo {
   int tiled = 0;             // tensor path: 1 for k_toeplitz_tiled (output groups, K chunks)
   int drain = 0;             // tensor path: tiled kernel draining each K chunk (8-bit digits at any n)
   int ws = 0;                // tensor path: the drained kernel's warp-specialised pipeline (k_toeplitz_ws)
+  int u64 = 0;               // tensor path: the 64-bit-word digit kernel (k_toeplitz_u64)
   int wb = 0, digits = 0;    // tensor path: the digit width and count a kernel fixes itself (0: the plan's)
   int rns = 0;               // tensor path: 1 for k_toeplitz_rns (residues of small moduli)
 };

@@ -46,7 +46,8 @@ struct polymul_plan {
   bool tuned = false;
   uint64_t tuned_batch = 0;  // batch bucket of the tuned choice
   void* d_tpc = nullptr;  // tensor-path constants
-  void* d_tpc8 = nullptr;  // the same for 8-bit digits (drained tiled kernel), when the plan's width is less
+  void* d_tpc8 = nullptr;
+  void* d_tp64 = nullptr;  // TensorPrime64 per prime (64-bit-word digit kernel)  // the same for 8-bit digits (drained tiled kernel), when the plan's width is less
   // tensor path, residue number system of small moduli: the base and its
   // per-prime constants (when the RNS kernel is a candidate)
   uint32_t rns_r = 0;

@@ -35,6 +35,7 @@
 
 #include "../../include/polymul.h"
 #include "host_math.h"
+#include "toeplitz_u64.h"
 #include "kernels.h"
 #include "trace.h"
 #include "plan.h"
@@ -64,6 +65,7 @@ struct ServeReq {
   size_t off = 0, bytes = 0;
   int lane = 0;
   int slot = -1;  // page-locked word that receives the lane's error word after the kernel
+  bool tensor = false;  // runs on the tensor path (decided at submission)
   cudaEvent_t ev = nullptr;     // the result is in host memory (end of the copy-out stage)
   cudaEvent_t ev_in = nullptr;  // operands are on the device (end of the copy-in stage)
   cudaEvent_t ev_k = nullptr;   // the kernel is done
@@ -79,6 +81,16 @@ struct polymul_server {
   void* d_pc = nullptr;  // PrimeConst<uint64_t>[pool][17]
   KernelInfo ki[kServeMaxLog + 1];
   int grid_cap[kServeMaxLog + 1] = {};
+  // the tensor path (polymul_server_set_path): the 64-bit-word digit kernel
+  // per degree 2^10 .. n_max and the pool's digit-weight constants, set up
+  // once by the first switch; `tensor` is read by the server thread at issue
+  std::atomic<int> tensor{0};
+  std::mutex tensor_mu;  // serialises the set-up
+  bool tensor_ready = false;
+  KernelInfo tki[kServeMaxLog + 1];
+  TiledCfg tcfg[kServeMaxLog + 1];
+  int tgrid_cap[kServeMaxLog + 1] = {};
+  void* d_tp64 = nullptr;
   int device = 0, num_sms = 0;
   int nlanes = 0;
   // each lane is a three-stage pipeline: copies in, kernels, copies out, on
@@ -169,6 +181,24 @@ size_t request_bytes(uint32_t n, uint32_t k) {
   return 3 * ((row + kArenaAlign - 1) / kArenaAlign * kArenaAlign) + map;
 }
 
+// after a request's kernel: its error word, the copy out and the
+// completion event (server thread)
+cudaError_t finish_issue(polymul_server* s, ServeReq* r, uint64_t* dc, size_t row, int* lane_err) {
+  cudaStream_t st = s->lanes[r->lane], st_out = s->lanes_out[r->lane];
+  cudaError_t e;
+  if (!s->d_err_mapped) {
+    // the lane's error word belongs to this request until the lane's next
+    // kernel: bring it back, then clear it, in the kernel stage
+    if ((e = cudaMemcpyAsync(s->h_err + r->slot, lane_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemsetAsync(lane_err, 0, sizeof(int), st)) != cudaSuccess) return e;
+  }
+  if ((e = cudaEventRecord(r->ev_k, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st_out, r->ev_k, 0)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(r->hc, dc, row, cudaMemcpyDeviceToHost, st_out)) != cudaSuccess) return e;
+  return cudaEventRecord(r->ev, st_out);
+}
+
 // issue copy-in, kernel, copy-out and the completion event (server thread)
 cudaError_t issue(polymul_server* s, ServeReq* r) {
   const size_t row = (size_t)r->k * r->n * 8;
@@ -192,11 +222,29 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
   if ((e = cudaMemcpyAsync(db, r->hb, row, cudaMemcpyHostToDevice, st_in)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(r->ev_in, st_in)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(st, r->ev_in, 0)) != cudaSuccess) return e;
+  int* lane_err = s->d_err + r->lane;
+  int* err = s->d_err_mapped ? s->d_err_mapped + r->slot : lane_err;
+  if (r->tensor) {
+    // the tensor path: the 64-bit-word digit kernel over the request's k
+    // rows, its prime map in the arena
+    if (inline_map) {
+      uint32_t* hmap = s->h_map + (size_t)r->slot * s->pool.size();
+      std::copy(r->primes.begin(), r->primes.end(), hmap);
+      if ((e = cudaMemcpyAsync(dmap, hmap, r->k * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    }
+    const TiledCfg& tc = s->tcfg[r->logn];
+    const KernelInfo& tk = s->tki[r->logn];
+    const uint64_t tunits = (uint64_t)r->k * tc.ngrp;
+    TensorU64Args targs{da, db, dc, (const TensorPrime64*)s->d_tp64, dmap, tunits, r->k, 0x80008000u, r->logn,
+                        tc.ngrp, tc.kc, tc.a_win, tc.bt_off, tc.tmem_cols, s->d_ctr + 2 * r->lane, err};
+    void* targv[] = {&targs};
+    const int tgrid = (int)std::min<uint64_t>(tunits, (uint64_t)s->tgrid_cap[r->logn]);
+    if ((e = cudaLaunchKernel(tk.fn, tgrid, tk.block, targv, tk.smem, st)) != cudaSuccess) return e;
+    return finish_issue(s, r, dc, row, lane_err);
+  }
   const KernelInfo& ki = s->ki[r->logn];
   uint32_t tx_pad = 0, polls = 0;
   if (ki.cluster == 0) take_injected_wait(&tx_pad, &polls);
-  int* lane_err = s->d_err + r->lane;
-  int* err = s->d_err_mapped ? s->d_err_mapped + r->slot : lane_err;
   NttBatchArgs<uint64_t> args{da,      db,       dc,      s->d_twf, s->d_twi, (const PrimeConst<uint64_t>*)s->d_pc,
                               r->k,    r->k,     s->d_ctr + 2 * r->lane, err, nullptr, inline_map ? nullptr : dmap,
                               s->nmax, (uint32_t)(kServeMaxLog + 1), r->logn, 0u, tx_pad, polls};
@@ -225,17 +273,7 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
     const int grid = std::min<int>((int)((r->k + ki.units_per_cta - 1) / ki.units_per_cta), s->grid_cap[r->logn]);
     if ((e = cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st)) != cudaSuccess) return e;
   }
-  if (!s->d_err_mapped) {
-    // the lane's error word belongs to this request until the lane's next
-    // kernel: bring it back, then clear it, in the kernel stage
-    if ((e = cudaMemcpyAsync(s->h_err + r->slot, lane_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-      return e;
-    if ((e = cudaMemsetAsync(lane_err, 0, sizeof(int), st)) != cudaSuccess) return e;
-  }
-  if ((e = cudaEventRecord(r->ev_k, st)) != cudaSuccess) return e;
-  if ((e = cudaStreamWaitEvent(st_out, r->ev_k, 0)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(r->hc, dc, row, cudaMemcpyDeviceToHost, st_out)) != cudaSuccess) return e;
-  return cudaEventRecord(r->ev, st_out);
+  return finish_issue(s, r, dc, row, lane_err);
 }
 
 void take_events(polymul_server* s, ServeReq* r) {
@@ -444,6 +482,7 @@ extern "C" void polymul_server_destroy(polymul_server* s) {
   cudaFree(s->d_ctr);
   cudaFree(s->d_err);
   cudaFree(s->d_arena);
+  cudaFree(s->d_tp64);
   if (s->h_err) cudaFreeHost(s->h_err);
   if (s->h_map) cudaFreeHost(s->h_map);
   delete s;
@@ -579,6 +618,7 @@ extern "C" int polymul_server_submit(polymul_server* s, const polymul_request* q
   r->n = q->n;
   r->k = q->k;
   r->logn = (uint32_t)__builtin_ctz(q->n);
+  r->tensor = s->tensor.load(std::memory_order_acquire) != 0 && r->logn >= 10 && s->tgrid_cap[r->logn] > 0;
   r->primes.assign(q->prime_idx, q->prime_idx + q->k);
   r->ha = q->a;
   r->hb = q->b;
@@ -615,6 +655,58 @@ static int request_failure(polymul_server* s, int code, uint64_t ticket) {
     return fail(code, "request %llu: a bounded device wait of its kernel expired; its result is invalid",
                 (unsigned long long)ticket);
   return fail(code, "request %llu failed: %s", (unsigned long long)ticket, s->cuda_error_msg.c_str());
+}
+
+// Requests submitted after this call run on `path`: POLYMUL_PATH_NTT (the
+// default) or POLYMUL_PATH_TENSOR (the 64-bit-word digit kernel, Sec. 2.2
+// matrix form, for degrees 2^10 .. n_max; smaller degrees stay on the NTT
+// path).  The first switch to the tensor path sets up its kernels and the
+// pool's constants (synchronous).
+extern "C" int polymul_server_set_path(polymul_server* s, uint32_t path) {
+  clear_error();
+  if (!s) return fail(POLYMUL_EINVAL, "server is NULL");
+  if (path != POLYMUL_PATH_NTT && path != POLYMUL_PATH_TENSOR)
+    return fail(POLYMUL_EINVAL, "path=%u must be POLYMUL_PATH_NTT or POLYMUL_PATH_TENSOR", path);
+  if (path == POLYMUL_PATH_NTT) {
+    s->tensor.store(0, std::memory_order_release);
+    return POLYMUL_OK;
+  }
+  std::lock_guard<std::mutex> lk(s->tensor_mu);
+  if (!s->tensor_ready) {
+    if (s->lognmax < 10) return fail(POLYMUL_ENOTSUP, "the tensor path needs n_max >= 1024");
+    const uint64_t qmax = *std::max_element(s->pool.begin(), s->pool.end());
+    const int L = std::max(5, u64_digits(qmax));  // at least the smallest instantiated digit count
+    std::vector<TensorPrime64> tp(s->pool.size());
+    for (size_t j = 0; j < s->pool.size(); ++j) {
+      const uint64_t q = s->pool[j];
+      memset(&tp[j], 0, sizeof tp[j]);
+      tp[j].q = q;
+      tp[j].bias = ((1ull << 28) + q - 1) / q * q;
+      for (int e = 0; e < 15; ++e) {
+        tp[j].pw[e] = pm::host::powmod(2, 8ull * e, q);
+        tp[j].pwp[e] = (uint64_t)(((pm::host::u128)tp[j].pw[e] << 64) / q);
+      }
+    }
+    if (cudaMalloc(&s->d_tp64, tp.size() * sizeof(TensorPrime64)) != cudaSuccess)
+      return fail(POLYMUL_ENOMEM, "tensor constants");
+    if (cudaMemcpy(s->d_tp64, tp.data(), tp.size() * sizeof(TensorPrime64), cudaMemcpyHostToDevice) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "tensor constants");
+    for (int logn = 10; logn <= (int)s->lognmax; ++logn) {
+      KernelInfo ki;
+      if (!lookup_toeplitz_u64(logn, L, &ki) || !toeplitz_u64_config(logn, L, &s->tcfg[logn])) continue;
+      if (cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "smem attribute");
+      int per_sm = 0;
+      const int rc = tmem_kernel_per_sm(ki, s->device, &per_sm);
+      if (rc != POLYMUL_OK) return rc;
+      if (per_sm < 1) continue;
+      s->tki[logn] = ki;
+      s->tgrid_cap[logn] = per_sm * s->num_sms;
+    }
+    s->tensor_ready = true;
+  }
+  s->tensor.store(1, std::memory_order_release);
+  return POLYMUL_OK;
 }
 
 extern "C" int polymul_server_poll(polymul_server* s, uint64_t ticket, int* done) {

@@ -144,6 +144,8 @@ def _load():
     lib.polymul_server_submit.argtypes = [vp, ctypes.POINTER(polymul_request), ctypes.POINTER(u64)]
     lib.polymul_server_submit.restype = i32
     lib.polymul_server_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int)]
+    lib.polymul_server_set_path.restype = ctypes.c_int
+    lib.polymul_server_set_path.argtypes = [vp, u32]
     lib.polymul_server_poll.restype = i32
     lib.polymul_server_wait.argtypes = [vp, u64, ctypes.c_double]
     lib.polymul_server_wait.restype = i32
@@ -489,6 +491,10 @@ class Server:
         t = ctypes.c_uint64()
         _check(_lib.polymul_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
         return t.value
+
+    def set_path(self, path: int) -> None:
+        """Path of the requests submitted from now on (PATH_NTT or PATH_TENSOR)."""
+        _check(_lib.polymul_server_set_path(self.handle, path))
 
     def poll(self, ticket: int) -> bool:
         d = ctypes.c_int()

@@ -57,14 +57,18 @@ def test_rns_u32_against_oracle(pm, n, bits):
 
 @pytest.mark.parametrize("n,bits,k", [(64, 59, 2), (256, 62, 1), (1024, 59, 2), (2048, 59, 1), (4096, 59, 2)])
 def test_rns_u64_against_oracle(pm, n, bits, k):
-    """64-bit words: the RNS kernel is the tensor path."""
+    """64-bit words: the RNS kernel (the tensor path's only kernel below
+    n = 1024; beside the 64-bit digit kernel from 1024 on, first there from
+    n = 4096)."""
     rng = np.random.default_rng(7 * n + bits)
     q_list = wl.draw_primes(rng, k, bits, bits, 1)
     batch = {64: 21, 256: 11, 1024: 5, 2048: 3, 4096: 2}[n]
     a = wl.uniform_coeffs(rng, batch, q_list, n, np.uint64)
     b = wl.uniform_coeffs(rng, batch, q_list, n, np.uint64)
     with pm.Plan(n, q_list, path=pm.PATH_TENSOR) as plan:
-        info = plan.info
+        codes = [plan.select(i)["tensor_kernel"] for i in range(plan.info["candidates"])]
+        assert codes == ([3] if n < 1024 else [6, 3] if n <= 2048 else [3, 6]), codes
+        info = plan.select(codes.index(3))
         assert plan.elem_bytes == 8 and info["path"] == pm.PATH_TENSOR and info["rns_moduli"] > 0
         got = run_plan_batch(plan, a, b)
         pm.polymul_plan_status(plan.handle)

@@ -39,6 +39,10 @@ def _drain_digits(q):
     return next((L for L in range(1, 5) if _reach(8, L) >= q // 2), None)
 
 
+def _drain_digits64(q):
+    return next(L for L in range(1, 9) if _reach(8, L) >= q // 2)
+
+
 def _default_digits(n, q):
     """The default digit kernel's (width, digits): the drained one where
     the undrained width is below 8 and it needs fewer digits, or where the
@@ -99,7 +103,11 @@ def test_sweep_fits_the_hardware(pm):
                 seen.add(info["kernel"])
                 assert info["smem_bytes"] <= 227 * 1024 and info["tmem_cols"] <= 512
                 assert info["tmem_cols"] >= 32 and info["tmem_cols"] & (info["tmem_cols"] - 1) == 0
-                if info["kernel"] in (1, 2, 4):
+                if info["kernel"] == 6:
+                    # 64-bit words: drained 8-bit digits, at least five
+                    assert info["digit_bits"] == 8 and q >= 1 << 32 and n >= 1024
+                    assert info["digits_a"] == info["digits_b"] == max(5, _drain_digits64(q))
+                elif info["kernel"] in (1, 2, 4):
                     w = info["digit_bits"]
                     # exact fp32 sums over the whole of K, or over chunks of
                     # at most 1024 for the drained kernel
@@ -114,7 +122,7 @@ def test_sweep_fits_the_hardware(pm):
                     assert info["rns_moduli"] * max(16, 8 * info["shifts"]) <= 512
                 blocks = max(1, n // 1024)
                 assert info["groups"] == 0 or info["groups"] * info["shifts"] * info["slices"] == blocks
-    assert seen == {1, 2, 3, 4}
+    assert seen == {1, 2, 3, 4, 6}
 
 
 def test_kernel_choice(pm):
@@ -129,7 +137,13 @@ def test_kernel_choice(pm):
     assert (i["kernel"], i["digits_b"], i["candidates"]) == (4, 4, 2)
     i = pm.polymul_tensor_shape(4096, (1 << 59) - 55)
     assert (i["kernel"], i["rns_moduli"], i["shifts"], i["groups"]) == (3, 21, 2, 2)
-    for n, q in ((8192, (1 << 59) - 55), (32768, 12289), (16, 12289), (32768, (1 << 30) - 35)):
+    i = pm.polymul_tensor_shape(8192, (1 << 59) - 55)   # no RNS base: the 64-bit digit kernel
+    assert (i["kernel"], i["digits_a"], i["digits_b"], i["groups"]) == (6, 8, 8, 8)
+    i = pm.polymul_tensor_shape(65536, (1 << 59) - 55)
+    assert (i["kernel"], i["groups"], i["candidates"]) == (6, 64, 1)
+    i = pm.polymul_tensor_shape(1024, (1 << 59) - 55)   # first up to n = 2048
+    assert (i["kernel"], i["candidates"]) == (6, 2)
+    for n, q in ((32768, 12289), (16, 12289), (32768, (1 << 30) - 35)):
         with pytest.raises(pm.PolymulError) as ei:
             pm.polymul_tensor_shape(n, q)
         assert ei.value.code == pm.POLYMUL_ENOTSUP, (n, q)

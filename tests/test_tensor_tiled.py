@@ -227,11 +227,12 @@ def test_tiled_candidate_matches_whole_product_kernel(pm, n):
 
 def test_tensor_path_limits(pm):
     """Outside the tensor path's shapes creation fails with ENOTSUP when the
-    path is forced: degree above 2^14; a 59-bit modulus at 2^13 (64-bit
-    words have only the RNS kernel, whose moduli there stay below 92)."""
-    for n, q in ((32768, 12289), (8192, (1 << 59) - 55)):
+    path is forced: 32-bit words above 2^14; a 59-bit modulus at 2^13 with
+    a ternary b (the 64-bit digit kernel has no one-digit A side, and the
+    RNS kernel's moduli there stay below 92)."""
+    for n, q, flags in ((32768, 12289, 0), (8192, (1 << 59) - 55, pm.FLAG_TERNARY_B)):
         with pytest.raises(pm.PolymulError) as ei:
-            pm.Plan(n, [q], path=pm.PATH_TENSOR)
+            pm.Plan(n, [q], path=pm.PATH_TENSOR, flags=flags)
         assert ei.value.code == pm.POLYMUL_ENOTSUP, (n, q)
 
 
