@@ -1102,12 +1102,45 @@ def serving(dev, peaks, samples, count=20000, lanes=8):
                 "service_p50_us": st["service_p50_us"], "service_p99_us": st["service_p99_us"],
                 "failed": st["failed"]}
             check_sample("poisson_%.1f" % load)
+        # the tensor path (polymul_server_set_path): the first requests of the
+        # mix, all submitted at t = 0, on the 64-bit-word digit kernel; a
+        # sample of them checked against the oracle
+        tcount = 200
+        tcheck = [0, 37, 99, 150, tcount - 1]
+        town = {i: torch.zeros(len(reqs[i].prime_idx) * reqs[i].n, dtype=torch.int64).pin_memory() for i in tcheck}
+        tlist = [(p[0], p[1], p[2], p[3], town[i].numpy() if i in town else p[4]) for i, p in enumerate(plist[:tcount])]
+        srv.set_path(polymul.PATH_TENSOR)
+        t0 = time.perf_counter()
+        srv.replay(tlist, [0.0] * tcount)
+        tel = time.perf_counter() - t0
+        tst = srv.stats(reset=True)
+        srv.set_path(polymul.PATH_NTT)
+        for i in tcheck:
+            r = reqs[i]
+            a, b = sets[i % nsets]
+            k, n = len(r.prime_idx), r.n
+            av = a.numpy().view(np.uint64)[:k * n].reshape(k, n)
+            bv = b.numpy().view(np.uint64)[:k * n].reshape(k, n)
+            cv = town[i].numpy().view(np.uint64).reshape(k, n)
+            js = [0, 1 + (7 * i) % (n - 2), n - 1]
+            for j, pidx in enumerate(r.prime_idx):
+                samples.add_coeffs("serve_20k_tensor", av[j].copy(), bv[j].copy(), pool[pidx], js, cv[j, js].copy())
+        tunits = sum(len(r.prime_idx) for r in reqs[:tcount])
+        tflops = sum(2.0 * r.n * r.n * 64 * len(r.prime_idx) for r in reqs[:tcount])
+        tensor_path = {"requests": tcount, "units": tunits, "seconds": tel, "products_per_s": tcount / tel,
+                       "units_per_s": tunits / tel, "failed": tst["failed"],
+                       "kernel": "k_toeplitz_u64: 8 x 8 balanced 8-bit digits, K chunks drained into 64-bit "
+                                 "modular sums, one launch per request",
+                       "tensor_frac_bf16": tflops / tel / 1e12 / peaks.get("bf16_tflops", 1911.7),
+                       "ntt_same_requests_per_s": len(plist) / el,
+                       "checked": "%d requests, 3 coefficients per prime" % len(tcheck)}
     return {"requests": len(plist), "units": units, "lanes": lanes, "arena_bytes": 8 << 30,
             "bytes_moved": byts,
             "saturated": {"products_per_s": len(plist) / el, "units_per_s": units / el, "seconds": el,
                           "host_link_GBs": byts / el / 1e9, "p50_us": sat["p50_us"], "p99_us": sat["p99_us"],
                           "arena_peak_bytes": sat["arena_peak_bytes"], "failed": sat["failed"]},
             **poisson,
+            "tensor_path": tensor_path,
             "bit_exact_sample": None,
             "checked": "%d requests of the mix (own output buffers), 3 coefficients per prime, after every replay"
                        % len(checked),
@@ -1357,6 +1390,9 @@ def run_ours(args, ws, rank, local):
         for name, x in extras.items():
             if isinstance(x, dict) and "bit_exact_sample" in x:
                 x["bit_exact_sample"] = verdict.get(name)
+        tp = (extras.get("serve_20k") or {}).get("tensor_path")
+        if isinstance(tp, dict):
+            tp["bit_exact_sample"] = verdict.get("serve_20k_tensor")
 
     out = {
         "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": ws, "steps": args.steps,
