@@ -340,6 +340,8 @@ def _case(name, launches):
     if name == "tensor_rns4096_pipelined":
         return _case_homogeneous(4096, wl.draw_primes(rng, 8, 30, 30, 13), 64, polymul.PATH_TENSOR, launches,
                                  tensor_kernel=5)
+    if name == "tensor_u64_16384":
+        return _case_homogeneous(16384, wl.draw_primes(rng, 2, 59, 59, 15), 8, polymul.PATH_TENSOR, launches)
     if name == "tensor_u64_4096":
         return _case_homogeneous(4096, wl.draw_primes(rng, 2, 59, 59, 13), 64, polymul.PATH_TENSOR, launches)
     if name == "n16384":
@@ -363,6 +365,7 @@ CASES = {
     "tensor_rns4096": "n = 4096, 8 primes of 30 bits, 64 products on the tiled tensor kernel",
     "tensor_rns4096_pipelined": "the same on the warp-specialised pipeline form of the drained kernel",
     "tensor_u64_4096": "n = 4096, 2 primes of 59 bits, 64 products on the residue-number-system tensor kernel",
+    "tensor_u64_16384": "n = 16384, 2 primes of 59 bits, 8 products on the 64-bit-word digit kernel",
     "n16384": "n = 16384, one 30-bit prime, 1024 products (one CTA per product)",
     "cluster_32768": "n = 32768, one 30-bit prime, 256 products (thread-block clusters)",
     "u64_4096": "n = 4096, one 59-bit prime, 1024 products (64-bit words)",
