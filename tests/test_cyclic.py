@@ -143,13 +143,23 @@ def test_cyclic_and_negacyclic_plans_differ(pm):
     assert_equal_residues(gn, native.polymul_batch(a, b, [q]), "negacyclic")
 
 
-def test_cyclic_unsupported_moduli(pm):
-    """64-bit moduli without an n-th root of unity have no NTT route; above
-    the tensor path's degrees (2^14) there is no route at all."""
+def test_cyclic_moduli_without_ntt_route(pm):
+    """64-bit moduli without an n-th root of unity have no NTT route; at
+    n = 2^15 the tensor path's 64-bit digit kernel serves them (sampled
+    coefficients against the oracle), and with a ternary b (no one-digit
+    form for 64-bit words, no RNS base at that degree) nothing does."""
     q = (1 << 61) - 1  # prime, q - 1 = 2 * odd: no root of order 2^15
-    with pytest.raises(pm.PolymulError) as ei:
-        pm.Plan(32768, [q], flags=pm.FLAG_CYCLIC)
-    assert ei.value.code == pm.POLYMUL_ENOTSUP
     with pytest.raises(pm.PolymulError) as ei:
         pm.Plan(1024, [q], path=pm.PATH_NTT, flags=pm.FLAG_CYCLIC)
     assert ei.value.code == pm.POLYMUL_ENOTSUP
+    with pytest.raises(pm.PolymulError) as ei:
+        pm.Plan(32768, [q], flags=pm.FLAG_CYCLIC | pm.FLAG_TERNARY_B)
+    assert ei.value.code == pm.POLYMUL_ENOTSUP
+    n = 32768
+    a, b = _case(11, 1, [q], n, np.uint64)
+    with pm.Plan(n, [q], flags=pm.FLAG_CYCLIC) as plan:
+        assert plan.info["path"] == pm.PATH_TENSOR and plan.info["tensor_kernel"] == 6
+        got = run_plan_batch(plan, a, b)
+        pm.polymul_plan_status(plan.handle)
+    js = [0, 1, 1023, 1024, 4097, n // 2, n - 2, n - 1]
+    assert np.array_equal(got[0, 0, js].astype(np.uint64), native.coeffs(a[0, 0], b[0, 0], q, js, cyclic=True))
