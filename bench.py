@@ -825,8 +825,9 @@ def other_workloads(dev, stream, peaks, alu_peak_g, samples):
                               "units": r.info["units"], "work_items": r.info["items"], "grid": r.info["grid"],
                               "path": "ntt, two concurrent persistent launches (2^14; 2^10..2^13) replayed as a CUDA graph",
                               "shape_sets": {"2^10..2^13": choice & 1, "2^14": (choice >> 1) & 1,
-                                             "legend": "0 swizzled, both operands; 1 padded, one operand at "
-                                                       "2^10, 2^11, 2^14 (polymul_ragged_tune)"},
+                                             "legend": "0 swizzled, both operands (at 2^14 the homogeneous "
+                                                       "one-CTA-per-product kernel over the segment's rows); 1 "
+                                                       "padded, one operand at 2^10, 2^11, 2^14 (polymul_ragged_tune)"},
                               "alu_frac": mm / (ms / 1e3) / 1e9 / alu_peak_g,
                               "hbm_frac": 3 * total * 4 / (ms / 1e3) / 1e9 / hbm,
                               "bit_exact_sample": None, "l2": "inputs 1.3 GB (> L2)"}

@@ -761,11 +761,14 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     uint64_t* bar = &mbar[0];
     if (threadIdx.x == 0) mbar_init(bar, 1);
     fence_mbar_init();
+    // element offset of unit u's row (a row table, or u n)
+    auto row_off = [&](unsigned long long u) -> size_t { return args.rows ? args.rows[u].offset : (size_t)u * S::N; };
     auto issue = [&](unsigned long long u) {  // thread 0 only
       fence_proxy_async();
       mbar_arrive_expect_tx(bar, 2 * ROW + args.tx_pad);
-      bulk_g2s(sa, args.a + (size_t)u * S::N, ROW, bar);
-      bulk_g2s(sb, args.b + (size_t)u * S::N, ROW, bar);
+      const size_t off = row_off(u);
+      bulk_g2s(sa, args.a + off, ROW, bar);
+      bulk_g2s(sb, args.b + off, ROW, bar);
     };
     // first unit by position, later ones from the counter (see above)
     const unsigned long long first_round = gridDim.x;
@@ -785,7 +788,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       }
       parity ^= 1u;
       const uint32_t j = (uint32_t)(cur % k);
-      const uint32_t pj = AUX ? 0u : table_index(args, j);
+      const uint32_t pj = AUX ? 0u : args.rows ? args.rows[cur].prime : table_index(args, j);
       const PrimeConst<W> pc = args.pc[(size_t)pj * args.pc_stride + args.pc_off];
       const W qo = AUX ? args.outer_q[j] : W(0);
       auto hook = [&]() {  // every thread, after a barrier: all are done with sa/sb
@@ -795,7 +798,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
           if (s_next < units) issue(s_next);
         }
       };
-      polymul_unit_any<S, MODE, AUX, SEQ>(args.c + (size_t)cur * S::N, twf + (size_t)pj * args.tw_stride,
+      polymul_unit_any<S, MODE, AUX, SEQ>(args.c + row_off(cur), twf + (size_t)pj * args.tw_stride,
                                           twi + (size_t)pj * args.tw_stride, pc, sa, sb, threadIdx.x, true,
                                           BlockSync{}, hook, qo);
       __syncthreads();

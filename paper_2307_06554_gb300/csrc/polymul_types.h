@@ -17,6 +17,14 @@ struct alignas(16) PrimeConst {
   W pad;
 };
 
+// One (product, prime) row of an uneven list: its element offset in a, b, c
+// and its prime's index in the pool.
+struct alignas(16) RaggedUnit {
+  uint64_t offset;  // element offset of the row in a, b, c
+  uint32_t prime;   // index into the prime pool
+  uint32_t pad;
+};
+
 template <typename W>
 struct NttBatchArgs {
   const W* a;
@@ -54,6 +62,10 @@ struct NttBatchArgs {
   // 256, carried by the launch itself instead of a device array
   uint32_t pmap_inline;
   uint32_t pmap_pack[8];
+  // kernels with one team per CTA only: when set, unit u is the row at
+  // rows[u].offset with tables of pool prime rows[u].prime (the rows of one
+  // degree class of an uneven list); k and the prime map are then unused
+  const RaggedUnit* rows;
 };
 
 // table index of unit prime j (see NttBatchArgs::pmap, pmap_pack)
@@ -72,11 +84,6 @@ __device__ __forceinline__ uint32_t table_index(const NttBatchArgs<W>& args, uin
 // Degree segments per list: at most one per degree; the work counters of a
 // list are kRaggedMaxSegs segment counters and one finished-CTA count.
 constexpr int kRaggedMaxSegs = 15;
-struct alignas(16) RaggedUnit {
-  uint64_t offset;  // element offset of the row in a, b, c
-  uint32_t prime;   // index into the prime pool
-  uint32_t pad;
-};
 
 // One degree segment: `count` consecutive units of degree 2^logn.
 struct alignas(16) RaggedItem {
