@@ -542,9 +542,13 @@ extern "C" void polymul_destroy(polymul_plan* p) {
   cudaFree(p->d_err);
   cudaFree(p->d_q);
   cudaFree(p->d_outer);
-  for (int s = 0; s < kHostStreams; ++s) {
-    cudaFree(p->d_stage[s]);
-    if (p->streams[s]) cudaStreamDestroy(p->streams[s]);
+  for (int s = 0; s < kHostSlots; ++s) {
+    cudaFree(p->d_hslot[s]);
+    for (int g = 0; g < 3; ++g)
+      if (p->hev[g][s]) cudaEventDestroy(p->hev[g][s]);
+  }
+  for (int g = 0; g < 3; ++g) {
+    if (p->hs[g]) cudaStreamDestroy(p->hs[g]);
   }
   if (p->ev_entry) cudaEventDestroy(p->ev_entry);
   delete p;
@@ -853,9 +857,13 @@ extern "C" int polymul_plan_status(polymul_plan* p, void* stream) {
   return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }
 
-// Host buffers: chunks of products flow round-robin through kHostStreams
-// plan-owned device staging slots, one stream each, so that the copies in of
-// some chunks, the kernels of others and the copies out of others overlap.
+// Host buffers: chunks of products flow through a three-stage pipeline --
+// copies in, kernel, copy out, each stage on a stream of its own -- over
+// kHostSlots plan-owned device staging slots, with one event per stage and
+// slot: a chunk's kernel waits for its copies in, its copy out for its
+// kernel, and the copies in of the chunk that next takes the slot for that
+// copy out.  So copies in of later chunks, kernels and copies out of
+// earlier ones overlap without one stream's order holding back another.
 extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch,
                                   void* stream) {
   clear_error();
@@ -865,10 +873,7 @@ extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b,
   if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
   const size_t prod_bytes = (size_t)p->k * p->n * p->elem;
   // about 4 MB of each operand per chunk by default (POLYMUL_HOST_CHUNK_BYTES
-  // overrides): several chunks in flight, so that copies in, kernels and
-  // copies out of different chunks overlap (the two copy directions use
-  // separate engines).  Measured on the 4096-product n = 1024 batch: 1, 2, 4,
-  // 8, 16 MB -> 340, 292, 264, 271, 304 us.
+  // overrides)
   static const size_t chunk_target = [] {
     const char* e = getenv("POLYMUL_HOST_CHUNK_BYTES");
     const long long v = e ? atoll(e) : 0;
@@ -876,39 +881,49 @@ extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b,
   }();
   const uint64_t chunk = std::max<uint64_t>(1, chunk_target / prod_bytes);
   const size_t slot_bytes = 3 * chunk * prod_bytes;
-  for (int s = 0; s < kHostStreams; ++s) {
-    if (!p->streams[s]) PM_CUDA(cudaStreamCreateWithFlags(&p->streams[s], cudaStreamNonBlocking));
-    if (p->stage_bytes < slot_bytes) {
-      cudaFree(p->d_stage[s]);
-      p->d_stage[s] = nullptr;
-      if (cudaMalloc(&p->d_stage[s], slot_bytes) != cudaSuccess)
+  for (int g = 0; g < 3; ++g)
+    if (!p->hs[g]) PM_CUDA(cudaStreamCreateWithFlags(&p->hs[g], cudaStreamNonBlocking));
+  for (int s = 0; s < kHostSlots; ++s) {
+    for (int g = 0; g < 3; ++g)
+      if (!p->hev[g][s]) PM_CUDA(cudaEventCreateWithFlags(&p->hev[g][s], cudaEventDisableTiming));
+    if (p->hslot_bytes < slot_bytes) {
+      cudaFree(p->d_hslot[s]);
+      p->d_hslot[s] = nullptr;
+      if (cudaMalloc(&p->d_hslot[s], slot_bytes) != cudaSuccess)
         return fail(POLYMUL_ENOMEM, "staging allocation of %zu bytes failed", slot_bytes);
     }
   }
-  p->stage_bytes = std::max(p->stage_bytes, slot_bytes);
+  p->hslot_bytes = std::max(p->hslot_bytes, slot_bytes);
   if (!p->ev_entry) PM_CUDA(cudaEventCreateWithFlags(&p->ev_entry, cudaEventDisableTiming));
   PM_CUDA(cudaEventRecord(p->ev_entry, (cudaStream_t)stream));
-  for (int s = 0; s < kHostStreams; ++s) PM_CUDA(cudaStreamWaitEvent(p->streams[s], p->ev_entry, 0));
+  for (int g = 0; g < 3; ++g) PM_CUDA(cudaStreamWaitEvent(p->hs[g], p->ev_entry, 0));
+  cudaStream_t s_in = p->hs[0], s_k = p->hs[1], s_out = p->hs[2];
   const char* ha = (const char*)a;
   const char* hb = (const char*)b;
   char* hc = (char*)c;
   int rc = POLYMUL_OK;
   for (uint64_t first = 0, it = 0; first < batch; first += chunk, ++it) {
     const uint64_t cnt = std::min<uint64_t>(chunk, batch - first);
-    const int s = (int)(it % kHostStreams);
-    cudaStream_t st = p->streams[s];
-    char* da = (char*)p->d_stage[s];
+    const int s = (int)(it % kHostSlots);
+    char* da = (char*)p->d_hslot[s];
     char* db = da + chunk * prod_bytes;
     char* dc = db + chunk * prod_bytes;
     const size_t off = first * prod_bytes, bytes = cnt * prod_bytes;
-    PM_CUDA(cudaMemcpyAsync(da, ha + off, bytes, cudaMemcpyHostToDevice, st));
-    PM_CUDA(cudaMemcpyAsync(db, hb + off, bytes, cudaMemcpyHostToDevice, st));
-    rc = launch_batch(p, da, db, dc, cnt, st, 1 + s);
+    // the slot's previous chunk has been copied out
+    if (it >= (uint64_t)kHostSlots) PM_CUDA(cudaStreamWaitEvent(s_in, p->hev[2][s], 0));
+    PM_CUDA(cudaMemcpyAsync(da, ha + off, bytes, cudaMemcpyHostToDevice, s_in));
+    PM_CUDA(cudaMemcpyAsync(db, hb + off, bytes, cudaMemcpyHostToDevice, s_in));
+    PM_CUDA(cudaEventRecord(p->hev[0][s], s_in));
+    PM_CUDA(cudaStreamWaitEvent(s_k, p->hev[0][s], 0));
+    rc = launch_batch(p, da, db, dc, cnt, s_k, 1);
     if (rc != POLYMUL_OK) break;
-    PM_CUDA(cudaMemcpyAsync(hc + off, dc, bytes, cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaEventRecord(p->hev[1][s], s_k));
+    PM_CUDA(cudaStreamWaitEvent(s_out, p->hev[1][s], 0));
+    PM_CUDA(cudaMemcpyAsync(hc + off, dc, bytes, cudaMemcpyDeviceToHost, s_out));
+    PM_CUDA(cudaEventRecord(p->hev[2][s], s_out));
   }
-  for (int s = 0; s < kHostStreams; ++s) {
-    cudaError_t e = cudaStreamSynchronize(p->streams[s]);
+  for (int g = 0; g < 3; ++g) {
+    cudaError_t e = cudaStreamSynchronize(p->hs[g]);
     if (e != cudaSuccess && rc == POLYMUL_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
   }
   return rc;

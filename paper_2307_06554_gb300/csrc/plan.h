@@ -9,7 +9,8 @@
 
 // polymul_batch_host pipeline depth: chunks of products round-robin over
 // this many plan-owned streams (copy in, kernel, copy out on each)
-constexpr int kHostStreams = 4;
+constexpr int kHostStreams = 4;  // counter slots reserved for the host-buffer entry
+constexpr int kHostSlots = 6;    // staging slots of the host-buffer entry's pipeline
 // work-counter slots: the device entry point, then one per host stream
 constexpr int kCounterSlots = 1 + kHostStreams;
 
@@ -70,10 +71,12 @@ struct polymul_plan {
   // polymul_batch_shared scratch (digit planes of b and of T(a))
   void* d_sh = nullptr;
   size_t sh_bytes = 0;
-  // polymul_batch_host staging
-  void* d_stage[kHostStreams] = {};
-  size_t stage_bytes = 0;
-  cudaStream_t streams[kHostStreams] = {};
+  // polymul_batch_host: staging slots (a, b, c of one chunk each) and the
+  // three streams of its pipeline with one event per stage and slot
+  void* d_hslot[kHostSlots] = {};
+  size_t hslot_bytes = 0;
+  cudaStream_t hs[3] = {};                // copies in, kernels, copies out
+  cudaEvent_t hev[3][kHostSlots] = {};    // after the copies in, the kernel, the copy out (slot free)
   cudaEvent_t ev_entry = nullptr;
 };
 

@@ -215,3 +215,27 @@ def test_chained_batches_on_one_stream(pm, n, batch):
     for i in range(4):
         want = native.polymul_batch(want.astype(np.uint32), b, q_list)
         assert_equal_residues(from_dev(outs[i], np.uint32), want, "link %d" % i)
+
+
+@pytest.mark.parametrize("path", ["ntt", "tensor"])
+def test_host_entry_more_chunks_than_slots(pm, path):
+    """polymul_batch_host on 256 products of n = 4096 with 8 primes: 8 chunks
+    of 32 products through the 6 staging slots of its three-stream pipeline
+    (every slot reused), on both paths; equal to the device entry and to the
+    oracle on a sample."""
+    import torch
+    w = wl.rns_4096()
+    p_id = pm.PATH_NTT if path == "ntt" else pm.PATH_TENSOR
+    with pm.Plan(w.n, w.q_list, path=p_id) as plan:
+        c = np.zeros_like(w.a)
+        plan.batch_host(w.a, w.b, c)
+        ta = torch.from_numpy(w.a.view(np.int32)).cuda()
+        tb = torch.from_numpy(w.b.view(np.int32)).cuda()
+        tc = torch.empty_like(ta)
+        plan.batch(ta, tb, tc)
+        torch.cuda.synchronize()
+        pm.polymul_plan_status(plan.handle)
+        dev = tc.cpu().numpy().view(np.uint32)
+    assert np.array_equal(c, dev)
+    for p in (0, 131, 255):
+        assert_equal_residues(c[p:p + 1], native.polymul_batch(w.a[p:p + 1], w.b[p:p + 1], w.q_list), "product %d" % p)
