@@ -222,18 +222,16 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_toeplitz_tiled(TensorTiled
         // the chunk's exact fp32 sums into the rows' integer recombination;
         // the next chunk's first MMA overwrites the accumulators only after
         // the barrier that precedes its issue
+        // (digit pairs of one weight summed in 32-bit integers first)
+        cfor<0, BD * S>([&](auto gc) {
+          constexpr int g = decltype(gc)::value;
+          int64_t (&acc)[8] = dacc[g];
+          drain_pairs<LA, LB, S, g % S, 0, LA>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((g / S) * LA * TS::NB),
+                                               args.tp[j].pw, acc);
 #pragma unroll
-        for (int bl = 0; bl < BD; ++bl) {
-#pragma unroll
-          for (int sh = 0; sh < S; ++sh) {
-            int64_t (&acc)[8] = dacc[bl * S + sh];
-            drain_shift<LA, LB, S>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(bl * LA * TS::NB), sh,
-                                   args.tp[j].pw, acc);
-#pragma unroll
-            for (int v = 0; v < 8; ++v)
-              acc[v] = barrett64((uint64_t)(acc[v] + (int64_t)args.tp[j].bias), q, args.tp[j].mu);
-          }
-        }
+          for (int v = 0; v < 8; ++v)
+            acc[v] = barrett64((uint64_t)(acc[v] + (int64_t)args.tp[j].bias), q, args.tp[j].mu);
+        });
       }
     }
     if (failed) break;

@@ -1,7 +1,7 @@
 // Device helpers shared by the tiled Toeplitz kernels (toeplitz_tiled.cu,
 // toeplitz_ws.cu): balanced digits of centred residues packed as bf16, the
-// MMA N and B-operand layout of a tiling, and the drain of one shifted
-// copy's accumulators into 64-bit integer sums.
+// MMA N and B-operand layout of a tiling, and the drain of a chunk's
+// accumulators into 64-bit integer sums.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -58,31 +58,6 @@ struct TTShape {
   // each, fall in distinct banks)
   static constexpr int BT_PITCH = NG * 128 + 16;
 };
-
-// Adds shift sh's accumulators of this thread's tensor-memory lane (one row
-// of the output block, 8 outputs) to acc: sum over digit pairs (s, g) of the
-// exact fp32 partial sum times 2^(w (s + g)) mod q.
-template <int LA, int LB, int S>
-__device__ __forceinline__ void drain_shift(uint32_t lane_base, int sh, const uint32_t* pw, int64_t (&acc)[8]) {
-  using TS = TTShape<LB, S>;
-#pragma unroll
-  for (int s = 0; s < LA; ++s) {
-#pragma unroll
-    for (int c16 = 0; c16 < TS::NB / 16; ++c16) {
-      if (16 * c16 + 16 <= 8 * sh * LB || 16 * c16 >= 8 * (sh + 1) * LB) continue;
-      uint32_t r[16];
-      // warp-collective: every lane loads
-      tmem_ld16(lane_base + s * TS::NB + 16 * c16, r);
-      tmem_wait_ld();
-#pragma unroll
-      for (int cc = 0; cc < 16; ++cc) {
-        const int col = 16 * c16 + cc, g = col / 8, v = col % 8;
-        if (g >= sh * LB && g < (sh + 1) * LB)
-          acc[v] += (int64_t)__float2int_rn(__uint_as_float(r[cc])) * (int64_t)pw[s + g - sh * LB];
-      }
-    }
-  }
-}
 
 // 32 lanes x 8 consecutive 32-bit columns: thread i of the warp receives
 // lane (taddr.lane + i); taddr.lane must be the warp's own 32-lane quarter
