@@ -60,3 +60,14 @@ def test_null_plan_calls(lib):
     assert L.polymul_batch_host(None, None, None, None, 1, None) == lib.POLYMUL_EINVAL
     L.polymul_destroy(None)  # no-op
     assert L.polymul_plan_info_get(None, None) == lib.POLYMUL_EINVAL
+
+
+def test_null_handles_of_lists_and_servers(lib):
+    """Entry points on uneven lists and servers report a NULL handle as
+    EINVAL without touching a GPU."""
+    L = lib.lib()
+    assert L.polymul_ragged_select(None, 0) == lib.POLYMUL_EINVAL
+    assert L.polymul_ragged_status(None, None) == lib.POLYMUL_EINVAL
+    assert L.polymul_ragged_run(None, None, None, None, None) == lib.POLYMUL_EINVAL
+    assert L.polymul_server_set_path(None, lib.PATH_TENSOR) == lib.POLYMUL_EINVAL
+    assert L.polymul_plan_select(None, 0) == lib.POLYMUL_EINVAL
