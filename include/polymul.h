@@ -177,11 +177,17 @@ typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
  *            4-byte words or q < 2^62 in 8-byte words; else, for q < 2^31
  *            and n <= 2^14, one 31-bit auxiliary prime when 2n floor(q/2)^2
  *            fits it.
- *   TENSOR   n = 2^6 .. 2^14: balanced bf16 digits for q < 2^31 with at
- *            most five digits (whole-product kernel at n = 1024, 2048,
- *            tiled kernel at every n); the residue number system of small
- *            moduli for any q < 2^62 whose base needs at most 32 moduli
- *            (polymul_tensor_rns_base).
+ *   TENSOR   (the matrix form, Sec. 2.2) n = 2^6 .. 2^14 for q < 2^31:
+ *            balanced bf16 digits, at most five digits whose fp32 sums
+ *            stay exact over the whole of K (whole-product kernel at
+ *            n = 1024, 2048, tiled kernel at every n), or four 8-bit digits
+ *            whose sums are drained into 64-bit integers after every K
+ *            chunk of at most 1024 (also as a warp-specialised pipeline);
+ *            64-bit words at n = 2^10 .. 2^16: five to eight drained 8-bit
+ *            digits; the residue number system of small moduli for any
+ *            q < 2^62 whose base needs at most 32 moduli
+ *            (polymul_tensor_rns_base).  polymul_plan_info reports which
+ *            kernel a plan holds (tensor_kernel).
  * Errors: EINVAL (n, q, k, duplicates, null out), ENOTSUP (no path can serve
  * the moduli at this n, or a forced path cannot), ENOMEM, ECUDA.
  */
