@@ -303,6 +303,87 @@ int main() {
 """
 
 
+# Host-link microbenchmark (`python bench.py --case host_link`,
+# profiles/host_link.md): page-locked host <-> device traffic by the copy
+# engines (cudaMemcpyAsync, one direction and both at once) and by SM loads
+# and stores on mapped page-locked memory (one direction, and the 2:1 mix of
+# a polynomial product: two operand rows in, one result row out).  The
+# second is the route of polymul_batch_host's direct form.  Buffers of
+# 256 MB in and 128 MB out, beyond L2.
+LINK_PROBE_SRC = r"""
+#include <cstdio>
+#include <cstdint>
+#include <cuda_runtime.h>
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { printf("{\"error\": \"%s\"}\n", cudaGetErrorString(e_)); return 1; } } while (0)
+__global__ void copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t n16) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = src[i];
+}
+__global__ void mix16(const uint4* __restrict__ a, const uint4* __restrict__ b, uint4* __restrict__ c, size_t n16) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+    const uint4 x = a[i], y = b[i];
+    c[i] = make_uint4(x.x ^ y.x, x.y ^ y.y, x.z ^ y.z, x.w ^ y.w);
+  }
+}
+struct Ctx { cudaStream_t s, s2; cudaEvent_t fork, join; char *hin, *hout, *din, *dout; size_t nin, nout; int grid; };
+static void run(Ctx& c, int what) {
+  switch (what) {
+    case 0: cudaMemcpyAsync(c.din, c.hin, c.nin, cudaMemcpyHostToDevice, c.s); break;
+    case 1: cudaMemcpyAsync(c.hout, c.dout, c.nout, cudaMemcpyDeviceToHost, c.s); break;
+    case 2:
+      cudaEventRecord(c.fork, c.s); cudaStreamWaitEvent(c.s2, c.fork, 0);
+      cudaMemcpyAsync(c.din, c.hin, c.nin, cudaMemcpyHostToDevice, c.s);
+      cudaMemcpyAsync(c.hout, c.dout, c.nout, cudaMemcpyDeviceToHost, c.s2);
+      cudaEventRecord(c.join, c.s2); cudaStreamWaitEvent(c.s, c.join, 0);
+      break;
+    case 3: copy16<<<c.grid, 512, 0, c.s>>>((const uint4*)c.hin, (uint4*)c.din, c.nin / 16); break;
+    case 4: copy16<<<c.grid, 512, 0, c.s>>>((const uint4*)c.dout, (uint4*)c.hout, c.nout / 16); break;
+    default: mix16<<<c.grid, 512, 0, c.s>>>((const uint4*)c.hin, (const uint4*)(c.hin + c.nout), (uint4*)c.hout, c.nout / 16);
+  }
+}
+int main() {
+  Ctx c{};
+  c.nin = 256u << 20; c.nout = 128u << 20;
+  int sms = 0; CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+  c.grid = 4 * sms;
+  CK(cudaHostAlloc((void**)&c.hin, c.nin, cudaHostAllocMapped));
+  CK(cudaHostAlloc((void**)&c.hout, c.nout, cudaHostAllocMapped));
+  CK(cudaMalloc((void**)&c.din, c.nin)); CK(cudaMalloc((void**)&c.dout, c.nout));
+  for (size_t i = 0; i < c.nin; i += 4096) c.hin[i] = 1;
+  CK(cudaMemset(c.dout, 2, c.nout));
+  CK(cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking)); CK(cudaStreamCreateWithFlags(&c.s2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming)); CK(cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming));
+  cudaEvent_t e0, e1; CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
+  const char* names[] = {"copy_engine_h2d", "copy_engine_d2h", "copy_engine_both", "sm_load_host", "sm_store_host", "sm_mix_2in_1out"};
+  const double bytes[] = {(double)c.nin, (double)c.nout, (double)(c.nin + c.nout), (double)c.nin, (double)c.nout, 3.0 * c.nout};
+  printf("{\"sms\": %d, \"results\": [", sms);
+  for (int w = 0; w < 6; ++w) {
+    for (int r = 0; r < 2; ++r) run(c, w);
+    CK(cudaEventRecord(e0, c.s));
+    for (int r = 0; r < 5; ++r) run(c, w);
+    CK(cudaEventRecord(e1, c.s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0; CK(cudaEventElapsedTime(&ms, e0, e1));
+    printf("%s{\"op\": \"%s\", \"GBs\": %.1f}", w ? ", " : "", names[w], bytes[w] * 5 / (ms * 1e-3) / 1e9);
+  }
+  printf("], \"error\": \"%s\"}\n", cudaGetErrorString(cudaGetLastError()));
+  return 0;
+}
+"""
+
+
+def _case_host_link():
+    from paper_2307_06554_gb300 import build as _build
+    work = tempfile.mkdtemp()
+    src = os.path.join(work, "host_link.cu")
+    exe = os.path.join(work, "host_link")
+    with open(src, "w") as f:
+        f.write(LINK_PROBE_SRC)
+    subprocess.check_call([_build.nvcc()] + _build.ARCH + ["-O3", "-o", exe, src])
+    return json.loads(subprocess.run([exe], capture_output=True, text=True, check=True).stdout)
+
+
 def _case_alu_peak():
     from paper_2307_06554_gb300 import build as _build
     work = tempfile.mkdtemp()
@@ -329,6 +410,8 @@ def _case(name, launches):
     rng = np.random.default_rng(8)
     if name == "alu_peak":
         return _case_alu_peak()
+    if name == "host_link":
+        return _case_host_link()
     if name == "ntt_ring1024":
         return _case_homogeneous(1024, [12289], 4096, polymul.PATH_NTT, launches)
     if name == "ntt_ring1024_overlap":
@@ -359,6 +442,7 @@ def _case(name, launches):
 
 CASES = {
     "alu_peak": "integer- and tensor-pipe microbenchmark (IMAD, Shoup 32/64-bit, mma.sync u8 and bf16)",
+    "host_link": "host-link microbenchmark: copy engines and SM loads/stores on mapped page-locked memory",
     "ntt_ring1024": "n = 1024, q = 12289, 4096 products (path a, default kernel)",
     "ntt_ring1024_overlap": "the same with POLYMUL_FLAG_OVERLAP",
     "tensor_ring1024": "the same batch through the Toeplitz tensor-core path",
@@ -1297,35 +1381,83 @@ def run_ours(args, ws, rank, local):
                   "_check": t_got}
         tplan.close()
 
-    # end to end through the host-buffer entry point (pinned host memory)
-    ha = torch.from_numpy(w.a.view(np.int32)).pin_memory()
-    hb = torch.from_numpy(w.b.view(np.int32)).pin_memory()
-    hc = torch.empty_like(ha).pin_memory()
-    for _ in range(2):
-        polymul.polymul_batch_host(plan.handle, ha, hb, hc, batch, None)
+    # end to end through the host-buffer entry point, from page-locked host
+    # buffers: its direct route (the kernel reads a, b and writes c in host
+    # memory over the host link) and, for comparison, the staged route
+    # (copy engines through device buffers).  Host sets rotate so that the
+    # operands of a step were last read more than 2x L2 of traffic earlier.
+    hsets = max(2, math.ceil(2 * L2_BYTES / set_bytes))
+    host_np = [(np.roll(w.a, s, axis=0), np.roll(w.b, s, axis=0)) for s in range(hsets)]
+    host = [(torch.from_numpy(x.view(np.int32)).pin_memory(), torch.from_numpy(y.view(np.int32)).pin_memory(),
+             torch.empty(x.shape, dtype=torch.int32).pin_memory()) for x, y in host_np]
+    staged_plan = polymul.Plan(n, q_list, flags=polymul.FLAG_OVERLAP | polymul.FLAG_HOST_STAGED)
     e2e_steps = max(3, min(args.steps, 20))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        polymul.polymul_batch_host(plan.handle, ha, hb, hc, batch, None)
-    e2e_s = time.perf_counter() - t0
+
+    def e2e_run(p):
+        """Synchronous host-buffer calls (polymul_batch_host), one per step."""
+        for i in range(2):  # warm-up on the last two sets, the timed steps start at set 0
+            polymul.polymul_batch_host(p.handle, *host[(hsets - 2 + i) % hsets], batch, None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            polymul.polymul_batch_host(p.handle, *host[i % hsets], batch, None)
+        return time.perf_counter() - t0
+
+    def e2e_stream():
+        """Streaming from host buffers (polymul_batch_mapped): step i is
+        queued on the stream, then the host waits for step i - 1's event and
+        reads that step's result, so one step is always queued behind the
+        running one and every step's result is read by the host."""
+        evs = [torch.cuda.Event() for _ in range(2)]
+        seen = []
+        with torch.cuda.stream(stream):
+            for i in range(2):
+                polymul.polymul_batch_mapped(plan.handle, *host[(hsets - 2 + i) % hsets], batch, sp)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            polymul.polymul_batch_mapped(plan.handle, *host[i % hsets], batch, sp)
+            evs[i % 2].record(stream)
+            if i >= 1:
+                evs[(i - 1) % 2].synchronize()
+                seen.append(int(host[(i - 1) % hsets][2][-1, 0, -1]))
+        evs[(e2e_steps - 1) % 2].synchronize()
+        seen.append(int(host[(e2e_steps - 1) % hsets][2][-1, 0, -1]))
+        return time.perf_counter() - t0
+
+    e2e_last = (e2e_steps - 1) % hsets
+    idx = [0, 1, 2047, 4095]
+    e2e_s = e2e_stream()
+    e2e_got = host[e2e_last][2].numpy().view(np.uint32)[idx].copy()
+    direct_before = polymul.polymul_plan_info_get(plan.handle)["host_direct"]
+    sync_s = e2e_run(plan)
+    sync_direct = polymul.polymul_plan_info_get(plan.handle)["host_direct"] - direct_before == e2e_steps + 2
+    sync_got = host[e2e_last][2].numpy().view(np.uint32)[idx].copy()
+    staged_s = e2e_run(staged_plan)
+    assert polymul.polymul_plan_info_get(staged_plan.handle)["host_direct"] == 0
+    staged_plan.close()
     clk = clocks.stop()
-    link = _host_link(dev, 2 * ha.numel() * ha.element_size(), hc.numel() * hc.element_size())  # a and b in, c out
+    link = _host_link(dev, 2 * batch * n * elem, batch * n * elem)  # a and b in, c out
 
     # sampled products of the timed batch, checked by the CPU oracle leg
     samples = Samples()
     c_last = sets[(args.warmup + args.steps - 1) % nsets][2]
-    idx = [0, 1, 2047, 4095]
     samples.add("ring_1024", w.a[idx], w.b[idx], q_list, c_last[idx].cpu().numpy().view(np.uint32))
-    samples.add("ring_1024", w.a[idx], w.b[idx], q_list, hc.numpy().view(np.uint32)[idx])
+    hx, hy = host_np[e2e_last]
+    samples.add("ring_1024", hx[idx], hy[idx], q_list, e2e_got)  # the streamed last step
+    samples.add("ring_1024", hx[idx], hy[idx], q_list, sync_got)  # the synchronous direct call's
+    samples.add("ring_1024", hx[idx], hy[idx], q_list,
+                host[e2e_last][2].numpy().view(np.uint32)[idx])  # the staged route's
     if tensor is not None:
         samples.add("ring_1024_tensor", w.a[[0, 4095]], w.b[[0, 4095]], q_list, tensor.pop("_check"))
 
-    elapsed_ms, e2e_s = aggregate_over_ranks([elapsed_ms, e2e_s], device=dev)
+    elapsed_ms, e2e_s, sync_s, staged_s = aggregate_over_ranks([elapsed_ms, e2e_s, sync_s, staged_s], device=dev)
     if rank != 0:
         return
     value = job_rate(batch * args.steps, elapsed_ms / 1e3, ws)
     e2e_value = job_rate(batch * e2e_steps, e2e_s, ws)
+    staged_value = job_rate(batch * e2e_steps, staged_s, ws)
+    sync_value = job_rate(batch * e2e_steps, sync_s, ws)
 
     peaks, peak_src = _peaks()
     isolated_ms = statistics.mean(per)
@@ -1413,9 +1545,20 @@ def run_ours(args, ws, rank, local):
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": "products/s", "h2d_bytes_per_step": 2 * batch * n * elem,
                 "d2h_bytes_per_step": batch * n * elem,
-                "api": "polymul_batch_host (pinned host buffers, copies + kernel inside the timed region)",
+                "api": "polymul_batch_mapped on page-locked host buffers: the NTT batch kernel loads a, b "
+                       "from and stores c to host memory over the host link, so every step moves a and b to "
+                       "the GPU and c back inside the timed region; step i is queued, then the host waits "
+                       "for step i-1's event and reads its result",
+                "host_sets": "%d rotating sets of a, b, c (%.0f MB)" % (hsets, hsets * set_bytes / 2**20),
+                "per_call_sync": {"value": sync_value, "unit": "products/s",
+                                  "api": "polymul_batch_host, synchronous per call",
+                                  "route": "direct" if sync_direct else "staged"},
+                "staged": {"value": staged_value, "unit": "products/s",
+                           "api": "polymul_batch_host on a POLYMUL_FLAG_HOST_STAGED plan: copy engines through "
+                                  "device staging buffers, synchronous per call"},
                 "host_link": dict(link, achieved_GBs=3 * batch * n * elem / (e2e_s / e2e_steps) / 1e9,
-                                  frac=(3 * batch * n * elem / (e2e_s / e2e_steps) / 1e9) / link["both_GBs"])},
+                                  frac_of_copy_engines_both=(3 * batch * n * elem / (e2e_s / e2e_steps) / 1e9)
+                                  / link["both_GBs"])},
         "gpu_launches": args.steps,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -101,6 +101,11 @@ extern "C" {
                                      on the legacy and per-thread default
                                      streams                                */
 
+#define POLYMUL_FLAG_HOST_STAGED 32u /* polymul_batch_host always streams
+                                     through the plan's device staging
+                                     buffers and copy engines, never takes
+                                     its direct route (see there)           */
+
 typedef struct polymul_opts {
     uint32_t path;        /* POLYMUL_PATH_*                                   */
     uint32_t flags;       /* POLYMUL_FLAG_*                                   */
@@ -156,6 +161,8 @@ typedef struct polymul_plan_info {
                              compiled to (from the CUDA runtime)            */
     uint32_t kernel_max_block;/* the largest CTA the main kernel can launch
                              with (from the CUDA runtime)                   */
+    uint32_t host_direct; /* polymul_batch_host calls on this plan that took
+                             the direct route (saturates at 2^32 - 1)       */
 } polymul_plan_info;
 
 typedef struct polymul_plan polymul_plan; /* opaque, owned by the library */
@@ -234,15 +241,52 @@ int polymul_batch_shared(polymul_plan *plan, const void *a, const void *b, void 
                          uint64_t batch, void *stream);
 
 /*
- * polymul_batch_host -- as polymul_batch with HOST arrays a, b, c.  The
- * library streams chunks through plan-owned device buffers, overlapping the
- * host-to-device copy of one chunk with the kernel of another and with the
- * device-to-host copy of a third (Sec. 4, "optimizing computation and I/O").
- * Page-locked host memory gives full overlap; pageable memory works but
- * copies synchronously.  Returns after c has been written (synchronous).
+ * polymul_batch_host -- as polymul_batch with HOST arrays a, b, c (layout as
+ * there).  Two routes, both overlapping the transfer of operands and
+ * results with the arithmetic (Sec. 4, "optimizing computation and I/O"):
+ *   direct: when polymul_batch_mapped accepts the call (a, b and c in
+ *     mapped page-locked host memory, an NTT plan it serves) and the plan
+ *     lacks POLYMUL_FLAG_HOST_STAGED: that call on `stream`, then a
+ *     synchronisation of `stream`.
+ *   staged: otherwise the library streams chunks through plan-owned device
+ *     buffers, overlapping the host-to-device copy of one chunk with the
+ *     kernel of another and with the device-to-host copy of a third.
+ *     Page-locked memory gives full overlap; pageable memory works but
+ *     copies synchronously.
+ * polymul_plan_info.host_direct counts the calls that took the direct
+ * route.  Returns after c has been written (synchronous).  Calls on one plan
+ * must not overlap.
  */
 int polymul_batch_host(polymul_plan *plan, const void *a, const void *b, void *c,
                        uint64_t batch, void *stream);
+
+/*
+ * polymul_batch_mapped -- as polymul_batch with a, b and c in page-locked
+ * HOST memory that the device maps (cudaHostAlloc, cudaHostRegister or a
+ * page-locked allocator; each range is checked at both ends with
+ * cudaPointerGetAttributes).  The NTT batch kernel, in its direct form,
+ * loads every row of a and b and stores every row of c in host memory
+ * itself: on a coherent host link (NVLink-C2C) the operands travel in and
+ * the results out at the same time, inside the kernel, with no staging
+ * buffer or copy engine (Sec. 4, overlapping computation with I/O).  The
+ * operands cross the link at every call; nothing of them stays on the
+ * device.
+ *   a, b, c  host pointers (as the device sees them with unified
+ *            addressing), [batch][k][n], aligned to the word size.
+ *   stream   cudaStream_t or NULL.
+ * Asynchronous like polymul_batch: c holds the results once `stream` has
+ * been synchronised; until then a and b must not change and c must not be
+ * read.  POLYMUL_FLAG_OVERLAP lets consecutive batches on a stream overlap
+ * as for polymul_batch; POLYMUL_FLAG_VALIDATE is honoured (an extra pass
+ * over a and b, synchronous).  Needs an NTT plan on its own primes (no
+ * auxiliary prime) with 32-bit words up to n = 2^14 or 64-bit words up to
+ * n = 2^13.
+ * Errors: EINVAL (null pointers with batch > 0, a range that is not mapped
+ * page-locked host memory, misalignment, batch > 2^40), ENOTSUP (another
+ * plan), EDOMAIN (validation), ECUDA.
+ */
+int polymul_batch_mapped(polymul_plan *plan, const void *a, const void *b, void *c,
+                         uint64_t batch, void *stream);
 
 /*
  * polymul_plan_status -- synchronise `stream`, then report whether a kernel

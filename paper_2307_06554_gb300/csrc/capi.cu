@@ -584,6 +584,7 @@ extern "C" int polymul_plan_info_get(const polymul_plan* p, polymul_plan_info* i
   info->exchange_pad = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.pad : 0u;
   info->one_operand = p->path == POLYMUL_PATH_NTT ? (uint32_t)p->ki.seq : 0u;
   info->tensor_kernel = p->path != POLYMUL_PATH_TENSOR ? 0u : tensor_kernel_code(p->ki);
+  info->host_direct = (uint32_t)std::min<uint64_t>(p->host_direct, 0xffffffffu);
   cudaFuncAttributes fa;
   if (p->ki.fn && cudaFuncGetAttributes(&fa, p->ki.fn) == cudaSuccess) {
     info->kernel_regs = (uint32_t)fa.numRegs;
@@ -673,10 +674,10 @@ __global__ void k_validate(const W* __restrict__ a, const W* __restrict__ b, uin
   }
 }
 
-int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st, int slot) {
-  const uint64_t units = batch * p->k;
-  unsigned long long* ctr = p->d_ctr + 2 * slot;
-  if (p->flags & POLYMUL_FLAG_VALIDATE) {
+// POLYMUL_FLAG_VALIDATE: every coefficient of a and b below its modulus
+// (one kernel over both operands, then a synchronous read of its flag).
+static int validate_operands(polymul_plan* p, const void* a, const void* b, uint64_t units, cudaStream_t st) {
+  {
     if (!p->d_flag) PM_CUDA(cudaMalloc(&p->d_flag, sizeof(int)));
     if (!p->d_q) {
       PM_CUDA(cudaMalloc(&p->d_q, p->k * sizeof(uint64_t)));
@@ -695,6 +696,16 @@ int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_
     PM_CUDA(cudaMemcpyAsync(&h, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     PM_CUDA(cudaStreamSynchronize(st));
     if (h) return fail(POLYMUL_EDOMAIN, "an input coefficient is not below its modulus");
+  }
+  return POLYMUL_OK;
+}
+
+int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st, int slot) {
+  const uint64_t units = batch * p->k;
+  unsigned long long* ctr = p->d_ctr + 2 * slot;
+  if (p->flags & POLYMUL_FLAG_VALIDATE) {
+    const int r = validate_operands(p, a, b, units, st);
+    if (r != POLYMUL_OK) return r;
   }
   const uint64_t need = (units + p->ki.units_per_cta - 1) / p->ki.units_per_cta;
   int grid = (int)std::min<uint64_t>(need, (uint64_t)p->grid_cap);
@@ -857,6 +868,132 @@ extern "C" int polymul_plan_status(polymul_plan* p, void* stream) {
   return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }
 
+namespace {
+
+// The device address of [x, x + bytes) when the whole range is page-locked
+// host memory that the device maps (both ends checked), else null.
+void* mapped_host_range(const void* x, size_t bytes) {
+  cudaPointerAttributes lo, hi;
+  if (cudaPointerGetAttributes(&lo, x) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (lo.type != cudaMemoryTypeHost || !lo.devicePointer) return nullptr;
+  if (cudaPointerGetAttributes(&hi, (const char*)x + (bytes - 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (hi.type != cudaMemoryTypeHost || (char*)hi.devicePointer != (char*)lo.devicePointer + (bytes - 1)) return nullptr;
+  return lo.devicePointer;
+}
+
+// The batch kernel in its direct form for the plan's word size and degree
+// (looked up and sized once per plan): false when none applies.
+bool direct_kernel(polymul_plan* p) {
+  if (p->dki.fn) return true;
+  KernelInfo ki;
+  if (!(p->elem == 4 ? lookup_ntt_direct_u32((int)p->logn, &ki) : lookup_ntt_direct_u64((int)p->logn, &ki)))
+    return false;
+  if (ki.smem > 48 * 1024 &&
+      cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, ki.block, ki.smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  p->dgrid_cap = per_sm * p->num_sms;
+  p->dki = ki;
+  return true;
+}
+
+}  // namespace
+
+// The direct form of the batch kernel on host memory the device maps:
+// one launch reads a and b and writes c in place over the coherent host
+// link, so the link carries operands in and results out at the same time
+// with no staging buffer, copy engine or chunk boundary.  a, b, c are the
+// device addresses of the ranges.  Counter slot 2 (its own: a host-buffer
+// call may follow device-pointer batches still running on other streams).
+// Like a device-pointer batch the launch is recorded for the stream-order
+// guard and, with POLYMUL_FLAG_OVERLAP, may run ahead of its predecessor.
+static int launch_direct(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st) {
+  const uint64_t units = batch * p->k;
+  if (p->flags & POLYMUL_FLAG_VALIDATE) {
+    const int r = validate_operands(p, a, b, units, st);
+    if (r != POLYMUL_OK) return r;
+  }
+  const uint64_t need = (units + p->dki.units_per_cta - 1) / p->dki.units_per_cta;
+  const int grid = (int)std::min<uint64_t>(need, (uint64_t)p->dgrid_cap);
+  unsigned long long* ctr = p->d_ctr + 2 * kDirectSlot;
+  const uintptr_t bytes = (uintptr_t)(units * p->n * p->elem);
+  LaunchFootprint fp;
+  fp.a_lo = (uintptr_t)a, fp.a_hi = (uintptr_t)a + bytes;
+  fp.b_lo = (uintptr_t)b, fp.b_hi = (uintptr_t)b + bytes;
+  fp.c_lo = (uintptr_t)c, fp.c_hi = (uintptr_t)c + bytes;
+  StreamOrderGuard order(p->device, st);
+  const uint32_t early = (p->flags & POLYMUL_FLAG_OVERLAP) && order.may_run_ahead(fp) ? 1u : 0u;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(p->dki.block);
+  cfg.dynamicSmemBytes = p->dki.smem;
+  cfg.stream = st;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  if (p->elem == 4) {
+    NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
+                                (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err,
+                                nullptr, nullptr, p->n, 1, 0, early, 0, 0};
+    void* argv[] = {&args};
+    PM_CUDA(cudaLaunchKernelExC(&cfg, p->dki.fn, argv));
+  } else {
+    NttBatchArgs<uint64_t> args{(const uint64_t*)a, (const uint64_t*)b, (uint64_t*)c, p->d_twf, p->d_twi,
+                                (const PrimeConst<uint64_t>*)p->d_pc, units, p->k, ctr, p->d_err,
+                                nullptr, nullptr, p->n, 1, 0, early, 0, 0};
+    void* argv[] = {&args};
+    PM_CUDA(cudaLaunchKernelExC(&cfg, p->dki.fn, argv));
+  }
+  order.record(&fp);
+  return POLYMUL_OK;
+}
+
+// The device addresses of a, b, c for the direct form, or a POLYMUL code:
+// ENOTSUP when the plan has no direct kernel, EINVAL when a range is not
+// mapped page-locked host memory or is misaligned.
+static int direct_ranges(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, void** da,
+                         void** db, void** dc) {
+  if (p->path != POLYMUL_PATH_NTT || p->aux_prime || !direct_kernel(p))
+    return fail(POLYMUL_ENOTSUP, "no direct-access kernel for this plan (NTT path on the plan's own primes, "
+                                 "32-bit words up to n = 2^14, 64-bit words up to 2^13)");
+  if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) % p->elem != 0)
+    return fail(POLYMUL_EINVAL, "operands must be aligned to the %u-byte word", p->elem);
+  const size_t bytes = (size_t)batch * p->k * p->n * p->elem;
+  *da = mapped_host_range(a, bytes);
+  *db = mapped_host_range(b, bytes);
+  *dc = mapped_host_range(c, bytes);
+  if (!*da || !*db || !*dc) return fail(POLYMUL_EINVAL, "a, b and c must lie in page-locked host memory the device maps");
+  return POLYMUL_OK;
+}
+
+extern "C" int polymul_batch_mapped(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch,
+                                    void* stream) {
+  clear_error();
+  TraceRange trace_("polymul_batch_mapped");
+  if (!p) return fail(POLYMUL_EINVAL, "plan is NULL");
+  if (batch == 0) return POLYMUL_OK;
+  if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
+  if (batch > (1ull << 40)) return fail(POLYMUL_EINVAL, "batch too large");
+  void *da, *db, *dc;
+  const int r = direct_ranges(p, a, b, c, batch, &da, &db, &dc);
+  return r != POLYMUL_OK ? r : launch_direct(p, da, db, dc, batch, (cudaStream_t)stream);
+}
+
 // Host buffers: chunks of products flow through a three-stage pipeline --
 // copies in, kernel, copy out, each stage on a stream of its own -- over
 // kHostSlots plan-owned device staging slots, with one event per stage and
@@ -872,6 +1009,16 @@ extern "C" int polymul_batch_host(polymul_plan* p, const void* a, const void* b,
   if (batch == 0) return POLYMUL_OK;
   if (!a || !b || !c) return fail(POLYMUL_EINVAL, "null operand pointer");
   const size_t prod_bytes = (size_t)p->k * p->n * p->elem;
+  void *da, *db, *dc;
+  if (!(p->flags & POLYMUL_FLAG_HOST_STAGED) && batch <= (1ull << 40) &&
+      direct_ranges(p, a, b, c, batch, &da, &db, &dc) == POLYMUL_OK) {
+    const int rc = launch_direct(p, da, db, dc, batch, (cudaStream_t)stream);
+    if (rc != POLYMUL_OK) return rc;
+    ++p->host_direct;
+    PM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return POLYMUL_OK;
+  }
+  clear_error();  // the staged route serves what the direct one cannot
   // about 4 MB of each operand per chunk by default (POLYMUL_HOST_CHUNK_BYTES
   // overrides)
   static const size_t chunk_target = [] {

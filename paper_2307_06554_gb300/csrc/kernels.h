@@ -43,6 +43,11 @@ bool lookup_ntt_u32_rb3(int logn, int mode, KernelInfo* ki);  // logn 9..12, mod
 // words, mode 1, logn 6..12
 bool lookup_ntt_alt(uint32_t elem, int logn, int mode, KernelInfo* ki);
 
+// the batch kernel reading a and b and writing c where they lie (host
+// memory the device maps): 32-bit words logn 4..14, 64-bit words logn 4..13
+bool lookup_ntt_direct_u32(int logn, KernelInfo* ki);
+bool lookup_ntt_direct_u64(int logn, KernelInfo* ki);
+
 // shared-operand products on the NTT path: a's transform once per prime
 // (prep), then forward(b), pointwise, inverse per product (32-bit words,
 // logn 10..13, modes 0..2)

@@ -485,6 +485,9 @@ __device__ __forceinline__ void inv_from2(W (&x)[S::R], W (&y)[S::R], B sx, B sy
 // (unswizzled, contiguous) in sa and sb.  Every thread of the team calls it;
 // inactive threads (act = false) compute on stale data and store nothing, so
 // that team barriers stay uniform.  `hook` is called once sa/sb are free.
+// The operands are read from ia and ib: the staged rows in sa and sb, or the
+// rows themselves in global memory (host memory the device maps included),
+// in the same coalesced order.
 // Auxiliary-prime mode (AUX = true): the ring modulus qo has no 2n-th root
 // of unity, so the product is formed over the integers instead.  Operands
 // are lifted to their centred representatives (|x| <= qo/2), which the NTT
@@ -493,16 +496,16 @@ __device__ __forceinline__ void inv_from2(W (&x)[S::R], W (&y)[S::R], B sx, B sy
 template <class S, int MODE, bool AUX, class Sync, class Hook, typename W = typename S::W>
 __device__ __forceinline__ void polymul_unit(W* __restrict__ c, const TwPair<W>* __restrict__ twf,
                                              const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
-                                             W* sa, W* sb, uint32_t t, bool act, Sync sync, Hook&& hook,
-                                             W qo = 0) {
+                                             W* sa, W* sb, const W* ia, const W* ib, uint32_t t, bool act,
+                                             Sync sync, Hook&& hook, W qo = 0) {
   constexpr int TOP = S::NPH - 1;
   W xa[S::R], xb[S::R];
   const W lift = pc.q - qo, half = qo >> 1;
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
     const uint32_t j = elem_index<S, TOP>(e, t);
-    xa[e] = sa[j];
-    xb[e] = sb[j];
+    xa[e] = ia[j];
+    xb[e] = ib[j];
     if constexpr (AUX) {
       xa[e] = xa[e] > half ? xa[e] + lift : xa[e];
       xb[e] = xb[e] > half ? xb[e] + lift : xb[e];
@@ -554,8 +557,8 @@ __device__ __forceinline__ void polymul_unit(W* __restrict__ c, const TwPair<W>*
 template <class S, int MODE, bool AUX, class Sync, class Hook, typename W = typename S::W>
 __device__ __forceinline__ void polymul_unit_seq(W* __restrict__ c, const TwPair<W>* __restrict__ twf,
                                                  const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
-                                                 W* sa, W* sb, uint32_t t, bool act, Sync sync, Hook&& hook,
-                                                 W qo = 0) {
+                                                 W* sa, W* sb, const W* ia, const W* ib, uint32_t t, bool act,
+                                                 Sync sync, Hook&& hook, W qo = 0) {
   constexpr int TOP = S::NPH - 1;
   W x[S::R];
   const W lift = pc.q - qo, half = qo >> 1;
@@ -566,14 +569,14 @@ __device__ __forceinline__ void polymul_unit_seq(W* __restrict__ c, const TwPair
       if constexpr (AUX) x[e] = x[e] > half ? x[e] + lift : x[e];
     });
   };
-  load_top(sa);
+  load_top(ia);
   fwd_from1<S, MODE, TOP>(x, sa, twf, pc, t, sync);
   if constexpr (S::NPH > 1) sync();  // every exchange read of sa is done
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
     sa[e * S::T + t] = x[e];
   });
-  load_top(sb);
+  load_top(ib);
   fwd_from1<S, MODE, TOP>(x, sb, twf, pc, t, sync);
   sfor<0, S::R>([&](auto ec) {
     constexpr int e = decltype(ec)::value;
@@ -611,12 +614,12 @@ __device__ __forceinline__ void polymul_unit_seq(W* __restrict__ c, const TwPair
 template <class S, int MODE, bool AUX, bool SEQ, class Sync, class Hook, typename W = typename S::W>
 __device__ __forceinline__ void polymul_unit_any(W* __restrict__ c, const TwPair<W>* __restrict__ twf,
                                                  const TwPair<W>* __restrict__ twi, const PrimeConst<W>& pc,
-                                                 W* sa, W* sb, uint32_t t, bool act, Sync sync, Hook&& hook,
-                                                 W qo = 0) {
+                                                 W* sa, W* sb, const W* ia, const W* ib, uint32_t t, bool act,
+                                                 Sync sync, Hook&& hook, W qo = 0) {
   if constexpr (SEQ)
-    polymul_unit_seq<S, MODE, AUX>(c, twf, twi, pc, sa, sb, t, act, sync, hook, qo);
+    polymul_unit_seq<S, MODE, AUX>(c, twf, twi, pc, sa, sb, ia, ib, t, act, sync, hook, qo);
   else
-    polymul_unit<S, MODE, AUX>(c, twf, twi, pc, sa, sb, t, act, sync, hook, qo);
+    polymul_unit<S, MODE, AUX>(c, twf, twi, pc, sa, sb, ia, ib, t, act, sync, hook, qo);
 }
 
 struct WarpSync {
@@ -651,7 +654,14 @@ constexpr int ntt_block() {
 // AUX: auxiliary-prime mode (see polymul_unit); every unit then uses the
 // single NTT prime pc[0] and the ring modulus outer_q[u % k].
 // SEQ: one operand in registers at a time (polymul_unit_seq).
-template <class S, int MODE, int WARPS, int REGS, bool AUX = false, bool SEQ = false>
+// DIRECT: no staging copies; each team reads its unit's rows of a and b
+// with plain coalesced loads where they lie and writes c the same way.  For
+// operands in page-locked host memory that the device maps: over a coherent
+// host link the loads and stores of many resident teams keep the link busy
+// in both directions at once, with no copy engine and no device buffer
+// (Sec. 4, overlapping computation with I/O, taken to the word level).
+// No bounded waits are made (nothing is asynchronous).
+template <class S, int MODE, int WARPS, int REGS, bool AUX = false, bool SEQ = false, bool DIRECT = false>
 __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, WARPS>() * REGS))
     k_ntt_batch(NttBatchArgs<typename S::W> args) {
   using W = typename S::W;
@@ -716,17 +726,20 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     // first units by position (no atomic on the critical path at start-up),
     // later ones from the counter, offset by the units handed out that way
     unsigned long long cur = ((unsigned long long)blockIdx.x * WARPS + warp) * TPW;
-    if (lane == 0 && cur < units) issue(cur);
+    if (!DIRECT && lane == 0 && cur < units) issue(cur);
     while (cur < units) {
-      const bool ok = mbar_wait(bar, parity, polls);
-      if (__any_sync(0xffffffffu, !ok)) {
-        // record the failure, let the copy in flight land, and leave through
-        // the finish protocol so that the work counter is reset as usual
-        if (lane == 0) atomicExch_system(args.err, 1);
-        mbar_wait(bar, parity, polls);
-        break;
+      if constexpr (!DIRECT) {
+        const bool ok = mbar_wait(bar, parity, polls);
+        if (__any_sync(0xffffffffu, !ok)) {
+          // record the failure, let the copy in flight land, and leave
+          // through the finish protocol so that the work counter is reset as
+          // usual
+          if (lane == 0) atomicExch_system(args.err, 1);
+          mbar_wait(bar, parity, polls);
+          break;
+        }
+        parity ^= 1u;
       }
-      parity ^= 1u;
       const uint64_t u = cur + team;
       const bool act = u < units;
       const uint32_t j = act ? (uint32_t)(u % k) : 0u;
@@ -736,11 +749,14 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
       unsigned long long nxt = units;
       auto hook = [&]() {
         nxt = grab();
-        if (lane == 0 && nxt < units) issue(nxt);
+        if (!DIRECT && lane == 0 && nxt < units) issue(nxt);
       };
-      polymul_unit_any<S, MODE, AUX, SEQ>(args.c + (act ? (size_t)u * S::N : 0), twf + (size_t)pj * args.tw_stride,
-                                          twi + (size_t)pj * args.tw_stride, pc, sa, sb, t, act, WarpSync{}, hook,
-                                          qo);
+      // an inactive team of the last round reads row 0 (it stores nothing)
+      const size_t row = act ? (size_t)u * S::N : 0;
+      polymul_unit_any<S, MODE, AUX, SEQ>(args.c + row, twf + (size_t)pj * args.tw_stride,
+                                          twi + (size_t)pj * args.tw_stride, pc, sa, sb,
+                                          DIRECT ? args.a + row : sa, DIRECT ? args.b + row : sb, t, act,
+                                          WarpSync{}, hook, qo);
       cur = nxt;
     }
     order();
@@ -774,19 +790,21 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
     const unsigned long long first_round = gridDim.x;
     if (threadIdx.x == 0) {
       s_next = blockIdx.x;
-      if (s_next < units) issue(s_next);
+      if (!DIRECT && s_next < units) issue(s_next);
     }
     __syncthreads();
     unsigned long long cur = s_next;
     uint32_t parity = 0;
     while (cur < units) {
-      const bool ok = mbar_wait(bar, parity, polls);
-      if (__syncthreads_or(!ok)) {  // as in the warp-team path
-        if (threadIdx.x == 0) atomicExch_system(args.err, 1);
-        mbar_wait(bar, parity, polls);
-        break;
+      if constexpr (!DIRECT) {
+        const bool ok = mbar_wait(bar, parity, polls);
+        if (__syncthreads_or(!ok)) {  // as in the warp-team path
+          if (threadIdx.x == 0) atomicExch_system(args.err, 1);
+          mbar_wait(bar, parity, polls);
+          break;
+        }
+        parity ^= 1u;
       }
-      parity ^= 1u;
       const uint32_t j = (uint32_t)(cur % k);
       const uint32_t pj = AUX ? 0u : args.rows ? args.rows[cur].prime : table_index(args, j);
       const PrimeConst<W> pc = args.pc[(size_t)pj * args.pc_stride + args.pc_off];
@@ -795,12 +813,14 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
         order();
         if (threadIdx.x == 0) {
           s_next = first_round + atomicAdd(ctr, 1ull);
-          if (s_next < units) issue(s_next);
+          if (!DIRECT && s_next < units) issue(s_next);
         }
       };
-      polymul_unit_any<S, MODE, AUX, SEQ>(args.c + row_off(cur), twf + (size_t)pj * args.tw_stride,
-                                          twi + (size_t)pj * args.tw_stride, pc, sa, sb, threadIdx.x, true,
-                                          BlockSync{}, hook, qo);
+      const size_t row = row_off(cur);
+      polymul_unit_any<S, MODE, AUX, SEQ>(args.c + row, twf + (size_t)pj * args.tw_stride,
+                                          twi + (size_t)pj * args.tw_stride, pc, sa, sb,
+                                          DIRECT ? args.a + row : sa, DIRECT ? args.b + row : sb, threadIdx.x,
+                                          true, BlockSync{}, hook, qo);
       __syncthreads();
       cur = s_next;
     }

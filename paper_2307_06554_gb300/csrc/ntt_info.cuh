@@ -31,11 +31,11 @@ struct NttCfg {
 };
 
 // every parameter explicit
-template <typename W, int LOGN, int MODE, bool AUX, int RB, int REGS, int PAD, bool SEQ>
+template <typename W, int LOGN, int MODE, bool AUX, int RB, int REGS, int PAD, bool SEQ, bool DIRECT = false>
 KernelInfo ntt_info_x() {
   using S = Shape<W, LOGN, RB, PAD>;
   KernelInfo ki;
-  ki.fn = (const void*)k_ntt_batch<S, MODE, kNttWarps, REGS, AUX, SEQ>;
+  ki.fn = (const void*)k_ntt_batch<S, MODE, kNttWarps, REGS, AUX, SEQ, DIRECT>;
   ki.rb = RB;
   ki.mode = MODE;
   ki.regs = REGS;

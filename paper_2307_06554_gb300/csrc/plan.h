@@ -7,12 +7,11 @@
 
 #include "kernels.h"
 
-// polymul_batch_host pipeline depth: chunks of products round-robin over
-// this many plan-owned streams (copy in, kernel, copy out on each)
-constexpr int kHostStreams = 4;  // counter slots reserved for the host-buffer entry
-constexpr int kHostSlots = 6;    // staging slots of the host-buffer entry's pipeline
-// work-counter slots: the device entry point, then one per host stream
-constexpr int kCounterSlots = 1 + kHostStreams;
+constexpr int kHostSlots = 6;  // staging slots of the host-buffer entry's pipeline
+// work-counter slots: 0 the device entry point, 1 the kernels of the staged
+// host-buffer pipeline, 2 the direct form on mapped host memory
+constexpr int kCounterSlots = 3;
+constexpr int kDirectSlot = 2;
 
 // One launchable way of computing a plan's products (the autotuner's choices).
 struct PlanCandidate {
@@ -47,8 +46,8 @@ struct polymul_plan {
   bool tuned = false;
   uint64_t tuned_batch = 0;  // batch bucket of the tuned choice
   void* d_tpc = nullptr;  // tensor-path constants
-  void* d_tpc8 = nullptr;
-  void* d_tp64 = nullptr;  // TensorPrime64 per prime (64-bit-word digit kernel)  // the same for 8-bit digits (drained tiled kernel), when the plan's width is less
+  void* d_tpc8 = nullptr;  // the same for 8-bit digits (drained tiled kernel), when the plan's width is less
+  void* d_tp64 = nullptr;  // TensorPrime64 per prime (64-bit-word digit kernel)
   // tensor path, residue number system of small moduli: the base and its
   // per-prime constants (when the RNS kernel is a candidate)
   uint32_t rns_r = 0;
@@ -78,6 +77,12 @@ struct polymul_plan {
   cudaStream_t hs[3] = {};                // copies in, kernels, copies out
   cudaEvent_t hev[3][kHostSlots] = {};    // after the copies in, the kernel, the copy out (slot free)
   cudaEvent_t ev_entry = nullptr;
+  // polymul_batch_host, direct route: the batch kernel that reads a and b
+  // and writes c where they lie (mapped page-locked host memory), its
+  // persistent grid, and the calls that took the route
+  pm::KernelInfo dki;
+  int dgrid_cap = 0;
+  uint64_t host_direct = 0;
 };
 
 inline void apply_candidate(polymul_plan* p, size_t i) {

@@ -106,7 +106,7 @@ __device__ __forceinline__ bool ragged_segment(const RaggedArgs& args, const Rag
     auto hook = [&]() {  // the whole team, once sa/sb are free
       if (t == 0) take();
     };
-    polymul_unit_any<S, MODE, false, SEQ>(args.c + unit.offset, twf, twi, pc, sa, sb, t, true, sync, hook);
+    polymul_unit_any<S, MODE, false, SEQ>(args.c + unit.offset, twf, twi, pc, sa, sb, sa, sb, t, true, sync, hook);
     sync();  // the leader's s_next[team] is visible
     cur = s_next[team];
   }

@@ -31,6 +31,7 @@ FLAG_TUNE = 2
 FLAG_CYCLIC = 4  # the ring Z_q[x]/(x^n-1) instead of Z_q[x]/(x^n+1)
 FLAG_TERNARY_B = 8  # b in {0, 1, q-1}: the tensor path takes b as one digit (c = b * T(a))
 FLAG_OVERLAP = 16  # a batch may start while the previous batch launch on its stream drains
+FLAG_HOST_STAGED = 32  # polymul_batch_host always copies through device staging buffers
 
 _ERRNAMES = {1: "EINVAL", 2: "ENOTSUP", 3: "EDOMAIN", 4: "ENOMEM", 5: "ETIMEOUT", 6: "ECUDA"}
 
@@ -51,7 +52,8 @@ class polymul_plan_info(ctypes.Structure):
                 ("n", "k", "elem_bytes", "path", "aux_primes", "block", "grid", "smem_bytes", "ctas_per_sm",
                  "digit_bits", "digits", "radix_bits", "candidates", "tuned", "tuned_batch",
                  "launch_flags", "ntt_mode", "regs", "cyclic", "tensor_groups", "rns_moduli",
-                 "exchange_pad", "one_operand", "tensor_kernel", "kernel_regs", "kernel_max_block")]
+                 "exchange_pad", "one_operand", "tensor_kernel", "kernel_regs", "kernel_max_block",
+                 "host_direct")]
 
 
 class polymul_tensor_shape_info(ctypes.Structure):
@@ -95,6 +97,8 @@ def _load():
     lib.polymul_batch.restype = i32
     lib.polymul_batch_host.argtypes = [vp, vp, vp, vp, u64, vp]
     lib.polymul_batch_host.restype = i32
+    lib.polymul_batch_mapped.argtypes = [vp, vp, vp, vp, u64, vp]
+    lib.polymul_batch_mapped.restype = i32
     lib.polymul_batch_shared.argtypes = [vp, vp, vp, vp, u64, vp]
     lib.polymul_batch_shared.restype = i32
     lib.polymul_selftest_wait.argtypes = [ctypes.c_uint32, vp]
@@ -215,6 +219,12 @@ def polymul_batch_host(plan: int, a, b, c, batch: int, stream=None) -> None:
     _check(_lib.polymul_batch_host(plan, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
 
 
+def polymul_batch_mapped(plan: int, a, b, c, batch: int, stream=None) -> None:
+    """a, b, c in page-locked host memory the device maps; asynchronous on
+    `stream` (results in c once it has been synchronised)."""
+    _check(_lib.polymul_batch_mapped(plan, _ptr(a), _ptr(b), _ptr(c), batch, _stream(stream)))
+
+
 def polymul_selftest_wait(polls: int, stream=None) -> None:
     """Device check that a bounded wait gives up: raises PolymulError with
     POLYMUL_ETIMEOUT when it does (the expected outcome)."""
@@ -316,6 +326,11 @@ class Plan:
     def batch_host(self, a, b, c) -> None:
         batch = self._check_shapes(a, b, c)
         polymul_batch_host(self.handle, a, b, c, batch, None)
+
+    def batch_mapped(self, a, b, c, stream=None) -> None:
+        """a, b, c: page-locked host tensors [batch][k][n]; asynchronous."""
+        batch = self._check_shapes(a, b, c)
+        polymul_batch_mapped(self.handle, a, b, c, batch, stream)
 
     def _check_shapes(self, a, b, c) -> int:
         shape = tuple(a.shape)

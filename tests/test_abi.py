@@ -58,6 +58,7 @@ def test_null_plan_calls(lib):
     L = lib.lib()
     assert L.polymul_batch(None, None, None, None, 1, None) == lib.POLYMUL_EINVAL
     assert L.polymul_batch_host(None, None, None, None, 1, None) == lib.POLYMUL_EINVAL
+    assert L.polymul_batch_mapped(None, None, None, None, 1, None) == lib.POLYMUL_EINVAL
     L.polymul_destroy(None)  # no-op
     assert L.polymul_plan_info_get(None, None) == lib.POLYMUL_EINVAL
 
