@@ -1125,9 +1125,13 @@ def serving(dev, peaks, samples, count=20000, lanes=8):
     page-locked host memory.  Operand data: 16 sets of 32 x 65536 words
     uniform below 2^58 -- canonical residues of every 59-bit pool prime -- so
     request i reads the first k*n words of set i mod 16 as its [k][n]
-    operands without a copy.  Throughput: all requests submitted at t = 0
-    (admitted as device memory frees up).  Latency: Poisson schedules at 0.5
-    and 0.8 of that throughput.  Results: a seeded sample of 24 requests of
+    operands without a copy.  Every buffer is page-locked, so requests take
+    the server's direct route (kernels read a, b and write c in host
+    memory); the saturated replay is repeated on the staged route (copies
+    through the device arena) for comparison.  Throughput: all requests
+    submitted at t = 0 (admitted as device memory frees up; the request
+    array is marshalled before the timed replays).  Latency: Poisson
+    schedules at 0.5 and 0.8 of that throughput.  Results: a seeded sample of 24 requests of
     the mix write to buffers of their own and are checked against the CPU
     oracle after each replay; the other requests share a pool of output
     buffers whose contents are not read (two of them may be in flight at
@@ -1165,14 +1169,23 @@ def serving(dev, peaks, samples, count=20000, lanes=8):
                 samples.add_coeffs("serve_20k", av[j].copy(), bv[j].copy(), pool[p], js, cv[j, js].copy())
             own[i].zero_()
 
+    prep = polymul.Server.prepare(plist)  # marshalled once, outside the timed replays
     with polymul.Server(pool, nmax, device_bytes=8 << 30, lanes=lanes) as srv:
         srv.replay(plist[:256], [0.0] * 256)  # warm-up
         srv.stats(reset=True)
         t0 = time.perf_counter()
-        srv.replay(plist, [0.0] * len(plist))
+        srv.replay(prep, [0.0] * len(plist))
         el = time.perf_counter() - t0
         sat = srv.stats(reset=True)
         check_sample("saturated")
+        # the same with every request copied through the device arena
+        srv.set_route(polymul.ROUTE_STAGED)
+        t0 = time.perf_counter()
+        srv.replay(prep, [0.0] * len(plist))
+        el_staged = time.perf_counter() - t0
+        sat_staged = srv.stats(reset=True)
+        srv.set_route(polymul.ROUTE_DIRECT)
+        check_sample("saturated_staged")
         # latency under Poisson arrivals at fractions of the measured
         # saturated rate (the host link it depends on varies between hosts)
         poisson = {}
@@ -1180,7 +1193,7 @@ def serving(dev, peaks, samples, count=20000, lanes=8):
             rate = load * len(plist) / el
             arrivals = np.cumsum(np.random.default_rng(5).exponential(1.0 / rate, size=len(plist))).tolist()
             t0 = time.perf_counter()
-            lat = np.array(srv.replay(plist, arrivals))
+            lat = np.array(srv.replay(prep, arrivals))
             el2 = time.perf_counter() - t0
             st = srv.stats(reset=True)
             poisson["poisson_%.1f" % load] = {
@@ -1188,6 +1201,7 @@ def serving(dev, peaks, samples, count=20000, lanes=8):
                 "p99_us": float(np.percentile(lat, 99)), "mean_us": float(lat.mean()),
                 "queue_p50_us": st["queue_p50_us"], "queue_p99_us": st["queue_p99_us"],
                 "service_p50_us": st["service_p50_us"], "service_p99_us": st["service_p99_us"],
+                "server_issue_us": st["issue_us_mean"], "direct_requests": st["completed_direct"],
                 "failed": st["failed"]}
             check_sample("poisson_%.1f" % load)
         # the tensor path (polymul_server_set_path): the first requests of the
@@ -1197,9 +1211,10 @@ def serving(dev, peaks, samples, count=20000, lanes=8):
         tcheck = [0, 37, 99, 150, tcount - 1]
         town = {i: torch.zeros(len(reqs[i].prime_idx) * reqs[i].n, dtype=torch.int64).pin_memory() for i in tcheck}
         tlist = [(p[0], p[1], p[2], p[3], town[i].numpy() if i in town else p[4]) for i, p in enumerate(plist[:tcount])]
+        tprep = polymul.Server.prepare(tlist)
         srv.set_path(polymul.PATH_TENSOR)
         t0 = time.perf_counter()
-        srv.replay(tlist, [0.0] * tcount)
+        srv.replay(tprep, [0.0] * tcount)
         tel = time.perf_counter() - t0
         tst = srv.stats(reset=True)
         srv.set_path(polymul.PATH_NTT)
@@ -1226,7 +1241,16 @@ def serving(dev, peaks, samples, count=20000, lanes=8):
             "bytes_moved": byts,
             "saturated": {"products_per_s": len(plist) / el, "units_per_s": units / el, "seconds": el,
                           "host_link_GBs": byts / el / 1e9, "p50_us": sat["p50_us"], "p99_us": sat["p99_us"],
-                          "arena_peak_bytes": sat["arena_peak_bytes"], "failed": sat["failed"]},
+                          "arena_peak_bytes": sat["arena_peak_bytes"], "failed": sat["failed"],
+                          "direct_requests": sat["completed_direct"], "server_issue_us": sat["issue_us_mean"],
+                          "route": "direct: each request's kernel reads a, b and writes c in page-locked host "
+                                   "memory over the host link"},
+            "saturated_staged": {"products_per_s": len(plist) / el_staged, "seconds": el_staged,
+                                 "host_link_GBs": byts / el_staged / 1e9, "p50_us": sat_staged["p50_us"],
+                                 "p99_us": sat_staged["p99_us"], "failed": sat_staged["failed"],
+                                 "server_issue_us": sat_staged["issue_us_mean"],
+                                 "route": "staged (polymul_server_set_route): copies in and out through the "
+                                          "device arena on each lane's copy streams"},
             **poisson,
             "tensor_path": tensor_path,
             "bit_exact_sample": None,
@@ -1391,7 +1415,7 @@ def run_ours(args, ws, rank, local):
     host = [(torch.from_numpy(x.view(np.int32)).pin_memory(), torch.from_numpy(y.view(np.int32)).pin_memory(),
              torch.empty(x.shape, dtype=torch.int32).pin_memory()) for x, y in host_np]
     staged_plan = polymul.Plan(n, q_list, flags=polymul.FLAG_OVERLAP | polymul.FLAG_HOST_STAGED)
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(10, args.steps)
 
     def e2e_run(p):
         """Synchronous host-buffer calls (polymul_batch_host), one per step."""

@@ -516,6 +516,11 @@ void polymul_ragged_destroy(polymul_ragged *ctx);               /* NULL-safe */
  * memory (an arena of `device_bytes`) and an in-flight slot free up, runs
  * each on one of `lanes` streams (copy in, kernel, copy out) so that work of
  * different requests overlaps on the device, and retires finished ones.
+ * A request whose a, b and c all lie in page-locked host memory the device
+ * maps (checked at submission as for polymul_batch_mapped) takes the direct
+ * route: its kernel loads a and b and stores c in host memory itself over
+ * the host link, with no arena memory and no copies
+ * (polymul_server_set_route turns this off).
  * Twiddle tables of the whole pool stay resident (Sec. 4, "fine-tuning the
  * design" (i)); copies overlap computation (Sec. 4 (ii)).
  * ---------------------------------------------------------------------- */
@@ -544,7 +549,13 @@ typedef struct polymul_server_stats {
                                                spends enqueuing one request */
     double server_busy_s;                   /* server-thread time in passes
                                                that admitted or retired work */
+    uint64_t completed_direct;              /* completed requests that took
+                                               the direct route             */
 } polymul_server_stats;
+
+#define POLYMUL_ROUTE_DIRECT 0  /* operands in mapped page-locked host memory
+                                   are read and written in place (default) */
+#define POLYMUL_ROUTE_STAGED 1  /* always copy through device memory       */
 
 /* Start a server on the current device.  Each lane is three streams (copies
  * in, kernels, copies out); with more than 8 streams in the process, set
@@ -565,6 +576,11 @@ int polymul_server_submit(polymul_server *srv, const polymul_request *req, uint6
  * and the pool's constants (synchronous).  Errors: EINVAL (path), ENOTSUP
  * (n_max below 1024), ENOMEM, ECUDA. */
 int polymul_server_set_path(polymul_server *srv, uint32_t path);
+/* The host route of requests submitted after the call: POLYMUL_ROUTE_DIRECT
+ * (the default; requests whose buffers are not all mapped page-locked
+ * memory, and tensor-path requests, are copied all the same) or
+ * POLYMUL_ROUTE_STAGED.  Errors: EINVAL. */
+int polymul_server_set_route(polymul_server *srv, uint32_t route);
 /* *done = 1 once the result is in req->c (the ticket is then released).  A
  * request that failed releases its ticket and returns its error: ETIMEOUT
  * when a bounded device wait of its kernel expired (c is invalid), ECUDA for

@@ -868,11 +868,7 @@ extern "C" int polymul_plan_status(polymul_plan* p, void* stream) {
   return fail(POLYMUL_ETIMEOUT, "a device wait expired; results of the affected launches are invalid");
 }
 
-namespace {
-
-// The device address of [x, x + bytes) when the whole range is page-locked
-// host memory that the device maps (both ends checked), else null.
-void* mapped_host_range(const void* x, size_t bytes) {
+void* pm::mapped_host_range(const void* x, size_t bytes) {
   cudaPointerAttributes lo, hi;
   if (cudaPointerGetAttributes(&lo, x) != cudaSuccess) {
     cudaGetLastError();
@@ -886,6 +882,8 @@ void* mapped_host_range(const void* x, size_t bytes) {
   if (hi.type != cudaMemoryTypeHost || (char*)hi.devicePointer != (char*)lo.devicePointer + (bytes - 1)) return nullptr;
   return lo.devicePointer;
 }
+
+namespace {
 
 // The batch kernel in its direct form for the plan's word size and degree
 // (looked up and sized once per plan): false when none applies.

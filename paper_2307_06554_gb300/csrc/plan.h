@@ -97,6 +97,9 @@ extern "C" int polymul_tune(polymul_plan* plan, uint64_t batch, void* stream);
 
 namespace pm {
 int launch_batch(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, cudaStream_t st, int slot);
+// The device address of [x, x + bytes) when the whole range is page-locked
+// host memory that the device maps (both ends checked), else null.
+void* mapped_host_range(const void* x, size_t bytes);
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 void clear_error();

@@ -16,8 +16,12 @@
 // releasing their memory to the next admissions.  Work of different requests
 // overlaps on the device (lanes are independent streams), and copies of one
 // request overlap kernels of others (Sec. 4, "optimizing computation and
-// I/O" (ii)).  Latency is taken from submission to the moment the server
-// observes completion.
+// I/O" (ii)).  A request whose a, b and c lie in page-locked host memory the
+// device maps takes the direct route instead: its kernel loads a and b and
+// stores c in host memory itself over the coherent host link, with no arena
+// memory, copy or copy stream (the batch kernel's direct form below 2^14;
+// the cluster kernels load and store with plain accesses already).  Latency
+// is taken from submission to the moment the server observes completion.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,6 +70,13 @@ struct ServeReq {
   int lane = 0;
   int slot = -1;  // page-locked word that receives the lane's error word after the kernel
   bool tensor = false;  // runs on the tensor path (decided at submission)
+  // direct route (decided at submission): a, b, c are mapped page-locked
+  // host memory, read and written in place at these device addresses
+  bool direct = false;
+  const void* da = nullptr;
+  const void* db = nullptr;
+  void* dc = nullptr;
+  size_t weight = 0;  // bytes the request moves (lane balancing)
   cudaEvent_t ev = nullptr;     // the result is in host memory (end of the copy-out stage)
   cudaEvent_t ev_in = nullptr;  // operands are on the device (end of the copy-in stage)
   cudaEvent_t ev_k = nullptr;   // the kernel is done
@@ -81,6 +92,11 @@ struct polymul_server {
   void* d_pc = nullptr;  // PrimeConst<uint64_t>[pool][17]
   KernelInfo ki[kServeMaxLog + 1];
   int grid_cap[kServeMaxLog + 1] = {};
+  // the direct route's kernel per degree: the batch kernel's direct form
+  // below 2^14, the cluster kernel (ki) from there
+  KernelInfo dki[kServeMaxLog + 1];
+  int dgrid_cap[kServeMaxLog + 1] = {};
+  std::atomic<int> staged{0};  // polymul_server_set_route: 1 keeps every request on copies
   // the tensor path (polymul_server_set_path): the 64-bit-word digit kernel
   // per degree 2^10 .. n_max and the pool's digit-weight constants, set up
   // once by the first switch; `tensor` is read by the server thread at issue
@@ -123,7 +139,7 @@ struct polymul_server {
   std::vector<double> latencies_us, queue_us, service_us;
   double issue_s = 0, loop_busy_s = 0;  // server-thread time issuing requests, and in passes that did work
   uint64_t issued = 0;
-  uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0;
+  uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0, completed_direct = 0;
   size_t published_inflight = 0, published_pending = 0;
   // owned by the server thread alone (no lock): requests taken from the
   // queue and not yet admitted, the requests in flight on each lane in issue
@@ -199,8 +215,69 @@ cudaError_t finish_issue(polymul_server* s, ServeReq* r, uint64_t* dc, size_t ro
   return cudaEventRecord(r->ev, st_out);
 }
 
+// one launch of an NTT kernel over `units` units on stream st: a cluster
+// launch for the cluster kernels, else a persistent grid of at most `cap`
+cudaError_t launch_ntt(const KernelInfo& ki, int cap, uint32_t units, void** argv, cudaStream_t st) {
+  if (ki.cluster > 0) {
+    const int clusters = std::min<int>((int)units, cap / ki.cluster);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = ki.cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(clusters * ki.cluster);
+    cfg.blockDim = dim3(ki.block);
+    cfg.dynamicSmemBytes = ki.smem;
+    cfg.stream = st;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, ki.fn, argv);
+  }
+  const int grid = std::min<int>((int)((units + ki.units_per_cta - 1) / ki.units_per_cta), cap);
+  return cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st);
+}
+
+// The prime map rides in the launch's arguments when it fits (up to 32
+// primes of a pool of at most 256), else it is copied to the arena.
+bool inline_map(const polymul_server* s, uint32_t k) { return k <= 32 && s->pool.size() <= 256; }
+
+// direct route: the kernel on the lane's kernel stream reads a and b and
+// writes c in host memory; then its error word and the completion event
+// (server thread)
+cudaError_t issue_direct(polymul_server* s, ServeReq* r) {
+  cudaStream_t st = s->lanes[r->lane];
+  cudaError_t e;
+  uint32_t* dmap = nullptr;
+  if (!inline_map(s, r->k)) {
+    dmap = reinterpret_cast<uint32_t*>(s->d_arena + r->off);
+    uint32_t* hmap = s->h_map + (size_t)r->slot * s->pool.size();
+    std::copy(r->primes.begin(), r->primes.end(), hmap);
+    if ((e = cudaMemcpyAsync(dmap, hmap, r->k * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  }
+  int* lane_err = s->d_err + r->lane;
+  int* err = s->d_err_mapped ? s->d_err_mapped + r->slot : lane_err;
+  NttBatchArgs<uint64_t> args{(const uint64_t*)r->da, (const uint64_t*)r->db, (uint64_t*)r->dc, s->d_twf, s->d_twi,
+                              (const PrimeConst<uint64_t>*)s->d_pc, r->k, r->k, s->d_ctr + 2 * r->lane, err,
+                              nullptr, dmap, s->nmax, (uint32_t)(kServeMaxLog + 1), r->logn, 0u, 0u, 0u};
+  if (!dmap) {
+    args.pmap_inline = 1;
+    for (uint32_t i = 0; i < r->k; ++i) args.pmap_pack[i >> 2] |= r->primes[i] << (8 * (i & 3));
+  }
+  void* argv[] = {&args};
+  if ((e = launch_ntt(s->dki[r->logn], s->dgrid_cap[r->logn], r->k, argv, st)) != cudaSuccess) return e;
+  if (!s->d_err_mapped) {
+    if ((e = cudaMemcpyAsync(s->h_err + r->slot, lane_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemsetAsync(lane_err, 0, sizeof(int), st)) != cudaSuccess) return e;
+  }
+  return cudaEventRecord(r->ev, st);
+}
+
 // issue copy-in, kernel, copy-out and the completion event (server thread)
 cudaError_t issue(polymul_server* s, ServeReq* r) {
+  if (r->direct) return issue_direct(s, r);
   const size_t row = (size_t)r->k * r->n * 8;
   const size_t rowa = (row + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
   char* base = s->d_arena + r->off;
@@ -210,9 +287,7 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
   uint32_t* dmap = reinterpret_cast<uint32_t*>(base + 3 * rowa);
   cudaStream_t st = s->lanes[r->lane], st_in = s->lanes_in[r->lane], st_out = s->lanes_out[r->lane];
   cudaError_t e;
-  // the prime map rides in the launch's arguments when it fits (up to 32
-  // primes of a pool of at most 256), else it is copied to the arena
-  const bool inline_map = r->k <= 32 && s->pool.size() <= 256;
+  const bool inline_map = ::inline_map(s, r->k);
   if (!inline_map) {
     uint32_t* hmap = s->h_map + (size_t)r->slot * s->pool.size();
     std::copy(r->primes.begin(), r->primes.end(), hmap);
@@ -253,26 +328,7 @@ cudaError_t issue(polymul_server* s, ServeReq* r) {
     for (uint32_t i = 0; i < r->k; ++i) args.pmap_pack[i >> 2] |= r->primes[i] << (8 * (i & 3));
   }
   void* argv[] = {&args};
-  if (ki.cluster > 0) {
-    const int clusters = std::min<int>((int)r->k, s->grid_cap[r->logn] / ki.cluster);
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof cfg);
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = ki.cluster;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.gridDim = dim3(clusters * ki.cluster);
-    cfg.blockDim = dim3(ki.block);
-    cfg.dynamicSmemBytes = ki.smem;
-    cfg.stream = st;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    if ((e = cudaLaunchKernelExC(&cfg, ki.fn, argv)) != cudaSuccess) return e;
-  } else {
-    const int grid = std::min<int>((int)((r->k + ki.units_per_cta - 1) / ki.units_per_cta), s->grid_cap[r->logn]);
-    if ((e = cudaLaunchKernel(ki.fn, grid, ki.block, argv, ki.smem, st)) != cudaSuccess) return e;
-  }
+  if ((e = launch_ntt(ki, s->grid_cap[r->logn], r->k, argv, st)) != cudaSuccess) return e;
   return finish_issue(s, r, dc, row, lane_err);
 }
 
@@ -337,8 +393,8 @@ void server_loop(polymul_server* s) {
         }
         s->free_slots.push_back(r->slot);
         r->slot = -1;
-        arena_free(s, r->off, r->bytes);
-        s->lane_bytes[r->lane] -= r->bytes;
+        if (r->bytes) arena_free(s, r->off, r->bytes);
+        s->lane_bytes[r->lane] -= r->weight;
         release_events(s, r);
         f.pop_front();
         --s->inflight;
@@ -348,7 +404,7 @@ void server_loop(polymul_server* s) {
     // admit in arrival order while memory and slots allow
     while (!s->pending.empty() && s->inflight < s->max_inflight) {
       ServeReq* r = s->pending.front();
-      const size_t off = arena_alloc(s, r->bytes);
+      const size_t off = r->bytes ? arena_alloc(s, r->bytes) : 0;  // a direct request may need none
       if (off == (size_t)-1) break;
       r->off = off;
       // the lane with the least work in flight: a small request does not
@@ -357,7 +413,7 @@ void server_loop(polymul_server* s) {
       for (int l = 1; l < s->nlanes; ++l)
         if (s->lane_bytes[l] < s->lane_bytes[lane]) lane = l;
       r->lane = lane;
-      s->lane_bytes[lane] += r->bytes;
+      s->lane_bytes[lane] += r->weight;
       take_events(s, r);
       r->slot = s->free_slots.back();  // fewer than max_inflight requests are in flight
       s->free_slots.pop_back();
@@ -374,8 +430,8 @@ void server_loop(polymul_server* s) {
         r->t_done = now_s();
         s->free_slots.push_back(r->slot);
         r->slot = -1;
-        arena_free(s, r->off, r->bytes);
-        s->lane_bytes[r->lane] -= r->bytes;
+        if (r->bytes) arena_free(s, r->off, r->bytes);
+        s->lane_bytes[r->lane] -= r->weight;
         release_events(s, r);
         done.push_back(r);
       } else {
@@ -392,6 +448,7 @@ void server_loop(polymul_server* s) {
       for (ServeReq* r : done) {
         r->state = r->outcome;
         if (r->outcome == 2) {
+          if (r->direct) ++s->completed_direct;
           s->latencies_us.push_back((r->t_done - r->t_submit) * 1e6);
           s->queue_us.push_back((r->t_admit - r->t_submit) * 1e6);
           s->service_us.push_back((r->t_done - r->t_admit) * 1e6);
@@ -589,6 +646,19 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
     }
     s->ki[logn] = ki;
     s->grid_cap[logn] = cap;
+    s->dki[logn] = ki;  // the cluster kernels read and write with plain accesses
+    s->dgrid_cap[logn] = cap;
+    KernelInfo dk;
+    if (ki.cluster == 0 && lookup_ntt_direct_u64(logn, &dk)) {
+      if (dk.smem > 48 * 1024 &&
+          cudaFuncSetAttribute(dk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dk.smem) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "smem attribute"));
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dk.fn, dk.block, dk.smem) != cudaSuccess || per_sm < 1)
+        return bail(fail(POLYMUL_ENOTSUP, "direct kernel for n=2^%d does not fit", logn));
+      s->dki[logn] = dk;
+      s->dgrid_cap[logn] = per_sm * s->num_sms;
+    }
   }
   for (auto* v : {&s->lanes_in, &s->lanes, &s->lanes_out})
     for (uint32_t l = 0; l < lanes; ++l) {
@@ -624,6 +694,19 @@ extern "C" int polymul_server_submit(polymul_server* s, const polymul_request* q
   r->hb = q->b;
   r->hc = q->c;
   r->bytes = bytes;
+  r->weight = bytes;
+  const size_t row = (size_t)q->k * q->n * 8;
+  if (!r->tensor && s->staged.load(std::memory_order_acquire) == 0 &&
+      (((uintptr_t)q->a | (uintptr_t)q->b | (uintptr_t)q->c) & 7) == 0) {
+    r->da = mapped_host_range(q->a, row);
+    r->db = r->da ? mapped_host_range(q->b, row) : nullptr;
+    r->dc = r->db ? mapped_host_range(q->c, row) : nullptr;
+    if (r->dc) {
+      r->direct = true;
+      r->bytes = inline_map(s, q->k) ? 0 : kArenaAlign;  // arena only for a map that does not fit the arguments
+      r->weight = 3 * row;
+    }
+  }
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lock(s->mu);
@@ -706,6 +789,18 @@ extern "C" int polymul_server_set_path(polymul_server* s, uint32_t path) {
     s->tensor_ready = true;
   }
   s->tensor.store(1, std::memory_order_release);
+  return POLYMUL_OK;
+}
+
+// Requests submitted after this call: POLYMUL_ROUTE_DIRECT (the default:
+// operands in mapped page-locked host memory are read and written in place)
+// or POLYMUL_ROUTE_STAGED (always copies through the arena).
+extern "C" int polymul_server_set_route(polymul_server* s, uint32_t route) {
+  clear_error();
+  if (!s) return fail(POLYMUL_EINVAL, "server is NULL");
+  if (route != POLYMUL_ROUTE_DIRECT && route != POLYMUL_ROUTE_STAGED)
+    return fail(POLYMUL_EINVAL, "route=%u must be POLYMUL_ROUTE_DIRECT or POLYMUL_ROUTE_STAGED", route);
+  s->staged.store(route == POLYMUL_ROUTE_STAGED ? 1 : 0, std::memory_order_release);
   return POLYMUL_OK;
 }
 
@@ -799,6 +894,7 @@ extern "C" int polymul_server_stats_get(polymul_server* s, polymul_server_stats*
     out->service_p50_us = pct(s->service_us, 0.50);
     out->service_p99_us = pct(s->service_us, 0.99);
   }
+  out->completed_direct = s->completed_direct;
   out->issue_us_mean = s->issued ? s->issue_s / s->issued * 1e6 : 0.0;
   out->server_busy_s = s->loop_busy_s;
   if (reset) {
@@ -807,7 +903,7 @@ extern "C" int polymul_server_stats_get(polymul_server* s, polymul_server_stats*
     s->service_us.clear();
     s->issue_s = s->loop_busy_s = 0;
     s->issued = 0;
-    s->completed = s->submitted = s->failed = 0;
+    s->completed = s->submitted = s->failed = s->completed_direct = 0;
     s->arena_peak = s->arena_used;
   }
   return POLYMUL_OK;

@@ -32,6 +32,8 @@ FLAG_CYCLIC = 4  # the ring Z_q[x]/(x^n-1) instead of Z_q[x]/(x^n+1)
 FLAG_TERNARY_B = 8  # b in {0, 1, q-1}: the tensor path takes b as one digit (c = b * T(a))
 FLAG_OVERLAP = 16  # a batch may start while the previous batch launch on its stream drains
 FLAG_HOST_STAGED = 32  # polymul_batch_host always copies through device staging buffers
+ROUTE_DIRECT = 0  # server: mapped page-locked operands read and written in place (default)
+ROUTE_STAGED = 1  # server: always copy through device memory
 
 _ERRNAMES = {1: "EINVAL", 2: "ENOTSUP", 3: "EDOMAIN", 4: "ENOMEM", 5: "ETIMEOUT", 6: "ECUDA"}
 
@@ -77,7 +79,8 @@ class polymul_server_stats(ctypes.Structure):
                                                "arena_bytes", "arena_peak_bytes")] + \
                [(x, ctypes.c_double) for x in ("p50_us", "p99_us", "mean_us", "max_us", "queue_p50_us",
                                                "queue_p99_us", "service_p50_us", "service_p99_us", "issue_us_mean",
-                                               "server_busy_s")]
+                                               "server_busy_s")] + \
+               [("completed_direct", ctypes.c_uint64)]
 
 
 def library_path() -> str:
@@ -150,6 +153,8 @@ def _load():
     lib.polymul_server_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int)]
     lib.polymul_server_set_path.restype = ctypes.c_int
     lib.polymul_server_set_path.argtypes = [vp, u32]
+    lib.polymul_server_set_route.restype = ctypes.c_int
+    lib.polymul_server_set_route.argtypes = [vp, u32]
     lib.polymul_server_poll.restype = i32
     lib.polymul_server_wait.argtypes = [vp, u64, ctypes.c_double]
     lib.polymul_server_wait.restype = i32
@@ -496,7 +501,8 @@ class Server:
         self.handle = out.value
         self._keep = {}
 
-    def _req(self, n, prime_idx, a, b, c):
+    @staticmethod
+    def _req(n, prime_idx, a, b, c):
         idx = (ctypes.c_uint32 * len(prime_idx))(*[int(x) for x in prime_idx])
         r = polymul_request(n, len(prime_idx), idx, _ptr(a), _ptr(b), _ptr(c))
         return r, idx
@@ -511,6 +517,11 @@ class Server:
         """Path of the requests submitted from now on (PATH_NTT or PATH_TENSOR)."""
         _check(_lib.polymul_server_set_path(self.handle, path))
 
+    def set_route(self, route: int) -> None:
+        """Host route of the requests submitted from now on (ROUTE_DIRECT or
+        ROUTE_STAGED)."""
+        _check(_lib.polymul_server_set_route(self.handle, route))
+
     def poll(self, ticket: int) -> bool:
         d = ctypes.c_int()
         _check(_lib.polymul_server_poll(self.handle, ticket, ctypes.byref(d)))
@@ -519,15 +530,24 @@ class Server:
     def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
         _check(_lib.polymul_server_wait(self.handle, ticket, timeout_s))
 
-    def replay(self, requests, arrival_s):
-        """requests: (n, prime_idx, a, b, c) tuples; returns latencies (us)."""
+    @staticmethod
+    def prepare(requests):
+        """The request array of a replay, built once: (n, prime_idx, a, b, c)
+        tuples marshalled into polymul_request structures (the operands are
+        referenced, not copied)."""
         m = len(requests)
         arr = (polymul_request * max(1, m))()
         keep = []
         for i, (n, idx, a, b, c) in enumerate(requests):
-            r, ix = self._req(n, idx, a, b, c)
+            r, ix = Server._req(n, idx, a, b, c)
             arr[i] = r
             keep.append(ix)
+        return (arr, m, keep)
+
+    def replay(self, requests, arrival_s):
+        """requests: (n, prime_idx, a, b, c) tuples, or what prepare()
+        returned for them; returns latencies (us)."""
+        arr, m, _keep = requests if isinstance(requests, tuple) else self.prepare(requests)
         times = (ctypes.c_double * max(1, m))(*[float(x) for x in arrival_s])
         lat = (ctypes.c_double * max(1, m))()
         _check(_lib.polymul_server_replay(self.handle, arr, m, times, lat))

@@ -71,4 +71,5 @@ def test_null_handles_of_lists_and_servers(lib):
     assert L.polymul_ragged_status(None, None) == lib.POLYMUL_EINVAL
     assert L.polymul_ragged_run(None, None, None, None, None) == lib.POLYMUL_EINVAL
     assert L.polymul_server_set_path(None, lib.PATH_TENSOR) == lib.POLYMUL_EINVAL
+    assert L.polymul_server_set_route(None, lib.ROUTE_STAGED) == lib.POLYMUL_EINVAL
     assert L.polymul_plan_select(None, 0) == lib.POLYMUL_EINVAL

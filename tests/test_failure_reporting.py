@@ -74,6 +74,7 @@ def test_server_request_with_expired_wait_fails(pm):
     pool = wl.draw_primes(rng, 4, 59, 59, 14)
     n, lanes = 4096, 4
     with pm.Server(pool, 8192, device_bytes=256 << 20, lanes=lanes) as srv:
+        srv.set_route(pm.ROUTE_STAGED)  # the injected expiry needs the kernel's copy waits
         a, b = _operands(12, 1, [pool[0], pool[2]], n, np.uint64)
         a, b = a[0], b[0]
         ha = torch.from_numpy(a.view(np.int64).copy()).pin_memory()

@@ -82,6 +82,56 @@ def test_alone_equals_in_the_mix(pm, pool):
         n, idx, a, b = reqs[i]
         _oracle_check(pool, n, idx, a, b, mix[i], seed=i)
     assert st["completed"] == 2 * len(reqs) and st["failed"] == 0
+    # alone: c pageable, so copied; in the mix: every buffer page-locked, so
+    # read and written in place
+    assert st["completed_direct"] == len(reqs)
+
+
+@pytest.mark.parametrize("route", ["direct", "staged"])
+def test_routes_agree_at_every_degree(pm, route):
+    """Degrees 2^4 .. 2^16 (the batch kernel's warp and CTA teams, the
+    cluster kernels) and requests of more primes than the launch arguments
+    carry (36 of a pool of 40: the prime map goes through the arena): the
+    direct route (page-locked a, b, c read and written in place) and the
+    staged one give the oracle's products."""
+    rng = np.random.default_rng(91)
+    pool40 = wl.draw_primes(rng, 40, 59, 59, 17)
+    cases = []
+    for n, k in ((16, 3), (256, 5), (2048, 36), (4096, 2), (16384, 3), (32768, 2), (65536, 1), (1024, 36)):
+        idx = sorted(int(x) for x in rng.choice(40, size=k, replace=False))
+        a = np.stack([rng.integers(0, pool40[i], size=n, dtype=np.uint64) for i in idx])
+        b = np.stack([rng.integers(0, pool40[i], size=n, dtype=np.uint64) for i in idx])
+        cases.append((n, idx, _pinned(a), _pinned(b), _pinned(np.zeros_like(a))))
+    with pm.Server(pool40, 65536, device_bytes=1 << 30, lanes=4) as srv:
+        if route == "staged":
+            srv.set_route(pm.ROUTE_STAGED)
+        tickets = [srv.submit(n, idx, a, b, c) for n, idx, a, b, c in cases]
+        for t in tickets:
+            srv.wait(t)
+        st = srv.stats()
+    assert st["completed"] == len(cases) and st["failed"] == 0
+    assert st["completed_direct"] == (len(cases) if route == "direct" else 0)
+    for i, (n, idx, a, b, c) in enumerate(cases):
+        _oracle_check(pool40, n, idx, a, b, c, seed=300 + i)
+
+
+def test_pageable_operands_are_copied(pm, pool):
+    """A request with any pageable buffer is copied whatever the route."""
+    reqs = _requests(pool, 4, seed=74, kmax=3, degrees=(4096, 16384))
+    with pm.Server(pool, 16384, device_bytes=1 << 28, lanes=2) as srv:
+        outs = []
+        for i, (n, idx, a, b) in enumerate(reqs):
+            # request 0 all page-locked; 1, 2, 3 with a pageable a, c or b
+            # (kept referenced until the request completes)
+            xa = a.copy() if i == 1 else a
+            xb = b.copy() if i == 3 else b
+            c = np.zeros_like(a) if i == 2 else _pinned(np.zeros_like(a))
+            srv.wait(srv.submit(n, idx, xa, xb, c))
+            outs.append(c)
+        st = srv.stats()
+    assert st["completed"] == 4 and st["completed_direct"] == 1
+    for i, (n, idx, a, b) in enumerate(reqs):
+        _oracle_check(pool, n, idx, a, b, outs[i], seed=400 + i)
 
 
 def test_admission_by_device_memory(pm, pool):
