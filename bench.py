@@ -162,6 +162,31 @@ def _case_homogeneous(n, q_list, batch, path, launches, seed=7, flags=0, tensor_
             "block": info["block"], "smem_bytes": info["smem_bytes"], "sets": nsets}
 
 
+def _case_mapped(n, q_list, batch, launches, seed=7):
+    """polymul_batch_mapped on page-locked host buffers (the direct form of
+    the batch kernel), launches back to back on one stream over host sets
+    rotated beyond L2."""
+    import torch
+    from paper_2307_06554_gb300 import polymul, workloads as wl
+    rng = np.random.default_rng(seed)
+    a = wl.uniform_coeffs(rng, batch, q_list, n)
+    b = wl.uniform_coeffs(rng, batch, q_list, n)
+    view = np.int32 if a.dtype == np.uint32 else np.int64
+    nsets = max(1, math.ceil(1.5 * L2_BYTES / (3 * a.nbytes)))
+    sets = [(torch.from_numpy(np.roll(a, s, axis=0).view(view)).pin_memory(),
+             torch.from_numpy(np.roll(b, s, axis=0).view(view)).pin_memory(),
+             torch.empty(a.shape, dtype=torch.int32 if view is np.int32 else torch.int64).pin_memory())
+            for s in range(nsets)]
+    stream = torch.cuda.Stream()
+    with polymul.Plan(n, q_list, flags=polymul.FLAG_OVERLAP) as plan:
+        for i in range(launches):
+            x, y, z = sets[i % nsets]
+            polymul.polymul_batch_mapped(plan.handle, x, y, z, batch, stream.cuda_stream)
+        stream.synchronize()
+        polymul.polymul_plan_status(plan.handle, stream.cuda_stream)
+    return {"n": n, "k": len(q_list), "batch": batch, "launches": launches, "sets": nsets}
+
+
 def _case_ragged(count, launches):
     import torch
     from paper_2307_06554_gb300 import polymul, workloads as wl
@@ -414,6 +439,8 @@ def _case(name, launches):
         return _case_host_link()
     if name == "ntt_ring1024":
         return _case_homogeneous(1024, [12289], 4096, polymul.PATH_NTT, launches)
+    if name == "mapped_ring1024":
+        return _case_mapped(1024, [12289], 4096, launches)
     if name == "ntt_ring1024_overlap":
         return _case_homogeneous(1024, [12289], 4096, polymul.PATH_NTT, launches, flags=polymul.FLAG_OVERLAP)
     if name == "tensor_ring1024":
@@ -445,6 +472,7 @@ CASES = {
     "host_link": "host-link microbenchmark: copy engines and SM loads/stores on mapped page-locked memory",
     "ntt_ring1024": "n = 1024, q = 12289, 4096 products (path a, default kernel)",
     "ntt_ring1024_overlap": "the same with POLYMUL_FLAG_OVERLAP",
+    "mapped_ring1024": "the same batch from page-locked host buffers through polymul_batch_mapped (direct form)",
     "tensor_ring1024": "the same batch through the Toeplitz tensor-core path",
     "tensor_rns4096": "n = 4096, 8 primes of 30 bits, 64 products on the tiled tensor kernel",
     "tensor_rns4096_pipelined": "the same on the warp-specialised pipeline form of the drained kernel",

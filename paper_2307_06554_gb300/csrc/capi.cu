@@ -902,7 +902,12 @@ bool direct_kernel(polymul_plan* p) {
     cudaGetLastError();
     return false;
   }
-  p->dgrid_cap = per_sm * p->num_sms;
+  // one CTA per SM: the link, not the SMs, bounds this kernel, and a shallow
+  // queue of loads (one unit per CTA, 8 KB and more per SM in flight) ends
+  // each launch sooner than a full one (n = 1024, 4096 products, back to
+  // back: 174 us per batch at 1 CTA per SM, 179 / 182 / 189 at 2 / 3 / 4,
+  // 188 at the occupancy limit of 10)
+  p->dgrid_cap = p->num_sms;
   p->dki = ki;
   return true;
 }

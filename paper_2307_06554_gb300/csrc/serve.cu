@@ -657,7 +657,7 @@ extern "C" int polymul_server_create(const uint64_t* pool, uint32_t pool_size, u
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dk.fn, dk.block, dk.smem) != cudaSuccess || per_sm < 1)
         return bail(fail(POLYMUL_ENOTSUP, "direct kernel for n=2^%d does not fit", logn));
       s->dki[logn] = dk;
-      s->dgrid_cap[logn] = per_sm * s->num_sms;
+      s->dgrid_cap[logn] = s->num_sms;  // one CTA per SM, as for polymul_batch_mapped
     }
   }
   for (auto* v : {&s->lanes_in, &s->lanes, &s->lanes_out})
