@@ -1490,6 +1490,15 @@ def run_ours(args, ws, rank, local):
     staged_plan.close()
     clk = clocks.stop()
     link = _host_link(dev, 2 * batch * n * elem, batch * n * elem)  # a and b in, c out
+    if ws == 1 and rank == 0:
+        # the SM-driven ceiling of the direct routes, measured now: loads and
+        # stores on mapped page-locked memory mixed 2:1 (the host-link probe)
+        try:
+            probe = {r["op"]: r["GBs"] for r in _case_host_link()["results"]}
+            link["sm_mix_2in_1out_GBs"] = probe["sm_mix_2in_1out"]
+            link["sm_probe"] = "bench.py --case host_link, run inside this bench"
+        except Exception as exc:  # no compiler on the GPU machine: the copy-engine figures stand alone
+            link["sm_probe_error"] = str(exc)[:200]
 
     # sampled products of the timed batch, checked by the CPU oracle leg
     samples = Samples()
@@ -1562,6 +1571,9 @@ def run_ours(args, ws, rank, local):
         extras["crossover"] = crossover(dev, stream, peaks, alu_peak, samples)
         extras["shared_operand"] = shared_operand(dev, stream, peaks, samples)
         extras["serve_20k"] = serving(dev, peaks, samples)
+        if link.get("sm_mix_2in_1out_GBs"):
+            sat = extras["serve_20k"]["saturated"]
+            sat["host_link_frac_of_sm_mix"] = sat["host_link_GBs"] / link["sm_mix_2in_1out_GBs"]
 
     # CPU oracle leg: its throughput (the CPU baseline) and its verdict on
     # the sampled GPU outputs; skipped with --no-cpu-baseline (verdicts null)
@@ -1596,6 +1608,12 @@ def run_ours(args, ws, rank, local):
                    "l2": "inputs rotated over %d buffer sets (%.0f MB > 3x L2)" % (nsets, nsets * set_bytes / 2**20),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": "products/s", "h2d_bytes_per_step": 2 * batch * n * elem,
+                "roofline": ({"bound": "host link", "achieved": 3 * batch * n * elem / (e2e_s / e2e_steps) / 1e9,
+                              "peak": link["sm_mix_2in_1out_GBs"], "unit": "GB/s",
+                              "frac": 3 * batch * n * elem / (e2e_s / e2e_steps) / 1e9 / link["sm_mix_2in_1out_GBs"],
+                              "peak_source": "SM loads and stores on mapped page-locked memory mixed 2:1, "
+                                             "measured in this run"}
+                             if link.get("sm_mix_2in_1out_GBs") else None),
                 "d2h_bytes_per_step": batch * n * elem,
                 "api": "polymul_batch_mapped on page-locked host buffers: the NTT batch kernel loads a, b "
                        "from and stores c to host memory over the host link, so every step moves a and b to "
