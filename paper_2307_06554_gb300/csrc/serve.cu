@@ -682,31 +682,39 @@ extern "C" int polymul_server_submit(polymul_server* s, const polymul_request* q
   if (!q->a || !q->b || !q->c) return fail(POLYMUL_EINVAL, "null operand pointer");
   for (uint32_t i = 0; i < q->k; ++i)
     if (q->prime_idx[i] >= s->pool.size()) return fail(POLYMUL_EINVAL, "prime index outside the pool");
-  const size_t bytes = request_bytes(q->n, q->k);
+  // the route: in place when a, b and c are mapped page-locked memory (no
+  // arena but for a prime map that does not fit the launch arguments), else
+  // copies through the arena
+  const bool tensor = s->tensor.load(std::memory_order_acquire) != 0 && q->n >= 1024 &&
+                      s->tgrid_cap[__builtin_ctz(q->n)] > 0;
+  const size_t row = (size_t)q->k * q->n * 8;
+  void *da = nullptr, *db = nullptr, *dc = nullptr;
+  if (!tensor && s->staged.load(std::memory_order_acquire) == 0 &&
+      (((uintptr_t)q->a | (uintptr_t)q->b | (uintptr_t)q->c) & 7) == 0) {
+    da = mapped_host_range(q->a, row);
+    db = da ? mapped_host_range(q->b, row) : nullptr;
+    dc = db ? mapped_host_range(q->c, row) : nullptr;
+  }
+  const bool direct = dc != nullptr;
+  const size_t bytes = !direct ? request_bytes(q->n, q->k)
+                       : inline_map(s, q->k) ? 0
+                                             : ((size_t)q->k * 4 + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
   if (bytes > s->arena_bytes) return fail(POLYMUL_EINVAL, "request larger than the server's device memory");
   ServeReq* r = new ServeReq();
   r->n = q->n;
   r->k = q->k;
   r->logn = (uint32_t)__builtin_ctz(q->n);
-  r->tensor = s->tensor.load(std::memory_order_acquire) != 0 && r->logn >= 10 && s->tgrid_cap[r->logn] > 0;
+  r->tensor = tensor;
   r->primes.assign(q->prime_idx, q->prime_idx + q->k);
   r->ha = q->a;
   r->hb = q->b;
   r->hc = q->c;
+  r->direct = direct;
+  r->da = da;
+  r->db = db;
+  r->dc = dc;
   r->bytes = bytes;
-  r->weight = bytes;
-  const size_t row = (size_t)q->k * q->n * 8;
-  if (!r->tensor && s->staged.load(std::memory_order_acquire) == 0 &&
-      (((uintptr_t)q->a | (uintptr_t)q->b | (uintptr_t)q->c) & 7) == 0) {
-    r->da = mapped_host_range(q->a, row);
-    r->db = r->da ? mapped_host_range(q->b, row) : nullptr;
-    r->dc = r->db ? mapped_host_range(q->c, row) : nullptr;
-    if (r->dc) {
-      r->direct = true;
-      r->bytes = inline_map(s, q->k) ? 0 : kArenaAlign;  // arena only for a map that does not fit the arguments
-      r->weight = 3 * row;
-    }
-  }
+  r->weight = direct ? 3 * row : bytes;
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lock(s->mu);

@@ -176,3 +176,33 @@ def test_submit_rejects_bad_requests(pm, pool):
             assert ei.value.code == pm.POLYMUL_EINVAL
         with pytest.raises(pm.PolymulError):
             srv.wait(12345, 0.01)
+
+
+def test_direct_requests_need_no_arena(pm):
+    """On the direct route a request needs device memory only for a prime
+    map that does not fit the launch arguments: a request larger than the
+    whole arena runs (it would be refused on the staged route), and so does
+    one of 70 primes of an 80-prime pool (its map takes 280 bytes of the
+    arena)."""
+    rng = np.random.default_rng(95)
+    pool80 = wl.draw_primes(rng, 80, 59, 59, 17)
+    n_max = 4096
+    small = 3 * n_max * 8 + (1 << 12)  # about one single-prime request of degree n_max
+    cases = []
+    for n, k in ((4096, 6), (1024, 70)):
+        idx = sorted(int(x) for x in rng.choice(80, size=k, replace=False))
+        a = np.stack([rng.integers(0, pool80[i], size=n, dtype=np.uint64) for i in idx])
+        b = np.stack([rng.integers(0, pool80[i], size=n, dtype=np.uint64) for i in idx])
+        cases.append((n, idx, _pinned(a), _pinned(b), _pinned(np.zeros_like(a))))
+    with pm.Server(pool80, n_max, device_bytes=small, lanes=2) as srv:
+        for n, idx, a, b, c in cases:
+            srv.wait(srv.submit(n, idx, a, b, c))
+        st = srv.stats()
+        assert st["completed_direct"] == 2 and st["arena_peak_bytes"] <= 512
+        srv.set_route(pm.ROUTE_STAGED)
+        n, idx, a, b, c = cases[0]
+        with pytest.raises(pm.PolymulError) as e:
+            srv.submit(n, idx, a, b, c)
+        assert e.value.code == pm.POLYMUL_EINVAL
+    for i, (n, idx, a, b, c) in enumerate(cases):
+        _oracle_check(pool80, n, idx, a, b, c, seed=500 + i)
