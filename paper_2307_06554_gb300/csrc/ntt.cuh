@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(ntt_block<S, WARPS>(), 65536 / (ntt_block<S, W
         nxt = grab();
         if (!DIRECT && lane == 0 && nxt < units) issue(nxt);
       };
-      // an inactive team of the last round reads row 0 (it stores nothing)
+      // an inactive team (past the last unit) reads row 0 and stores nothing
       const size_t row = act ? (size_t)u * S::N : 0;
       polymul_unit_any<S, MODE, AUX, SEQ>(args.c + row, twf + (size_t)pj * args.tw_stride,
                                           twi + (size_t)pj * args.tw_stride, pc, sa, sb,

@@ -64,7 +64,7 @@ def _run_both(pm, n, q_list, a, b, flags=0):
 
 def test_ring_1024_direct_equals_oracle_and_staged(pm):
     """n = 1024, q = 12289 (the unreduced-mode plan): 1000 products, not a
-    multiple of the teams per round."""
+    multiple of the units the teams take at once."""
     n, q_list = 1024, [12289]
     a, b = _case(1, 1000, q_list, n, np.uint32)
     got, staged = _run_both(pm, n, q_list, a, b)
