@@ -885,10 +885,18 @@ void* pm::mapped_host_range(const void* x, size_t bytes) {
 
 namespace {
 
-// The batch kernel in its direct form for the plan's word size and degree
-// (looked up and sized once per plan): false when none applies.
+// The kernel of the direct route for the plan's word size and degree
+// (looked up and sized once per plan): the plan's own thread-block-cluster
+// kernel where it has one (it loads and stores with plain accesses
+// already), else the batch kernel in its direct form; false when neither
+// applies.
 bool direct_kernel(polymul_plan* p) {
   if (p->dki.fn) return true;
+  if (p->ki.cluster > 0) {
+    p->dki = p->ki;
+    p->dgrid_cap = p->grid_cap;
+    return true;
+  }
   KernelInfo ki;
   if (!(p->elem == 4 ? lookup_ntt_direct_u32((int)p->logn, &ki) : lookup_ntt_direct_u64((int)p->logn, &ki)))
     return false;
@@ -937,13 +945,25 @@ static int launch_direct(polymul_plan* p, const void* a, const void* b, void* c,
   fp.b_lo = (uintptr_t)b, fp.b_hi = (uintptr_t)b + bytes;
   fp.c_lo = (uintptr_t)c, fp.c_hi = (uintptr_t)c + bytes;
   StreamOrderGuard order(p->device, st);
-  const uint32_t early = (p->flags & POLYMUL_FLAG_OVERLAP) && order.may_run_ahead(fp) ? 1u : 0u;
+  // the cluster kernels take no dependent launch (their successor starts at
+  // their completion; recording them is harmless)
+  const bool cluster = p->dki.cluster > 0;
+  const uint32_t early = !cluster && (p->flags & POLYMUL_FLAG_OVERLAP) && order.may_run_ahead(fp) ? 1u : 0u;
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof cfg);
   cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr.val.programmaticStreamSerializationAllowed = 1;
-  cfg.gridDim = dim3(grid);
+  if (cluster) {
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = p->dki.cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+  } else {
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+  }
+  cfg.gridDim = dim3(cluster ? (unsigned)(std::min<uint64_t>(units, (uint64_t)(p->dgrid_cap / p->dki.cluster)) *
+                                          p->dki.cluster)
+                             : (unsigned)grid);
   cfg.blockDim = dim3(p->dki.block);
   cfg.dynamicSmemBytes = p->dki.smem;
   cfg.stream = st;
@@ -972,8 +992,7 @@ static int launch_direct(polymul_plan* p, const void* a, const void* b, void* c,
 static int direct_ranges(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, void** da,
                          void** db, void** dc) {
   if (p->path != POLYMUL_PATH_NTT || p->aux_prime || !direct_kernel(p))
-    return fail(POLYMUL_ENOTSUP, "no direct-access kernel for this plan (NTT path on the plan's own primes, "
-                                 "32-bit words up to n = 2^14, 64-bit words up to 2^13)");
+    return fail(POLYMUL_ENOTSUP, "no direct-access kernel for this plan (NTT path on the plan's own primes)");
   if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) % p->elem != 0)
     return fail(POLYMUL_EINVAL, "operands must be aligned to the %u-byte word", p->elem);
   const size_t bytes = (size_t)batch * p->k * p->n * p->elem;

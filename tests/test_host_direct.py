@@ -41,6 +41,18 @@ def _as(t, dtype):
     return t.numpy().view(dtype)
 
 
+def _sampled_check(got, a, b, q_list, what, seed=0):
+    """Degrees where the whole schoolbook product is slow: the first and
+    last coefficient and six random ones of every row, from the oracle."""
+    rng = np.random.default_rng(seed)
+    n = a.shape[-1]
+    for p in range(a.shape[0]):
+        for j, q in enumerate(q_list):
+            js = sorted({0, n - 1, *[int(x) for x in rng.integers(0, n, 6)]})
+            want = native.coeffs(a[p, j], b[p, j], q, js)
+            assert np.array_equal(got[p, j, js].astype(np.uint64), want), "%s product %d prime %d" % (what, p, j)
+
+
 def _direct_calls(plan, pm):
     return pm.polymul_plan_info_get(plan.handle)["host_direct"]
 
@@ -89,17 +101,33 @@ def test_u32_degrees(pm, logn, bits):
     assert_equal_residues(got[idx], native.polymul_batch(a[idx], b[idx], q_list), "n=%d" % n)
 
 
-@pytest.mark.parametrize("logn", [4, 6, 8, 10, 12, 13])
+@pytest.mark.parametrize("logn", [15, 16])
+def test_u32_cluster_degrees(pm, logn):
+    """32-bit words above 2^14: the plan's thread-block-cluster kernel reads
+    and writes the host rows itself."""
+    n = 1 << logn
+    q_list = _primes(200 + logn, 2, 30, n)
+    a, b = _case(logn * 5, 3, q_list, n, np.uint32)
+    got, staged = _run_both(pm, n, q_list, a, b)
+    assert np.array_equal(got, staged)
+    _sampled_check(got, a, b, q_list, "n=%d" % n, seed=logn)
+
+
+@pytest.mark.parametrize("logn", [4, 6, 8, 10, 12, 13, 14, 16])
 def test_u64_degrees(pm, logn):
-    """64-bit words: 59-bit primes, every direct shape family."""
+    """64-bit words: 59-bit primes, every direct shape family and the
+    cluster kernels from 2^14."""
     n = 1 << logn
     q_list = _primes(300 + logn, 2, 59, n)
-    batch = max(3, min(64, (1 << 16) // n))
+    batch = max(2, min(64, (1 << 16) // n))
     a, b = _case(logn * 11, batch, q_list, n, np.uint64)
     got, staged = _run_both(pm, n, q_list, a, b)
     assert np.array_equal(got, staged)
-    idx = sorted({0, batch - 1})
-    assert_equal_residues(got[idx], native.polymul_batch(a[idx], b[idx], q_list), "n=%d" % n)
+    if logn >= 14:
+        _sampled_check(got, a, b, q_list, "n=%d" % n, seed=logn)
+    else:
+        idx = sorted({0, batch - 1})
+        assert_equal_residues(got[idx], native.polymul_batch(a[idx], b[idx], q_list), "n=%d" % n)
 
 
 def test_cyclic_direct(pm):
@@ -241,8 +269,8 @@ def test_mapped_chain_waits_for_its_operand(pm):
 
 
 def test_mapped_rejects_what_it_cannot_read(pm):
-    """Pageable memory, a misaligned row start, a tensor-path plan and a
-    thread-block-cluster degree: EINVAL or ENOTSUP, nothing launched."""
+    """Pageable memory, a misaligned row start and a tensor-path plan:
+    EINVAL or ENOTSUP, nothing launched."""
     import torch
     n, q_list = 1024, [12289]
     a, b = _case(81, 8, q_list, n, np.uint32)
@@ -258,13 +286,6 @@ def test_mapped_rejects_what_it_cannot_read(pm):
     with pm.Plan(n, q_list, path=pm.PATH_TENSOR) as plan:
         with pytest.raises(pm.PolymulError) as e:
             plan.batch_mapped(ta, tb, tc)
-        assert e.value.code == pm.POLYMUL_ENOTSUP
-    n = 32768
-    q_list = _primes(82, 1, 30, n)
-    a, b = _case(83, 1, q_list, n, np.uint32)
-    with pm.Plan(n, q_list) as plan:
-        with pytest.raises(pm.PolymulError) as e:
-            plan.batch_mapped(_pinned(a), _pinned(b), _pinned(np.zeros_like(a)))
         assert e.value.code == pm.POLYMUL_ENOTSUP
 
 
