@@ -73,3 +73,19 @@ def test_null_handles_of_lists_and_servers(lib):
     assert L.polymul_server_set_path(None, lib.PATH_TENSOR) == lib.POLYMUL_EINVAL
     assert L.polymul_server_set_route(None, lib.ROUTE_STAGED) == lib.POLYMUL_EINVAL
     assert L.polymul_plan_select(None, 0) == lib.POLYMUL_EINVAL
+
+
+def test_replay_requests_are_marshalled_once(lib):
+    """Server.prepare builds a replay's request structures ahead of time
+    (outside any timed region): each carries the degree, the prime count,
+    the prime indices and the operands' addresses, and replay accepts the
+    prepared form (host logic only; nothing is submitted here)."""
+    import numpy as np
+    a = np.zeros((3, 64), np.uint64)
+    b = np.ones((3, 64), np.uint64)
+    c = np.empty((3, 64), np.uint64)
+    arr, m, keep = lib.Server.prepare([(64, [0, 5, 9], a, b, c), (64, [2], a[:1], b[:1], c[:1])])
+    assert m == 2 and len(keep) == 2
+    assert (arr[0].n, arr[0].k, arr[1].k) == (64, 3, 1)
+    assert [arr[0].prime_idx[i] for i in range(3)] == [0, 5, 9]
+    assert arr[0].a == a.ctypes.data and arr[0].b == b.ctypes.data and arr[0].c == c.ctypes.data
