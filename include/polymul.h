@@ -279,13 +279,13 @@ int polymul_batch_host(polymul_plan *plan, const void *a, const void *b, void *c
  * read.  POLYMUL_FLAG_OVERLAP lets consecutive batches on a stream overlap
  * as for polymul_batch (below the thread-block-cluster degrees);
  * POLYMUL_FLAG_VALIDATE is honoured (an extra pass over a and b,
- * synchronous).  Needs an NTT plan on its own primes (no auxiliary prime);
- * every degree: the batch kernel's direct form up to n = 2^14 (32-bit
- * words) or 2^13 (64-bit words), the plan's thread-block-cluster kernel
- * above (it reads and writes with plain accesses already).
+ * synchronous).  Needs an NTT-path plan (its own primes or one auxiliary
+ * prime); every degree: the batch kernel's direct form up to n = 2^14
+ * (32-bit words) or 2^13 (64-bit words), the plan's thread-block-cluster
+ * kernel above (it reads and writes with plain accesses already).
  * Errors: EINVAL (null pointers with batch > 0, a range that is not mapped
- * page-locked host memory, misalignment, batch > 2^40), ENOTSUP (another
- * plan), EDOMAIN (validation), ECUDA.
+ * page-locked host memory, misalignment, batch > 2^40), ENOTSUP (a
+ * tensor-path plan), EDOMAIN (validation), ECUDA.
  */
 int polymul_batch_mapped(polymul_plan *plan, const void *a, const void *b, void *c,
                          uint64_t batch, void *stream);

@@ -898,7 +898,10 @@ bool direct_kernel(polymul_plan* p) {
     return true;
   }
   KernelInfo ki;
-  if (!(p->elem == 4 ? lookup_ntt_direct_u32((int)p->logn, &ki) : lookup_ntt_direct_u64((int)p->logn, &ki)))
+  const int logn = (int)p->logn;
+  if (!(p->aux_prime        ? lookup_ntt_direct_aux(logn, &ki)
+        : p->elem == 4 ? lookup_ntt_direct_u32(logn, &ki)
+                       : lookup_ntt_direct_u64(logn, &ki)))
     return false;
   if (ki.smem > 48 * 1024 &&
       cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess) {
@@ -972,7 +975,7 @@ static int launch_direct(polymul_plan* p, const void* a, const void* b, void* c,
   if (p->elem == 4) {
     NttBatchArgs<uint32_t> args{(const uint32_t*)a, (const uint32_t*)b, (uint32_t*)c, p->d_twf, p->d_twi,
                                 (const PrimeConst<uint32_t>*)p->d_pc, units, p->k, ctr, p->d_err,
-                                nullptr, nullptr, p->n, 1, 0, early, 0, 0};
+                                (const uint32_t*)p->d_outer, nullptr, p->n, 1, 0, early, 0, 0};
     void* argv[] = {&args};
     PM_CUDA(cudaLaunchKernelExC(&cfg, p->dki.fn, argv));
   } else {
@@ -991,8 +994,8 @@ static int launch_direct(polymul_plan* p, const void* a, const void* b, void* c,
 // mapped page-locked host memory or is misaligned.
 static int direct_ranges(polymul_plan* p, const void* a, const void* b, void* c, uint64_t batch, void** da,
                          void** db, void** dc) {
-  if (p->path != POLYMUL_PATH_NTT || p->aux_prime || !direct_kernel(p))
-    return fail(POLYMUL_ENOTSUP, "no direct-access kernel for this plan (NTT path on the plan's own primes)");
+  if (p->path != POLYMUL_PATH_NTT || !direct_kernel(p))
+    return fail(POLYMUL_ENOTSUP, "no direct-access kernel for this plan (NTT path only)");
   if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) % p->elem != 0)
     return fail(POLYMUL_EINVAL, "operands must be aligned to the %u-byte word", p->elem);
   const size_t bytes = (size_t)batch * p->k * p->n * p->elem;

@@ -47,6 +47,7 @@ bool lookup_ntt_alt(uint32_t elem, int logn, int mode, KernelInfo* ki);
 // memory the device maps): 32-bit words logn 4..14, 64-bit words logn 4..13
 bool lookup_ntt_direct_u32(int logn, KernelInfo* ki);
 bool lookup_ntt_direct_u64(int logn, KernelInfo* ki);
+bool lookup_ntt_direct_aux(int logn, KernelInfo* ki);  // auxiliary-prime mode, logn 4..14
 
 // shared-operand products on the NTT path: a's transform once per prime
 // (prep), then forward(b), pointwise, inverse per product (32-bit words,

@@ -208,20 +208,18 @@ def test_validate_flag_on_the_direct_route(pm):
         assert e.value.code == pm.POLYMUL_EDOMAIN
 
 
-def test_aux_plans_stage(pm):
-    """An auxiliary-prime plan runs another kernel: its host calls stay
-    staged, and polymul_batch_mapped refuses it."""
-    n, q_aux = 256, [3329]  # 3329 - 1 = 2^8 * 13: no 512-th root of unity
-    a, b = _case(42, 20, q_aux, n, np.uint32)
-    ta, tb, tc = _pinned(a), _pinned(b), _pinned(np.zeros_like(a))
-    with pm.Plan(n, q_aux) as plan:
+@pytest.mark.parametrize("n,q_list", [(256, [3329]), (64, [1000, 3329]), (2048, [97, 193])])
+def test_aux_plans_direct(pm, n, q_list):
+    """Auxiliary-prime plans (moduli without a 2n-th root of unity, n = 256,
+    q = 3329 among them) read and write host rows in place too: the direct
+    form of their kernel (centred lift, one 31-bit NTT prime, reduction mod
+    each q) against the oracle and the staged route."""
+    a, b = _case(42 + n, 20, q_list, n, np.uint32)
+    with pm.Plan(n, q_list) as plan:
         assert plan.info["aux_primes"] == 1
-        plan.batch_host(ta, tb, tc)
-        assert _direct_calls(plan, pm) == 0
-        with pytest.raises(pm.PolymulError) as e:
-            plan.batch_mapped(ta, tb, tc)
-        assert e.value.code == pm.POLYMUL_ENOTSUP
-    assert_equal_residues(_as(tc, np.uint32), native.polymul_batch(a, b, q_aux), "auxiliary prime")
+    got, staged = _run_both(pm, n, q_list, a, b)
+    assert np.array_equal(got, staged)
+    assert_equal_residues(got, native.polymul_batch(a, b, q_list), "auxiliary prime n=%d" % n)
 
 
 @pytest.mark.parametrize("flags", [0, 16])
