@@ -272,7 +272,8 @@ int polymul_batch_host(polymul_plan *plan, const void *a, const void *b, void *c
  * operands cross the link at every call; nothing of them stays on the
  * device.
  *   a, b, c  host pointers (as the device sees them with unified
- *            addressing), [batch][k][n], aligned to the word size.
+ *            addressing), [batch][k][n], aligned to the word size; c
+ *            writable by the device (not registered read-only).
  *   stream   cudaStream_t or NULL.
  * Asynchronous like polymul_batch: c holds the results once `stream` has
  * been synchronised; until then a and b must not change and c must not be

@@ -925,11 +925,12 @@ bool direct_kernel(polymul_plan* p) {
 
 }  // namespace
 
-// The direct form of the batch kernel on host memory the device maps:
-// one launch reads a and b and writes c in place over the coherent host
-// link, so the link carries operands in and results out at the same time
-// with no staging buffer, copy engine or chunk boundary.  a, b, c are the
-// device addresses of the ranges.  Counter slot 2 (its own: a host-buffer
+// The direct route on host memory the device maps: one launch of the batch
+// kernel's direct form (or of the plan's thread-block-cluster kernel) reads
+// a and b and writes c in place over the coherent host link, so the link
+// carries operands in and results out at the same time with no staging
+// buffer, copy engine or chunk boundary.  a, b, c are the device addresses
+// of the ranges.  Counter slot 2 (its own: a host-buffer
 // call may follow device-pointer batches still running on other streams).
 // Like a device-pointer batch the launch is recorded for the stream-order
 // guard and, with POLYMUL_FLAG_OVERLAP, may run ahead of its predecessor.
